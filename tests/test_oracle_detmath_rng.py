@@ -1,0 +1,98 @@
+"""Pins for the oracle's deterministic exponential, kernels and random numbers.
+
+Each check ties the oracle to something outside itself: libm's exp and the
+closed-form kernels, the mathematical definitions of the Philox Weyl
+increments, distribution laws of uniforms / normals / gamma variates
+(scipy.stats), and bit-avalanche behaviour of a 10-round Philox.
+"""
+import math
+from decimal import Decimal, getcontext
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import detmath, rng
+
+
+def test_det_exp_within_one_ulp_of_libm():
+    g = np.random.default_rng(0)
+    x = np.concatenate([-g.uniform(0, 708, 100000), -g.uniform(0, 1, 50000),
+                        -g.uniform(0, 1e-8, 1000), [0.0, -1e-300, -708.0]])
+    y = detmath.det_exp(x)
+    ref = np.array([math.exp(v) for v in x])
+    ulp = np.abs(y - ref) / np.spacing(ref)
+    assert ulp.max() <= 1.0
+
+
+def test_det_exp_special_values():
+    assert detmath.det_exp(np.array([0.0]))[0] == 1.0
+    assert detmath.det_exp(np.array([-708.5, -1e4]))[1] == 0.0
+    # ln2 split: 32 significand bits in the high part, and hi + lo = ln 2 to half an ulp of lo (~1.3e-26)
+    bits = np.float64(detmath.LN2_HI).view(np.uint64)
+    assert int(bits) & ((1 << 21) - 1) == 0
+    getcontext().prec = 50
+    assert abs(Decimal(detmath.LN2_HI) + Decimal(detmath.LN2_LO) - Decimal(2).ln()) < Decimal("2e-26")
+
+
+@pytest.mark.parametrize("kind", [detmath.KERNEL_SE, detmath.KERNEL_MATERN52])
+def test_kernels_match_closed_form(kind):
+    g = np.random.default_rng(1)
+    rho = 0.07
+    c = detmath.kernel_const(kind, rho)
+    xa, xb = g.uniform(0, 1, 2000), g.uniform(0, 1, 2000)
+    got = detmath.kernel_entries(kind, c, xa, xb)
+    d = np.abs(xa - xb)
+    if kind == detmath.KERNEL_SE:
+        ref = np.exp(-d * d / (2 * rho * rho))
+    else:
+        t = math.sqrt(5.0) * d / rho
+        ref = (1 + t + t * t / 3) * np.exp(-t)
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-300)
+    # symmetric in the argument order, bit for bit
+    assert np.array_equal(got, detmath.kernel_entries(kind, c, xb, xa))
+
+
+def test_philox_weyl_increments_from_definition():
+    getcontext().prec = 60
+    phi = (1 + Decimal(5).sqrt()) / 2
+    assert rng.W0 == int((phi - 1) * (1 << 32))
+    assert rng.W1 == int((Decimal(3).sqrt() - 1) * (1 << 32))
+
+
+def test_philox_avalanche():
+    # flipping one counter bit should flip about half of the 128 output bits
+    g = np.random.default_rng(2)
+    ctr = g.integers(0, 2 ** 32, (4000, 4), dtype=np.uint64)
+    base = rng.philox4x32_10(ctr, (123, 456))
+    flips = []
+    for word in range(4):
+        for bit in (0, 13, 31):
+            c2 = ctr.copy()
+            c2[:, word] ^= np.uint64(1 << bit)
+            out = rng.philox4x32_10(c2, (123, 456))
+            x = (base ^ out).astype(np.uint64)
+            nb = sum(np.unpackbits(x[:, w].astype(">u4").view(np.uint8)).reshape(len(x), 32).sum(1) for w in range(4))
+            flips.append(nb.mean())
+    assert all(abs(f - 64.0) < 1.0 for f in flips)
+
+
+def test_uniform_and_normal_laws():
+    z = rng.normals(400000, seed=9, tag=rng.TAG_A, it=3, chain=1)
+    assert abs(z.mean()) < 5 / math.sqrt(len(z))
+    assert abs(z.var() - 1.0) < 5 * math.sqrt(2.0 / len(z))
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    # different streams are independent
+    z2 = rng.normals(400000, seed=9, tag=rng.TAG_B, it=3, chain=1)
+    assert abs(np.corrcoef(z, z2)[0, 1]) < 5 / math.sqrt(len(z))
+    w = rng.philox4x32_10(np.stack([np.arange(200000), np.zeros(200000), np.zeros(200000), np.zeros(200000)], 1), (1, 0))
+    u = rng.uniforms_from_words(w[:, 0], w[:, 1])
+    assert u.min() > 0.0 and u.max() < 1.0
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+
+
+@pytest.mark.parametrize("alpha", [1.0, 2.5, 1025.0])
+def test_gamma_sampler_law(alpha):
+    draws = np.array([rng.gamma_draw(alpha, seed=5, tag=rng.TAG_TAU2, it=t, chain=0)[0] for t in range(4000)])
+    assert stats.kstest(draws, stats.gamma(alpha).cdf).pvalue > 1e-3
+    assert abs(draws.mean() - alpha) < 5 * math.sqrt(alpha / len(draws))
