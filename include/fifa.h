@@ -1,0 +1,217 @@
+/*
+ * fifa.h -- C ABI of the GB300 FIFA-GP Gibbs-step library.
+ *
+ * Method: Moran & Wheeler, "Fast increased fidelity approximate Gibbs samplers
+ * for Bayesian Gaussian process regression" (arXiv 2006.06537).  The library
+ * computes, on one GPU, every step of one Gibbs iteration for 1-D inputs:
+ * HODLR assembly of the kernel matrix (Sec. 3.2), its symmetric factorization
+ * and log-determinant (SI, "HODLR decomposition and factorization",
+ * "Determinant computation speedup"), the solves, matrix-vector products and
+ * factor applications of Algorithm 1 (Sec. 4.1.1), and the conditional draws
+ * of Eqs. (posterior_gibs1)-(posterior_gibs4).
+ *
+ * Model and notation used by every call:
+ *   y = f + e,  e ~ N(0, sigma2 I);   f ~ N(0, tau2 * C(rho))
+ *   C(rho)[a][b] = k(x_a, x_b) + nugget * [a == b]   (unit-variance kernel)
+ *   SE:         k = exp(-(x_a - x_b)^2 / (2 rho^2))
+ *   Matern-5/2: k = (1 + t + t^2/3) exp(-t),  t = sqrt(5) |x_a - x_b| / rho
+ *   C~ is the HODLR approximation of C; M~ = s C~ + I with s = tau2 / sigma2
+ *   (the paper's M = tau K + I with precision tau = 1/sigma2 and K = tau2 C).
+ *
+ * Conventions for all calls:
+ *   - Device pointers ("_dev") are CUDA global-memory addresses on the
+ *     context's device; host pointers ("_host") are ordinary memory.
+ *   - The caller owns every buffer it passes; the library owns the opaque
+ *     objects, which live inside the context's device arena.
+ *   - Calls are asynchronous on the context's stream unless they return a
+ *     value through a _host pointer, in which case they synchronize it.
+ *   - Inputs x must be sorted non-decreasing (Sec. 3.2 sorts 1-D inputs);
+ *     otherwise FIFA_ERR_UNSORTED.  Any n >= 1 is accepted.
+ *   - Device-side failures (a non-positive pivot, a timed-out wait) set a
+ *     status word in the object; the next synchronizing call on it returns it.
+ *   - No C++ exception crosses this boundary.
+ */
+#ifndef FIFA_H
+#define FIFA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FIFA_OK = 0,
+  FIFA_ERR_INVALID_ARG = 1,
+  FIFA_ERR_UNSORTED = 2,
+  FIFA_ERR_NOT_SPD = 3,     /* a Cholesky pivot was not positive (PSD loss, SI "Practical considerations") */
+  FIFA_ERR_RANK_CAP = 4,    /* an ACA block reached the rank cap before the tolerance */
+  FIFA_ERR_OOM = 5,         /* the context arena has no room for the object */
+  FIFA_ERR_CUDA = 6,        /* a CUDA runtime call failed */
+  FIFA_ERR_TIMEOUT = 7,     /* a bounded device-side wait gave up */
+  FIFA_ERR_UNSUPPORTED = 8  /* a size outside what the kernels handle (leaf size, rank cap) */
+} fifa_status;
+
+typedef enum { FIFA_KERNEL_SE = 0, FIFA_KERNEL_MATERN52 = 1 } fifa_kernel;
+typedef enum { FIFA_FP64 = 0, FIFA_MIXED = 1 } fifa_precision;
+
+/* Hyperparameters Theta of Sec. 4.1 in the length-scale form above. */
+typedef struct {
+  int kernel;     /* fifa_kernel */
+  double tau2;    /* signal variance (the paper's sigma_f^2) */
+  double rho;     /* length-scale */
+  double sigma2;  /* noise variance (1 / the paper's precision tau) */
+  double nugget;  /* added to the diagonal of C before construction (Sec. 4.1.4) */
+} fifa_hyper;
+
+/* H-matrix options: Algorithm 1 inputs B (maximum block size) and epsilon. */
+typedef struct {
+  int leaf_size;      /* B: leaves hold at most B points; 1..128 */
+  double aca_tol;     /* absolute max-norm tolerance of every ACA block of C */
+  int rank_cap;       /* maximum ACA rank per block; 1..64 */
+  int prec;           /* fifa_precision: FP64, or MIXED (M~ factor in FP32 + FP64 refinement) */
+  double refine_tol;  /* MIXED: stop refining when ||b - M~ x|| <= refine_tol ||b|| */
+  int refine_max;     /* MIXED: refinement steps captured per solve (fixed; converged steps are no-ops) */
+} fifa_opts;
+
+/* Priors: inverse-gamma IG(shape, scale) on tau2 and sigma2 (the conjugate
+ * forms of Eqs. posterior_gibs2-3), normal prior on log rho with a random-walk
+ * Metropolis step of standard deviation prop_sd (Sec. 4.1, the Metropolis
+ * alternative to the discrete rho grid). */
+typedef struct {
+  double a_tau2, b_tau2, a_sigma2, b_sigma2;
+  double logrho_mu, logrho_sd, prop_sd;
+} fifa_prior;
+
+typedef struct fifa_ctx fifa_ctx;     /* device arena, stream, plans, scratch */
+typedef struct fifa_hmat fifa_hmat;   /* C~ (assembled) or M~ = s C~ + I (a view of a C~) */
+typedef struct fifa_fact fifa_fact;   /* W with W W^T = A, and log det A */
+typedef struct fifa_chain fifa_chain; /* Gibbs chain state resident on the device */
+
+/* Create a context on the current CUDA device.
+ *   cuda_stream: cudaStream_t to launch on (NULL = legacy default stream).
+ *   arena_dev / arena_bytes: device memory the library sub-allocates all its
+ *     objects and scratch from (e.g. a torch uint8 tensor); the caller keeps it
+ *     alive until fifa_destroy_ctx.  arena_dev == NULL: the library allocates
+ *     arena_bytes itself and frees them in fifa_destroy_ctx.
+ * Errors: FIFA_ERR_INVALID_ARG (bad opts), FIFA_ERR_UNSUPPORTED, FIFA_ERR_CUDA. */
+fifa_status fifa_create(fifa_ctx** out, const fifa_opts* opts, void* cuda_stream,
+                        void* arena_dev, size_t arena_bytes);
+void fifa_destroy_ctx(fifa_ctx* ctx);
+
+/* Assemble C~(rho) (Sec. 3.2; Algorithm 1 "Construct"): dense leaves
+ * C(I_i, I_i) + nugget I and, for every non-leaf node, a partial-pivoted ACA
+ * factorization U V^T of its upper off-diagonal block (proof of Lemma 1).
+ * x_dev: n sorted doubles (read during this call's kernels only).
+ * hyper->tau2 and ->sigma2 are not used here.  Errors: INVALID_ARG, UNSORTED,
+ * OOM, CUDA; a block that hits the rank cap sets FIFA_ERR_RANK_CAP as the
+ * object's status (results remain usable, the tolerance is not met there). */
+fifa_status fifa_assemble(fifa_ctx* ctx, const double* x_dev, int64_t n, const fifa_hyper* hyper,
+                          fifa_hmat** out);
+
+/* M~ = s C~ + I (proof of Theorem 4.1: M~ built from K~), as a view that
+ * shares C's storage: leaves s D_i + I, U scaled by s, V shared.  C must
+ * outlive M.  Errors: INVALID_ARG, OOM. */
+fifa_status fifa_shift_scale(fifa_ctx* ctx, const fifa_hmat* C, double s, fifa_hmat** M);
+
+/* Symmetric factorization A = W W^T, W = A_L ... A_0 (SI, Ambikasaran Thm 3.1)
+ * and log det A.  Precision: FP64, or FP32 storage and bulk arithmetic when the
+ * context is MIXED and A is a shift_scale view (the M~ of Algorithm 1); leaf
+ * and capacitance Cholesky factors and the log-determinant stay FP64.
+ * Errors: OOM, CUDA; NOT_SPD is reported through fifa_fact_status/logdet. */
+fifa_status fifa_factor(fifa_ctx* ctx, const fifa_hmat* A, fifa_fact** out);
+
+/* log det A (SI "Determinant computation speedup"); synchronizes.
+ * Returns the factor's device status (FIFA_ERR_NOT_SPD if a pivot failed). */
+fifa_status fifa_logdet(fifa_ctx* ctx, const fifa_fact* F, double* out_host);
+
+/* x = A^-1 b = W^-T W^-1 b for nrhs column-major vectors of length n.
+ * b_dev and x_dev may alias.  For an FP32 factor the solve is refined with
+ * the FP64 operator (see fifa_opts).  Errors: INVALID_ARG. */
+fifa_status fifa_solve(fifa_ctx* ctx, const fifa_fact* F, const double* b_dev, double* x_dev, int nrhs);
+
+/* out = op(W) in, op = W, W^T, W^-1 or W^-T (trans, inverse in {0,1});
+ * in_dev and out_dev may alias.  Errors: INVALID_ARG. */
+fifa_status fifa_apply_W(fifa_ctx* ctx, const fifa_fact* F, int trans, int inverse,
+                         const double* in_dev, double* out_dev, int nrhs);
+
+/* out = A in (H-matrix product: leaf products plus low-rank blocks).
+ * in_dev and out_dev must not alias.  Errors: INVALID_ARG. */
+fifa_status fifa_matvec(fifa_ctx* ctx, const fifa_hmat* A, const double* in_dev, double* out_dev, int nrhs);
+
+/* Algorithm 1: a, b ~ N(0, I) from Philox4x32-10 (key = seed, counter =
+ * (pair index, stream tag 0/1, iter, stream_id)); Z = (tau2/sigma) C~ a +
+ * tau W_C b; solve M~ w = Z; solve M~ r = y / sigma2; f = w + tau2 C~ r.
+ * C: C~; WC: factor of C~; WM: factor of M~ = (tau2/sigma2) C~ + I.
+ * mean_dev (nullable) receives tau2 C~ r, the posterior mean.  Errors: INVALID_ARG. */
+fifa_status fifa_sample(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, const fifa_fact* WM,
+                        const double* y_dev, double tau2, double sigma2, uint64_t seed,
+                        uint64_t stream_id, uint64_t iter, double* f_dev, double* mean_dev);
+
+/* A Gibbs chain: copies x, y to the device arena, assembles and factors
+ * C~(init->rho); state sigma2 = init->sigma2, tau2 = init->tau2, f = 0.
+ * init->nugget and ->kernel fix those settings for the chain.  Errors as
+ * fifa_assemble / fifa_factor. */
+fifa_status fifa_chain_create(fifa_ctx* ctx, const double* x_dev, const double* y_dev, int64_t n,
+                              const fifa_hyper* init, const fifa_prior* prior, uint64_t seed,
+                              uint64_t chain_id, fifa_chain** out);
+
+/* Run `iters` Gibbs iterations (Eqs. posterior_gibs1-4 in order: f by
+ * Algorithm 1, sigma2, tau2, then the Metropolis step on log rho).  The
+ * whole iteration is captured once in a CUDA graph and replayed; nothing
+ * returns to the host in between.  trace_host (nullable): iters rows of
+ * FIFA_TRACE_FIELDS doubles (written after the last iteration, synchronizes):
+ * iteration, sigma2, tau2, rho, accepted, log alpha, logdet C~(rho), q = f^T C~^-1 f,
+ * ||y - f||^2, refinement residual, status.  Errors: the chain's device status. */
+#define FIFA_TRACE_FIELDS 11
+fifa_status fifa_gibbs_step(fifa_ctx* ctx, fifa_chain* chain, int iters, double* trace_host);
+
+/* Current state: f (and the last posterior mean tau2 C~ r) to device buffers
+ * (nullable), hyperparameters to h_host (nullable); synchronizes. */
+fifa_status fifa_chain_get(fifa_ctx* ctx, const fifa_chain* chain, double* f_dev, double* mean_dev,
+                           fifa_hyper* h_host);
+
+/* Introspection for tests and tools (synchronize).  Layouts:
+ *   ranks[node], node = 2^l - 1 + i for node i of level l (2^L - 1 nodes);
+ *   row_piv / col_piv [node * rank_cap + k] (block-local indices, -1 unused);
+ *   bases[(l * rank_cap + k) * n + p]: column k of the level-l basis at global
+ *     row p (U of the node for rows in its left child, V for its right child);
+ *   leaves[(leaf * Bm + b) * Bm + a] = C~ leaf entry (a, b), Bm = max leaf size. */
+fifa_status fifa_hmat_dims(const fifa_hmat* H, int64_t* n, int* levels, int* nleaf, int* leaf_max,
+                           int* rank_cap);
+fifa_status fifa_hmat_export(fifa_ctx* ctx, const fifa_hmat* H, int* ranks_host, int* row_piv_host,
+                             int* col_piv_host, double* bases_host, double* leaves_host);
+/* Factor pieces in the same layouts: bases are the orthonormal Q_U / Q_V,
+ * leaves the lower Cholesky factors (as double even for FP32 factors),
+ * Zf / Zi [node * (2 cap)^2 + a * 2cap + b] = (L_S - I) and (L_S^-1 - I). */
+fifa_status fifa_fact_export(fifa_ctx* ctx, const fifa_fact* F, double* bases_host, double* leaves_host,
+                             double* Zf_host, double* Zi_host);
+
+void fifa_destroy_hmat(fifa_ctx* ctx, fifa_hmat* H);
+void fifa_destroy_fact(fifa_ctx* ctx, fifa_fact* F);
+void fifa_destroy_chain(fifa_ctx* ctx, fifa_chain* chain);
+
+const char* fifa_status_str(fifa_status s);
+
+/* Text of the last CUDA runtime error a call on this context met (for
+ * FIFA_ERR_CUDA), or "no error". */
+const char* fifa_last_cuda_error(const fifa_ctx* ctx);
+
+/* Deterministic exponential used for every kernel entry (same operation
+ * sequence as the CPU reference, so ACA pivots agree bit for bit):
+ * out[i] = det_exp(in[i]) for n device doubles.  Exposed for parity tests. */
+fifa_status fifa_det_exp(fifa_ctx* ctx, const double* in_dev, double* out_dev, int64_t n);
+
+/* Philox4x32-10 normals of stream (seed, tag, iter, stream_id), n values. */
+fifa_status fifa_normals(fifa_ctx* ctx, uint64_t seed, uint32_t tag, uint64_t iter, uint64_t stream_id,
+                         double* out_dev, int64_t n);
+
+/* Raw Philox4x32-10 words: out[4i..4i+3] = Philox(ctr[4i..4i+3], key = seed),
+ * for `count` counters (device uint32 arrays).  Exposed for parity tests. */
+fifa_status fifa_philox(fifa_ctx* ctx, uint64_t seed, const uint32_t* ctr_dev, uint32_t* out_dev, int64_t count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIFA_H */

@@ -1,0 +1,813 @@
+// C ABI of the FIFA-GP GB300 library (declared in include/fifa.h).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/fifa.h"
+#include "fifa_api_internal.h"
+#include "fifa_chain.h"
+#include "fifa_common.cuh"
+#include "fifa_launch.h"
+
+// ---------------------------------------------------------------------------
+// Arena: first-fit sub-allocator over one device buffer (256-byte granules).
+// ---------------------------------------------------------------------------
+void* Arena::alloc(size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (bytes == 0) bytes = 256;
+  for (auto it = free_.begin(); it != free_.end(); ++it) {
+    if (it->second >= bytes) {
+      size_t off = it->first, sz = it->second;
+      free_.erase(it);
+      if (sz > bytes) free_[off + bytes] = sz - bytes;
+      used_[off] = bytes;
+      in_use += bytes;
+      peak = std::max(peak, in_use);
+      return base + off;
+    }
+  }
+  return nullptr;
+}
+
+void Arena::release(void* p) {
+  if (!p) return;
+  size_t off = (char*)p - base;
+  auto it = used_.find(off);
+  if (it == used_.end()) return;
+  size_t sz = it->second;
+  used_.erase(it);
+  in_use -= sz;
+  auto nx = free_.lower_bound(off);
+  if (nx != free_.end() && nx->first == off + sz) {
+    sz += nx->second;
+    nx = free_.erase(nx);
+  }
+  if (nx != free_.begin()) {
+    auto pv = std::prev(nx);
+    if (pv->first + pv->second == off) {
+      pv->second += sz;
+      return;
+    }
+  }
+  free_[off] = sz;
+}
+
+#define CK(call)                          \
+  do {                                    \
+    cudaError_t e_ = (call);              \
+    if (e_ != cudaSuccess) {              \
+      ctx->last_cuda = e_;                \
+      return FIFA_ERR_CUDA;               \
+    }                                     \
+  } while (0)
+
+static fifa_status dev_status_to_api(int s) {
+  if (s & FIFA_DEV_TIMEOUT) return FIFA_ERR_TIMEOUT;
+  if (s & FIFA_DEV_NOT_SPD) return FIFA_ERR_NOT_SPD;
+  if (s & FIFA_DEV_RANK_CAP) return FIFA_ERR_RANK_CAP;
+  return FIFA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Plans: tree bounds and launch shapes for one (n, B).
+// ---------------------------------------------------------------------------
+static int levels_for(int64_t n, int B) {
+  int L = 0;
+  while ((n + ((int64_t)1 << L) - 1) / ((int64_t)1 << L) > B) ++L;
+  return L;
+}
+
+Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st) {
+  auto key = std::make_pair(n, ctx->opts.leaf_size);
+  auto it = ctx->plans.find(key);
+  if (it != ctx->plans.end()) return it->second;
+  Plan* P = new Plan();
+  P->n = n;
+  P->B = ctx->opts.leaf_size;
+  P->L = levels_for(n, P->B);
+  if (P->L >= FIFA_LEVELS_MAX) {
+    delete P;
+    *st = FIFA_ERR_UNSUPPORTED;
+    return nullptr;
+  }
+  P->nleaf = 1 << P->L;
+  P->nnodes = P->nleaf - 1;
+  // bounds: level l at offset 2^l - 1 + l
+  std::vector<int> b;
+  b.push_back(0);
+  b.push_back((int)n);
+  P->bnd_host = b;
+  std::vector<int> prev = b;
+  for (int l = 0; l < P->L; ++l) {
+    std::vector<int> nxt;
+    nxt.push_back(0);
+    for (size_t i = 0; i + 1 < prev.size(); ++i) {
+      int s = prev[i], e = prev[i + 1];
+      nxt.push_back(s + (e - s) / 2);
+      nxt.push_back(e);
+    }
+    P->bnd_host.insert(P->bnd_host.end(), nxt.begin(), nxt.end());
+    prev = nxt;
+  }
+  P->Bm = 0;
+  for (size_t i = 0; i + 1 < prev.size(); ++i) P->Bm = std::max(P->Bm, prev[i + 1] - prev[i]);
+  const int cap = ctx->opts.rank_cap;
+  // ACA groups.  A level-l block has ~n/2^l rows + columns and every level has
+  // about the same total work, so the co-resident CTA budget is split evenly
+  // over the top levels: level l gets G_l = budget / (levels * 2^l) CTAs per
+  // block (>= 2 to be worth a group).  Levels below run one CTA per block in a
+  // second launch.
+  const int coresident = ctx->aca_coresident;
+  std::vector<int> Gl(P->L, 1);
+  int ncoop_levels = 0;
+  for (int l = 0; l < P->L; ++l) {
+    const int64_t entries = n >> l;
+    if (entries < 8192) break;
+    ncoop_levels = l + 1;
+  }
+  while (ncoop_levels > 0) {
+    const int per_level = coresident / ncoop_levels;
+    if ((per_level >> (ncoop_levels - 1)) >= 2) break;
+    --ncoop_levels;  // the deepest candidate level cannot get two CTAs per block
+  }
+  if (ncoop_levels > 0) {
+    const int per_level = coresident / ncoop_levels;
+    for (int l = 0; l < ncoop_levels; ++l) {
+      const int64_t want = std::max<int64_t>(2, (n >> l) / 4096);
+      Gl[l] = (int)std::min<int64_t>(want, per_level >> l);
+      if (Gl[l] < 2) Gl[l] = 1;
+    }
+  }
+  std::vector<int4> coop, solo;
+  for (int l = 0; l < P->L; ++l) {
+    for (int i = 0; i < (1 << l); ++i) {
+      if (Gl[l] > 1)
+        for (int g = 0; g < Gl[l]; ++g) coop.push_back(make_int4(l, i, g, Gl[l]));
+      else
+        solo.push_back(make_int4(l, i, 0, 1));
+    }
+  }
+  P->aca_ncoop = (int)coop.size();
+  P->aca_nsolo = (int)solo.size();
+  // factor / sweep groups per level: one CTA per node up to 8192 rows
+  const int lvl_cores = ctx->level_coresident[0];
+  P->lvl_G.assign(P->L, 1);
+  P->sweep_G.assign(P->L, 1);
+  for (int l = 0; l < P->L; ++l) {
+    int64_t len = (n + ((int64_t)1 << l) - 1) >> l;
+    if (len > 8192) {
+      int64_t G = (len + 4095) / 4096;
+      while (((int64_t)1 << l) * G > lvl_cores && G > 1) G = (G + 1) / 2;
+      P->lvl_G[l] = (int)G;
+    }
+    P->sweep_G[l] = (int)std::max<int64_t>(1, (len + 2047) / 2048);
+  }
+  // device copies
+  size_t bytes = P->bnd_host.size() * sizeof(int) + (coop.size() + solo.size()) * sizeof(int4);
+  char* mem = (char*)ctx->arena.alloc(bytes);
+  if (!mem) {
+    delete P;
+    *st = FIFA_ERR_OOM;
+    return nullptr;
+  }
+  P->bnd_dev = (int*)mem;
+  size_t wo = (P->bnd_host.size() * sizeof(int) + 15) & ~(size_t)15;
+  P->aca_work = (int4*)(mem + wo);
+  if (wo + (coop.size() + solo.size()) * sizeof(int4) > ((bytes + 255) & ~(size_t)255)) {
+    // re-allocate with the alignment padding included
+    ctx->arena.release(mem);
+    mem = (char*)ctx->arena.alloc(wo + (coop.size() + solo.size()) * sizeof(int4));
+    if (!mem) {
+      delete P;
+      *st = FIFA_ERR_OOM;
+      return nullptr;
+    }
+    P->bnd_dev = (int*)mem;
+    P->aca_work = (int4*)(mem + wo);
+  }
+  cudaMemcpy(P->bnd_dev, P->bnd_host.data(), P->bnd_host.size() * sizeof(int), cudaMemcpyHostToDevice);
+  std::vector<int4> all = coop;
+  all.insert(all.end(), solo.begin(), solo.end());
+  if (!all.empty()) cudaMemcpy(P->aca_work, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  // scratch requirement (bytes)
+  size_t need = 0;
+  auto add = [&](size_t b) { need += (b + 255) & ~(size_t)255; };
+  add((size_t)3 * sizeof(ArgMax) * std::max(1, P->aca_ncoop));  // ACA partials
+  add(sizeof(unsigned int) * std::max(1, P->aca_ncoop));         // ACA barriers
+  int64_t lvl_ctas = 1, sweep_ctas = 1;
+  for (int l = 0; l < P->L; ++l) {
+    lvl_ctas = std::max<int64_t>(lvl_ctas, ((int64_t)1 << l) * P->lvl_G[l]);
+    sweep_ctas = std::max<int64_t>(sweep_ctas, ((int64_t)1 << l) * P->sweep_G[l]);
+  }
+  P->lvl_ctas_max = (int)lvl_ctas;
+  add(sizeof(double) * 2 * lvl_ctas * level_part_stride(cap));           // level partials (2 slots)
+  add(sizeof(unsigned int) * lvl_ctas);                                  // level barriers
+  add(sizeof(double) * sweep_ctas * 2 * cap * SWEEP_RHS_MAX);            // sweep partials
+  add(sizeof(double) * (size_t)P->nleaf * std::max(1, P->L) * cap * SWEEP_RHS_MAX);  // matvec partials
+  add(sizeof(double) * (size_t)std::max(1, P->nnodes) * 2 * cap * SWEEP_RHS_MAX);     // matvec projections
+  add(sizeof(double) * (size_t)n * 10);                                   // work vectors
+  add(sizeof(double) * 512);                                              // reduction partials
+  add(256);                                                               // flags
+  P->scratch_bytes = need;
+  ctx->plans[key] = P;
+  return P;
+}
+
+// Carve the context scratch for a plan (after ensure_scratch).
+Scratch carve(fifa_ctx* ctx, Plan* P) {
+  Scratch S;
+  char* p = (char*)(ctx->active_scratch ? ctx->active_scratch : ctx->scratch);
+  auto take = [&](size_t b) {
+    char* r = p;
+    p += (b + 255) & ~(size_t)255;
+    return (void*)r;
+  };
+  const int cap = ctx->opts.rank_cap;
+  S.aca_part = (ArgMax*)take((size_t)3 * sizeof(ArgMax) * std::max(1, P->aca_ncoop));
+  S.aca_bar = (unsigned int*)take(sizeof(unsigned int) * std::max(1, P->aca_ncoop));
+  S.lvl_part = (double*)take(sizeof(double) * 2 * (size_t)P->lvl_ctas_max * level_part_stride(cap));
+  S.lvl_bar = (unsigned int*)take(sizeof(unsigned int) * P->lvl_ctas_max);
+  int64_t sweep_ctas = 1;
+  for (int l = 0; l < P->L; ++l) sweep_ctas = std::max<int64_t>(sweep_ctas, ((int64_t)1 << l) * P->sweep_G[l]);
+  S.sweep_part = (double*)take(sizeof(double) * sweep_ctas * 2 * cap * SWEEP_RHS_MAX);
+  S.mv_part = (double*)take(sizeof(double) * (size_t)P->nleaf * std::max(1, P->L) * cap * SWEEP_RHS_MAX);
+  S.mv_proj = (double*)take(sizeof(double) * (size_t)std::max(1, P->nnodes) * 2 * cap * SWEEP_RHS_MAX);
+  S.vec = (double*)take(sizeof(double) * (size_t)P->n * 10);
+  S.red = (double*)take(sizeof(double) * 512);
+  S.flags = (int*)take(256);
+  return S;
+}
+
+fifa_status ensure_scratch(fifa_ctx* ctx, Plan* P) {
+  if (ctx->active_scratch) return FIFA_OK;  // a chain enqueues into its own scratch
+  if (ctx->scratch_bytes >= P->scratch_bytes) return FIFA_OK;
+  if (ctx->capturing) return FIFA_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->arena.release(ctx->scratch);
+  ctx->scratch = ctx->arena.alloc(P->scratch_bytes);
+  if (!ctx->scratch) {
+    ctx->scratch_bytes = 0;
+    return FIFA_ERR_OOM;
+  }
+  ctx->scratch_bytes = P->scratch_bytes;
+  return FIFA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+extern "C" fifa_status fifa_create(fifa_ctx** out, const fifa_opts* opts, void* cuda_stream, void* arena_dev,
+                                   size_t arena_bytes) {
+  if (!out || !opts) return FIFA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (opts->leaf_size < 1 || opts->rank_cap < 1 || !(opts->aca_tol >= 0.0)) return FIFA_ERR_INVALID_ARG;
+  if (opts->leaf_size > FIFA_LEAF_MAX || opts->rank_cap > FIFA_CAP_MAX) return FIFA_ERR_UNSUPPORTED;
+  if (opts->prec != FIFA_FP64 && opts->prec != FIFA_MIXED) return FIFA_ERR_INVALID_ARG;
+  if (arena_bytes < (1u << 20)) return FIFA_ERR_INVALID_ARG;
+  fifa_ctx* ctx = new (std::nothrow) fifa_ctx();
+  if (!ctx) return FIFA_ERR_OOM;
+  ctx->opts = *opts;
+  if (ctx->opts.refine_max < 0) ctx->opts.refine_max = 0;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&ctx->device);
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (arena_dev) {
+    ctx->arena.base = (char*)arena_dev;
+    ctx->own_arena = false;
+  } else {
+    void* p = nullptr;
+    if (cudaMalloc(&p, arena_bytes) != cudaSuccess) {
+      delete ctx;
+      return FIFA_ERR_OOM;
+    }
+    ctx->arena.base = (char*)p;
+    ctx->own_arena = true;
+  }
+  ctx->arena.size = arena_bytes & ~(size_t)255;
+  ctx->arena.free_[0] = ctx->arena.size;
+  ctx->aca_coresident = aca_max_coresident_ctas();
+  ctx->level_coresident[0] = level_max_coresident(0, ctx->opts.rank_cap);
+  ctx->level_coresident[1] = level_max_coresident(1, ctx->opts.rank_cap);
+  ctx->level_coresident[0] = std::min(ctx->level_coresident[0], ctx->level_coresident[1]);
+  ctx->flags = (int*)ctx->arena.alloc(256);
+  ctx->host_flags = nullptr;
+  cudaMallocHost((void**)&ctx->host_flags, 256);
+  if (!ctx->flags || !ctx->host_flags) {
+    fifa_destroy_ctx(ctx);
+    return FIFA_ERR_OOM;
+  }
+  if (ctx->aca_coresident <= 0 || ctx->level_coresident[0] <= 0) {
+    fifa_destroy_ctx(ctx);
+    return FIFA_ERR_UNSUPPORTED;
+  }
+  // leave no error behind for the caller's next runtime call to pick up
+  cudaError_t pending = cudaGetLastError();
+  if (pending != cudaSuccess) {
+    ctx->last_cuda = pending;
+    fifa_destroy_ctx(ctx);
+    return FIFA_ERR_CUDA;
+  }
+  *out = ctx;
+  return FIFA_OK;
+}
+
+extern "C" void fifa_destroy_ctx(fifa_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->plans) delete kv.second;
+  if (ctx->own_arena && ctx->arena.base) cudaFree(ctx->arena.base);
+  if (ctx->host_flags) cudaFreeHost(ctx->host_flags);
+  delete ctx;
+}
+
+// ---------------------------------------------------------------------------
+// H-matrix objects
+// ---------------------------------------------------------------------------
+static fifa_status upload_desc(fifa_ctx* ctx, fifa_hmat* H) {
+  CK(cudaMemcpyAsync(H->dev, &H->host, sizeof(HmatDesc), cudaMemcpyHostToDevice, ctx->stream));
+  return FIFA_OK;
+}
+
+fifa_status hmat_alloc(fifa_ctx* ctx, Plan* P, int kind, fifa_hmat** out) {
+  fifa_hmat* H = new (std::nothrow) fifa_hmat();
+  if (!H) return FIFA_ERR_OOM;
+  H->plan = P;
+  const int cap = ctx->opts.rank_cap;
+  const size_t nn = std::max(1, P->nnodes);
+  HmatDesc& d = H->host;
+  memset(&d, 0, sizeof(d));
+  d.n = P->n;
+  d.L = P->L;
+  d.nleaf = P->nleaf;
+  d.Bm = P->Bm;
+  d.cap = cap;
+  d.kind = kind;
+  d.bnd = P->bnd_dev;
+  d.scale = 1.0;
+  d.shift = 0.0;
+  d.eps = ctx->opts.aca_tol;
+  d.leaves = (double*)ctx->arena.alloc(sizeof(double) * (size_t)P->nleaf * P->Bm * P->Bm);
+  d.bases = (double*)ctx->arena.alloc(sizeof(double) * (size_t)std::max(1, P->L) * cap * P->n);
+  d.rank = (int*)ctx->arena.alloc(sizeof(int) * nn);
+  d.row_piv = (int*)ctx->arena.alloc(sizeof(int) * nn * cap);
+  d.col_piv = (int*)ctx->arena.alloc(sizeof(int) * nn * cap);
+  d.status = (int*)ctx->arena.alloc(sizeof(int));
+  H->dev = (HmatDesc*)ctx->arena.alloc(sizeof(HmatDesc));
+  if (!d.leaves || !d.bases || !d.rank || !d.row_piv || !d.col_piv || !d.status || !H->dev) {
+    fifa_destroy_hmat(ctx, H);
+    return FIFA_ERR_OOM;
+  }
+  H->owns = true;
+  *out = H;
+  return FIFA_OK;
+}
+
+// Enqueue assembly of H for inputs x (device) with kernel constant kc (host value).
+fifa_status hmat_assemble_enqueue(fifa_ctx* ctx, fifa_hmat* H) {
+  Plan* P = H->plan;
+  fifa_status st = ensure_scratch(ctx, P);
+  if (st != FIFA_OK) return st;
+  Scratch S = carve(ctx, P);
+  cudaStream_t s = ctx->stream;
+  CK(launch_prep_hmat(H->dev, P->nnodes, s));
+  CK(launch_leaf_assemble(H->dev, P->nleaf, s));
+  if (P->aca_ncoop > 0) {
+    CK(cudaMemsetAsync(S.aca_bar, 0, sizeof(unsigned int) * P->aca_ncoop, s));
+    CK(cudaMemsetAsync(S.flags, 0, sizeof(int), s));
+    CK(launch_aca(H->dev, P->aca_work, P->aca_ncoop, true, S.aca_part, S.aca_bar, S.flags, s));
+  }
+  if (P->aca_nsolo > 0) CK(launch_aca(H->dev, P->aca_work + P->aca_ncoop, P->aca_nsolo, false, S.aca_part, S.aca_bar, S.flags, s));
+  return FIFA_OK;
+}
+
+static double kernel_const(int kind, double rho) { return kind == 0 ? 0.5 / (rho * rho) : sqrt(5.0) / rho; }
+
+extern "C" fifa_status fifa_assemble(fifa_ctx* ctx, const double* x_dev, int64_t n, const fifa_hyper* hyper,
+                                     fifa_hmat** out) {
+  if (!ctx || !x_dev || !hyper || !out || n < 1) return FIFA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (hyper->kernel != 0 && hyper->kernel != 1) return FIFA_ERR_INVALID_ARG;
+  if (!(hyper->rho > 0.0) || !(hyper->nugget >= 0.0) || !isfinite(hyper->rho)) return FIFA_ERR_INVALID_ARG;
+  if (n > (int64_t)1 << 30) return FIFA_ERR_UNSUPPORTED;
+  // sortedness / finiteness check (synchronous)
+  CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int), ctx->stream));
+  CK(launch_check_sorted(x_dev, n, ctx->flags, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->host_flags, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->host_flags[0] & 2) return FIFA_ERR_INVALID_ARG;
+  if (ctx->host_flags[0] & 1) return FIFA_ERR_UNSORTED;
+  fifa_status st = FIFA_OK;
+  Plan* P = get_plan(ctx, n, &st);
+  if (!P) return st;
+  fifa_hmat* H = nullptr;
+  st = hmat_alloc(ctx, P, hyper->kernel, &H);
+  if (st != FIFA_OK) return st;
+  H->host.x = x_dev;
+  H->host.rho = hyper->rho;
+  H->host.kc = kernel_const(hyper->kernel, hyper->rho);
+  H->host.nugget = hyper->nugget;
+  st = upload_desc(ctx, H);
+  if (st == FIFA_OK) st = hmat_assemble_enqueue(ctx, H);
+  if (st != FIFA_OK) {
+    fifa_destroy_hmat(ctx, H);
+    return st;
+  }
+  *out = H;
+  return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_shift_scale(fifa_ctx* ctx, const fifa_hmat* C, double s, fifa_hmat** M) {
+  if (!ctx || !C || !M || !isfinite(s)) return FIFA_ERR_INVALID_ARG;
+  if (C->host.shift != 0.0 || C->host.scale != 1.0) return FIFA_ERR_INVALID_ARG;
+  fifa_hmat* H = new (std::nothrow) fifa_hmat();
+  if (!H) return FIFA_ERR_OOM;
+  H->plan = C->plan;
+  H->host = C->host;
+  H->host.scale = s;
+  H->host.shift = 1.0;
+  H->owns = false;
+  H->base = C;
+  H->dev = (HmatDesc*)ctx->arena.alloc(sizeof(HmatDesc));
+  if (!H->dev) {
+    delete H;
+    return FIFA_ERR_OOM;
+  }
+  fifa_status st = upload_desc(ctx, H);
+  if (st != FIFA_OK) {
+    fifa_destroy_hmat(ctx, H);
+    return st;
+  }
+  *M = H;
+  return FIFA_OK;
+}
+
+extern "C" void fifa_destroy_hmat(fifa_ctx* ctx, fifa_hmat* H) {
+  if (!ctx || !H) return;
+  cudaStreamSynchronize(ctx->stream);
+  if (H->owns) {
+    ctx->arena.release(H->host.leaves);
+    ctx->arena.release(H->host.bases);
+    ctx->arena.release(H->host.rank);
+    ctx->arena.release(H->host.row_piv);
+    ctx->arena.release(H->host.col_piv);
+    ctx->arena.release(H->host.status);
+  }
+  ctx->arena.release(H->dev);
+  delete H;
+}
+
+// ---------------------------------------------------------------------------
+// Factor
+// ---------------------------------------------------------------------------
+fifa_status fact_alloc(fifa_ctx* ctx, Plan* P, int prec, fifa_fact** out) {
+  fifa_fact* F = new (std::nothrow) fifa_fact();
+  if (!F) return FIFA_ERR_OOM;
+  F->plan = P;
+  const int cap = ctx->opts.rank_cap;
+  const size_t nn = std::max(1, P->nnodes);
+  const size_t esz = prec ? sizeof(float) : sizeof(double);
+  FactDesc& d = F->host;
+  memset(&d, 0, sizeof(d));
+  d.n = P->n;
+  d.L = P->L;
+  d.nleaf = P->nleaf;
+  d.Bm = P->Bm;
+  d.cap = cap;
+  d.prec = prec;
+  d.bnd = P->bnd_dev;
+  d.Lleaf = ctx->arena.alloc(esz * (size_t)P->nleaf * P->Bm * P->Bm);
+  d.Q = ctx->arena.alloc(esz * (size_t)std::max(1, P->L) * cap * P->n);
+  d.Zf = (double*)ctx->arena.alloc(sizeof(double) * nn * 4 * cap * cap);
+  d.Zi = (double*)ctx->arena.alloc(sizeof(double) * nn * 4 * cap * cap);
+  d.rank = (int*)ctx->arena.alloc(sizeof(int) * nn);
+  d.ld_parts = (double*)ctx->arena.alloc(sizeof(double) * (P->nleaf + nn));
+  d.logdet = (double*)ctx->arena.alloc(sizeof(double));
+  d.status = (int*)ctx->arena.alloc(sizeof(int));
+  F->dev = (FactDesc*)ctx->arena.alloc(sizeof(FactDesc));
+  if (!d.Lleaf || !d.Q || !d.Zf || !d.Zi || !d.rank || !d.ld_parts || !d.logdet || !d.status || !F->dev) {
+    fifa_destroy_fact(ctx, F);
+    return FIFA_ERR_OOM;
+  }
+  CK(cudaMemcpyAsync(F->dev, &F->host, sizeof(FactDesc), cudaMemcpyHostToDevice, ctx->stream));
+  *out = F;
+  return FIFA_OK;
+}
+
+// Enqueue the factorization of the (possibly view) matrix described by Hdev.
+fifa_status fact_enqueue(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev) {
+  Plan* P = F->plan;
+  fifa_status st = ensure_scratch(ctx, P);
+  if (st != FIFA_OK) return st;
+  Scratch S = carve(ctx, P);
+  cudaStream_t s = ctx->stream;
+  const int prec = F->host.prec, cap = ctx->opts.rank_cap;
+  CK(launch_prep_fact(F->dev, Hdev, P->nnodes, s));
+  CK(launch_leaf_factor(Hdev, F->dev, prec, P->nleaf, P->Bm, P->L, cap, s));
+  for (int l = P->L - 1; l >= 0; --l) {
+    const int G = P->lvl_G[l];
+    if (G > 1) {
+      CK(cudaMemsetAsync(S.lvl_bar, 0, sizeof(unsigned int) * ((size_t)1 << l) * G, s));
+      CK(cudaMemsetAsync(S.flags, 0, sizeof(int), s));
+    }
+    CK(launch_level(F->dev, prec, l, 1 << l, G, cap, S.lvl_part, S.lvl_bar, S.flags, s));
+  }
+  CK(launch_logdet_reduce(F->dev, s));
+  return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_factor(fifa_ctx* ctx, const fifa_hmat* A, fifa_fact** out) {
+  if (!ctx || !A || !out) return FIFA_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int prec = (ctx->opts.prec == FIFA_MIXED && A->host.shift != 0.0) ? 1 : 0;
+  fifa_fact* F = nullptr;
+  fifa_status st = fact_alloc(ctx, A->plan, prec, &F);
+  if (st != FIFA_OK) return st;
+  F->src = A;
+  st = fact_enqueue(ctx, F, A->dev);
+  if (st != FIFA_OK) {
+    fifa_destroy_fact(ctx, F);
+    return st;
+  }
+  *out = F;
+  return FIFA_OK;
+}
+
+extern "C" void fifa_destroy_fact(fifa_ctx* ctx, fifa_fact* F) {
+  if (!ctx || !F) return;
+  cudaStreamSynchronize(ctx->stream);
+  FactDesc& d = F->host;
+  ctx->arena.release(d.Lleaf);
+  ctx->arena.release(d.Q);
+  ctx->arena.release(d.Zf);
+  ctx->arena.release(d.Zi);
+  ctx->arena.release(d.rank);
+  ctx->arena.release(d.ld_parts);
+  ctx->arena.release(d.logdet);
+  ctx->arena.release(d.status);
+  ctx->arena.release(F->dev);
+  delete F;
+}
+
+extern "C" fifa_status fifa_logdet(fifa_ctx* ctx, const fifa_fact* F, double* out_host) {
+  if (!ctx || !F || !out_host) return FIFA_ERR_INVALID_ARG;
+  double* hb = (double*)ctx->host_flags;
+  CK(cudaMemcpyAsync(hb, F->host.logdet, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->host_flags + 4, F->host.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *out_host = hb[0];
+  return dev_status_to_api(ctx->host_flags[4]);
+}
+
+// ---------------------------------------------------------------------------
+// Sweeps, solve, matvec
+// ---------------------------------------------------------------------------
+fifa_status sweep_enqueue(fifa_ctx* ctx, const fifa_fact* F, int trans, int inverse, double* v, int nrhs) {
+  Plan* P = F->plan;
+  Scratch S = carve(ctx, P);
+  cudaStream_t s = ctx->stream;
+  const int prec = F->host.prec;
+  auto level = [&](int l, int zsel, int zt) -> cudaError_t {
+    return launch_sweep_level(F->dev, prec, l, 1 << l, P->sweep_G[l], v, nrhs, S.sweep_part, zsel, zt, s);
+  };
+  if (!trans && !inverse) {
+    for (int l = 0; l < P->L; ++l) CK(level(l, 0, 0));
+    CK(launch_sweep_leaf(F->dev, prec, P->nleaf, v, nrhs, 0, s));
+  } else if (!trans && inverse) {
+    CK(launch_sweep_leaf(F->dev, prec, P->nleaf, v, nrhs, 1, s));
+    for (int l = P->L - 1; l >= 0; --l) CK(level(l, 1, 0));
+  } else if (trans && !inverse) {
+    CK(launch_sweep_leaf(F->dev, prec, P->nleaf, v, nrhs, 2, s));
+    for (int l = P->L - 1; l >= 0; --l) CK(level(l, 0, 1));
+  } else {
+    for (int l = 0; l < P->L; ++l) CK(level(l, 1, 1));
+    CK(launch_sweep_leaf(F->dev, prec, P->nleaf, v, nrhs, 3, s));
+  }
+  return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_apply_W(fifa_ctx* ctx, const fifa_fact* F, int trans, int inverse, const double* in_dev,
+                                    double* out_dev, int nrhs) {
+  if (!ctx || !F || !in_dev || !out_dev || nrhs < 1 || nrhs > SWEEP_RHS_MAX) return FIFA_ERR_INVALID_ARG;
+  fifa_status st = ensure_scratch(ctx, F->plan);
+  if (st != FIFA_OK) return st;
+  if (in_dev != out_dev)
+    CK(cudaMemcpyAsync(out_dev, in_dev, sizeof(double) * F->plan->n * nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
+  return sweep_enqueue(ctx, F, trans ? 1 : 0, inverse ? 1 : 0, out_dev, nrhs);
+}
+
+fifa_status matvec_enqueue(fifa_ctx* ctx, const fifa_hmat* A, const double* in, double* out, int nrhs) {
+  Plan* P = A->plan;
+  Scratch S = carve(ctx, P);
+  CK(launch_matvec(A->dev, P->nleaf, P->L, in, nrhs, S.mv_part, S.mv_proj, out, ctx->stream));
+  return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_matvec(fifa_ctx* ctx, const fifa_hmat* A, const double* in_dev, double* out_dev, int nrhs) {
+  if (!ctx || !A || !in_dev || !out_dev || in_dev == out_dev || nrhs < 1 || nrhs > SWEEP_RHS_MAX)
+    return FIFA_ERR_INVALID_ARG;
+  fifa_status st = ensure_scratch(ctx, A->plan);
+  if (st != FIFA_OK) return st;
+  return matvec_enqueue(ctx, A, in_dev, out_dev, nrhs);
+}
+
+// x = A^-1 b, refined against the FP64 operator when the factor is FP32.
+fifa_status solve_enqueue(fifa_ctx* ctx, const fifa_fact* F, const double* b, double* x, int nrhs, double* work,
+                          double* res_dev) {
+  const int64_t n = F->plan->n;
+  cudaStream_t s = ctx->stream;
+  if (x != b) CK(cudaMemcpyAsync(x, b, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
+  fifa_status st = sweep_enqueue(ctx, F, 0, 1, x, nrhs);
+  if (st == FIFA_OK) st = sweep_enqueue(ctx, F, 1, 1, x, nrhs);
+  if (st != FIFA_OK || F->host.prec == 0 || !F->src) return st;
+  // iterative refinement: r = b - A x (FP64 operator), x += A32^-1 r
+  double* r = work;  // n * nrhs
+  for (int it = 0; it < ctx->opts.refine_max; ++it) {
+    st = matvec_enqueue(ctx, F->src, x, r, nrhs);
+    if (st != FIFA_OK) return st;
+    CK(launch_residual_axpy(b, r, n * nrhs, s));  // r <- b - r
+    st = sweep_enqueue(ctx, F, 0, 1, r, nrhs);
+    if (st == FIFA_OK) st = sweep_enqueue(ctx, F, 1, 1, r, nrhs);
+    if (st != FIFA_OK) return st;
+    CK(launch_axpy(1.0, r, x, n * nrhs, s));  // x += r
+  }
+  if (res_dev) {  // final relative residual ||b - A x|| / ||b|| in FP64
+    Scratch S = carve(ctx, F->plan);
+    st = matvec_enqueue(ctx, F->src, x, r, nrhs);
+    if (st != FIFA_OK) return st;
+    CK(launch_residual_axpy(b, r, n * nrhs, s));
+    CK(launch_sumsq(r, nullptr, n * nrhs, S.red, S.red + 256, s));
+    CK(launch_sumsq(b, nullptr, n * nrhs, S.red, S.red + 257, s));
+    CK(launch_ratio_sqrt(S.red + 256, S.red + 257, res_dev, s));
+  }
+  return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_solve(fifa_ctx* ctx, const fifa_fact* F, const double* b_dev, double* x_dev, int nrhs) {
+  if (!ctx || !F || !b_dev || !x_dev || nrhs < 1 || nrhs > SWEEP_RHS_MAX) return FIFA_ERR_INVALID_ARG;
+  fifa_status st = ensure_scratch(ctx, F->plan);
+  if (st != FIFA_OK) return st;
+  Scratch S = carve(ctx, F->plan);
+  const int64_t n = F->plan->n;
+  const double* b = b_dev;
+  if (b_dev == x_dev && F->host.prec) {  // refinement needs the original right-hand side
+    CK(cudaMemcpyAsync(S.vec + 2 * n * nrhs, b_dev, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
+    b = S.vec + 2 * n * nrhs;
+  }
+  return solve_enqueue(ctx, F, b, x_dev, nrhs, S.vec);
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1
+// ---------------------------------------------------------------------------
+fifa_status sample_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, const fifa_fact* WM, const double* y,
+                           double tau2, double sigma2, uint64_t seed, uint64_t sid, const uint64_t* iter_dev,
+                           uint64_t iter_host, double* f, double* mean, const double* scal_dev, double* res_dev) {
+  Plan* P = C->plan;
+  const int64_t n = P->n;
+  Scratch S = carve(ctx, P);
+  cudaStream_t s = ctx->stream;
+  double* a = S.vec;          // n
+  double* b = S.vec + n;      // n
+  double* Ca = S.vec + 2 * n; // n
+  double* rhs = S.vec + 3 * n;// 2n : [Z, y/sigma2] -> [w, r]
+  double* Cr = S.vec + 5 * n; // n
+  double* work = S.vec + 6 * n; // 2n (refinement)
+  double* bsave = S.vec + 8 * n; // 2n (refinement rhs)
+  CK(launch_normals(seed, 0, iter_dev, iter_host, sid, a, n, s));
+  CK(launch_normals(seed, 1, iter_dev, iter_host, sid, b, n, s));
+  fifa_status st = matvec_enqueue(ctx, C, a, Ca, 1);
+  if (st != FIFA_OK) return st;
+  st = sweep_enqueue(ctx, WC, 0, 0, b, 1);
+  if (st != FIFA_OK) return st;
+  // rhs0 = (tau2/sigma) Ca + tau Wb ; rhs1 = y / sigma2
+  CK(launch_alg1_rhs(Ca, b, y, rhs, n, tau2, sigma2, scal_dev, s));
+  if (WM->host.prec) {
+    CK(cudaMemcpyAsync(bsave, rhs, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, s));
+    st = solve_enqueue(ctx, WM, bsave, rhs, 2, work, res_dev);
+  } else {
+    st = solve_enqueue(ctx, WM, rhs, rhs, 2, work);
+  }
+  if (st != FIFA_OK) return st;
+  st = matvec_enqueue(ctx, C, rhs + n, Cr, 1);
+  if (st != FIFA_OK) return st;
+  CK(launch_alg1_finish(rhs, Cr, f, mean, n, tau2, scal_dev, s));
+  return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_sample(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, const fifa_fact* WM,
+                                   const double* y_dev, double tau2, double sigma2, uint64_t seed, uint64_t stream_id,
+                                   uint64_t iter, double* f_dev, double* mean_dev) {
+  if (!ctx || !C || !WC || !WM || !y_dev || !f_dev || !(tau2 > 0.0) || !(sigma2 > 0.0)) return FIFA_ERR_INVALID_ARG;
+  if (C->plan != WC->plan || C->plan != WM->plan) return FIFA_ERR_INVALID_ARG;
+  fifa_status st = ensure_scratch(ctx, C->plan);
+  if (st != FIFA_OK) return st;
+  return sample_enqueue(ctx, C, WC, WM, y_dev, tau2, sigma2, seed, stream_id, nullptr, iter, f_dev, mean_dev, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Introspection
+// ---------------------------------------------------------------------------
+extern "C" fifa_status fifa_hmat_dims(const fifa_hmat* H, int64_t* n, int* levels, int* nleaf, int* leaf_max,
+                                      int* rank_cap) {
+  if (!H) return FIFA_ERR_INVALID_ARG;
+  if (n) *n = H->plan->n;
+  if (levels) *levels = H->plan->L;
+  if (nleaf) *nleaf = H->plan->nleaf;
+  if (leaf_max) *leaf_max = H->plan->Bm;
+  if (rank_cap) *rank_cap = H->host.cap;
+  return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_hmat_export(fifa_ctx* ctx, const fifa_hmat* H, int* ranks_host, int* row_piv_host,
+                                        int* col_piv_host, double* bases_host, double* leaves_host) {
+  if (!ctx || !H) return FIFA_ERR_INVALID_ARG;
+  Plan* P = H->plan;
+  const int cap = H->host.cap;
+  cudaStream_t s = ctx->stream;
+  CK(cudaStreamSynchronize(s));
+  if (ranks_host && P->nnodes) CK(cudaMemcpy(ranks_host, H->host.rank, sizeof(int) * P->nnodes, cudaMemcpyDeviceToHost));
+  if (row_piv_host && P->nnodes)
+    CK(cudaMemcpy(row_piv_host, H->host.row_piv, sizeof(int) * P->nnodes * cap, cudaMemcpyDeviceToHost));
+  if (col_piv_host && P->nnodes)
+    CK(cudaMemcpy(col_piv_host, H->host.col_piv, sizeof(int) * P->nnodes * cap, cudaMemcpyDeviceToHost));
+  if (bases_host && P->L)
+    CK(cudaMemcpy(bases_host, H->host.bases, sizeof(double) * (size_t)P->L * cap * P->n, cudaMemcpyDeviceToHost));
+  if (leaves_host)
+    CK(cudaMemcpy(leaves_host, H->host.leaves, sizeof(double) * (size_t)P->nleaf * P->Bm * P->Bm, cudaMemcpyDeviceToHost));
+  int hs = 0;
+  CK(cudaMemcpy(&hs, H->host.status, sizeof(int), cudaMemcpyDeviceToHost));
+  return dev_status_to_api(hs);
+}
+
+extern "C" fifa_status fifa_fact_export(fifa_ctx* ctx, const fifa_fact* F, double* bases_host, double* leaves_host,
+                                        double* Zf_host, double* Zi_host) {
+  if (!ctx || !F) return FIFA_ERR_INVALID_ARG;
+  Plan* P = F->plan;
+  const int cap = F->host.cap;
+  CK(cudaStreamSynchronize(ctx->stream));
+  const size_t nb = (size_t)P->L * cap * P->n, nl = (size_t)P->nleaf * P->Bm * P->Bm;
+  auto fetch = [&](double* dst, const void* src, size_t cnt) -> cudaError_t {
+    if (!dst || cnt == 0) return cudaSuccess;
+    if (F->host.prec == 0) return cudaMemcpy(dst, src, sizeof(double) * cnt, cudaMemcpyDeviceToHost);
+    std::vector<float> tmp(cnt);
+    cudaError_t e = cudaMemcpy(tmp.data(), src, sizeof(float) * cnt, cudaMemcpyDeviceToHost);
+    for (size_t i = 0; i < cnt; ++i) dst[i] = tmp[i];
+    return e;
+  };
+  CK(fetch(bases_host, F->host.Q, nb));
+  CK(fetch(leaves_host, F->host.Lleaf, nl));
+  const size_t nz = (size_t)std::max(1, P->nnodes) * 4 * cap * cap;
+  if (Zf_host && P->nnodes) CK(cudaMemcpy(Zf_host, F->host.Zf, sizeof(double) * nz, cudaMemcpyDeviceToHost));
+  if (Zi_host && P->nnodes) CK(cudaMemcpy(Zi_host, F->host.Zi, sizeof(double) * nz, cudaMemcpyDeviceToHost));
+  int hs = 0;
+  CK(cudaMemcpy(&hs, F->host.status, sizeof(int), cudaMemcpyDeviceToHost));
+  return dev_status_to_api(hs);
+}
+
+extern "C" fifa_status fifa_det_exp(fifa_ctx* ctx, const double* in_dev, double* out_dev, int64_t n) {
+  if (!ctx || !in_dev || !out_dev || n < 0) return FIFA_ERR_INVALID_ARG;
+  if (n == 0) return FIFA_OK;
+  CK(launch_det_exp(in_dev, out_dev, n, ctx->stream));
+  return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_normals(fifa_ctx* ctx, uint64_t seed, uint32_t tag, uint64_t iter, uint64_t stream_id,
+                                    double* out_dev, int64_t n) {
+  if (!ctx || !out_dev || n < 0) return FIFA_ERR_INVALID_ARG;
+  if (n == 0) return FIFA_OK;
+  CK(launch_normals(seed, tag, nullptr, iter, stream_id, out_dev, n, ctx->stream));
+  return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_philox(fifa_ctx* ctx, uint64_t seed, const uint32_t* ctr_dev, uint32_t* out_dev,
+                                   int64_t count) {
+  if (!ctx || !ctr_dev || !out_dev || count < 0) return FIFA_ERR_INVALID_ARG;
+  if (count == 0) return FIFA_OK;
+  CK(launch_philox(seed, ctr_dev, out_dev, count, ctx->stream));
+  return FIFA_OK;
+}
+
+extern "C" const char* fifa_last_cuda_error(const fifa_ctx* ctx) {
+  return ctx ? cudaGetErrorString(ctx->last_cuda) : "no context";
+}
+
+extern "C" const char* fifa_status_str(fifa_status s) {
+  switch (s) {
+    case FIFA_OK: return "ok";
+    case FIFA_ERR_INVALID_ARG: return "invalid argument";
+    case FIFA_ERR_UNSORTED: return "inputs are not sorted";
+    case FIFA_ERR_NOT_SPD: return "matrix is not positive definite";
+    case FIFA_ERR_RANK_CAP: return "ACA rank cap reached before the tolerance";
+    case FIFA_ERR_OOM: return "device arena exhausted";
+    case FIFA_ERR_CUDA: return "CUDA runtime error";
+    case FIFA_ERR_TIMEOUT: return "bounded device wait timed out";
+    case FIFA_ERR_UNSUPPORTED: return "unsupported size";
+  }
+  return "unknown status";
+}

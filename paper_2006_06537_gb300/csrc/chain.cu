@@ -1,0 +1,319 @@
+// Gibbs chain: device-resident state and one iteration captured in a CUDA graph.
+//
+// Per iteration (Sec. 4.1, in the order of Eqs. posterior_gibs1-4):
+//   M~ = s C~ + I view (s = tau2 / sigma2), factor M~ (FP64, or FP32 + refinement)
+//   f by Algorithm 1 (Philox a, b; C~ a, W_C b, two-right-hand-side solve, C~ r)
+//   sigma2 | y, f ;  q = ||W_C^-1 f||^2 ;  tau2 | f
+//   propose rho', assemble C~(rho') (leaves + ACA), factor it, q' = ||W'^-1 f||^2
+//   Metropolis accept / reject (descriptor swap on the device)
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/fifa.h"
+#include "fifa_api_internal.h"
+#include "fifa_chain.h"
+#include "fifa_launch.h"
+
+#define CK(call)                 \
+  do {                           \
+    cudaError_t e_ = (call);     \
+    if (e_ != cudaSuccess) {     \
+      ctx->last_cuda = e_;       \
+      return FIFA_ERR_CUDA;      \
+    }                            \
+  } while (0)
+
+#define CHAIN_TRACE_CAP 1024
+
+struct fifa_chain {
+  Plan* plan = nullptr;
+  fifa_hmat* H[2] = {nullptr, nullptr};  // slot 0: current C~, slot 1: proposal (device descriptors swap)
+  fifa_fact* F[2] = {nullptr, nullptr};
+  fifa_fact* FM = nullptr;
+  fifa_hmat* Mv = nullptr;  // view descriptor refreshed every iteration
+  double *x = nullptr, *y = nullptr, *f = nullptr, *mean = nullptr, *tmp = nullptr, *trace = nullptr;
+  void* scratch = nullptr;
+  ChainDev* dev = nullptr;
+  ChainDev init{};
+  uint64_t iter_host = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_failed = false;
+};
+
+static fifa_status chain_iteration_enqueue(fifa_ctx* ctx, fifa_chain* ch) {
+  Plan* P = ch->plan;
+  const int64_t n = P->n;
+  cudaStream_t s = ctx->stream;
+  ctx->active_scratch = ch->scratch;
+  Scratch S = carve(ctx, P);
+  fifa_status st = FIFA_OK;
+  ChainDev* c = ch->dev;
+  HmatDesc* Hc = ch->H[0]->dev;
+  HmatDesc* Hp = ch->H[1]->dev;
+  do {
+    // M~ = (tau2 / sigma2) C~ + I and its factor
+    if (launch_chain_make_view(Hc, ch->Mv->dev, c, s) != cudaSuccess) { st = FIFA_ERR_CUDA; break; }
+    st = fact_enqueue(ctx, ch->FM, ch->Mv->dev);
+    if (st != FIFA_OK) break;
+    // f by Algorithm 1
+    st = sample_enqueue(ctx, ch->H[0], ch->F[0], ch->FM, ch->y, 0.0, 0.0, c ? ch->init.seed : 0, ch->init.chain_id,
+                        &c->iter, 0, ch->f, ch->mean, &c->tau2, &c->refine_res);
+    if (st != FIFA_OK) break;
+    // sigma2 | y, f
+    if (launch_sumsq(ch->y, ch->f, n, S.red, &c->rss, s) != cudaSuccess) { st = FIFA_ERR_CUDA; break; }
+    if (launch_chain_sigma2(c, s) != cudaSuccess) { st = FIFA_ERR_CUDA; break; }
+    // tau2 | f, rho : q = ||W_C^-1 f||^2
+    if (cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      st = FIFA_ERR_CUDA;
+      break;
+    }
+    st = sweep_enqueue(ctx, ch->F[0], 0, 1, ch->tmp, 1);
+    if (st != FIFA_OK) break;
+    if (launch_sumsq(ch->tmp, nullptr, n, S.red, &c->q, s) != cudaSuccess) { st = FIFA_ERR_CUDA; break; }
+    if (launch_chain_tau2(c, s) != cudaSuccess) { st = FIFA_ERR_CUDA; break; }
+    // rho | f, tau2 : propose, assemble, factor, q'
+    if (launch_chain_propose(c, Hp, s) != cudaSuccess) { st = FIFA_ERR_CUDA; break; }
+    st = hmat_assemble_enqueue(ctx, ch->H[1]);
+    if (st != FIFA_OK) break;
+    st = fact_enqueue(ctx, ch->F[1], Hp);
+    if (st != FIFA_OK) break;
+    if (cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      st = FIFA_ERR_CUDA;
+      break;
+    }
+    st = sweep_enqueue(ctx, ch->F[1], 0, 1, ch->tmp, 1);
+    if (st != FIFA_OK) break;
+    if (launch_sumsq(ch->tmp, nullptr, n, S.red, &c->q_prop, s) != cudaSuccess) { st = FIFA_ERR_CUDA; break; }
+    if (launch_chain_mh(c, Hc, Hp, ch->F[0]->dev, ch->F[1]->dev, ch->FM->dev, s) != cudaSuccess) {
+      st = FIFA_ERR_CUDA;
+      break;
+    }
+  } while (0);
+  ctx->active_scratch = nullptr;
+  if (st == FIFA_ERR_CUDA) ctx->last_cuda = cudaGetLastError();
+  return st;
+}
+
+static double kconst(int kind, double rho) { return kind == 0 ? 0.5 / (rho * rho) : sqrt(5.0) / rho; }
+
+extern "C" fifa_status fifa_chain_create(fifa_ctx* ctx, const double* x_dev, const double* y_dev, int64_t n,
+                                         const fifa_hyper* init, const fifa_prior* prior, uint64_t seed,
+                                         uint64_t chain_id, fifa_chain** out) {
+  if (!ctx || !x_dev || !y_dev || !init || !prior || !out || n < 2) return FIFA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!(init->rho > 0.0) || !(init->tau2 > 0.0) || !(init->sigma2 > 0.0) || !(init->nugget >= 0.0)) return FIFA_ERR_INVALID_ARG;
+  if (init->kernel != 0 && init->kernel != 1) return FIFA_ERR_INVALID_ARG;
+  if (!(prior->logrho_sd > 0.0) || !(prior->prop_sd >= 0.0) || prior->a_tau2 + 0.5 * n < 1.0 ||
+      prior->a_sigma2 + 0.5 * n < 1.0)
+    return FIFA_ERR_INVALID_ARG;
+  // validate inputs through the assembly check
+  CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int), ctx->stream));
+  CK(launch_check_sorted(x_dev, n, ctx->flags, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->host_flags, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->host_flags[0] & 2) return FIFA_ERR_INVALID_ARG;
+  if (ctx->host_flags[0] & 1) return FIFA_ERR_UNSORTED;
+  fifa_status st = FIFA_OK;
+  Plan* P = get_plan(ctx, n, &st);
+  if (!P) return st;
+  fifa_chain* ch = new (std::nothrow) fifa_chain();
+  if (!ch) return FIFA_ERR_OOM;
+  ch->plan = P;
+  auto fail = [&](fifa_status e) {
+    fifa_destroy_chain(ctx, ch);
+    return e;
+  };
+  ch->x = (double*)ctx->arena.alloc(sizeof(double) * n);
+  ch->y = (double*)ctx->arena.alloc(sizeof(double) * n);
+  ch->f = (double*)ctx->arena.alloc(sizeof(double) * n);
+  ch->mean = (double*)ctx->arena.alloc(sizeof(double) * n);
+  ch->tmp = (double*)ctx->arena.alloc(sizeof(double) * n);
+  ch->trace = (double*)ctx->arena.alloc(sizeof(double) * CHAIN_TRACE_CAP * CHAIN_TRACE_FIELDS);
+  ch->scratch = ctx->arena.alloc(P->scratch_bytes);
+  ch->dev = (ChainDev*)ctx->arena.alloc(sizeof(ChainDev));
+  if (!ch->x || !ch->y || !ch->f || !ch->mean || !ch->tmp || !ch->trace || !ch->scratch || !ch->dev)
+    return fail(FIFA_ERR_OOM);
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemcpyAsync(ch->x, x_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(ch->y, y_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(ch->f, 0, sizeof(double) * n, s));
+  CK(cudaMemsetAsync(ch->mean, 0, sizeof(double) * n, s));
+  for (int k = 0; k < 2; ++k) {
+    st = hmat_alloc(ctx, P, init->kernel, &ch->H[k]);
+    if (st != FIFA_OK) return fail(st);
+    HmatDesc& d = ch->H[k]->host;
+    d.x = ch->x;
+    d.rho = init->rho;
+    d.kc = kconst(init->kernel, init->rho);
+    d.nugget = init->nugget;
+    CK(cudaMemcpyAsync(ch->H[k]->dev, &d, sizeof(HmatDesc), cudaMemcpyHostToDevice, s));
+    st = fact_alloc(ctx, P, 0, &ch->F[k]);
+    if (st != FIFA_OK) return fail(st);
+    ch->F[k]->src = ch->H[k];
+  }
+  ch->Mv = new (std::nothrow) fifa_hmat();
+  if (!ch->Mv) return fail(FIFA_ERR_OOM);
+  ch->Mv->plan = P;
+  ch->Mv->host = ch->H[0]->host;
+  ch->Mv->host.shift = 1.0;
+  ch->Mv->owns = false;
+  ch->Mv->dev = (HmatDesc*)ctx->arena.alloc(sizeof(HmatDesc));
+  if (!ch->Mv->dev) return fail(FIFA_ERR_OOM);
+  st = fact_alloc(ctx, P, ctx->opts.prec == FIFA_MIXED ? 1 : 0, &ch->FM);
+  if (st != FIFA_OK) return fail(st);
+  ch->FM->src = ch->Mv;
+  ChainDev& c = ch->init;
+  memset(&c, 0, sizeof(c));
+  c.tau2 = init->tau2;
+  c.sigma2 = init->sigma2;
+  c.eta = log(init->rho);
+  c.rho = init->rho;
+  c.a_tau2 = prior->a_tau2;
+  c.b_tau2 = prior->b_tau2;
+  c.a_sigma2 = prior->a_sigma2;
+  c.b_sigma2 = prior->b_sigma2;
+  c.logrho_mu = prior->logrho_mu;
+  c.logrho_sd = prior->logrho_sd;
+  c.prop_sd = prior->prop_sd;
+  c.seed = seed;
+  c.chain_id = chain_id;
+  c.iter = 0;
+  c.n = n;
+  c.kind = init->kernel;
+  c.trace_cap = CHAIN_TRACE_CAP;
+  c.trace = ch->trace;
+  CK(cudaMemcpyAsync(ch->dev, &c, sizeof(ChainDev), cudaMemcpyHostToDevice, s));
+  // C~(rho_0) and its factor
+  ctx->active_scratch = ch->scratch;
+  st = hmat_assemble_enqueue(ctx, ch->H[0]);
+  if (st == FIFA_OK) st = fact_enqueue(ctx, ch->F[0], ch->H[0]->dev);
+  ctx->active_scratch = nullptr;
+  if (st != FIFA_OK) return fail(st);
+  int fs = 0;
+  CK(cudaMemcpyAsync(ctx->host_flags, ch->F[0]->host.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  fs = ctx->host_flags[0];
+  if (fs & FIFA_DEV_NOT_SPD) return fail(FIFA_ERR_NOT_SPD);
+  if (fs & FIFA_DEV_TIMEOUT) return fail(FIFA_ERR_TIMEOUT);
+  *out = ch;
+  return FIFA_OK;
+}
+
+static fifa_status chain_build_graph(fifa_ctx* ctx, fifa_chain* ch) {
+  if (ch->exec || ch->graph_failed) return FIFA_OK;
+  cudaStream_t s = ctx->stream;
+  if (s == nullptr) {  // the legacy default stream cannot be captured
+    ch->graph_failed = true;
+    return FIFA_OK;
+  }
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    ch->graph_failed = true;
+    return FIFA_OK;
+  }
+  ctx->capturing = true;
+  fifa_status st = chain_iteration_enqueue(ctx, ch);
+  ctx->capturing = false;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (st != FIFA_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    ch->graph_failed = true;
+    return FIFA_OK;
+  }
+  if (cudaGraphInstantiate(&ch->exec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    ch->exec = nullptr;
+    ch->graph_failed = true;
+    return FIFA_OK;
+  }
+  ch->graph = g;
+  return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_gibbs_step(fifa_ctx* ctx, fifa_chain* ch, int iters, double* trace_host) {
+  if (!ctx || !ch || iters < 0) return FIFA_ERR_INVALID_ARG;
+  cudaStream_t s = ctx->stream;
+  fifa_status st = chain_build_graph(ctx, ch);
+  if (st != FIFA_OK) return st;
+  int done = 0;
+  while (done < iters) {
+    const int chunk = std::min(iters - done, CHAIN_TRACE_CAP);
+    for (int k = 0; k < chunk; ++k) {
+      if (ch->exec) {
+        CK(cudaGraphLaunch(ch->exec, s));
+      } else {
+        st = chain_iteration_enqueue(ctx, ch);
+        if (st != FIFA_OK) return st;
+      }
+    }
+    if (trace_host) {
+      const uint64_t first = ch->iter_host % CHAIN_TRACE_CAP;
+      const uint64_t n1 = std::min<uint64_t>(chunk, CHAIN_TRACE_CAP - first);
+      CK(cudaMemcpyAsync(trace_host + (size_t)done * CHAIN_TRACE_FIELDS, ch->trace + first * CHAIN_TRACE_FIELDS,
+                         sizeof(double) * n1 * CHAIN_TRACE_FIELDS, cudaMemcpyDeviceToHost, s));
+      if (n1 < (uint64_t)chunk)
+        CK(cudaMemcpyAsync(trace_host + (size_t)(done + n1) * CHAIN_TRACE_FIELDS, ch->trace,
+                           sizeof(double) * (chunk - n1) * CHAIN_TRACE_FIELDS, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    ch->iter_host += chunk;
+    done += chunk;
+  }
+  CK(cudaMemcpyAsync(ctx->host_flags, &ch->dev->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int cs = ctx->host_flags[0];
+  if (cs & FIFA_DEV_TIMEOUT) return FIFA_ERR_TIMEOUT;
+  if (cs & FIFA_DEV_NOT_SPD) return FIFA_ERR_NOT_SPD;
+  return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_chain_get(fifa_ctx* ctx, const fifa_chain* ch, double* f_dev, double* mean_dev,
+                                      fifa_hyper* h_host) {
+  if (!ctx || !ch) return FIFA_ERR_INVALID_ARG;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ch->plan->n;
+  if (f_dev) CK(cudaMemcpyAsync(f_dev, ch->f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  if (mean_dev) CK(cudaMemcpyAsync(mean_dev, ch->mean, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  ChainDev c;
+  CK(cudaMemcpyAsync(&c, ch->dev, sizeof(ChainDev), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h_host) {
+    h_host->kernel = c.kind;
+    h_host->tau2 = c.tau2;
+    h_host->rho = c.rho;
+    h_host->sigma2 = c.sigma2;
+    h_host->nugget = ch->H[0]->host.nugget;
+  }
+  return FIFA_OK;
+}
+
+extern "C" void fifa_destroy_chain(fifa_ctx* ctx, fifa_chain* ch) {
+  if (!ctx || !ch) return;
+  cudaStreamSynchronize(ctx->stream);
+  if (ch->exec) cudaGraphExecDestroy(ch->exec);
+  if (ch->graph) cudaGraphDestroy(ch->graph);
+  for (int k = 0; k < 2; ++k) {
+    if (ch->F[k]) fifa_destroy_fact(ctx, ch->F[k]);
+    if (ch->H[k]) fifa_destroy_hmat(ctx, ch->H[k]);
+  }
+  if (ch->FM) fifa_destroy_fact(ctx, ch->FM);
+  if (ch->Mv) fifa_destroy_hmat(ctx, ch->Mv);
+  ctx->arena.release(ch->x);
+  ctx->arena.release(ch->y);
+  ctx->arena.release(ch->f);
+  ctx->arena.release(ch->mean);
+  ctx->arena.release(ch->tmp);
+  ctx->arena.release(ch->trace);
+  ctx->arena.release(ch->scratch);
+  ctx->arena.release(ch->dev);
+  delete ch;
+}

@@ -1,0 +1,103 @@
+// Host-side object definitions behind the opaque handles of fifa.h.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <utility>
+#include <vector>
+
+#include "../../include/fifa.h"
+#include "fifa_common.cuh"
+
+struct Arena {
+  char* base = nullptr;
+  size_t size = 0, in_use = 0, peak = 0;
+  std::map<size_t, size_t> free_;  // offset -> size
+  std::map<size_t, size_t> used_;
+  void* alloc(size_t bytes);
+  void release(void* p);
+};
+
+struct Plan {
+  int64_t n = 0;
+  int B = 0, L = 0, nleaf = 0, nnodes = 0, Bm = 0;
+  std::vector<int> bnd_host;
+  int* bnd_dev = nullptr;
+  int4* aca_work = nullptr;  // coop entries first, then solo entries
+  int aca_ncoop = 0, aca_nsolo = 0;
+  std::vector<int> lvl_G, sweep_G;
+  int lvl_ctas_max = 1;
+  size_t scratch_bytes = 0;
+};
+
+struct Scratch {
+  ArgMax* aca_part;
+  unsigned int* aca_bar;
+  double* lvl_part;
+  unsigned int* lvl_bar;
+  double* sweep_part;
+  double* mv_part;
+  double* mv_proj;
+  double* vec;  // 10 n doubles
+  double* red;  // 512 doubles of reduction partials
+  int* flags;
+};
+
+struct fifa_ctx {
+  fifa_opts opts{};
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 0;
+  Arena arena;
+  bool own_arena = false;
+  std::map<std::pair<int64_t, int>, Plan*> plans;
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  int aca_coresident = 0;
+  int level_coresident[2] = {0, 0};
+  int* flags = nullptr;       // device
+  int* host_flags = nullptr;  // pinned
+  bool capturing = false;
+  void* active_scratch = nullptr;  // a chain's own scratch while it enqueues work
+  cudaError_t last_cuda = cudaSuccess;
+};
+
+struct fifa_hmat {
+  Plan* plan = nullptr;
+  HmatDesc host{};
+  HmatDesc* dev = nullptr;
+  bool owns = false;
+  const fifa_hmat* base = nullptr;
+};
+
+struct fifa_fact {
+  Plan* plan = nullptr;
+  FactDesc host{};
+  FactDesc* dev = nullptr;
+  const fifa_hmat* src = nullptr;  // operator used for refinement (FP32 factors)
+};
+
+Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st);
+Scratch carve(fifa_ctx* ctx, Plan* P);
+fifa_status ensure_scratch(fifa_ctx* ctx, Plan* P);
+fifa_status hmat_alloc(fifa_ctx* ctx, Plan* P, int kind, fifa_hmat** out);
+fifa_status hmat_assemble_enqueue(fifa_ctx* ctx, fifa_hmat* H);
+fifa_status fact_alloc(fifa_ctx* ctx, Plan* P, int prec, fifa_fact** out);
+fifa_status fact_enqueue(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev);
+fifa_status sweep_enqueue(fifa_ctx* ctx, const fifa_fact* F, int trans, int inverse, double* v, int nrhs);
+fifa_status matvec_enqueue(fifa_ctx* ctx, const fifa_hmat* A, const double* in, double* out, int nrhs);
+fifa_status solve_enqueue(fifa_ctx* ctx, const fifa_fact* F, const double* b, double* x, int nrhs, double* work,
+                          double* res_dev = nullptr);
+fifa_status sample_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, const fifa_fact* WM, const double* y,
+                           double tau2, double sigma2, uint64_t seed, uint64_t sid, const uint64_t* iter_dev,
+                           uint64_t iter_host, double* f, double* mean, const double* scal_dev, double* res_dev = nullptr);
+
+// vector kernels (k_vec.cu)
+cudaError_t launch_prep_hmat(HmatDesc* H, int nnodes, cudaStream_t st);
+cudaError_t launch_prep_fact(FactDesc* F, const HmatDesc* H, int nnodes, cudaStream_t st);
+cudaError_t launch_sumsq(const double* a, const double* b, int64_t n, double* part, double* out, cudaStream_t st);
+cudaError_t launch_axpy(double a, const double* x, double* y, int64_t n, cudaStream_t st);
+cudaError_t launch_residual_axpy(const double* b, double* r, int64_t n, cudaStream_t st);
+cudaError_t launch_alg1_rhs(const double* Ca, const double* Wb, const double* y, double* rhs, int64_t n, double tau2,
+                            double sigma2, const double* scal_dev, cudaStream_t st);
+cudaError_t launch_alg1_finish(const double* wr, const double* Cr, double* f, double* mean, int64_t n, double tau2,
+                               const double* scal_dev, cudaStream_t st);

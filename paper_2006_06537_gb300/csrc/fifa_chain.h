@@ -1,0 +1,28 @@
+// Device-resident Gibbs chain state (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fifa_common.cuh"
+
+#define CHAIN_TRACE_FIELDS 11
+
+struct ChainDev {
+  double tau2, sigma2;  // adjacent: read as scal[0], scal[1] by the Algorithm 1 kernels
+  double eta, rho, eta_prop, rho_prop;
+  double rss, q, q_prop, log_alpha, refine_res;
+  double a_tau2, b_tau2, a_sigma2, b_sigma2, logrho_mu, logrho_sd, prop_sd;
+  double red_num, red_den;
+  uint64_t seed, chain_id, iter;
+  int64_t n;
+  int kind, accept, status, trace_cap;
+  double* trace;
+};
+
+cudaError_t launch_chain_make_view(const HmatDesc* Hc, HmatDesc* Mv, const ChainDev* c, cudaStream_t st);
+cudaError_t launch_chain_sigma2(ChainDev* c, cudaStream_t st);
+cudaError_t launch_chain_tau2(ChainDev* c, cudaStream_t st);
+cudaError_t launch_chain_propose(ChainDev* c, HmatDesc* Hp, cudaStream_t st);
+cudaError_t launch_chain_mh(ChainDev* c, HmatDesc* Hc, HmatDesc* Hp, FactDesc* Fc, FactDesc* Fp, const FactDesc* Fm,
+                            cudaStream_t st);
+cudaError_t launch_ratio_sqrt(const double* num, const double* den, double* out, cudaStream_t st);

@@ -1,0 +1,295 @@
+// Shared device definitions of the FIFA-GP GB300 library.
+//
+// Data layout in HBM (one HODLR matrix C~ for n sorted points, leaf size B,
+// L levels, rank cap R):
+//   bnd      int32   tree bounds; level l occupies bnd[2^l - 1 + l .. 2^(l+1) - 1 + l],
+//                    node i of level l is [bnd[off(l)+i], bnd[off(l)+i+1])
+//   leaves   f64     nleaf x Bm x Bm, column-major per leaf (Bm = max leaf size)
+//   bases    f64     L x R x n: column k of level l at bases[(l*R + k)*n + p]; row p
+//                    holds U of the level-l node containing p when p lies in the
+//                    node's left child and V when it lies in the right child, so a
+//                    level's bases tile all n rows and every access is a
+//                    contiguous, coalesced column segment.
+//   rank     int32   per node (heap order: node i of level l is 2^l - 1 + i)
+// A factor stores the same shapes (leaves -> lower Cholesky factors, bases ->
+// orthonormal Q_U / Q_V) in f64 or f32, plus per node the (2R)^2 matrices
+// Zf = L_S - I and Zi = L_S^-1 - I in f64.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define FIFA_CAP_MAX 64
+#define FIFA_LEAF_MAX 128
+#define FIFA_LEVELS_MAX 26
+#define FIFA_SPIN_LIMIT (1u << 26)
+
+// Status bits written by device code (OR-ed into a status word).
+#define FIFA_DEV_NOT_SPD 1
+#define FIFA_DEV_RANK_CAP 2
+#define FIFA_DEV_TIMEOUT 4
+
+struct HmatDesc {
+  int64_t n;
+  int L, nleaf, Bm, cap, kind;
+  const int* bnd;
+  const double* x;
+  double* leaves;
+  double* bases;
+  int* rank;
+  int* row_piv;
+  int* col_piv;
+  int* status;
+  double kc;      // kernel constant (0.5/rho^2 or sqrt(5)/rho)
+  double rho;
+  double nugget;
+  double eps;
+  double scale;   // view: A = scale * C~ + shift * I (U scaled by `scale`)
+  double shift;
+};
+
+struct FactDesc {
+  int64_t n;
+  int L, nleaf, Bm, cap, prec;  // prec: 0 = f64 storage, 1 = f32 storage
+  const int* bnd;
+  void* Lleaf;                  // nleaf x Bm x Bm lower Cholesky factors
+  void* Q;                      // L x cap x n orthonormal bases
+  double* Zf;                   // nnodes x (2cap)^2 : L_S - I
+  double* Zi;                   // nnodes x (2cap)^2 : L_S^-1 - I
+  double* Rw;                   // nnodes x 2 x cap^2 workspace (upper R of each side)
+  int* rank;                    // nnodes
+  double* ld_parts;             // nleaf + nnodes partial log-determinants
+  double* logdet;               // [1]
+  int* status;                  // [1]
+};
+
+__host__ __device__ inline int bnd_off(int l) { return (1 << l) - 1 + l; }
+__host__ __device__ inline int node_id(int l, int i) { return (1 << l) - 1 + i; }
+
+__device__ __forceinline__ void node_range(const int* bnd, int l, int i, int& s, int& h, int& e) {
+  s = bnd[bnd_off(l) + i];
+  e = bnd[bnd_off(l) + i + 1];
+  h = s + (e - s) / 2;
+}
+
+// Index of the level-l node that contains row p (binary search over bounds).
+__device__ __forceinline__ int node_of_row(const int* bnd, int l, int p) {
+  const int* b = bnd + bnd_off(l);
+  int lo = 0, hi = 1 << l;  // b[lo] <= p < b[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (b[mid] <= p) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic exponential (Cody-Waite reduction + degree-13 Taylor/Horner,
+// plain IEEE binary64 products and sums, never fused), the same operation
+// sequence as the CPU reference so kernel entries agree bit for bit.
+//   LN2_HI: ln 2 rounded to binary64 then truncated to 32 significand bits
+//   LN2_LO: (ln 2 - LN2_HI) rounded to binary64;  INV_LN2: 1/ln 2 rounded.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double det_exp(double x) {
+  if (!(x >= -708.0)) return x != x ? x : 0.0;
+  const double INV_LN2 = 0x1.71547652b82fep+0;
+  const double LN2_HI = 0x1.62e42fee00000p-1;
+  const double LN2_LO = 0x1.a39ef35793c76p-33;
+  double k = rint(__dmul_rn(x, INV_LN2));
+  double r = __dsub_rn(__dsub_rn(x, __dmul_rn(k, LN2_HI)), __dmul_rn(k, LN2_LO));
+  double p = 1.0 / 6227020800.0;                      // 1/13!
+  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 479001600.0);  // 1/12!
+  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 39916800.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 3628800.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 362880.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 40320.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 5040.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 720.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 120.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 24.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 6.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 2.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0);
+  long long kk = (long long)k;
+  double sc = __longlong_as_double((kk + 1023) << 52);
+  return __dmul_rn(p, sc);
+}
+
+// Unit-variance kernel entry k(xa, xb), bit-identical to the CPU reference.
+__device__ __forceinline__ double kern_entry(int kind, double kc, double xa, double xb) {
+  double d = __dsub_rn(xa, xb);
+  if (kind == 0) return det_exp(-__dmul_rn(__dmul_rn(d, d), kc));
+  double t = __dmul_rn(fabs(d), kc);
+  double poly = __dadd_rn(__dadd_rn(1.0, t), __ddiv_rn(__dmul_rn(t, t), 3.0));
+  return __dmul_rn(poly, det_exp(-t));
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide helpers (blockDim.x a multiple of 32, <= 1024).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum: result valid in every thread. `sh` >= 32 doubles.
+__device__ inline double block_sum(double v, double* sh) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double t = lane < nw ? sh[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) sh[32] = t;
+  }
+  __syncthreads();
+  double r = sh[32];
+  __syncthreads();
+  return r;
+}
+
+// (value, index) argmax with ties to the lowest index; value -1 = none.
+struct ArgMax {
+  double v;
+  int i;
+  double sv;  // signed value carried along
+};
+__device__ __forceinline__ ArgMax am_better(ArgMax a, ArgMax b) {
+  if (b.v > a.v || (b.v == a.v && b.i < a.i)) return b;
+  return a;
+}
+__device__ __forceinline__ ArgMax warp_argmax(ArgMax a) {
+  for (int o = 16; o > 0; o >>= 1) {
+    ArgMax b;
+    b.v = __shfl_down_sync(0xffffffffu, a.v, o);
+    b.i = __shfl_down_sync(0xffffffffu, a.i, o);
+    b.sv = __shfl_down_sync(0xffffffffu, a.sv, o);
+    a = am_better(a, b);
+  }
+  return a;
+}
+// Block argmax; result valid in every thread. `sh` >= 33 ArgMax slots.
+__device__ inline ArgMax block_argmax(ArgMax a, ArgMax* sh) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  a = warp_argmax(a);
+  __syncthreads();
+  if (lane == 0) sh[w] = a;
+  __syncthreads();
+  if (w == 0) {
+    ArgMax t = lane < nw ? sh[lane] : ArgMax{-1.0, 0x7fffffff, 0.0};
+    t = warp_argmax(t);
+    if (lane == 0) sh[32] = t;
+  }
+  __syncthreads();
+  ArgMax r = sh[32];
+  __syncthreads();
+  return r;
+}
+__device__ __forceinline__ double block_max(double v, double* sh) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double t = lane < nw ? sh[lane] : -1.0;
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
+    if (lane == 0) sh[32] = t;
+  }
+  __syncthreads();
+  double r = sh[32];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Small dense routines run by a whole block on row-major matrices with
+// leading dimension ld (shared or global memory).
+// ---------------------------------------------------------------------------
+// In place: A (r x r, symmetric, upper triangle read) -> upper R with A = R^T R.
+// Lower triangle is zeroed.  Returns false (in every thread) on a non-positive pivot.
+__device__ inline bool blk_chol_upper(double* A, int ld, int r, int* flag) {
+  if (threadIdx.x == 0) *flag = 0;
+  __syncthreads();
+  for (int k = 0; k < r; ++k) {
+    if (threadIdx.x == 0) {
+      double d = A[k * ld + k];
+      if (!(d > 0.0)) { *flag = 1; d = 1.0; }
+      A[k * ld + k] = sqrt(d);
+    }
+    __syncthreads();
+    double dk = A[k * ld + k];
+    for (int j = k + 1 + threadIdx.x; j < r; j += blockDim.x) A[k * ld + j] /= dk;
+    __syncthreads();
+    int m = r - k - 1;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      int i = k + 1 + t / m, j = k + 1 + t % m;
+      if (j >= i) A[i * ld + j] -= A[k * ld + i] * A[k * ld + j];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+    int i = t / r, j = t % r;
+    if (j < i) A[i * ld + j] = 0.0;
+  }
+  __syncthreads();
+  return *flag == 0;
+}
+
+// Rinv = R^-1 for upper-triangular R (r x r); one thread per column.
+__device__ inline void blk_triinv_upper(const double* R, int ldr, double* Ri, int ldi, int r) {
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
+    for (int i = r - 1; i >= 0; --i) {
+      double acc = (i == j) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= j; ++k) acc -= R[i * ldr + k] * Ri[k * ldi + j];
+      Ri[i * ldi + j] = (i <= j) ? acc / R[i * ldr + i] : 0.0;
+    }
+  }
+  __syncthreads();
+}
+
+// Li = L^-1 for lower-triangular L (r x r); one thread per column.
+__device__ inline void blk_triinv_lower(const double* Lm, int ldl, double* Li, int ldi, int r) {
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
+    for (int i = 0; i < r; ++i) {
+      double acc = (i == j) ? 1.0 : 0.0;
+      for (int k = j; k < i; ++k) acc -= Lm[i * ldl + k] * Li[k * ldi + j];
+      Li[i * ldi + j] = (i >= j) ? acc / Lm[i * ldl + i] : 0.0;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T> __device__ __forceinline__ double to_d(T v) { return (double)v; }
+
+// Bounded spin barrier among the G blocks of one group (counter monotone).
+// Returns false (in every thread) if the wait gave up; *err then has the
+// TIMEOUT bit set.
+__device__ inline bool group_barrier(unsigned int* counter, unsigned int target, int* err,
+                                     volatile int* abort_flag) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(counter, 1u);
+    unsigned int spins = 0;
+    ok = 1;
+    while (true) {
+      unsigned int v = *((volatile unsigned int*)counter);
+      if (v >= target) break;
+      if (*abort_flag) { ok = 0; break; }
+      if (++spins > FIFA_SPIN_LIMIT) {
+        atomicOr(err, FIFA_DEV_TIMEOUT);
+        *abort_flag = 1;
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}

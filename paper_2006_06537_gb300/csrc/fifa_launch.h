@@ -1,0 +1,34 @@
+// Host-side launchers of the device kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include "fifa_common.cuh"
+
+cudaError_t launch_leaf_assemble(const HmatDesc* Hd, int nleaf, cudaStream_t st);
+cudaError_t launch_aca(const HmatDesc* Hd, const int4* work, int ncta, bool cooperative, ArgMax* part,
+                       unsigned int* bar, int* abort_flag, cudaStream_t st);
+int aca_max_coresident_ctas();
+
+size_t leaf_factor_smem(int Bm, int L, int cap, int prec);
+size_t level_smem(int cap);
+size_t level_part_stride(int cap);
+cudaError_t launch_leaf_factor(const HmatDesc* Hd, const FactDesc* Fd, int prec, int nleaf, int Bm, int L, int cap,
+                               cudaStream_t st);
+cudaError_t launch_level(const FactDesc* Fd, int prec, int lvl, int nodes, int G, int cap, double* part,
+                         unsigned int* bar, int* abort_flag, cudaStream_t st);
+int level_max_coresident(int prec, int cap);
+cudaError_t launch_logdet_reduce(const FactDesc* Fd, cudaStream_t st);
+
+#define SWEEP_RHS_MAX 2
+cudaError_t launch_sweep_level(const FactDesc* Fd, int prec, int lvl, int nodes, int G, double* v, int nrhs, double* part,
+                               int zsel, int ztrans, cudaStream_t st);
+cudaError_t launch_sweep_leaf(const FactDesc* Fd, int prec, int nleaf, double* v, int nrhs, int mode, cudaStream_t st);
+cudaError_t launch_matvec(const HmatDesc* Hd, int nleaf, int L, const double* x, int nrhs, double* part, double* proj,
+                          double* y, cudaStream_t st);
+
+// vector / random / scalar kernels (k_gibbs.cu)
+cudaError_t launch_det_exp(const double* in, double* out, int64_t n, cudaStream_t st);
+cudaError_t launch_normals(uint64_t seed, uint32_t tag, const uint64_t* iter_dev, uint64_t iter_host, uint64_t stream_id,
+                           double* out, int64_t n, cudaStream_t st);
+cudaError_t launch_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64_t cnt, cudaStream_t st);
+cudaError_t launch_check_sorted(const double* x, int64_t n, int* flag, cudaStream_t st);

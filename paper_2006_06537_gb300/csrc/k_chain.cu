@@ -1,0 +1,126 @@
+// Scalar Gibbs updates on the device (one thread), so a whole iteration runs
+// without returning to the host (Sec. 4.1, Eqs. posterior_gibs2-4):
+//   sigma2 ~ IG(a_s + n/2, b_s + ||y - f||^2 / 2)
+//   tau2   ~ IG(a_t + n/2, b_t + q / 2),   q = ||W_C^-1 f||^2
+//   eta'   = eta + prop_sd z,  rho' = exp(eta')  (random-walk Metropolis on log rho)
+//   log alpha = -(logdet C~' - logdet C~)/2 - (q' - q)/(2 tau2) + log p(eta') - log p(eta)
+// On acceptance the current and proposed H-matrix / factor descriptors are
+// swapped in device memory, so the captured graph keeps reading "current"
+// from the same address.
+#include "fifa_chain.h"
+#include "fifa_common.cuh"
+#include "fifa_rng.cuh"
+
+__global__ void k_chain_make_view(const HmatDesc* __restrict__ Hc, HmatDesc* __restrict__ Mv, const ChainDev* __restrict__ c) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    HmatDesc d = *Hc;
+    d.scale = c->tau2 / c->sigma2;
+    d.shift = 1.0;
+    *Mv = d;
+  }
+}
+
+__global__ void k_chain_sigma2(ChainDev* __restrict__ c) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double shape = c->a_sigma2 + 0.5 * (double)c->n;
+  const double scale = c->b_sigma2 + 0.5 * c->rss;
+  const double g = gamma_mt(shape, c->seed, 2u, c->iter, c->chain_id);
+  c->sigma2 = scale / g;
+}
+
+__global__ void k_chain_tau2(ChainDev* __restrict__ c) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double shape = c->a_tau2 + 0.5 * (double)c->n;
+  const double scale = c->b_tau2 + 0.5 * c->q;
+  const double g = gamma_mt(shape, c->seed, 3u, c->iter, c->chain_id);
+  c->tau2 = scale / g;
+}
+
+__global__ void k_chain_propose(ChainDev* __restrict__ c, HmatDesc* __restrict__ Hp) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double z = philox_normal(c->seed, 0u, 4u, c->iter, c->chain_id);
+  const double eta = c->eta + c->prop_sd * z;
+  const double rho = exp(eta);
+  c->eta_prop = eta;
+  c->rho_prop = rho;
+  Hp->rho = rho;
+  Hp->kc = (c->kind == 0) ? __ddiv_rn(0.5, __dmul_rn(rho, rho)) : __ddiv_rn(sqrt(5.0), rho);
+}
+
+__device__ __forceinline__ double log_prior_eta(const ChainDev* c, double eta) {
+  const double z = (eta - c->logrho_mu) / c->logrho_sd;
+  return -0.5 * z * z;
+}
+
+template <typename D>
+__device__ __forceinline__ void swap_desc(D* a, D* b) {
+  D t = *a;
+  *a = *b;
+  *b = t;
+}
+
+__global__ void k_chain_mh(ChainDev* __restrict__ c, HmatDesc* __restrict__ Hc, HmatDesc* __restrict__ Hp,
+                           FactDesc* __restrict__ Fc, FactDesc* __restrict__ Fp, const FactDesc* __restrict__ Fm) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double ld_cur = *Fc->logdet, ld_prop = *Fp->logdet;
+  const int pst = *Fp->status | (*Hp->status & ~FIFA_DEV_RANK_CAP);
+  double la = -0.5 * (ld_prop - ld_cur) - (c->q_prop - c->q) / (2.0 * c->tau2) + log_prior_eta(c, c->eta_prop) -
+              log_prior_eta(c, c->eta);
+  if (pst != 0 || !isfinite(la)) la = -INFINITY;
+  const double u = philox_uniform(c->seed, 0u, 5u, c->iter, c->chain_id);
+  const int acc = (log(u) < la) ? 1 : 0;
+  c->status |= *Fm->status | (*Fc->status & ~FIFA_DEV_RANK_CAP);
+  c->accept = acc;
+  c->log_alpha = la;
+  if (acc) {
+    swap_desc(Hc, Hp);
+    swap_desc(Fc, Fp);
+    c->eta = c->eta_prop;
+    c->rho = c->rho_prop;
+  }
+  if (c->trace && c->trace_cap > 0) {
+    double* row = c->trace + (size_t)(c->iter % (uint64_t)c->trace_cap) * CHAIN_TRACE_FIELDS;
+    row[0] = (double)c->iter;
+    row[1] = c->sigma2;
+    row[2] = c->tau2;
+    row[3] = c->rho;
+    row[4] = (double)acc;
+    row[5] = la;
+    row[6] = acc ? ld_prop : ld_cur;
+    row[7] = c->q;
+    row[8] = c->rss;
+    row[9] = c->refine_res;
+    row[10] = (double)c->status;
+  }
+  c->iter += 1;
+}
+
+__global__ void k_ratio_sqrt(const double* __restrict__ num, const double* __restrict__ den, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = (*den > 0.0) ? sqrt(*num / *den) : 0.0;
+}
+
+cudaError_t launch_chain_make_view(const HmatDesc* Hc, HmatDesc* Mv, const ChainDev* c, cudaStream_t st) {
+  k_chain_make_view<<<1, 32, 0, st>>>(Hc, Mv, c);
+  return cudaGetLastError();
+}
+cudaError_t launch_chain_sigma2(ChainDev* c, cudaStream_t st) {
+  k_chain_sigma2<<<1, 32, 0, st>>>(c);
+  return cudaGetLastError();
+}
+cudaError_t launch_chain_tau2(ChainDev* c, cudaStream_t st) {
+  k_chain_tau2<<<1, 32, 0, st>>>(c);
+  return cudaGetLastError();
+}
+cudaError_t launch_chain_propose(ChainDev* c, HmatDesc* Hp, cudaStream_t st) {
+  k_chain_propose<<<1, 32, 0, st>>>(c, Hp);
+  return cudaGetLastError();
+}
+cudaError_t launch_chain_mh(ChainDev* c, HmatDesc* Hc, HmatDesc* Hp, FactDesc* Fc, FactDesc* Fp, const FactDesc* Fm,
+                            cudaStream_t st) {
+  k_chain_mh<<<1, 32, 0, st>>>(c, Hc, Hp, Fc, Fp, Fm);
+  return cudaGetLastError();
+}
+cudaError_t launch_ratio_sqrt(const double* num, const double* den, double* out, cudaStream_t st) {
+  k_ratio_sqrt<<<1, 32, 0, st>>>(num, den, out);
+  return cudaGetLastError();
+}

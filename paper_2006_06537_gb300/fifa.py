@@ -1,0 +1,275 @@
+"""Thin Python binding of the FIFA-GP C ABI (include/fifa.h).
+
+Argument marshalling only: every step runs in the CUDA library
+``_lib/libfifa.so``.  PyTorch provides the device arena, the stream and the
+device buffers (their ``data_ptr()`` is passed through).  Importing this module
+does not load the library; the first call does, and it raises if the library
+is missing -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libfifa.so")
+
+FIFA_OK, FIFA_ERR_INVALID_ARG, FIFA_ERR_UNSORTED, FIFA_ERR_NOT_SPD = 0, 1, 2, 3
+FIFA_ERR_RANK_CAP, FIFA_ERR_OOM, FIFA_ERR_CUDA, FIFA_ERR_TIMEOUT, FIFA_ERR_UNSUPPORTED = 4, 5, 6, 7, 8
+FIFA_KERNEL_SE, FIFA_KERNEL_MATERN52 = 0, 1
+FIFA_FP64, FIFA_MIXED = 0, 1
+FIFA_TRACE_FIELDS = 11
+TRACE_COLUMNS = ["iter", "sigma2", "tau2", "rho", "accept", "log_alpha", "logdet", "q", "rss", "refine_res", "status"]
+
+
+class fifa_hyper(C.Structure):
+    _fields_ = [("kernel", C.c_int), ("tau2", C.c_double), ("rho", C.c_double), ("sigma2", C.c_double),
+                ("nugget", C.c_double)]
+
+
+class fifa_opts(C.Structure):
+    _fields_ = [("leaf_size", C.c_int), ("aca_tol", C.c_double), ("rank_cap", C.c_int), ("prec", C.c_int),
+                ("refine_tol", C.c_double), ("refine_max", C.c_int)]
+
+
+class fifa_prior(C.Structure):
+    _fields_ = [("a_tau2", C.c_double), ("b_tau2", C.c_double), ("a_sigma2", C.c_double), ("b_sigma2", C.c_double),
+                ("logrho_mu", C.c_double), ("logrho_sd", C.c_double), ("prop_sd", C.c_double)]
+
+
+class FifaError(RuntimeError):
+    def __init__(self, code, where, detail=""):
+        self.code = code
+        super().__init__(f"{where}: {status_str(code)} ({code}){detail}")
+
+
+_lib = None
+_P = C.c_void_p
+
+
+def lib():
+    """Load libfifa.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"FIFA CUDA library not built: {LIB_PATH} missing (run __graft_entry__.build())")
+    L = C.CDLL(LIB_PATH)
+    sig = {
+        "fifa_create": (C.c_int, [C.POINTER(_P), C.POINTER(fifa_opts), _P, _P, C.c_size_t]),
+        "fifa_destroy_ctx": (None, [_P]),
+        "fifa_assemble": (C.c_int, [_P, _P, C.c_int64, C.POINTER(fifa_hyper), C.POINTER(_P)]),
+        "fifa_shift_scale": (C.c_int, [_P, _P, C.c_double, C.POINTER(_P)]),
+        "fifa_factor": (C.c_int, [_P, _P, C.POINTER(_P)]),
+        "fifa_logdet": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
+        "fifa_solve": (C.c_int, [_P, _P, _P, _P, C.c_int]),
+        "fifa_apply_W": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, C.c_int]),
+        "fifa_matvec": (C.c_int, [_P, _P, _P, _P, C.c_int]),
+        "fifa_sample": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_double, C.c_uint64, C.c_uint64, C.c_uint64,
+                                  _P, _P]),
+        "fifa_chain_create": (C.c_int, [_P, _P, _P, C.c_int64, C.POINTER(fifa_hyper), C.POINTER(fifa_prior),
+                                        C.c_uint64, C.c_uint64, C.POINTER(_P)]),
+        "fifa_gibbs_step": (C.c_int, [_P, _P, C.c_int, _P]),
+        "fifa_chain_get": (C.c_int, [_P, _P, _P, _P, C.POINTER(fifa_hyper)]),
+        "fifa_hmat_dims": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "fifa_hmat_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+        "fifa_fact_export": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+        "fifa_destroy_hmat": (None, [_P, _P]),
+        "fifa_destroy_fact": (None, [_P, _P]),
+        "fifa_destroy_chain": (None, [_P, _P]),
+        "fifa_status_str": (C.c_char_p, [C.c_int]),
+        "fifa_last_cuda_error": (C.c_char_p, [_P]),
+        "fifa_det_exp": (C.c_int, [_P, _P, _P, C.c_int64]),
+        "fifa_normals": (C.c_int, [_P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint64, _P, C.c_int64]),
+        "fifa_philox": (C.c_int, [_P, C.c_uint64, _P, _P, C.c_int64]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def status_str(code: int) -> str:
+    return lib().fifa_status_str(int(code)).decode()
+
+
+def _check(code, where, allow=(), ctx=None):
+    if code != FIFA_OK and code not in allow:
+        detail = ""
+        if code == FIFA_ERR_CUDA and ctx is not None:
+            detail = " [" + lib().fifa_last_cuda_error(ctx).decode() + "]"
+        raise FifaError(code, where, detail)
+    return code
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+# ---------------------------------------------------------------------------
+# One function per C entry point.
+# ---------------------------------------------------------------------------
+def fifa_create(opts: fifa_opts, stream_ptr: int, arena_ptr: int, arena_bytes: int):
+    h = C.c_void_p()
+    _check(lib().fifa_create(C.byref(h), C.byref(opts), C.c_void_p(stream_ptr), C.c_void_p(arena_ptr),
+                             C.c_size_t(arena_bytes)), "fifa_create")
+    return h
+
+
+def fifa_destroy_ctx(ctx):
+    lib().fifa_destroy_ctx(ctx)
+
+
+def fifa_assemble(ctx, x, n: int, hyper: fifa_hyper):
+    h = C.c_void_p()
+    _check(lib().fifa_assemble(ctx, _ptr(x), C.c_int64(n), C.byref(hyper), C.byref(h)), "fifa_assemble", ctx=ctx)
+    return h
+
+
+def fifa_shift_scale(ctx, Cm, s: float):
+    h = C.c_void_p()
+    _check(lib().fifa_shift_scale(ctx, Cm, C.c_double(s), C.byref(h)), "fifa_shift_scale", ctx=ctx)
+    return h
+
+
+def fifa_factor(ctx, A):
+    h = C.c_void_p()
+    _check(lib().fifa_factor(ctx, A, C.byref(h)), "fifa_factor", ctx=ctx)
+    return h
+
+
+def fifa_logdet(ctx, F, allow=()):
+    out = C.c_double()
+    code = _check(lib().fifa_logdet(ctx, F, C.byref(out)), "fifa_logdet", allow, ctx=ctx)
+    return out.value, code
+
+
+def fifa_solve(ctx, F, b, x, nrhs: int = 1):
+    _check(lib().fifa_solve(ctx, F, _ptr(b), _ptr(x), int(nrhs)), "fifa_solve", ctx=ctx)
+
+
+def fifa_apply_W(ctx, F, trans: int, inverse: int, x_in, x_out, nrhs: int = 1):
+    _check(lib().fifa_apply_W(ctx, F, int(trans), int(inverse), _ptr(x_in), _ptr(x_out), int(nrhs)), "fifa_apply_W", ctx=ctx)
+
+
+def fifa_matvec(ctx, A, x_in, x_out, nrhs: int = 1):
+    _check(lib().fifa_matvec(ctx, A, _ptr(x_in), _ptr(x_out), int(nrhs)), "fifa_matvec", ctx=ctx)
+
+
+def fifa_sample(ctx, Cm, WC, WM, y, tau2, sigma2, seed, stream_id, it, f, mean=None):
+    _check(lib().fifa_sample(ctx, Cm, WC, WM, _ptr(y), C.c_double(tau2), C.c_double(sigma2), C.c_uint64(seed),
+                             C.c_uint64(stream_id), C.c_uint64(it), _ptr(f), _ptr(mean)), "fifa_sample", ctx=ctx)
+
+
+def fifa_chain_create(ctx, x, y, n, init: fifa_hyper, prior: fifa_prior, seed: int, chain_id: int):
+    h = C.c_void_p()
+    _check(lib().fifa_chain_create(ctx, _ptr(x), _ptr(y), C.c_int64(n), C.byref(init), C.byref(prior),
+                                   C.c_uint64(seed), C.c_uint64(chain_id), C.byref(h)), "fifa_chain_create", ctx=ctx)
+    return h
+
+
+def fifa_gibbs_step(ctx, chain, iters: int, trace: np.ndarray | None = None, allow=()):
+    tp = trace.ctypes.data_as(C.c_void_p) if trace is not None else None
+    return _check(lib().fifa_gibbs_step(ctx, chain, int(iters), tp), "fifa_gibbs_step", allow, ctx=ctx)
+
+
+def fifa_chain_get(ctx, chain, f=None, mean=None):
+    h = fifa_hyper()
+    _check(lib().fifa_chain_get(ctx, chain, _ptr(f), _ptr(mean), C.byref(h)), "fifa_chain_get", ctx=ctx)
+    return h
+
+
+def fifa_hmat_dims(H):
+    n, L, nl, bm, cap = C.c_int64(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(lib().fifa_hmat_dims(H, C.byref(n), C.byref(L), C.byref(nl), C.byref(bm), C.byref(cap)), "fifa_hmat_dims")
+    return n.value, L.value, nl.value, bm.value, cap.value
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def fifa_hmat_export(ctx, H, allow=(FIFA_ERR_RANK_CAP,)):
+    n, L, nl, bm, cap = fifa_hmat_dims(H)
+    nn = max(1, (1 << L) - 1)
+    ranks = np.zeros(nn, np.int32)
+    rp = np.zeros(nn * cap, np.int32)
+    cp = np.zeros(nn * cap, np.int32)
+    bases = np.zeros(max(1, L) * cap * n)
+    leaves = np.zeros(nl * bm * bm)
+    code = _check(lib().fifa_hmat_export(ctx, H, _np_ptr(ranks), _np_ptr(rp), _np_ptr(cp), _np_ptr(bases),
+                                         _np_ptr(leaves)), "fifa_hmat_export", allow, ctx=ctx)
+    return dict(n=n, L=L, nleaf=nl, Bm=bm, cap=cap, ranks=ranks, row_piv=rp.reshape(nn, cap),
+                col_piv=cp.reshape(nn, cap), bases=bases.reshape(max(1, L), cap, n),
+                leaves=leaves.reshape(nl, bm, bm), status=code)
+
+
+def fifa_fact_export(ctx, F, dims, allow=()):
+    n, L, nl, bm, cap = dims
+    nn = max(1, (1 << L) - 1)
+    bases = np.zeros(max(1, L) * cap * n)
+    leaves = np.zeros(nl * bm * bm)
+    zf = np.zeros(nn * 4 * cap * cap)
+    zi = np.zeros(nn * 4 * cap * cap)
+    code = _check(lib().fifa_fact_export(ctx, F, _np_ptr(bases), _np_ptr(leaves), _np_ptr(zf), _np_ptr(zi)),
+                  "fifa_fact_export", allow)
+    return dict(bases=bases.reshape(max(1, L), cap, n), leaves=leaves.reshape(nl, bm, bm),
+                Zf=zf.reshape(nn, 2 * cap, 2 * cap), Zi=zi.reshape(nn, 2 * cap, 2 * cap), status=code)
+
+
+def fifa_destroy_hmat(ctx, H):
+    lib().fifa_destroy_hmat(ctx, H)
+
+
+def fifa_destroy_fact(ctx, F):
+    lib().fifa_destroy_fact(ctx, F)
+
+
+def fifa_destroy_chain(ctx, ch):
+    lib().fifa_destroy_chain(ctx, ch)
+
+
+def fifa_det_exp(ctx, x_in, x_out, n):
+    _check(lib().fifa_det_exp(ctx, _ptr(x_in), _ptr(x_out), C.c_int64(n)), "fifa_det_exp", ctx=ctx)
+
+
+def fifa_normals(ctx, seed, tag, it, stream_id, out, n):
+    _check(lib().fifa_normals(ctx, C.c_uint64(seed), C.c_uint32(tag), C.c_uint64(it), C.c_uint64(stream_id),
+                              _ptr(out), C.c_int64(n)), "fifa_normals", ctx=ctx)
+
+
+def fifa_philox(ctx, seed, ctr, out, count):
+    _check(lib().fifa_philox(ctx, C.c_uint64(seed), _ptr(ctr), _ptr(out), C.c_int64(count)), "fifa_philox", ctx=ctx)
+
+
+# ---------------------------------------------------------------------------
+# Convenience: a context whose arena and stream come from PyTorch.
+# ---------------------------------------------------------------------------
+class Context:
+    def __init__(self, leaf_size=64, aca_tol=1e-12, rank_cap=32, prec=FIFA_FP64, refine_tol=1e-12, refine_max=3,
+                 arena_bytes=1 << 30, device="cuda", stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.device)
+        self.opts = fifa_opts(int(leaf_size), float(aca_tol), int(rank_cap), int(prec), float(refine_tol),
+                              int(refine_max))
+        self.h = fifa_create(self.opts, self.stream.cuda_stream, self.arena.data_ptr(), int(arena_bytes))
+
+    def close(self):
+        if self.h is not None:
+            fifa_destroy_ctx(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
