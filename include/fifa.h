@@ -167,6 +167,11 @@ fifa_status fifa_chain_create(fifa_ctx* ctx, const double* x_dev, const double* 
 #define FIFA_TRACE_FIELDS 11
 fifa_status fifa_gibbs_step(fifa_ctx* ctx, fifa_chain* chain, int iters, double* trace_host);
 
+/* Kernel launches of one Gibbs iteration: the kernel nodes of the captured
+ * iteration graph (built by the first fifa_gibbs_step), or -1 if the chain
+ * runs without a graph.  Synchronizes nothing. */
+fifa_status fifa_chain_kernel_nodes(const fifa_chain* chain, int* out_host);
+
 /* Current state: f (and the last posterior mean tau2 C~ r) to device buffers
  * (nullable), hyperparameters to h_host (nullable); synchronizes. */
 fifa_status fifa_chain_get(fifa_ctx* ctx, const fifa_chain* chain, double* f_dev, double* mean_dev,

@@ -67,6 +67,8 @@ void Arena::release(void* p) {
     }                                     \
   } while (0)
 
+static inline int64_t n_of(const Plan* P) { return P->n; }
+
 static fifa_status dev_status_to_api(int s) {
   if (s & FIFA_DEV_TIMEOUT) return FIFA_ERR_TIMEOUT;
   if (s & FIFA_DEV_NOT_SPD) return FIFA_ERR_NOT_SPD;
@@ -160,11 +162,13 @@ Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st) {
   P->lvl_G.assign(P->L, 1);
   P->sweep_G.assign(P->L, 1);
   for (int l = 0; l < P->L; ++l) {
-    int64_t len = (n + ((int64_t)1 << l) - 1) >> l;
-    if (len > 8192) {
-      int64_t G = (len + 4095) / 4096;
-      while (((int64_t)1 << l) * G > lvl_cores && G > 1) G = (G + 1) / 2;
-      P->lvl_G[l] = (int)G;
+    const int64_t len = (n + ((int64_t)1 << l) - 1) >> l;
+    const int64_t nodes = (int64_t)1 << l;
+    // levels with fewer nodes than the co-resident CTAs split each node's rows
+    // over a group of CTAs (>= 1024 rows each) that fills the GPU
+    if (2 * nodes <= lvl_cores && len >= 2048) {
+      const int64_t G = std::min<int64_t>(len / 1024, lvl_cores / nodes);
+      P->lvl_G[l] = (int)std::max<int64_t>(1, G);
     }
     P->sweep_G[l] = (int)std::max<int64_t>(1, (len + 2047) / 2048);
   }
@@ -211,7 +215,7 @@ Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st) {
   add(sizeof(double) * sweep_ctas * 2 * cap * SWEEP_RHS_MAX);            // sweep partials
   add(sizeof(double) * (size_t)P->nleaf * std::max(1, P->L) * cap * SWEEP_RHS_MAX);  // matvec partials
   add(sizeof(double) * (size_t)std::max(1, P->nnodes) * 2 * cap * SWEEP_RHS_MAX);     // matvec projections
-  add(sizeof(double) * (size_t)n * 10);                                   // work vectors
+  add(sizeof(double) * (size_t)n * 16);                                   // work vectors
   add(sizeof(double) * 512);                                              // reduction partials
   add(256);                                                               // flags
   P->scratch_bytes = need;
@@ -238,7 +242,7 @@ Scratch carve(fifa_ctx* ctx, Plan* P) {
   S.sweep_part = (double*)take(sizeof(double) * sweep_ctas * 2 * cap * SWEEP_RHS_MAX);
   S.mv_part = (double*)take(sizeof(double) * (size_t)P->nleaf * std::max(1, P->L) * cap * SWEEP_RHS_MAX);
   S.mv_proj = (double*)take(sizeof(double) * (size_t)std::max(1, P->nnodes) * 2 * cap * SWEEP_RHS_MAX);
-  S.vec = (double*)take(sizeof(double) * (size_t)P->n * 10);
+  S.vec = (double*)take(sizeof(double) * (size_t)P->n * 16);
   S.red = (double*)take(sizeof(double) * 512);
   S.flags = (int*)take(256);
   return S;
@@ -515,7 +519,8 @@ fifa_status fact_enqueue(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev) {
       CK(cudaMemsetAsync(S.lvl_bar, 0, sizeof(unsigned int) * ((size_t)1 << l) * G, s));
       CK(cudaMemsetAsync(S.flags, 0, sizeof(int), s));
     }
-    CK(launch_level(F->dev, prec, l, 1 << l, G, cap, S.lvl_part, S.lvl_bar, S.flags, s));
+    const int side_max = (int)(((n_of(P) + ((int64_t)1 << l) - 1) >> l) + 1) / 2;
+    CK(launch_level(F->dev, prec, l, 1 << l, G, cap, S.lvl_part, S.lvl_bar, S.flags, side_max, s));
   }
   CK(launch_logdet_reduce(F->dev, s));
   return FIFA_OK;
@@ -617,33 +622,58 @@ extern "C" fifa_status fifa_matvec(fifa_ctx* ctx, const fifa_hmat* A, const doub
 }
 
 // x = A^-1 b, refined against the FP64 operator when the factor is FP32.
+// x = A^-1 b.  FP64 factor: W^-T W^-1 b.  FP32 factor: preconditioned conjugate
+// gradients on the FP64 operator F->src with W32 W32^T as preconditioner,
+// refine_max steps captured (a converged system's steps are no-ops); work
+// holds 4 n nrhs doubles.
 fifa_status solve_enqueue(fifa_ctx* ctx, const fifa_fact* F, const double* b, double* x, int nrhs, double* work,
                           double* res_dev) {
   const int64_t n = F->plan->n;
+  const int64_t nn = n * nrhs;
   cudaStream_t s = ctx->stream;
-  if (x != b) CK(cudaMemcpyAsync(x, b, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
+  if (x != b) CK(cudaMemcpyAsync(x, b, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
   fifa_status st = sweep_enqueue(ctx, F, 0, 1, x, nrhs);
   if (st == FIFA_OK) st = sweep_enqueue(ctx, F, 1, 1, x, nrhs);
   if (st != FIFA_OK || F->host.prec == 0 || !F->src) return st;
-  // iterative refinement: r = b - A x (FP64 operator), x += A32^-1 r
-  double* r = work;  // n * nrhs
+  Scratch S = carve(ctx, F->plan);
+  double* part = S.red;        // DOT_BLOCKS * nrhs partial sums
+  double* pst = S.red + 256;   // PCG state, 8 per right-hand side
+  double* r = work;
+  double* z = work + nn;
+  double* p = work + 2 * nn;
+  double* q = work + 3 * nn;
+  const double tol = ctx->opts.refine_tol > 0.0 ? ctx->opts.refine_tol : 1e-12;
+  auto prec_solve = [&](double* v) -> fifa_status {
+    fifa_status e = sweep_enqueue(ctx, F, 0, 1, v, nrhs);
+    return e == FIFA_OK ? sweep_enqueue(ctx, F, 1, 1, v, nrhs) : e;
+  };
+  st = matvec_enqueue(ctx, F->src, x, r, nrhs);
+  if (st != FIFA_OK) return st;
+  CK(launch_residual_axpy(b, r, nn, s));  // r = b - A x0
+  CK(launch_dot(b, b, n, nrhs, part, pst, 4, s));
+  CK(cudaMemcpyAsync(z, r, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  if ((st = prec_solve(z)) != FIFA_OK) return st;
+  CK(launch_dot(r, z, n, nrhs, part, pst, 0, s));
+  CK(cudaMemcpyAsync(p, z, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
   for (int it = 0; it < ctx->opts.refine_max; ++it) {
-    st = matvec_enqueue(ctx, F->src, x, r, nrhs);
-    if (st != FIFA_OK) return st;
-    CK(launch_residual_axpy(b, r, n * nrhs, s));  // r <- b - r
-    st = sweep_enqueue(ctx, F, 0, 1, r, nrhs);
-    if (st == FIFA_OK) st = sweep_enqueue(ctx, F, 1, 1, r, nrhs);
-    if (st != FIFA_OK) return st;
-    CK(launch_axpy(1.0, r, x, n * nrhs, s));  // x += r
+    if ((st = matvec_enqueue(ctx, F->src, p, q, nrhs)) != FIFA_OK) return st;
+    CK(launch_dot(p, q, n, nrhs, part, pst, 1, s));
+    CK(launch_dot(r, r, n, nrhs, part, pst, 3, s));
+    CK(launch_pcg_alpha(pst, nrhs, tol * tol, s));
+    CK(launch_pcg_xr(x, r, p, q, pst, n, nrhs, s));
+    CK(cudaMemcpyAsync(z, r, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    if ((st = prec_solve(z)) != FIFA_OK) return st;
+    CK(launch_dot(r, z, n, nrhs, part, pst, 5, s));
+    CK(launch_pcg_beta(pst, nrhs, s));
+    CK(launch_pcg_p(p, z, pst, n, nrhs, s));
   }
-  if (res_dev) {  // final relative residual ||b - A x|| / ||b|| in FP64
-    Scratch S = carve(ctx, F->plan);
+  if (res_dev) {  // true relative residual ||b - A x|| / ||b|| in FP64
     st = matvec_enqueue(ctx, F->src, x, r, nrhs);
     if (st != FIFA_OK) return st;
-    CK(launch_residual_axpy(b, r, n * nrhs, s));
-    CK(launch_sumsq(r, nullptr, n * nrhs, S.red, S.red + 256, s));
-    CK(launch_sumsq(b, nullptr, n * nrhs, S.red, S.red + 257, s));
-    CK(launch_ratio_sqrt(S.red + 256, S.red + 257, res_dev, s));
+    CK(launch_residual_axpy(b, r, nn, s));
+    CK(launch_sumsq(r, nullptr, nn, S.red, S.red + 300, s));
+    CK(launch_sumsq(b, nullptr, nn, S.red, S.red + 301, s));
+    CK(launch_ratio_sqrt(S.red + 300, S.red + 301, res_dev, s));
   }
   return FIFA_OK;
 }
@@ -655,9 +685,9 @@ extern "C" fifa_status fifa_solve(fifa_ctx* ctx, const fifa_fact* F, const doubl
   Scratch S = carve(ctx, F->plan);
   const int64_t n = F->plan->n;
   const double* b = b_dev;
-  if (b_dev == x_dev && F->host.prec) {  // refinement needs the original right-hand side
-    CK(cudaMemcpyAsync(S.vec + 2 * n * nrhs, b_dev, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
-    b = S.vec + 2 * n * nrhs;
+  if (b_dev == x_dev && F->host.prec) {  // the iteration needs the original right-hand side
+    CK(cudaMemcpyAsync(S.vec + 8 * n, b_dev, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
+    b = S.vec + 8 * n;
   }
   return solve_enqueue(ctx, F, b, x_dev, nrhs, S.vec);
 }
@@ -677,8 +707,8 @@ fifa_status sample_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* W
   double* Ca = S.vec + 2 * n; // n
   double* rhs = S.vec + 3 * n;// 2n : [Z, y/sigma2] -> [w, r]
   double* Cr = S.vec + 5 * n; // n
-  double* work = S.vec + 6 * n; // 2n (refinement)
-  double* bsave = S.vec + 8 * n; // 2n (refinement rhs)
+  double* bsave = S.vec + 6 * n; // 2n (iteration right-hand sides)
+  double* work = S.vec + 8 * n; // 8n (conjugate-gradient vectors)
   CK(launch_normals(seed, 0, iter_dev, iter_host, sid, a, n, s));
   CK(launch_normals(seed, 1, iter_dev, iter_host, sid, b, n, s));
   fifa_status st = matvec_enqueue(ctx, C, a, Ca, 1);

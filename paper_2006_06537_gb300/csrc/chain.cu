@@ -317,3 +317,20 @@ extern "C" void fifa_destroy_chain(fifa_ctx* ctx, fifa_chain* ch) {
   ctx->arena.release(ch->dev);
   delete ch;
 }
+
+extern "C" fifa_status fifa_chain_kernel_nodes(const fifa_chain* ch, int* out_host) {
+  if (!ch || !out_host) return FIFA_ERR_INVALID_ARG;
+  *out_host = -1;
+  if (!ch->graph) return FIFA_OK;
+  size_t count = 0;
+  if (cudaGraphGetNodes(ch->graph, nullptr, &count) != cudaSuccess) return FIFA_ERR_CUDA;
+  std::vector<cudaGraphNode_t> nodes(count);
+  if (count && cudaGraphGetNodes(ch->graph, nodes.data(), &count) != cudaSuccess) return FIFA_ERR_CUDA;
+  int kernels = 0;
+  for (size_t i = 0; i < count; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+  }
+  *out_host = kernels;
+  return FIFA_OK;
+}

@@ -38,7 +38,7 @@ struct Scratch {
   double* sweep_part;
   double* mv_part;
   double* mv_proj;
-  double* vec;  // 10 n doubles
+  double* vec;  // 16 n doubles
   double* red;  // 512 doubles of reduction partials
   int* flags;
 };
@@ -96,6 +96,13 @@ cudaError_t launch_prep_hmat(HmatDesc* H, int nnodes, cudaStream_t st);
 cudaError_t launch_prep_fact(FactDesc* F, const HmatDesc* H, int nnodes, cudaStream_t st);
 cudaError_t launch_sumsq(const double* a, const double* b, int64_t n, double* part, double* out, cudaStream_t st);
 cudaError_t launch_axpy(double a, const double* x, double* y, int64_t n, cudaStream_t st);
+cudaError_t launch_dot(const double* a, const double* b, int64_t n, int nrhs, double* part, double* st, int slot,
+                       cudaStream_t stream);
+cudaError_t launch_pcg_alpha(double* st, int nrhs, double tol2, cudaStream_t stream);
+cudaError_t launch_pcg_beta(double* st, int nrhs, cudaStream_t stream);
+cudaError_t launch_pcg_xr(double* x, double* r, const double* p, const double* q, const double* st, int64_t n, int nrhs,
+                          cudaStream_t stream);
+cudaError_t launch_pcg_p(double* p, const double* z, const double* st, int64_t n, int nrhs, cudaStream_t stream);
 cudaError_t launch_residual_axpy(const double* b, double* r, int64_t n, cudaStream_t st);
 cudaError_t launch_alg1_rhs(const double* Ca, const double* Wb, const double* y, double* rhs, int64_t n, double tau2,
                             double sigma2, const double* scal_dev, cudaStream_t st);

@@ -209,13 +209,24 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
 // leading dimension ld (shared or global memory).
 // ---------------------------------------------------------------------------
 // In place: A (r x r, symmetric, upper triangle read) -> upper R with A = R^T R.
-// Lower triangle is zeroed.  Returns false (in every thread) on a non-positive pivot.
-__device__ inline bool blk_chol_upper(double* A, int ld, int r, int* flag) {
-  if (threadIdx.x == 0) *flag = 0;
+// Lower triangle is zeroed.  Returns false (in every thread) on a non-positive
+// pivot.  clamp > 0: a pivot below clamp * (largest diagonal entry) is raised to
+// that value instead (modified Cholesky: the result factors a nearby SPD
+// matrix; used for factors that only precondition an FP64 iteration).
+__device__ inline bool blk_chol_upper(double* A, int ld, int r, int* flag, double clamp = 0.0) {
+  __shared__ double chol_floor;
+  if (threadIdx.x == 0) {
+    *flag = 0;
+    double dmax = 0.0;
+    for (int k = 0; k < r; ++k) dmax = fmax(dmax, A[k * ld + k]);
+    chol_floor = clamp * dmax;
+  }
   __syncthreads();
+  const double floor_v = chol_floor;
   for (int k = 0; k < r; ++k) {
     if (threadIdx.x == 0) {
       double d = A[k * ld + k];
+      if (clamp > 0.0 && !(d > floor_v)) d = floor_v > 0.0 ? floor_v : 1.0;
       if (!(d > 0.0)) { *flag = 1; d = 1.0; }
       A[k * ld + k] = sqrt(d);
     }

@@ -11,11 +11,15 @@ int aca_max_coresident_ctas();
 
 size_t leaf_factor_smem(int Bm, int L, int cap, int prec);
 size_t level_smem(int cap);
-size_t level_part_stride(int cap);
+// Doubles per CTA slot of the level kernel's partial sums: a cap x cap Gram
+// matrix or a 2cap x 8 projection block.
+__host__ __device__ inline size_t level_part_stride(int cap) {
+  return (size_t)(cap * cap > 2 * cap * 8 ? cap * cap : 2 * cap * 8);
+}
 cudaError_t launch_leaf_factor(const HmatDesc* Hd, const FactDesc* Fd, int prec, int nleaf, int Bm, int L, int cap,
                                cudaStream_t st);
 cudaError_t launch_level(const FactDesc* Fd, int prec, int lvl, int nodes, int G, int cap, double* part,
-                         unsigned int* bar, int* abort_flag, cudaStream_t st);
+                         unsigned int* bar, int* abort_flag, int side_max, cudaStream_t st);
 int level_max_coresident(int prec, int cap);
 cudaError_t launch_logdet_reduce(const FactDesc* Fd, cudaStream_t st);
 

@@ -201,8 +201,7 @@ __global__ void __launch_bounds__(256) k_mv_proj(const HmatDesc* __restrict__ Hd
   const int s = bnd[bnd_off(L) + leaf], e = bnd[bnd_off(L) + leaf + 1], m = e - s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int l = 0; l < L; ++l) {
-    const int a = node_of_row(bnd, l, s);
-    const int r = Hd->rank[node_id(l, a)];
+    const int r = Hd->rank[node_id(l, leaf >> (L - l))];  // level-l ancestor of the leaf
     for (int t = warp; t < r * nrhs; t += nw) {
       const int c = t / nrhs, j = t % nrhs;
       const double* bc = Hd->bases + ((size_t)l * cap + c) * n + s;
@@ -254,12 +253,9 @@ __global__ void __launch_bounds__(128) k_mv_expand(const HmatDesc* __restrict__ 
     xs[j * FIFA_LEAF_MAX + i] = x[(size_t)j * n + s + i];
   }
   for (int l = threadIdx.x; l < L; l += blockDim.x) {
-    int a = node_of_row(bnd, l, s);
-    int as, ah, ae;
-    node_range(bnd, l, a, as, ah, ae);
-    int nid = node_id(l, a);
+    const int nid = node_id(l, leaf >> (L - l));           // level-l ancestor of the leaf
     rk[l] = Hd->rank[nid];
-    int other = s < ah ? 1 : 0;  // rows in the left child use V^T x_right
+    const int other = ((leaf >> (L - l - 1)) & 1) ? 0 : 1;  // rows in the left child use V^T x_right
     for (int c = 0; c < rk[l]; ++c)
       for (int j = 0; j < nrhs; ++j)
         pr[(l * FIFA_CAP_MAX + c) * SW_RHS_MAX + j] = proj[(((size_t)nid * 2 + other) * cap + c) * SW_RHS_MAX + j];

@@ -17,8 +17,6 @@
 #include "fifa_launch.h"
 
 #define LF_NCH 32
-#define LV_TR 32
-#define LV_NC 16
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict__ Hd, const FactDesc* __restrict__ Fd) {
@@ -79,15 +77,21 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
   if (sizeof(T) != sizeof(double)) {
     for (int t = threadIdx.x; t < m * ld; t += blockDim.x) La[t] = (T)A[t];
   }
-  // column list of all ancestor bases restricted to this leaf
+  // column list of all ancestor bases restricted to this leaf: the level-l
+  // ancestor of leaf i is node i >> (L - l); the leaf lies in its left child
+  // (U rows, scaled in a view) when bit L - l - 1 of i is clear
   __shared__ int ncols;
+  __shared__ int rkl[FIFA_LEVELS_MAX];
+  __shared__ double lscale[FIFA_LEVELS_MAX];
+  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    rkl[l] = Hd->rank[node_id(l, leaf >> (L - l))];
+    lscale[l] = ((leaf >> (L - l - 1)) & 1) ? 1.0 : sc;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int c = 0;
-    for (int l = 0; l < L; ++l) {
-      int a = node_of_row(bnd, l, s);
-      int r = Hd->rank[node_id(l, a)];
-      for (int q = 0; q < r; ++q) clist[c++] = (l << 8) | q;
-    }
+    for (int l = 0; l < L; ++l)
+      for (int q = 0; q < rkl[l]; ++q) clist[c++] = (l << 8) | q;
     ncols = c;
   }
   __syncthreads();
@@ -97,10 +101,7 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
     for (int t = threadIdx.x; t < w * m; t += blockDim.x) {
       int cc = t / m, i = t % m;
       int code = clist[c0 + cc], l = code >> 8, q = code & 255;
-      int a = node_of_row(bnd, l, s);
-      int as, ah, ae;
-      node_range(bnd, l, a, as, ah, ae);
-      double scl = (s < ah) ? sc : 1.0;  // U rows of the view are scaled
+      const double scl = lscale[l];
       double v = Hd->bases[((size_t)l * cap + q) * n + s + i];
       X[cc * ld + i] = (T)((scl == 1.0) ? v : __dmul_rn(scl, v));
     }
@@ -126,109 +127,189 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// Level kernel helpers.
+// Level kernel.  Every pass over a node's rows is row-parallel: each thread
+// walks rows p = a0 + tid, a0 + tid + NT, ... with coalesced column loads and
+// keeps its partial sums in registers (register tiles of at most 4 x 8 or the
+// 36 pair products of a rank <= 8 Gram matrix); one deterministic block
+// reduction (fixed butterfly, fixed warp order) then combines them.  Small
+// dense algebra (r <= cap) runs in shared memory.
 // ---------------------------------------------------------------------------
-// Partial Gram (upper triangle + mirror) of columns 0..r-1 of Xb over rows [a0, a1).
-template <typename T>
-__device__ void gram_rows(const T* Xb, int64_t n, int r, int a0, int a1, double* tile, double* out, int ld) {
-  const int npair = r * (r + 1) / 2;
-  double acc[9];
+#define LV_QB 4  // basis columns per register tile
+#define LV_W 8   // ancestor columns per register tile / update chunk
+#define LV_RED 64
+
+// Sum nv per-thread values over the block into out[0..nv) (shared); NV >= nv.
+template <int NV>
+__device__ __forceinline__ void block_reduce_vec(double (&v)[NV], double* scratch, double* out, int nv) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-  for (int q = 0; q < 9; ++q) acc[q] = 0.0;
-  for (int p0 = a0; p0 < a1; p0 += LV_TR) {
-    const int tr = min(LV_TR, a1 - p0);
-    __syncthreads();
-    for (int t = threadIdx.x; t < tr * r; t += blockDim.x) {
-      int c = t / tr, p = t % tr;
-      tile[p * FIFA_CAP_MAX + c] = to_d(Xb[(size_t)c * n + p0 + p]);
+  for (int q = 0; q < NV; ++q) {
+    double x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    v[q] = x;
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+      if (q < nv) scratch[w * LV_RED + q] = v[q];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += scratch[k * LV_RED + q];
+    out[q] = s;
+  }
+  __syncthreads();
+}
+
+// G[a*ldg + b] = sum over rows [a0, a1) of X[a][p] X[b][p] for a, b < r.
+template <typename T>
+__device__ void gram_pass(const T* __restrict__ Xb, int64_t n, int r, int a0, int a1, double* scratch, double* tmp,
+                          double* G, int ldg) {
+  if (r <= 8) {
+    constexpr int NP = 36;
+    double acc[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) acc[q] = 0.0;
+    for (int p = a0 + threadIdx.x; p < a1; p += blockDim.x) {
+      double x[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) x[c] = c < r ? to_d(Xb[(size_t)c * n + p]) : 0.0;
+      int q = 0;
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = a; b < 8; ++b) acc[q++] += x[a] * x[b];
+    }
+    block_reduce_vec<NP>(acc, scratch, tmp, NP);
+    for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+      const int a = t / r, b = t % r, i = min(a, b), j = max(a, b);
+      G[a * ldg + b] = tmp[i * 8 - i * (i - 1) / 2 + (j - i)];
     }
     __syncthreads();
+    return;
+  }
+  const int nb = (r + LV_QB - 1) / LV_QB;
+  for (int bi = 0; bi < nb; ++bi) {
+    for (int bj = bi; bj < nb; ++bj) {
+      double acc[LV_QB * LV_QB];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      int pr = threadIdx.x + q * blockDim.x;
-      if (pr < npair) {
-        int a = 0, rem = pr;
-        while (rem >= r - a) { rem -= r - a; ++a; }
-        int b = a + rem;
-        double sacc = 0.0;
-        for (int p = 0; p < tr; ++p) sacc += tile[p * FIFA_CAP_MAX + a] * tile[p * FIFA_CAP_MAX + b];
-        acc[q] += sacc;
+      for (int q = 0; q < LV_QB * LV_QB; ++q) acc[q] = 0.0;
+      for (int p = a0 + threadIdx.x; p < a1; p += blockDim.x) {
+        double xa[LV_QB], xb[LV_QB];
+#pragma unroll
+        for (int c = 0; c < LV_QB; ++c) {
+          const int ca = bi * LV_QB + c, cb = bj * LV_QB + c;
+          xa[c] = ca < r ? to_d(Xb[(size_t)ca * n + p]) : 0.0;
+          xb[c] = cb < r ? to_d(Xb[(size_t)cb * n + p]) : 0.0;
+        }
+#pragma unroll
+        for (int a = 0; a < LV_QB; ++a)
+#pragma unroll
+          for (int b = 0; b < LV_QB; ++b) acc[a * LV_QB + b] += xa[a] * xb[b];
       }
+      block_reduce_vec<LV_QB * LV_QB>(acc, scratch, tmp, LV_QB * LV_QB);
+      for (int t = threadIdx.x; t < LV_QB * LV_QB; t += blockDim.x) {
+        const int a = bi * LV_QB + t / LV_QB, b = bj * LV_QB + t % LV_QB;
+        if (a < r && b < r) {
+          G[a * ldg + b] = tmp[t];
+          G[b * ldg + a] = tmp[t];
+        }
+      }
+      __syncthreads();
     }
   }
+}
+
+template <typename T, int RB>
+__device__ __forceinline__ void rowmul_row(T* __restrict__ Xb, int64_t n, int r, int p, const double* Ri, int ldr) {
+  double x[RB];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    int pr = threadIdx.x + q * blockDim.x;
-    if (pr < npair) {
-      int a = 0, rem = pr;
-      while (rem >= r - a) { rem -= r - a; ++a; }
-      int b = a + rem;
-      out[a * ld + b] = acc[q];
-      out[b * ld + a] = acc[q];
+  for (int c = 0; c < RB; ++c) x[c] = c < r ? to_d(Xb[(size_t)c * n + p]) : 0.0;
+#pragma unroll
+  for (int c = 0; c < RB; ++c) {
+    if (c < r) {
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a <= c; ++a) v += x[a] * Ri[a * ldr + c];
+      Xb[(size_t)c * n + p] = (T)v;
+    }
+  }
+}
+
+// Rows [a0, a1): X[:, p] <- X[:, p] Ri (r x r upper triangular, shared, ld ldr).
+template <typename T>
+__device__ void rowmul_pass(T* __restrict__ Xb, int64_t n, int r, int a0, int a1, const double* Ri, int ldr) {
+  for (int p = a0 + threadIdx.x; p < a1; p += blockDim.x) {
+    if (r <= 8) rowmul_row<T, 8>(Xb, n, r, p, Ri, ldr);
+    else if (r <= 16) rowmul_row<T, 16>(Xb, n, r, p, Ri, ldr);
+    else {
+      for (int c = r - 1; c >= 0; --c) {  // right to left: column c reads only columns <= c
+        double v = 0.0;
+        for (int a = 0; a <= c; ++a) v += to_d(Xb[(size_t)a * n + p]) * Ri[a * ldr + c];
+        Xb[(size_t)c * n + p] = (T)v;
+      }
     }
   }
   __syncthreads();
 }
 
-// Xb rows [a0, a1) <- Xb rows * Ri (r x r upper), optionally accumulating the
-// Gram matrix of the result into out (r x r, ld).
+// Pm[a * LV_W + j] = sum over rows [a0, a1) of Q[a][p] B_j[p] (storage-precision products).
 template <typename T>
-__device__ void rowmul_rows(T* Xb, int64_t n, int r, int a0, int a1, const double* Ri, int ldr, double* tile,
-                            double* tile2, double* out, int ld, bool gram) {
-  const int npair = r * (r + 1) / 2;
-  double acc[9];
+__device__ void proj_pass(const T* __restrict__ Qb, T* const* Bp, int w, int64_t n, int r, int a0, int a1,
+                          double* scratch, double* tmp, double* Pm) {
+  const int nb = (r + LV_QB - 1) / LV_QB;
+  for (int bi = 0; bi < nb; ++bi) {
+    T acc[LV_QB * LV_W];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) acc[q] = 0.0;
-  for (int p0 = a0; p0 < a1; p0 += LV_TR) {
-    const int tr = min(LV_TR, a1 - p0);
-    __syncthreads();
-    for (int t = threadIdx.x; t < tr * r; t += blockDim.x) {
-      int c = t / tr, p = t % tr;
-      tile[p * FIFA_CAP_MAX + c] = to_d(Xb[(size_t)c * n + p0 + p]);
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < tr * r; t += blockDim.x) {
-      int c = t / tr, p = t % tr;
-      double v = 0.0;
-      for (int a = 0; a <= c; ++a) v += tile[p * FIFA_CAP_MAX + a] * Ri[a * ldr + c];
-      tile2[p * FIFA_CAP_MAX + c] = v;
-      Xb[(size_t)c * n + p0 + p] = (T)v;
-    }
-    __syncthreads();
-    if (gram) {
+    for (int q = 0; q < LV_QB * LV_W; ++q) acc[q] = (T)0;
+    for (int p = a0 + threadIdx.x; p < a1; p += blockDim.x) {
+      T qv[LV_QB], bv[LV_W];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        int pr = threadIdx.x + q * blockDim.x;
-        if (pr < npair) {
-          int a = 0, rem = pr;
-          while (rem >= r - a) { rem -= r - a; ++a; }
-          int b = a + rem;
-          double sacc = 0.0;
-          for (int p = 0; p < tr; ++p) {
-            // use the stored (possibly rounded) values so Gram2 sees what Q holds
-            double va = to_d((T)tile2[p * FIFA_CAP_MAX + a]), vb = to_d((T)tile2[p * FIFA_CAP_MAX + b]);
-            sacc += va * vb;
-          }
-          acc[q] += sacc;
-        }
-      }
+      for (int c = 0; c < LV_QB; ++c) qv[c] = (bi * LV_QB + c < r) ? Qb[(size_t)(bi * LV_QB + c) * n + p] : (T)0;
+#pragma unroll
+      for (int j = 0; j < LV_W; ++j) bv[j] = j < w ? Bp[j][p] : (T)0;
+#pragma unroll
+      for (int a = 0; a < LV_QB; ++a)
+#pragma unroll
+        for (int j = 0; j < LV_W; ++j) acc[a * LV_W + j] += qv[a] * bv[j];
     }
+    double dv[LV_QB * LV_W];
+#pragma unroll
+    for (int q = 0; q < LV_QB * LV_W; ++q) dv[q] = (double)acc[q];
+    block_reduce_vec<LV_QB * LV_W>(dv, scratch, tmp, LV_QB * LV_W);
+    for (int t = threadIdx.x; t < LV_QB * LV_W; t += blockDim.x) {
+      const int a = bi * LV_QB + t / LV_W, j = t % LV_W;
+      if (a < r && j < w) Pm[a * LV_W + j] = tmp[t];
+    }
+    __syncthreads();
   }
-  if (gram) {
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      int pr = threadIdx.x + q * blockDim.x;
-      if (pr < npair) {
-        int a = 0, rem = pr;
-        while (rem >= r - a) { rem -= r - a; ++a; }
-        int b = a + rem;
-        out[a * ld + b] = acc[q];
-        out[b * ld + a] = acc[q];
-      }
-    }
-  }
-  __syncthreads();
 }
+
+// Rows [a0, a1): B_j[p] += sum_a Q[a][p] Tm[a * LV_W + j].
+template <typename T>
+__device__ void update_pass(const T* __restrict__ Qb, T* const* Bp, int w, int64_t n, int r, int a0, int a1,
+                            const T* Tm) {
+  for (int p = a0 + threadIdx.x; p < a1; p += blockDim.x) {
+    T acc[LV_W];
+#pragma unroll
+    for (int j = 0; j < LV_W; ++j) acc[j] = j < w ? Bp[j][p] : (T)0;
+    for (int a = 0; a < r; ++a) {
+      const T q = Qb[(size_t)a * n + p];
+#pragma unroll
+      for (int j = 0; j < LV_W; ++j) acc[j] += q * Tm[a * LV_W + j];
+    }
+#pragma unroll
+    for (int j = 0; j < LV_W; ++j)
+      if (j < w) Bp[j][p] = acc[j];
+  }
+}
+
+// Pivot floors of the modified Cholesky used by FP32-stored factors, which only
+// precondition an FP64 iteration (0: plain Cholesky, failures are reported).
+template <typename T> __device__ __forceinline__ double clamp_gram() { return sizeof(T) == 4 ? 1e-12 : 0.0; }
+template <typename T> __device__ __forceinline__ double clamp_cap() { return sizeof(T) == 4 ? 1e-6 : 0.0; }
 
 // Reduce `count` doubles of the G partials of this group (slot order fixed)
 // into dst; if G == 1 the partial already sits in dst.
@@ -253,8 +334,9 @@ __device__ inline bool group_reduce(double* dst, const double* src_local, int co
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_level(const FactDesc* __restrict__ Fd, int lvl, int G, double* __restrict__ part,
-                                               unsigned int* __restrict__ bar, int* __restrict__ abort_flag) {
+__global__ void __launch_bounds__(256, 2) k_level(const FactDesc* __restrict__ Fd, int lvl, int G, double* __restrict__ part,
+                                               unsigned int* __restrict__ bar, int* __restrict__ abort_flag,
+                                               int skip_le) {
   extern __shared__ double sm[];
   const int bi = blockIdx.x / G, g = blockIdx.x % G, base = blockIdx.x - g;
   const int nid = node_id(lvl, bi);
@@ -264,6 +346,7 @@ __global__ void __launch_bounds__(256) k_level(const FactDesc* __restrict__ Fd, 
   int s, h, e;
   node_range(bnd, lvl, bi, s, h, e);
   const int r = Fd->rank[nid];
+  if (r <= skip_le) return;  // handled by the small-node kernels
   if (r == 0) {
     if (g == 0 && threadIdx.x == 0) Fd->ld_parts[nleaf + nid] = 0.0;
     return;
@@ -279,47 +362,42 @@ __global__ void __launch_bounds__(256) k_level(const FactDesc* __restrict__ Fd, 
   double* R1 = Ri + cc2;
   double* RU = R1 + cc2;
   double* RV = RU + cc2;
-  double* tile = RV + cc2;                 // LV_TR x FIFA_CAP_MAX
-  double* tile2 = tile + LV_TR * FIFA_CAP_MAX;
-  double* Pm = tile2 + LV_TR * FIFA_CAP_MAX;  // 2cap x LV_NC
-  double* red = Pm + 2 * cap * LV_NC;       // 40
-  int* iflag = (int*)(red + 40);
-  int* alist = iflag + 4;                  // ancestor columns (level << 8 | col)
-  const size_t pstride = (size_t)max(cc2, 2 * cap * LV_NC);
+  double* scratch = RV + cc2;             // 8 warps x LV_RED
+  double* tmp = scratch + 8 * LV_RED;     // LV_RED
+  double* Pm = tmp + LV_RED;              // 2cap x LV_W
+  T* Tm = (T*)(Pm + 2 * cap * LV_W);      // 2cap x LV_W, storage precision
+  T** Bp = (T**)(Pm + 4 * cap * LV_W);    // LV_W column pointers
+  int* iflag = (int*)(Bp + LV_W);
+  int* alist = iflag + 4;                 // ancestor columns (level << 8 | col)
+  const size_t pstride = level_part_stride(cap);
   unsigned int phase = 0;
   bool ok = true;
 
   for (int side = 0; side < 2; ++side) {
     const int a0 = side == 0 ? max(r0, s) : max(r0, h);
     const int a1 = side == 0 ? min(r1, h) : min(r1, e);
-    T* Xb = Qb;  // columns at Qb + c*n, rows a0..a1
-    // Gram 1
-    for (int t = threadIdx.x; t < cc2; t += blockDim.x) Gm[t] = 0.0;
-    __syncthreads();
-    if (a1 > a0) gram_rows<T>(Xb, n, r, a0, a1, tile, Gm, cap);
+    // CholeskyQR2 of this side's basis: Gram, R1, Q1 = X R1^-1, Gram, R2, Q = Q1 R2^-1
+    gram_pass<T>(Qb, n, r, a0, a1, scratch, tmp, Gm, cap);
     if (!group_reduce(Gm, Gm, cc2, G, g, base, part, pstride, bar, phase, status, abort_flag)) return;
-    ok = blk_chol_upper(Gm, cap, r, iflag) && ok;
+    ok = blk_chol_upper(Gm, cap, r, iflag, clamp_gram<T>()) && ok;
     for (int t = threadIdx.x; t < cc2; t += blockDim.x) R1[t] = Gm[t];
     __syncthreads();
     blk_triinv_upper(Gm, cap, Ri, cap, r);
-    // Q1 = X R1^-1 in place, and its Gram
-    for (int t = threadIdx.x; t < cc2; t += blockDim.x) Gm[t] = 0.0;
-    __syncthreads();
-    if (a1 > a0) rowmul_rows<T>(Xb, n, r, a0, a1, Ri, cap, tile, tile2, Gm, cap, true);
+    rowmul_pass<T>(Qb, n, r, a0, a1, Ri, cap);
+    gram_pass<T>(Qb, n, r, a0, a1, scratch, tmp, Gm, cap);
     if (!group_reduce(Gm, Gm, cc2, G, g, base, part, pstride, bar, phase, status, abort_flag)) return;
-    ok = blk_chol_upper(Gm, cap, r, iflag) && ok;
+    ok = blk_chol_upper(Gm, cap, r, iflag, clamp_gram<T>()) && ok;
     blk_triinv_upper(Gm, cap, Ri, cap, r);
     double* Rs = side == 0 ? RU : RV;
     for (int t = threadIdx.x; t < cc2; t += blockDim.x) {
-      int i = t / cap, j = t % cap;
+      const int i = t / cap, j = t % cap;
       double v = 0.0;
       if (i < r && j < r && i <= j)
         for (int k = i; k <= j; ++k) v += Gm[i * cap + k] * R1[k * cap + j];
       Rs[t] = v;
     }
     __syncthreads();
-    // Q = Q1 R2^-1 in place
-    if (a1 > a0) rowmul_rows<T>(Xb, n, r, a0, a1, Ri, cap, tile, tile2, nullptr, cap, false);
+    rowmul_pass<T>(Qb, n, r, a0, a1, Ri, cap);
   }
   if (!ok && g == 0 && threadIdx.x == 0) atomicOr(status, FIFA_DEV_NOT_SPD);
 
@@ -329,26 +407,25 @@ __global__ void __launch_bounds__(256) k_level(const FactDesc* __restrict__ Fd, 
   double* Zi = Fd->Zi + (size_t)nid * ld2 * ld2;
   if (g == 0) {
     for (int t = threadIdx.x; t < r2 * r2; t += blockDim.x) {
-      int a = t / r2, b = t % r2;
+      const int a = t / r2, b = t % r2;
       double v = (a == b) ? 1.0 : 0.0;
       if (a < r && b >= r) {
-        int bb = b - r;
+        const int bb = b - r;
         for (int k = 0; k < r; ++k) v += RU[a * cap + k] * RV[bb * cap + k];
       } else if (a >= r && b < r) {
-        int aa = a - r;
+        const int aa = a - r;
         for (int k = 0; k < r; ++k) v += RV[aa * cap + k] * RU[b * cap + k];
       }
       Zf[a * ld2 + b] = v;
     }
     __syncthreads();
-    bool ok2 = blk_chol_upper(Zf, ld2, r2, iflag);  // Zf <- R_S (upper), S = R_S^T R_S, L_S = R_S^T
+    const bool ok2 = blk_chol_upper(Zf, ld2, r2, iflag, clamp_cap<T>());  // Zf <- R_S (upper), S = R_S^T R_S, L_S = R_S^T
     double ls = 0.0;
     for (int k = threadIdx.x; k < r2; k += blockDim.x) ls += log(Zf[k * ld2 + k]);
-    ls = block_sum(ls, red);
-    blk_triinv_upper(Zf, ld2, Zi, ld2, r2);         // Zi <- R_S^-1 (upper) = (L_S^-1)^T
-    // transpose both in place and subtract I
-    for (int t = threadIdx.x; t < r2 * r2; t += blockDim.x) {
-      int a = t / r2, b = t % r2;
+    ls = block_sum(ls, tmp);
+    blk_triinv_upper(Zf, ld2, Zi, ld2, r2);  // Zi <- R_S^-1 (upper) = (L_S^-1)^T
+    for (int t = threadIdx.x; t < r2 * r2; t += blockDim.x) {  // transpose in place, then subtract I
+      const int a = t / r2, b = t % r2;
       if (a < b) {
         double u = Zf[a * ld2 + b], l = Zf[b * ld2 + a];
         Zf[a * ld2 + b] = l;
@@ -376,68 +453,219 @@ __global__ void __launch_bounds__(256) k_level(const FactDesc* __restrict__ Fd, 
   }
   if (lvl == 0) return;
 
-  // ancestor columns on this node's rows
+  // the inverse node factor I + Q Zi Q^T applied to every ancestor basis on these rows
   __shared__ int nanc;
+  __shared__ int rka[FIFA_LEVELS_MAX];
+  for (int j = threadIdx.x; j < lvl; j += blockDim.x) rka[j] = Fd->rank[node_id(j, bi >> (lvl - j))];
+  __syncthreads();
   if (threadIdx.x == 0) {
     int c = 0;
-    for (int j = 0; j < lvl; ++j) {
-      int a = node_of_row(bnd, j, s);
-      int rj = Fd->rank[node_id(j, a)];
-      for (int q = 0; q < rj; ++q) alist[c++] = (j << 8) | q;
-    }
+    for (int j = 0; j < lvl; ++j)
+      for (int q = 0; q < rka[j]; ++q) alist[c++] = (j << 8) | q;
     nanc = c;
   }
   __syncthreads();
   const int na = nanc;
-  for (int c0 = 0; c0 < na; c0 += LV_NC) {
-    const int w = min(LV_NC, na - c0);
-    // P = Q^T B over own rows: rows < h -> P[0:r), rows >= h -> P[r:2r)
-    for (int t = threadIdx.x; t < 2 * cap * LV_NC; t += blockDim.x) Pm[t] = 0.0;
-    __syncthreads();
-    for (int t = threadIdx.x; t < r2 * w; t += blockDim.x) {
-      int a = t / w, cc = t % w;
-      int code = alist[c0 + cc], jl = code >> 8, q = code & 255;
-      const T* Bc = Qall + ((size_t)jl * cap + q) * n;
-      int p0 = a < r ? max(r0, s) : max(r0, h);
-      int p1 = a < r ? min(r1, h) : min(r1, e);
-      const T* Qc = Qb + (size_t)(a < r ? a : a - r) * n;
-      T acc = 0;
-      for (int p = p0; p < p1; ++p) acc += Qc[p] * Bc[p];
-      Pm[a * LV_NC + cc] = (double)acc;
+  for (int c0 = 0; c0 < na; c0 += LV_W) {
+    const int w = min(LV_W, na - c0);
+    if (threadIdx.x < LV_W) {
+      const int code = alist[c0 + min((int)threadIdx.x, w - 1)];
+      Bp[threadIdx.x] = Qall + ((size_t)(code >> 8) * cap + (code & 255)) * n;
     }
+    for (int t = threadIdx.x; t < 2 * cap * LV_W; t += blockDim.x) Pm[t] = 0.0;
     __syncthreads();
-    if (!group_reduce(Pm, Pm, 2 * cap * LV_NC, G, g, base, part, pstride, bar, phase, status, abort_flag)) return;
-    // T = Zi P
-    double tv[8];
-    int cnt = 0;
-    for (int t = threadIdx.x; t < r2 * w; t += blockDim.x) {
-      int a = t / w, cc = t % w;
+    proj_pass<T>(Qb, Bp, w, n, r, max(r0, s), min(r1, h), scratch, tmp, Pm);
+    proj_pass<T>(Qb, Bp, w, n, r, max(r0, h), min(r1, e), scratch, tmp, Pm + r * LV_W);
+    if (!group_reduce(Pm, Pm, 2 * cap * LV_W, G, g, base, part, pstride, bar, phase, status, abort_flag)) return;
+    for (int t = threadIdx.x; t < r2 * LV_W; t += blockDim.x) {
+      const int a = t / LV_W, j = t % LV_W;
       double acc = 0.0;
-      for (int b = 0; b < r2; ++b) acc += Zi[a * ld2 + b] * Pm[b * LV_NC + cc];
-      tv[cnt++] = acc;
+      if (j < w)
+        for (int b = 0; b < r2; ++b) acc += Zi[a * ld2 + b] * Pm[b * LV_W + j];
+      Tm[a * LV_W + j] = (T)acc;
     }
     __syncthreads();
-    cnt = 0;
+    update_pass<T>(Qb, Bp, w, n, r, max(r0, s), min(r1, h), Tm);
+    update_pass<T>(Qb, Bp, w, n, r, max(r0, h), min(r1, e), Tm + r * LV_W);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Small-node level kernel.  One CTA per node with sides of at most MS rows and
+// rank in (RLO, R].  The node's basis rows and each chunk of ancestor columns
+// are staged in shared memory, and every reduction is computed by one thread
+// per output entry (a dot product over the node's rows): no cross-thread FP64
+// reductions, so FP64 instructions are spent on the products alone.
+// ---------------------------------------------------------------------------
+template <typename T, int R, int RLO, int MS, int W>
+__global__ void __launch_bounds__(128) k_level_small(const FactDesc* __restrict__ Fd, int lvl) {
+  constexpr int R2 = 2 * R;
+  __shared__ double Xs[2][R][MS];   // side-major basis rows (FP64 during the QR)
+  __shared__ T Bs[W][2 * MS];       // ancestor-column chunk on the node's rows
+  __shared__ double Gm[R * R], Ri[R * R], R1[R * R], RU[R * R], RV[R * R];
+  __shared__ double S[R2 * R2], Si[R2 * R2];
+  __shared__ double Pm[R2 * W];
+  __shared__ T Tm[R2 * W];
+  __shared__ double red[40];
+  __shared__ int iflag[4];
+  __shared__ int alist[FIFA_LEVELS_MAX * FIFA_CAP_MAX];
+  __shared__ int rka[FIFA_LEVELS_MAX];
+  __shared__ int nanc;
+  const int bi = blockIdx.x;
+  const int nid = node_id(lvl, bi);
+  const int r = Fd->rank[nid];
+  if (r > R || r <= RLO) return;  // another bucket's launch takes this node
+  const int cap = Fd->cap, nleaf = Fd->nleaf;
+  const int64_t n = Fd->n;
+  const int* bnd = Fd->bnd;
+  int s, h, e;
+  node_range(bnd, lvl, bi, s, h, e);
+  if (r == 0) {
+    if (threadIdx.x == 0) Fd->ld_parts[nleaf + nid] = 0.0;
+    return;
+  }
+  T* Qall = (T*)Fd->Q;
+  T* Qb = Qall + (size_t)lvl * cap * n;
+  int* status = Fd->status;
+  const int mu = h - s, mv = e - h;  // rows per side
+  for (int t = threadIdx.x; t < r * MS; t += blockDim.x) {
+    const int c = t / MS, p = t % MS;
+    Xs[0][c][p] = p < mu ? (double)Qb[(size_t)c * n + s + p] : 0.0;
+    Xs[1][c][p] = p < mv ? (double)Qb[(size_t)c * n + h + p] : 0.0;
+  }
+  __syncthreads();
+  bool ok = true;
+  const double cg = clamp_gram<T>();
+  for (int side = 0; side < 2; ++side) {
+    const int m = side ? mv : mu;
+    double(*X)[MS] = Xs[side];
+    for (int pass = 0; pass < 2; ++pass) {
+      // Gram matrix, one thread per entry a <= b
+      for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+        const int a = t / r, b = t % r;
+        if (a <= b) {
+          double acc = 0.0;
+          for (int p = 0; p < m; ++p) acc += X[a][p] * X[b][p];
+          Gm[a * R + b] = acc;
+          Gm[b * R + a] = acc;
+        }
+      }
+      __syncthreads();
+      ok = blk_chol_upper(Gm, R, r, iflag, cg) && ok;
+      if (pass == 0) {
+        for (int t = threadIdx.x; t < R * R; t += blockDim.x) R1[t] = Gm[t];
+      } else {
+        double* Rs = side ? RV : RU;
+        for (int t = threadIdx.x; t < R * R; t += blockDim.x) {
+          const int i = t / R, j = t % R;
+          double v = 0.0;
+          if (i < r && j < r && i <= j)
+            for (int k = i; k <= j; ++k) v += Gm[i * R + k] * R1[k * R + j];
+          Rs[t] = v;
+        }
+      }
+      __syncthreads();
+      blk_triinv_upper(Gm, R, Ri, R, r);
+      // X <- X Ri, one thread per row (the row is read before it is overwritten)
+      for (int p = threadIdx.x; p < m; p += blockDim.x) {
+        double xr[R];
+#pragma unroll
+        for (int c = 0; c < R; ++c) xr[c] = c < r ? X[c][p] : 0.0;
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+          if (c < r) {
+            double v = 0.0;
+#pragma unroll
+            for (int a = 0; a <= c; ++a) v += xr[a] * Ri[a * R + c];
+            X[c][p] = (double)(T)v;  // the stored basis is rounded to T
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < r * MS; t += blockDim.x) {
+    const int c = t / MS, p = t % MS;
+    if (p < mu) Qb[(size_t)c * n + s + p] = (T)Xs[0][c][p];
+    if (p < mv) Qb[(size_t)c * n + h + p] = (T)Xs[1][c][p];
+  }
+  // capacitance: S = I + R X R^T, L_S = chol(S) = R_S^T
+  const int r2 = 2 * r;
+  for (int t = threadIdx.x; t < r2 * r2; t += blockDim.x) {
+    const int a = t / r2, b = t % r2;
+    double v = (a == b) ? 1.0 : 0.0;
+    if (a < r && b >= r) {
+      for (int k = 0; k < r; ++k) v += RU[a * R + k] * RV[(b - r) * R + k];
+    } else if (a >= r && b < r) {
+      for (int k = 0; k < r; ++k) v += RV[(a - r) * R + k] * RU[b * R + k];
+    }
+    S[a * R2 + b] = v;
+  }
+  __syncthreads();
+  ok = blk_chol_upper(S, R2, r2, iflag, clamp_cap<T>()) && ok;
+  double ls = 0.0;
+  for (int k = threadIdx.x; k < r2; k += blockDim.x) ls += log(S[k * R2 + k]);
+  ls = block_sum(ls, red);
+  blk_triinv_upper(S, R2, Si, R2, r2);
+  const int ld2 = 2 * cap;
+  double* Zf = Fd->Zf + (size_t)nid * ld2 * ld2;
+  double* Zi = Fd->Zi + (size_t)nid * ld2 * ld2;
+  for (int t = threadIdx.x; t < r2 * r2; t += blockDim.x) {
+    const int a = t / r2, b = t % r2;
+    const double d = (a == b) ? 1.0 : 0.0;
+    Zf[a * ld2 + b] = (a >= b ? S[b * R2 + a] : 0.0) - d;
+    Zi[a * ld2 + b] = (a >= b ? Si[b * R2 + a] : 0.0) - d;
+  }
+  if (threadIdx.x == 0) {
+    Fd->ld_parts[nleaf + nid] = ls;
+    if (!ok) atomicOr(status, FIFA_DEV_NOT_SPD);
+  }
+  if (lvl == 0) return;
+  // ancestor bases on the node's rows: B <- B + Q (L_S^-1 - I) Q^T B
+  for (int j = threadIdx.x; j < lvl; j += blockDim.x) rka[j] = Fd->rank[node_id(j, bi >> (lvl - j))];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int j = 0; j < lvl; ++j)
+      for (int q = 0; q < rka[j]; ++q) alist[c++] = (j << 8) | q;
+    nanc = c;
+  }
+  __syncthreads();
+  const int na = nanc, mn = e - s;
+  for (int c0 = 0; c0 < na; c0 += W) {
+    const int w = min(W, na - c0);
+    for (int t = threadIdx.x; t < w * mn; t += blockDim.x) {
+      const int j = t / mn, p = t % mn;
+      const int code = alist[c0 + j];
+      Bs[j][p] = Qall[((size_t)(code >> 8) * cap + (code & 255)) * n + s + p];
+    }
+    __syncthreads();
+    // P[a][j] = Q^T B: rows a < r from the left child, r <= a < 2r from the right
     for (int t = threadIdx.x; t < r2 * w; t += blockDim.x) {
-      int a = t / w, cc = t % w;
-      Pm[a * LV_NC + cc] = tv[cnt++];
+      const int a = t / w, j = t % w;
+      const int side = a >= r, c = side ? a - r : a, m = side ? mv : mu, off = side ? mu : 0;
+      T acc = (T)0;
+      for (int p = 0; p < m; ++p) acc += (T)Xs[side][c][p] * Bs[j][off + p];
+      Pm[a * W + j] = (double)acc;
     }
     __syncthreads();
-    // B += Q T over own rows (storage precision)
-    T* Tt = (T*)tile2;  // 2cap x LV_NC copy of T in the storage precision
+    // T = (L_S^-1 - I) P
     for (int t = threadIdx.x; t < r2 * w; t += blockDim.x) {
-      int a = t / w, cc = t % w;
-      Tt[a * LV_NC + cc] = (T)Pm[a * LV_NC + cc];
+      const int a = t / w, j = t % w;
+      double v = -Pm[a * W + j];
+      for (int b = 0; b <= a; ++b) v += Si[b * R2 + a] * Pm[b * W + j];
+      Tm[a * W + j] = (T)v;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < (r1 - r0) * w; t += blockDim.x) {
-      int cc = t / (r1 - r0), p = r0 + t % (r1 - r0);
-      int code = alist[c0 + cc], jl = code >> 8, q = code & 255;
-      T* Bc = Qall + ((size_t)jl * cap + q) * n;
-      const int off = p < h ? 0 : r;
-      T acc = Bc[p];
-      for (int a = 0; a < r; ++a) acc += Qb[(size_t)a * n + p] * Tt[(off + a) * LV_NC + cc];
-      Bc[p] = acc;
+    // B += Q T, one thread per (row, column)
+    for (int t = threadIdx.x; t < w * mn; t += blockDim.x) {
+      const int j = t / mn, p = t % mn;
+      const int side = p >= mu, pp = side ? p - mu : p, toff = side ? r : 0;
+      T acc = Bs[j][p];
+      for (int a = 0; a < r; ++a) acc += (T)Xs[side][a][pp] * Tm[(toff + a) * W + j];
+      const int code = alist[c0 + j];
+      Qall[((size_t)(code >> 8) * cap + (code & 255)) * n + s + p] = acc;
     }
     __syncthreads();
   }
@@ -462,10 +690,9 @@ size_t leaf_factor_smem(int Bm, int L, int cap, int prec) {
   return b;
 }
 size_t level_smem(int cap) {
-  return ((size_t)5 * cap * cap + 2 * LV_TR * FIFA_CAP_MAX + 2 * (size_t)cap * LV_NC + 40) * sizeof(double) +
+  return ((size_t)5 * cap * cap + 9 * LV_RED + 4 * (size_t)cap * LV_W) * sizeof(double) + LV_W * sizeof(void*) +
          (4 + (size_t)FIFA_LEVELS_MAX * cap) * sizeof(int);
 }
-size_t level_part_stride(int cap) { return (size_t)(cap * cap > 2 * cap * LV_NC ? cap * cap : 2 * cap * LV_NC); }
 
 static int smem_optin() {
   static int v = -1;
@@ -496,7 +723,22 @@ cudaError_t launch_leaf_factor(const HmatDesc* Hd, const FactDesc* Fd, int prec,
 
 template <typename T>
 static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, int G, int cap, double* part, unsigned int* bar,
-                                  int* abort_flag, cudaStream_t st) {
+                                  int* abort_flag, int side_max, cudaStream_t st) {
+  int skip = -1;
+  if (G == 1 && side_max <= 256) {
+    // small nodes staged in (static, < 48 KB) shared memory: rank buckets (0,4]
+    // and (4,8] for sides of <= 128 rows, (0,4] for sides of <= 256 rows
+    if (side_max <= 128) {
+      k_level_small<T, 4, -1, 128, 8><<<nodes, 128, 0, st>>>(Fd, lvl);
+      k_level_small<T, 8, 4, 128, 8><<<nodes, 128, 0, st>>>(Fd, lvl);
+      skip = 8;
+    } else {
+      k_level_small<T, 4, -1, 256, 4><<<nodes, 128, 0, st>>>(Fd, lvl);
+      skip = 4;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const size_t smem = level_smem(cap);
   if (smem > (size_t)smem_optin()) return cudaErrorInvalidConfiguration;
   if (smem > 48 * 1024) {
@@ -513,13 +755,13 @@ static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, int G,
   attr[0].val.cooperative = G > 1 ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_level<T>, Fd, lvl, G, part, bar, abort_flag);
+  return cudaLaunchKernelEx(&cfg, k_level<T>, Fd, lvl, G, part, bar, abort_flag, skip);
 }
 
 cudaError_t launch_level(const FactDesc* Fd, int prec, int lvl, int nodes, int G, int cap, double* part,
-                         unsigned int* bar, int* abort_flag, cudaStream_t st) {
-  return prec ? launch_level_t<float>(Fd, lvl, nodes, G, cap, part, bar, abort_flag, st)
-              : launch_level_t<double>(Fd, lvl, nodes, G, cap, part, bar, abort_flag, st);
+                         unsigned int* bar, int* abort_flag, int side_max, cudaStream_t st) {
+  return prec ? launch_level_t<float>(Fd, lvl, nodes, G, cap, part, bar, abort_flag, side_max, st)
+              : launch_level_t<double>(Fd, lvl, nodes, G, cap, part, bar, abort_flag, side_max, st);
 }
 
 int level_max_coresident(int prec, int cap) {

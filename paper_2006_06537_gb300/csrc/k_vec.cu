@@ -185,3 +185,98 @@ cudaError_t launch_sumsq(const double* a, const double* b, int64_t n, double* pa
   k_sumsq_final<<<1, 256, 0, st>>>(part, SUMSQ_BLOCKS, out);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Preconditioned conjugate gradients for nrhs independent systems, scalars on
+// the device.  State per right-hand side j at st[8 j + k]:
+//   k = 0 rho = r^T z, 1 p^T q, 2 alpha, 3 r^T r, 4 b^T b, 5 new rho, 6 beta.
+// A system whose residual has reached tol^2 b^T b takes alpha = 0 (no-op).
+// ---------------------------------------------------------------------------
+#define DOT_BLOCKS 120
+
+__global__ void k_dot_part(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                           double* __restrict__ part) {
+  __shared__ double red[40];
+  const int j = blockIdx.y;
+  const double* aj = a + (size_t)j * n;
+  const double* bj = b + (size_t)j * n;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += aj[i] * bj[i];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part[j * DOT_BLOCKS + blockIdx.x] = acc;
+}
+
+__global__ void k_dot_final(const double* __restrict__ part, double* __restrict__ st, int slot) {
+  __shared__ double red[40];
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < DOT_BLOCKS; i += blockDim.x) acc += part[j * DOT_BLOCKS + i];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) st[8 * j + slot] = acc;
+}
+
+__global__ void k_pcg_alpha(double* __restrict__ st, int nrhs, double tol2) {
+  const int j = threadIdx.x;
+  if (j >= nrhs) return;
+  double* s = st + 8 * j;
+  const double pq = s[1], rho = s[0];
+  double alpha = 0.0;
+  if (s[3] > tol2 * s[4] && pq > 0.0 && rho > 0.0 && isfinite(rho / pq)) alpha = rho / pq;
+  s[2] = alpha;
+}
+
+__global__ void k_pcg_beta(double* __restrict__ st, int nrhs) {
+  const int j = threadIdx.x;
+  if (j >= nrhs) return;
+  double* s = st + 8 * j;
+  const double beta = (s[2] != 0.0 && s[0] > 0.0 && isfinite(s[5] / s[0])) ? s[5] / s[0] : 0.0;
+  s[6] = beta;
+  if (s[2] != 0.0) s[0] = s[5];
+}
+
+__global__ void k_pcg_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                         const double* __restrict__ q, const double* __restrict__ st, int64_t n, int nrhs) {
+  const int64_t tot = n * nrhs;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = st[8 * (i / n) + 2];
+    if (a != 0.0) {
+      x[i] += a * p[i];
+      r[i] -= a * q[i];
+    }
+  }
+}
+
+// p <- z + beta p for systems still iterating (alpha != 0)
+__global__ void k_pcg_p(double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ st, int64_t n,
+                        int nrhs) {
+  const int64_t tot = n * nrhs;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const double* s = st + 8 * (i / n);
+    if (s[2] != 0.0) p[i] = z[i] + s[6] * p[i];
+  }
+}
+
+cudaError_t launch_dot(const double* a, const double* b, int64_t n, int nrhs, double* part, double* st, int slot,
+                       cudaStream_t stream) {
+  k_dot_part<<<dim3(DOT_BLOCKS, nrhs), 256, 0, stream>>>(a, b, n, part);
+  k_dot_final<<<nrhs, 128, 0, stream>>>(part, st, slot);
+  return cudaGetLastError();
+}
+cudaError_t launch_pcg_alpha(double* st, int nrhs, double tol2, cudaStream_t stream) {
+  k_pcg_alpha<<<1, 32, 0, stream>>>(st, nrhs, tol2);
+  return cudaGetLastError();
+}
+cudaError_t launch_pcg_beta(double* st, int nrhs, cudaStream_t stream) {
+  k_pcg_beta<<<1, 32, 0, stream>>>(st, nrhs);
+  return cudaGetLastError();
+}
+cudaError_t launch_pcg_xr(double* x, double* r, const double* p, const double* q, const double* st, int64_t n, int nrhs,
+                          cudaStream_t stream) {
+  k_pcg_xr<<<grid_for(n * nrhs), 256, 0, stream>>>(x, r, p, q, st, n, nrhs);
+  return cudaGetLastError();
+}
+cudaError_t launch_pcg_p(double* p, const double* z, const double* st, int64_t n, int nrhs, cudaStream_t stream) {
+  k_pcg_p<<<grid_for(n * nrhs), 256, 0, stream>>>(p, z, st, n, nrhs);
+  return cudaGetLastError();
+}

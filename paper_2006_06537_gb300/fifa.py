@@ -73,6 +73,7 @@ def lib():
                                         C.c_uint64, C.c_uint64, C.POINTER(_P)]),
         "fifa_gibbs_step": (C.c_int, [_P, _P, C.c_int, _P]),
         "fifa_chain_get": (C.c_int, [_P, _P, _P, _P, C.POINTER(fifa_hyper)]),
+        "fifa_chain_kernel_nodes": (C.c_int, [_P, C.POINTER(C.c_int)]),
         "fifa_hmat_dims": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "fifa_hmat_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
@@ -184,6 +185,12 @@ def fifa_chain_get(ctx, chain, f=None, mean=None):
     return h
 
 
+def fifa_chain_kernel_nodes(chain):
+    k = C.c_int()
+    _check(lib().fifa_chain_kernel_nodes(chain, C.byref(k)), "fifa_chain_kernel_nodes")
+    return k.value
+
+
 def fifa_hmat_dims(H):
     n, L, nl, bm, cap = C.c_int64(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
     _check(lib().fifa_hmat_dims(H, C.byref(n), C.byref(L), C.byref(nl), C.byref(bm), C.byref(cap)), "fifa_hmat_dims")
@@ -194,19 +201,19 @@ def _np_ptr(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
 
 
-def fifa_hmat_export(ctx, H, allow=(FIFA_ERR_RANK_CAP,)):
+def fifa_hmat_export(ctx, H, allow=(FIFA_ERR_RANK_CAP,), bases=True, leaves=True):
     n, L, nl, bm, cap = fifa_hmat_dims(H)
     nn = max(1, (1 << L) - 1)
     ranks = np.zeros(nn, np.int32)
     rp = np.zeros(nn * cap, np.int32)
     cp = np.zeros(nn * cap, np.int32)
-    bases = np.zeros(max(1, L) * cap * n)
-    leaves = np.zeros(nl * bm * bm)
-    code = _check(lib().fifa_hmat_export(ctx, H, _np_ptr(ranks), _np_ptr(rp), _np_ptr(cp), _np_ptr(bases),
-                                         _np_ptr(leaves)), "fifa_hmat_export", allow, ctx=ctx)
+    bs = np.zeros(max(1, L) * cap * n) if bases else None
+    lv = np.zeros(nl * bm * bm) if leaves else None
+    code = _check(lib().fifa_hmat_export(ctx, H, _np_ptr(ranks), _np_ptr(rp), _np_ptr(cp), _np_ptr(bs),
+                                         _np_ptr(lv)), "fifa_hmat_export", allow)
     return dict(n=n, L=L, nleaf=nl, Bm=bm, cap=cap, ranks=ranks, row_piv=rp.reshape(nn, cap),
-                col_piv=cp.reshape(nn, cap), bases=bases.reshape(max(1, L), cap, n),
-                leaves=leaves.reshape(nl, bm, bm), status=code)
+                col_piv=cp.reshape(nn, cap), bases=bs.reshape(max(1, L), cap, n) if bases else None,
+                leaves=lv.reshape(nl, bm, bm) if leaves else None, status=code)
 
 
 def fifa_fact_export(ctx, F, dims, allow=()):
