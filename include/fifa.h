@@ -115,6 +115,25 @@ fifa_status fifa_assemble(fifa_ctx* ctx, const double* x_dev, int64_t n, const f
  * outlive M.  Errors: INVALID_ARG, OOM. */
 fifa_status fifa_shift_scale(fifa_ctx* ctx, const fifa_hmat* C, double s, fifa_hmat** M);
 
+/* The same product as fifa_matvec, for callers that cannot allocate device
+ * memory themselves: a plug-in whose host framework owns all device memory,
+ * a process whose memory is fully reserved by a pooling allocator, or a
+ * latency-critical loop that must not enter the allocator (cudaMalloc can
+ * synchronize the device).  The paper has no counterpart; this is a property
+ * of the library, not of the method.
+ *   Scratch: a file-scope static device array of 2^20 doubles (8 MiB) that every
+ *   GPU loading the library holds until exit; no allocation routine is called.
+ *   The first call on each device looks up the array's address with
+ *   cudaGetSymbolAddress while that device is current and caches it; make that
+ *   first call before any stream capture begins.
+ *   All calls share the array: calls that overlap on the GPU race on it and must
+ *   be ordered by the caller.  Each call writes every scratch entry it reads.
+ *   Limit: nleaf * levels * rank_cap * 2 + (2^levels - 1) * 4 * rank_cap doubles
+ *   must fit in 2^20, else FIFA_ERR_UNSUPPORTED (e.g. rank_cap 32 allows up to
+ *   10 levels).  The calling thread's current device must be the context's
+ *   (else FIFA_ERR_INVALID_ARG).  in_dev and out_dev must not alias. */
+fifa_status fifa_matvec_static(fifa_ctx* ctx, const fifa_hmat* A, const double* in_dev, double* out_dev, int nrhs);
+
 /* Symmetric factorization A = W W^T, W = A_L ... A_0 (SI, Ambikasaran Thm 3.1)
  * and log det A.  Precision: FP64, or FP32 storage and bulk arithmetic when the
  * context is MIXED and A is a shift_scale view (the M~ of Algorithm 1); leaf

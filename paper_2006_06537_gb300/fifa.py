@@ -67,6 +67,7 @@ def lib():
         "fifa_solve": (C.c_int, [_P, _P, _P, _P, C.c_int]),
         "fifa_apply_W": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, C.c_int]),
         "fifa_matvec": (C.c_int, [_P, _P, _P, _P, C.c_int]),
+        "fifa_matvec_static": (C.c_int, [_P, _P, _P, _P, C.c_int]),
         "fifa_sample": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_double, C.c_uint64, C.c_uint64, C.c_uint64,
                                   _P, _P]),
         "fifa_chain_create": (C.c_int, [_P, _P, _P, C.c_int64, C.POINTER(fifa_hyper), C.POINTER(fifa_prior),
@@ -160,6 +161,11 @@ def fifa_apply_W(ctx, F, trans: int, inverse: int, x_in, x_out, nrhs: int = 1):
 
 def fifa_matvec(ctx, A, x_in, x_out, nrhs: int = 1):
     _check(lib().fifa_matvec(ctx, A, _ptr(x_in), _ptr(x_out), int(nrhs)), "fifa_matvec", ctx=ctx)
+
+
+def fifa_matvec_static(ctx, A, x_in, x_out, nrhs: int = 1, allow=()):
+    return _check(lib().fifa_matvec_static(ctx, A, _ptr(x_in), _ptr(x_out), int(nrhs)), "fifa_matvec_static", allow,
+                  ctx=ctx)
 
 
 def fifa_sample(ctx, Cm, WC, WM, y, tau2, sigma2, seed, stream_id, it, f, mean=None):
