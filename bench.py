@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fifa", choices=["fifa", "reference"])
     ap.add_argument("--n", type=int, default=N_FULL)
-    ap.add_argument("--leaf", type=int, default=0, help="leaf size (0 = autotune among 64/128)")
+    ap.add_argument("--leaf", type=int, default=0, help="leaf size (0 = the autotuner's cached choice)")
     ap.add_argument("--nugget", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -237,15 +237,18 @@ def gpu_arm(args):
         ctx.close()
         torch.cuda.synchronize()
 
-    # leaf-size autotune on the FP64 path (short runs on the workload's own data)
-    leaves = [args.leaf] if args.leaf else [32, 64, 128]
-    tune = {}
-    for lf in leaves:
-        ctx, ch, xd, yd = make(fifa.FIFA_FP64, lf)
-        ms, _ = time_chain(ctx, ch, 2, 1)
-        close(ctx, ch)
-        tune[lf] = ms / 2
-    leaf = min(tune, key=tune.get)
+    # leaf size: the autotuner's cached choice for this workload (tuned.json),
+    # measured once by `python -m paper_2006_06537_gb300.autotune`; tuned here
+    # (and cached) only if no entry exists yet
+    from paper_2006_06537_gb300 import autotune
+
+    if args.leaf:
+        leaf, tune = args.leaf, {}
+    else:
+        entry = autotune.load(autotune.workload_key("clustered_se", n))
+        if entry is None and rank == 0:
+            entry = autotune.tune_clustered(n, nugget=args.nugget)
+        leaf, tune = (entry["leaf"], entry["ms_per_iter"]) if entry else (32, {})
 
     results = {}
     for name, prec in (("fp64", fifa.FIFA_FP64), ("mixed", fifa.FIFA_MIXED)):

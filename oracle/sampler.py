@@ -142,3 +142,84 @@ def gibbs_step(st: State, x, y, prior: Prior, opts: Opts, seed: int, chain: int)
         st.eta, st.HC, st.FC = eta_p, HCp, FCp
     st.it = it + 1
     return st
+
+
+# ---------------------------------------------------------------------------
+# Additive model built from 1-D GPs (Sec. 4.2 notes that an additive model may
+# suffice; the workload's d-dimensional surface): y = sum_k f_k(x_k) + e,
+# f_k ~ GP(0, tau2_k C(rho_k)) on the k-th input coordinate, shared sigma2.
+# One block-Gibbs sweep:
+#   for k = 0..d-1:  r = y - sum_{j != k} f_j (subtracted in j order), sorted by
+#                    x_k; f_k | r by Algorithm 1 with (tau2_k, sigma2, rho_k)
+#   sigma2 | y, f    (Philox stream id d)
+#   for k:           tau2_k | f_k, then the Metropolis step on log rho_k
+# Block k draws its normals, gamma variates and Metropolis numbers from Philox
+# stream id k, all at counter word 2 = sweep index.
+# ---------------------------------------------------------------------------
+@dataclass
+class AdditiveState:
+    F: np.ndarray          # n x d, original order
+    sigma2: float
+    blocks: list           # per block: dict(perm, x, tau2, eta, HC, FC)
+    it: int = 0
+    trace: list = field(default_factory=list)
+
+
+def additive_init(X, y, rho0, opts: Opts, sigma2=None, tau2=None):
+    n, d = X.shape
+    vy = float(np.var(y))
+    blocks = []
+    for k in range(d):
+        perm = np.argsort(X[:, k], kind="stable")
+        xs = X[perm, k]
+        HC, FC = assemble_factor(xs, rho0, opts)
+        blocks.append(dict(perm=perm, x=xs, tau2=(vy / d if tau2 is None else tau2), eta=math.log(rho0), HC=HC, FC=FC))
+    return AdditiveState(F=np.zeros((n, d)), sigma2=(0.5 * vy if sigma2 is None else sigma2), blocks=blocks)
+
+
+def additive_sweep(st: AdditiveState, y, prior: Prior, opts: Opts, seed: int):
+    n, d = st.F.shape
+    it = st.it
+    y = np.asarray(y, dtype=np.float64)
+    for k, b in enumerate(st.blocks):
+        r = y.copy()
+        for j in range(d):
+            if j != k:
+                r = r - st.F[:, j]
+        rs = r[b["perm"]]
+        FM = factorize(shift_scale(b["HC"], b["tau2"] / st.sigma2))
+        a_ = rng.normals(n, seed, rng.TAG_A, it, k)
+        b_ = rng.normals(n, seed, rng.TAG_B, it, k)
+        fs, _ = draw_f(b["HC"], b["FC"], FM, rs, b["tau2"], st.sigma2, a_, b_)
+        b["f"] = fs
+        st.F[b["perm"], k] = fs
+    res = y.copy()
+    for j in range(d):
+        res = res - st.F[:, j]
+    rss = float(np.sum(res * res))
+    st.sigma2 = rng.inv_gamma_draw(prior.a_sigma2 + 0.5 * n, prior.b_sigma2 + 0.5 * rss, seed, rng.TAG_SIGMA2, it, d)
+    row = dict(it=it, sigma2=st.sigma2, rss=rss, tau2=[], rho=[], accept=[])
+    for k, b in enumerate(st.blocks):
+        fs = b["f"]
+        q = float(np.sum(apply_W(b["FC"], fs, inverse=True) ** 2))
+        b["tau2"] = rng.inv_gamma_draw(prior.a_tau2 + 0.5 * n, prior.b_tau2 + 0.5 * q, seed, rng.TAG_TAU2, it, k)
+        z = rng.scalar_normal(0, seed, rng.TAG_MH_PROP, it, k)
+        eta_p = b["eta"] + prior.prop_sd * z
+        u = rng.scalar_uniform(0, seed, rng.TAG_MH_UNIF, it, k)
+        accept = False
+        try:
+            HCp, FCp = assemble_factor(b["x"], math.exp(eta_p), opts)
+            qp = float(np.sum(apply_W(FCp, fs, inverse=True) ** 2))
+            la = (-0.5 * (FCp.logdet - b["FC"].logdet) - (qp - q) / (2.0 * b["tau2"])
+                  + log_prior_eta(eta_p, prior) - log_prior_eta(b["eta"], prior))
+            accept = math.log(u) < la
+        except NotSPD:
+            pass
+        if accept:
+            b["eta"], b["HC"], b["FC"] = eta_p, HCp, FCp
+        row["tau2"].append(b["tau2"])
+        row["rho"].append(math.exp(b["eta"]))
+        row["accept"].append(accept)
+    st.trace.append(row)
+    st.it = it + 1
+    return st

@@ -1,0 +1,86 @@
+"""Leaf-size autotuner for the Gibbs chain (results cached in tuned.json).
+
+For a workload key (kernel, input recipe, n) it times a few Gibbs iterations of
+the FP64 chain for every candidate leaf size B and stores the per-B times and
+the fastest B.  bench.py and users read the cached choice, so repeated runs
+(and profiled runs, whose timings are distorted) use the same configuration.
+
+    python -m paper_2006_06537_gb300.autotune [--n 1048576] [--leaves 32 64 128]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE = os.path.join(HERE, "tuned.json")
+
+
+def workload_key(kind: str, n: int) -> str:
+    return f"{kind}_n{n}"
+
+
+def load(key: str):
+    if not os.path.exists(CACHE):
+        return None
+    return json.load(open(CACHE)).get(key)
+
+
+def store(key: str, entry: dict):
+    data = json.load(open(CACHE)) if os.path.exists(CACHE) else {}
+    data[key] = entry
+    with open(CACHE, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+
+
+def time_leaf(x, y, leaf, rho0, eps, cap, nugget, iters=3, warmup=1):
+    import torch
+
+    from . import fifa
+
+    stream = torch.cuda.Stream()
+    vy = float(np.var(y))
+    with torch.cuda.stream(stream):
+        ctx = fifa.Context(leaf_size=leaf, aca_tol=eps, rank_cap=cap, prec=fifa.FIFA_FP64, arena_bytes=40 << 30,
+                           stream=stream)
+        xd = torch.tensor(x, device="cuda")
+        yd = torch.tensor(y, device="cuda")
+        pr = fifa.fifa_prior(1.0, 1.0, 1.0, 1.0, math.log(rho0), 1.0, 0.2)
+        ch = fifa.fifa_chain_create(ctx.h, xd, yd, len(x), fifa.fifa_hyper(0, vy, rho0, 0.5 * vy, nugget), pr, 0, 0)
+        fifa.fifa_gibbs_step(ctx.h, ch, warmup)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fifa.fifa_gibbs_step(ctx.h, ch, iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / iters
+        fifa.fifa_destroy_chain(ctx.h, ch)
+        ctx.close()
+    return ms
+
+
+def tune_clustered(n: int, leaves=(32, 64, 128), rho0=0.01, eps=1e-10, cap=32, nugget=1e-6, noise=0.05):
+    from .build import build
+    from .inputs import clustered
+
+    build()
+    x, y = clustered(n, 2, noise=noise)
+    times = {str(b): time_leaf(x, y, b, rho0, eps, cap, nugget) for b in leaves}
+    best = int(min(times, key=times.get))
+    entry = {"leaf": best, "ms_per_iter": times, "rho0": rho0, "eps": eps, "cap": cap, "nugget": nugget}
+    store(workload_key("clustered_se", n), entry)
+    return entry
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--leaves", type=int, nargs="+", default=[32, 64, 128])
+    a = ap.parse_args()
+    print(json.dumps(tune_clustered(a.n, tuple(a.leaves))))

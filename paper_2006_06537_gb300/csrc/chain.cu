@@ -17,6 +17,7 @@
 #include "../../include/fifa.h"
 #include "fifa_api_internal.h"
 #include "fifa_chain.h"
+#include "fifa_chain_impl.h"
 #include "fifa_launch.h"
 
 #define CK(call)                 \
@@ -28,73 +29,58 @@
     }                            \
   } while (0)
 
-#define CHAIN_TRACE_CAP 1024
-
-struct fifa_chain {
-  Plan* plan = nullptr;
-  fifa_hmat* H[2] = {nullptr, nullptr};  // slot 0: current C~, slot 1: proposal (device descriptors swap)
-  fifa_fact* F[2] = {nullptr, nullptr};
-  fifa_fact* FM = nullptr;
-  fifa_hmat* Mv = nullptr;  // view descriptor refreshed every iteration
-  double *x = nullptr, *y = nullptr, *f = nullptr, *mean = nullptr, *tmp = nullptr, *trace = nullptr;
-  void* scratch = nullptr;
-  ChainDev* dev = nullptr;
-  ChainDev init{};
-  uint64_t iter_host = 0;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  bool graph_failed = false;
-};
-
-static fifa_status chain_iteration_enqueue(fifa_ctx* ctx, fifa_chain* ch) {
-  Plan* P = ch->plan;
-  const int64_t n = P->n;
+// Phase 1: M~ = (tau2 / sigma2) C~ + I, its factor, and f | y by Algorithm 1.
+fifa_status chain_phase_draw(fifa_ctx* ctx, fifa_chain* ch) {
   cudaStream_t s = ctx->stream;
-  ctx->active_scratch = ch->scratch;
-  Scratch S = carve(ctx, P);
-  fifa_status st = FIFA_OK;
+  ChainDev* c = ch->dev;
+  if (launch_chain_make_view(ch->H[0]->dev, ch->Mv->dev, c, s) != cudaSuccess) return FIFA_ERR_CUDA;
+  fifa_status st = fact_enqueue(ctx, ch->FM, ch->Mv->dev);
+  if (st != FIFA_OK) return st;
+  return sample_enqueue(ctx, ch->H[0], ch->F[0], ch->FM, ch->y, 0.0, 0.0, ch->init.seed, ch->init.chain_id, &c->iter,
+                        0, ch->f, ch->mean, &c->tau2, &c->refine_res);
+}
+
+// Phase 2: sigma2 | y, f.
+fifa_status chain_phase_sigma2(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
+  if (launch_sumsq(ch->y, ch->f, ch->plan->n, S.red, &ch->dev->rss, ctx->stream) != cudaSuccess) return FIFA_ERR_CUDA;
+  if (launch_chain_sigma2(ch->dev, ctx->stream) != cudaSuccess) return FIFA_ERR_CUDA;
+  return FIFA_OK;
+}
+
+// Phase 3: tau2 | f, rho, then the Metropolis step on log rho (advances the
+// chain's iteration counter).
+fifa_status chain_phase_hyper(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
+  const int64_t n = ch->plan->n;
+  cudaStream_t s = ctx->stream;
   ChainDev* c = ch->dev;
   HmatDesc* Hc = ch->H[0]->dev;
   HmatDesc* Hp = ch->H[1]->dev;
-  do {
-    // M~ = (tau2 / sigma2) C~ + I and its factor
-    if (launch_chain_make_view(Hc, ch->Mv->dev, c, s) != cudaSuccess) { st = FIFA_ERR_CUDA; break; }
-    st = fact_enqueue(ctx, ch->FM, ch->Mv->dev);
-    if (st != FIFA_OK) break;
-    // f by Algorithm 1
-    st = sample_enqueue(ctx, ch->H[0], ch->F[0], ch->FM, ch->y, 0.0, 0.0, c ? ch->init.seed : 0, ch->init.chain_id,
-                        &c->iter, 0, ch->f, ch->mean, &c->tau2, &c->refine_res);
-    if (st != FIFA_OK) break;
-    // sigma2 | y, f
-    if (launch_sumsq(ch->y, ch->f, n, S.red, &c->rss, s) != cudaSuccess) { st = FIFA_ERR_CUDA; break; }
-    if (launch_chain_sigma2(c, s) != cudaSuccess) { st = FIFA_ERR_CUDA; break; }
-    // tau2 | f, rho : q = ||W_C^-1 f||^2
-    if (cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
-      st = FIFA_ERR_CUDA;
-      break;
-    }
-    st = sweep_enqueue(ctx, ch->F[0], 0, 1, ch->tmp, 1);
-    if (st != FIFA_OK) break;
-    if (launch_sumsq(ch->tmp, nullptr, n, S.red, &c->q, s) != cudaSuccess) { st = FIFA_ERR_CUDA; break; }
-    if (launch_chain_tau2(c, s) != cudaSuccess) { st = FIFA_ERR_CUDA; break; }
-    // rho | f, tau2 : propose, assemble, factor, q'
-    if (launch_chain_propose(c, Hp, s) != cudaSuccess) { st = FIFA_ERR_CUDA; break; }
-    st = hmat_assemble_enqueue(ctx, ch->H[1]);
-    if (st != FIFA_OK) break;
-    st = fact_enqueue(ctx, ch->F[1], Hp);
-    if (st != FIFA_OK) break;
-    if (cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
-      st = FIFA_ERR_CUDA;
-      break;
-    }
-    st = sweep_enqueue(ctx, ch->F[1], 0, 1, ch->tmp, 1);
-    if (st != FIFA_OK) break;
-    if (launch_sumsq(ch->tmp, nullptr, n, S.red, &c->q_prop, s) != cudaSuccess) { st = FIFA_ERR_CUDA; break; }
-    if (launch_chain_mh(c, Hc, Hp, ch->F[0]->dev, ch->F[1]->dev, ch->FM->dev, s) != cudaSuccess) {
-      st = FIFA_ERR_CUDA;
-      break;
-    }
-  } while (0);
+  if (cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return FIFA_ERR_CUDA;
+  fifa_status st = sweep_enqueue(ctx, ch->F[0], 0, 1, ch->tmp, 1);
+  if (st != FIFA_OK) return st;
+  if (launch_sumsq(ch->tmp, nullptr, n, S.red, &c->q, s) != cudaSuccess) return FIFA_ERR_CUDA;
+  if (launch_chain_tau2(c, s) != cudaSuccess) return FIFA_ERR_CUDA;
+  if (launch_chain_propose(c, Hp, s) != cudaSuccess) return FIFA_ERR_CUDA;
+  st = hmat_assemble_enqueue(ctx, ch->H[1]);
+  if (st != FIFA_OK) return st;
+  st = fact_enqueue(ctx, ch->F[1], Hp);
+  if (st != FIFA_OK) return st;
+  if (cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return FIFA_ERR_CUDA;
+  st = sweep_enqueue(ctx, ch->F[1], 0, 1, ch->tmp, 1);
+  if (st != FIFA_OK) return st;
+  if (launch_sumsq(ch->tmp, nullptr, n, S.red, &c->q_prop, s) != cudaSuccess) return FIFA_ERR_CUDA;
+  if (launch_chain_mh(c, Hc, Hp, ch->F[0]->dev, ch->F[1]->dev, ch->FM->dev, s) != cudaSuccess) return FIFA_ERR_CUDA;
+  return FIFA_OK;
+}
+
+static fifa_status chain_iteration_enqueue(fifa_ctx* ctx, fifa_chain* ch) {
+  ctx->active_scratch = ch->scratch;
+  Scratch S = carve(ctx, ch->plan);
+  fifa_status st = chain_phase_draw(ctx, ch);
+  if (st == FIFA_OK) st = chain_phase_sigma2(ctx, ch, S);
+  if (st == FIFA_OK) st = chain_phase_hyper(ctx, ch, S);
   ctx->active_scratch = nullptr;
   if (st == FIFA_ERR_CUDA) ctx->last_cuda = cudaGetLastError();
   return st;

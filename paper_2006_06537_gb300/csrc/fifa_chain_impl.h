@@ -1,0 +1,37 @@
+// Host-side Gibbs chain object and its iteration phases (internal; shared by
+// the single chain and the additive block model).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fifa.h"
+#include "fifa_api_internal.h"
+#include "fifa_chain.h"
+
+#define CHAIN_TRACE_CAP 1024
+
+struct fifa_chain {
+  Plan* plan = nullptr;
+  fifa_hmat* H[2] = {nullptr, nullptr};  // slot 0: current C~, slot 1: proposal (device descriptors swap)
+  fifa_fact* F[2] = {nullptr, nullptr};
+  fifa_fact* FM = nullptr;
+  fifa_hmat* Mv = nullptr;  // view descriptor refreshed every iteration
+  double *x = nullptr, *y = nullptr, *f = nullptr, *mean = nullptr, *tmp = nullptr, *trace = nullptr;
+  void* scratch = nullptr;
+  ChainDev* dev = nullptr;
+  ChainDev init{};
+  uint64_t iter_host = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_failed = false;
+};
+
+// The three phases of one iteration, enqueued on ctx->stream with
+// ctx->active_scratch = chain->scratch (S carved from it):
+//   draw   M~ view, its factor, f | y by Algorithm 1 (data chain->y)
+//   sigma2 ||y - f||^2 and sigma2 | y, f
+//   hyper  q, tau2 | f, proposal C~(rho'), its factor, q', Metropolis step;
+//          advances the chain's iteration counter
+fifa_status chain_phase_draw(fifa_ctx* ctx, fifa_chain* ch);
+fifa_status chain_phase_sigma2(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
+fifa_status chain_phase_hyper(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);

@@ -127,100 +127,13 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// Level kernel.  Every pass over a node's rows is row-parallel: each thread
-// walks rows p = a0 + tid, a0 + tid + NT, ... with coalesced column loads and
-// keeps its partial sums in registers (register tiles of at most 4 x 8 or the
-// 36 pair products of a rank <= 8 Gram matrix); one deterministic block
-// reduction (fixed butterfly, fixed warp order) then combines them.  Small
-// dense algebra (r <= cap) runs in shared memory.
+// General level kernel (large nodes, ranks above the small-node buckets).  Row
+// transforms and updates are row-parallel with coalesced column accesses;
+// reductions over rows use the tiled output-major helpers below; small dense
+// algebra (r <= cap) runs in shared memory.
 // ---------------------------------------------------------------------------
-#define LV_QB 4  // basis columns per register tile
-#define LV_W 8   // ancestor columns per register tile / update chunk
+#define LV_W 8   // ancestor columns per update chunk
 #define LV_RED 64
-
-// Sum nv per-thread values over the block into out[0..nv) (shared); NV >= nv.
-template <int NV>
-__device__ __forceinline__ void block_reduce_vec(double (&v)[NV], double* scratch, double* out, int nv) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    double x = v[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    v[q] = x;
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q)
-      if (q < nv) scratch[w * LV_RED + q] = v[q];
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < nv; q += blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < nw; ++k) s += scratch[k * LV_RED + q];
-    out[q] = s;
-  }
-  __syncthreads();
-}
-
-// G[a*ldg + b] = sum over rows [a0, a1) of X[a][p] X[b][p] for a, b < r.
-template <typename T>
-__device__ void gram_pass(const T* __restrict__ Xb, int64_t n, int r, int a0, int a1, double* scratch, double* tmp,
-                          double* G, int ldg) {
-  if (r <= 8) {
-    constexpr int NP = 36;
-    double acc[NP];
-#pragma unroll
-    for (int q = 0; q < NP; ++q) acc[q] = 0.0;
-    for (int p = a0 + threadIdx.x; p < a1; p += blockDim.x) {
-      double x[8];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) x[c] = c < r ? to_d(Xb[(size_t)c * n + p]) : 0.0;
-      int q = 0;
-#pragma unroll
-      for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int b = a; b < 8; ++b) acc[q++] += x[a] * x[b];
-    }
-    block_reduce_vec<NP>(acc, scratch, tmp, NP);
-    for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
-      const int a = t / r, b = t % r, i = min(a, b), j = max(a, b);
-      G[a * ldg + b] = tmp[i * 8 - i * (i - 1) / 2 + (j - i)];
-    }
-    __syncthreads();
-    return;
-  }
-  const int nb = (r + LV_QB - 1) / LV_QB;
-  for (int bi = 0; bi < nb; ++bi) {
-    for (int bj = bi; bj < nb; ++bj) {
-      double acc[LV_QB * LV_QB];
-#pragma unroll
-      for (int q = 0; q < LV_QB * LV_QB; ++q) acc[q] = 0.0;
-      for (int p = a0 + threadIdx.x; p < a1; p += blockDim.x) {
-        double xa[LV_QB], xb[LV_QB];
-#pragma unroll
-        for (int c = 0; c < LV_QB; ++c) {
-          const int ca = bi * LV_QB + c, cb = bj * LV_QB + c;
-          xa[c] = ca < r ? to_d(Xb[(size_t)ca * n + p]) : 0.0;
-          xb[c] = cb < r ? to_d(Xb[(size_t)cb * n + p]) : 0.0;
-        }
-#pragma unroll
-        for (int a = 0; a < LV_QB; ++a)
-#pragma unroll
-          for (int b = 0; b < LV_QB; ++b) acc[a * LV_QB + b] += xa[a] * xb[b];
-      }
-      block_reduce_vec<LV_QB * LV_QB>(acc, scratch, tmp, LV_QB * LV_QB);
-      for (int t = threadIdx.x; t < LV_QB * LV_QB; t += blockDim.x) {
-        const int a = bi * LV_QB + t / LV_QB, b = bj * LV_QB + t % LV_QB;
-        if (a < r && b < r) {
-          G[a * ldg + b] = tmp[t];
-          G[b * ldg + a] = tmp[t];
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
 
 template <typename T, int RB>
 __device__ __forceinline__ void rowmul_row(T* __restrict__ Xb, int64_t n, int r, int p, const double* Ri, int ldr) {
@@ -253,38 +166,6 @@ __device__ void rowmul_pass(T* __restrict__ Xb, int64_t n, int r, int a0, int a1
     }
   }
   __syncthreads();
-}
-
-// Pm[a * LV_W + j] = sum over rows [a0, a1) of Q[a][p] B_j[p] (storage-precision products).
-template <typename T>
-__device__ void proj_pass(const T* __restrict__ Qb, T* const* Bp, int w, int64_t n, int r, int a0, int a1,
-                          double* scratch, double* tmp, double* Pm) {
-  const int nb = (r + LV_QB - 1) / LV_QB;
-  for (int bi = 0; bi < nb; ++bi) {
-    T acc[LV_QB * LV_W];
-#pragma unroll
-    for (int q = 0; q < LV_QB * LV_W; ++q) acc[q] = (T)0;
-    for (int p = a0 + threadIdx.x; p < a1; p += blockDim.x) {
-      T qv[LV_QB], bv[LV_W];
-#pragma unroll
-      for (int c = 0; c < LV_QB; ++c) qv[c] = (bi * LV_QB + c < r) ? Qb[(size_t)(bi * LV_QB + c) * n + p] : (T)0;
-#pragma unroll
-      for (int j = 0; j < LV_W; ++j) bv[j] = j < w ? Bp[j][p] : (T)0;
-#pragma unroll
-      for (int a = 0; a < LV_QB; ++a)
-#pragma unroll
-        for (int j = 0; j < LV_W; ++j) acc[a * LV_W + j] += qv[a] * bv[j];
-    }
-    double dv[LV_QB * LV_W];
-#pragma unroll
-    for (int q = 0; q < LV_QB * LV_W; ++q) dv[q] = (double)acc[q];
-    block_reduce_vec<LV_QB * LV_W>(dv, scratch, tmp, LV_QB * LV_W);
-    for (int t = threadIdx.x; t < LV_QB * LV_W; t += blockDim.x) {
-      const int a = bi * LV_QB + t / LV_W, j = t % LV_W;
-      if (a < r && j < w) Pm[a * LV_W + j] = tmp[t];
-    }
-    __syncthreads();
-  }
 }
 
 // Rows [a0, a1): B_j[p] += sum_a Q[a][p] Tm[a * LV_W + j].
@@ -333,8 +214,99 @@ __device__ inline bool group_reduce(double* dst, const double* src_local, int co
   return true;
 }
 
+
+// ---------------------------------------------------------------------------
+// Tiled, output-major reductions for the general level kernel: a tile of rows
+// is staged in shared memory (coalesced loads), each output entry is owned by a
+// group of threads that walk disjoint rows of the tile, and the groups' partial
+// sums are combined by one short shared-memory loop per output.  FP64
+// instructions go to products of nonzero entries only.
+// ---------------------------------------------------------------------------
+#define LV_TR 64
+#define LV_TRP (LV_TR + 1)
+
+__device__ __forceinline__ void pair_decode(int o, int r, int& a, int& b) {
+  int rem = o;
+  a = 0;
+  while (rem >= r - a) {
+    rem -= r - a;
+    ++a;
+  }
+  b = a + rem;
+}
+
+// G[a*ldg + b] = sum over rows [a0, a1) of X[a][p] X[b][p], a, b < r.
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_level(const FactDesc* __restrict__ Fd, int lvl, int G, double* __restrict__ part,
+__device__ void gram_tiled(const T* __restrict__ Xb, int64_t n, int r, int a0, int a1, double* tile, double* part,
+                           double* G, int ldg) {
+  const int np = r * (r + 1) / 2;
+  const int ng = max(1, (int)blockDim.x / np);
+  const int t = threadIdx.x;
+  const bool active = t < np * ng;
+  const int o = active ? t % np : 0, gidx = active ? t / np : 0;
+  int a = 0, b = 0;
+  pair_decode(o, r, a, b);
+  double acc = 0.0;
+  for (int p0 = a0; p0 < a1; p0 += LV_TR) {
+    const int tr = min(LV_TR, a1 - p0);
+    __syncthreads();
+    for (int i = t; i < r * tr; i += blockDim.x) {
+      const int c = i / tr, p = i % tr;
+      tile[c * LV_TRP + p] = to_d(Xb[(size_t)c * n + p0 + p]);
+    }
+    __syncthreads();
+    if (active)
+      for (int p = gidx; p < tr; p += ng) acc += tile[a * LV_TRP + p] * tile[b * LV_TRP + p];
+  }
+  __syncthreads();
+  if (active) part[gidx * np + o] = acc;
+  __syncthreads();
+  for (int q = t; q < np; q += blockDim.x) {
+    double v = 0.0;
+    for (int g = 0; g < ng; ++g) v += part[g * np + q];
+    int qa, qb;
+    pair_decode(q, r, qa, qb);
+    G[qa * ldg + qb] = v;
+    G[qb * ldg + qa] = v;
+  }
+  __syncthreads();
+}
+
+// Pm[a * LV_W + j] = sum over rows [a0, a1) of Q[a][p] B_j[p], products in the storage precision.
+template <typename T>
+__device__ void proj_tiled(const T* __restrict__ Qb, T* const* Bp, int w, int64_t n, int r, int a0, int a1,
+                           double* tile, double* part, double* Pm) {
+  const int np = r * w;
+  const int ng = max(1, (int)blockDim.x / np);
+  const int t = threadIdx.x;
+  const bool active = t < np * ng;
+  const int o = active ? t % np : 0, gidx = active ? t / np : 0;
+  const int a = o / w, j = o % w;
+  T acc = (T)0;
+  for (int p0 = a0; p0 < a1; p0 += LV_TR) {
+    const int tr = min(LV_TR, a1 - p0);
+    __syncthreads();
+    for (int i = t; i < (r + w) * tr; i += blockDim.x) {
+      const int c = i / tr, p = i % tr;
+      tile[c * LV_TRP + p] = c < r ? to_d(Qb[(size_t)c * n + p0 + p]) : to_d(Bp[c - r][p0 + p]);
+    }
+    __syncthreads();
+    if (active)
+      for (int p = gidx; p < tr; p += ng) acc += (T)tile[a * LV_TRP + p] * (T)tile[(r + j) * LV_TRP + p];
+  }
+  __syncthreads();
+  if (active) part[gidx * np + o] = (double)acc;
+  __syncthreads();
+  for (int q = t; q < np; q += blockDim.x) {
+    double v = 0.0;
+    for (int g = 0; g < ng; ++g) v += part[g * np + q];
+    Pm[(q / w) * LV_W + q % w] = v;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_level(const FactDesc* __restrict__ Fd, int lvl, int G, double* __restrict__ gpart,
                                                unsigned int* __restrict__ bar, int* __restrict__ abort_flag,
                                                int skip_le) {
   extern __shared__ double sm[];
@@ -362,8 +334,9 @@ __global__ void __launch_bounds__(256, 2) k_level(const FactDesc* __restrict__ F
   double* R1 = Ri + cc2;
   double* RU = R1 + cc2;
   double* RV = RU + cc2;
-  double* scratch = RV + cc2;             // 8 warps x LV_RED
-  double* tmp = scratch + 8 * LV_RED;     // LV_RED
+  double* tile = RV + cc2;                // (cap + LV_W) x LV_TRP row tile
+  double* part = tile + (cap + LV_W) * LV_TRP;  // 256 group partial sums
+  double* tmp = part + 256;               // LV_RED
   double* Pm = tmp + LV_RED;              // 2cap x LV_W
   T* Tm = (T*)(Pm + 2 * cap * LV_W);      // 2cap x LV_W, storage precision
   T** Bp = (T**)(Pm + 4 * cap * LV_W);    // LV_W column pointers
@@ -377,15 +350,15 @@ __global__ void __launch_bounds__(256, 2) k_level(const FactDesc* __restrict__ F
     const int a0 = side == 0 ? max(r0, s) : max(r0, h);
     const int a1 = side == 0 ? min(r1, h) : min(r1, e);
     // CholeskyQR2 of this side's basis: Gram, R1, Q1 = X R1^-1, Gram, R2, Q = Q1 R2^-1
-    gram_pass<T>(Qb, n, r, a0, a1, scratch, tmp, Gm, cap);
-    if (!group_reduce(Gm, Gm, cc2, G, g, base, part, pstride, bar, phase, status, abort_flag)) return;
+    gram_tiled<T>(Qb, n, r, a0, a1, tile, part, Gm, cap);
+    if (!group_reduce(Gm, Gm, cc2, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
     ok = blk_chol_upper(Gm, cap, r, iflag, clamp_gram<T>()) && ok;
     for (int t = threadIdx.x; t < cc2; t += blockDim.x) R1[t] = Gm[t];
     __syncthreads();
     blk_triinv_upper(Gm, cap, Ri, cap, r);
     rowmul_pass<T>(Qb, n, r, a0, a1, Ri, cap);
-    gram_pass<T>(Qb, n, r, a0, a1, scratch, tmp, Gm, cap);
-    if (!group_reduce(Gm, Gm, cc2, G, g, base, part, pstride, bar, phase, status, abort_flag)) return;
+    gram_tiled<T>(Qb, n, r, a0, a1, tile, part, Gm, cap);
+    if (!group_reduce(Gm, Gm, cc2, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
     ok = blk_chol_upper(Gm, cap, r, iflag, clamp_gram<T>()) && ok;
     blk_triinv_upper(Gm, cap, Ri, cap, r);
     double* Rs = side == 0 ? RU : RV;
@@ -474,9 +447,9 @@ __global__ void __launch_bounds__(256, 2) k_level(const FactDesc* __restrict__ F
     }
     for (int t = threadIdx.x; t < 2 * cap * LV_W; t += blockDim.x) Pm[t] = 0.0;
     __syncthreads();
-    proj_pass<T>(Qb, Bp, w, n, r, max(r0, s), min(r1, h), scratch, tmp, Pm);
-    proj_pass<T>(Qb, Bp, w, n, r, max(r0, h), min(r1, e), scratch, tmp, Pm + r * LV_W);
-    if (!group_reduce(Pm, Pm, 2 * cap * LV_W, G, g, base, part, pstride, bar, phase, status, abort_flag)) return;
+    proj_tiled<T>(Qb, Bp, w, n, r, max(r0, s), min(r1, h), tile, part, Pm);
+    proj_tiled<T>(Qb, Bp, w, n, r, max(r0, h), min(r1, e), tile, part, Pm + r * LV_W);
+    if (!group_reduce(Pm, Pm, 2 * cap * LV_W, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
     for (int t = threadIdx.x; t < r2 * LV_W; t += blockDim.x) {
       const int a = t / LV_W, j = t % LV_W;
       double acc = 0.0;
@@ -690,8 +663,9 @@ size_t leaf_factor_smem(int Bm, int L, int cap, int prec) {
   return b;
 }
 size_t level_smem(int cap) {
-  return ((size_t)5 * cap * cap + 9 * LV_RED + 4 * (size_t)cap * LV_W) * sizeof(double) + LV_W * sizeof(void*) +
-         (4 + (size_t)FIFA_LEVELS_MAX * cap) * sizeof(int);
+  return ((size_t)5 * cap * cap + (size_t)(cap + LV_W) * LV_TRP + 256 + LV_RED + 4 * (size_t)cap * LV_W) *
+             sizeof(double) +
+         LV_W * sizeof(void*) + (4 + (size_t)FIFA_LEVELS_MAX * cap) * sizeof(int);
 }
 
 static int smem_optin() {

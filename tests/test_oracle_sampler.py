@@ -146,3 +146,23 @@ def test_gibbs_chain_recovers_noise_level():
     s2 = np.array([t["sigma2"] for t in st.trace[10:]])
     assert 0.007 < np.median(s2) < 0.014
     assert any(t["accept"] for t in st.trace)
+
+
+def test_additive_block_gibbs_recovers_components():
+    # y = f_1(x_1) + f_2(x_2) + noise; the sweep must separate the two components
+    g = np.random.default_rng(21)
+    n = 400
+    X = g.uniform(0, 1, (n, 2))
+    f1, f2 = np.sin(2 * math.pi * X[:, 0]), 0.5 * np.cos(2 * math.pi * X[:, 1])
+    y = f1 + f2 + 0.05 * g.standard_normal(n)
+    opts = sampler.Opts(B=32, eps=1e-10, cap=32, kind=0, nugget=1e-6)
+    prior = sampler.Prior(a_sigma2=1e-3, b_sigma2=1e-3, logrho_mu=math.log(0.2))
+    st = sampler.additive_init(X, y, 0.2, opts)
+    for _ in range(25):
+        sampler.additive_sweep(st, y, prior, opts, seed=3)
+    s2 = np.median([t["sigma2"] for t in st.trace[10:]])
+    assert 0.0015 < s2 < 0.004
+    # each component is identified up to a constant shift between the two
+    c1 = st.F[:, 0] - st.F[:, 0].mean()
+    c2 = st.F[:, 1] - st.F[:, 1].mean()
+    assert np.corrcoef(c1, f1)[0, 1] > 0.95 and np.corrcoef(c2, f2)[0, 1] > 0.9
