@@ -59,6 +59,11 @@ def parse():
     ap.add_argument("--leaf", type=int, default=0, help="leaf size (0 = the autotuner's cached choice)")
     ap.add_argument("--nugget", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=256,
+                    help="requests of the serving stream to run (0 = skip the serving leg)")
+    ap.add_argument("--serve-slots", type=int, default=32)
+    ap.add_argument("--paths", default="fp64,mixed", help="chain precisions to time (comma list of fp64, mixed)")
+    ap.add_argument("--additive-sweeps", type=int, default=10, help="0 = skip the d-block additive leg")
     return ap.parse_args()
 
 
@@ -251,7 +256,10 @@ def gpu_arm(args):
         leaf, tune = (entry["leaf"], entry["ms_per_iter"]) if entry else (32, {})
 
     results = {}
+    wanted = [p.strip() for p in args.paths.split(",") if p.strip()]
     for name, prec in (("fp64", fifa.FIFA_FP64), ("mixed", fifa.FIFA_MIXED)):
+        if name not in wanted:
+            continue
         ctx, ch, xd, yd = make(prec, leaf)
         try:
             clocks = ClockSampler(local)
@@ -299,6 +307,14 @@ def gpu_arm(args):
     roof = roofline_probe(pctx, fifa, torch, stream, xd, n, leaf, args.nugget)
     pctx.close()
 
+    # serving (continuous batching, p50/p99) and the d-block additive model:
+    # measured after the headline, outside its timed region
+    serving = additive = None
+    if rank == 0 and args.serve_requests > 0:
+        serving = serving_leg(fifa, args.serve_requests, args.serve_slots, fifa.FIFA_FP64, 64)
+    if rank == 0 and args.additive_sweeps > 0:
+        additive = additive_leg(fifa, torch, args.additive_sweeps, 64)
+
     vals = torch.tensor([per_head, e2e_s], device="cuda", dtype=torch.float64)
     if world > 1:
         torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
@@ -329,11 +345,125 @@ def gpu_arm(args):
         "chain": {"rho": float(tr[-1, 3]), "sigma2": float(tr[-1, 1]), "tau2": float(tr[-1, 2]),
                   "accept_rate": float(tr[:, 4].mean())},
         "roofline": roof,
+        "serving": serving,
+        "additive": additive,
         "cpu_baseline": cpu,
         "gpu_launches": int(results[head]["kernels"]) * args.steps,
         "clocks": results[head]["clocks"],
     }
     print(json.dumps(line))
+
+
+def serving_leg(fifa, count, slots, prec, leaf, iters=100, ndraws=20, rate=200.0, budget=120 << 30,
+                wide_min_n=1 << 16):
+    """The serving workload: the first `count` requests of a Poisson stream at
+    `rate` req/s, n log-uniform in [2^10, 2^18], SE or Matern-5/2 per request,
+    each `iters` Gibbs iterations returning the posterior mean and `ndraws`
+    draws, admitted under an HBM budget.  Requests are submitted at their
+    arrival times; latency = completion - submission on the server's clock."""
+    from paper_2006_06537_gb300.inputs import request_data, serving_requests
+
+    reqs = serving_requests(count, rate)
+    data = [request_data(r) for r in reqs]
+    opts = fifa.fifa_opts(leaf, EPS, CAP, prec, 1e-12, 8, 1)
+    srv = fifa.fifa_server_create(opts, budget, slots, wide_min_n)
+    ids = [None] * count
+    res = [None] * count
+    done = threading.Event()
+
+    def waiter():
+        for i in range(count):
+            while ids[i] is None:
+                time.sleep(0.0002)
+            if ids[i] < 0:  # submission failed: nothing to wait for
+                res[i] = (-1, 0.0, 0.0, 0.0)
+                continue
+            n = reqs[i]["n"]
+            mean, draws = np.empty(n), np.empty((ndraws, n))
+            st, r = fifa.fifa_server_wait(srv, ids[i], mean, draws, allow=tuple(range(16)))
+            res[i] = (st, r.t_submit, r.t_start, r.t_done)
+        done.set()
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    pr = fifa.fifa_prior(1.0, 1.0, 1.0, 1.0, math.log(0.1), 1.0, 0.2)
+    t0 = time.perf_counter()
+    try:
+        for i, r in enumerate(reqs):
+            wait = r["t"] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            x, y = data[i]
+            vy = float(np.var(y))
+            try:
+                ids[i] = fifa.fifa_server_submit(srv, x, y, fifa.fifa_hyper(r["kind"], vy, 0.1, 0.5 * vy, 1e-6), pr,
+                                                 0, r["id"], iters, iters // 2, ndraws)
+            except fifa.FifaError:
+                ids[i] = -1
+    finally:
+        for i in range(count):
+            if ids[i] is None:
+                ids[i] = -1
+        th.join()
+    stats = fifa.fifa_server_stats(srv)
+    fifa.fifa_server_destroy(srv)
+    ok = [r for r in res if r[0] == 0]
+    if not ok:
+        return {"requests": count, "completed": 0, "statuses": sorted({int(r[0]) for r in res})}
+    lat = np.array([r[3] - r[1] for r in ok])
+    span = max(r[3] for r in ok) - min(r[1] for r in ok)
+    sizes = np.array([r["n"] for r in reqs])
+    return {
+        "workload": f"first {count} requests of a Poisson stream at {rate:g} req/s, n log-uniform in [2^10, 2^18], "
+                    f"SE or Matern-5/2, {iters} iterations + posterior mean + {ndraws} draws each",
+        "requests": count, "completed": len(ok), "offered_req_per_s": rate, "slots": slots,
+        "wide_min_n": wide_min_n,
+        "hbm_budget_gb": budget / 2**30, "precision": "fp64" if prec == fifa.FIFA_FP64 else "mixed",
+        "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+        "mean_latency_s": float(lat.mean()), "iters_per_s": len(ok) * iters / span,
+        "points_iters_per_s": float(sizes[[r[0] == 0 for r in res]].sum()) * iters / span,
+        "served_req_per_s": len(ok) / span, "span_s": span, "peak_in_flight": stats.peak_in_flight,
+        "peak_hbm_gb": stats.peak_bytes / 2**30,
+    }
+
+
+def additive_leg(fifa, torch, sweeps, leaf, n=65536, d=4):
+    """The d-block additive workload: n points uniform in [0,1]^d,
+    y = sum_k sin(2 pi (k+1) x_k) + N(0, 0.1^2), one SE block per coordinate;
+    block-Gibbs sweeps per second on each precision (mixed valid only if every
+    M~ solve refined to 1e-8)."""
+    from paper_2006_06537_gb300.inputs import additive4
+
+    X, y = additive4(n)
+    vy = float(np.var(y))
+    out = {"workload": f"additive d={d}, n={n}, SE blocks, sigma=0.1", "n": n, "d": d, "leaf": leaf}
+    for name, prec in (("fp64", fifa.FIFA_FP64), ("mixed", fifa.FIFA_MIXED)):
+        stream = torch.cuda.Stream()
+        ctx = fifa.Context(leaf_size=leaf, aca_tol=EPS, rank_cap=CAP, prec=prec, refine_max=8, refine_tol=1e-12,
+                           arena_bytes=8 << 30, stream=stream)
+        Xd = torch.tensor(np.ascontiguousarray(X[:, :d].T), device="cuda")
+        yd = torch.tensor(y, device="cuda")
+        torch.cuda.synchronize()
+        pr = fifa.fifa_prior(1.0, 1.0, 1.0, 1.0, math.log(0.1), 1.0, 0.2)
+        m = fifa.fifa_additive_create(ctx.h, Xd, yd, n, d, fifa.fifa_hyper(0, vy / d, 0.1, 0.5 * vy, 1e-6), pr, 0)
+        tr = np.zeros((sweeps, fifa.fifa_additive_trace_fields(d)))
+        st = fifa.fifa_additive_sweep(ctx.h, m, 3, None, allow=tuple(range(16)))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        if st == 0:
+            st = fifa.fifa_additive_sweep(ctx.h, m, sweeps, tr, allow=tuple(range(16)))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / sweeps
+        res = float(tr[:, 4].max())
+        ok = st == 0 and (prec == fifa.FIFA_FP64 or res <= 1e-8)
+        out[name] = {"sweeps_per_s": 1e3 / ms if ok else None, "ms_per_sweep": ms if ok else None, "valid": ok,
+                     "refine_residual": res, "status": int(st), "kernels_per_sweep": fifa.fifa_additive_kernel_nodes(m),
+                     "sigma2": float(tr[-1, 1]), "rho": [float(v) for v in tr[-1, 5 + d:5 + 2 * d]]}
+        fifa.fifa_destroy_additive(ctx.h, m)
+        ctx.close()
+    return out
 
 
 def count_launches(L: int, mixed: bool, refine_max: int, grouped_aca: bool) -> int:

@@ -73,6 +73,10 @@ typedef struct {
   int prec;           /* fifa_precision: FP64, or MIXED (M~ factor in FP32 + FP64 refinement) */
   double refine_tol;  /* MIXED: stop refining when ||b - M~ x|| <= refine_tol ||b|| */
   int refine_max;     /* MIXED: refinement steps captured per solve (fixed; converged steps are no-ops) */
+  int independent_ctas; /* 1: no kernel splits a tree node over a group of CTAs that wait on each
+                           other (every CTA runs independently); required when several contexts
+                           launch work concurrently on one GPU, since grouped kernels size their
+                           groups to the whole GPU.  0: groups fill the GPU for the top levels. */
 } fifa_opts;
 
 /* Priors: inverse-gamma IG(shape, scale) on tau2 and sigma2 (the conjugate
@@ -195,6 +199,125 @@ fifa_status fifa_chain_kernel_nodes(const fifa_chain* chain, int* out_host);
  * (nullable), hyperparameters to h_host (nullable); synchronizes. */
 fifa_status fifa_chain_get(fifa_ctx* ctx, const fifa_chain* chain, double* f_dev, double* mean_dev,
                            fifa_hyper* h_host);
+
+/* Device bytes a context needs for one Gibbs chain of n points with these
+ * options (its plan, scratch, H-matrices, factors, vectors and trace): an
+ * arena of this size holds exactly fifa_chain_create's allocations.
+ * Synchronizes nothing.  Errors: INVALID_ARG, UNSUPPORTED (as fifa_create). */
+fifa_status fifa_chain_bytes(const fifa_opts* opts, int64_t n, size_t* bytes_out);
+
+/* Additive model of d one-dimensional GP blocks (Sec. 4.2 allows an additive
+ * model instead of the tensor-product kernel for d-dimensional inputs):
+ *   y = sum_k f_k(x_k) + e,  e ~ N(0, sigma2 I),  f_k ~ GP(0, tau2_k C(rho_k)).
+ * X_dev: d columns of n doubles, coordinate k of point i at X_dev[k n + i],
+ * points in any order; y_dev: n doubles.  Each block stably sorts its
+ * coordinate at creation (ties keep the lower point index first) and keeps a
+ * chain on the sorted coordinate.  init gives the kernel, nugget, and the
+ * starting rho and tau2 of every block and the shared sigma2.  Block k draws
+ * from Philox stream id k, the shared sigma2 from stream id d.  The caller's
+ * buffers are copied; they may be freed after the call (synchronizes).
+ * Errors: INVALID_ARG (d outside 1..FIFA_ADDITIVE_MAX_D, non-finite x),
+ * OOM, and those of fifa_chain_create. */
+typedef struct fifa_additive fifa_additive;
+#define FIFA_ADDITIVE_MAX_D 16
+fifa_status fifa_additive_create(fifa_ctx* ctx, const double* X_dev, const double* y_dev, int64_t n, int d,
+                                 const fifa_hyper* init, const fifa_prior* prior, uint64_t seed,
+                                 fifa_additive** out);
+
+/* Run `sweeps` block-Gibbs sweeps: for k = 0..d-1, f_k by Algorithm 1 on the
+ * partial residual y - sum_{j != k} f_j (subtracted in ascending j, sorted by
+ * x_k); then sigma2 | y, f_1..f_d; then for each k, tau2_k | f_k and the
+ * Metropolis step on log rho_k.  One sweep is captured in a CUDA graph.
+ * trace_host (nullable): sweeps rows of FIFA_ADDITIVE_TRACE_FIELDS(d) doubles:
+ * sweep, sigma2, ||y - sum_k f_k||^2, status, largest refinement residual of the
+ * blocks' M~ solves, tau2[d], rho[d], accepted[d].
+ * Errors: the blocks' device status (NOT_SPD, TIMEOUT). */
+#define FIFA_ADDITIVE_TRACE_FIELDS(d) (5 + 3 * (d))
+fifa_status fifa_additive_sweep(fifa_ctx* ctx, fifa_additive* model, int sweeps, double* trace_host);
+
+/* Current state (synchronizes): F_dev (nullable) receives f_1..f_d as d
+ * columns of n doubles in the original point order; sigma2_host (nullable);
+ * blocks_host (nullable) d entries with each block's tau2 and rho (sigma2
+ * the shared value). */
+fifa_status fifa_additive_get(fifa_ctx* ctx, const fifa_additive* model, double* F_dev, double* sigma2_host,
+                              fifa_hyper* blocks_host);
+
+/* Kernel nodes of the captured sweep graph, or -1 without a graph. */
+fifa_status fifa_additive_kernel_nodes(const fifa_additive* model, int* out_host);
+
+void fifa_destroy_additive(fifa_ctx* ctx, fifa_additive* model);
+
+/* Serving: independent 1-D GP regression requests (each a Gibbs chain on its
+ * own sorted inputs) with continuous batching on the current GPU.  The server
+ * allocates hbm_budget device bytes once and runs `slots` workers, each a host
+ * thread with its own CUDA stream.  A queued request is admitted, oldest first
+ * among those a worker may run, when that worker is idle and the budget can
+ * hold its chain (fifa_chain_bytes plus its input and result buffers);
+ * admitted requests run concurrently and their kernels overlap on the GPU.
+ * Narrow workers use independent CTAs (opts.independent_ctas forced to 1).
+ * With wide_min_n > 0, worker 0 alone runs the requests with n >= wide_min_n,
+ * with CTA groups and fused sweeps spanning the GPU (the only stream whose
+ * kernels' CTAs wait on each other).  A request's worker type depends only on
+ * its n, so its result does not depend on what else is in flight.  This API
+ * has no counterpart in the paper; it serves its sampler to many users. */
+typedef struct fifa_server fifa_server;
+typedef struct {
+  fifa_opts opts;     /* leaf size, ACA tolerance, rank cap, precision of every request */
+  size_t hbm_budget;  /* device bytes reserved once for all requests in flight */
+  int slots;          /* requests in flight at once, 1..256 */
+  int64_t wide_min_n; /* 0: all workers narrow; > 0: worker 0 is wide (needs slots >= 2) */
+} fifa_server_opts;
+
+typedef struct {
+  const double* x_host;  /* n inputs, sorted ascending (copied at submit) */
+  const double* y_host;  /* n observations (copied at submit) */
+  int64_t n;
+  fifa_hyper init;       /* kernel, nugget, starting tau2, rho, sigma2 */
+  fifa_prior prior;
+  uint64_t seed, chain_id;  /* Philox key and stream id of the chain */
+  int iters;             /* Gibbs iterations (Eqs. posterior_gibs1-4 and the Metropolis step) */
+  int burn;              /* iterations left out of the returned estimates, 0 <= burn < iters */
+  int ndraws;            /* draws of f returned, 0 <= ndraws <= iters - burn */
+} fifa_request;
+
+typedef struct {
+  int status;                         /* fifa_status of the request */
+  double t_submit, t_start, t_done;   /* seconds on the server's monotonic clock */
+  fifa_hyper last;                    /* hyperparameters after the last iteration */
+  double accept_rate;                 /* accepted Metropolis proposals / iters */
+  size_t bytes;                       /* device bytes the request held while running */
+} fifa_result;
+
+typedef struct {
+  double now;               /* seconds on the server's clock */
+  int queued, in_flight, peak_in_flight;
+  size_t bytes_in_use, peak_bytes;
+  uint64_t completed, iterations_done;
+} fifa_server_counters;
+
+/* Errors: INVALID_ARG (slots outside 1..256, budget below 16 MiB, bad opts),
+ * UNSUPPORTED, OOM (the budget cannot be allocated). */
+fifa_status fifa_server_create(const fifa_server_opts* opts, fifa_server** out);
+
+/* Queue a request; returns at once with its id.  The result (posterior mean =
+ * average over iterations [burn, iters) of the conditional means tau2 C~ r,
+ * and f at iterations burn + floor((j + 1)(iters - burn) / ndraws) - 1) is
+ * kept until fifa_server_wait collects it.  Errors: INVALID_ARG (sizes,
+ * non-finite data), UNSORTED, OOM (one request larger than the budget). */
+fifa_status fifa_server_submit(fifa_server* server, const fifa_request* req, uint64_t* id_out);
+
+/* Block until request `id` is done; copy its posterior mean (n doubles) and
+ * draws (ndraws x n) to host buffers (nullable) and its timing to res
+ * (nullable); then forget the request.  Returns the request's status
+ * (INVALID_ARG for an unknown id). */
+fifa_status fifa_server_wait(fifa_server* server, uint64_t id, double* mean_host, double* draws_host,
+                             fifa_result* res);
+
+fifa_status fifa_server_stats(fifa_server* server, fifa_server_counters* out);
+
+/* Finish the requests in flight, drop the queued ones, free the budget.  Call
+ * it after every fifa_server_wait has returned. */
+void fifa_server_destroy(fifa_server* server);
 
 /* Introspection for tests and tools (synchronize).  Layouts:
  *   ranks[node], node = 2^l - 1 + i for node i of level l (2^L - 1 nodes);

@@ -1,0 +1,297 @@
+// Additive model of d one-dimensional GP blocks (Sec. 4.2 allows an additive
+// model in place of the tensor-product kernel):
+//   y = sum_k f_k(x_k) + e,  e ~ N(0, sigma2 I),  f_k ~ GP(0, tau2_k C(rho_k)).
+// One block-Gibbs sweep:
+//   for k = 0..d-1: r = y - sum_{j != k} f_j, sorted by x_k; f_k | r by
+//                   Algorithm 1 with (tau2_k, sigma2, rho_k); scattered back
+//   sigma2 | y, f_1..f_d
+//   for k:          tau2_k | f_k, then the Metropolis step on log rho_k
+// Each block is a Gibbs chain on its sorted coordinate (Philox stream id k);
+// the shared sigma2 has its own small state (stream id d).  The sweep is
+// captured once in a CUDA graph and replayed.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "../../include/fifa.h"
+#include "fifa_api_internal.h"
+#include "fifa_chain.h"
+#include "fifa_chain_impl.h"
+#include "fifa_launch.h"
+
+#define CK(call)                 \
+  do {                           \
+    cudaError_t e_ = (call);     \
+    if (e_ != cudaSuccess) {     \
+      ctx->last_cuda = e_;       \
+      return FIFA_ERR_CUDA;      \
+    }                            \
+  } while (0)
+
+#define ADD_TRACE_FIELDS_G 3
+
+struct fifa_additive {
+  int d = 0;
+  int64_t n = 0;
+  fifa_chain* blk[FIFA_ADDITIVE_MAX_D] = {};
+  int64_t* perm = nullptr;  // d x n
+  double* F = nullptr;      // n x d, column k at F + k n, original order
+  double* y = nullptr;
+  double* res = nullptr;
+  ChainDev* g = nullptr;  // shared sigma2 state
+  ChainDev** blk_dev = nullptr;
+  double* gtrace = nullptr;
+  uint64_t iter_host = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_failed = false;
+};
+
+static fifa_status additive_sweep_enqueue(fifa_ctx* ctx, fifa_additive* A) {
+  const int64_t n = A->n;
+  const int d = A->d;
+  cudaStream_t s = ctx->stream;
+  fifa_status st = FIFA_OK;
+  // f_k | y - sum_{j != k} f_j, blocks in order
+  for (int k = 0; k < d && st == FIFA_OK; ++k) {
+    fifa_chain* ch = A->blk[k];
+    if (launch_add_gather(A->y, A->F, A->perm + (size_t)k * n, n, d, k, ch->y, s) != cudaSuccess) {
+      st = FIFA_ERR_CUDA;
+      break;
+    }
+    ctx->active_scratch = ch->scratch;
+    st = chain_phase_draw(ctx, ch);
+    if (st == FIFA_OK && launch_add_scatter(ch->f, A->perm + (size_t)k * n, n, A->F + (size_t)k * n, s) != cudaSuccess)
+      st = FIFA_ERR_CUDA;
+  }
+  // shared sigma2
+  if (st == FIFA_OK) {
+    ctx->active_scratch = A->blk[0]->scratch;
+    Scratch S = carve(ctx, A->blk[0]->plan);
+    if (launch_add_residual(A->y, A->F, n, d, A->res, s) != cudaSuccess ||
+        launch_sumsq(A->res, A->F + (size_t)(d - 1) * n, n, S.red, &A->g->rss, s) != cudaSuccess ||
+        launch_add_sigma2(A->g, A->blk_dev, d, s) != cudaSuccess)
+      st = FIFA_ERR_CUDA;
+  }
+  // tau2_k and rho_k of every block
+  for (int k = 0; k < d && st == FIFA_OK; ++k) {
+    fifa_chain* ch = A->blk[k];
+    ctx->active_scratch = ch->scratch;
+    Scratch S = carve(ctx, ch->plan);
+    st = chain_phase_hyper(ctx, ch, S);
+  }
+  ctx->active_scratch = nullptr;
+  if (st == FIFA_ERR_CUDA) ctx->last_cuda = cudaGetLastError();
+  return st;
+}
+
+extern "C" fifa_status fifa_additive_create(fifa_ctx* ctx, const double* X_dev, const double* y_dev, int64_t n,
+                                            int d, const fifa_hyper* init, const fifa_prior* prior, uint64_t seed,
+                                            fifa_additive** out) {
+  if (!ctx || !X_dev || !y_dev || !init || !prior || !out || n < 2 || d < 1 || d > FIFA_ADDITIVE_MAX_D)
+    return FIFA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (ctx->capturing) return FIFA_ERR_INVALID_ARG;
+  fifa_additive* A = new (std::nothrow) fifa_additive();
+  if (!A) return FIFA_ERR_OOM;
+  A->d = d;
+  A->n = n;
+  auto fail = [&](fifa_status e) {
+    fifa_destroy_additive(ctx, A);
+    return e;
+  };
+  cudaStream_t s = ctx->stream;
+  A->perm = (int64_t*)ctx->arena.alloc(sizeof(int64_t) * n * d);
+  A->F = (double*)ctx->arena.alloc(sizeof(double) * n * d);
+  A->y = (double*)ctx->arena.alloc(sizeof(double) * n);
+  A->res = (double*)ctx->arena.alloc(sizeof(double) * n);
+  A->g = (ChainDev*)ctx->arena.alloc(sizeof(ChainDev));
+  A->blk_dev = (ChainDev**)ctx->arena.alloc(sizeof(ChainDev*) * FIFA_ADDITIVE_MAX_D);
+  A->gtrace = (double*)ctx->arena.alloc(sizeof(double) * CHAIN_TRACE_CAP * ADD_TRACE_FIELDS_G);
+  if (!A->perm || !A->F || !A->y || !A->res || !A->g || !A->blk_dev || !A->gtrace) return fail(FIFA_ERR_OOM);
+  CK(cudaMemcpyAsync(A->y, y_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(A->F, 0, sizeof(double) * n * d, s));
+  CK(cudaMemsetAsync(A->res, 0, sizeof(double) * n, s));
+  // per block: stable sort of coordinate k (ties keep the lower point index first)
+  std::vector<double> xk(n), xs(n);
+  std::vector<int64_t> idx(n);
+  for (int k = 0; k < d; ++k) {
+    CK(cudaMemcpyAsync(xk.data(), X_dev + (size_t)k * n, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < n; ++i)
+      if (!std::isfinite(xk[i])) return fail(FIFA_ERR_INVALID_ARG);
+    std::iota(idx.begin(), idx.end(), (int64_t)0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return xk[a] < xk[b]; });
+    for (int64_t i = 0; i < n; ++i) xs[i] = xk[idx[i]];
+    CK(cudaMemcpyAsync(A->perm + (size_t)k * n, idx.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(A->res, xs.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    // the block's data buffer is overwritten by the partial residual every sweep
+    fifa_status st = fifa_chain_create(ctx, A->res, A->y, n, init, prior, seed, (uint64_t)k, &A->blk[k]);
+    if (st != FIFA_OK) return fail(st);
+  }
+  ChainDev* ptrs[FIFA_ADDITIVE_MAX_D] = {};
+  for (int k = 0; k < d; ++k) ptrs[k] = A->blk[k]->dev;
+  CK(cudaMemcpyAsync(A->blk_dev, ptrs, sizeof(ptrs), cudaMemcpyHostToDevice, s));
+  ChainDev g = A->blk[0]->init;
+  g.chain_id = (uint64_t)d;
+  g.iter = 0;
+  g.rss = 0.0;
+  g.trace = A->gtrace;
+  g.trace_cap = CHAIN_TRACE_CAP;
+  CK(cudaMemcpyAsync(A->g, &g, sizeof(ChainDev), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(A->res, 0, sizeof(double) * n, s));
+  CK(cudaStreamSynchronize(s));
+  *out = A;
+  return FIFA_OK;
+}
+
+static void additive_build_graph(fifa_ctx* ctx, fifa_additive* A) {
+  if (A->exec || A->graph_failed) return;
+  cudaStream_t s = ctx->stream;
+  if (s == nullptr || cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    A->graph_failed = true;
+    return;
+  }
+  ctx->capturing = true;
+  fifa_status st = additive_sweep_enqueue(ctx, A);
+  ctx->capturing = false;
+  cudaGraph_t gr = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &gr);
+  if (st != FIFA_OK || e != cudaSuccess || !gr || cudaGraphInstantiate(&A->exec, gr, 0) != cudaSuccess) {
+    if (gr) cudaGraphDestroy(gr);
+    cudaGetLastError();
+    A->exec = nullptr;
+    A->graph_failed = true;
+    return;
+  }
+  A->graph = gr;
+}
+
+extern "C" fifa_status fifa_additive_sweep(fifa_ctx* ctx, fifa_additive* A, int sweeps, double* trace_host) {
+  if (!ctx || !A || sweeps < 0 || ctx->capturing) return FIFA_ERR_INVALID_ARG;
+  cudaStream_t s = ctx->stream;
+  additive_build_graph(ctx, A);
+  const int d = A->d;
+  const int TF = FIFA_ADDITIVE_TRACE_FIELDS(d);
+  std::vector<double> gt, bt;
+  int done = 0;
+  while (done < sweeps) {
+    const int chunk = std::min(sweeps - done, CHAIN_TRACE_CAP);
+    for (int k = 0; k < chunk; ++k) {
+      if (A->exec) {
+        CK(cudaGraphLaunch(A->exec, s));
+      } else {
+        fifa_status st = additive_sweep_enqueue(ctx, A);
+        if (st != FIFA_OK) return st;
+      }
+    }
+    if (trace_host) {
+      // rows [first, first + chunk) of the rings, possibly wrapping
+      gt.assign((size_t)chunk * ADD_TRACE_FIELDS_G, 0.0);
+      bt.assign((size_t)chunk * CHAIN_TRACE_FIELDS * d, 0.0);
+      const uint64_t first = A->iter_host % CHAIN_TRACE_CAP;
+      const uint64_t n1 = std::min<uint64_t>(chunk, CHAIN_TRACE_CAP - first);
+      auto fetch = [&](double* dst, const double* ring, int fields) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(dst, ring + first * fields, sizeof(double) * n1 * fields,
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && n1 < (uint64_t)chunk)
+          e = cudaMemcpyAsync(dst + n1 * fields, ring, sizeof(double) * (chunk - n1) * fields, cudaMemcpyDeviceToHost,
+                              s);
+        return e;
+      };
+      CK(fetch(gt.data(), A->gtrace, ADD_TRACE_FIELDS_G));
+      for (int k = 0; k < d; ++k)
+        CK(fetch(bt.data() + (size_t)k * chunk * CHAIN_TRACE_FIELDS, A->blk[k]->trace, CHAIN_TRACE_FIELDS));
+      CK(cudaStreamSynchronize(s));
+      for (int t = 0; t < chunk; ++t) {
+        double* row = trace_host + (size_t)(done + t) * TF;
+        row[0] = gt[(size_t)t * ADD_TRACE_FIELDS_G + 0];
+        row[1] = gt[(size_t)t * ADD_TRACE_FIELDS_G + 1];
+        row[2] = gt[(size_t)t * ADD_TRACE_FIELDS_G + 2];
+        int status = 0;
+        double res = 0.0;
+        for (int k = 0; k < d; ++k) {
+          const double* br = bt.data() + ((size_t)k * chunk + t) * CHAIN_TRACE_FIELDS;
+          status |= (int)br[10];
+          res = std::max(res, br[9]);
+          row[5 + k] = br[2];
+          row[5 + d + k] = br[3];
+          row[5 + 2 * d + k] = br[4];
+        }
+        row[3] = (double)status;
+        row[4] = res;
+      }
+    }
+    A->iter_host += chunk;
+    for (int k = 0; k < d; ++k) A->blk[k]->iter_host += chunk;
+    done += chunk;
+  }
+  int cs = 0;
+  for (int k = 0; k < d; ++k) {
+    CK(cudaMemcpyAsync(ctx->host_flags, &A->blk[k]->dev->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    cs |= ctx->host_flags[0];
+  }
+  if (cs & FIFA_DEV_TIMEOUT) return FIFA_ERR_TIMEOUT;
+  if (cs & FIFA_DEV_NOT_SPD) return FIFA_ERR_NOT_SPD;
+  return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_additive_get(fifa_ctx* ctx, const fifa_additive* A, double* F_dev, double* sigma2_host,
+                                         fifa_hyper* blocks_host) {
+  if (!ctx || !A) return FIFA_ERR_INVALID_ARG;
+  cudaStream_t s = ctx->stream;
+  if (F_dev) CK(cudaMemcpyAsync(F_dev, A->F, sizeof(double) * A->n * A->d, cudaMemcpyDeviceToDevice, s));
+  ChainDev g;
+  CK(cudaMemcpyAsync(&g, A->g, sizeof(ChainDev), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (sigma2_host) *sigma2_host = g.sigma2;
+  if (blocks_host)
+    for (int k = 0; k < A->d; ++k) {
+      fifa_status st = fifa_chain_get(ctx, A->blk[k], nullptr, nullptr, &blocks_host[k]);
+      if (st != FIFA_OK) return st;
+    }
+  return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_additive_kernel_nodes(const fifa_additive* A, int* out_host) {
+  if (!A || !out_host) return FIFA_ERR_INVALID_ARG;
+  *out_host = -1;
+  if (!A->graph) return FIFA_OK;
+  size_t count = 0;
+  if (cudaGraphGetNodes(A->graph, nullptr, &count) != cudaSuccess) return FIFA_ERR_CUDA;
+  std::vector<cudaGraphNode_t> nodes(count);
+  if (count && cudaGraphGetNodes(A->graph, nodes.data(), &count) != cudaSuccess) return FIFA_ERR_CUDA;
+  int kernels = 0;
+  for (size_t i = 0; i < count; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+  }
+  *out_host = kernels;
+  return FIFA_OK;
+}
+
+extern "C" void fifa_destroy_additive(fifa_ctx* ctx, fifa_additive* A) {
+  if (!ctx || !A) return;
+  cudaStreamSynchronize(ctx->stream);
+  if (A->exec) cudaGraphExecDestroy(A->exec);
+  if (A->graph) cudaGraphDestroy(A->graph);
+  for (int k = 0; k < A->d; ++k)
+    if (A->blk[k]) fifa_destroy_chain(ctx, A->blk[k]);
+  ctx->arena.release(A->perm);
+  ctx->arena.release(A->F);
+  ctx->arena.release(A->y);
+  ctx->arena.release(A->res);
+  ctx->arena.release(A->g);
+  ctx->arena.release(A->blk_dev);
+  ctx->arena.release(A->gtrace);
+  delete A;
+}

@@ -85,13 +85,23 @@ static int levels_for(int64_t n, int B) {
   return L;
 }
 
-Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st) {
-  auto key = std::make_pair(n, ctx->opts.leaf_size);
-  auto it = ctx->plans.find(key);
-  if (it != ctx->plans.end()) return it->second;
-  Plan* P = new Plan();
+// Partials of the fused sweep: two buffers of one projection per CTA, for up to
+// min(nleaf, FS_CTAS_MAX) CTAs (none with independent CTAs: no grid barriers).
+static size_t fused_sweep_part_doubles(const Plan* P, const fifa_opts& o) {
+  if (o.independent_ctas) return 1;
+  return (size_t)2 * std::min(P->nleaf, FS_CTAS_MAX) * FS_PART_STRIDE;
+}
+
+// Host part of a plan: bounds, ACA / level / sweep groups, scratch size.
+// aca_cores / lvl_cores: co-resident CTA budgets of the ACA and level kernels.
+static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, int lvl_cores, fifa_status* st) {
+  Plan* P = new (std::nothrow) Plan();
+  if (!P) {
+    *st = FIFA_ERR_OOM;
+    return nullptr;
+  }
   P->n = n;
-  P->B = ctx->opts.leaf_size;
+  P->B = o.leaf_size;
   P->L = levels_for(n, P->B);
   if (P->L >= FIFA_LEVELS_MAX) {
     delete P;
@@ -119,27 +129,27 @@ Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st) {
   }
   P->Bm = 0;
   for (size_t i = 0; i + 1 < prev.size(); ++i) P->Bm = std::max(P->Bm, prev[i + 1] - prev[i]);
-  const int cap = ctx->opts.rank_cap;
+  const int cap = o.rank_cap;
+  const bool groups = !o.independent_ctas;
   // ACA groups.  A level-l block has ~n/2^l rows + columns and every level has
   // about the same total work, so the co-resident CTA budget is split evenly
   // over the top levels: level l gets G_l = budget / (levels * 2^l) CTAs per
   // block (>= 2 to be worth a group).  Levels below run one CTA per block in a
   // second launch.
-  const int coresident = ctx->aca_coresident;
   std::vector<int> Gl(P->L, 1);
   int ncoop_levels = 0;
-  for (int l = 0; l < P->L; ++l) {
+  for (int l = 0; groups && l < P->L; ++l) {
     const int64_t entries = n >> l;
     if (entries < 8192) break;
     ncoop_levels = l + 1;
   }
   while (ncoop_levels > 0) {
-    const int per_level = coresident / ncoop_levels;
+    const int per_level = aca_cores / ncoop_levels;
     if ((per_level >> (ncoop_levels - 1)) >= 2) break;
     --ncoop_levels;  // the deepest candidate level cannot get two CTAs per block
   }
   if (ncoop_levels > 0) {
-    const int per_level = coresident / ncoop_levels;
+    const int per_level = aca_cores / ncoop_levels;
     for (int l = 0; l < ncoop_levels; ++l) {
       const int64_t want = std::max<int64_t>(2, (n >> l) / 4096);
       Gl[l] = (int)std::min<int64_t>(want, per_level >> l);
@@ -157,8 +167,9 @@ Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st) {
   }
   P->aca_ncoop = (int)coop.size();
   P->aca_nsolo = (int)solo.size();
+  P->work_host = coop;
+  P->work_host.insert(P->work_host.end(), solo.begin(), solo.end());
   // factor / sweep groups per level: one CTA per node up to 8192 rows
-  const int lvl_cores = ctx->level_coresident[0];
   P->lvl_G.assign(P->L, 1);
   P->sweep_G.assign(P->L, 1);
   for (int l = 0; l < P->L; ++l) {
@@ -166,39 +177,15 @@ Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st) {
     const int64_t nodes = (int64_t)1 << l;
     // levels with fewer nodes than the co-resident CTAs split each node's rows
     // over a group of CTAs (>= 1024 rows each) that fills the GPU
-    if (2 * nodes <= lvl_cores && len >= 2048) {
+    if (groups && 2 * nodes <= lvl_cores && len >= 2048) {
       const int64_t G = std::min<int64_t>(len / 1024, lvl_cores / nodes);
       P->lvl_G[l] = (int)std::max<int64_t>(1, G);
     }
     P->sweep_G[l] = (int)std::max<int64_t>(1, (len + 2047) / 2048);
   }
-  // device copies
-  size_t bytes = P->bnd_host.size() * sizeof(int) + (coop.size() + solo.size()) * sizeof(int4);
-  char* mem = (char*)ctx->arena.alloc(bytes);
-  if (!mem) {
-    delete P;
-    *st = FIFA_ERR_OOM;
-    return nullptr;
-  }
-  P->bnd_dev = (int*)mem;
-  size_t wo = (P->bnd_host.size() * sizeof(int) + 15) & ~(size_t)15;
-  P->aca_work = (int4*)(mem + wo);
-  if (wo + (coop.size() + solo.size()) * sizeof(int4) > ((bytes + 255) & ~(size_t)255)) {
-    // re-allocate with the alignment padding included
-    ctx->arena.release(mem);
-    mem = (char*)ctx->arena.alloc(wo + (coop.size() + solo.size()) * sizeof(int4));
-    if (!mem) {
-      delete P;
-      *st = FIFA_ERR_OOM;
-      return nullptr;
-    }
-    P->bnd_dev = (int*)mem;
-    P->aca_work = (int4*)(mem + wo);
-  }
-  cudaMemcpy(P->bnd_dev, P->bnd_host.data(), P->bnd_host.size() * sizeof(int), cudaMemcpyHostToDevice);
-  std::vector<int4> all = coop;
-  all.insert(all.end(), solo.begin(), solo.end());
-  if (!all.empty()) cudaMemcpy(P->aca_work, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  // device arrays: bounds, then the ACA work list at a 16-byte offset
+  P->work_off = (P->bnd_host.size() * sizeof(int) + 15) & ~(size_t)15;
+  P->dev_bytes = P->work_off + P->work_host.size() * sizeof(int4);
   // scratch requirement (bytes)
   size_t need = 0;
   auto add = [&](size_t b) { need += (b + 255) & ~(size_t)255; };
@@ -218,9 +205,90 @@ Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st) {
   add(sizeof(double) * (size_t)n * 16);                                   // work vectors
   add(sizeof(double) * 512);                                              // reduction partials
   add(256);                                                               // flags
+  add(sizeof(double) * fused_sweep_part_doubles(P, o));                   // fused sweep partials
+  add(256);                                                               // fused sweep barrier
   P->scratch_bytes = need;
+  return P;
+}
+
+Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st) {
+  auto key = std::make_pair(n, ctx->opts.leaf_size);
+  auto it = ctx->plans.find(key);
+  if (it != ctx->plans.end()) return it->second;
+  Plan* P = plan_build(n, ctx->opts, ctx->aca_coresident, ctx->level_coresident[0], st);
+  if (!P) return nullptr;
+  // fused sweep: the largest power-of-two grid (<= nleaf, FS_CTAS_MAX) whose
+  // CTAs, each holding the longest level-k node in shared memory, are all
+  // co-resident (for both factor precisions)
+  if (!ctx->opts.independent_ctas) {
+    for (int k = std::min(P->L, 10); k >= 0; --k) {
+      if ((1 << k) > FS_CTAS_MAX) continue;
+      int rows = 0;
+      for (int i = 0; i < (1 << k); ++i)
+        rows = std::max(rows, P->bnd_host[bnd_off(k) + i + 1] - P->bnd_host[bnd_off(k) + i]);
+      const int cap = ctx->opts.rank_cap;
+      const int co = std::min(sweep_fused_coresident(0, rows, cap), sweep_fused_coresident(1, rows, cap));
+      if (co >= (1 << k)) {
+        P->fs_ls = k;
+        P->fs_rows = rows;
+        break;
+      }
+    }
+  }
+  char* mem = (char*)ctx->arena.alloc(P->dev_bytes);
+  if (!mem) {
+    delete P;
+    *st = FIFA_ERR_OOM;
+    return nullptr;
+  }
+  P->bnd_dev = (int*)mem;
+  P->aca_work = (int4*)(mem + P->work_off);
+  cudaError_t e = cudaMemcpyAsync(P->bnd_dev, P->bnd_host.data(), P->bnd_host.size() * sizeof(int),
+                                  cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess && !P->work_host.empty())
+    e = cudaMemcpyAsync(P->aca_work, P->work_host.data(), P->work_host.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                        ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // the host vectors stay, but keep the copy simple
+  if (e != cudaSuccess) {
+    ctx->last_cuda = e;
+    ctx->arena.release(mem);
+    delete P;
+    *st = FIFA_ERR_CUDA;
+    return nullptr;
+  }
   ctx->plans[key] = P;
   return P;
+}
+
+// Device bytes of one arena allocation of b bytes.
+static inline size_t arena_round(size_t b) { return b == 0 ? 256 : (b + 255) & ~(size_t)255; }
+
+size_t hmat_bytes(const Plan* P, int cap) {
+  const size_t nn = std::max(1, P->nnodes);
+  return arena_round(sizeof(double) * (size_t)P->nleaf * P->Bm * P->Bm) +
+         arena_round(sizeof(double) * (size_t)std::max(1, P->L) * cap * P->n) + arena_round(sizeof(int) * nn) +
+         2 * arena_round(sizeof(int) * nn * cap) + arena_round(sizeof(int)) + arena_round(sizeof(HmatDesc));
+}
+
+size_t fact_bytes(const Plan* P, int cap, int prec) {
+  const size_t nn = std::max(1, P->nnodes);
+  const size_t esz = prec ? sizeof(float) : sizeof(double);
+  return arena_round(esz * (size_t)P->nleaf * P->Bm * P->Bm) + arena_round(esz * (size_t)std::max(1, P->L) * cap * P->n) +
+         2 * arena_round(sizeof(double) * nn * 4 * cap * cap) + arena_round(sizeof(int) * nn) +
+         arena_round(sizeof(double) * (P->nleaf + nn)) + arena_round(sizeof(double)) + arena_round(sizeof(int)) +
+         arena_round(sizeof(FactDesc));
+}
+
+extern "C" fifa_status fifa_chain_bytes(const fifa_opts* opts, int64_t n, size_t* bytes_out) {
+  if (!opts || !bytes_out || n < 2) return FIFA_ERR_INVALID_ARG;
+  if (opts->leaf_size < 1 || opts->rank_cap < 1) return FIFA_ERR_INVALID_ARG;
+  if (opts->leaf_size > FIFA_LEAF_MAX || opts->rank_cap > FIFA_CAP_MAX) return FIFA_ERR_UNSUPPORTED;
+  fifa_status st = FIFA_OK;
+  Plan* P = plan_build(n, *opts, aca_max_coresident_ctas(), level_max_coresident(0, opts->rank_cap), &st);
+  if (!P) return st;
+  *bytes_out = arena_round(256) /* context flags */ + arena_round(P->dev_bytes) + chain_bytes(P, *opts);
+  delete P;
+  return FIFA_OK;
 }
 
 // Carve the context scratch for a plan (after ensure_scratch).
@@ -245,6 +313,8 @@ Scratch carve(fifa_ctx* ctx, Plan* P) {
   S.vec = (double*)take(sizeof(double) * (size_t)P->n * 16);
   S.red = (double*)take(sizeof(double) * 512);
   S.flags = (int*)take(256);
+  S.fs_part = (double*)take(sizeof(double) * fused_sweep_part_doubles(P, ctx->opts));
+  S.fs_bar = (unsigned int*)take(256);
   return S;
 }
 
@@ -273,6 +343,7 @@ extern "C" fifa_status fifa_create(fifa_ctx** out, const fifa_opts* opts, void* 
   if (opts->leaf_size < 1 || opts->rank_cap < 1 || !(opts->aca_tol >= 0.0)) return FIFA_ERR_INVALID_ARG;
   if (opts->leaf_size > FIFA_LEAF_MAX || opts->rank_cap > FIFA_CAP_MAX) return FIFA_ERR_UNSUPPORTED;
   if (opts->prec != FIFA_FP64 && opts->prec != FIFA_MIXED) return FIFA_ERR_INVALID_ARG;
+  if (opts->independent_ctas != 0 && opts->independent_ctas != 1) return FIFA_ERR_INVALID_ARG;
   if (arena_bytes < (1u << 20)) return FIFA_ERR_INVALID_ARG;
   fifa_ctx* ctx = new (std::nothrow) fifa_ctx();
   if (!ctx) return FIFA_ERR_OOM;
@@ -319,6 +390,25 @@ extern "C" fifa_status fifa_create(fifa_ctx** out, const fifa_opts* opts, void* 
   }
   *out = ctx;
   return FIFA_OK;
+}
+
+fifa_status ctx_rebind_arena(fifa_ctx* ctx, void* base, size_t bytes) {
+  if (!ctx || !base || bytes < 1024) return FIFA_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->own_arena) return FIFA_ERR_INVALID_ARG;
+  for (auto& kv : ctx->plans) delete kv.second;
+  ctx->plans.clear();
+  ctx->arena.base = (char*)base;
+  ctx->arena.size = bytes & ~(size_t)255;
+  ctx->arena.in_use = ctx->arena.peak = 0;
+  ctx->arena.free_.clear();
+  ctx->arena.used_.clear();
+  ctx->arena.free_[0] = ctx->arena.size;
+  ctx->scratch = nullptr;
+  ctx->scratch_bytes = 0;
+  ctx->active_scratch = nullptr;
+  ctx->flags = (int*)ctx->arena.alloc(256);
+  return ctx->flags ? FIFA_OK : FIFA_ERR_OOM;
 }
 
 extern "C" void fifa_destroy_ctx(fifa_ctx* ctx) {
@@ -577,6 +667,14 @@ fifa_status sweep_enqueue(fifa_ctx* ctx, const fifa_fact* F, int trans, int inve
   Scratch S = carve(ctx, P);
   cudaStream_t s = ctx->stream;
   const int prec = F->host.prec;
+  if (P->fs_ls >= 0) {
+    const int mode = trans ? (inverse ? 3 : 2) : (inverse ? 1 : 0);
+    CK(cudaMemsetAsync(S.fs_bar, 0, sizeof(unsigned int), s));
+    CK(cudaMemsetAsync(S.flags, 0, sizeof(int), s));
+    CK(launch_sweep_fused(F->dev, prec, P->fs_ls, P->fs_rows, ctx->opts.rank_cap, v, nrhs, mode, S.fs_part, S.fs_bar,
+                          S.flags, s));
+    return FIFA_OK;
+  }
   auto level = [&](int l, int zsel, int zt) -> cudaError_t {
     return launch_sweep_level(F->dev, prec, l, 1 << l, P->sweep_G[l], v, nrhs, S.sweep_part, zsel, zt, s);
   };

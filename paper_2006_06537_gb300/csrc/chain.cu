@@ -86,6 +86,14 @@ static fifa_status chain_iteration_enqueue(fifa_ctx* ctx, fifa_chain* ch) {
   return st;
 }
 
+size_t chain_bytes(const Plan* P, const fifa_opts& o) {
+  auto r = [](size_t b) { return b == 0 ? (size_t)256 : (b + 255) & ~(size_t)255; };
+  const int cap = o.rank_cap;
+  return 5 * r(sizeof(double) * P->n) + r(sizeof(double) * CHAIN_TRACE_CAP * CHAIN_TRACE_FIELDS) + r(P->scratch_bytes) +
+         r(sizeof(ChainDev)) + 2 * hmat_bytes(P, cap) + 2 * fact_bytes(P, cap, 0) + r(sizeof(HmatDesc)) +
+         fact_bytes(P, cap, o.prec == FIFA_MIXED ? 1 : 0);
+}
+
 static double kconst(int kind, double rho) { return kind == 0 ? 0.5 / (rho * rho) : sqrt(5.0) / rho; }
 
 extern "C" fifa_status fifa_chain_create(fifa_ctx* ctx, const double* x_dev, const double* y_dev, int64_t n,
@@ -259,6 +267,46 @@ extern "C" fifa_status fifa_gibbs_step(fifa_ctx* ctx, fifa_chain* ch, int iters,
   const int cs = ctx->host_flags[0];
   if (cs & FIFA_DEV_TIMEOUT) return FIFA_ERR_TIMEOUT;
   if (cs & FIFA_DEV_NOT_SPD) return FIFA_ERR_NOT_SPD;
+  return FIFA_OK;
+}
+
+fifa_status chain_run_collect(fifa_ctx* ctx, fifa_chain* ch, int iters, int burn, int ndraws, double* mean_acc,
+                              double* draws) {
+  if (iters < 1 || burn < 0 || burn >= iters || ndraws < 0 || ndraws > iters - burn) return FIFA_ERR_INVALID_ARG;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ch->plan->n;
+  fifa_status st = chain_build_graph(ctx, ch);
+  if (st != FIFA_OK) return st;
+  CK(cudaMemsetAsync(mean_acc, 0, sizeof(double) * n, s));
+  const int kept = iters - burn;
+  int next_draw = 0;
+  for (int t = 0; t < iters; ++t) {
+    if (ch->exec) {
+      CK(cudaGraphLaunch(ch->exec, s));
+    } else {
+      st = chain_iteration_enqueue(ctx, ch);
+      if (st != FIFA_OK) return st;
+    }
+    if (t < burn) continue;
+    CK(launch_axpy(1.0, ch->mean, mean_acc, n, s));
+    // draw j is taken at iteration burn + floor((j + 1) kept / ndraws) - 1
+    while (next_draw < ndraws && t == burn + (int)(((int64_t)(next_draw + 1) * kept) / ndraws) - 1) {
+      CK(cudaMemcpyAsync(draws + (size_t)next_draw * n, ch->f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      ++next_draw;
+    }
+  }
+  ch->iter_host += iters;
+  CK(cudaMemcpyAsync(ctx->host_flags, &ch->dev->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int cs = ctx->host_flags[0];
+  if (cs & FIFA_DEV_TIMEOUT) return FIFA_ERR_TIMEOUT;
+  if (cs & FIFA_DEV_NOT_SPD) return FIFA_ERR_NOT_SPD;
+  return FIFA_OK;
+}
+
+fifa_status chain_state(fifa_ctx* ctx, const fifa_chain* ch, ChainDev* out) {
+  CK(cudaMemcpyAsync(out, ch->dev, sizeof(ChainDev), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return FIFA_OK;
 }
 

@@ -25,8 +25,11 @@ struct Plan {
   int* bnd_dev = nullptr;
   int4* aca_work = nullptr;  // coop entries first, then solo entries
   int aca_ncoop = 0, aca_nsolo = 0;
+  std::vector<int4> work_host;
+  size_t work_off = 0, dev_bytes = 0;  // device block: bounds, then the work list at work_off
   std::vector<int> lvl_G, sweep_G;
   int lvl_ctas_max = 1;
+  int fs_ls = -1, fs_rows = 0;  // fused sweep: 2^fs_ls CTAs of fs_rows rows (-1: per-level sweeps)
   size_t scratch_bytes = 0;
 };
 
@@ -41,6 +44,8 @@ struct Scratch {
   double* vec;  // 16 n doubles
   double* red;  // 512 doubles of reduction partials
   int* flags;
+  double* fs_part;        // fused sweep partials
+  unsigned int* fs_bar;   // fused sweep grid barrier
 };
 
 struct fifa_ctx {
@@ -77,6 +82,13 @@ struct fifa_fact {
 };
 
 Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st);
+// Point a context (created on a caller-provided arena) at another device
+// range: drops its plans and every object in the old arena (synchronizes).
+fifa_status ctx_rebind_arena(fifa_ctx* ctx, void* base, size_t bytes);
+// Arena bytes of one hmat / fact / chain (every allocation rounded as the arena does).
+size_t hmat_bytes(const Plan* P, int cap);
+size_t fact_bytes(const Plan* P, int cap, int prec);
+size_t chain_bytes(const Plan* P, const fifa_opts& o);
 Scratch carve(fifa_ctx* ctx, Plan* P);
 fifa_status ensure_scratch(fifa_ctx* ctx, Plan* P);
 fifa_status hmat_alloc(fifa_ctx* ctx, Plan* P, int kind, fifa_hmat** out);

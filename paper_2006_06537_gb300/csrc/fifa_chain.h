@@ -17,6 +17,7 @@ struct ChainDev {
   int64_t n;
   int kind, accept, status, trace_cap;
   double* trace;
+  uint64_t n_accept;  // accepted Metropolis proposals since creation
 };
 
 cudaError_t launch_chain_make_view(const HmatDesc* Hc, HmatDesc* Mv, const ChainDev* c, cudaStream_t st);
@@ -26,3 +27,9 @@ cudaError_t launch_chain_propose(ChainDev* c, HmatDesc* Hp, cudaStream_t st);
 cudaError_t launch_chain_mh(ChainDev* c, HmatDesc* Hc, HmatDesc* Hp, FactDesc* Fc, FactDesc* Fp, const FactDesc* Fm,
                             cudaStream_t st);
 cudaError_t launch_ratio_sqrt(const double* num, const double* den, double* out, cudaStream_t st);
+
+cudaError_t launch_add_gather(const double* y, const double* F, const int64_t* perm, int64_t n, int d, int k,
+                              double* out, cudaStream_t st);
+cudaError_t launch_add_scatter(const double* fs, const int64_t* perm, int64_t n, double* Fk, cudaStream_t st);
+cudaError_t launch_add_residual(const double* y, const double* F, int64_t n, int d, double* out, cudaStream_t st);
+cudaError_t launch_add_sigma2(ChainDev* g, ChainDev* const* blocks, int d, cudaStream_t st);

@@ -35,3 +35,12 @@ struct fifa_chain {
 fifa_status chain_phase_draw(fifa_ctx* ctx, fifa_chain* ch);
 fifa_status chain_phase_sigma2(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
 fifa_status chain_phase_hyper(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
+
+// Serving helpers.  chain_run_collect runs `iters` iterations (graph replay)
+// and gathers on the device: mean_acc = sum of the conditional means
+// tau2 C~ r over iterations [burn, iters); draws (ndraws x n) = f at
+// iterations burn + floor((j + 1)(iters - burn) / ndraws) - 1.  Synchronizes
+// once at the end and returns the chain's device status.
+fifa_status chain_run_collect(fifa_ctx* ctx, fifa_chain* ch, int iters, int burn, int ndraws, double* mean_acc,
+                              double* draws);
+fifa_status chain_state(fifa_ctx* ctx, const fifa_chain* ch, ChainDev* out);

@@ -26,6 +26,13 @@ cudaError_t launch_logdet_reduce(const FactDesc* Fd, cudaStream_t st);
 #define SWEEP_RHS_MAX 2
 cudaError_t launch_sweep_level(const FactDesc* Fd, int prec, int lvl, int nodes, int G, double* v, int nrhs, double* part,
                                int zsel, int ztrans, cudaStream_t st);
+// Fused sweep (one cooperative launch of 2^ls CTAs; rows >= the longest
+// level-ls node).  part: 2 * 2^ls * FS_PART_STRIDE doubles; bar zeroed before.
+#define FS_PART_STRIDE (2 * FIFA_CAP_MAX * SWEEP_RHS_MAX)
+#define FS_CTAS_MAX 1024
+int sweep_fused_coresident(int prec, int rows, int cap);
+cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, int cap, double* v, int nrhs,
+                               int mode, double* part, unsigned int* bar, int* abort_flag, cudaStream_t st);
 cudaError_t launch_sweep_leaf(const FactDesc* Fd, int prec, int nleaf, double* v, int nrhs, int mode, cudaStream_t st);
 cudaError_t launch_matvec(const HmatDesc* Hd, int nleaf, int L, const double* x, int nrhs, double* part, double* proj,
                           double* y, cudaStream_t st);

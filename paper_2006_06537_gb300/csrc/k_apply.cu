@@ -1,6 +1,8 @@
 // Application kernels: W, W^T, W^-1, W^-T sweeps (SI: W = A_L ... A_0 with
 // node factors I + Q Z Q^T) and the H-matrix product (leaf products plus the
 // low-rank off-diagonal blocks), for nrhs column-major vectors.
+#include <algorithm>
+
 #include "fifa_common.cuh"
 #include "fifa_launch.h"
 
@@ -97,9 +99,85 @@ __device__ __forceinline__ double reg_sel(const double (&a)[N], int q) {
 }
 
 // ---------------------------------------------------------------------------
-// Leaf step: one warp per leaf.  mode 0: v <- L v, 1: v <- L^-1 v,
-// 2: v <- L^T v, 3: v <- L^-T v.  L column-major (L[i][k] at k*Bm + i).
+// Leaf step of one leaf by one warp, on m entries at vj (global or shared
+// memory).  mode 0: v <- L v, 1: v <- L^-1 v, 2: v <- L^T v, 3: v <- L^-T v.
+// L column-major (L[i][k] at k*Bm + i).
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void leaf_warp_apply(const T* __restrict__ Lm, int Bm, int m, double* vj, int mode, int lane) {
+  constexpr int RPL = FIFA_LEAF_MAX / 32;  // rows per lane
+  double x[RPL], o[RPL];
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    int i = lane + 32 * q;
+    x[q] = i < m ? vj[i] : 0.0;
+    o[q] = 0.0;
+  }
+  if (mode == 0) {  // o_i = sum_{k<=i} L[i][k] x_k
+    for (int k = 0; k < m; ++k) {
+      double xk = __shfl_sync(0xffffffffu, reg_sel<RPL>(x, k >> 5), k & 31);
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        int i = lane + 32 * q;
+        if (i >= k && i < m) o[q] += to_d(Lm[(size_t)k * Bm + i]) * xk;
+      }
+    }
+  } else if (mode == 1) {  // forward substitution
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) o[q] = x[q];
+    for (int k = 0; k < m; ++k) {
+      const int qk = k >> 5;
+      double ok = 0.0;
+#pragma unroll
+      for (int q = 0; q < RPL; ++q)
+        if (q == qk) ok = o[q];
+      double xk = __shfl_sync(0xffffffffu, ok, k & 31) / to_d(Lm[(size_t)k * Bm + k]);
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        int i = lane + 32 * q;
+        if (i == k) o[q] = xk;
+        else if (i > k && i < m) o[q] -= to_d(Lm[(size_t)k * Bm + i]) * xk;
+      }
+    }
+  } else if (mode == 2) {  // o_j = sum_{k>=j} L[k][j] x_k (column j contiguous)
+    for (int jj = 0; jj < m; ++jj) {
+      double part = 0.0;
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        int k = lane + 32 * q;
+        if (k >= jj && k < m) part += to_d(Lm[(size_t)jj * Bm + k]) * x[q];
+      }
+      part = warp_sum(part);
+      part = __shfl_sync(0xffffffffu, part, 0);
+#pragma unroll
+      for (int q = 0; q < RPL; ++q)
+        if (lane + 32 * q == jj) o[q] = part;
+    }
+  } else {  // backward substitution L^T x = v
+    for (int jj = m - 1; jj >= 0; --jj) {
+      double part = 0.0;
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        int k = lane + 32 * q;
+        if (k > jj && k < m) part += to_d(Lm[(size_t)jj * Bm + k]) * o[q];
+      }
+      part = warp_sum(part);
+      part = __shfl_sync(0xffffffffu, part, 0);
+      const double xj = (__shfl_sync(0xffffffffu, reg_sel<RPL>(x, jj >> 5), jj & 31) - part) /
+                        to_d(Lm[(size_t)jj * Bm + jj]);
+#pragma unroll
+      for (int q = 0; q < RPL; ++q)
+        if (lane + 32 * q == jj) o[q] = xj;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    int i = lane + 32 * q;
+    if (i < m) vj[i] = o[q];
+  }
+}
+
+// Leaf step over all leaves: one warp per leaf.
 template <typename T>
 __global__ void __launch_bounds__(256) k_sweep_leaf(const FactDesc* __restrict__ Fd, double* __restrict__ v, int nrhs, int mode) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -107,81 +185,283 @@ __global__ void __launch_bounds__(256) k_sweep_leaf(const FactDesc* __restrict__
   const int L = Fd->L, Bm = Fd->Bm, nleaf = Fd->nleaf;
   if (warp >= nleaf) return;
   const int64_t n = Fd->n;
-  const int s = Fd->bnd[bnd_off(L) + warp], e = Fd->bnd[bnd_off(L) + warp + 1], m = e - s;
+  const int s = Fd->bnd[bnd_off(L) + warp], e = Fd->bnd[bnd_off(L) + warp + 1];
   const T* Lm = (const T*)Fd->Lleaf + (size_t)warp * Bm * Bm;
-  constexpr int RPL = FIFA_LEAF_MAX / 32;  // rows per lane
-  for (int j = 0; j < nrhs; ++j) {
-    double* vj = v + (size_t)j * n + s;
-    double x[RPL], o[RPL];
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-      int i = lane + 32 * q;
-      x[q] = i < m ? vj[i] : 0.0;
-      o[q] = 0.0;
+  for (int j = 0; j < nrhs; ++j) leaf_warp_apply<T>(Lm, Bm, e - s, v + (size_t)j * n + s, mode, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Fused sweep: a whole W / W^-1 / W^T / W^-T application in one cooperative
+// launch of 2^ls CTAs.  CTA c owns the rows [S, E) of the level-ls node c and
+// keeps v on them in shared memory for the whole sweep, so v crosses HBM once
+// each way.  The leaves and every level >= ls act inside one CTA (a node there
+// lies in one CTA's rows); each level < ls exchanges one partial projection
+// per CTA through `part` (two buffers alternating by level) around one grid
+// barrier.  Same arithmetic as the per-level kernels above:
+//   p = [Q_left^T v_left ; Q_right^T v_right],  t = op(Z) p,  v += Q t.
+// ---------------------------------------------------------------------------
+#define FS_WARPS 8
+#define FS_K (2 * FIFA_CAP_MAX * SW_RHS_MAX)  // stride of one CTA's partial in `part`
+
+// Shared scratch carved after v: three FS_WARPS x K arrays, K = 2 cap SW_RHS_MAX.
+struct FsShared {
+  double* wpart;  // per-warp partial projections / reduction scratch
+  double* pv;     // per node group: projection p
+  double* tv;     // per node group: t = op(Z) p
+  int K;
+};
+
+// One level >= ls inside CTA c: the level's nodes in c's subtree, a group of
+// wpn warps per node (one warp per node once there are >= 8 nodes).
+template <typename T>
+__device__ void fs_local_level(const FactDesc* __restrict__ Fd, int l, int ls, int c, double* vs, int rows, int S,
+                               int nrhs, int zsel, int zt, FsShared& sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cap = Fd->cap, ld2 = 2 * cap;
+  const int64_t n = Fd->n;
+  const int nsub = 1 << (l - ls), i0 = c << (l - ls);
+  const int wpn = nsub >= FS_WARPS ? 1 : FS_WARPS / nsub;
+  const int groups = FS_WARPS / wpn, g = warp / wpn, wr = warp % wpn;
+  const T* Qb = (const T*)Fd->Q + (size_t)l * cap * n;
+  for (int base = 0; base < nsub; base += groups) {
+    const int li = base + g;
+    int r = 0, s = 0, h = 0, e = 0, nid = 0;
+    if (li < nsub) {
+      nid = node_id(l, i0 + li);
+      r = Fd->rank[nid];
+      node_range(Fd->bnd, l, i0 + li, s, h, e);
     }
-    if (mode == 0) {  // o_i = sum_{k<=i} L[i][k] x_k
-      for (int k = 0; k < m; ++k) {
-        double xk = __shfl_sync(0xffffffffu, reg_sel<RPL>(x, k >> 5), k & 31);
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-          int i = lane + 32 * q;
-          if (i >= k && i < m) o[q] += to_d(Lm[(size_t)k * Bm + i]) * xk;
+    // partial projections over this warp's slice of the node's rows
+    for (int side = 0; side < 2 && r > 0; ++side) {
+      const int a0 = side ? h : s, a1 = side ? e : h;
+      for (int a = 0; a < r; ++a) {
+        const T* Qc = Qb + (size_t)a * n;
+        double acc0 = 0.0, acc1 = 0.0;
+        for (int p = a0 + wr * 32 + lane; p < a1; p += wpn * 32) {
+          const double q = to_d(Qc[p]);
+          acc0 += q * vs[p - S];
+          if (nrhs > 1) acc1 += q * vs[rows + p - S];
         }
-      }
-    } else if (mode == 1) {  // forward substitution
-#pragma unroll
-      for (int q = 0; q < RPL; ++q) o[q] = x[q];
-      for (int k = 0; k < m; ++k) {
-        const int qk = k >> 5;
-        double ok = 0.0;
-#pragma unroll
-        for (int q = 0; q < RPL; ++q)
-          if (q == qk) ok = o[q];
-        double xk = __shfl_sync(0xffffffffu, ok, k & 31) / to_d(Lm[(size_t)k * Bm + k]);
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-          int i = lane + 32 * q;
-          if (i == k) o[q] = xk;
-          else if (i > k && i < m) o[q] -= to_d(Lm[(size_t)k * Bm + i]) * xk;
+        acc0 = warp_sum(acc0);
+        acc1 = warp_sum(acc1);
+        if (lane == 0) {
+          sh.wpart[warp * sh.K + (side * r + a) * nrhs] = acc0;
+          if (nrhs > 1) sh.wpart[warp * sh.K + (side * r + a) * nrhs + 1] = acc1;
         }
-      }
-    } else if (mode == 2) {  // o_j = sum_{k>=j} L[k][j] x_k (column j contiguous)
-      for (int jj = 0; jj < m; ++jj) {
-        double part = 0.0;
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-          int k = lane + 32 * q;
-          if (k >= jj && k < m) part += to_d(Lm[(size_t)jj * Bm + k]) * x[q];
-        }
-        part = warp_sum(part);
-        part = __shfl_sync(0xffffffffu, part, 0);
-#pragma unroll
-        for (int q = 0; q < RPL; ++q)
-          if (lane + 32 * q == jj) o[q] = part;
-      }
-    } else {  // backward substitution L^T x = v
-      for (int jj = m - 1; jj >= 0; --jj) {
-        double part = 0.0;
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-          int k = lane + 32 * q;
-          if (k > jj && k < m) part += to_d(Lm[(size_t)jj * Bm + k]) * o[q];
-        }
-        part = warp_sum(part);
-        part = __shfl_sync(0xffffffffu, part, 0);
-        const double xj = (__shfl_sync(0xffffffffu, reg_sel<RPL>(x, jj >> 5), jj & 31) - part) /
-                          to_d(Lm[(size_t)jj * Bm + jj]);
-#pragma unroll
-        for (int q = 0; q < RPL; ++q)
-          if (lane + 32 * q == jj) o[q] = xj;
       }
     }
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-      int i = lane + 32 * q;
-      if (i < m) vj[i] = o[q];
+    __syncthreads();
+    const int K = 2 * r * nrhs;
+    if (r > 0 && wr == 0) {  // group leader: sum the group's partials, t = op(Z) p
+      for (int k = lane; k < K; k += 32) {
+        double acc = 0.0;
+        for (int w = 0; w < wpn; ++w) acc += sh.wpart[(warp + w) * sh.K + k];
+        sh.pv[g * sh.K + k] = acc;
+      }
+      __syncwarp();
+      const double* Z = (zsel ? Fd->Zi : Fd->Zf) + (size_t)nid * ld2 * ld2;
+      for (int k = lane; k < K; k += 32) {
+        const int a = k / nrhs, j = k % nrhs;
+        double acc = 0.0;
+        for (int b = 0; b < 2 * r; ++b) acc += (zt ? Z[b * ld2 + a] : Z[a * ld2 + b]) * sh.pv[g * sh.K + b * nrhs + j];
+        sh.tv[g * sh.K + k] = acc;
+      }
+    }
+    __syncthreads();
+    if (r > 0) {
+      for (int p = s + wr * 32 + lane; p < e; p += wpn * 32) {
+        const int off = p < h ? 0 : r;
+        double acc0 = 0.0, acc1 = 0.0;
+        for (int a = 0; a < r; ++a) {
+          const double q = to_d(Qb[(size_t)a * n + p]);
+          acc0 += q * sh.tv[g * sh.K + (off + a) * nrhs];
+          if (nrhs > 1) acc1 += q * sh.tv[g * sh.K + (off + a) * nrhs + 1];
+        }
+        vs[p - S] += acc0;
+        if (nrhs > 1) vs[rows + p - S] += acc1;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One level < ls: node i = c >> (ls - l) spans 2^(ls - l) CTAs; c's rows lie in
+// one child (side).  Returns false if the grid barrier gave up.
+template <typename T>
+__device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, int c, double* vs, int rows, int S,
+                                int E, int nrhs, int zsel, int zt, double* __restrict__ part, int buf,
+                                unsigned int* bar, unsigned int& phase, int* abort_flag, FsShared& sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int C = gridDim.x;
+  const int cap = Fd->cap, ld2 = 2 * cap;
+  const int64_t n = Fd->n;
+  const int span = ls - l, i = c >> span, side = (c >> (span - 1)) & 1;
+  const int nid = node_id(l, i);
+  const int r = Fd->rank[nid];
+  const T* Qb = (const T*)Fd->Q + (size_t)l * cap * n;
+  double* mine = part + ((size_t)buf * C + c) * FS_K;
+  // partial projection of this CTA's rows onto its side's r columns
+  for (int a = warp; a < r; a += FS_WARPS) {
+    const T* Qc = Qb + (size_t)a * n;
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int p = S + lane; p < E; p += 32) {
+      const double q = to_d(Qc[p]);
+      acc0 += q * vs[p - S];
+      if (nrhs > 1) acc1 += q * vs[rows + p - S];
+    }
+    acc0 = warp_sum(acc0);
+    acc1 = warp_sum(acc1);
+    if (lane == 0) {
+      __stcg(mine + a * nrhs, acc0);
+      if (nrhs > 1) __stcg(mine + a * nrhs + 1, acc1);
     }
   }
+  ++phase;
+  if (!group_barrier(bar, (unsigned)C * phase, Fd->status, abort_flag)) return false;
+  if (r == 0) return true;
+  // p over the node: the left half of its CTAs for rows of the left child, the
+  // right half for the right child, summed in a fixed order
+  const int K = 2 * r * nrhs, half = 1 << (span - 1), c0 = i << span;
+  const int nch = blockDim.x / K;
+  double* red = sh.wpart;
+  if ((int)threadIdx.x < nch * K) {
+    const int k = threadIdx.x % K, ch = threadIdx.x / K;
+    const int sd = (k / nrhs) >= r ? 1 : 0, kk = k - sd * r * nrhs;
+    const double* src = part + ((size_t)buf * C + c0 + sd * half) * FS_K + kk;
+    double acc = 0.0;
+    for (int q = ch; q < half; q += nch) acc += __ldcg(src + (size_t)q * FS_K);
+    red[ch * K + k] = acc;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < K) {
+    double acc = 0.0;
+    for (int ch = 0; ch < nch; ++ch) acc += red[ch * K + threadIdx.x];
+    sh.pv[threadIdx.x] = acc;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < K) {
+    const int a = threadIdx.x / nrhs, j = threadIdx.x % nrhs;
+    const double* Z = (zsel ? Fd->Zi : Fd->Zf) + (size_t)nid * ld2 * ld2;
+    double acc = 0.0;
+    for (int b = 0; b < 2 * r; ++b) acc += (zt ? Z[b * ld2 + a] : Z[a * ld2 + b]) * sh.pv[b * nrhs + j];
+    sh.tv[threadIdx.x] = acc;
+  }
+  __syncthreads();
+  const int off = side * r;
+  for (int p = S + (int)threadIdx.x; p < E; p += blockDim.x) {
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int a = 0; a < r; ++a) {
+      const double q = to_d(Qb[(size_t)a * n + p]);
+      acc0 += q * sh.tv[(off + a) * nrhs];
+      if (nrhs > 1) acc1 += q * sh.tv[(off + a) * nrhs + 1];
+    }
+    vs[p - S] += acc0;
+    if (nrhs > 1) vs[rows + p - S] += acc1;
+  }
+  __syncthreads();
+  return true;
+}
+
+template <typename T>
+__device__ void fs_leaves(const FactDesc* __restrict__ Fd, int ls, int c, double* vs, int rows, int S, int nrhs,
+                          int mode) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int L = Fd->L, Bm = Fd->Bm;
+  const int nl = 1 << (L - ls), first = c << (L - ls);
+  for (int q = warp; q < nl; q += FS_WARPS) {
+    const int leaf = first + q;
+    const int s = Fd->bnd[bnd_off(L) + leaf], e = Fd->bnd[bnd_off(L) + leaf + 1];
+    const T* Lm = (const T*)Fd->Lleaf + (size_t)leaf * Bm * Bm;
+    for (int j = 0; j < nrhs; ++j) leaf_warp_apply<T>(Lm, Bm, e - s, vs + (size_t)j * rows + (s - S), mode, lane);
+  }
+  __syncthreads();
+}
+
+// mode 0: v <- W v, 1: W^-1 v, 2: W^T v, 3: W^-T v.  Dynamic shared memory:
+// nrhs * rows doubles (rows >= the longest level-ls node), then the FsShared
+// arrays.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_fused(const FactDesc* __restrict__ Fd, double* __restrict__ v, int nrhs,
+                                                     int mode, int ls, int rows, double* __restrict__ part,
+                                                     unsigned int* __restrict__ bar, int* __restrict__ abort_flag) {
+  extern __shared__ double vs[];
+  FsShared sh;
+  sh.K = max(2 * Fd->cap * SW_RHS_MAX, 32);  // FS_WARPS * K >= blockDim: the reduction scratch
+  sh.wpart = vs + (size_t)rows * nrhs;
+  sh.pv = sh.wpart + FS_WARPS * sh.K;
+  sh.tv = sh.pv + FS_WARPS * sh.K;
+  const int c = blockIdx.x;
+  const int L = Fd->L;
+  const int64_t n = Fd->n;
+  const int S = Fd->bnd[bnd_off(ls) + c], E = Fd->bnd[bnd_off(ls) + c + 1];
+  for (int j = 0; j < nrhs; ++j)
+    for (int p = threadIdx.x; p < E - S; p += blockDim.x) vs[(size_t)j * rows + p] = v[(size_t)j * n + S + p];
+  __syncthreads();
+  const int zsel = (mode == 1 || mode == 3) ? 1 : 0, zt = (mode == 2 || mode == 3) ? 1 : 0;
+  unsigned int phase = 0;
+  bool ok = true;
+  if (mode == 1 || mode == 2) {  // leaves first, then the levels upward
+    fs_leaves<T>(Fd, ls, c, vs, rows, S, nrhs, mode);
+    for (int l = L - 1; l >= ls; --l) fs_local_level<T>(Fd, l, ls, c, vs, rows, S, nrhs, zsel, zt, sh);
+    for (int l = ls - 1; l >= 0 && ok; --l)
+      ok = fs_global_level<T>(Fd, l, ls, c, vs, rows, S, E, nrhs, zsel, zt, part, l & 1, bar, phase, abort_flag, sh);
+  } else {  // the levels downward, then the leaves
+    for (int l = 0; l < ls && ok; ++l)
+      ok = fs_global_level<T>(Fd, l, ls, c, vs, rows, S, E, nrhs, zsel, zt, part, l & 1, bar, phase, abort_flag, sh);
+    if (ok) {
+      for (int l = ls; l < L; ++l) fs_local_level<T>(Fd, l, ls, c, vs, rows, S, nrhs, zsel, zt, sh);
+      fs_leaves<T>(Fd, ls, c, vs, rows, S, nrhs, mode);
+    }
+  }
+  if (!ok) return;  // the status word carries TIMEOUT; v is left as it was
+  for (int j = 0; j < nrhs; ++j)
+    for (int p = threadIdx.x; p < E - S; p += blockDim.x) v[(size_t)j * n + S + p] = vs[(size_t)j * rows + p];
+}
+
+size_t sweep_fused_smem(int rows, int nrhs, int cap) {
+  return sizeof(double) * ((size_t)rows * nrhs + 3 * FS_WARPS * std::max(2 * cap * SW_RHS_MAX, 32));
+}
+
+int sweep_fused_coresident(int prec, int rows, int cap) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = sweep_fused_smem(rows, SW_RHS_MAX, cap);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem > (size_t)optin) return 0;
+  cudaError_t e;
+  if (prec) {
+    cudaFuncSetAttribute(k_sweep_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_fused<float>, 256, smem);
+  } else {
+    cudaFuncSetAttribute(k_sweep_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_fused<double>, 256, smem);
+  }
+  cudaGetLastError();
+  return e == cudaSuccess ? sms * per_sm : 0;
+}
+
+cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, int cap, double* v, int nrhs,
+                               int mode, double* part, unsigned int* bar, int* abort_flag, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1u << ls);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = sweep_fused_smem(rows, nrhs, cap);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (prec) {
+    cudaFuncSetAttribute(k_sweep_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sweep_fused_smem(rows, SW_RHS_MAX, cap));
+    return cudaLaunchKernelEx(&cfg, k_sweep_fused<float>, Fd, v, nrhs, mode, ls, rows, part, bar, abort_flag);
+  }
+  cudaFuncSetAttribute(k_sweep_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sweep_fused_smem(rows, SW_RHS_MAX, cap));
+  return cudaLaunchKernelEx(&cfg, k_sweep_fused<double>, Fd, v, nrhs, mode, ls, rows, part, bar, abort_flag);
 }
 
 // ---------------------------------------------------------------------------

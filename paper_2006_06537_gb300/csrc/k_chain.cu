@@ -7,6 +7,8 @@
 // On acceptance the current and proposed H-matrix / factor descriptors are
 // swapped in device memory, so the captured graph keeps reading "current"
 // from the same address.
+#include <algorithm>
+
 #include "fifa_chain.h"
 #include "fifa_common.cuh"
 #include "fifa_rng.cuh"
@@ -71,6 +73,7 @@ __global__ void k_chain_mh(ChainDev* __restrict__ c, HmatDesc* __restrict__ Hc, 
   const int acc = (log(u) < la) ? 1 : 0;
   c->status |= *Fm->status | (*Fc->status & ~FIFA_DEV_RANK_CAP);
   c->accept = acc;
+  c->n_accept += (uint64_t)acc;
   c->log_alpha = la;
   if (acc) {
     swap_desc(Hc, Hp);
@@ -122,5 +125,80 @@ cudaError_t launch_chain_mh(ChainDev* c, HmatDesc* Hc, HmatDesc* Hp, FactDesc* F
 }
 cudaError_t launch_ratio_sqrt(const double* num, const double* den, double* out, cudaStream_t st) {
   k_ratio_sqrt<<<1, 32, 0, st>>>(num, den, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Additive model of d one-dimensional blocks (Sec. 4.2): F is n x d in the
+// original point order, column k at F + k n; perm_k sorts x_k (stable).
+// ---------------------------------------------------------------------------
+
+// Partial residual of block k in x_k-sorted order:
+//   out[i] = y[p] - F[p, j0] - F[p, j1] - ...  (j != k, ascending), p = perm_k[i]
+__global__ void k_add_gather(const double* __restrict__ y, const double* __restrict__ F,
+                             const int64_t* __restrict__ perm, int64_t n, int d, int k, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = perm[i];
+    double r = y[p];
+    for (int j = 0; j < d; ++j)
+      if (j != k) r = __dsub_rn(r, F[(int64_t)j * n + p]);
+    out[i] = r;
+  }
+}
+
+// F[perm_k[i], k] = f_sorted[i]
+__global__ void k_add_scatter(const double* __restrict__ fs, const int64_t* __restrict__ perm, int64_t n,
+                              double* __restrict__ Fk) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    Fk[perm[i]] = fs[i];
+}
+
+// Full residual minus the last block: out = y - F[:, 0] - ... - F[:, d-2], so
+// that ||out - F[:, d-1]||^2 is the model's residual sum of squares.
+__global__ void k_add_residual(const double* __restrict__ y, const double* __restrict__ F, int64_t n, int d,
+                               double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double r = y[i];
+    for (int j = 0; j + 1 < d; ++j) r = __dsub_rn(r, F[(int64_t)j * n + i]);
+    out[i] = r;
+  }
+}
+
+// Shared sigma2 | y, F_1..F_d, drawn from the stream of g (chain id d), copied
+// into every block's state; appends (iteration, sigma2, rss) to g's trace.
+__global__ void k_add_sigma2(ChainDev* __restrict__ g, ChainDev* const* __restrict__ blocks, int d) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double shape = g->a_sigma2 + 0.5 * (double)g->n;
+  const double scale = g->b_sigma2 + 0.5 * g->rss;
+  const double gm = gamma_mt(shape, g->seed, 2u, g->iter, g->chain_id);
+  const double s2 = scale / gm;
+  g->sigma2 = s2;
+  for (int k = 0; k < d; ++k) blocks[k]->sigma2 = s2;
+  if (g->trace && g->trace_cap > 0) {
+    double* row = g->trace + (size_t)(g->iter % (uint64_t)g->trace_cap) * 3;
+    row[0] = (double)g->iter;
+    row[1] = s2;
+    row[2] = g->rss;
+  }
+  g->iter += 1;
+}
+
+static inline int add_grid(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 8); }
+
+cudaError_t launch_add_gather(const double* y, const double* F, const int64_t* perm, int64_t n, int d, int k,
+                              double* out, cudaStream_t st) {
+  k_add_gather<<<add_grid(n), 256, 0, st>>>(y, F, perm, n, d, k, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_add_scatter(const double* fs, const int64_t* perm, int64_t n, double* Fk, cudaStream_t st) {
+  k_add_scatter<<<add_grid(n), 256, 0, st>>>(fs, perm, n, Fk);
+  return cudaGetLastError();
+}
+cudaError_t launch_add_residual(const double* y, const double* F, int64_t n, int d, double* out, cudaStream_t st) {
+  k_add_residual<<<add_grid(n), 256, 0, st>>>(y, F, n, d, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_add_sigma2(ChainDev* g, ChainDev* const* blocks, int d, cudaStream_t st) {
+  k_add_sigma2<<<1, 32, 0, st>>>(g, blocks, d);
   return cudaGetLastError();
 }

@@ -13,6 +13,7 @@
 //                  I + Q Zi Q^T applied to every ancestor basis on the node's rows.
 //                  Small nodes: one CTA each.  Large nodes: G CTAs split the rows
 //                  and exchange partial sums through bounded-spin group barriers.
+#include <atomic>
 #include "fifa_common.cuh"
 #include "fifa_launch.h"
 
@@ -669,11 +670,13 @@ size_t level_smem(int cap) {
 }
 
 static int smem_optin() {
-  static int v = -1;
+  static std::atomic<int> cached{-1};  // several host threads may launch at once
+  int v = cached.load(std::memory_order_relaxed);
   if (v < 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) v = 48 * 1024;
+    cached.store(v, std::memory_order_relaxed);
   }
   return v;
 }

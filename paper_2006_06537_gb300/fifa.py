@@ -31,12 +31,33 @@ class fifa_hyper(C.Structure):
 
 class fifa_opts(C.Structure):
     _fields_ = [("leaf_size", C.c_int), ("aca_tol", C.c_double), ("rank_cap", C.c_int), ("prec", C.c_int),
-                ("refine_tol", C.c_double), ("refine_max", C.c_int)]
+                ("refine_tol", C.c_double), ("refine_max", C.c_int), ("independent_ctas", C.c_int)]
 
 
 class fifa_prior(C.Structure):
     _fields_ = [("a_tau2", C.c_double), ("b_tau2", C.c_double), ("a_sigma2", C.c_double), ("b_sigma2", C.c_double),
                 ("logrho_mu", C.c_double), ("logrho_sd", C.c_double), ("prop_sd", C.c_double)]
+
+
+class fifa_server_opts(C.Structure):
+    _fields_ = [("opts", fifa_opts), ("hbm_budget", C.c_size_t), ("slots", C.c_int), ("wide_min_n", C.c_int64)]
+
+
+class fifa_request(C.Structure):
+    _fields_ = [("x_host", C.c_void_p), ("y_host", C.c_void_p), ("n", C.c_int64), ("init", fifa_hyper),
+                ("prior", fifa_prior), ("seed", C.c_uint64), ("chain_id", C.c_uint64), ("iters", C.c_int),
+                ("burn", C.c_int), ("ndraws", C.c_int)]
+
+
+class fifa_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
+                ("last", fifa_hyper), ("accept_rate", C.c_double), ("bytes", C.c_size_t)]
+
+
+class fifa_server_counters(C.Structure):
+    _fields_ = [("now", C.c_double), ("queued", C.c_int), ("in_flight", C.c_int), ("peak_in_flight", C.c_int),
+                ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t), ("completed", C.c_uint64),
+                ("iterations_done", C.c_uint64)]
 
 
 class FifaError(RuntimeError):
@@ -75,6 +96,18 @@ def lib():
         "fifa_gibbs_step": (C.c_int, [_P, _P, C.c_int, _P]),
         "fifa_chain_get": (C.c_int, [_P, _P, _P, _P, C.POINTER(fifa_hyper)]),
         "fifa_chain_kernel_nodes": (C.c_int, [_P, C.POINTER(C.c_int)]),
+        "fifa_chain_bytes": (C.c_int, [C.POINTER(fifa_opts), C.c_int64, C.POINTER(C.c_size_t)]),
+        "fifa_server_create": (C.c_int, [C.POINTER(fifa_server_opts), C.POINTER(_P)]),
+        "fifa_server_submit": (C.c_int, [_P, C.POINTER(fifa_request), C.POINTER(C.c_uint64)]),
+        "fifa_server_wait": (C.c_int, [_P, C.c_uint64, _P, _P, C.POINTER(fifa_result)]),
+        "fifa_server_stats": (C.c_int, [_P, C.POINTER(fifa_server_counters)]),
+        "fifa_server_destroy": (None, [_P]),
+        "fifa_additive_create": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, C.POINTER(fifa_hyper),
+                                           C.POINTER(fifa_prior), C.c_uint64, C.POINTER(_P)]),
+        "fifa_additive_sweep": (C.c_int, [_P, _P, C.c_int, _P]),
+        "fifa_additive_get": (C.c_int, [_P, _P, _P, C.POINTER(C.c_double), C.POINTER(fifa_hyper)]),
+        "fifa_additive_kernel_nodes": (C.c_int, [_P, C.POINTER(C.c_int)]),
+        "fifa_destroy_additive": (None, [_P, _P]),
         "fifa_hmat_dims": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "fifa_hmat_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
@@ -197,6 +230,88 @@ def fifa_chain_kernel_nodes(chain):
     return k.value
 
 
+FIFA_ADDITIVE_MAX_D = 16
+
+
+def fifa_chain_bytes(opts: fifa_opts, n: int) -> int:
+    b = C.c_size_t()
+    _check(lib().fifa_chain_bytes(C.byref(opts), C.c_int64(n), C.byref(b)), "fifa_chain_bytes")
+    return b.value
+
+
+def fifa_additive_trace_fields(d: int) -> int:
+    return 5 + 3 * d
+
+
+def fifa_additive_create(ctx, X_cols, y, n, d, init: fifa_hyper, prior: fifa_prior, seed: int):
+    """X_cols: d x n device doubles (coordinate k of point i at [k, i])."""
+    h = C.c_void_p()
+    _check(lib().fifa_additive_create(ctx, _ptr(X_cols), _ptr(y), C.c_int64(n), C.c_int(d), C.byref(init),
+                                      C.byref(prior), C.c_uint64(seed), C.byref(h)), "fifa_additive_create", ctx=ctx)
+    return h
+
+
+def fifa_additive_sweep(ctx, model, sweeps: int, trace: np.ndarray | None = None, allow=()):
+    tp = trace.ctypes.data_as(C.c_void_p) if trace is not None else None
+    return _check(lib().fifa_additive_sweep(ctx, model, int(sweeps), tp), "fifa_additive_sweep", allow, ctx=ctx)
+
+
+def fifa_additive_get(ctx, model, d: int, F=None):
+    """Returns (sigma2, [fifa_hyper] * d); F (d x n device doubles) receives f_1..f_d."""
+    s2 = C.c_double()
+    hs = (fifa_hyper * d)()
+    _check(lib().fifa_additive_get(ctx, model, _ptr(F), C.byref(s2), hs), "fifa_additive_get", ctx=ctx)
+    return s2.value, list(hs)
+
+
+def fifa_additive_kernel_nodes(model):
+    k = C.c_int()
+    _check(lib().fifa_additive_kernel_nodes(model, C.byref(k)), "fifa_additive_kernel_nodes")
+    return k.value
+
+
+def fifa_destroy_additive(ctx, model):
+    lib().fifa_destroy_additive(ctx, model)
+
+
+def fifa_server_create(opts: fifa_opts, hbm_budget: int, slots: int, wide_min_n: int = 0):
+    h = C.c_void_p()
+    so = fifa_server_opts(opts, C.c_size_t(int(hbm_budget)), int(slots), int(wide_min_n))
+    _check(lib().fifa_server_create(C.byref(so), C.byref(h)), "fifa_server_create")
+    return h
+
+
+def fifa_server_submit(server, x: np.ndarray, y: np.ndarray, init: fifa_hyper, prior: fifa_prior, seed: int,
+                       chain_id: int, iters: int, burn: int, ndraws: int) -> int:
+    """x, y: host float64 arrays (copied by the call)."""
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    r = fifa_request(x.ctypes.data, y.ctypes.data, len(x), init, prior, int(seed), int(chain_id), int(iters),
+                     int(burn), int(ndraws))
+    rid = C.c_uint64()
+    _check(lib().fifa_server_submit(server, C.byref(r), C.byref(rid)), "fifa_server_submit")
+    return rid.value
+
+
+def fifa_server_wait(server, rid: int, mean: np.ndarray | None = None, draws: np.ndarray | None = None, allow=()):
+    """Blocks until request rid is done; returns (status, fifa_result)."""
+    res = fifa_result()
+    mp = mean.ctypes.data_as(C.c_void_p) if mean is not None else None
+    dp = draws.ctypes.data_as(C.c_void_p) if draws is not None else None
+    st = _check(lib().fifa_server_wait(server, C.c_uint64(rid), mp, dp, C.byref(res)), "fifa_server_wait", allow)
+    return st, res
+
+
+def fifa_server_stats(server) -> fifa_server_counters:
+    c = fifa_server_counters()
+    _check(lib().fifa_server_stats(server, C.byref(c)), "fifa_server_stats")
+    return c
+
+
+def fifa_server_destroy(server):
+    lib().fifa_server_destroy(server)
+
+
 def fifa_hmat_dims(H):
     n, L, nl, bm, cap = C.c_int64(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
     _check(lib().fifa_hmat_dims(H, C.byref(n), C.byref(L), C.byref(nl), C.byref(bm), C.byref(cap)), "fifa_hmat_dims")
@@ -265,7 +380,7 @@ def fifa_philox(ctx, seed, ctr, out, count):
 # ---------------------------------------------------------------------------
 class Context:
     def __init__(self, leaf_size=64, aca_tol=1e-12, rank_cap=32, prec=FIFA_FP64, refine_tol=1e-12, refine_max=3,
-                 arena_bytes=1 << 30, device="cuda", stream=None):
+                 arena_bytes=1 << 30, device="cuda", stream=None, independent_ctas=0):
         import torch
 
         self.torch = torch
@@ -273,7 +388,7 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.device)
         self.opts = fifa_opts(int(leaf_size), float(aca_tol), int(rank_cap), int(prec), float(refine_tol),
-                              int(refine_max))
+                              int(refine_max), int(independent_ctas))
         self.h = fifa_create(self.opts, self.stream.cuda_stream, self.arena.data_ptr(), int(arena_bytes))
 
     def close(self):

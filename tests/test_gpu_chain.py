@@ -34,14 +34,18 @@ def _prior():
 
 
 def _gpu_chain(x, y, nugget, prec=fifa.FIFA_FP64, sigma2=None, tau2=None):
-    ctx = fifa.Context(leaf_size=B, aca_tol=EPS, rank_cap=32, prec=prec, refine_max=3, arena_bytes=1 << 30)
+    # a stream of its own, so the iteration runs as a captured graph (the
+    # legacy default stream cannot be captured)
+    ctx = fifa.Context(leaf_size=B, aca_tol=EPS, rank_cap=32, prec=prec, refine_max=3, arena_bytes=1 << 30,
+                       stream=torch.cuda.Stream())
     vy = float(np.var(y))
     s2 = 0.5 * vy if sigma2 is None else sigma2
     t2 = vy if tau2 is None else tau2
     p = _prior()
     pr = fifa.fifa_prior(p.a_tau2, p.b_tau2, p.a_sigma2, p.b_sigma2, p.logrho_mu, p.logrho_sd, p.prop_sd)
-    ch = fifa.fifa_chain_create(ctx.h, dev(x, torch), dev(y, torch), len(x), fifa.fifa_hyper(0, t2, RHO0, s2, nugget),
-                                pr, 0, 0)
+    xd, yd = dev(x, torch), dev(y, torch)
+    torch.cuda.synchronize()
+    ch = fifa.fifa_chain_create(ctx.h, xd, yd, len(x), fifa.fifa_hyper(0, t2, RHO0, s2, nugget), pr, 0, 0)
     return ctx, ch
 
 
@@ -82,6 +86,7 @@ def test_chain_matches_oracle(nugget):
     assert hyp.rho == pytest.approx(math.exp(st.eta), rel=1e-12)
     assert rel(host(mean), st.mean) <= 1e-8
     assert rel(host(f), st.f) <= 100 * tol
+    assert fifa.fifa_chain_kernel_nodes(ch) > 0  # the graph path ran
 
 
 def test_mixed_chain_refines_to_fp64_tolerance():

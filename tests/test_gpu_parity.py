@@ -29,9 +29,9 @@ build_lib()
 from paper_2006_06537_gb300 import fifa  # noqa: E402
 
 
-def make_ctx(B=64, eps=1e-12, cap=32, prec=fifa.FIFA_FP64, refine_max=3):
+def make_ctx(B=64, eps=1e-12, cap=32, prec=fifa.FIFA_FP64, refine_max=3, indep=0):
     return fifa.Context(leaf_size=B, aca_tol=eps, rank_cap=cap, prec=prec, refine_max=refine_max,
-                        arena_bytes=1 << 30)
+                        arena_bytes=1 << 30, independent_ctas=indep)
 
 
 def test_det_exp_bitwise():
@@ -105,9 +105,9 @@ def test_assembly_bit_exact(case):
         assert np.array_equal(ex["leaves"][li, :m, :m].T.copy().view(np.uint64), D.view(np.uint64))
 
 
-def _factor_setup(n, B, kind, rho, nug, eps, s_shift=None, prec=fifa.FIFA_FP64, data="sine"):
+def _factor_setup(n, B, kind, rho, nug, eps, s_shift=None, prec=fifa.FIFA_FP64, data="sine", indep=0):
     x, y = _data(n, data)
-    ctx = make_ctx(B=B, eps=eps, prec=prec, refine_max=4)
+    ctx = make_ctx(B=B, eps=eps, prec=prec, refine_max=4, indep=indep)
     xd = dev(x, torch)
     H = fifa.fifa_assemble(ctx.h, xd, n, fifa.fifa_hyper(kind, 1.0, rho, 1.0, nug))
     Ho = oracle_hmat(x, B, kind, rho, nug, eps, 32)
@@ -129,10 +129,11 @@ FACTOR_CASES = [
 ]
 
 
+@pytest.mark.parametrize("indep", [0, 1])  # 0: grouped CTAs and the fused sweep; 1: independent CTAs, per-level sweeps
 @pytest.mark.parametrize("case", FACTOR_CASES)
-def test_factor_apply_solve_parity(case):
+def test_factor_apply_solve_parity(case, indep):
     n, B, kind, rho, nug, eps, sh, data = case
-    ctx, x, y, xd, H, Ho, A, Ao, F, Fo = _factor_setup(n, B, kind, rho, nug, eps, sh, data=data)
+    ctx, x, y, xd, H, Ho, A, Ao, F, Fo = _factor_setup(n, B, kind, rho, nug, eps, sh, data=data, indep=indep)
     ld, code = fifa.fifa_logdet(ctx.h, F)
     assert code == fifa.FIFA_OK
     # logdet: both sides backward stable; bound 1e-10 relative plus n * u * cond(W)^2 slack
@@ -149,6 +150,10 @@ def test_factor_apply_solve_parity(case):
             torch.cuda.synchronize()
             ref = factor.apply_W(Fo, v.T, trans=bool(trans), inverse=bool(inv)).T
             assert rel(host(out), ref) <= wtol, (trans, inv, rel(host(out), ref), wtol)
+            out1 = torch.empty(n, dtype=torch.float64, device="cuda")  # one right-hand side
+            fifa.fifa_apply_W(ctx.h, F, trans, inv, vd[1], out1, 1)
+            torch.cuda.synchronize()
+            assert rel(host(out1), ref[1]) <= wtol
     fifa.fifa_solve(ctx.h, F, vd, out, 2)
     torch.cuda.synchronize()
     ref = factor.solve(Fo, v.T).T
