@@ -273,7 +273,8 @@ size_t hmat_bytes(const Plan* P, int cap) {
 size_t fact_bytes(const Plan* P, int cap, int prec) {
   const size_t nn = std::max(1, P->nnodes);
   const size_t esz = prec ? sizeof(float) : sizeof(double);
-  return arena_round(esz * (size_t)P->nleaf * P->Bm * P->Bm) + arena_round(esz * (size_t)std::max(1, P->L) * cap * P->n) +
+  return arena_round(esz * (size_t)P->nleaf * P->Bm * P->Bm) + arena_round(sizeof(double) * (size_t)P->nleaf * P->Bm) +
+         arena_round(esz * (size_t)std::max(1, P->L) * cap * P->n) +
          2 * arena_round(sizeof(double) * nn * 4 * cap * cap) + arena_round(sizeof(int) * nn) +
          arena_round(sizeof(double) * (P->nleaf + nn)) + arena_round(sizeof(double)) + arena_round(sizeof(int)) +
          arena_round(sizeof(FactDesc));
@@ -576,6 +577,7 @@ fifa_status fact_alloc(fifa_ctx* ctx, Plan* P, int prec, fifa_fact** out) {
   d.prec = prec;
   d.bnd = P->bnd_dev;
   d.Lleaf = ctx->arena.alloc(esz * (size_t)P->nleaf * P->Bm * P->Bm);
+  d.Ldinv = (double*)ctx->arena.alloc(sizeof(double) * (size_t)P->nleaf * P->Bm);
   d.Q = ctx->arena.alloc(esz * (size_t)std::max(1, P->L) * cap * P->n);
   d.Zf = (double*)ctx->arena.alloc(sizeof(double) * nn * 4 * cap * cap);
   d.Zi = (double*)ctx->arena.alloc(sizeof(double) * nn * 4 * cap * cap);
@@ -584,7 +586,7 @@ fifa_status fact_alloc(fifa_ctx* ctx, Plan* P, int prec, fifa_fact** out) {
   d.logdet = (double*)ctx->arena.alloc(sizeof(double));
   d.status = (int*)ctx->arena.alloc(sizeof(int));
   F->dev = (FactDesc*)ctx->arena.alloc(sizeof(FactDesc));
-  if (!d.Lleaf || !d.Q || !d.Zf || !d.Zi || !d.rank || !d.ld_parts || !d.logdet || !d.status || !F->dev) {
+  if (!d.Lleaf || !d.Ldinv || !d.Q || !d.Zf || !d.Zi || !d.rank || !d.ld_parts || !d.logdet || !d.status || !F->dev) {
     fifa_destroy_fact(ctx, F);
     return FIFA_ERR_OOM;
   }
@@ -638,6 +640,7 @@ extern "C" void fifa_destroy_fact(fifa_ctx* ctx, fifa_fact* F) {
   cudaStreamSynchronize(ctx->stream);
   FactDesc& d = F->host;
   ctx->arena.release(d.Lleaf);
+  ctx->arena.release(d.Ldinv);
   ctx->arena.release(d.Q);
   ctx->arena.release(d.Zf);
   ctx->arena.release(d.Zi);

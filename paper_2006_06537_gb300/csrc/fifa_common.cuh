@@ -52,6 +52,7 @@ struct FactDesc {
   int L, nleaf, Bm, cap, prec;  // prec: 0 = f64 storage, 1 = f32 storage
   const int* bnd;
   void* Lleaf;                  // nleaf x Bm x Bm lower Cholesky factors
+  double* Ldinv;                // nleaf x Bm reciprocals of their diagonals
   void* Q;                      // L x cap x n orthonormal bases
   double* Zf;                   // nnodes x (2cap)^2 : L_S - I
   double* Zi;                   // nnodes x (2cap)^2 : L_S^-1 - I

@@ -103,9 +103,9 @@ __device__ __forceinline__ double reg_sel(const double (&a)[N], int q) {
 // memory).  mode 0: v <- L v, 1: v <- L^-1 v, 2: v <- L^T v, 3: v <- L^-T v.
 // L column-major (L[i][k] at k*Bm + i).
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void leaf_warp_apply(const T* __restrict__ Lm, int Bm, int m, double* vj, int mode, int lane) {
-  constexpr int RPL = FIFA_LEAF_MAX / 32;  // rows per lane
+template <typename T, int RPL>  // RPL: rows per lane, 32 RPL >= m; dinv: reciprocal pivots
+__device__ __forceinline__ void leaf_warp_apply_r(const T* __restrict__ Lm, const double* __restrict__ dinv, int Bm,
+                                                  int m, double* vj, int mode, int lane) {
   double x[RPL], o[RPL];
 #pragma unroll
   for (int q = 0; q < RPL; ++q) {
@@ -131,7 +131,7 @@ __device__ __forceinline__ void leaf_warp_apply(const T* __restrict__ Lm, int Bm
 #pragma unroll
       for (int q = 0; q < RPL; ++q)
         if (q == qk) ok = o[q];
-      double xk = __shfl_sync(0xffffffffu, ok, k & 31) / to_d(Lm[(size_t)k * Bm + k]);
+      double xk = __shfl_sync(0xffffffffu, ok, k & 31) * dinv[k];
 #pragma unroll
       for (int q = 0; q < RPL; ++q) {
         int i = lane + 32 * q;
@@ -163,8 +163,7 @@ __device__ __forceinline__ void leaf_warp_apply(const T* __restrict__ Lm, int Bm
       }
       part = warp_sum(part);
       part = __shfl_sync(0xffffffffu, part, 0);
-      const double xj = (__shfl_sync(0xffffffffu, reg_sel<RPL>(x, jj >> 5), jj & 31) - part) /
-                        to_d(Lm[(size_t)jj * Bm + jj]);
+      const double xj = (__shfl_sync(0xffffffffu, reg_sel<RPL>(x, jj >> 5), jj & 31) - part) * dinv[jj];
 #pragma unroll
       for (int q = 0; q < RPL; ++q)
         if (lane + 32 * q == jj) o[q] = xj;
@@ -177,6 +176,14 @@ __device__ __forceinline__ void leaf_warp_apply(const T* __restrict__ Lm, int Bm
   }
 }
 
+template <typename T>
+__device__ __forceinline__ void leaf_warp_apply(const T* __restrict__ Lm, const double* __restrict__ dinv, int Bm, int m,
+                                                double* vj, int mode, int lane) {
+  if (Bm <= 32) leaf_warp_apply_r<T, 1>(Lm, dinv, Bm, m, vj, mode, lane);
+  else if (Bm <= 64) leaf_warp_apply_r<T, 2>(Lm, dinv, Bm, m, vj, mode, lane);
+  else leaf_warp_apply_r<T, FIFA_LEAF_MAX / 32>(Lm, dinv, Bm, m, vj, mode, lane);
+}
+
 // Leaf step over all leaves: one warp per leaf.
 template <typename T>
 __global__ void __launch_bounds__(256) k_sweep_leaf(const FactDesc* __restrict__ Fd, double* __restrict__ v, int nrhs, int mode) {
@@ -187,7 +194,8 @@ __global__ void __launch_bounds__(256) k_sweep_leaf(const FactDesc* __restrict__
   const int64_t n = Fd->n;
   const int s = Fd->bnd[bnd_off(L) + warp], e = Fd->bnd[bnd_off(L) + warp + 1];
   const T* Lm = (const T*)Fd->Lleaf + (size_t)warp * Bm * Bm;
-  for (int j = 0; j < nrhs; ++j) leaf_warp_apply<T>(Lm, Bm, e - s, v + (size_t)j * n + s, mode, lane);
+  const double* dinv = Fd->Ldinv + (size_t)warp * Bm;
+  for (int j = 0; j < nrhs; ++j) leaf_warp_apply<T>(Lm, dinv, Bm, e - s, v + (size_t)j * n + s, mode, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -243,7 +251,7 @@ __device__ void fs_local_level(const FactDesc* __restrict__ Fd, int l, int ls, i
           if (nrhs > 1) acc1 += q * vs[rows + p - S];
         }
         acc0 = warp_sum(acc0);
-        acc1 = warp_sum(acc1);
+        if (nrhs > 1) acc1 = warp_sum(acc1);
         if (lane == 0) {
           sh.wpart[warp * sh.K + (side * r + a) * nrhs] = acc0;
           if (nrhs > 1) sh.wpart[warp * sh.K + (side * r + a) * nrhs + 1] = acc1;
@@ -310,7 +318,7 @@ __device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, 
       if (nrhs > 1) acc1 += q * vs[rows + p - S];
     }
     acc0 = warp_sum(acc0);
-    acc1 = warp_sum(acc1);
+    if (nrhs > 1) acc1 = warp_sum(acc1);
     if (lane == 0) {
       __stcg(mine + a * nrhs, acc0);
       if (nrhs > 1) __stcg(mine + a * nrhs + 1, acc1);
@@ -372,7 +380,9 @@ __device__ void fs_leaves(const FactDesc* __restrict__ Fd, int ls, int c, double
     const int leaf = first + q;
     const int s = Fd->bnd[bnd_off(L) + leaf], e = Fd->bnd[bnd_off(L) + leaf + 1];
     const T* Lm = (const T*)Fd->Lleaf + (size_t)leaf * Bm * Bm;
-    for (int j = 0; j < nrhs; ++j) leaf_warp_apply<T>(Lm, Bm, e - s, vs + (size_t)j * rows + (s - S), mode, lane);
+    const double* dinv = Fd->Ldinv + (size_t)leaf * Bm;
+    for (int j = 0; j < nrhs; ++j)
+      leaf_warp_apply<T>(Lm, dinv, Bm, e - s, vs + (size_t)j * rows + (s - S), mode, lane);
   }
   __syncthreads();
 }

@@ -43,17 +43,21 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
     if (i == j) v = __dadd_rn(v, shf);
     A[j * ld + i] = v;
   }
+  // reciprocals of the pivots: one division per column, products elsewhere
+  __shared__ double rinv[FIFA_LEAF_MAX];
   if (threadIdx.x == 0) flag[0] = 0;
   __syncthreads();
   for (int k = 0; k < m; ++k) {
     if (threadIdx.x == 0) {
       double d = A[k * ld + k];
       if (!(d > 0.0)) { flag[0] = 1; d = 1.0; }
-      A[k * ld + k] = sqrt(d);
+      d = sqrt(d);
+      A[k * ld + k] = d;
+      rinv[k] = 1.0 / d;
     }
     __syncthreads();
-    const double dk = A[k * ld + k];
-    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[k * ld + i] /= dk;
+    const double dinv = rinv[k];
+    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[k * ld + i] *= dinv;
     __syncthreads();
     const int w = m - k - 1;
     for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
@@ -69,6 +73,7 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
     Fd->ld_parts[leaf] = lsum;
     if (flag[0]) atomicOr(Fd->status, FIFA_DEV_NOT_SPD);
   }
+  for (int k = threadIdx.x; k < m; k += blockDim.x) Fd->Ldinv[(size_t)leaf * Bm + k] = rinv[k];
   T* Lout = (T*)Fd->Lleaf + (size_t)leaf * Bm * Bm;
   for (int t = threadIdx.x; t < Bm * Bm; t += blockDim.x) {
     int i = t % Bm, j = t / Bm;
@@ -108,7 +113,7 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
     }
     __syncthreads();
     for (int k = 0; k < m; ++k) {
-      if (threadIdx.x < w) X[threadIdx.x * ld + k] /= La[k * ld + k];
+      if (threadIdx.x < w) X[threadIdx.x * ld + k] *= (T)rinv[k];
       __syncthreads();
       const int rem = m - k - 1;
       for (int t = threadIdx.x; t < rem * w; t += blockDim.x) {
@@ -236,39 +241,52 @@ __device__ __forceinline__ void pair_decode(int o, int r, int& a, int& b) {
   b = a + rem;
 }
 
-// G[a*ldg + b] = sum over rows [a0, a1) of X[a][p] X[b][p], a, b < r.
+// Packed Gram matrix: Gp[q] = sum over rows [a0, a1) of X[a][p] X[b][p] for the
+// pair (a, b), a <= b < r, q = pair index (row-major upper triangle).  More
+// pairs than threads are taken in chunks of blockDim.x pairs.
 template <typename T>
 __device__ void gram_tiled(const T* __restrict__ Xb, int64_t n, int r, int a0, int a1, double* tile, double* part,
-                           double* G, int ldg) {
-  const int np = r * (r + 1) / 2;
-  const int ng = max(1, (int)blockDim.x / np);
+                           double* Gp) {
+  const int np_all = r * (r + 1) / 2;
   const int t = threadIdx.x;
-  const bool active = t < np * ng;
-  const int o = active ? t % np : 0, gidx = active ? t / np : 0;
-  int a = 0, b = 0;
-  pair_decode(o, r, a, b);
-  double acc = 0.0;
-  for (int p0 = a0; p0 < a1; p0 += LV_TR) {
-    const int tr = min(LV_TR, a1 - p0);
-    __syncthreads();
-    for (int i = t; i < r * tr; i += blockDim.x) {
-      const int c = i / tr, p = i % tr;
-      tile[c * LV_TRP + p] = to_d(Xb[(size_t)c * n + p0 + p]);
+  for (int q0 = 0; q0 < np_all; q0 += blockDim.x) {
+    const int np = min((int)blockDim.x, np_all - q0);
+    const int ng = max(1, (int)blockDim.x / np);
+    const bool active = t < np * ng;
+    const int o = active ? t % np : 0, gidx = active ? t / np : 0;
+    int a = 0, b = 0;
+    pair_decode(q0 + o, r, a, b);
+    double acc = 0.0;
+    for (int p0 = a0; p0 < a1; p0 += LV_TR) {
+      const int tr = min(LV_TR, a1 - p0);
+      __syncthreads();
+      for (int i = t; i < r * tr; i += blockDim.x) {
+        const int c = i / tr, p = i % tr;
+        tile[c * LV_TRP + p] = to_d(Xb[(size_t)c * n + p0 + p]);
+      }
+      __syncthreads();
+      if (active)
+        for (int p = gidx; p < tr; p += ng) acc += tile[a * LV_TRP + p] * tile[b * LV_TRP + p];
     }
     __syncthreads();
-    if (active)
-      for (int p = gidx; p < tr; p += ng) acc += tile[a * LV_TRP + p] * tile[b * LV_TRP + p];
+    if (active) part[gidx * np + o] = acc;
+    __syncthreads();
+    for (int q = t; q < np; q += blockDim.x) {
+      double v = 0.0;
+      for (int g = 0; g < ng; ++g) v += part[g * np + q];
+      Gp[q0 + q] = v;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  if (active) part[gidx * np + o] = acc;
-  __syncthreads();
-  for (int q = t; q < np; q += blockDim.x) {
-    double v = 0.0;
-    for (int g = 0; g < ng; ++g) v += part[g * np + q];
-    int qa, qb;
-    pair_decode(q, r, qa, qb);
-    G[qa * ldg + qb] = v;
-    G[qb * ldg + qa] = v;
+}
+
+// Unpack a packed Gram matrix into G (r x r, both triangles, ld ldg).
+__device__ void gram_unpack(const double* Gp, int r, double* G, int ldg) {
+  for (int q = threadIdx.x; q < r * (r + 1) / 2; q += blockDim.x) {
+    int a, b;
+    pair_decode(q, r, a, b);
+    G[a * ldg + b] = Gp[q];
+    G[b * ldg + a] = Gp[q];
   }
   __syncthreads();
 }
@@ -351,15 +369,19 @@ __global__ void __launch_bounds__(256, 2) k_level(const FactDesc* __restrict__ F
     const int a0 = side == 0 ? max(r0, s) : max(r0, h);
     const int a1 = side == 0 ? min(r1, h) : min(r1, e);
     // CholeskyQR2 of this side's basis: Gram, R1, Q1 = X R1^-1, Gram, R2, Q = Q1 R2^-1
-    gram_tiled<T>(Qb, n, r, a0, a1, tile, part, Gm, cap);
-    if (!group_reduce(Gm, Gm, cc2, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
+    // (the group exchanges only the r(r+1)/2 packed Gram entries, staged in Ri)
+    const int npk = r * (r + 1) / 2;
+    gram_tiled<T>(Qb, n, r, a0, a1, tile, part, Ri);
+    if (!group_reduce(Ri, Ri, npk, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
+    gram_unpack(Ri, r, Gm, cap);
     ok = blk_chol_upper(Gm, cap, r, iflag, clamp_gram<T>()) && ok;
     for (int t = threadIdx.x; t < cc2; t += blockDim.x) R1[t] = Gm[t];
     __syncthreads();
     blk_triinv_upper(Gm, cap, Ri, cap, r);
     rowmul_pass<T>(Qb, n, r, a0, a1, Ri, cap);
-    gram_tiled<T>(Qb, n, r, a0, a1, tile, part, Gm, cap);
-    if (!group_reduce(Gm, Gm, cc2, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
+    gram_tiled<T>(Qb, n, r, a0, a1, tile, part, Ri);
+    if (!group_reduce(Ri, Ri, npk, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
+    gram_unpack(Ri, r, Gm, cap);
     ok = blk_chol_upper(Gm, cap, r, iflag, clamp_gram<T>()) && ok;
     blk_triinv_upper(Gm, cap, Ri, cap, r);
     double* Rs = side == 0 ? RU : RV;
@@ -450,7 +472,7 @@ __global__ void __launch_bounds__(256, 2) k_level(const FactDesc* __restrict__ F
     __syncthreads();
     proj_tiled<T>(Qb, Bp, w, n, r, max(r0, s), min(r1, h), tile, part, Pm);
     proj_tiled<T>(Qb, Bp, w, n, r, max(r0, h), min(r1, e), tile, part, Pm + r * LV_W);
-    if (!group_reduce(Pm, Pm, 2 * cap * LV_W, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
+    if (!group_reduce(Pm, Pm, r2 * LV_W, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
     for (int t = threadIdx.x; t < r2 * LV_W; t += blockDim.x) {
       const int a = t / LV_W, j = t % LV_W;
       double acc = 0.0;
