@@ -59,9 +59,9 @@ def parse():
     ap.add_argument("--leaf", type=int, default=0, help="leaf size (0 = the autotuner's cached choice)")
     ap.add_argument("--nugget", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=256,
+    ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests of the serving stream to run (0 = skip the serving leg)")
-    ap.add_argument("--serve-slots", type=int, default=32)
+    ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--paths", default="fp64,mixed", help="chain precisions to time (comma list of fp64, mixed)")
     ap.add_argument("--additive-sweeps", type=int, default=10, help="0 = skip the d-block additive leg")
     return ap.parse_args()

@@ -8,7 +8,10 @@
 //   for k:          tau2_k | f_k, then the Metropolis step on log rho_k
 // Each block is a Gibbs chain on its sorted coordinate (Philox stream id k);
 // the shared sigma2 has its own small state (stream id d).  The sweep is
-// captured once in a CUDA graph and replayed.
+// captured once in a CUDA graph and replayed.  The blocks' M~ factorizations
+// (which depend only on the hyperparameters) and their tau2 / rho updates are
+// independent across blocks: on a context with independent CTAs they are
+// captured as concurrent graph branches, one per block.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -51,41 +54,83 @@ struct fifa_additive {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool graph_failed = false;
+  // concurrent branches (contexts with independent CTAs only): one stream and
+  // fork / join events per block
+  cudaStream_t side[FIFA_ADDITIVE_MAX_D] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[FIFA_ADDITIVE_MAX_D] = {};
+  bool branches = false;
 };
+
+// Enqueue fn(k) for every block k, as concurrent branches forked from and
+// joined back into ctx->stream when the model has branches, else in order.
+template <typename Fn>
+static fifa_status for_blocks(fifa_ctx* ctx, fifa_additive* A, Fn fn) {
+  if (!A->branches) {
+    for (int k = 0; k < A->d; ++k) {
+      fifa_status st = fn(k);
+      if (st != FIFA_OK) return st;
+    }
+    return FIFA_OK;
+  }
+  cudaStream_t main = ctx->stream;
+  if (cudaEventRecord(A->ev_fork, main) != cudaSuccess) return FIFA_ERR_CUDA;
+  fifa_status st = FIFA_OK;
+  for (int k = 0; k < A->d && st == FIFA_OK; ++k) {
+    if (cudaStreamWaitEvent(A->side[k], A->ev_fork, 0) != cudaSuccess) {
+      st = FIFA_ERR_CUDA;
+      break;
+    }
+    ctx->stream = A->side[k];
+    st = fn(k);
+    ctx->stream = main;
+    if (st == FIFA_OK && (cudaEventRecord(A->ev_join[k], A->side[k]) != cudaSuccess ||
+                          cudaStreamWaitEvent(main, A->ev_join[k], 0) != cudaSuccess))
+      st = FIFA_ERR_CUDA;
+  }
+  ctx->stream = main;
+  return st;
+}
 
 static fifa_status additive_sweep_enqueue(fifa_ctx* ctx, fifa_additive* A) {
   const int64_t n = A->n;
   const int d = A->d;
-  cudaStream_t s = ctx->stream;
   fifa_status st = FIFA_OK;
+  // M~_k = (tau2_k / sigma2) C~_k + I and its factor for every block: they
+  // depend only on the hyperparameters, so the blocks run side by side
+  st = for_blocks(ctx, A, [&](int k) {
+    ctx->active_scratch = A->blk[k]->scratch;
+    return chain_phase_factor_m(ctx, A->blk[k]);
+  });
   // f_k | y - sum_{j != k} f_j, blocks in order
   for (int k = 0; k < d && st == FIFA_OK; ++k) {
     fifa_chain* ch = A->blk[k];
-    if (launch_add_gather(A->y, A->F, A->perm + (size_t)k * n, n, d, k, ch->y, s) != cudaSuccess) {
+    if (launch_add_gather(A->y, A->F, A->perm + (size_t)k * n, n, d, k, ch->y, ctx->stream) != cudaSuccess) {
       st = FIFA_ERR_CUDA;
       break;
     }
     ctx->active_scratch = ch->scratch;
-    st = chain_phase_draw(ctx, ch);
-    if (st == FIFA_OK && launch_add_scatter(ch->f, A->perm + (size_t)k * n, n, A->F + (size_t)k * n, s) != cudaSuccess)
+    st = chain_phase_sample(ctx, ch);
+    if (st == FIFA_OK &&
+        launch_add_scatter(ch->f, A->perm + (size_t)k * n, n, A->F + (size_t)k * n, ctx->stream) != cudaSuccess)
       st = FIFA_ERR_CUDA;
   }
   // shared sigma2
   if (st == FIFA_OK) {
     ctx->active_scratch = A->blk[0]->scratch;
     Scratch S = carve(ctx, A->blk[0]->plan);
-    if (launch_add_residual(A->y, A->F, n, d, A->res, s) != cudaSuccess ||
-        launch_sumsq(A->res, A->F + (size_t)(d - 1) * n, n, S.red, &A->g->rss, s) != cudaSuccess ||
-        launch_add_sigma2(A->g, A->blk_dev, d, s) != cudaSuccess)
+    if (launch_add_residual(A->y, A->F, n, d, A->res, ctx->stream) != cudaSuccess ||
+        launch_sumsq(A->res, A->F + (size_t)(d - 1) * n, n, S.red, &A->g->rss, ctx->stream) != cudaSuccess ||
+        launch_add_sigma2(A->g, A->blk_dev, d, ctx->stream) != cudaSuccess)
       st = FIFA_ERR_CUDA;
   }
-  // tau2_k and rho_k of every block
-  for (int k = 0; k < d && st == FIFA_OK; ++k) {
-    fifa_chain* ch = A->blk[k];
-    ctx->active_scratch = ch->scratch;
-    Scratch S = carve(ctx, ch->plan);
-    st = chain_phase_hyper(ctx, ch, S);
-  }
+  // tau2_k and rho_k of every block, side by side
+  if (st == FIFA_OK)
+    st = for_blocks(ctx, A, [&](int k) {
+      fifa_chain* ch = A->blk[k];
+      ctx->active_scratch = ch->scratch;
+      Scratch S = carve(ctx, ch->plan);
+      return chain_phase_hyper(ctx, ch, S);
+    });
   ctx->active_scratch = nullptr;
   if (st == FIFA_ERR_CUDA) ctx->last_cuda = cudaGetLastError();
   return st;
@@ -135,6 +180,14 @@ extern "C" fifa_status fifa_additive_create(fifa_ctx* ctx, const double* X_dev, 
     // the block's data buffer is overwritten by the partial residual every sweep
     fifa_status st = fifa_chain_create(ctx, A->res, A->y, n, init, prior, seed, (uint64_t)k, &A->blk[k]);
     if (st != FIFA_OK) return fail(st);
+  }
+  // concurrent block branches only where no kernel's CTAs wait on each other
+  if (ctx->opts.independent_ctas && d > 1) {
+    A->branches = cudaEventCreateWithFlags(&A->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < d && A->branches; ++k)
+      A->branches = cudaStreamCreateWithFlags(&A->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&A->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!A->branches) return fail(FIFA_ERR_CUDA);
   }
   ChainDev* ptrs[FIFA_ADDITIVE_MAX_D] = {};
   for (int k = 0; k < d; ++k) ptrs[k] = A->blk[k]->dev;
@@ -286,6 +339,11 @@ extern "C" void fifa_destroy_additive(fifa_ctx* ctx, fifa_additive* A) {
   if (A->graph) cudaGraphDestroy(A->graph);
   for (int k = 0; k < A->d; ++k)
     if (A->blk[k]) fifa_destroy_chain(ctx, A->blk[k]);
+  for (int k = 0; k < FIFA_ADDITIVE_MAX_D; ++k) {
+    if (A->side[k]) cudaStreamDestroy(A->side[k]);
+    if (A->ev_join[k]) cudaEventDestroy(A->ev_join[k]);
+  }
+  if (A->ev_fork) cudaEventDestroy(A->ev_fork);
   ctx->arena.release(A->perm);
   ctx->arena.release(A->F);
   ctx->arena.release(A->y);

@@ -92,9 +92,16 @@ static size_t fused_sweep_part_doubles(const Plan* P, const fifa_opts& o) {
   return (size_t)2 * std::min(P->nleaf, FS_CTAS_MAX) * FS_PART_STRIDE;
 }
 
+// Partials of the fused H-matvec: one projection per CTA and level below the
+// CTA level, for up to min(nleaf, FS_CTAS_MAX) CTAs and 10 such levels.
+static size_t fused_mv_part_doubles(const Plan* P, const fifa_opts& o) {
+  if (o.independent_ctas) return 1;
+  return (size_t)std::min(P->nleaf, FS_CTAS_MAX) * std::max(1, std::min(P->L, 10)) * FIFA_CAP_MAX * SWEEP_RHS_MAX;
+}
+
 // Host part of a plan: bounds, ACA / level / sweep groups, scratch size.
 // aca_cores / lvl_cores: co-resident CTA budgets of the ACA and level kernels.
-static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, int lvl_cores, fifa_status* st) {
+static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, int lvl_cores, int lvl4_cores, fifa_status* st) {
   Plan* P = new (std::nothrow) Plan();
   if (!P) {
     *st = FIFA_ERR_OOM;
@@ -171,15 +178,21 @@ static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, int lvl_co
   P->work_host.insert(P->work_host.end(), solo.begin(), solo.end());
   // factor / sweep groups per level: one CTA per node up to 8192 rows
   P->lvl_G.assign(P->L, 1);
+  P->lvl_G4.assign(P->L, 1);
   P->sweep_G.assign(P->L, 1);
   for (int l = 0; l < P->L; ++l) {
     const int64_t len = (n + ((int64_t)1 << l) - 1) >> l;
     const int64_t nodes = (int64_t)1 << l;
     // levels with fewer nodes than the co-resident CTAs split each node's rows
-    // over a group of CTAs (>= 1024 rows each) that fills the GPU
+    // over a group of CTAs (>= 1024 rows each) that fills the GPU; the rank
+    // <= 4 kernel fits more CTAs per SM and gets its own group size
     if (groups && 2 * nodes <= lvl_cores && len >= 2048) {
       const int64_t G = std::min<int64_t>(len / 1024, lvl_cores / nodes);
       P->lvl_G[l] = (int)std::max<int64_t>(1, G);
+    }
+    if (groups && 2 * nodes <= lvl4_cores && len >= 2048) {
+      const int64_t G = std::min<int64_t>(len / 1024, lvl4_cores / nodes);
+      P->lvl_G4[l] = (int)std::max<int64_t>(1, G);
     }
     P->sweep_G[l] = (int)std::max<int64_t>(1, (len + 2047) / 2048);
   }
@@ -193,12 +206,12 @@ static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, int lvl_co
   add(sizeof(unsigned int) * std::max(1, P->aca_ncoop));         // ACA barriers
   int64_t lvl_ctas = 1, sweep_ctas = 1;
   for (int l = 0; l < P->L; ++l) {
-    lvl_ctas = std::max<int64_t>(lvl_ctas, ((int64_t)1 << l) * P->lvl_G[l]);
+    lvl_ctas = std::max<int64_t>(lvl_ctas, ((int64_t)1 << l) * std::max(P->lvl_G[l], P->lvl_G4[l]));
     sweep_ctas = std::max<int64_t>(sweep_ctas, ((int64_t)1 << l) * P->sweep_G[l]);
   }
   P->lvl_ctas_max = (int)lvl_ctas;
   add(sizeof(double) * 2 * lvl_ctas * level_part_stride(cap));           // level partials (2 slots)
-  add(sizeof(unsigned int) * lvl_ctas);                                  // level barriers
+  add(sizeof(unsigned int) * LEVEL_BUCKETS * lvl_ctas);                  // level barriers, one set per rank bucket
   add(sizeof(double) * sweep_ctas * 2 * cap * SWEEP_RHS_MAX);            // sweep partials
   add(sizeof(double) * (size_t)P->nleaf * std::max(1, P->L) * cap * SWEEP_RHS_MAX);  // matvec partials
   add(sizeof(double) * (size_t)std::max(1, P->nnodes) * 2 * cap * SWEEP_RHS_MAX);     // matvec projections
@@ -207,6 +220,8 @@ static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, int lvl_co
   add(256);                                                               // flags
   add(sizeof(double) * fused_sweep_part_doubles(P, o));                   // fused sweep partials
   add(256);                                                               // fused sweep barrier
+  add(sizeof(double) * fused_mv_part_doubles(P, o));                      // fused matvec partials
+  add(256);                                                               // fused matvec barrier
   P->scratch_bytes = need;
   return P;
 }
@@ -215,7 +230,7 @@ Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st) {
   auto key = std::make_pair(n, ctx->opts.leaf_size);
   auto it = ctx->plans.find(key);
   if (it != ctx->plans.end()) return it->second;
-  Plan* P = plan_build(n, ctx->opts, ctx->aca_coresident, ctx->level_coresident[0], st);
+  Plan* P = plan_build(n, ctx->opts, ctx->aca_coresident, ctx->level_coresident[0], ctx->level4_coresident, st);
   if (!P) return nullptr;
   // fused sweep: the largest power-of-two grid (<= nleaf, FS_CTAS_MAX) whose
   // CTAs, each holding the longest level-k node in shared memory, are all
@@ -231,6 +246,18 @@ Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st) {
       if (co >= (1 << k)) {
         P->fs_ls = k;
         P->fs_rows = rows;
+        break;
+      }
+    }
+    // fused H-matvec: the same kind of grid, rows per CTA <= MV_FUSED_ROWS_MAX
+    for (int k = std::min(P->L, 10); k >= 0; --k) {
+      int rows = 0;
+      for (int i = 0; i < (1 << k); ++i)
+        rows = std::max(rows, P->bnd_host[bnd_off(k) + i + 1] - P->bnd_host[bnd_off(k) + i]);
+      if (rows > MV_FUSED_ROWS_MAX) break;
+      if (mv_fused_coresident(rows) >= (1 << k)) {
+        P->mv_ls = k;
+        P->mv_rows = rows;
         break;
       }
     }
@@ -285,7 +312,8 @@ extern "C" fifa_status fifa_chain_bytes(const fifa_opts* opts, int64_t n, size_t
   if (opts->leaf_size < 1 || opts->rank_cap < 1) return FIFA_ERR_INVALID_ARG;
   if (opts->leaf_size > FIFA_LEAF_MAX || opts->rank_cap > FIFA_CAP_MAX) return FIFA_ERR_UNSUPPORTED;
   fifa_status st = FIFA_OK;
-  Plan* P = plan_build(n, *opts, aca_max_coresident_ctas(), level_max_coresident(0, opts->rank_cap), &st);
+  Plan* P = plan_build(n, *opts, aca_max_coresident_ctas(), level_max_coresident(0, opts->rank_cap),
+                       level4_max_coresident(0, opts->rank_cap), &st);
   if (!P) return st;
   *bytes_out = arena_round(256) /* context flags */ + arena_round(P->dev_bytes) + chain_bytes(P, *opts);
   delete P;
@@ -305,7 +333,7 @@ Scratch carve(fifa_ctx* ctx, Plan* P) {
   S.aca_part = (ArgMax*)take((size_t)3 * sizeof(ArgMax) * std::max(1, P->aca_ncoop));
   S.aca_bar = (unsigned int*)take(sizeof(unsigned int) * std::max(1, P->aca_ncoop));
   S.lvl_part = (double*)take(sizeof(double) * 2 * (size_t)P->lvl_ctas_max * level_part_stride(cap));
-  S.lvl_bar = (unsigned int*)take(sizeof(unsigned int) * P->lvl_ctas_max);
+  S.lvl_bar = (unsigned int*)take(sizeof(unsigned int) * LEVEL_BUCKETS * P->lvl_ctas_max);
   int64_t sweep_ctas = 1;
   for (int l = 0; l < P->L; ++l) sweep_ctas = std::max<int64_t>(sweep_ctas, ((int64_t)1 << l) * P->sweep_G[l]);
   S.sweep_part = (double*)take(sizeof(double) * sweep_ctas * 2 * cap * SWEEP_RHS_MAX);
@@ -316,6 +344,8 @@ Scratch carve(fifa_ctx* ctx, Plan* P) {
   S.flags = (int*)take(256);
   S.fs_part = (double*)take(sizeof(double) * fused_sweep_part_doubles(P, ctx->opts));
   S.fs_bar = (unsigned int*)take(256);
+  S.mv_fpart = (double*)take(sizeof(double) * fused_mv_part_doubles(P, ctx->opts));
+  S.mv_bar = (unsigned int*)take(256);
   return S;
 }
 
@@ -371,6 +401,8 @@ extern "C" fifa_status fifa_create(fifa_ctx** out, const fifa_opts* opts, void* 
   ctx->level_coresident[0] = level_max_coresident(0, ctx->opts.rank_cap);
   ctx->level_coresident[1] = level_max_coresident(1, ctx->opts.rank_cap);
   ctx->level_coresident[0] = std::min(ctx->level_coresident[0], ctx->level_coresident[1]);
+  ctx->level4_coresident = std::min(level4_max_coresident(0, ctx->opts.rank_cap),
+                                    level4_max_coresident(1, ctx->opts.rank_cap));
   ctx->flags = (int*)ctx->arena.alloc(256);
   ctx->host_flags = nullptr;
   cudaMallocHost((void**)&ctx->host_flags, 256);
@@ -606,13 +638,13 @@ fifa_status fact_enqueue(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev) {
   CK(launch_prep_fact(F->dev, Hdev, P->nnodes, s));
   CK(launch_leaf_factor(Hdev, F->dev, prec, P->nleaf, P->Bm, P->L, cap, s));
   for (int l = P->L - 1; l >= 0; --l) {
-    const int G = P->lvl_G[l];
-    if (G > 1) {
-      CK(cudaMemsetAsync(S.lvl_bar, 0, sizeof(unsigned int) * ((size_t)1 << l) * G, s));
+    const int G = P->lvl_G[l], G4 = P->lvl_G4[l];
+    if (G > 1 || G4 > 1) {  // every rank bucket has its own barrier set
+      CK(cudaMemsetAsync(S.lvl_bar, 0, sizeof(unsigned int) * LEVEL_BUCKETS * P->lvl_ctas_max, s));
       CK(cudaMemsetAsync(S.flags, 0, sizeof(int), s));
     }
     const int side_max = (int)(((n_of(P) + ((int64_t)1 << l) - 1) >> l) + 1) / 2;
-    CK(launch_level(F->dev, prec, l, 1 << l, G, cap, S.lvl_part, S.lvl_bar, S.flags, side_max, s));
+    CK(launch_level(F->dev, prec, l, 1 << l, G, G4, cap, S.lvl_part, S.lvl_bar, P->lvl_ctas_max, S.flags, side_max, s));
   }
   CK(launch_logdet_reduce(F->dev, s));
   return FIFA_OK;
@@ -710,6 +742,12 @@ extern "C" fifa_status fifa_apply_W(fifa_ctx* ctx, const fifa_fact* F, int trans
 fifa_status matvec_enqueue(fifa_ctx* ctx, const fifa_hmat* A, const double* in, double* out, int nrhs) {
   Plan* P = A->plan;
   Scratch S = carve(ctx, P);
+  if (P->mv_ls >= 0) {
+    CK(cudaMemsetAsync(S.mv_bar, 0, sizeof(unsigned int), ctx->stream));
+    CK(cudaMemsetAsync(S.flags, 0, sizeof(int), ctx->stream));
+    CK(launch_mv_fused(A->dev, P->mv_ls, P->mv_rows, in, nrhs, out, S.mv_fpart, S.mv_bar, S.flags, ctx->stream));
+    return FIFA_OK;
+  }
   CK(launch_matvec(A->dev, P->nleaf, P->L, in, nrhs, S.mv_part, S.mv_proj, out, ctx->stream));
   return FIFA_OK;
 }

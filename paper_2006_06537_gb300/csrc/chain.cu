@@ -29,15 +29,23 @@
     }                            \
   } while (0)
 
-// Phase 1: M~ = (tau2 / sigma2) C~ + I, its factor, and f | y by Algorithm 1.
-fifa_status chain_phase_draw(fifa_ctx* ctx, fifa_chain* ch) {
-  cudaStream_t s = ctx->stream;
+// Phase 1a: M~ = (tau2 / sigma2) C~ + I and its factor.
+fifa_status chain_phase_factor_m(fifa_ctx* ctx, fifa_chain* ch) {
+  if (launch_chain_make_view(ch->H[0]->dev, ch->Mv->dev, ch->dev, ctx->stream) != cudaSuccess) return FIFA_ERR_CUDA;
+  return fact_enqueue(ctx, ch->FM, ch->Mv->dev);
+}
+
+// Phase 1b: f | y by Algorithm 1 (after phase 1a).
+fifa_status chain_phase_sample(fifa_ctx* ctx, fifa_chain* ch) {
   ChainDev* c = ch->dev;
-  if (launch_chain_make_view(ch->H[0]->dev, ch->Mv->dev, c, s) != cudaSuccess) return FIFA_ERR_CUDA;
-  fifa_status st = fact_enqueue(ctx, ch->FM, ch->Mv->dev);
-  if (st != FIFA_OK) return st;
   return sample_enqueue(ctx, ch->H[0], ch->F[0], ch->FM, ch->y, 0.0, 0.0, ch->init.seed, ch->init.chain_id, &c->iter,
                         0, ch->f, ch->mean, &c->tau2, &c->refine_res);
+}
+
+// Phase 1: phases 1a and 1b.
+fifa_status chain_phase_draw(fifa_ctx* ctx, fifa_chain* ch) {
+  fifa_status st = chain_phase_factor_m(ctx, ch);
+  return st == FIFA_OK ? chain_phase_sample(ctx, ch) : st;
 }
 
 // Phase 2: sigma2 | y, f.

@@ -27,9 +27,10 @@ struct Plan {
   int aca_ncoop = 0, aca_nsolo = 0;
   std::vector<int4> work_host;
   size_t work_off = 0, dev_bytes = 0;  // device block: bounds, then the work list at work_off
-  std::vector<int> lvl_G, sweep_G;
+  std::vector<int> lvl_G, lvl_G4, sweep_G;  // lvl_G4: group size of the rank <= 4 level kernel
   int lvl_ctas_max = 1;
   int fs_ls = -1, fs_rows = 0;  // fused sweep: 2^fs_ls CTAs of fs_rows rows (-1: per-level sweeps)
+  int mv_ls = -1, mv_rows = 0;  // fused H-matvec: 2^mv_ls CTAs of mv_rows rows (-1: three-pass product)
   size_t scratch_bytes = 0;
 };
 
@@ -46,6 +47,8 @@ struct Scratch {
   int* flags;
   double* fs_part;        // fused sweep partials
   unsigned int* fs_bar;   // fused sweep grid barrier
+  double* mv_fpart;       // fused H-matvec partials
+  unsigned int* mv_bar;   // fused H-matvec grid barrier
 };
 
 struct fifa_ctx {
@@ -59,6 +62,7 @@ struct fifa_ctx {
   size_t scratch_bytes = 0;
   int aca_coresident = 0;
   int level_coresident[2] = {0, 0};
+  int level4_coresident = 0;
   int* flags = nullptr;       // device
   int* host_flags = nullptr;  // pinned
   bool capturing = false;

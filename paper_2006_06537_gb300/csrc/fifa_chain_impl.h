@@ -33,6 +33,8 @@ struct fifa_chain {
 //   hyper  q, tau2 | f, proposal C~(rho'), its factor, q', Metropolis step;
 //          advances the chain's iteration counter
 fifa_status chain_phase_draw(fifa_ctx* ctx, fifa_chain* ch);
+fifa_status chain_phase_factor_m(fifa_ctx* ctx, fifa_chain* ch);  // first half of draw: M~ and its factor
+fifa_status chain_phase_sample(fifa_ctx* ctx, fifa_chain* ch);    // second half: Algorithm 1
 fifa_status chain_phase_sigma2(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
 fifa_status chain_phase_hyper(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
 

@@ -214,8 +214,15 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
 // pivot.  clamp > 0: a pivot below clamp * (largest diagonal entry) is raised to
 // that value instead (modified Cholesky: the result factors a nearby SPD
 // matrix; used for factors that only precondition an FP64 iteration).
+// Reciprocal pivots of the last blk_chol_upper call in this CTA (r <= 2 FIFA_CAP_MAX).
+__device__ inline double* blk_chol_rinv() {
+  __shared__ double rinv[2 * FIFA_CAP_MAX];
+  return rinv;
+}
+
 __device__ inline bool blk_chol_upper(double* A, int ld, int r, int* flag, double clamp = 0.0) {
   __shared__ double chol_floor;
+  double* rinv = blk_chol_rinv();
   if (threadIdx.x == 0) {
     *flag = 0;
     double dmax = 0.0;
@@ -229,11 +236,13 @@ __device__ inline bool blk_chol_upper(double* A, int ld, int r, int* flag, doubl
       double d = A[k * ld + k];
       if (clamp > 0.0 && !(d > floor_v)) d = floor_v > 0.0 ? floor_v : 1.0;
       if (!(d > 0.0)) { *flag = 1; d = 1.0; }
-      A[k * ld + k] = sqrt(d);
+      const double rs = rsqrt(d);  // one reciprocal square root gives the pivot and its reciprocal
+      A[k * ld + k] = d * rs;
+      rinv[k] = rs;
     }
     __syncthreads();
-    double dk = A[k * ld + k];
-    for (int j = k + 1 + threadIdx.x; j < r; j += blockDim.x) A[k * ld + j] /= dk;
+    const double dinv = rinv[k];
+    for (int j = k + 1 + threadIdx.x; j < r; j += blockDim.x) A[k * ld + j] *= dinv;
     __syncthreads();
     int m = r - k - 1;
     for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
@@ -250,13 +259,16 @@ __device__ inline bool blk_chol_upper(double* A, int ld, int r, int* flag, doubl
   return *flag == 0;
 }
 
-// Rinv = R^-1 for upper-triangular R (r x r); one thread per column.
+// Rinv = R^-1 for upper-triangular R (r x r); one thread per column.  R must
+// be the factor of the CTA's last blk_chol_upper call (its reciprocal pivots
+// replace the divisions).
 __device__ inline void blk_triinv_upper(const double* R, int ldr, double* Ri, int ldi, int r) {
+  const double* rinv = blk_chol_rinv();
   for (int j = threadIdx.x; j < r; j += blockDim.x) {
     for (int i = r - 1; i >= 0; --i) {
       double acc = (i == j) ? 1.0 : 0.0;
       for (int k = i + 1; k <= j; ++k) acc -= R[i * ldr + k] * Ri[k * ldi + j];
-      Ri[i * ldi + j] = (i <= j) ? acc / R[i * ldr + i] : 0.0;
+      Ri[i * ldi + j] = (i <= j) ? acc * rinv[i] : 0.0;
     }
   }
   __syncthreads();

@@ -10,7 +10,7 @@ cudaError_t launch_aca(const HmatDesc* Hd, const int4* work, int ncta, bool coop
 int aca_max_coresident_ctas();
 
 size_t leaf_factor_smem(int Bm, int L, int cap, int prec);
-size_t level_smem(int cap);
+size_t level_smem(int ldm, int cap);
 // Doubles per CTA slot of the level kernel's partial sums: a cap x cap Gram
 // matrix or a 2cap x 8 projection block.
 __host__ __device__ inline size_t level_part_stride(int cap) {
@@ -18,9 +18,13 @@ __host__ __device__ inline size_t level_part_stride(int cap) {
 }
 cudaError_t launch_leaf_factor(const HmatDesc* Hd, const FactDesc* Fd, int prec, int nleaf, int Bm, int L, int cap,
                                cudaStream_t st);
-cudaError_t launch_level(const FactDesc* Fd, int prec, int lvl, int nodes, int G, int cap, double* part,
-                         unsigned int* bar, int* abort_flag, int side_max, cudaStream_t st);
+// Level kernels: rank buckets (.., 4] with groups of G4 CTAs, (4, 16] and
+// (16, cap] with groups of G; bucket b uses the barriers at bar + b * bar_stride.
+#define LEVEL_BUCKETS 3
+cudaError_t launch_level(const FactDesc* Fd, int prec, int lvl, int nodes, int G, int G4, int cap, double* part,
+                         unsigned int* bar, int bar_stride, int* abort_flag, int side_max, cudaStream_t st);
 int level_max_coresident(int prec, int cap);
+int level4_max_coresident(int prec, int cap);
 cudaError_t launch_logdet_reduce(const FactDesc* Fd, cudaStream_t st);
 
 #define SWEEP_RHS_MAX 2
@@ -33,6 +37,12 @@ cudaError_t launch_sweep_level(const FactDesc* Fd, int prec, int lvl, int nodes,
 int sweep_fused_coresident(int prec, int rows, int cap);
 cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, int cap, double* v, int nrhs,
                                int mode, double* part, unsigned int* bar, int* abort_flag, cudaStream_t st);
+// Fused H-matrix product (one cooperative launch of 2^ls CTAs, rows <= 4096).
+// part: 2^ls * ls * MV_PART_STRIDE doubles; bar zeroed before.
+#define MV_FUSED_ROWS_MAX 4096
+int mv_fused_coresident(int rows);
+cudaError_t launch_mv_fused(const HmatDesc* Hd, int ls, int rows, const double* x, int nrhs, double* y, double* part,
+                            unsigned int* bar, int* abort_flag, cudaStream_t st);
 cudaError_t launch_sweep_leaf(const FactDesc* Fd, int prec, int nleaf, double* v, int nrhs, int mode, cudaStream_t st);
 cudaError_t launch_matvec(const HmatDesc* Hd, int nleaf, int L, const double* x, int nrhs, double* part, double* proj,
                           double* y, cudaStream_t st);

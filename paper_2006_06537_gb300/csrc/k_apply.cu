@@ -475,6 +475,291 @@ cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, i
 }
 
 // ---------------------------------------------------------------------------
+// Fused H-matrix product y = scale (C~ x) + shift x in one cooperative launch
+// of 2^ls CTAs (the fused sweep's decomposition).  CTA c owns the rows [S, E)
+// of level-ls node c: x on them sits in shared memory and each thread keeps
+// the sums for its rows (S + tid + 256 i) in registers.  The leaf blocks and
+// the levels >= ls (whose nodes lie in the CTA) need nothing from other CTAs;
+// each level < ls needs the projection of the partner child, which spans
+// other CTAs: every CTA writes its partial projections for all those levels,
+// passes ONE grid barrier, and sums the partner half's partials.
+//   row p in the left child of a level-l node:  y_p += U_p (V^T x_right)
+//   row p in the right child:                   y_p += V_p (U^T x_left)
+// (U, V share one basis array: row p holds U if p is in the left child.)
+// ---------------------------------------------------------------------------
+#define MV_PROJ_BUF 1024                       // doubles of node projections per batch
+#define MV_PART_STRIDE (FIFA_CAP_MAX * SW_RHS_MAX)  // one CTA's partial of one level
+
+// Sum over rows [a0, a1) of bases[l][cc][p] * xs[j][p - S] for K outputs
+// o = (unit, c, j) described by fn(o, &a0, &a1, &col, &j) (col < 0: skip);
+// results to out[o].  Threads take (output, row chunk) pairs; chunk partials
+// are combined in a fixed order.
+template <typename F>
+__device__ void mv_dots(int K, const double* __restrict__ Bl, int64_t n, const double* xs, int rows, int S, F fn,
+                        double* red, double* out) {
+  const int nt = blockDim.x;
+  const int nch = K >= nt ? 1 : nt / K;
+  for (int o0 = 0; o0 < K; o0 += nt) {
+    const int kk = min(nt, K - o0);
+    const int ch = nch == 1 ? 0 : threadIdx.x / kk;
+    const int o = o0 + (nch == 1 ? threadIdx.x : threadIdx.x % kk);
+    double acc = 0.0;
+    if ((nch == 1 && threadIdx.x < kk) || (nch > 1 && ch < nch)) {
+      int a0, a1, col, j;
+      fn(o, a0, a1, col, j);
+      if (col >= 0) {
+        const double* b = Bl + (size_t)col * n;
+        const double* xj = xs + (size_t)j * rows - S;
+        for (int p = a0 + ch; p < a1; p += nch) acc += b[p] * xj[p];
+      }
+    }
+    __syncthreads();
+    if (nch > 1) {
+      if (ch < nch) red[ch * kk + (threadIdx.x % kk)] = acc;
+      __syncthreads();
+      if ((int)threadIdx.x < kk) {
+        double v = 0.0;
+        for (int q = 0; q < nch; ++q) v += red[q * kk + threadIdx.x];
+        out[o0 + threadIdx.x] = v;
+      }
+    } else if ((int)threadIdx.x < kk) {
+      out[o] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(256, RPT <= 8 ? 4 : 2) k_mv_fused(const HmatDesc* __restrict__ Hd, const double* __restrict__ x, int nrhs,
+                                                  double* __restrict__ y, int ls, int rows, double* __restrict__ part,
+                                                  unsigned int* __restrict__ bar, int* __restrict__ abort_flag) {
+  extern __shared__ double sm[];
+  double* xs = sm;                                   // nrhs x rows
+  double* pj = xs + (size_t)rows * nrhs;             // MV_PROJ_BUF node projections
+  double* red = pj + MV_PROJ_BUF;                    // 256 reduction partials
+  int* lmap = (int*)(red + 256);                     // rows: local leaf of each row
+  const int c = blockIdx.x, C = gridDim.x, tid = threadIdx.x;
+  const int L = Hd->L, cap = Hd->cap, Bm = Hd->Bm;
+  const int64_t n = Hd->n;
+  const int* bnd = Hd->bnd;
+  const int S = bnd[bnd_off(ls) + c], E = bnd[bnd_off(ls) + c + 1], R = E - S;
+  for (int j = 0; j < nrhs; ++j)
+    for (int p = tid; p < R; p += blockDim.x) xs[(size_t)j * rows + p] = x[(size_t)j * n + S + p];
+  const int nl = 1 << (L - ls), first = c << (L - ls);
+  for (int q = tid; q < nl; q += blockDim.x) {
+    const int s0 = bnd[bnd_off(L) + first + q], e0 = bnd[bnd_off(L) + first + q + 1];
+    for (int p = s0; p < e0; ++p) lmap[p - S] = q;
+  }
+  __syncthreads();
+  double acc[RPT][SW_RHS_MAX];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) acc[i][0] = acc[i][1] = 0.0;
+  // leaf blocks: y_p = sum_k D[p][k] x_k over the leaf of p
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int p = S + tid + i * (int)blockDim.x;
+    if (p < E) {
+      const int q = lmap[p - S], leaf = first + q;
+      const int s0 = bnd[bnd_off(L) + leaf], e0 = bnd[bnd_off(L) + leaf + 1];
+      const double* D = Hd->leaves + (size_t)leaf * Bm * Bm + (p - s0);
+      double a0 = 0.0, a1 = 0.0;
+      for (int k = s0; k < e0; ++k) {
+        const double dv = D[(size_t)(k - s0) * Bm];
+        a0 += dv * xs[k - S];
+        if (nrhs > 1) a1 += dv * xs[rows + k - S];
+      }
+      acc[i][0] = a0;
+      acc[i][1] = a1;
+    }
+  }
+  // levels >= ls: nodes inside this CTA, in batches whose projections fit pj
+  for (int l = ls; l < L; ++l) {
+    const double* Bl = Hd->bases + (size_t)l * cap * n;
+    const int nsub = 1 << (l - ls), i0 = c << (l - ls);
+    int rmax = 0;
+    for (int q = 0; q < nsub; ++q) rmax = max(rmax, Hd->rank[node_id(l, i0 + q)]);
+    if (rmax == 0) continue;
+    const int per = 2 * rmax * nrhs;  // projection entries per node: (side, c, j)
+    const int nb = max(1, MV_PROJ_BUF / per);
+    for (int b0 = 0; b0 < nsub; b0 += nb) {
+      const int bn = min(nb, nsub - b0);
+      mv_dots(bn * per, Bl, n, xs, rows, S,
+              [&](int o, int& a0, int& a1, int& col, int& j) {
+                const int node = o / per, rem = o % per, side = rem / (rmax * nrhs), cj = rem % (rmax * nrhs);
+                const int cc = cj / nrhs;
+                j = cj % nrhs;
+                const int nid = node_id(l, i0 + b0 + node);
+                int s0, h0, e0;
+                node_range(bnd, l, i0 + b0 + node, s0, h0, e0);
+                a0 = side ? h0 : s0;
+                a1 = side ? e0 : h0;
+                col = cc < Hd->rank[nid] ? cc : -1;
+              },
+              red, pj);
+      // rows of the batch's nodes: y_p += basis_l[p] . proj(partner side)
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int p = S + tid + i * (int)blockDim.x;
+        if (p < E) {
+          const int node = (lmap[p - S] >> (L - l)) - b0;
+          if (node >= 0 && node < bn) {
+            const int gi = i0 + b0 + node;
+            const int r = Hd->rank[node_id(l, gi)];
+            int s0, h0, e0;
+            node_range(bnd, l, gi, s0, h0, e0);
+            const int other = p < h0 ? 1 : 0;
+            const double* pr = pj + node * per + other * rmax * nrhs;
+            double a0 = 0.0, a1 = 0.0;
+            for (int cc = 0; cc < r; ++cc) {
+              const double bv = Bl[(size_t)cc * n + p];
+              a0 += bv * pr[cc * nrhs];
+              if (nrhs > 1) a1 += bv * pr[cc * nrhs + 1];
+            }
+            acc[i][0] += a0;
+            acc[i][1] += a1;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // levels < ls: partial projections of this CTA's rows for every such level
+  for (int l = 0; l < ls; ++l) {
+    const double* Bl = Hd->bases + (size_t)l * cap * n;
+    const int r = Hd->rank[node_id(l, c >> (ls - l))];
+    mv_dots(r * nrhs, Bl, n, xs, rows, S,
+            [&](int o, int& a0, int& a1, int& col, int& j) {
+              a0 = S;
+              a1 = E;
+              col = o / nrhs;
+              j = o % nrhs;
+            },
+            red, pj);
+    for (int k = tid; k < r * nrhs; k += blockDim.x) __stcg(part + ((size_t)c * ls + l) * MV_PART_STRIDE + k, pj[k]);
+    __syncthreads();
+  }
+  if (ls > 0) {
+    unsigned int phase = 1;
+    if (!group_barrier(bar, (unsigned)C * phase, Hd->status, abort_flag)) return;
+  }
+  // levels < ls: the partner half's projection, then the rows' sums
+  for (int l = 0; l < ls; ++l) {
+    const double* Bl = Hd->bases + (size_t)l * cap * n;
+    const int span = ls - l, i = c >> span, side = (c >> (span - 1)) & 1;
+    const int r = Hd->rank[node_id(l, i)];
+    if (r == 0) continue;
+    const int K = r * nrhs, half = 1 << (span - 1);
+    const int c0 = (i << span) + (1 - side) * half;  // first CTA of the partner child
+    const int nch = max(1, (int)blockDim.x / K);
+    if (tid < nch * K) {
+      const int k = tid % K, ch = tid / K;
+      double v = 0.0;
+      for (int q = ch; q < half; q += nch) v += __ldcg(part + ((size_t)(c0 + q) * ls + l) * MV_PART_STRIDE + k);
+      red[ch * K + k] = v;
+    }
+    __syncthreads();
+    if (tid < K) {
+      double v = 0.0;
+      for (int ch = 0; ch < nch; ++ch) v += red[ch * K + tid];
+      pj[tid] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ii = 0; ii < RPT; ++ii) {
+      const int p = S + tid + ii * (int)blockDim.x;
+      if (p < E) {
+        double a0 = 0.0, a1 = 0.0;
+        for (int cc = 0; cc < r; ++cc) {
+          const double bv = Bl[(size_t)cc * n + p];
+          a0 += bv * pj[cc * nrhs];
+          if (nrhs > 1) a1 += bv * pj[cc * nrhs + 1];
+        }
+        acc[ii][0] += a0;
+        acc[ii][1] += a1;
+      }
+    }
+    __syncthreads();
+  }
+  const double sc = Hd->scale, shf = Hd->shift;
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int p = S + tid + i * (int)blockDim.x;
+    if (p < E) {
+      const bool plain = shf == 0.0 && sc == 1.0;
+      y[p] = plain ? acc[i][0] : sc * acc[i][0] + shf * xs[p - S];
+      if (nrhs > 1) y[n + p] = plain ? acc[i][1] : sc * acc[i][1] + shf * xs[rows + p - S];
+    }
+  }
+}
+
+size_t mv_fused_smem(int rows) {
+  return sizeof(double) * ((size_t)rows * SW_RHS_MAX + MV_PROJ_BUF + 256) + sizeof(int) * (size_t)rows;
+}
+
+template <int RPT>
+static int mv_fused_per_sm(int rows) {
+  const size_t smem = mv_fused_smem(rows);
+  int dev = 0, optin = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem > (size_t)optin) return 0;
+  cudaFuncSetAttribute(k_mv_fused<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mv_fused<RPT>, 256, smem) != cudaSuccess) per_sm = 0;
+  cudaGetLastError();
+  return per_sm;
+}
+
+static int mv_rpt(int rows) {
+  int rpt = 1;
+  while (rpt * 256 < rows) rpt *= 2;
+  return rpt;
+}
+
+int mv_fused_coresident(int rows) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  switch (mv_rpt(rows)) {
+    case 1: return sms * mv_fused_per_sm<1>(rows);
+    case 2: return sms * mv_fused_per_sm<2>(rows);
+    case 4: return sms * mv_fused_per_sm<4>(rows);
+    case 8: return sms * mv_fused_per_sm<8>(rows);
+    case 16: return sms * mv_fused_per_sm<16>(rows);
+    default: return 0;
+  }
+}
+
+template <int RPT>
+static cudaError_t launch_mv_fused_t(const HmatDesc* Hd, int ls, int rows, const double* x, int nrhs, double* y,
+                                     double* part, unsigned int* bar, int* abort_flag, cudaStream_t st) {
+  const size_t smem = mv_fused_smem(rows);
+  cudaFuncSetAttribute(k_mv_fused<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1u << ls);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_mv_fused<RPT>, Hd, x, nrhs, y, ls, rows, part, bar, abort_flag);
+}
+
+cudaError_t launch_mv_fused(const HmatDesc* Hd, int ls, int rows, const double* x, int nrhs, double* y, double* part,
+                            unsigned int* bar, int* abort_flag, cudaStream_t st) {
+  switch (mv_rpt(rows)) {
+    case 1: return launch_mv_fused_t<1>(Hd, ls, rows, x, nrhs, y, part, bar, abort_flag, st);
+    case 2: return launch_mv_fused_t<2>(Hd, ls, rows, x, nrhs, y, part, bar, abort_flag, st);
+    case 4: return launch_mv_fused_t<4>(Hd, ls, rows, x, nrhs, y, part, bar, abort_flag, st);
+    case 8: return launch_mv_fused_t<8>(Hd, ls, rows, x, nrhs, y, part, bar, abort_flag, st);
+    case 16: return launch_mv_fused_t<16>(Hd, ls, rows, x, nrhs, y, part, bar, abort_flag, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // H-matrix product y = scale * C~ x + shift * x.
 // Pass 1 (one CTA per leaf): per level, the projection of the leaf's rows onto
 //   the level's basis: part[(leaf * L + l) * cap + c][j].

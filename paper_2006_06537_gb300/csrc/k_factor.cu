@@ -13,6 +13,7 @@
 //                  I + Q Zi Q^T applied to every ancestor basis on the node's rows.
 //                  Small nodes: one CTA each.  Large nodes: G CTAs split the rows
 //                  and exchange partial sums through bounded-spin group barriers.
+#include <algorithm>
 #include <atomic>
 #include "fifa_common.cuh"
 #include "fifa_launch.h"
@@ -51,18 +52,23 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
     if (threadIdx.x == 0) {
       double d = A[k * ld + k];
       if (!(d > 0.0)) { flag[0] = 1; d = 1.0; }
-      d = sqrt(d);
-      A[k * ld + k] = d;
-      rinv[k] = 1.0 / d;
+      const double rs = rsqrt(d);  // the pivot and its reciprocal from one reciprocal square root
+      A[k * ld + k] = d * rs;
+      rinv[k] = rs;
     }
     __syncthreads();
     const double dinv = rinv[k];
     for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[k * ld + i] *= dinv;
     __syncthreads();
+    // trailing update on the lower triangle only: t -> (a, b), b <= a, t = a(a+1)/2 + b
     const int w = m - k - 1;
-    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
-      int i = k + 1 + t % w, j = k + 1 + t / w;
-      if (i >= j) A[j * ld + i] -= A[k * ld + i] * A[k * ld + j];
+    for (int t = threadIdx.x; t < w * (w + 1) / 2; t += blockDim.x) {
+      int a = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+      if ((a + 1) * (a + 2) / 2 <= t) ++a;
+      if (a * (a + 1) / 2 > t) --a;
+      const int b = t - a * (a + 1) / 2;
+      const int i = k + 1 + a, j = k + 1 + b;
+      A[j * ld + i] -= A[k * ld + i] * A[k * ld + j];
     }
     __syncthreads();
   }
@@ -161,7 +167,8 @@ __device__ __forceinline__ void rowmul_row(T* __restrict__ Xb, int64_t n, int r,
 template <typename T>
 __device__ void rowmul_pass(T* __restrict__ Xb, int64_t n, int r, int a0, int a1, const double* Ri, int ldr) {
   for (int p = a0 + threadIdx.x; p < a1; p += blockDim.x) {
-    if (r <= 8) rowmul_row<T, 8>(Xb, n, r, p, Ri, ldr);
+    if (r <= 4) rowmul_row<T, 4>(Xb, n, r, p, Ri, ldr);
+    else if (r <= 8) rowmul_row<T, 8>(Xb, n, r, p, Ri, ldr);
     else if (r <= 16) rowmul_row<T, 16>(Xb, n, r, p, Ri, ldr);
     else {
       for (int c = r - 1; c >= 0; --c) {  // right to left: column c reads only columns <= c
@@ -324,10 +331,13 @@ __device__ void proj_tiled(const T* __restrict__ Qb, T* const* Bp, int w, int64_
   __syncthreads();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256, 2) k_level(const FactDesc* __restrict__ Fd, int lvl, int G, double* __restrict__ gpart,
-                                               unsigned int* __restrict__ bar, int* __restrict__ abort_flag,
-                                               int skip_le) {
+// RB > 0: a rank bucket, nodes with RLO < r <= RB, small matrices with leading
+// dimension RB (less shared memory and registers, more CTAs per SM); RB == 0:
+// nodes with r > RLO, leading dimension cap.
+template <typename T, int RB, int RLO>
+__global__ void __launch_bounds__(256, RB == 4 ? 4 : 2)
+    k_level(const FactDesc* __restrict__ Fd, int lvl, int G, double* __restrict__ gpart,
+            unsigned int* __restrict__ bar, int* __restrict__ abort_flag, int skip_le) {
   extern __shared__ double sm[];
   const int bi = blockIdx.x / G, g = blockIdx.x % G, base = blockIdx.x - g;
   const int nid = node_id(lvl, bi);
@@ -337,7 +347,7 @@ __global__ void __launch_bounds__(256, 2) k_level(const FactDesc* __restrict__ F
   int s, h, e;
   node_range(bnd, lvl, bi, s, h, e);
   const int r = Fd->rank[nid];
-  if (r <= skip_le) return;  // handled by the small-node kernels
+  if (r <= skip_le || r <= RLO || (RB > 0 && r > RB)) return;  // another launch takes this node
   if (r == 0) {
     if (g == 0 && threadIdx.x == 0) Fd->ld_parts[nleaf + nid] = 0.0;
     return;
@@ -347,18 +357,19 @@ __global__ void __launch_bounds__(256, 2) k_level(const FactDesc* __restrict__ F
   T* Qb = Qall + (size_t)lvl * cap * n;
   const int len = e - s, rc = (len + G - 1) / G;
   const int r0 = s + min(len, g * rc), r1 = s + min(len, g * rc + rc);
-  const int cc2 = cap * cap;
+  const int ldm = RB > 0 ? RB : cap;  // leading dimension of the small matrices
+  const int cc2 = ldm * ldm;
   double* Gm = sm;
   double* Ri = Gm + cc2;
   double* R1 = Ri + cc2;
   double* RU = R1 + cc2;
   double* RV = RU + cc2;
-  double* tile = RV + cc2;                // (cap + LV_W) x LV_TRP row tile
-  double* part = tile + (cap + LV_W) * LV_TRP;  // 256 group partial sums
+  double* tile = RV + cc2;                // (ldm + LV_W) x LV_TRP row tile
+  double* part = tile + (ldm + LV_W) * LV_TRP;  // 256 group partial sums
   double* tmp = part + 256;               // LV_RED
-  double* Pm = tmp + LV_RED;              // 2cap x LV_W
-  T* Tm = (T*)(Pm + 2 * cap * LV_W);      // 2cap x LV_W, storage precision
-  T** Bp = (T**)(Pm + 4 * cap * LV_W);    // LV_W column pointers
+  double* Pm = tmp + LV_RED;              // 2ldm x LV_W
+  T* Tm = (T*)(Pm + 2 * ldm * LV_W);      // 2ldm x LV_W, storage precision
+  T** Bp = (T**)(Pm + 4 * ldm * LV_W);    // LV_W column pointers
   int* iflag = (int*)(Bp + LV_W);
   int* alist = iflag + 4;                 // ancestor columns (level << 8 | col)
   const size_t pstride = level_part_stride(cap);
@@ -373,27 +384,27 @@ __global__ void __launch_bounds__(256, 2) k_level(const FactDesc* __restrict__ F
     const int npk = r * (r + 1) / 2;
     gram_tiled<T>(Qb, n, r, a0, a1, tile, part, Ri);
     if (!group_reduce(Ri, Ri, npk, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
-    gram_unpack(Ri, r, Gm, cap);
-    ok = blk_chol_upper(Gm, cap, r, iflag, clamp_gram<T>()) && ok;
+    gram_unpack(Ri, r, Gm, ldm);
+    ok = blk_chol_upper(Gm, ldm, r, iflag, clamp_gram<T>()) && ok;
     for (int t = threadIdx.x; t < cc2; t += blockDim.x) R1[t] = Gm[t];
     __syncthreads();
-    blk_triinv_upper(Gm, cap, Ri, cap, r);
-    rowmul_pass<T>(Qb, n, r, a0, a1, Ri, cap);
+    blk_triinv_upper(Gm, ldm, Ri, ldm, r);
+    rowmul_pass<T>(Qb, n, r, a0, a1, Ri, ldm);
     gram_tiled<T>(Qb, n, r, a0, a1, tile, part, Ri);
     if (!group_reduce(Ri, Ri, npk, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
-    gram_unpack(Ri, r, Gm, cap);
-    ok = blk_chol_upper(Gm, cap, r, iflag, clamp_gram<T>()) && ok;
-    blk_triinv_upper(Gm, cap, Ri, cap, r);
+    gram_unpack(Ri, r, Gm, ldm);
+    ok = blk_chol_upper(Gm, ldm, r, iflag, clamp_gram<T>()) && ok;
+    blk_triinv_upper(Gm, ldm, Ri, ldm, r);
     double* Rs = side == 0 ? RU : RV;
     for (int t = threadIdx.x; t < cc2; t += blockDim.x) {
-      const int i = t / cap, j = t % cap;
+      const int i = t / ldm, j = t % ldm;
       double v = 0.0;
       if (i < r && j < r && i <= j)
-        for (int k = i; k <= j; ++k) v += Gm[i * cap + k] * R1[k * cap + j];
+        for (int k = i; k <= j; ++k) v += Gm[i * ldm + k] * R1[k * ldm + j];
       Rs[t] = v;
     }
     __syncthreads();
-    rowmul_pass<T>(Qb, n, r, a0, a1, Ri, cap);
+    rowmul_pass<T>(Qb, n, r, a0, a1, Ri, ldm);
   }
   if (!ok && g == 0 && threadIdx.x == 0) atomicOr(status, FIFA_DEV_NOT_SPD);
 
@@ -407,10 +418,10 @@ __global__ void __launch_bounds__(256, 2) k_level(const FactDesc* __restrict__ F
       double v = (a == b) ? 1.0 : 0.0;
       if (a < r && b >= r) {
         const int bb = b - r;
-        for (int k = 0; k < r; ++k) v += RU[a * cap + k] * RV[bb * cap + k];
+        for (int k = 0; k < r; ++k) v += RU[a * ldm + k] * RV[bb * ldm + k];
       } else if (a >= r && b < r) {
         const int aa = a - r;
-        for (int k = 0; k < r; ++k) v += RV[aa * cap + k] * RU[b * cap + k];
+        for (int k = 0; k < r; ++k) v += RV[aa * ldm + k] * RU[b * ldm + k];
       }
       Zf[a * ld2 + b] = v;
     }
@@ -468,7 +479,7 @@ __global__ void __launch_bounds__(256, 2) k_level(const FactDesc* __restrict__ F
       const int code = alist[c0 + min((int)threadIdx.x, w - 1)];
       Bp[threadIdx.x] = Qall + ((size_t)(code >> 8) * cap + (code & 255)) * n;
     }
-    for (int t = threadIdx.x; t < 2 * cap * LV_W; t += blockDim.x) Pm[t] = 0.0;
+    for (int t = threadIdx.x; t < 2 * ldm * LV_W; t += blockDim.x) Pm[t] = 0.0;
     __syncthreads();
     proj_tiled<T>(Qb, Bp, w, n, r, max(r0, s), min(r1, h), tile, part, Pm);
     proj_tiled<T>(Qb, Bp, w, n, r, max(r0, h), min(r1, e), tile, part, Pm + r * LV_W);
@@ -505,9 +516,8 @@ __global__ void __launch_bounds__(128) k_level_small(const FactDesc* __restrict_
   __shared__ T Tm[R2 * W];
   __shared__ double red[40];
   __shared__ int iflag[4];
-  __shared__ int alist[FIFA_LEVELS_MAX * FIFA_CAP_MAX];
-  __shared__ int rka[FIFA_LEVELS_MAX];
-  __shared__ int nanc;
+  __shared__ int rpre[FIFA_LEVELS_MAX + 1];  // prefix sums of the ancestor ranks
+  __shared__ int ccode[W];                    // (level << 8) | column of the chunk's columns
   const int bi = blockIdx.x;
   const int nid = node_id(lvl, bi);
   const int r = Fd->rank[nid];
@@ -619,21 +629,28 @@ __global__ void __launch_bounds__(128) k_level_small(const FactDesc* __restrict_
   }
   if (lvl == 0) return;
   // ancestor bases on the node's rows: B <- B + Q (L_S^-1 - I) Q^T B
-  for (int j = threadIdx.x; j < lvl; j += blockDim.x) rka[j] = Fd->rank[node_id(j, bi >> (lvl - j))];
-  __syncthreads();
   if (threadIdx.x == 0) {
     int c = 0;
-    for (int j = 0; j < lvl; ++j)
-      for (int q = 0; q < rka[j]; ++q) alist[c++] = (j << 8) | q;
-    nanc = c;
+    for (int j = 0; j < lvl; ++j) {
+      rpre[j] = c;
+      c += Fd->rank[node_id(j, bi >> (lvl - j))];
+    }
+    rpre[lvl] = c;
   }
   __syncthreads();
-  const int na = nanc, mn = e - s;
+  const int na = rpre[lvl], mn = e - s;
   for (int c0 = 0; c0 < na; c0 += W) {
     const int w = min(W, na - c0);
+    if (threadIdx.x < w) {  // ancestor column c0 + t: level j with rpre[j] <= c < rpre[j + 1]
+      const int c = c0 + threadIdx.x;
+      int j = 0;
+      while (rpre[j + 1] <= c) ++j;
+      ccode[threadIdx.x] = (j << 8) | (c - rpre[j]);
+    }
+    __syncthreads();
     for (int t = threadIdx.x; t < w * mn; t += blockDim.x) {
       const int j = t / mn, p = t % mn;
-      const int code = alist[c0 + j];
+      const int code = ccode[j];
       Bs[j][p] = Qall[((size_t)(code >> 8) * cap + (code & 255)) * n + s + p];
     }
     __syncthreads();
@@ -660,7 +677,7 @@ __global__ void __launch_bounds__(128) k_level_small(const FactDesc* __restrict_
       const int side = p >= mu, pp = side ? p - mu : p, toff = side ? r : 0;
       T acc = Bs[j][p];
       for (int a = 0; a < r; ++a) acc += (T)Xs[side][a][pp] * Tm[(toff + a) * W + j];
-      const int code = alist[c0 + j];
+      const int code = ccode[j];
       Qall[((size_t)(code >> 8) * cap + (code & 255)) * n + s + p] = acc;
     }
     __syncthreads();
@@ -685,8 +702,8 @@ size_t leaf_factor_smem(int Bm, int L, int cap, int prec) {
   b += 16 + 40 * sizeof(double) + (4 + (size_t)L * cap) * sizeof(int);
   return b;
 }
-size_t level_smem(int cap) {
-  return ((size_t)5 * cap * cap + (size_t)(cap + LV_W) * LV_TRP + 256 + LV_RED + 4 * (size_t)cap * LV_W) *
+size_t level_smem(int ldm, int cap) {
+  return ((size_t)5 * ldm * ldm + (size_t)(ldm + LV_W) * LV_TRP + 256 + LV_RED + 4 * (size_t)ldm * LV_W) *
              sizeof(double) +
          LV_W * sizeof(void*) + (4 + (size_t)FIFA_LEVELS_MAX * cap) * sizeof(int);
 }
@@ -720,9 +737,31 @@ cudaError_t launch_leaf_factor(const HmatDesc* Hd, const FactDesc* Fd, int prec,
   return prec ? launch_leaf_factor_t<float>(Hd, Fd, nleaf, smem, st) : launch_leaf_factor_t<double>(Hd, Fd, nleaf, smem, st);
 }
 
+template <typename T, int RB, int RLO>
+static cudaError_t launch_level_bucket(const FactDesc* Fd, int lvl, int nodes, int G, int cap, double* part,
+                                       unsigned int* bar, int* abort_flag, int skip, cudaStream_t st) {
+  const size_t smem = level_smem(RB > 0 ? RB : cap, cap);
+  if (smem > (size_t)smem_optin()) return cudaErrorInvalidConfiguration;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_level<T, RB, RLO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nodes * G);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = G > 1 ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_level<T, RB, RLO>, Fd, lvl, G, part, bar, abort_flag, skip);
+}
+
 template <typename T>
-static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, int G, int cap, double* part, unsigned int* bar,
-                                  int* abort_flag, int side_max, cudaStream_t st) {
+static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, int G, int G4, int cap, double* part,
+                                  unsigned int* bar, int bar_stride, int* abort_flag, int side_max, cudaStream_t st) {
   int skip = -1;
   if (G == 1 && side_max <= 256) {
     // small nodes staged in (static, < 48 KB) shared memory: rank buckets (0,4]
@@ -738,46 +777,56 @@ static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, int G,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const size_t smem = level_smem(cap);
-  if (smem > (size_t)smem_optin()) return cudaErrorInvalidConfiguration;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nodes * G);
-  cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = G > 1 ? 1 : 0;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_level<T>, Fd, lvl, G, part, bar, abort_flag, skip);
+  // rank buckets: (.., 4] and (4, 16] with small-matrix storage sized by the
+  // bucket, then (16, cap]; a node's CTAs skip the launches of other buckets
+  // (buckets entirely below the small kernels' ranks are not launched)
+  cudaError_t e = cudaSuccess;
+  if (skip < 4) e = launch_level_bucket<T, 4, -1>(Fd, lvl, nodes, G4, cap, part, bar, abort_flag, skip, st);
+  if (e == cudaSuccess && cap > 4 && skip < 16)
+    e = launch_level_bucket<T, 16, 4>(Fd, lvl, nodes, G, cap, part, bar + bar_stride, abort_flag, skip, st);
+  if (e == cudaSuccess && cap > 16)
+    e = launch_level_bucket<T, 0, 16>(Fd, lvl, nodes, G, cap, part, bar + 2 * bar_stride, abort_flag, skip, st);
+  return e;
 }
 
-cudaError_t launch_level(const FactDesc* Fd, int prec, int lvl, int nodes, int G, int cap, double* part,
-                         unsigned int* bar, int* abort_flag, int side_max, cudaStream_t st) {
-  return prec ? launch_level_t<float>(Fd, lvl, nodes, G, cap, part, bar, abort_flag, side_max, st)
-              : launch_level_t<double>(Fd, lvl, nodes, G, cap, part, bar, abort_flag, side_max, st);
+cudaError_t launch_level(const FactDesc* Fd, int prec, int lvl, int nodes, int G, int G4, int cap, double* part,
+                         unsigned int* bar, int bar_stride, int* abort_flag, int side_max, cudaStream_t st) {
+  return prec ? launch_level_t<float>(Fd, lvl, nodes, G, G4, cap, part, bar, bar_stride, abort_flag, side_max, st)
+              : launch_level_t<double>(Fd, lvl, nodes, G, G4, cap, part, bar, bar_stride, abort_flag, side_max, st);
 }
 
-int level_max_coresident(int prec, int cap) {
-  int dev = 0, sms = 0, per_sm = 0;
+template <typename T, int RB, int RLO>
+static int level_bucket_per_sm(int cap) {
+  const size_t smem = level_smem(RB > 0 ? RB : cap, cap);
+  if (smem > (size_t)smem_optin()) return 0;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_level<T, RB, RLO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level<T, RB, RLO>, 256, smem) != cudaSuccess) per_sm = 0;
+  cudaGetLastError();
+  return per_sm;
+}
+
+// Co-resident CTAs of the rank <= 4 level kernel (its own group size).
+int level4_max_coresident(int prec, int cap) {
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = level_smem(cap);
-  if (smem > (size_t)smem_optin()) return 0;
-  cudaError_t e;
-  if (prec) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_level<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level<float>, 256, smem);
-  } else {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_level<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level<double>, 256, smem);
-  }
-  if (e != cudaSuccess) per_sm = 1;
+  return sms * (prec ? level_bucket_per_sm<float, 4, -1>(cap) : level_bucket_per_sm<double, 4, -1>(cap));
+}
+
+// Co-resident CTAs of the level kernels: the least over the rank buckets (a
+// group's CTAs must all be resident whichever bucket its node falls in).
+int level_max_coresident(int prec, int cap) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm;
+  if (prec)
+    per_sm = std::min(level_bucket_per_sm<float, 4, -1>(cap),
+                      std::min(level_bucket_per_sm<float, 16, 4>(cap), level_bucket_per_sm<float, 0, 16>(cap)));
+  else
+    per_sm = std::min(level_bucket_per_sm<double, 4, -1>(cap),
+                      std::min(level_bucket_per_sm<double, 16, 4>(cap), level_bucket_per_sm<double, 0, 16>(cap)));
   return sms * per_sm;
 }
 

@@ -33,11 +33,12 @@ def _prior():
                          prop_sd=0.2)
 
 
-def _gpu_model(X, y, seed):
+def _gpu_model(X, y, seed, indep=0):
     n, d = X.shape
-    # a stream of its own: the sweep graph cannot be captured on the legacy default stream
+    # a stream of its own: the sweep graph cannot be captured on the legacy default stream;
+    # with independent CTAs the blocks' factorizations and hyper steps run as concurrent branches
     ctx = fifa.Context(leaf_size=B, aca_tol=EPS, rank_cap=32, prec=fifa.FIFA_FP64, arena_bytes=1 << 30,
-                       stream=torch.cuda.Stream())
+                       stream=torch.cuda.Stream(), independent_ctas=indep)
     vy = float(np.var(y))
     p = _prior()
     pr = fifa.fifa_prior(p.a_tau2, p.b_tau2, p.a_sigma2, p.b_sigma2, p.logrho_mu, p.logrho_sd, p.prop_sd)
@@ -48,12 +49,13 @@ def _gpu_model(X, y, seed):
     return ctx, m
 
 
+@pytest.mark.parametrize("indep", [0, 1])
 @pytest.mark.parametrize("n,d,sweeps", [(1024, 4, 3), (1500, 2, 4)])
-def test_additive_matches_oracle(n, d, sweeps):
+def test_additive_matches_oracle(n, d, sweeps, indep):
     X, y = additive4(n, seed=5)
     X = np.ascontiguousarray(X[:, :d])
     seed = 7
-    ctx, m = _gpu_model(X, y, seed)
+    ctx, m = _gpu_model(X, y, seed, indep)
     tr = np.zeros((sweeps, fifa.fifa_additive_trace_fields(d)))
     fifa.fifa_additive_sweep(ctx.h, m, sweeps, tr)
     F = torch.empty((d, n), dtype=torch.float64, device="cuda")
