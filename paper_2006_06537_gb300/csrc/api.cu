@@ -100,8 +100,9 @@ static size_t fused_mv_part_doubles(const Plan* P, const fifa_opts& o) {
 }
 
 // Host part of a plan: bounds, ACA / level / sweep groups, scratch size.
-// aca_cores / lvl_cores: co-resident CTA budgets of the ACA and level kernels.
-static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, int lvl_cores, int lvl4_cores, fifa_status* st) {
+// aca_cores / lvl_cores[b]: co-resident CTA budgets of the ACA kernel and of
+// the level kernel of rank bucket b.
+static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, const int* lvl_cores, fifa_status* st) {
   Plan* P = new (std::nothrow) Plan();
   if (!P) {
     *st = FIFA_ERR_OOM;
@@ -176,24 +177,20 @@ static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, int lvl_co
   P->aca_nsolo = (int)solo.size();
   P->work_host = coop;
   P->work_host.insert(P->work_host.end(), solo.begin(), solo.end());
-  // factor / sweep groups per level: one CTA per node up to 8192 rows
-  P->lvl_G.assign(P->L, 1);
-  P->lvl_G4.assign(P->L, 1);
+  // factor / sweep groups per level: levels with fewer nodes than the
+  // co-resident CTAs split each node's rows over a group of CTAs (>= 1024 rows
+  // each) that fills the GPU; each rank bucket's kernel has its own CTAs per SM
+  // and so its own group size
+  for (int b = 0; b < LEVEL_BUCKETS; ++b) P->lvl_G[b].assign(P->L, 1);
   P->sweep_G.assign(P->L, 1);
   for (int l = 0; l < P->L; ++l) {
     const int64_t len = (n + ((int64_t)1 << l) - 1) >> l;
     const int64_t nodes = (int64_t)1 << l;
-    // levels with fewer nodes than the co-resident CTAs split each node's rows
-    // over a group of CTAs (>= 1024 rows each) that fills the GPU; the rank
-    // <= 4 kernel fits more CTAs per SM and gets its own group size
-    if (groups && 2 * nodes <= lvl_cores && len >= 2048) {
-      const int64_t G = std::min<int64_t>(len / 1024, lvl_cores / nodes);
-      P->lvl_G[l] = (int)std::max<int64_t>(1, G);
-    }
-    if (groups && 2 * nodes <= lvl4_cores && len >= 2048) {
-      const int64_t G = std::min<int64_t>(len / 1024, lvl4_cores / nodes);
-      P->lvl_G4[l] = (int)std::max<int64_t>(1, G);
-    }
+    for (int b = 0; b < LEVEL_BUCKETS; ++b)
+      if (groups && 2 * nodes <= lvl_cores[b] && len >= 2048) {
+        const int64_t G = std::min<int64_t>(len / 1024, lvl_cores[b] / nodes);
+        P->lvl_G[b][l] = (int)std::max<int64_t>(1, G);
+      }
     P->sweep_G[l] = (int)std::max<int64_t>(1, (len + 2047) / 2048);
   }
   // device arrays: bounds, then the ACA work list at a 16-byte offset
@@ -206,7 +203,7 @@ static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, int lvl_co
   add(sizeof(unsigned int) * std::max(1, P->aca_ncoop));         // ACA barriers
   int64_t lvl_ctas = 1, sweep_ctas = 1;
   for (int l = 0; l < P->L; ++l) {
-    lvl_ctas = std::max<int64_t>(lvl_ctas, ((int64_t)1 << l) * std::max(P->lvl_G[l], P->lvl_G4[l]));
+    for (int b = 0; b < LEVEL_BUCKETS; ++b) lvl_ctas = std::max<int64_t>(lvl_ctas, ((int64_t)1 << l) * P->lvl_G[b][l]);
     sweep_ctas = std::max<int64_t>(sweep_ctas, ((int64_t)1 << l) * P->sweep_G[l]);
   }
   P->lvl_ctas_max = (int)lvl_ctas;
@@ -230,7 +227,7 @@ Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st) {
   auto key = std::make_pair(n, ctx->opts.leaf_size);
   auto it = ctx->plans.find(key);
   if (it != ctx->plans.end()) return it->second;
-  Plan* P = plan_build(n, ctx->opts, ctx->aca_coresident, ctx->level_coresident[0], ctx->level4_coresident, st);
+  Plan* P = plan_build(n, ctx->opts, ctx->aca_coresident, ctx->level_coresident, st);
   if (!P) return nullptr;
   // fused sweep: the largest power-of-two grid (<= nleaf, FS_CTAS_MAX) whose
   // CTAs, each holding the longest level-k node in shared memory, are all
@@ -312,8 +309,10 @@ extern "C" fifa_status fifa_chain_bytes(const fifa_opts* opts, int64_t n, size_t
   if (opts->leaf_size < 1 || opts->rank_cap < 1) return FIFA_ERR_INVALID_ARG;
   if (opts->leaf_size > FIFA_LEAF_MAX || opts->rank_cap > FIFA_CAP_MAX) return FIFA_ERR_UNSUPPORTED;
   fifa_status st = FIFA_OK;
-  Plan* P = plan_build(n, *opts, aca_max_coresident_ctas(), level_max_coresident(0, opts->rank_cap),
-                       level4_max_coresident(0, opts->rank_cap), &st);
+  int lvl_cores[LEVEL_BUCKETS];
+  for (int b = 0; b < LEVEL_BUCKETS; ++b)
+    lvl_cores[b] = std::min(level_bucket_coresident(0, b, opts->rank_cap), level_bucket_coresident(1, b, opts->rank_cap));
+  Plan* P = plan_build(n, *opts, aca_max_coresident_ctas(), lvl_cores, &st);
   if (!P) return st;
   *bytes_out = arena_round(256) /* context flags */ + arena_round(P->dev_bytes) + chain_bytes(P, *opts);
   delete P;
@@ -398,11 +397,9 @@ extern "C" fifa_status fifa_create(fifa_ctx** out, const fifa_opts* opts, void* 
   ctx->arena.size = arena_bytes & ~(size_t)255;
   ctx->arena.free_[0] = ctx->arena.size;
   ctx->aca_coresident = aca_max_coresident_ctas();
-  ctx->level_coresident[0] = level_max_coresident(0, ctx->opts.rank_cap);
-  ctx->level_coresident[1] = level_max_coresident(1, ctx->opts.rank_cap);
-  ctx->level_coresident[0] = std::min(ctx->level_coresident[0], ctx->level_coresident[1]);
-  ctx->level4_coresident = std::min(level4_max_coresident(0, ctx->opts.rank_cap),
-                                    level4_max_coresident(1, ctx->opts.rank_cap));
+  for (int b = 0; b < LEVEL_BUCKETS; ++b)
+    ctx->level_coresident[b] = std::min(level_bucket_coresident(0, b, ctx->opts.rank_cap),
+                                        level_bucket_coresident(1, b, ctx->opts.rank_cap));
   ctx->flags = (int*)ctx->arena.alloc(256);
   ctx->host_flags = nullptr;
   cudaMallocHost((void**)&ctx->host_flags, 256);
@@ -410,7 +407,7 @@ extern "C" fifa_status fifa_create(fifa_ctx** out, const fifa_opts* opts, void* 
     fifa_destroy_ctx(ctx);
     return FIFA_ERR_OOM;
   }
-  if (ctx->aca_coresident <= 0 || ctx->level_coresident[0] <= 0) {
+  if (ctx->aca_coresident <= 0 || *std::min_element(ctx->level_coresident, ctx->level_coresident + LEVEL_BUCKETS) <= 0) {
     fifa_destroy_ctx(ctx);
     return FIFA_ERR_UNSUPPORTED;
   }
@@ -638,13 +635,13 @@ fifa_status fact_enqueue(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev) {
   CK(launch_prep_fact(F->dev, Hdev, P->nnodes, s));
   CK(launch_leaf_factor(Hdev, F->dev, prec, P->nleaf, P->Bm, P->L, cap, s));
   for (int l = P->L - 1; l >= 0; --l) {
-    const int G = P->lvl_G[l], G4 = P->lvl_G4[l];
-    if (G > 1 || G4 > 1) {  // every rank bucket has its own barrier set
+    const int Gb[LEVEL_BUCKETS] = {P->lvl_G[0][l], P->lvl_G[1][l], P->lvl_G[2][l]};
+    if (*std::max_element(Gb, Gb + LEVEL_BUCKETS) > 1) {  // every rank bucket has its own barrier set
       CK(cudaMemsetAsync(S.lvl_bar, 0, sizeof(unsigned int) * LEVEL_BUCKETS * P->lvl_ctas_max, s));
       CK(cudaMemsetAsync(S.flags, 0, sizeof(int), s));
     }
     const int side_max = (int)(((n_of(P) + ((int64_t)1 << l) - 1) >> l) + 1) / 2;
-    CK(launch_level(F->dev, prec, l, 1 << l, G, G4, cap, S.lvl_part, S.lvl_bar, P->lvl_ctas_max, S.flags, side_max, s));
+    CK(launch_level(F->dev, prec, l, 1 << l, Gb, cap, S.lvl_part, S.lvl_bar, P->lvl_ctas_max, S.flags, side_max, s));
   }
   CK(launch_logdet_reduce(F->dev, s));
   return FIFA_OK;

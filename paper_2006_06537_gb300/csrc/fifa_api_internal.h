@@ -27,7 +27,7 @@ struct Plan {
   int aca_ncoop = 0, aca_nsolo = 0;
   std::vector<int4> work_host;
   size_t work_off = 0, dev_bytes = 0;  // device block: bounds, then the work list at work_off
-  std::vector<int> lvl_G, lvl_G4, sweep_G;  // lvl_G4: group size of the rank <= 4 level kernel
+  std::vector<int> lvl_G[3], sweep_G;  // lvl_G[b]: group size of the level kernel of rank bucket b
   int lvl_ctas_max = 1;
   int fs_ls = -1, fs_rows = 0;  // fused sweep: 2^fs_ls CTAs of fs_rows rows (-1: per-level sweeps)
   int mv_ls = -1, mv_rows = 0;  // fused H-matvec: 2^mv_ls CTAs of mv_rows rows (-1: three-pass product)
@@ -61,8 +61,7 @@ struct fifa_ctx {
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
   int aca_coresident = 0;
-  int level_coresident[2] = {0, 0};
-  int level4_coresident = 0;
+  int level_coresident[3] = {0, 0, 0};  // per rank bucket, least over the two precisions
   int* flags = nullptr;       // device
   int* host_flags = nullptr;  // pinned
   bool capturing = false;

@@ -18,13 +18,13 @@ __host__ __device__ inline size_t level_part_stride(int cap) {
 }
 cudaError_t launch_leaf_factor(const HmatDesc* Hd, const FactDesc* Fd, int prec, int nleaf, int Bm, int L, int cap,
                                cudaStream_t st);
-// Level kernels: rank buckets (.., 4] with groups of G4 CTAs, (4, 16] and
-// (16, cap] with groups of G; bucket b uses the barriers at bar + b * bar_stride.
 #define LEVEL_BUCKETS 3
-cudaError_t launch_level(const FactDesc* Fd, int prec, int lvl, int nodes, int G, int G4, int cap, double* part,
+// Level kernels: rank buckets (.., 4], (4, 16], (16, cap] with groups of G[b]
+// CTAs; bucket b uses the barriers at bar + b * bar_stride.
+cudaError_t launch_level(const FactDesc* Fd, int prec, int lvl, int nodes, const int* G, int cap, double* part,
                          unsigned int* bar, int bar_stride, int* abort_flag, int side_max, cudaStream_t st);
-int level_max_coresident(int prec, int cap);
-int level4_max_coresident(int prec, int cap);
+// Co-resident CTAs of the level kernel of rank bucket b (0: <= 4, 1: 5..16, 2: > 16).
+int level_bucket_coresident(int prec, int b, int cap);
 cudaError_t launch_logdet_reduce(const FactDesc* Fd, cudaStream_t st);
 
 #define SWEEP_RHS_MAX 2

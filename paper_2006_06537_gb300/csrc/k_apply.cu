@@ -211,83 +211,120 @@ __global__ void __launch_bounds__(256) k_sweep_leaf(const FactDesc* __restrict__
 #define FS_WARPS 8
 #define FS_K (2 * FIFA_CAP_MAX * SW_RHS_MAX)  // stride of one CTA's partial in `part`
 
-// Shared scratch carved after v: three FS_WARPS x K arrays, K = 2 cap SW_RHS_MAX.
+// Sum over rows [a0, a1) of Bl[col][p] * xs[j][p - S] for K outputs
+// o = (unit, c, j) described by fn(o, &a0, &a1, &col, &j) (col < 0: skip);
+// results to out[o].  Threads take (output, row chunk) pairs; chunk partials
+// are combined in a fixed order.
+template <typename TB, typename F>
+__device__ void tile_dots(int K, const TB* __restrict__ Bl, int64_t n, const double* xs, int rows, int S, F fn,
+                        double* red, double* out) {
+  const int nt = blockDim.x;
+  const int nch = K >= nt ? 1 : nt / K;
+  for (int o0 = 0; o0 < K; o0 += nt) {
+    const int kk = min(nt, K - o0);
+    const int ch = nch == 1 ? 0 : threadIdx.x / kk;
+    const int o = o0 + (nch == 1 ? threadIdx.x : threadIdx.x % kk);
+    double acc = 0.0;
+    if ((nch == 1 && threadIdx.x < kk) || (nch > 1 && ch < nch)) {
+      int a0, a1, col, j;
+      fn(o, a0, a1, col, j);
+      if (col >= 0) {
+        const TB* b = Bl + (size_t)col * n;
+        const double* xj = xs + (size_t)j * rows - S;
+        for (int p = a0 + ch; p < a1; p += nch) acc += to_d(b[p]) * xj[p];
+      }
+    }
+    __syncthreads();
+    if (nch > 1) {
+      if (ch < nch) red[ch * kk + (threadIdx.x % kk)] = acc;
+      __syncthreads();
+      if ((int)threadIdx.x < kk) {
+        double v = 0.0;
+        for (int q = 0; q < nch; ++q) v += red[q * kk + threadIdx.x];
+        out[o0 + threadIdx.x] = v;
+      }
+    } else if ((int)threadIdx.x < kk) {
+      out[o] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+#define FS_BUF 512  // doubles of node projections (and of op(Z) p) per batch
+
+// Shared scratch carved after v.
 struct FsShared {
-  double* wpart;  // per-warp partial projections / reduction scratch
-  double* pv;     // per node group: projection p
-  double* tv;     // per node group: t = op(Z) p
-  int K;
+  double* pj;             // FS_BUF: projections p of a batch of nodes
+  double* tv;             // FS_BUF: t = op(Z) p of the batch
+  double* red;            // 256 reduction partials
+  unsigned short* lmap;   // rows: local leaf of each row
 };
 
-// One level >= ls inside CTA c: the level's nodes in c's subtree, a group of
-// wpn warps per node (one warp per node once there are >= 8 nodes).
+// One level >= ls inside CTA c (rows [S, S + R)): the level's nodes in c's
+// subtree in batches whose projections fit FS_BUF; each batch takes one pass of
+// dot products (output-major, no cross-lane FP64 reductions), t = op(Z) p per
+// node, and the row update v += Q t.
 template <typename T>
 __device__ void fs_local_level(const FactDesc* __restrict__ Fd, int l, int ls, int c, double* vs, int rows, int S,
-                               int nrhs, int zsel, int zt, FsShared& sh) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cap = Fd->cap, ld2 = 2 * cap;
+                               int R, int nrhs, int zsel, int zt, FsShared& sh) {
+  const int L = Fd->L, cap = Fd->cap, ld2 = 2 * cap;
   const int64_t n = Fd->n;
+  const int* bnd = Fd->bnd;
   const int nsub = 1 << (l - ls), i0 = c << (l - ls);
-  const int wpn = nsub >= FS_WARPS ? 1 : FS_WARPS / nsub;
-  const int groups = FS_WARPS / wpn, g = warp / wpn, wr = warp % wpn;
   const T* Qb = (const T*)Fd->Q + (size_t)l * cap * n;
-  for (int base = 0; base < nsub; base += groups) {
-    const int li = base + g;
-    int r = 0, s = 0, h = 0, e = 0, nid = 0;
-    if (li < nsub) {
-      nid = node_id(l, i0 + li);
-      r = Fd->rank[nid];
-      node_range(Fd->bnd, l, i0 + li, s, h, e);
+  int rmax = 0;
+  for (int q = 0; q < nsub; ++q) rmax = max(rmax, Fd->rank[node_id(l, i0 + q)]);
+  if (rmax == 0) return;
+  const int per = 2 * rmax * nrhs;  // entries per node: (side, a, j)
+  const int nb = max(1, FS_BUF / per);
+  for (int b0 = 0; b0 < nsub; b0 += nb) {
+    const int bn = min(nb, nsub - b0);
+    tile_dots(bn * per, Qb, n, vs, rows, S,
+              [&](int o, int& a0, int& a1, int& col, int& j) {
+                const int node = o / per, rem = o % per, side = rem / (rmax * nrhs), aj = rem % (rmax * nrhs);
+                const int a = aj / nrhs;
+                j = aj % nrhs;
+                int s0, h0, e0;
+                node_range(bnd, l, i0 + b0 + node, s0, h0, e0);
+                a0 = side ? h0 : s0;
+                a1 = side ? e0 : h0;
+                col = a < Fd->rank[node_id(l, i0 + b0 + node)] ? a : -1;
+              },
+              sh.red, sh.pj);
+    for (int k = threadIdx.x; k < bn * per; k += blockDim.x) {
+      const int node = k / per, rem = k % per, sa = rem / nrhs, j = rem % nrhs;
+      const int side = sa / rmax, a = sa % rmax;
+      const int nid = node_id(l, i0 + b0 + node);
+      const int r = Fd->rank[nid];
+      double acc = 0.0;
+      if (a < r) {
+        const double* Z = (zsel ? Fd->Zi : Fd->Zf) + (size_t)nid * ld2 * ld2;
+        const int row = side * r + a;
+        const double* pn = sh.pj + node * per;
+        for (int bb = 0; bb < 2 * r; ++bb) {
+          const int bs = bb >= r ? 1 : 0, ba = bb - bs * r;
+          acc += (zt ? Z[bb * ld2 + row] : Z[row * ld2 + bb]) * pn[(bs * rmax + ba) * nrhs + j];
+        }
+      }
+      sh.tv[k] = acc;
     }
-    // partial projections over this warp's slice of the node's rows
-    for (int side = 0; side < 2 && r > 0; ++side) {
-      const int a0 = side ? h : s, a1 = side ? e : h;
+    __syncthreads();
+    for (int p = S + (int)threadIdx.x; p < S + R; p += blockDim.x) {
+      const int node = ((int)sh.lmap[p - S] >> (L - l)) - b0;
+      if (node < 0 || node >= bn) continue;
+      const int gi = i0 + b0 + node;
+      const int r = Fd->rank[node_id(l, gi)];
+      int s0, h0, e0;
+      node_range(bnd, l, gi, s0, h0, e0);
+      const double* tn = sh.tv + node * per + (p < h0 ? 0 : rmax) * nrhs;
+      double acc0 = 0.0, acc1 = 0.0;
       for (int a = 0; a < r; ++a) {
-        const T* Qc = Qb + (size_t)a * n;
-        double acc0 = 0.0, acc1 = 0.0;
-        for (int p = a0 + wr * 32 + lane; p < a1; p += wpn * 32) {
-          const double q = to_d(Qc[p]);
-          acc0 += q * vs[p - S];
-          if (nrhs > 1) acc1 += q * vs[rows + p - S];
-        }
-        acc0 = warp_sum(acc0);
-        if (nrhs > 1) acc1 = warp_sum(acc1);
-        if (lane == 0) {
-          sh.wpart[warp * sh.K + (side * r + a) * nrhs] = acc0;
-          if (nrhs > 1) sh.wpart[warp * sh.K + (side * r + a) * nrhs + 1] = acc1;
-        }
+        const double q = to_d(Qb[(size_t)a * n + p]);
+        acc0 += q * tn[a * nrhs];
+        if (nrhs > 1) acc1 += q * tn[a * nrhs + 1];
       }
-    }
-    __syncthreads();
-    const int K = 2 * r * nrhs;
-    if (r > 0 && wr == 0) {  // group leader: sum the group's partials, t = op(Z) p
-      for (int k = lane; k < K; k += 32) {
-        double acc = 0.0;
-        for (int w = 0; w < wpn; ++w) acc += sh.wpart[(warp + w) * sh.K + k];
-        sh.pv[g * sh.K + k] = acc;
-      }
-      __syncwarp();
-      const double* Z = (zsel ? Fd->Zi : Fd->Zf) + (size_t)nid * ld2 * ld2;
-      for (int k = lane; k < K; k += 32) {
-        const int a = k / nrhs, j = k % nrhs;
-        double acc = 0.0;
-        for (int b = 0; b < 2 * r; ++b) acc += (zt ? Z[b * ld2 + a] : Z[a * ld2 + b]) * sh.pv[g * sh.K + b * nrhs + j];
-        sh.tv[g * sh.K + k] = acc;
-      }
-    }
-    __syncthreads();
-    if (r > 0) {
-      for (int p = s + wr * 32 + lane; p < e; p += wpn * 32) {
-        const int off = p < h ? 0 : r;
-        double acc0 = 0.0, acc1 = 0.0;
-        for (int a = 0; a < r; ++a) {
-          const double q = to_d(Qb[(size_t)a * n + p]);
-          acc0 += q * sh.tv[g * sh.K + (off + a) * nrhs];
-          if (nrhs > 1) acc1 += q * sh.tv[g * sh.K + (off + a) * nrhs + 1];
-        }
-        vs[p - S] += acc0;
-        if (nrhs > 1) vs[rows + p - S] += acc1;
-      }
+      vs[p - S] += acc0;
+      if (nrhs > 1) vs[rows + p - S] += acc1;
     }
     __syncthreads();
   }
@@ -331,7 +368,7 @@ __device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, 
   // right half for the right child, summed in a fixed order
   const int K = 2 * r * nrhs, half = 1 << (span - 1), c0 = i << span;
   const int nch = blockDim.x / K;
-  double* red = sh.wpart;
+  double* red = sh.red;
   if ((int)threadIdx.x < nch * K) {
     const int k = threadIdx.x % K, ch = threadIdx.x / K;
     const int sd = (k / nrhs) >= r ? 1 : 0, kk = k - sd * r * nrhs;
@@ -344,14 +381,14 @@ __device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, 
   if ((int)threadIdx.x < K) {
     double acc = 0.0;
     for (int ch = 0; ch < nch; ++ch) acc += red[ch * K + threadIdx.x];
-    sh.pv[threadIdx.x] = acc;
+    sh.pj[threadIdx.x] = acc;
   }
   __syncthreads();
   if ((int)threadIdx.x < K) {
     const int a = threadIdx.x / nrhs, j = threadIdx.x % nrhs;
     const double* Z = (zsel ? Fd->Zi : Fd->Zf) + (size_t)nid * ld2 * ld2;
     double acc = 0.0;
-    for (int b = 0; b < 2 * r; ++b) acc += (zt ? Z[b * ld2 + a] : Z[a * ld2 + b]) * sh.pv[b * nrhs + j];
+    for (int b = 0; b < 2 * r; ++b) acc += (zt ? Z[b * ld2 + a] : Z[a * ld2 + b]) * sh.pj[b * nrhs + j];
     sh.tv[threadIdx.x] = acc;
   }
   __syncthreads();
@@ -396,30 +433,37 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const FactDesc* __restrict_
                                                      unsigned int* __restrict__ bar, int* __restrict__ abort_flag) {
   extern __shared__ double vs[];
   FsShared sh;
-  sh.K = max(2 * Fd->cap * SW_RHS_MAX, 32);  // FS_WARPS * K >= blockDim: the reduction scratch
-  sh.wpart = vs + (size_t)rows * nrhs;
-  sh.pv = sh.wpart + FS_WARPS * sh.K;
-  sh.tv = sh.pv + FS_WARPS * sh.K;
+  sh.pj = vs + (size_t)rows * nrhs;
+  sh.tv = sh.pj + FS_BUF;
+  sh.red = sh.tv + FS_BUF;
+  sh.lmap = (unsigned short*)(sh.red + 256);
   const int c = blockIdx.x;
   const int L = Fd->L;
   const int64_t n = Fd->n;
   const int S = Fd->bnd[bnd_off(ls) + c], E = Fd->bnd[bnd_off(ls) + c + 1];
   for (int j = 0; j < nrhs; ++j)
     for (int p = threadIdx.x; p < E - S; p += blockDim.x) vs[(size_t)j * rows + p] = v[(size_t)j * n + S + p];
+  {
+    const int nl = 1 << (L - ls), first = c << (L - ls);
+    for (int q = threadIdx.x; q < nl; q += blockDim.x) {
+      const int s0 = Fd->bnd[bnd_off(L) + first + q], e0 = Fd->bnd[bnd_off(L) + first + q + 1];
+      for (int p = s0; p < e0; ++p) sh.lmap[p - S] = (unsigned short)q;
+    }
+  }
   __syncthreads();
   const int zsel = (mode == 1 || mode == 3) ? 1 : 0, zt = (mode == 2 || mode == 3) ? 1 : 0;
   unsigned int phase = 0;
   bool ok = true;
   if (mode == 1 || mode == 2) {  // leaves first, then the levels upward
     fs_leaves<T>(Fd, ls, c, vs, rows, S, nrhs, mode);
-    for (int l = L - 1; l >= ls; --l) fs_local_level<T>(Fd, l, ls, c, vs, rows, S, nrhs, zsel, zt, sh);
+    for (int l = L - 1; l >= ls; --l) fs_local_level<T>(Fd, l, ls, c, vs, rows, S, E - S, nrhs, zsel, zt, sh);
     for (int l = ls - 1; l >= 0 && ok; --l)
       ok = fs_global_level<T>(Fd, l, ls, c, vs, rows, S, E, nrhs, zsel, zt, part, l & 1, bar, phase, abort_flag, sh);
   } else {  // the levels downward, then the leaves
     for (int l = 0; l < ls && ok; ++l)
       ok = fs_global_level<T>(Fd, l, ls, c, vs, rows, S, E, nrhs, zsel, zt, part, l & 1, bar, phase, abort_flag, sh);
     if (ok) {
-      for (int l = ls; l < L; ++l) fs_local_level<T>(Fd, l, ls, c, vs, rows, S, nrhs, zsel, zt, sh);
+      for (int l = ls; l < L; ++l) fs_local_level<T>(Fd, l, ls, c, vs, rows, S, E - S, nrhs, zsel, zt, sh);
       fs_leaves<T>(Fd, ls, c, vs, rows, S, nrhs, mode);
     }
   }
@@ -429,7 +473,8 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const FactDesc* __restrict_
 }
 
 size_t sweep_fused_smem(int rows, int nrhs, int cap) {
-  return sizeof(double) * ((size_t)rows * nrhs + 3 * FS_WARPS * std::max(2 * cap * SW_RHS_MAX, 32));
+  (void)cap;
+  return sizeof(double) * ((size_t)rows * nrhs + 2 * FS_BUF + 256) + sizeof(unsigned short) * (size_t)rows;
 }
 
 int sweep_fused_coresident(int prec, int rows, int cap) {
@@ -490,45 +535,6 @@ cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, i
 #define MV_PROJ_BUF 1024                       // doubles of node projections per batch
 #define MV_PART_STRIDE (FIFA_CAP_MAX * SW_RHS_MAX)  // one CTA's partial of one level
 
-// Sum over rows [a0, a1) of bases[l][cc][p] * xs[j][p - S] for K outputs
-// o = (unit, c, j) described by fn(o, &a0, &a1, &col, &j) (col < 0: skip);
-// results to out[o].  Threads take (output, row chunk) pairs; chunk partials
-// are combined in a fixed order.
-template <typename F>
-__device__ void mv_dots(int K, const double* __restrict__ Bl, int64_t n, const double* xs, int rows, int S, F fn,
-                        double* red, double* out) {
-  const int nt = blockDim.x;
-  const int nch = K >= nt ? 1 : nt / K;
-  for (int o0 = 0; o0 < K; o0 += nt) {
-    const int kk = min(nt, K - o0);
-    const int ch = nch == 1 ? 0 : threadIdx.x / kk;
-    const int o = o0 + (nch == 1 ? threadIdx.x : threadIdx.x % kk);
-    double acc = 0.0;
-    if ((nch == 1 && threadIdx.x < kk) || (nch > 1 && ch < nch)) {
-      int a0, a1, col, j;
-      fn(o, a0, a1, col, j);
-      if (col >= 0) {
-        const double* b = Bl + (size_t)col * n;
-        const double* xj = xs + (size_t)j * rows - S;
-        for (int p = a0 + ch; p < a1; p += nch) acc += b[p] * xj[p];
-      }
-    }
-    __syncthreads();
-    if (nch > 1) {
-      if (ch < nch) red[ch * kk + (threadIdx.x % kk)] = acc;
-      __syncthreads();
-      if ((int)threadIdx.x < kk) {
-        double v = 0.0;
-        for (int q = 0; q < nch; ++q) v += red[q * kk + threadIdx.x];
-        out[o0 + threadIdx.x] = v;
-      }
-    } else if ((int)threadIdx.x < kk) {
-      out[o] = acc;
-    }
-    __syncthreads();
-  }
-}
-
 template <int RPT>
 __global__ void __launch_bounds__(256, RPT <= 8 ? 4 : 2) k_mv_fused(const HmatDesc* __restrict__ Hd, const double* __restrict__ x, int nrhs,
                                                   double* __restrict__ y, int ls, int rows, double* __restrict__ part,
@@ -583,7 +589,7 @@ __global__ void __launch_bounds__(256, RPT <= 8 ? 4 : 2) k_mv_fused(const HmatDe
     const int nb = max(1, MV_PROJ_BUF / per);
     for (int b0 = 0; b0 < nsub; b0 += nb) {
       const int bn = min(nb, nsub - b0);
-      mv_dots(bn * per, Bl, n, xs, rows, S,
+      tile_dots(bn * per, Bl, n, xs, rows, S,
               [&](int o, int& a0, int& a1, int& col, int& j) {
                 const int node = o / per, rem = o % per, side = rem / (rmax * nrhs), cj = rem % (rmax * nrhs);
                 const int cc = cj / nrhs;
@@ -627,7 +633,7 @@ __global__ void __launch_bounds__(256, RPT <= 8 ? 4 : 2) k_mv_fused(const HmatDe
   for (int l = 0; l < ls; ++l) {
     const double* Bl = Hd->bases + (size_t)l * cap * n;
     const int r = Hd->rank[node_id(l, c >> (ls - l))];
-    mv_dots(r * nrhs, Bl, n, xs, rows, S,
+    tile_dots(r * nrhs, Bl, n, xs, rows, S,
             [&](int o, int& a0, int& a1, int& col, int& j) {
               a0 = S;
               a1 = E;

@@ -278,11 +278,18 @@ __device__ void gram_tiled(const T* __restrict__ Xb, int64_t n, int r, int a0, i
     __syncthreads();
     if (active) part[gidx * np + o] = acc;
     __syncthreads();
-    for (int q = t; q < np; q += blockDim.x) {
-      double v = 0.0;
-      for (int g = 0; g < ng; ++g) v += part[g * np + q];
-      Gp[q0 + q] = v;
+    // pairwise tree over the ng group partials, all outputs at once (few FP64
+    // instructions per output instead of ng serial adds)
+    for (int w = ng; w > 1;) {
+      const int hw = (w + 1) / 2;
+      for (int i = t; i < (w - hw) * np; i += blockDim.x) {
+        const int g = i / np, q = i % np;
+        part[g * np + q] += part[(g + hw) * np + q];
+      }
+      w = hw;
+      __syncthreads();
     }
+    for (int q = t; q < np; q += blockDim.x) Gp[q0 + q] = part[q];
     __syncthreads();
   }
 }
@@ -323,11 +330,16 @@ __device__ void proj_tiled(const T* __restrict__ Qb, T* const* Bp, int w, int64_
   __syncthreads();
   if (active) part[gidx * np + o] = (double)acc;
   __syncthreads();
-  for (int q = t; q < np; q += blockDim.x) {
-    double v = 0.0;
-    for (int g = 0; g < ng; ++g) v += part[g * np + q];
-    Pm[(q / w) * LV_W + q % w] = v;
+  for (int gw = ng; gw > 1;) {  // pairwise tree over the group partials
+    const int hw = (gw + 1) / 2;
+    for (int i = t; i < (gw - hw) * np; i += blockDim.x) {
+      const int g = i / np, q = i % np;
+      part[g * np + q] += part[(g + hw) * np + q];
+    }
+    gw = hw;
+    __syncthreads();
   }
+  for (int q = t; q < np; q += blockDim.x) Pm[(q / w) * LV_W + q % w] = part[q];
   __syncthreads();
 }
 
@@ -335,7 +347,7 @@ __device__ void proj_tiled(const T* __restrict__ Qb, T* const* Bp, int w, int64_
 // dimension RB (less shared memory and registers, more CTAs per SM); RB == 0:
 // nodes with r > RLO, leading dimension cap.
 template <typename T, int RB, int RLO>
-__global__ void __launch_bounds__(256, RB == 4 ? 4 : 2)
+__global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
     k_level(const FactDesc* __restrict__ Fd, int lvl, int G, double* __restrict__ gpart,
             unsigned int* __restrict__ bar, int* __restrict__ abort_flag, int skip_le) {
   extern __shared__ double sm[];
@@ -760,10 +772,10 @@ static cudaError_t launch_level_bucket(const FactDesc* Fd, int lvl, int nodes, i
 }
 
 template <typename T>
-static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, int G, int G4, int cap, double* part,
+static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, const int* G, int cap, double* part,
                                   unsigned int* bar, int bar_stride, int* abort_flag, int side_max, cudaStream_t st) {
   int skip = -1;
-  if (G == 1 && side_max <= 256) {
+  if (G[0] == 1 && side_max <= 256) {  // (nodes this small are never split over CTAs)
     // small nodes staged in (static, < 48 KB) shared memory: rank buckets (0,4]
     // and (4,8] for sides of <= 128 rows, (0,4] for sides of <= 256 rows
     if (side_max <= 128) {
@@ -781,18 +793,18 @@ static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, int G,
   // bucket, then (16, cap]; a node's CTAs skip the launches of other buckets
   // (buckets entirely below the small kernels' ranks are not launched)
   cudaError_t e = cudaSuccess;
-  if (skip < 4) e = launch_level_bucket<T, 4, -1>(Fd, lvl, nodes, G4, cap, part, bar, abort_flag, skip, st);
+  if (skip < 4) e = launch_level_bucket<T, 4, -1>(Fd, lvl, nodes, G[0], cap, part, bar, abort_flag, skip, st);
   if (e == cudaSuccess && cap > 4 && skip < 16)
-    e = launch_level_bucket<T, 16, 4>(Fd, lvl, nodes, G, cap, part, bar + bar_stride, abort_flag, skip, st);
+    e = launch_level_bucket<T, 16, 4>(Fd, lvl, nodes, G[1], cap, part, bar + bar_stride, abort_flag, skip, st);
   if (e == cudaSuccess && cap > 16)
-    e = launch_level_bucket<T, 0, 16>(Fd, lvl, nodes, G, cap, part, bar + 2 * bar_stride, abort_flag, skip, st);
+    e = launch_level_bucket<T, 0, 16>(Fd, lvl, nodes, G[2], cap, part, bar + 2 * bar_stride, abort_flag, skip, st);
   return e;
 }
 
-cudaError_t launch_level(const FactDesc* Fd, int prec, int lvl, int nodes, int G, int G4, int cap, double* part,
+cudaError_t launch_level(const FactDesc* Fd, int prec, int lvl, int nodes, const int* G, int cap, double* part,
                          unsigned int* bar, int bar_stride, int* abort_flag, int side_max, cudaStream_t st) {
-  return prec ? launch_level_t<float>(Fd, lvl, nodes, G, G4, cap, part, bar, bar_stride, abort_flag, side_max, st)
-              : launch_level_t<double>(Fd, lvl, nodes, G, G4, cap, part, bar, bar_stride, abort_flag, side_max, st);
+  return prec ? launch_level_t<float>(Fd, lvl, nodes, G, cap, part, bar, bar_stride, abort_flag, side_max, st)
+              : launch_level_t<double>(Fd, lvl, nodes, G, cap, part, bar, bar_stride, abort_flag, side_max, st);
 }
 
 template <typename T, int RB, int RLO>
@@ -806,27 +818,14 @@ static int level_bucket_per_sm(int cap) {
   return per_sm;
 }
 
-// Co-resident CTAs of the rank <= 4 level kernel (its own group size).
-int level4_max_coresident(int prec, int cap) {
+int level_bucket_coresident(int prec, int b, int cap) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms * (prec ? level_bucket_per_sm<float, 4, -1>(cap) : level_bucket_per_sm<double, 4, -1>(cap));
-}
-
-// Co-resident CTAs of the level kernels: the least over the rank buckets (a
-// group's CTAs must all be resident whichever bucket its node falls in).
-int level_max_coresident(int prec, int cap) {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int per_sm;
-  if (prec)
-    per_sm = std::min(level_bucket_per_sm<float, 4, -1>(cap),
-                      std::min(level_bucket_per_sm<float, 16, 4>(cap), level_bucket_per_sm<float, 0, 16>(cap)));
-  else
-    per_sm = std::min(level_bucket_per_sm<double, 4, -1>(cap),
-                      std::min(level_bucket_per_sm<double, 16, 4>(cap), level_bucket_per_sm<double, 0, 16>(cap)));
+  int per_sm = 0;
+  if (b == 0) per_sm = prec ? level_bucket_per_sm<float, 4, -1>(cap) : level_bucket_per_sm<double, 4, -1>(cap);
+  else if (b == 1) per_sm = prec ? level_bucket_per_sm<float, 16, 4>(cap) : level_bucket_per_sm<double, 16, 4>(cap);
+  else per_sm = prec ? level_bucket_per_sm<float, 0, 16>(cap) : level_bucket_per_sm<double, 0, 16>(cap);
   return sms * per_sm;
 }
 
