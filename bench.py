@@ -506,17 +506,24 @@ def factor_work(n, leaf, ranks):
         r_l = ranks[(1 << l) - 1:(1 << (l + 1)) - 1]
         canc_leaf += np.repeat(r_l, nl >> l)
     flops = float(np.sum(leaves_m ** 3) / 3.0 + np.sum(leaves_m ** 2 * canc_leaf))
+    per_level = [flops]  # leaves first, then levels L-1 .. 0
     # levels: CholeskyQR2 (two Gram passes + two row transforms) and the ancestor update
+    lv = []
     for l in range(L):
         r_l = ranks[(1 << l) - 1:(1 << (l + 1)) - 1].astype(np.float64)
         m = n / (1 << l)
         canc = np.zeros_like(r_l)
         for j in range(l):
             canc += np.repeat(ranks[(1 << j) - 1:(1 << (j + 1)) - 1], 1 << (l - j))
-        flops += float(np.sum(4.0 * r_l * r_l * m + 4.0 * r_l * canc * m))
+        f = float(np.sum(4.0 * r_l * r_l * m + 4.0 * r_l * canc * m))
+        lv.append(f)
+        flops += f
+    per_level += lv[::-1]
+    # one fused W^-1 sweep with two right-hand sides: the leaf factors (lower
+    # triangles), the bases once, v read and written once
     sweep_bytes = 8.0 * (np.sum(leaves_m ** 2) / 2.0 + n * float(sum(
-        ranks[(1 << l) - 1:(1 << (l + 1)) - 1].mean() for l in range(L)))) + 16.0 * n * 2 * (L + 1)
-    return flops, sweep_bytes, L
+        ranks[(1 << l) - 1:(1 << (l + 1)) - 1].mean() for l in range(L)))) + 2 * 8.0 * n * 2
+    return flops, sweep_bytes, L, per_level
 
 
 def roofline_probe(ctx, fifa, torch, stream, xd, n, leaf, nugget):
@@ -552,13 +559,15 @@ def roofline_probe(ctx, fifa, torch, stream, xd, n, leaf, nugget):
         ms_sw = e0.elapsed_time(e1) / 5
         fifa.fifa_destroy_fact(ctx.h, F)
         fifa.fifa_destroy_hmat(ctx.h, H)
-    flops, sweep_bytes, L = factor_work(n, leaf, ranks)
+    flops, sweep_bytes, L, per_level = factor_work(n, leaf, ranks)
     peak_fp64 = 1.20  # measured FP64 FMA throughput of this GB300 (independent DFMA chains)
     achieved = flops / (ms * 1e-3) / 1e12
     return {"bound": "alu", "op": "FP64 HODLR factorization of C~ (leaf Cholesky + TRSM, per-level CholeskyQR2, "
                                   "capacitance, ancestor update)",
             "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s", "frac": achieved / peak_fp64,
             "traffic": None, "ms": ms, "flops": flops, "rank_mean": float(ranks.mean()), "levels": L,
+            "gflops_leaves_then_levels_deep_to_top": [round(f / 1e9, 4) for f in per_level],
+            "rank_mean_per_level": [round(float(ranks[(1 << l) - 1:(1 << (l + 1)) - 1].mean()), 2) for l in range(L)],
             "peak_source": "measured FP64 FMA throughput",
             "sweep": {"bound": "hbm", "op": "W^-1 sweep, 2 right-hand sides", "ms": ms_sw,
                       "achieved": sweep_bytes / (ms_sw * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",

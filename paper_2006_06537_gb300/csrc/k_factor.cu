@@ -696,6 +696,340 @@ __global__ void __launch_bounds__(128) k_level_small(const FactDesc* __restrict_
   }
 }
 
+// ---------------------------------------------------------------------------
+// Multi-node small-level kernel: NPC nodes of one level per CTA (sides of at
+// most MS rows, rank <= R), the same arithmetic as k_level_small.  Every step
+// is spread over the nodes: the per-node dense algebra (Cholesky, triangular
+// inverse, capacitance) runs one thread per node and side, and the row and
+// column work runs over all the CTA's nodes at once, so few lanes idle while
+// FP64 instructions issue.
+// ---------------------------------------------------------------------------
+#define LM_W 4  // ancestor columns per chunk
+
+// Serial upper Cholesky of A (r x r, ld) in place by one thread, pivots from
+// one rsqrt each (as blk_chol_upper); rinv receives the reciprocal pivots.
+__device__ inline bool thr_chol_upper(double* A, int ld, int r, double* rinv, double clamp) {
+  double dmax = 0.0;
+  for (int k = 0; k < r; ++k) dmax = fmax(dmax, A[k * ld + k]);
+  const double floor_v = clamp * dmax;
+  bool ok = true;
+  for (int k = 0; k < r; ++k) {
+    double d = A[k * ld + k];
+    if (clamp > 0.0 && !(d > floor_v)) d = floor_v > 0.0 ? floor_v : 1.0;
+    if (!(d > 0.0)) {
+      ok = false;
+      d = 1.0;
+    }
+    const double rs = rsqrt(d);
+    A[k * ld + k] = d * rs;
+    rinv[k] = rs;
+    for (int j = k + 1; j < r; ++j) A[k * ld + j] *= rs;
+    for (int i = k + 1; i < r; ++i)
+      for (int j = i; j < r; ++j) A[i * ld + j] -= A[k * ld + i] * A[k * ld + j];
+  }
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < i; ++j) A[i * ld + j] = 0.0;
+  return ok;
+}
+
+// Ri = R^-1 (upper, r x r) by one thread, with the reciprocal pivots rinv.
+__device__ inline void thr_triinv_upper(const double* R, int ldr, const double* rinv, double* Ri, int ldi, int r) {
+  for (int j = 0; j < r; ++j)
+    for (int i = r - 1; i >= 0; --i) {
+      double acc = (i == j) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= j; ++k) acc -= R[i * ldr + k] * Ri[k * ldi + j];
+      Ri[i * ldi + j] = (i <= j) ? acc * rinv[i] : 0.0;
+    }
+}
+
+template <int R, int MS, int NPC>
+struct LmLayout {
+  static constexpr int R2 = 2 * R;
+  static constexpr size_t xs = (size_t)NPC * 2 * R * MS;  // doubles
+  static constexpr size_t mats = (size_t)NPC * 2 * R * R;  // Gm / Ri / R1 / rinv (doubles each)
+  static constexpr size_t ruv = (size_t)NPC * R * R;       // RU / RV
+  static constexpr size_t sm = (size_t)NPC * R2 * R2;      // S / Si
+  static constexpr size_t pm = (size_t)NPC * R2 * LM_W;    // Pm / Tm
+  static constexpr size_t doubles = xs + 3 * mats + (size_t)NPC * 2 * R + 2 * ruv + 2 * sm + pm;
+  static size_t bytes(int elt) {
+    return doubles * sizeof(double) + (size_t)NPC * LM_W * 2 * MS * elt + pm * elt +
+           (size_t)NPC * (FIFA_LEVELS_MAX + 1 + LM_W + 8) * sizeof(int) + 64;
+  }
+};
+
+template <typename T, int R, int MS, int NPC>
+__global__ void __launch_bounds__(256) k_level_multi(const FactDesc* __restrict__ Fd, int lvl, int nodes) {
+  using LY = LmLayout<R, MS, NPC>;
+  constexpr int R2 = 2 * R;
+  extern __shared__ double smd[];
+  double* Xs = smd;                       // [j][side][c][p]
+  double* Gm = Xs + LY::xs;               // [j][side][R*R]
+  double* Ri = Gm + LY::mats;
+  double* R1 = Ri + LY::mats;
+  double* rv = R1 + LY::mats;             // [j][side][R] reciprocal pivots
+  double* RU = rv + NPC * 2 * R;          // [j][R*R]
+  double* RV = RU + LY::ruv;
+  double* S = RV + LY::ruv;               // [j][R2*R2]
+  double* Si = S + LY::sm;
+  double* Pm = Si + LY::sm;               // [j][R2][LM_W]
+  T* Bs = (T*)(Pm + LY::pm);              // [j][LM_W][2 MS]
+  T* Tm = Bs + (size_t)NPC * LM_W * 2 * MS;  // [j][R2][LM_W]
+  int* ib = (int*)(Tm + LY::pm);
+  int* rpre = ib;                          // [j][LEVELS_MAX + 1]
+  int* ccode = rpre + NPC * (FIFA_LEVELS_MAX + 1);  // [j][LM_W]
+  int* info = ccode + NPC * LM_W;          // [j][8]: r, s, h, e, active, ok
+
+  const int cap = Fd->cap, nleaf = Fd->nleaf;
+  const int64_t n = Fd->n;
+  const int* bnd = Fd->bnd;
+  T* Qall = (T*)Fd->Q;
+  T* Qb = Qall + (size_t)lvl * cap * n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int b0 = blockIdx.x * NPC;
+
+  if (tid < NPC) {
+    const int bi = b0 + tid;
+    int* in = info + tid * 8;
+    in[4] = 0;
+    in[5] = 1;
+    if (bi < nodes) {
+      const int nid = node_id(lvl, bi);
+      const int r = Fd->rank[nid];
+      int s, h, e;
+      node_range(bnd, lvl, bi, s, h, e);
+      in[0] = r;
+      in[1] = s;
+      in[2] = h;
+      in[3] = e;
+      if (r == 0) Fd->ld_parts[nleaf + nid] = 0.0;
+      in[4] = (r > 0 && r <= R) ? 1 : 0;  // larger ranks: another launch takes the node
+    }
+  }
+  __syncthreads();
+  // stage the bases of every node's two sides (FP64 during the QR)
+  for (int t = tid; t < NPC * 2 * R * MS; t += nt) {
+    const int j = t / (2 * R * MS), rem = t % (2 * R * MS), side = rem / (R * MS), c = (rem / MS) % R, p = rem % MS;
+    const int* in = info + j * 8;
+    double v = 0.0;
+    if (in[4] && c < in[0]) {
+      const int a0 = side ? in[2] : in[1], m = side ? in[3] - in[2] : in[2] - in[1];
+      if (p < m) v = (double)Qb[(size_t)c * n + a0 + p];
+    }
+    Xs[t] = v;
+  }
+  __syncthreads();
+  const double cg = clamp_gram<T>();
+  for (int pass = 0; pass < 2; ++pass) {
+    // Gram entries (j, side, a <= b), one thread each, serial over the side's rows
+    constexpr int NPAIR = R * (R + 1) / 2;
+    for (int t = tid; t < NPC * 2 * NPAIR; t += nt) {
+      const int js = t / NPAIR, q = t % NPAIR, j = js / 2, side = js % 2;
+      const int* in = info + j * 8;
+      const int r = in[0];
+      if (!in[4]) continue;
+      int a, b;
+      pair_decode(q, R, a, b);
+      if (b >= r) continue;
+      const int m = side ? in[3] - in[2] : in[2] - in[1];
+      const double* X = Xs + (size_t)js * R * MS;
+      double acc = 0.0;
+      for (int p = 0; p < m; ++p) acc += X[a * MS + p] * X[b * MS + p];
+      Gm[js * R * R + a * R + b] = acc;
+      Gm[js * R * R + b * R + a] = acc;
+    }
+    __syncthreads();
+    // Cholesky, R1 / R = R2 R1, inverse: one thread per (node, side)
+    if (tid < NPC * 2) {
+      const int js = tid, j = js / 2, side = js % 2;
+      int* in = info + j * 8;
+      if (in[4]) {
+        const int r = in[0];
+        double* G = Gm + js * R * R;
+        if (!thr_chol_upper(G, R, r, rv + js * R, cg)) atomicAnd(&in[5], 0);
+        if (pass == 0) {
+          for (int t = 0; t < R * R; ++t) R1[js * R * R + t] = G[t];
+        } else {
+          double* Rs = (side ? RV : RU) + j * R * R;
+          for (int i = 0; i < R; ++i)
+            for (int jj = 0; jj < R; ++jj) {
+              double v = 0.0;
+              if (i < r && jj < r && i <= jj)
+                for (int k = i; k <= jj; ++k) v += G[i * R + k] * R1[js * R * R + k * R + jj];
+              Rs[i * R + jj] = v;
+            }
+        }
+        thr_triinv_upper(G, R, rv + js * R, Ri + js * R * R, R, r);
+      }
+    }
+    __syncthreads();
+    // X <- X Ri, one thread per row (rounded to the storage precision)
+    for (int t = tid; t < NPC * 2 * MS; t += nt) {
+      const int js = t / MS, p = t % MS, j = js / 2, side = js % 2;
+      const int* in = info + j * 8;
+      if (!in[4]) continue;
+      const int r = in[0], m = side ? in[3] - in[2] : in[2] - in[1];
+      if (p >= m) continue;
+      double* X = Xs + (size_t)js * R * MS;
+      const double* Rij = Ri + js * R * R;
+      double xr[R];
+#pragma unroll
+      for (int c = 0; c < R; ++c) xr[c] = c < r ? X[c * MS + p] : 0.0;
+#pragma unroll
+      for (int c = 0; c < R; ++c)
+        if (c < r) {
+          double v = 0.0;
+#pragma unroll
+          for (int a = 0; a <= c; ++a) v += xr[a] * Rij[a * R + c];
+          X[c * MS + p] = (double)(T)v;
+        }
+    }
+    __syncthreads();
+  }
+  // orthonormal bases back to global memory
+  for (int t = tid; t < NPC * 2 * R * MS; t += nt) {
+    const int j = t / (2 * R * MS), rem = t % (2 * R * MS), side = rem / (R * MS), c = (rem / MS) % R, p = rem % MS;
+    const int* in = info + j * 8;
+    if (!in[4] || c >= in[0]) continue;
+    const int a0 = side ? in[2] : in[1], m = side ? in[3] - in[2] : in[2] - in[1];
+    if (p < m) Qb[(size_t)c * n + a0 + p] = (T)Xs[t];
+  }
+  // capacitance S = I + R X R^T, L_S = chol(S) = R_S^T, one thread per node
+  if (tid < NPC) {
+    const int j = tid;
+    int* in = info + j * 8;
+    if (in[4]) {
+      const int r = in[0], r2 = 2 * r;
+      const double* ru = RU + j * R * R;
+      const double* rvv = RV + j * R * R;
+      double* Sj = S + j * R2 * R2;
+      for (int a = 0; a < r2; ++a)
+        for (int b = 0; b < r2; ++b) {
+          double v = (a == b) ? 1.0 : 0.0;
+          if (a < r && b >= r) {
+            for (int k = 0; k < r; ++k) v += ru[a * R + k] * rvv[(b - r) * R + k];
+          } else if (a >= r && b < r) {
+            for (int k = 0; k < r; ++k) v += rvv[(a - r) * R + k] * ru[b * R + k];
+          }
+          Sj[a * R2 + b] = v;
+        }
+      double srv[R2];
+      if (!thr_chol_upper(Sj, R2, r2, srv, clamp_cap<T>())) in[5] = 0;
+      double ls = 0.0;
+      for (int k = 0; k < r2; ++k) ls += log(Sj[k * R2 + k]);
+      thr_triinv_upper(Sj, R2, srv, Si + j * R2 * R2, R2, r2);
+      const int nid = node_id(lvl, b0 + j), ld2 = 2 * cap;
+      double* Zf = Fd->Zf + (size_t)nid * ld2 * ld2;
+      double* Zi = Fd->Zi + (size_t)nid * ld2 * ld2;
+      for (int a = 0; a < r2; ++a)
+        for (int b = 0; b < r2; ++b) {
+          const double d = (a == b) ? 1.0 : 0.0;
+          Zf[a * ld2 + b] = (a >= b ? Sj[b * R2 + a] : 0.0) - d;
+          Zi[a * ld2 + b] = (a >= b ? Si[j * R2 * R2 + b * R2 + a] : 0.0) - d;
+        }
+      Fd->ld_parts[nleaf + nid] = ls;
+      if (!in[5]) atomicOr(Fd->status, FIFA_DEV_NOT_SPD);
+      // ancestor columns of this node: prefix sums of the ancestor ranks
+      int* rp = rpre + j * (FIFA_LEVELS_MAX + 1);
+      int c = 0;
+      for (int a = 0; a < lvl; ++a) {
+        rp[a] = c;
+        c += Fd->rank[node_id(a, (b0 + j) >> (lvl - a))];
+      }
+      rp[lvl] = c;
+    }
+  }
+  __syncthreads();
+  if (lvl == 0) return;
+  int nmax = 0;
+  for (int j = 0; j < NPC; ++j)
+    if (info[j * 8 + 4]) nmax = max(nmax, rpre[j * (FIFA_LEVELS_MAX + 1) + lvl]);
+  // B <- B + Q (L_S^-1 - I) Q^T B for every ancestor column, LM_W at a time
+  for (int c0 = 0; c0 < nmax; c0 += LM_W) {
+    if (tid < NPC * LM_W) {
+      const int j = tid / LM_W, w = tid % LM_W;
+      const int* rp = rpre + j * (FIFA_LEVELS_MAX + 1);
+      int code = -1;
+      if (info[j * 8 + 4] && c0 + w < rp[lvl]) {
+        const int c = c0 + w;
+        int a = 0;
+        while (rp[a + 1] <= c) ++a;
+        code = (a << 8) | (c - rp[a]);
+      }
+      ccode[tid] = code;
+    }
+    __syncthreads();
+    for (int t = tid; t < NPC * LM_W * 2 * MS; t += nt) {
+      const int j = t / (LM_W * 2 * MS), w = (t / (2 * MS)) % LM_W, p = t % (2 * MS);
+      const int code = ccode[j * LM_W + w];
+      const int* in = info + j * 8;
+      T v = (T)0;
+      if (code >= 0 && p < in[3] - in[1])
+        v = Qall[((size_t)(code >> 8) * cap + (code & 255)) * n + in[1] + p];
+      Bs[t] = v;
+    }
+    __syncthreads();
+    // P[a][w] = Q^T B (rows a < r from the left child, r <= a < 2r from the right)
+    for (int t = tid; t < NPC * R2 * LM_W; t += nt) {
+      const int j = t / (R2 * LM_W), a = (t / LM_W) % R2, w = t % LM_W;
+      const int* in = info + j * 8;
+      const int r = in[0];
+      T acc = (T)0;
+      if (in[4] && ccode[j * LM_W + w] >= 0 && a < 2 * r) {
+        const int side = a >= r, c = side ? a - r : a;
+        const int m = side ? in[3] - in[2] : in[2] - in[1], off = side ? in[2] - in[1] : 0;
+        const double* X = Xs + ((size_t)(j * 2 + side) * R + c) * MS;
+        const T* B = Bs + ((size_t)j * LM_W + w) * 2 * MS + off;
+        for (int p = 0; p < m; ++p) acc += (T)X[p] * B[p];
+      }
+      Pm[t] = (double)acc;
+    }
+    __syncthreads();
+    // T = (L_S^-1 - I) P, in the node's compact 2r layout
+    for (int t = tid; t < NPC * R2 * LM_W; t += nt) {
+      const int j = t / (R2 * LM_W), a = (t / LM_W) % R2, w = t % LM_W;
+      const int* in = info + j * 8;
+      const int r = in[0];
+      double v = 0.0;
+      if (in[4] && a < 2 * r) {
+        // a is the compact index of the 2r x 2r factor (a < r: left child, else right)
+        const double* Sij = Si + j * R2 * R2;
+        const double* P = Pm + (size_t)j * R2 * LM_W;
+        v = -P[a * LM_W + w];
+        for (int b = 0; b <= a; ++b) v += Sij[b * R2 + a] * P[b * LM_W + w];
+      }
+      Tm[t] = (T)v;
+    }
+    __syncthreads();
+    // B += Q T, one thread per (node, column, row), written back
+    for (int t = tid; t < NPC * LM_W * 2 * MS; t += nt) {
+      const int j = t / (LM_W * 2 * MS), w = (t / (2 * MS)) % LM_W, p = t % (2 * MS);
+      const int code = ccode[j * LM_W + w];
+      const int* in = info + j * 8;
+      const int mu = in[2] - in[1], mn = in[3] - in[1];
+      if (code < 0 || p >= mn) continue;
+      const int r = in[0], side = p >= mu, pp = side ? p - mu : p, toff = side ? r : 0;
+      const double* X = Xs + (size_t)(j * 2 + side) * R * MS;
+      const T* Tj = Tm + (size_t)j * R2 * LM_W;
+      T acc = Bs[t];
+      for (int a = 0; a < r; ++a) acc += (T)X[a * MS + pp] * Tj[(toff + a) * LM_W + w];
+      Qall[((size_t)(code >> 8) * cap + (code & 255)) * n + in[1] + p] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int R, int MS, int NPC>
+static cudaError_t launch_level_multi(const FactDesc* Fd, int lvl, int nodes, cudaStream_t st) {
+  const size_t smem = LmLayout<R, MS, NPC>::bytes(sizeof(T));
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_level_multi<T, R, MS, NPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_level_multi<T, R, MS, NPC><<<(nodes + NPC - 1) / NPC, 256, smem, st>>>(Fd, lvl, nodes);
+  return cudaGetLastError();
+}
+
 __global__ void k_logdet_reduce(const FactDesc* __restrict__ Fd) {
   __shared__ double red[40];
   const int cnt = Fd->nleaf + (1 << Fd->L) - 1;
@@ -779,7 +1113,11 @@ static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, const 
     // small nodes staged in (static, < 48 KB) shared memory: rank buckets (0,4]
     // and (4,8] for sides of <= 128 rows, (0,4] for sides of <= 256 rows
     if (side_max <= 128) {
-      k_level_small<T, 4, -1, 128, 8><<<nodes, 128, 0, st>>>(Fd, lvl);
+      // rank <= 4: several nodes per CTA; rank 5..8: one node per CTA
+      cudaError_t e0 = side_max <= 32   ? launch_level_multi<T, 4, 32, 8>(Fd, lvl, nodes, st)
+                       : side_max <= 64 ? launch_level_multi<T, 4, 64, 4>(Fd, lvl, nodes, st)
+                                        : launch_level_multi<T, 4, 128, 2>(Fd, lvl, nodes, st);
+      if (e0 != cudaSuccess) return e0;
       k_level_small<T, 8, 4, 128, 8><<<nodes, 128, 0, st>>>(Fd, lvl);
       skip = 8;
     } else {
