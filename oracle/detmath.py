@@ -4,14 +4,17 @@ The ACA pivots must be bit-identical between this oracle and the GPU, so the
 kernel entries feeding them must be bit-identical too.  Library ``exp``
 functions differ in their last bit between platforms, so both sides evaluate
 ``det_exp``: a fixed sequence of IEEE-754 binary64 multiplications and
-additions (no fused multiply-add), defined here from the textbook method:
+additions (no fused multiply-add), defined here from the textbook method
+(Tang's table-driven exponential):
 
-* Cody & Waite (1980) argument reduction: x = k ln2 + r with k = rint(x / ln2),
-  ln2 split as LN2_HI + LN2_LO where LN2_HI keeps only the leading 32 significand
-  bits of ln2 so that k * LN2_HI is exact for |k| < 2**21;
-* the Taylor series of e**r truncated after r**13/13! (|r| <= ln2/2, truncation
-  error below 2e-18 relative), evaluated by Horner's rule highest power first;
-* scaling by 2**k, built exactly as a power of two.
+* argument reduction x = (32 m + j) ln2/32 + r with k = 32 m + j = rint(x 32/ln2),
+  0 <= j < 32, ln2/32 split as HI + LO where HI keeps only the leading 32
+  significand bits so that k * HI is exact for |k| < 2**21 (Cody & Waite);
+* e**x = 2**m 2**(j/32) e**r with 2**(j/32) from a 32-entry table of correctly
+  rounded values (computed here in 60-digit decimal arithmetic) and
+  e**r = 1 + q, q = r(1 + r/2 + ... + r**5/6!) (|r| <= ln2/64, truncation
+  below 4e-18 relative) by Horner's rule highest power first;
+* the result t + t q with t = 2**(j/32) 2**m built exactly (exponent field).
 
 Inputs below -708 return exactly 0.0 (the true value is below 3.3e-308, and
 this cut keeps every nonzero result a normal number).
@@ -52,22 +55,38 @@ def _ln2_split():
 
 LN2_HI, LN2_LO = _ln2_split()
 INV_LN2 = float(1 / Decimal(2).ln())
+EXP_TABLE_N = 32
+# ln2/32 split (exact divisions by 32 of the ln2 split) and 32/ln2
+LN2N_HI, LN2N_LO = LN2_HI / EXP_TABLE_N, LN2_LO / EXP_TABLE_N
+INV_LN2N = INV_LN2 * EXP_TABLE_N
+
+
+def _exp2_table():
+    """2**(j/32), j = 0..31, correctly rounded to binary64 from 60-digit decimals."""
+    getcontext().prec = 60
+    return np.array([float(Decimal(2) ** (Decimal(j) / EXP_TABLE_N)) for j in range(EXP_TABLE_N)])
+
+
+EXP2_TABLE = _exp2_table()
 # 1/j! correctly rounded; j! is exact in binary64 for j <= 18.
-TAYLOR = [1.0 / math.factorial(j) for j in range(14)]
+TAYLOR = [1.0 / math.factorial(j) for j in range(7)]
 EXP_MIN_ARG = -708.0
 
 
 def det_exp(x):
     """Elementwise e**x by the fixed operation sequence described in the module doc."""
     x = np.asarray(x, dtype=np.float64)
-    k = np.rint(x * INV_LN2)
-    r = (x - k * LN2_HI) - k * LN2_LO
-    p = np.full_like(x, TAYLOR[13])
-    for j in range(12, -1, -1):
-        p = p * r + TAYLOR[j]
-    kk = np.where(x < EXP_MIN_ARG, 0, k).astype(np.int64)
-    scale = ((kk + 1023) << 52).view(np.float64)
-    out = p * scale
+    k = np.rint(x * INV_LN2N)
+    r = (x - k * LN2N_HI) - k * LN2N_LO
+    q = np.full_like(x, TAYLOR[6])
+    for j in range(5, 0, -1):
+        q = q * r + TAYLOR[j]
+    q = q * r
+    ki = np.where(x < EXP_MIN_ARG, 0, k).astype(np.int64)
+    j = ki & (EXP_TABLE_N - 1)
+    m = ki >> 5
+    t = (EXP2_TABLE[j].view(np.int64) + (m << 52)).view(np.float64)
+    out = t + t * q
     return np.where(x < EXP_MIN_ARG, 0.0, out)
 
 

@@ -90,30 +90,41 @@ __device__ __forceinline__ int node_of_row(const int* bnd, int l, int p) {
 //   LN2_HI: ln 2 rounded to binary64 then truncated to 32 significand bits
 //   LN2_LO: (ln 2 - LN2_HI) rounded to binary64;  INV_LN2: 1/ln 2 rounded.
 // ---------------------------------------------------------------------------
+// 2^(j/32), j = 0..31, correctly rounded (Tang's table-driven exponential).
+static __device__ const double kExp2Tab[32] = {
+    0x1.0000000000000p+0, 0x1.059b0d3158574p+0, 0x1.0b5586cf9890fp+0, 0x1.11301d0125b51p+0,
+    0x1.172b83c7d517bp+0, 0x1.1d4873168b9aap+0, 0x1.2387a6e756238p+0, 0x1.29e9df51fdee1p+0,
+    0x1.306fe0a31b715p+0, 0x1.371a7373aa9cbp+0, 0x1.3dea64c123422p+0, 0x1.44e086061892dp+0,
+    0x1.4bfdad5362a27p+0, 0x1.5342b569d4f82p+0, 0x1.5ab07dd485429p+0, 0x1.6247eb03a5585p+0,
+    0x1.6a09e667f3bcdp+0, 0x1.71f75e8ec5f74p+0, 0x1.7a11473eb0187p+0, 0x1.82589994cce13p+0,
+    0x1.8ace5422aa0dbp+0, 0x1.93737b0cdc5e5p+0, 0x1.9c49182a3f090p+0, 0x1.a5503b23e255dp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b7f76f2fb5e47p+0, 0x1.c199bdd85529cp+0, 0x1.cb720dcef9069p+0,
+    0x1.d5818dcfba487p+0, 0x1.dfc97337b9b5fp+0, 0x1.ea4afa2a490dap+0, 0x1.f50765b6e4540p+0};
+
+// Deterministic e^x: x = (32 m + j) ln2/32 + r, k = rint(32 x / ln2) (ln2/32
+// split so that k * HI is exact), e^x = 2^m 2^(j/32) (1 + q) with
+// q = r (1 + r/2 + ... + r^5/6!) by Horner's rule, returned as t + t q with
+// t = 2^(j/32) 2^m built exactly.  Separate IEEE products and sums only (no
+// fused multiply-add), the same sequence as the CPU reference; x < -708 -> 0.
 __device__ __forceinline__ double det_exp(double x) {
   if (!(x >= -708.0)) return x != x ? x : 0.0;
-  const double INV_LN2 = 0x1.71547652b82fep+0;
-  const double LN2_HI = 0x1.62e42fee00000p-1;
-  const double LN2_LO = 0x1.a39ef35793c76p-33;
-  double k = rint(__dmul_rn(x, INV_LN2));
-  double r = __dsub_rn(__dsub_rn(x, __dmul_rn(k, LN2_HI)), __dmul_rn(k, LN2_LO));
-  double p = 1.0 / 6227020800.0;                      // 1/13!
-  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 479001600.0);  // 1/12!
-  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 39916800.0);
-  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 3628800.0);
-  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 362880.0);
-  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 40320.0);
-  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 5040.0);
-  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 720.0);
-  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 120.0);
-  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 24.0);
-  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 6.0);
-  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 2.0);
-  p = __dadd_rn(__dmul_rn(p, r), 1.0);
-  p = __dadd_rn(__dmul_rn(p, r), 1.0);
-  long long kk = (long long)k;
-  double sc = __longlong_as_double((kk + 1023) << 52);
-  return __dmul_rn(p, sc);
+  const double INV_LN2N = 0x1.71547652b82fep+5;
+  const double LN2N_HI = 0x1.62e42fee00000p-6;
+  const double LN2N_LO = 0x1.a39ef35793c76p-38;
+  const double k = rint(__dmul_rn(x, INV_LN2N));
+  const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(k, LN2N_HI)), __dmul_rn(k, LN2N_LO));
+  double q = 1.0 / 720.0;
+  q = __dadd_rn(__dmul_rn(q, r), 1.0 / 120.0);
+  q = __dadd_rn(__dmul_rn(q, r), 1.0 / 24.0);
+  q = __dadd_rn(__dmul_rn(q, r), 1.0 / 6.0);
+  q = __dadd_rn(__dmul_rn(q, r), 0.5);
+  q = __dadd_rn(__dmul_rn(q, r), 1.0);
+  q = __dmul_rn(q, r);
+  const long long ki = (long long)k;
+  const unsigned long long tb = (unsigned long long)__double_as_longlong(__ldg(&kExp2Tab[ki & 31])) +
+                                ((unsigned long long)(ki >> 5) << 52);
+  const double t = __longlong_as_double((long long)tb);
+  return __dadd_rn(t, __dmul_rn(t, q));
 }
 
 // Unit-variance kernel entry k(xa, xb), bit-identical to the CPU reference.

@@ -33,6 +33,34 @@ def test_det_exp_special_values():
     assert int(bits) & ((1 << 21) - 1) == 0
     getcontext().prec = 50
     assert abs(Decimal(detmath.LN2_HI) + Decimal(detmath.LN2_LO) - Decimal(2).ln()) < Decimal("2e-26")
+    # the ln2/32 split is the ln2 split scaled by an exact power of two, and 32/ln2 is correctly rounded
+    assert detmath.LN2N_HI * 32 == detmath.LN2_HI and detmath.LN2N_LO * 32 == detmath.LN2_LO
+    inv = Decimal(32) / Decimal(2).ln()
+    assert abs(Decimal(detmath.INV_LN2N) - inv) <= Decimal(np.spacing(detmath.INV_LN2N)) / 2
+
+
+def test_exp2_table_against_independent_values():
+    t = detmath.EXP2_TABLE
+    assert t[0] == 1.0
+    assert t[16] == math.sqrt(2.0)          # IEEE square root is correctly rounded
+    assert t[8] == math.sqrt(math.sqrt(2.0)) or abs(t[8] - 2 ** 0.25) <= np.spacing(t[8])
+    for j in range(32):
+        ref = 2.0 ** (j / 32)                # libm pow: within an ulp of the correctly rounded value
+        assert abs(t[j] - ref) <= np.spacing(ref), j
+        if j:
+            assert abs(t[j] * t[32 - j] - 2.0) <= 4 * np.spacing(2.0), j
+    assert np.all(np.diff(t) > 0)
+
+
+def test_det_exp_near_reduction_boundaries():
+    # arguments at and next to multiples of ln2/32, where r changes sign and j wraps
+    k = np.arange(-32685, 1)
+    x0 = k * (math.log(2.0) / 32)
+    x = np.concatenate([x0, np.nextafter(x0, -np.inf), np.nextafter(x0, np.inf)])
+    x = x[(x <= 0) & (x >= -708)]
+    y = detmath.det_exp(x)
+    ref = np.exp(x)
+    assert (np.abs(y - ref) / np.spacing(ref)).max() <= 1.0
 
 
 @pytest.mark.parametrize("kind", [detmath.KERNEL_SE, detmath.KERNEL_MATERN52])

@@ -108,7 +108,12 @@ def test_matvec_and_shift_scale():
     np.testing.assert_allclose(hodlr.matvec(H, v), A @ v, rtol=0, atol=1e-12 * np.abs(A @ v).max())
     s = 37.5
     M = hodlr.shift_scale(H, s)
-    np.testing.assert_allclose(hodlr.dense(M), s * A + np.eye(len(x)), rtol=0, atol=4 * np.spacing(s * np.abs(A).max()))
+    # an off-diagonal entry is a rank-r dot product, formed as (s U) V^T in the
+    # view and s (U V^T) here: the two roundings differ by up to ~r ulps of the
+    # largest entry (dot-product error bound gamma_r), plus the scale and shift
+    rmax = max(H.rank(l, i) for l in range(H.tree.L) for i in range(1 << l)) if H.tree.L else 0
+    np.testing.assert_allclose(hodlr.dense(M), s * A + np.eye(len(x)), rtol=0,
+                               atol=(rmax + 4) * np.spacing(s * np.abs(A).max()))
 
 
 def test_single_leaf_reduces_to_dense_cholesky():
