@@ -1109,21 +1109,16 @@ template <typename T>
 static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, const int* G, int cap, double* part,
                                   unsigned int* bar, int bar_stride, int* abort_flag, int side_max, cudaStream_t st) {
   int skip = -1;
-  if (G[0] == 1 && side_max <= 256) {  // (nodes this small are never split over CTAs)
-    // small nodes staged in (static, < 48 KB) shared memory: rank buckets (0,4]
-    // and (4,8] for sides of <= 128 rows, (0,4] for sides of <= 256 rows
-    if (side_max <= 128) {
-      // rank <= 4: several nodes per CTA; rank 5..8: one node per CTA
-      cudaError_t e0 = side_max <= 32   ? launch_level_multi<T, 4, 32, 8>(Fd, lvl, nodes, st)
-                       : side_max <= 64 ? launch_level_multi<T, 4, 64, 4>(Fd, lvl, nodes, st)
-                                        : launch_level_multi<T, 4, 128, 2>(Fd, lvl, nodes, st);
-      if (e0 != cudaSuccess) return e0;
-      k_level_small<T, 8, 4, 128, 8><<<nodes, 128, 0, st>>>(Fd, lvl);
-      skip = 8;
-    } else {
-      k_level_small<T, 4, -1, 256, 4><<<nodes, 128, 0, st>>>(Fd, lvl);
-      skip = 4;
-    }
+  if (G[0] == 1 && side_max <= 128) {  // (nodes this small are never split over CTAs)
+    // small nodes: rank <= 4 several nodes per CTA, rank 5..8 one node per CTA
+    // (static shared memory); larger nodes take the tiled bucket kernels below,
+    // whose output-major Gram and projection passes use the lanes better
+    cudaError_t e0 = side_max <= 32   ? launch_level_multi<T, 4, 32, 8>(Fd, lvl, nodes, st)
+                     : side_max <= 64 ? launch_level_multi<T, 4, 64, 4>(Fd, lvl, nodes, st)
+                                      : launch_level_multi<T, 4, 128, 2>(Fd, lvl, nodes, st);
+    if (e0 != cudaSuccess) return e0;
+    k_level_small<T, 8, 4, 128, 8><<<nodes, 128, 0, st>>>(Fd, lvl);
+    skip = 8;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
