@@ -5,8 +5,9 @@
 
 // ---------------------------------------------------------------------------
 // Leaf assembly: leaves[leaf](a, b) = k(x_a, x_b) + nugget [a == b], padding 0.
-// One CTA per leaf.  Kernel entries are evaluated once per unordered pair and
-// mirrored through a shared-memory tile so both stores stay coalesced.
+// One CTA per leaf.  Kernel entries are evaluated once per unordered pair:
+// diagonal tiles over their lower triangle, off-diagonal tiles mirrored through
+// a shared-memory tile so both stores stay coalesced.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_leaf_assemble(const HmatDesc* __restrict__ Hd) {
   const int leaf = blockIdx.x;
@@ -22,8 +23,28 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(const HmatDesc* __restric
   __syncthreads();
   const int nt = (Bm + 31) / 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  // diagonal 32 x 32 tiles: entries (a, b) with a >= b only, mirrored (the
+  // kernel is symmetric bit for bit: fl(xa - xb) = -fl(xb - xa))
+  for (int bd = 0; bd < nt; ++bd) {
+    for (int t = threadIdx.x; t < 32 * 33 / 2; t += blockDim.x) {
+      int ia = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+      if ((ia + 1) * (ia + 2) / 2 <= t) ++ia;
+      if (ia * (ia + 1) / 2 > t) --ia;
+      const int ib = t - ia * (ia + 1) / 2;
+      const int a = 32 * bd + ia, b = 32 * bd + ib;
+      double v = 0.0;
+      if (a < m && b < m) {
+        v = kern_entry(kind, kc, xs[a], xs[b]);
+        if (a == b) v = __dadd_rn(v, nug);
+      }
+      if (a < Bm && b < Bm) {
+        D[(size_t)b * Bm + a] = v;
+        D[(size_t)a * Bm + b] = v;
+      }
+    }
+  }
   for (int bj = 0; bj < nt; ++bj) {
-    for (int bi = bj; bi < nt; ++bi) {
+    for (int bi = bj + 1; bi < nt; ++bi) {
       // tile rows a in [32 bi, +32), cols b in [32 bj, +32): entry (a, b)
       for (int yy = ty; yy < 32; yy += 8) {
         int a = 32 * bi + tx, b = 32 * bj + yy;
@@ -36,12 +57,10 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(const HmatDesc* __restric
         tile[yy][tx] = v;
       }
       __syncthreads();
-      if (bi != bj) {
-        // mirror: entry (b, a) for b in tile cols, a in tile rows -> column a, row b
-        for (int yy = ty; yy < 32; yy += 8) {
-          int b = 32 * bj + tx, a = 32 * bi + yy;
-          if (a < Bm && b < Bm) D[(size_t)a * Bm + b] = tile[tx][yy];
-        }
+      // mirror: entry (b, a) for b in tile cols, a in tile rows -> column a, row b
+      for (int yy = ty; yy < 32; yy += 8) {
+        int b = 32 * bj + tx, a = 32 * bi + yy;
+        if (a < Bm && b < Bm) D[(size_t)a * Bm + b] = tile[tx][yy];
       }
       __syncthreads();
     }

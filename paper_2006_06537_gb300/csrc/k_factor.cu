@@ -144,7 +144,9 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
 // reductions over rows use the tiled output-major helpers below; small dense
 // algebra (r <= cap) runs in shared memory.
 // ---------------------------------------------------------------------------
-#define LV_W 8   // ancestor columns per update chunk
+// Ancestor columns per update chunk (the same for every rank bucket: 16 for the
+// rank <= 4 kernel measured slower, its accumulators spill).
+#define LEVEL_W(RB) 8
 #define LV_RED 64
 
 template <typename T, int RB>
@@ -181,21 +183,21 @@ __device__ void rowmul_pass(T* __restrict__ Xb, int64_t n, int r, int a0, int a1
   __syncthreads();
 }
 
-// Rows [a0, a1): B_j[p] += sum_a Q[a][p] Tm[a * LV_W + j].
-template <typename T>
+// Rows [a0, a1): B_j[p] += sum_a Q[a][p] Tm[a * W + j] (W columns per chunk).
+template <typename T, int W>
 __device__ void update_pass(const T* __restrict__ Qb, T* const* Bp, int w, int64_t n, int r, int a0, int a1,
                             const T* Tm) {
   for (int p = a0 + threadIdx.x; p < a1; p += blockDim.x) {
-    T acc[LV_W];
+    T acc[W];
 #pragma unroll
-    for (int j = 0; j < LV_W; ++j) acc[j] = j < w ? Bp[j][p] : (T)0;
+    for (int j = 0; j < W; ++j) acc[j] = j < w ? Bp[j][p] : (T)0;
     for (int a = 0; a < r; ++a) {
       const T q = Qb[(size_t)a * n + p];
 #pragma unroll
-      for (int j = 0; j < LV_W; ++j) acc[j] += q * Tm[a * LV_W + j];
+      for (int j = 0; j < W; ++j) acc[j] += q * Tm[a * W + j];
     }
 #pragma unroll
-    for (int j = 0; j < LV_W; ++j)
+    for (int j = 0; j < W; ++j)
       if (j < w) Bp[j][p] = acc[j];
   }
 }
@@ -235,7 +237,7 @@ __device__ inline bool group_reduce(double* dst, const double* src_local, int co
 // sums are combined by one short shared-memory loop per output.  FP64
 // instructions go to products of nonzero entries only.
 // ---------------------------------------------------------------------------
-#define LV_TR 64
+#define LV_TR 256  // rows per staged tile (fewer barriers per row)
 #define LV_TRP (LV_TR + 1)
 
 __device__ __forceinline__ void pair_decode(int o, int r, int& a, int& b) {
@@ -305,8 +307,8 @@ __device__ void gram_unpack(const double* Gp, int r, double* G, int ldg) {
   __syncthreads();
 }
 
-// Pm[a * LV_W + j] = sum over rows [a0, a1) of Q[a][p] B_j[p], products in the storage precision.
-template <typename T>
+// Pm[a * W + j] = sum over rows [a0, a1) of Q[a][p] B_j[p], products in the storage precision.
+template <typename T, int W>
 __device__ void proj_tiled(const T* __restrict__ Qb, T* const* Bp, int w, int64_t n, int r, int a0, int a1,
                            double* tile, double* part, double* Pm) {
   const int np = r * w;
@@ -339,7 +341,7 @@ __device__ void proj_tiled(const T* __restrict__ Qb, T* const* Bp, int w, int64_
     gw = hw;
     __syncthreads();
   }
-  for (int q = t; q < np; q += blockDim.x) Pm[(q / w) * LV_W + q % w] = part[q];
+  for (int q = t; q < np; q += blockDim.x) Pm[(q / w) * W + q % w] = part[q];
   __syncthreads();
 }
 
@@ -370,19 +372,20 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
   const int len = e - s, rc = (len + G - 1) / G;
   const int r0 = s + min(len, g * rc), r1 = s + min(len, g * rc + rc);
   const int ldm = RB > 0 ? RB : cap;  // leading dimension of the small matrices
+  constexpr int W = LEVEL_W(RB);      // ancestor columns per update chunk
   const int cc2 = ldm * ldm;
   double* Gm = sm;
   double* Ri = Gm + cc2;
   double* R1 = Ri + cc2;
   double* RU = R1 + cc2;
   double* RV = RU + cc2;
-  double* tile = RV + cc2;                // (ldm + LV_W) x LV_TRP row tile
-  double* part = tile + (ldm + LV_W) * LV_TRP;  // 256 group partial sums
+  double* tile = RV + cc2;                // (ldm + W) x LV_TRP row tile
+  double* part = tile + (ldm + W) * LV_TRP;  // 256 group partial sums
   double* tmp = part + 256;               // LV_RED
-  double* Pm = tmp + LV_RED;              // 2ldm x LV_W
-  T* Tm = (T*)(Pm + 2 * ldm * LV_W);      // 2ldm x LV_W, storage precision
-  T** Bp = (T**)(Pm + 4 * ldm * LV_W);    // LV_W column pointers
-  int* iflag = (int*)(Bp + LV_W);
+  double* Pm = tmp + LV_RED;              // 2ldm x W
+  T* Tm = (T*)(Pm + 2 * ldm * W);      // 2ldm x W, storage precision
+  T** Bp = (T**)(Pm + 4 * ldm * W);    // W column pointers
+  int* iflag = (int*)(Bp + W);
   int* alist = iflag + 4;                 // ancestor columns (level << 8 | col)
   const size_t pstride = level_part_stride(cap);
   unsigned int phase = 0;
@@ -485,27 +488,27 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
   }
   __syncthreads();
   const int na = nanc;
-  for (int c0 = 0; c0 < na; c0 += LV_W) {
-    const int w = min(LV_W, na - c0);
-    if (threadIdx.x < LV_W) {
+  for (int c0 = 0; c0 < na; c0 += W) {
+    const int w = min(W, na - c0);
+    if (threadIdx.x < W) {
       const int code = alist[c0 + min((int)threadIdx.x, w - 1)];
       Bp[threadIdx.x] = Qall + ((size_t)(code >> 8) * cap + (code & 255)) * n;
     }
-    for (int t = threadIdx.x; t < 2 * ldm * LV_W; t += blockDim.x) Pm[t] = 0.0;
+    for (int t = threadIdx.x; t < 2 * ldm * W; t += blockDim.x) Pm[t] = 0.0;
     __syncthreads();
-    proj_tiled<T>(Qb, Bp, w, n, r, max(r0, s), min(r1, h), tile, part, Pm);
-    proj_tiled<T>(Qb, Bp, w, n, r, max(r0, h), min(r1, e), tile, part, Pm + r * LV_W);
-    if (!group_reduce(Pm, Pm, r2 * LV_W, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
-    for (int t = threadIdx.x; t < r2 * LV_W; t += blockDim.x) {
-      const int a = t / LV_W, j = t % LV_W;
+    proj_tiled<T, W>(Qb, Bp, w, n, r, max(r0, s), min(r1, h), tile, part, Pm);
+    proj_tiled<T, W>(Qb, Bp, w, n, r, max(r0, h), min(r1, e), tile, part, Pm + r * W);
+    if (!group_reduce(Pm, Pm, r2 * W, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
+    for (int t = threadIdx.x; t < r2 * W; t += blockDim.x) {
+      const int a = t / W, j = t % W;
       double acc = 0.0;
       if (j < w)
-        for (int b = 0; b < r2; ++b) acc += Zi[a * ld2 + b] * Pm[b * LV_W + j];
-      Tm[a * LV_W + j] = (T)acc;
+        for (int b = 0; b < r2; ++b) acc += Zi[a * ld2 + b] * Pm[b * W + j];
+      Tm[a * W + j] = (T)acc;
     }
     __syncthreads();
-    update_pass<T>(Qb, Bp, w, n, r, max(r0, s), min(r1, h), Tm);
-    update_pass<T>(Qb, Bp, w, n, r, max(r0, h), min(r1, e), Tm + r * LV_W);
+    update_pass<T, W>(Qb, Bp, w, n, r, max(r0, s), min(r1, h), Tm);
+    update_pass<T, W>(Qb, Bp, w, n, r, max(r0, h), min(r1, e), Tm + r * W);
     __syncthreads();
   }
 }
@@ -1049,9 +1052,9 @@ size_t leaf_factor_smem(int Bm, int L, int cap, int prec) {
   return b;
 }
 size_t level_smem(int ldm, int cap) {
-  return ((size_t)5 * ldm * ldm + (size_t)(ldm + LV_W) * LV_TRP + 256 + LV_RED + 4 * (size_t)ldm * LV_W) *
-             sizeof(double) +
-         LV_W * sizeof(void*) + (4 + (size_t)FIFA_LEVELS_MAX * cap) * sizeof(int);
+  const size_t W = LEVEL_W(ldm);
+  return ((size_t)5 * ldm * ldm + (size_t)(ldm + W) * LV_TRP + 256 + LV_RED + 4 * (size_t)ldm * W) * sizeof(double) +
+         W * sizeof(void*) + (4 + (size_t)FIFA_LEVELS_MAX * cap) * sizeof(int);
 }
 
 static int smem_optin() {
