@@ -208,10 +208,13 @@ template <typename T> __device__ __forceinline__ double clamp_gram() { return si
 template <typename T> __device__ __forceinline__ double clamp_cap() { return sizeof(T) == 4 ? 1e-6 : 0.0; }
 
 // Reduce `count` doubles of the G partials of this group (slot order fixed)
-// into dst; if G == 1 the partial already sits in dst.
+// into dst; if G == 1 the partial already sits in dst.  The G partials of each
+// output are split over the CTA's threads in chunks and the chunk sums
+// combined by a pairwise tree in `red` (>= blockDim.x doubles of shared
+// memory), so a large group costs a few loads per thread, not G serial ones.
 __device__ inline bool group_reduce(double* dst, const double* src_local, int count, int G, int g, int base,
                                     double* part, size_t pstride, unsigned int* bar, unsigned int& phase,
-                                    int* status, int* abort_flag) {
+                                    int* status, int* abort_flag, double* red) {
   if (G == 1) return true;
   // two slot sets alternate with the barrier count: a slot is rewritten only
   // after a later barrier that every reader of its previous contents has passed
@@ -220,11 +223,32 @@ __device__ inline bool group_reduce(double* dst, const double* src_local, int co
   for (int t = threadIdx.x; t < count; t += blockDim.x) mine[t] = src_local[t];
   ++phase;
   if (!group_barrier(bar + base, (unsigned)G * phase, status, abort_flag)) return false;
-  for (int t = threadIdx.x; t < count; t += blockDim.x) {
-    double v = 0.0;
-    for (int q = 0; q < G; ++q) v += __ldcg(part + (set + base + q) * pstride + t);
-    dst[t] = v;
+  const double* slots = part + (set + base) * pstride;
+  if (count >= (int)blockDim.x) {
+    for (int t = threadIdx.x; t < count; t += blockDim.x) {
+      double v = 0.0;
+      for (int q = 0; q < G; ++q) v += __ldcg(slots + (size_t)q * pstride + t);
+      dst[t] = v;
+    }
+    __syncthreads();
+    return true;
   }
+  const int nch = min(G, (int)blockDim.x / count);
+  const int t = threadIdx.x;
+  if (t < nch * count) {
+    const int o = t % count, ch = t / count;
+    double v = 0.0;
+    for (int q = ch; q < G; q += nch) v += __ldcg(slots + (size_t)q * pstride + o);
+    red[ch * count + o] = v;
+  }
+  __syncthreads();
+  for (int w = nch; w > 1;) {
+    const int hw = (w + 1) / 2;
+    for (int i = t; i < (w - hw) * count; i += blockDim.x) red[i] += red[i + hw * count];
+    w = hw;
+    __syncthreads();
+  }
+  for (int o = t; o < count; o += blockDim.x) dst[o] = red[o];
   __syncthreads();
   return true;
 }
@@ -398,7 +422,7 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
     // (the group exchanges only the r(r+1)/2 packed Gram entries, staged in Ri)
     const int npk = r * (r + 1) / 2;
     gram_tiled<T>(Qb, n, r, a0, a1, tile, part, Ri);
-    if (!group_reduce(Ri, Ri, npk, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
+    if (!group_reduce(Ri, Ri, npk, G, g, base, gpart, pstride, bar, phase, status, abort_flag, part)) return;
     gram_unpack(Ri, r, Gm, ldm);
     ok = blk_chol_upper(Gm, ldm, r, iflag, clamp_gram<T>()) && ok;
     for (int t = threadIdx.x; t < cc2; t += blockDim.x) R1[t] = Gm[t];
@@ -406,7 +430,7 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
     blk_triinv_upper(Gm, ldm, Ri, ldm, r);
     rowmul_pass<T>(Qb, n, r, a0, a1, Ri, ldm);
     gram_tiled<T>(Qb, n, r, a0, a1, tile, part, Ri);
-    if (!group_reduce(Ri, Ri, npk, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
+    if (!group_reduce(Ri, Ri, npk, G, g, base, gpart, pstride, bar, phase, status, abort_flag, part)) return;
     gram_unpack(Ri, r, Gm, ldm);
     ok = blk_chol_upper(Gm, ldm, r, iflag, clamp_gram<T>()) && ok;
     blk_triinv_upper(Gm, ldm, Ri, ldm, r);
@@ -427,7 +451,39 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
   const int r2 = 2 * r, ld2 = 2 * cap;
   double* Zf = Fd->Zf + (size_t)nid * ld2 * ld2;
   double* Zi = Fd->Zi + (size_t)nid * ld2 * ld2;
-  if (g == 0) {
+  if (g == 0 && 8 * ldm * ldm <= (ldm + W) * LV_TRP) {
+    // S and its inverse factor in shared memory (the row tile is free here),
+    // so the serial pivot chain never waits on global memory
+    double* Sm = tile;
+    double* Sim = tile + 4 * ldm * ldm;
+    for (int t = threadIdx.x; t < r2 * r2; t += blockDim.x) {
+      const int a = t / r2, b = t % r2;
+      double v = (a == b) ? 1.0 : 0.0;
+      if (a < r && b >= r) {
+        for (int k = 0; k < r; ++k) v += RU[a * ldm + k] * RV[(b - r) * ldm + k];
+      } else if (a >= r && b < r) {
+        for (int k = 0; k < r; ++k) v += RV[(a - r) * ldm + k] * RU[b * ldm + k];
+      }
+      Sm[a * r2 + b] = v;
+    }
+    __syncthreads();
+    const bool ok2 = blk_chol_upper(Sm, r2, r2, iflag, clamp_cap<T>());  // R_S (upper), L_S = R_S^T
+    double ls = 0.0;
+    for (int k = threadIdx.x; k < r2; k += blockDim.x) ls += log(Sm[k * r2 + k]);
+    ls = block_sum(ls, tmp);
+    blk_triinv_upper(Sm, r2, Sim, r2, r2);  // R_S^-1 (upper) = (L_S^-1)^T
+    for (int t = threadIdx.x; t < r2 * r2; t += blockDim.x) {
+      const int a = t / r2, b = t % r2;
+      const double dd = (a == b) ? 1.0 : 0.0;
+      Zf[a * ld2 + b] = (a >= b ? Sm[b * r2 + a] : 0.0) - dd;
+      Zi[a * ld2 + b] = (a >= b ? Sim[b * r2 + a] : 0.0) - dd;
+    }
+    if (threadIdx.x == 0) {
+      Fd->ld_parts[nleaf + nid] = ls;
+      if (!ok2) atomicOr(status, FIFA_DEV_NOT_SPD);
+    }
+    __syncthreads();
+  } else if (g == 0) {
     for (int t = threadIdx.x; t < r2 * r2; t += blockDim.x) {
       const int a = t / r2, b = t % r2;
       double v = (a == b) ? 1.0 : 0.0;
@@ -498,7 +554,7 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
     __syncthreads();
     proj_tiled<T, W>(Qb, Bp, w, n, r, max(r0, s), min(r1, h), tile, part, Pm);
     proj_tiled<T, W>(Qb, Bp, w, n, r, max(r0, h), min(r1, e), tile, part, Pm + r * W);
-    if (!group_reduce(Pm, Pm, r2 * W, G, g, base, gpart, pstride, bar, phase, status, abort_flag)) return;
+    if (!group_reduce(Pm, Pm, r2 * W, G, g, base, gpart, pstride, bar, phase, status, abort_flag, part)) return;
     for (int t = threadIdx.x; t < r2 * W; t += blockDim.x) {
       const int a = t / W, j = t % W;
       double acc = 0.0;
@@ -707,7 +763,7 @@ __global__ void __launch_bounds__(128) k_level_small(const FactDesc* __restrict_
 // column work runs over all the CTA's nodes at once, so few lanes idle while
 // FP64 instructions issue.
 // ---------------------------------------------------------------------------
-#define LM_W 4  // ancestor columns per chunk
+#define LM_W 8  // ancestor columns per chunk
 
 // Serial upper Cholesky of A (r x r, ld) in place by one thread, pivots from
 // one rsqrt each (as blk_chol_upper); rinv receives the reciprocal pivots.
@@ -1129,6 +1185,14 @@ static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, const 
   // bucket, then (16, cap]; a node's CTAs skip the launches of other buckets
   // (buckets entirely below the small kernels' ranks are not launched)
   cudaError_t e = cudaSuccess;
+  if (G[0] > 1 || G[1] > 1) {
+    // a level with CTA groups has few nodes: one launch for every rank <= 16
+    // instead of two launches that would each leave the other bucket's groups idle
+    e = launch_level_bucket<T, 16, -1>(Fd, lvl, nodes, G[1], cap, part, bar + bar_stride, abort_flag, skip, st);
+    if (e == cudaSuccess && cap > 16)
+      e = launch_level_bucket<T, 0, 16>(Fd, lvl, nodes, G[2], cap, part, bar + 2 * bar_stride, abort_flag, skip, st);
+    return e;
+  }
   if (skip < 4) e = launch_level_bucket<T, 4, -1>(Fd, lvl, nodes, G[0], cap, part, bar, abort_flag, skip, st);
   if (e == cudaSuccess && cap > 4 && skip < 16)
     e = launch_level_bucket<T, 16, 4>(Fd, lvl, nodes, G[1], cap, part, bar + bar_stride, abort_flag, skip, st);
@@ -1160,7 +1224,9 @@ int level_bucket_coresident(int prec, int b, int cap) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int per_sm = 0;
   if (b == 0) per_sm = prec ? level_bucket_per_sm<float, 4, -1>(cap) : level_bucket_per_sm<double, 4, -1>(cap);
-  else if (b == 1) per_sm = prec ? level_bucket_per_sm<float, 16, 4>(cap) : level_bucket_per_sm<double, 16, 4>(cap);
+  else if (b == 1)  // also launched as <16, -1> at levels with CTA groups
+    per_sm = prec ? std::min(level_bucket_per_sm<float, 16, 4>(cap), level_bucket_per_sm<float, 16, -1>(cap))
+                  : std::min(level_bucket_per_sm<double, 16, 4>(cap), level_bucket_per_sm<double, 16, -1>(cap));
   else per_sm = prec ? level_bucket_per_sm<float, 0, 16>(cap) : level_bucket_per_sm<double, 0, 16>(cap);
   return sms * per_sm;
 }
