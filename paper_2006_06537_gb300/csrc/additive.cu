@@ -9,9 +9,11 @@
 // Each block is a Gibbs chain on its sorted coordinate (Philox stream id k);
 // the shared sigma2 has its own small state (stream id d).  The sweep is
 // captured once in a CUDA graph and replayed.  The blocks' M~ factorizations
-// (which depend only on the hyperparameters) and their tau2 / rho updates are
-// independent across blocks: on a context with independent CTAs they are
-// captured as concurrent graph branches, one per block.
+// depend only on the hyperparameters: all d are factored in one batched pass
+// (one launch per step and tree level for every block, the blocks' descriptors
+// and scratch laid out contiguously).  On a context with independent CTAs the
+// factorizations and the blocks' tau2 / rho updates instead run as concurrent
+// graph branches, one per block.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -59,6 +61,12 @@ struct fifa_additive {
   cudaStream_t side[FIFA_ADDITIVE_MAX_D] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[FIFA_ADDITIVE_MAX_D] = {};
   bool branches = false;
+  // batched factorization of the blocks' M~ (all blocks share one plan): the
+  // blocks' M~ factor and view descriptors and their scratch are contiguous
+  FactDesc* fm_desc = nullptr;  // d
+  HmatDesc* mv_desc = nullptr;  // d
+  char* scratch = nullptr;      // d * scratch_stride
+  size_t scratch_stride = 0;
 };
 
 // Enqueue fn(k) for every block k, as concurrent branches forked from and
@@ -96,11 +104,22 @@ static fifa_status additive_sweep_enqueue(fifa_ctx* ctx, fifa_additive* A) {
   const int d = A->d;
   fifa_status st = FIFA_OK;
   // M~_k = (tau2_k / sigma2) C~_k + I and its factor for every block: they
-  // depend only on the hyperparameters, so the blocks run side by side
-  st = for_blocks(ctx, A, [&](int k) {
-    ctx->active_scratch = A->blk[k]->scratch;
-    return chain_phase_factor_m(ctx, A->blk[k]);
-  });
+  // depend only on the hyperparameters, so all blocks are factored together,
+  // one launch per tree level for all d blocks
+  if (A->fm_desc) {
+    for (int k = 0; k < d && st == FIFA_OK; ++k) {
+      fifa_chain* ch = A->blk[k];
+      if (launch_chain_make_view(ch->H[0]->dev, ch->Mv->dev, ch->dev, ctx->stream) != cudaSuccess) st = FIFA_ERR_CUDA;
+    }
+    if (st == FIFA_OK)
+      st = fact_enqueue_batched(ctx, A->blk[0]->plan, A->blk[0]->FM->host.prec, A->fm_desc, A->mv_desc, d, A->scratch,
+                                A->scratch_stride);
+  } else {
+    st = for_blocks(ctx, A, [&](int k) {
+      ctx->active_scratch = A->blk[k]->scratch;
+      return chain_phase_factor_m(ctx, A->blk[k]);
+    });
+  }
   // f_k | y - sum_{j != k} f_j, blocks in order
   for (int k = 0; k < d && st == FIFA_OK; ++k) {
     fifa_chain* ch = A->blk[k];
@@ -188,6 +207,28 @@ extern "C" fifa_status fifa_additive_create(fifa_ctx* ctx, const double* X_dev, 
       A->branches = cudaStreamCreateWithFlags(&A->side[k], cudaStreamNonBlocking) == cudaSuccess &&
                     cudaEventCreateWithFlags(&A->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
     if (!A->branches) return fail(FIFA_ERR_CUDA);
+  }
+  // contiguous M~ factor / view descriptors and scratch for the batched
+  // factorization (the graph is built later, so re-pointing is safe now)
+  if (!A->branches && d > 1) {
+    const Plan* P = A->blk[0]->plan;
+    A->scratch_stride = (P->scratch_bytes + 255) & ~(size_t)255;
+    A->fm_desc = (FactDesc*)ctx->arena.alloc(sizeof(FactDesc) * d);
+    A->mv_desc = (HmatDesc*)ctx->arena.alloc(sizeof(HmatDesc) * d);
+    A->scratch = (char*)ctx->arena.alloc(A->scratch_stride * d);
+    if (!A->fm_desc || !A->mv_desc || !A->scratch) return fail(FIFA_ERR_OOM);
+    for (int k = 0; k < d; ++k) {
+      fifa_chain* ch = A->blk[k];
+      CK(cudaMemcpyAsync(A->fm_desc + k, ch->FM->dev, sizeof(FactDesc), cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(A->mv_desc + k, ch->Mv->dev, sizeof(HmatDesc), cudaMemcpyDeviceToDevice, s));
+      CK(cudaStreamSynchronize(s));
+      ctx->arena.release(ch->FM->dev);
+      ctx->arena.release(ch->Mv->dev);
+      ctx->arena.release(ch->scratch);
+      ch->FM->dev = A->fm_desc + k;
+      ch->Mv->dev = A->mv_desc + k;
+      ch->scratch = A->scratch + (size_t)k * A->scratch_stride;
+    }
   }
   ChainDev* ptrs[FIFA_ADDITIVE_MAX_D] = {};
   for (int k = 0; k < d; ++k) ptrs[k] = A->blk[k]->dev;
@@ -338,7 +379,17 @@ extern "C" void fifa_destroy_additive(fifa_ctx* ctx, fifa_additive* A) {
   if (A->exec) cudaGraphExecDestroy(A->exec);
   if (A->graph) cudaGraphDestroy(A->graph);
   for (int k = 0; k < A->d; ++k)
-    if (A->blk[k]) fifa_destroy_chain(ctx, A->blk[k]);
+    if (A->blk[k]) {
+      if (A->fm_desc) {  // these point into the model's shared arrays, released below
+        A->blk[k]->FM->dev = nullptr;
+        A->blk[k]->Mv->dev = nullptr;
+        A->blk[k]->scratch = nullptr;
+      }
+      fifa_destroy_chain(ctx, A->blk[k]);
+    }
+  ctx->arena.release(A->fm_desc);
+  ctx->arena.release(A->mv_desc);
+  ctx->arena.release(A->scratch);
   for (int k = 0; k < FIFA_ADDITIVE_MAX_D; ++k) {
     if (A->side[k]) cudaStreamDestroy(A->side[k]);
     if (A->ev_join[k]) cudaEventDestroy(A->ev_join[k]);

@@ -647,6 +647,34 @@ fifa_status fact_enqueue(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev) {
   return FIFA_OK;
 }
 
+// Factor nprob matrices of one plan in one launch per step and tree level:
+// F0[q] from H0[q] (contiguous descriptor arrays), problem q's scratch at
+// scratch0 + q * sstride bytes.  Groups shrink to fit all problems' CTAs.
+fifa_status fact_enqueue_batched(fifa_ctx* ctx, Plan* P, int prec, FactDesc* F0, const HmatDesc* H0, int nprob,
+                                 void* scratch0, size_t sstride) {
+  void* saved = ctx->active_scratch;
+  ctx->active_scratch = scratch0;
+  Scratch S = carve(ctx, P);
+  ctx->active_scratch = saved;
+  cudaStream_t s = ctx->stream;
+  const int cap = ctx->opts.rank_cap;
+  CK(launch_prep_fact(F0, H0, P->nnodes, s, nprob));
+  CK(launch_leaf_factor(H0, F0, prec, P->nleaf, P->Bm, P->L, cap, s, nprob));
+  for (int l = P->L - 1; l >= 0; --l) {
+    int Gb[LEVEL_BUCKETS];
+    for (int b = 0; b < LEVEL_BUCKETS; ++b) Gb[b] = std::max(1, P->lvl_G[b][l] / nprob);
+    if (*std::max_element(Gb, Gb + LEVEL_BUCKETS) > 1) {
+      CK(cudaMemset2DAsync(S.lvl_bar, sstride, 0, sizeof(unsigned int) * LEVEL_BUCKETS * P->lvl_ctas_max, nprob, s));
+      CK(cudaMemset2DAsync(S.flags, sstride, 0, sizeof(int), nprob, s));
+    }
+    const int side_max = (int)(((n_of(P) + ((int64_t)1 << l) - 1) >> l) + 1) / 2;
+    CK(launch_level(F0, prec, l, 1 << l, Gb, cap, S.lvl_part, S.lvl_bar, P->lvl_ctas_max, S.flags, side_max, s, nprob,
+                    sstride));
+  }
+  CK(launch_logdet_reduce(F0, s, nprob));
+  return FIFA_OK;
+}
+
 extern "C" fifa_status fifa_factor(fifa_ctx* ctx, const fifa_hmat* A, fifa_fact** out) {
   if (!ctx || !A || !out) return FIFA_ERR_INVALID_ARG;
   *out = nullptr;

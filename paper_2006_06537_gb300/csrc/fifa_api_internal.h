@@ -98,6 +98,8 @@ fifa_status hmat_alloc(fifa_ctx* ctx, Plan* P, int kind, fifa_hmat** out);
 fifa_status hmat_assemble_enqueue(fifa_ctx* ctx, fifa_hmat* H);
 fifa_status fact_alloc(fifa_ctx* ctx, Plan* P, int prec, fifa_fact** out);
 fifa_status fact_enqueue(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev);
+fifa_status fact_enqueue_batched(fifa_ctx* ctx, Plan* P, int prec, FactDesc* F0, const HmatDesc* H0, int nprob,
+                                 void* scratch0, size_t sstride);
 fifa_status sweep_enqueue(fifa_ctx* ctx, const fifa_fact* F, int trans, int inverse, double* v, int nrhs);
 fifa_status matvec_enqueue(fifa_ctx* ctx, const fifa_hmat* A, const double* in, double* out, int nrhs);
 fifa_status solve_enqueue(fifa_ctx* ctx, const fifa_fact* F, const double* b, double* x, int nrhs, double* work,
@@ -108,7 +110,7 @@ fifa_status sample_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* W
 
 // vector kernels (k_vec.cu)
 cudaError_t launch_prep_hmat(HmatDesc* H, int nnodes, cudaStream_t st);
-cudaError_t launch_prep_fact(FactDesc* F, const HmatDesc* H, int nnodes, cudaStream_t st);
+cudaError_t launch_prep_fact(FactDesc* F, const HmatDesc* H, int nnodes, cudaStream_t st, int nprob = 1);
 cudaError_t launch_sumsq(const double* a, const double* b, int64_t n, double* part, double* out, cudaStream_t st);
 cudaError_t launch_axpy(double a, const double* x, double* y, int64_t n, cudaStream_t st);
 cudaError_t launch_dot(const double* a, const double* b, int64_t n, int nrhs, double* part, double* st, int slot,

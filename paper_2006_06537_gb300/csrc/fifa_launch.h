@@ -17,15 +17,17 @@ __host__ __device__ inline size_t level_part_stride(int cap) {
   return (size_t)(cap * cap > 2 * cap * 8 ? cap * cap : 2 * cap * 8);
 }
 cudaError_t launch_leaf_factor(const HmatDesc* Hd, const FactDesc* Fd, int prec, int nleaf, int Bm, int L, int cap,
-                               cudaStream_t st);
+                               cudaStream_t st, int nprob = 1);
 #define LEVEL_BUCKETS 3
 // Level kernels: rank buckets (.., 4], (4, 16], (16, cap] with groups of G[b]
 // CTAs; bucket b uses the barriers at bar + b * bar_stride.
+// nprob problems in one launch (grid.y): descriptor arrays, scratch sstride bytes apart.
 cudaError_t launch_level(const FactDesc* Fd, int prec, int lvl, int nodes, const int* G, int cap, double* part,
-                         unsigned int* bar, int bar_stride, int* abort_flag, int side_max, cudaStream_t st);
+                         unsigned int* bar, int bar_stride, int* abort_flag, int side_max, cudaStream_t st,
+                         int nprob = 1, size_t sstride = 0);
 // Co-resident CTAs of the level kernel of rank bucket b (0: <= 4, 1: 5..16, 2: > 16).
 int level_bucket_coresident(int prec, int b, int cap);
-cudaError_t launch_logdet_reduce(const FactDesc* Fd, cudaStream_t st);
+cudaError_t launch_logdet_reduce(const FactDesc* Fd, cudaStream_t st, int nprob = 1);
 
 #define SWEEP_RHS_MAX 2
 cudaError_t launch_sweep_level(const FactDesc* Fd, int prec, int lvl, int nodes, int G, double* v, int nrhs, double* part,

@@ -23,6 +23,8 @@
 template <typename T>
 __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict__ Hd, const FactDesc* __restrict__ Fd) {
   extern __shared__ double sm[];
+  Hd += blockIdx.y;  // problem of a batched launch (descriptor arrays)
+  Fd += blockIdx.y;
   const int leaf = blockIdx.x;
   const int L = Fd->L, Bm = Fd->Bm, cap = Fd->cap;
   const int64_t n = Fd->n;
@@ -375,8 +377,13 @@ __device__ void proj_tiled(const T* __restrict__ Qb, T* const* Bp, int w, int64_
 template <typename T, int RB, int RLO>
 __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
     k_level(const FactDesc* __restrict__ Fd, int lvl, int G, double* __restrict__ gpart,
-            unsigned int* __restrict__ bar, int* __restrict__ abort_flag, int skip_le) {
+            unsigned int* __restrict__ bar, int* __restrict__ abort_flag, int skip_le, size_t sstride) {
   extern __shared__ double sm[];
+  // problem of a batched launch: its descriptor, and its scratch sstride bytes on
+  Fd += blockIdx.y;
+  gpart = (double*)((char*)gpart + blockIdx.y * sstride);
+  bar = (unsigned int*)((char*)bar + blockIdx.y * sstride);
+  abort_flag = (int*)((char*)abort_flag + blockIdx.y * sstride);
   const int bi = blockIdx.x / G, g = blockIdx.x % G, base = blockIdx.x - g;
   const int nid = node_id(lvl, bi);
   const int cap = Fd->cap, nleaf = Fd->nleaf;
@@ -578,6 +585,7 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
 // ---------------------------------------------------------------------------
 template <typename T, int R, int RLO, int MS, int W>
 __global__ void __launch_bounds__(128) k_level_small(const FactDesc* __restrict__ Fd, int lvl) {
+  Fd += blockIdx.y;  // problem of a batched launch
   constexpr int R2 = 2 * R;
   __shared__ double Xs[2][R][MS];   // side-major basis rows (FP64 during the QR)
   __shared__ T Bs[W][2 * MS];       // ancestor-column chunk on the node's rows
@@ -818,6 +826,7 @@ struct LmLayout {
 
 template <typename T, int R, int MS, int NPC>
 __global__ void __launch_bounds__(256) k_level_multi(const FactDesc* __restrict__ Fd, int lvl, int nodes) {
+  Fd += blockIdx.y;  // problem of a batched launch
   using LY = LmLayout<R, MS, NPC>;
   constexpr int R2 = 2 * R;
   extern __shared__ double smd[];
@@ -1078,18 +1087,19 @@ __global__ void __launch_bounds__(256) k_level_multi(const FactDesc* __restrict_
 }
 
 template <typename T, int R, int MS, int NPC>
-static cudaError_t launch_level_multi(const FactDesc* Fd, int lvl, int nodes, cudaStream_t st) {
+static cudaError_t launch_level_multi(const FactDesc* Fd, int lvl, int nodes, cudaStream_t st, int nprob) {
   const size_t smem = LmLayout<R, MS, NPC>::bytes(sizeof(T));
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_level_multi<T, R, MS, NPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_level_multi<T, R, MS, NPC><<<(nodes + NPC - 1) / NPC, 256, smem, st>>>(Fd, lvl, nodes);
+  k_level_multi<T, R, MS, NPC><<<dim3((nodes + NPC - 1) / NPC, nprob), 256, smem, st>>>(Fd, lvl, nodes);
   return cudaGetLastError();
 }
 
 __global__ void k_logdet_reduce(const FactDesc* __restrict__ Fd) {
+  Fd += blockIdx.y;  // problem of a batched launch
   __shared__ double red[40];
   const int cnt = Fd->nleaf + (1 << Fd->L) - 1;
   double v = 0.0;
@@ -1126,25 +1136,28 @@ static int smem_optin() {
 }
 
 template <typename T>
-static cudaError_t launch_leaf_factor_t(const HmatDesc* Hd, const FactDesc* Fd, int nleaf, size_t smem, cudaStream_t st) {
+static cudaError_t launch_leaf_factor_t(const HmatDesc* Hd, const FactDesc* Fd, int nleaf, size_t smem, cudaStream_t st,
+                                        int nprob) {
   if (smem > (size_t)smem_optin()) return cudaErrorInvalidConfiguration;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_leaf_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_leaf_factor<T><<<nleaf, 256, smem, st>>>(Hd, Fd);
+  k_leaf_factor<T><<<dim3(nleaf, nprob), 256, smem, st>>>(Hd, Fd);
   return cudaGetLastError();
 }
 
 cudaError_t launch_leaf_factor(const HmatDesc* Hd, const FactDesc* Fd, int prec, int nleaf, int Bm, int L, int cap,
-                               cudaStream_t st) {
+                               cudaStream_t st, int nprob) {
   size_t smem = leaf_factor_smem(Bm, L, cap, prec);
-  return prec ? launch_leaf_factor_t<float>(Hd, Fd, nleaf, smem, st) : launch_leaf_factor_t<double>(Hd, Fd, nleaf, smem, st);
+  return prec ? launch_leaf_factor_t<float>(Hd, Fd, nleaf, smem, st, nprob)
+              : launch_leaf_factor_t<double>(Hd, Fd, nleaf, smem, st, nprob);
 }
 
 template <typename T, int RB, int RLO>
 static cudaError_t launch_level_bucket(const FactDesc* Fd, int lvl, int nodes, int G, int cap, double* part,
-                                       unsigned int* bar, int* abort_flag, int skip, cudaStream_t st) {
+                                       unsigned int* bar, int* abort_flag, int skip, cudaStream_t st, int nprob,
+                                       size_t sstride) {
   const size_t smem = level_smem(RB > 0 ? RB : cap, cap);
   if (smem > (size_t)smem_optin()) return cudaErrorInvalidConfiguration;
   if (smem > 48 * 1024) {
@@ -1152,7 +1165,7 @@ static cudaError_t launch_level_bucket(const FactDesc* Fd, int lvl, int nodes, i
     if (e != cudaSuccess) return e;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nodes * G);
+  cfg.gridDim = dim3(nodes * G, nprob);
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
@@ -1161,22 +1174,23 @@ static cudaError_t launch_level_bucket(const FactDesc* Fd, int lvl, int nodes, i
   attr[0].val.cooperative = G > 1 ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_level<T, RB, RLO>, Fd, lvl, G, part, bar, abort_flag, skip);
+  return cudaLaunchKernelEx(&cfg, k_level<T, RB, RLO>, Fd, lvl, G, part, bar, abort_flag, skip, sstride);
 }
 
 template <typename T>
 static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, const int* G, int cap, double* part,
-                                  unsigned int* bar, int bar_stride, int* abort_flag, int side_max, cudaStream_t st) {
+                                  unsigned int* bar, int bar_stride, int* abort_flag, int side_max, cudaStream_t st,
+                                  int nprob, size_t sstride) {
   int skip = -1;
   if (G[0] == 1 && side_max <= 128) {  // (nodes this small are never split over CTAs)
     // small nodes: rank <= 4 several nodes per CTA, rank 5..8 one node per CTA
     // (static shared memory); larger nodes take the tiled bucket kernels below,
     // whose output-major Gram and projection passes use the lanes better
-    cudaError_t e0 = side_max <= 32   ? launch_level_multi<T, 4, 32, 8>(Fd, lvl, nodes, st)
-                     : side_max <= 64 ? launch_level_multi<T, 4, 64, 4>(Fd, lvl, nodes, st)
-                                      : launch_level_multi<T, 4, 128, 2>(Fd, lvl, nodes, st);
+    cudaError_t e0 = side_max <= 32   ? launch_level_multi<T, 4, 32, 8>(Fd, lvl, nodes, st, nprob)
+                     : side_max <= 64 ? launch_level_multi<T, 4, 64, 4>(Fd, lvl, nodes, st, nprob)
+                                      : launch_level_multi<T, 4, 128, 2>(Fd, lvl, nodes, st, nprob);
     if (e0 != cudaSuccess) return e0;
-    k_level_small<T, 8, 4, 128, 8><<<nodes, 128, 0, st>>>(Fd, lvl);
+    k_level_small<T, 8, 4, 128, 8><<<dim3(nodes, nprob), 128, 0, st>>>(Fd, lvl);
     skip = 8;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1188,23 +1202,26 @@ static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, const 
   if (G[0] > 1 || G[1] > 1) {
     // a level with CTA groups has few nodes: one launch for every rank <= 16
     // instead of two launches that would each leave the other bucket's groups idle
-    e = launch_level_bucket<T, 16, -1>(Fd, lvl, nodes, G[1], cap, part, bar + bar_stride, abort_flag, skip, st);
+    e = launch_level_bucket<T, 16, -1>(Fd, lvl, nodes, G[1], cap, part, bar + bar_stride, abort_flag, skip, st, nprob, sstride);
     if (e == cudaSuccess && cap > 16)
-      e = launch_level_bucket<T, 0, 16>(Fd, lvl, nodes, G[2], cap, part, bar + 2 * bar_stride, abort_flag, skip, st);
+      e = launch_level_bucket<T, 0, 16>(Fd, lvl, nodes, G[2], cap, part, bar + 2 * bar_stride, abort_flag, skip, st, nprob, sstride);
     return e;
   }
-  if (skip < 4) e = launch_level_bucket<T, 4, -1>(Fd, lvl, nodes, G[0], cap, part, bar, abort_flag, skip, st);
+  if (skip < 4) e = launch_level_bucket<T, 4, -1>(Fd, lvl, nodes, G[0], cap, part, bar, abort_flag, skip, st, nprob, sstride);
   if (e == cudaSuccess && cap > 4 && skip < 16)
-    e = launch_level_bucket<T, 16, 4>(Fd, lvl, nodes, G[1], cap, part, bar + bar_stride, abort_flag, skip, st);
+    e = launch_level_bucket<T, 16, 4>(Fd, lvl, nodes, G[1], cap, part, bar + bar_stride, abort_flag, skip, st, nprob, sstride);
   if (e == cudaSuccess && cap > 16)
-    e = launch_level_bucket<T, 0, 16>(Fd, lvl, nodes, G[2], cap, part, bar + 2 * bar_stride, abort_flag, skip, st);
+    e = launch_level_bucket<T, 0, 16>(Fd, lvl, nodes, G[2], cap, part, bar + 2 * bar_stride, abort_flag, skip, st, nprob, sstride);
   return e;
 }
 
 cudaError_t launch_level(const FactDesc* Fd, int prec, int lvl, int nodes, const int* G, int cap, double* part,
-                         unsigned int* bar, int bar_stride, int* abort_flag, int side_max, cudaStream_t st) {
-  return prec ? launch_level_t<float>(Fd, lvl, nodes, G, cap, part, bar, bar_stride, abort_flag, side_max, st)
-              : launch_level_t<double>(Fd, lvl, nodes, G, cap, part, bar, bar_stride, abort_flag, side_max, st);
+                         unsigned int* bar, int bar_stride, int* abort_flag, int side_max, cudaStream_t st, int nprob,
+                         size_t sstride) {
+  return prec ? launch_level_t<float>(Fd, lvl, nodes, G, cap, part, bar, bar_stride, abort_flag, side_max, st, nprob,
+                                      sstride)
+              : launch_level_t<double>(Fd, lvl, nodes, G, cap, part, bar, bar_stride, abort_flag, side_max, st, nprob,
+                                       sstride);
 }
 
 template <typename T, int RB, int RLO>
@@ -1231,7 +1248,7 @@ int level_bucket_coresident(int prec, int b, int cap) {
   return sms * per_sm;
 }
 
-cudaError_t launch_logdet_reduce(const FactDesc* Fd, cudaStream_t st) {
-  k_logdet_reduce<<<1, 256, 0, st>>>(Fd);
+cudaError_t launch_logdet_reduce(const FactDesc* Fd, cudaStream_t st, int nprob) {
+  k_logdet_reduce<<<dim3(1, nprob), 256, 0, st>>>(Fd);
   return cudaGetLastError();
 }

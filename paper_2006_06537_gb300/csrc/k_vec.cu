@@ -146,6 +146,8 @@ __global__ void k_prep_hmat(HmatDesc* __restrict__ H, int nnodes) {
 }
 
 __global__ void k_prep_fact(FactDesc* __restrict__ F, const HmatDesc* __restrict__ H, int nnodes) {
+  F += blockIdx.y;  // problem of a batched launch (descriptor arrays)
+  H += blockIdx.y;
   int* dst = F->rank;
   const int* src = H->rank;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nnodes; i += gridDim.x * blockDim.x) dst[i] = src[i];
@@ -156,8 +158,8 @@ cudaError_t launch_prep_hmat(HmatDesc* H, int nnodes, cudaStream_t st) {
   k_prep_hmat<<<grid_for(nnodes > 0 ? nnodes : 1), 256, 0, st>>>(H, nnodes);
   return cudaGetLastError();
 }
-cudaError_t launch_prep_fact(FactDesc* F, const HmatDesc* H, int nnodes, cudaStream_t st) {
-  k_prep_fact<<<grid_for(nnodes > 0 ? nnodes : 1), 256, 0, st>>>(F, H, nnodes);
+cudaError_t launch_prep_fact(FactDesc* F, const HmatDesc* H, int nnodes, cudaStream_t st, int nprob) {
+  k_prep_fact<<<dim3(grid_for(nnodes > 0 ? nnodes : 1), nprob), 256, 0, st>>>(F, H, nnodes);
   return cudaGetLastError();
 }
 
