@@ -313,7 +313,7 @@ def gpu_arm(args):
     if rank == 0 and args.serve_requests > 0:
         serving = serving_leg(fifa, args.serve_requests, args.serve_slots, fifa.FIFA_FP64, 64)
     if rank == 0 and args.additive_sweeps > 0:
-        additive = additive_leg(fifa, torch, args.additive_sweeps, 64)
+        additive = additive_leg(fifa, torch, args.additive_sweeps, 32)
 
     vals = torch.tensor([per_head, e2e_s], device="cuda", dtype=torch.float64)
     if world > 1:

@@ -11,7 +11,7 @@
 // captured once in a CUDA graph and replayed.  The blocks' M~ factorizations
 // depend only on the hyperparameters: all d are factored in one batched pass
 // (one launch per step and tree level for every block, the blocks' descriptors
-// and scratch laid out contiguously).  On a context with independent CTAs the
+// and scratch laid out contiguously); so are the d proposals C~(rho'_k).  On a context with independent CTAs the
 // factorizations and the blocks' tau2 / rho updates instead run as concurrent
 // graph branches, one per block.
 #include <cuda_runtime.h>
@@ -65,6 +65,8 @@ struct fifa_additive {
   // blocks' M~ factor and view descriptors and their scratch are contiguous
   FactDesc* fm_desc = nullptr;  // d
   HmatDesc* mv_desc = nullptr;  // d
+  FactDesc* f_desc[2] = {nullptr, nullptr};  // d each: current / proposal factor of C~
+  HmatDesc* h_desc[2] = {nullptr, nullptr};  // d each: current / proposal C~
   char* scratch = nullptr;      // d * scratch_stride
   size_t scratch_stride = 0;
 };
@@ -142,14 +144,30 @@ static fifa_status additive_sweep_enqueue(fifa_ctx* ctx, fifa_additive* A) {
         launch_add_sigma2(A->g, A->blk_dev, d, ctx->stream) != cudaSuccess)
       st = FIFA_ERR_CUDA;
   }
-  // tau2_k and rho_k of every block, side by side
-  if (st == FIFA_OK)
+  // tau2_k and rho_k of every block: the proposals' factorizations batched
+  if (st == FIFA_OK && A->fm_desc) {
+    for (int k = 0; k < d && st == FIFA_OK; ++k) {
+      fifa_chain* ch = A->blk[k];
+      ctx->active_scratch = ch->scratch;
+      Scratch S = carve(ctx, ch->plan);
+      st = chain_phase_hyper_pre(ctx, ch, S);
+    }
+    if (st == FIFA_OK)
+      st = fact_enqueue_batched(ctx, A->blk[0]->plan, 0, A->f_desc[1], A->h_desc[1], d, A->scratch, A->scratch_stride);
+    for (int k = 0; k < d && st == FIFA_OK; ++k) {
+      fifa_chain* ch = A->blk[k];
+      ctx->active_scratch = ch->scratch;
+      Scratch S = carve(ctx, ch->plan);
+      st = chain_phase_hyper_post(ctx, ch, S);
+    }
+  } else if (st == FIFA_OK) {
     st = for_blocks(ctx, A, [&](int k) {
       fifa_chain* ch = A->blk[k];
       ctx->active_scratch = ch->scratch;
       Scratch S = carve(ctx, ch->plan);
       return chain_phase_hyper(ctx, ch, S);
     });
+  }
   ctx->active_scratch = nullptr;
   if (st == FIFA_ERR_CUDA) ctx->last_cuda = cudaGetLastError();
   return st;
@@ -215,18 +233,33 @@ extern "C" fifa_status fifa_additive_create(fifa_ctx* ctx, const double* X_dev, 
     A->scratch_stride = (P->scratch_bytes + 255) & ~(size_t)255;
     A->fm_desc = (FactDesc*)ctx->arena.alloc(sizeof(FactDesc) * d);
     A->mv_desc = (HmatDesc*)ctx->arena.alloc(sizeof(HmatDesc) * d);
+    for (int q = 0; q < 2; ++q) {
+      A->f_desc[q] = (FactDesc*)ctx->arena.alloc(sizeof(FactDesc) * d);
+      A->h_desc[q] = (HmatDesc*)ctx->arena.alloc(sizeof(HmatDesc) * d);
+    }
     A->scratch = (char*)ctx->arena.alloc(A->scratch_stride * d);
-    if (!A->fm_desc || !A->mv_desc || !A->scratch) return fail(FIFA_ERR_OOM);
+    if (!A->fm_desc || !A->mv_desc || !A->f_desc[0] || !A->f_desc[1] || !A->h_desc[0] || !A->h_desc[1] || !A->scratch)
+      return fail(FIFA_ERR_OOM);
     for (int k = 0; k < d; ++k) {
       fifa_chain* ch = A->blk[k];
       CK(cudaMemcpyAsync(A->fm_desc + k, ch->FM->dev, sizeof(FactDesc), cudaMemcpyDeviceToDevice, s));
       CK(cudaMemcpyAsync(A->mv_desc + k, ch->Mv->dev, sizeof(HmatDesc), cudaMemcpyDeviceToDevice, s));
+      for (int q = 0; q < 2; ++q) {
+        CK(cudaMemcpyAsync(A->f_desc[q] + k, ch->F[q]->dev, sizeof(FactDesc), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(A->h_desc[q] + k, ch->H[q]->dev, sizeof(HmatDesc), cudaMemcpyDeviceToDevice, s));
+      }
       CK(cudaStreamSynchronize(s));
       ctx->arena.release(ch->FM->dev);
       ctx->arena.release(ch->Mv->dev);
       ctx->arena.release(ch->scratch);
       ch->FM->dev = A->fm_desc + k;
       ch->Mv->dev = A->mv_desc + k;
+      for (int q = 0; q < 2; ++q) {
+        ctx->arena.release(ch->F[q]->dev);
+        ctx->arena.release(ch->H[q]->dev);
+        ch->F[q]->dev = A->f_desc[q] + k;
+        ch->H[q]->dev = A->h_desc[q] + k;
+      }
       ch->scratch = A->scratch + (size_t)k * A->scratch_stride;
     }
   }
@@ -383,12 +416,20 @@ extern "C" void fifa_destroy_additive(fifa_ctx* ctx, fifa_additive* A) {
       if (A->fm_desc) {  // these point into the model's shared arrays, released below
         A->blk[k]->FM->dev = nullptr;
         A->blk[k]->Mv->dev = nullptr;
+        for (int q = 0; q < 2; ++q) {
+          A->blk[k]->F[q]->dev = nullptr;
+          A->blk[k]->H[q]->dev = nullptr;
+        }
         A->blk[k]->scratch = nullptr;
       }
       fifa_destroy_chain(ctx, A->blk[k]);
     }
   ctx->arena.release(A->fm_desc);
   ctx->arena.release(A->mv_desc);
+  for (int q = 0; q < 2; ++q) {
+    ctx->arena.release(A->f_desc[q]);
+    ctx->arena.release(A->h_desc[q]);
+  }
   ctx->arena.release(A->scratch);
   for (int k = 0; k < FIFA_ADDITIVE_MAX_D; ++k) {
     if (A->side[k]) cudaStreamDestroy(A->side[k]);

@@ -57,30 +57,44 @@ fifa_status chain_phase_sigma2(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) 
 
 // Phase 3: tau2 | f, rho, then the Metropolis step on log rho (advances the
 // chain's iteration counter).
-fifa_status chain_phase_hyper(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
+// Phase 3a: q, tau2 | f, rho, the proposal rho' and the assembly of C~(rho').
+fifa_status chain_phase_hyper_pre(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
   const int64_t n = ch->plan->n;
   cudaStream_t s = ctx->stream;
   ChainDev* c = ch->dev;
-  HmatDesc* Hc = ch->H[0]->dev;
-  HmatDesc* Hp = ch->H[1]->dev;
   if (cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return FIFA_ERR_CUDA;
   fifa_status st = sweep_enqueue(ctx, ch->F[0], 0, 1, ch->tmp, 1);
   if (st != FIFA_OK) return st;
   if (launch_sumsq(ch->tmp, nullptr, n, S.red, &c->q, s) != cudaSuccess) return FIFA_ERR_CUDA;
   if (launch_chain_tau2(c, s) != cudaSuccess) return FIFA_ERR_CUDA;
-  if (launch_chain_propose(c, Hp, s) != cudaSuccess) return FIFA_ERR_CUDA;
-  st = hmat_assemble_enqueue(ctx, ch->H[1]);
-  if (st != FIFA_OK) return st;
-  st = fact_enqueue(ctx, ch->F[1], Hp);
-  if (st != FIFA_OK) return st;
+  if (launch_chain_propose(c, ch->H[1]->dev, s) != cudaSuccess) return FIFA_ERR_CUDA;
+  return hmat_assemble_enqueue(ctx, ch->H[1]);
+}
+
+// Phase 3c (after the factorization of C~(rho'), phase 3b): q' and the
+// Metropolis step on log rho (advances the chain's iteration counter).
+fifa_status chain_phase_hyper_post(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
+  const int64_t n = ch->plan->n;
+  cudaStream_t s = ctx->stream;
+  ChainDev* c = ch->dev;
   if (cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return FIFA_ERR_CUDA;
-  st = sweep_enqueue(ctx, ch->F[1], 0, 1, ch->tmp, 1);
+  fifa_status st = sweep_enqueue(ctx, ch->F[1], 0, 1, ch->tmp, 1);
   if (st != FIFA_OK) return st;
   if (launch_sumsq(ch->tmp, nullptr, n, S.red, &c->q_prop, s) != cudaSuccess) return FIFA_ERR_CUDA;
-  if (launch_chain_mh(c, Hc, Hp, ch->F[0]->dev, ch->F[1]->dev, ch->FM->dev, s) != cudaSuccess) return FIFA_ERR_CUDA;
+  if (launch_chain_mh(c, ch->H[0]->dev, ch->H[1]->dev, ch->F[0]->dev, ch->F[1]->dev, ch->FM->dev, s) != cudaSuccess)
+    return FIFA_ERR_CUDA;
   return FIFA_OK;
+}
+
+// Phase 3: tau2 | f, rho, then the Metropolis step on log rho (advances the
+// chain's iteration counter).
+fifa_status chain_phase_hyper(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
+  fifa_status st = chain_phase_hyper_pre(ctx, ch, S);
+  if (st == FIFA_OK) st = fact_enqueue(ctx, ch->F[1], ch->H[1]->dev);
+  if (st == FIFA_OK) st = chain_phase_hyper_post(ctx, ch, S);
+  return st;
 }
 
 static fifa_status chain_iteration_enqueue(fifa_ctx* ctx, fifa_chain* ch) {

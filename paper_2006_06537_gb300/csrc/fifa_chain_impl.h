@@ -37,6 +37,10 @@ fifa_status chain_phase_factor_m(fifa_ctx* ctx, fifa_chain* ch);  // first half 
 fifa_status chain_phase_sample(fifa_ctx* ctx, fifa_chain* ch);    // second half: Algorithm 1
 fifa_status chain_phase_sigma2(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
 fifa_status chain_phase_hyper(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
+// hyper in three parts: pre (q, tau2, proposal, assembly of C~(rho')), the
+// factorization of C~(rho') into F[1], post (q' and the Metropolis step)
+fifa_status chain_phase_hyper_pre(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
+fifa_status chain_phase_hyper_post(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
 
 // Serving helpers.  chain_run_collect runs `iters` iterations (graph replay)
 // and gathers on the device: mean_acc = sum of the conditional means
