@@ -311,7 +311,7 @@ def gpu_arm(args):
     # measured after the headline, outside its timed region
     serving = additive = None
     if rank == 0 and args.serve_requests > 0:
-        serving = serving_leg(fifa, args.serve_requests, args.serve_slots, fifa.FIFA_FP64, 64)
+        serving = serving_leg(fifa, args.serve_requests, args.serve_slots, fifa.FIFA_FP64, 32)
     if rank == 0 and args.additive_sweeps > 0:
         additive = additive_leg(fifa, torch, args.additive_sweeps, 32)
 
@@ -355,7 +355,7 @@ def gpu_arm(args):
 
 
 def serving_leg(fifa, count, slots, prec, leaf, iters=100, ndraws=20, rate=200.0, budget=120 << 30,
-                wide_min_n=1 << 16):
+                wide_min_n=1 << 15):
     """The serving workload: the first `count` requests of a Poisson stream at
     `rate` req/s, n log-uniform in [2^10, 2^18], SE or Matern-5/2 per request,
     each `iters` Gibbs iterations returning the posterior mean and `ndraws`

@@ -1199,9 +1199,11 @@ static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, const 
   // bucket, then (16, cap]; a node's CTAs skip the launches of other buckets
   // (buckets entirely below the small kernels' ranks are not launched)
   cudaError_t e = cudaSuccess;
-  if (G[0] > 1 || G[1] > 1) {
-    // a level with CTA groups has few nodes: one launch for every rank <= 16
-    // instead of two launches that would each leave the other bucket's groups idle
+  if ((G[0] > 1 || G[1] > 1) && nodes <= 64) {
+    // a top level with CTA groups has few nodes, often of both rank buckets:
+    // one launch for every rank <= 16 instead of two launches that would each
+    // leave the other bucket's groups idle (measured: the split is faster only
+    // at levels of >= 128 nodes, which are mostly of one bucket)
     e = launch_level_bucket<T, 16, -1>(Fd, lvl, nodes, G[1], cap, part, bar + bar_stride, abort_flag, skip, st, nprob, sstride);
     if (e == cudaSuccess && cap > 16)
       e = launch_level_bucket<T, 0, 16>(Fd, lvl, nodes, G[2], cap, part, bar + 2 * bar_stride, abort_flag, skip, st, nprob, sstride);
