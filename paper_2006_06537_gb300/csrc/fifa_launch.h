@@ -14,7 +14,9 @@ size_t level_smem(int ldm, int cap);
 // Doubles per CTA slot of the level kernel's partial sums: a cap x cap Gram
 // matrix or a 2cap x 8 projection block.
 __host__ __device__ inline size_t level_part_stride(int cap) {
-  return (size_t)(cap * cap > 2 * cap * 8 ? cap * cap : 2 * cap * 8);
+  // the larger of the packed Gram entries of both sides, r (r + 1) <= cap (cap + 1),
+  // and a 2 cap x 8 projection chunk
+  return (size_t)(cap * (cap + 1) > 2 * cap * 8 ? cap * (cap + 1) : 2 * cap * 8);
 }
 cudaError_t launch_leaf_factor(const HmatDesc* Hd, const FactDesc* Fd, int prec, int nleaf, int Bm, int L, int cap,
                                cudaStream_t st, int nprob = 1);

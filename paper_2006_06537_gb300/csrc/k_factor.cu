@@ -151,6 +151,42 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
 #define LEVEL_W(RB) 8
 #define LV_RED 64
 
+// Serial upper Cholesky of A (r x r, ld) in place by one thread, pivots from
+// one rsqrt each (as blk_chol_upper); rinv receives the reciprocal pivots.
+__device__ inline bool thr_chol_upper(double* A, int ld, int r, double* rinv, double clamp) {
+  double dmax = 0.0;
+  for (int k = 0; k < r; ++k) dmax = fmax(dmax, A[k * ld + k]);
+  const double floor_v = clamp * dmax;
+  bool ok = true;
+  for (int k = 0; k < r; ++k) {
+    double d = A[k * ld + k];
+    if (clamp > 0.0 && !(d > floor_v)) d = floor_v > 0.0 ? floor_v : 1.0;
+    if (!(d > 0.0)) {
+      ok = false;
+      d = 1.0;
+    }
+    const double rs = rsqrt(d);
+    A[k * ld + k] = d * rs;
+    rinv[k] = rs;
+    for (int j = k + 1; j < r; ++j) A[k * ld + j] *= rs;
+    for (int i = k + 1; i < r; ++i)
+      for (int j = i; j < r; ++j) A[i * ld + j] -= A[k * ld + i] * A[k * ld + j];
+  }
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < i; ++j) A[i * ld + j] = 0.0;
+  return ok;
+}
+
+// Ri = R^-1 (upper, r x r) by one thread, with the reciprocal pivots rinv.
+__device__ inline void thr_triinv_upper(const double* R, int ldr, const double* rinv, double* Ri, int ldi, int r) {
+  for (int j = 0; j < r; ++j)
+    for (int i = r - 1; i >= 0; --i) {
+      double acc = (i == j) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= j; ++k) acc -= R[i * ldr + k] * Ri[k * ldi + j];
+      Ri[i * ldi + j] = (i <= j) ? acc * rinv[i] : 0.0;
+    }
+}
+
 template <typename T, int RB>
 __device__ __forceinline__ void rowmul_row(T* __restrict__ Xb, int64_t n, int r, int p, const double* Ri, int ldr) {
   double x[RB];
@@ -405,12 +441,14 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
   const int ldm = RB > 0 ? RB : cap;  // leading dimension of the small matrices
   constexpr int W = LEVEL_W(RB);      // ancestor columns per update chunk
   const int cc2 = ldm * ldm;
-  double* Gm = sm;
-  double* Ri = Gm + cc2;
-  double* R1 = Ri + cc2;
-  double* RU = R1 + cc2;
-  double* RV = RU + cc2;
-  double* tile = RV + cc2;                // (ldm + W) x LV_TRP row tile
+  double* Gm = sm;                        // Gram / factor of the left side
+  double* Gm2 = Gm + cc2;                 // ... of the right side
+  double* Ri = Gm2 + cc2;                 // inverse factors of both sides (Ri2 follows Ri:
+  double* Ri2 = Ri + cc2;                 // the packed Gram entries of both sides span them)
+  double* RU = Ri2 + cc2;                 // R1, then R = R2 R1 of the left side
+  double* RV = RU + cc2;                  // ... of the right side
+  double* rvs = RV + cc2;                 // 2 x 8 reciprocal pivots (serial small factorizations)
+  double* tile = rvs + 16;                // (ldm + W) x LV_TRP row tile
   double* part = tile + (ldm + W) * LV_TRP;  // 256 group partial sums
   double* tmp = part + 256;               // LV_RED
   double* Pm = tmp + LV_RED;              // 2ldm x W
@@ -422,36 +460,64 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
   unsigned int phase = 0;
   bool ok = true;
 
-  for (int side = 0; side < 2; ++side) {
-    const int a0 = side == 0 ? max(r0, s) : max(r0, h);
-    const int a1 = side == 0 ? min(r1, h) : min(r1, e);
-    // CholeskyQR2 of this side's basis: Gram, R1, Q1 = X R1^-1, Gram, R2, Q = Q1 R2^-1
-    // (the group exchanges only the r(r+1)/2 packed Gram entries, staged in Ri)
-    const int npk = r * (r + 1) / 2;
-    gram_tiled<T>(Qb, n, r, a0, a1, tile, part, Ri);
-    if (!group_reduce(Ri, Ri, npk, G, g, base, gpart, pstride, bar, phase, status, abort_flag, part)) return;
+  // CholeskyQR2 of both sides at once (Gram, R1, Q1 = X R1^-1, Gram, R2,
+  // Q = Q1 R2^-1, R = R2 R1): one group reduction per pass carries the packed
+  // Gram entries of both sides, so CTAs whose rows lie in one side never idle
+  // while the other side is factored
+  const int npk = r * (r + 1) / 2;
+  const int sa0 = max(r0, s), sa1 = min(r1, h), sb0 = max(r0, h), sb1 = min(r1, e);
+  if (threadIdx.x == 0) iflag[2] = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    gram_tiled<T>(Qb, n, r, sa0, sa1, tile, part, Ri);
+    gram_tiled<T>(Qb, n, r, sb0, sb1, tile, part, Ri + npk);
+    if (!group_reduce(Ri, Ri, 2 * npk, G, g, base, gpart, pstride, bar, phase, status, abort_flag, part)) return;
     gram_unpack(Ri, r, Gm, ldm);
-    ok = blk_chol_upper(Gm, ldm, r, iflag, clamp_gram<T>()) && ok;
-    for (int t = threadIdx.x; t < cc2; t += blockDim.x) R1[t] = Gm[t];
-    __syncthreads();
-    blk_triinv_upper(Gm, ldm, Ri, ldm, r);
-    rowmul_pass<T>(Qb, n, r, a0, a1, Ri, ldm);
-    gram_tiled<T>(Qb, n, r, a0, a1, tile, part, Ri);
-    if (!group_reduce(Ri, Ri, npk, G, g, base, gpart, pstride, bar, phase, status, abort_flag, part)) return;
-    gram_unpack(Ri, r, Gm, ldm);
-    ok = blk_chol_upper(Gm, ldm, r, iflag, clamp_gram<T>()) && ok;
-    blk_triinv_upper(Gm, ldm, Ri, ldm, r);
-    double* Rs = side == 0 ? RU : RV;
-    for (int t = threadIdx.x; t < cc2; t += blockDim.x) {
-      const int i = t / ldm, j = t % ldm;
-      double v = 0.0;
-      if (i < r && j < r && i <= j)
-        for (int k = i; k <= j; ++k) v += Gm[i * ldm + k] * R1[k * ldm + j];
-      Rs[t] = v;
+    gram_unpack(Ri + npk, r, Gm2, ldm);
+    if (r <= 8) {
+      // small ranks: each side's factorization by one thread (two warps side by side)
+      if (threadIdx.x == 0 || threadIdx.x == 32) {
+        const int sd = threadIdx.x >> 5;
+        double* Gs = sd ? Gm2 : Gm;
+        double* Rs = sd ? RV : RU;
+        double* rv = rvs + 8 * sd;
+        if (!thr_chol_upper(Gs, ldm, r, rv, clamp_gram<T>())) iflag[2] = 1;
+        thr_triinv_upper(Gs, ldm, rv, sd ? Ri2 : Ri, ldm, r);
+        for (int i = 0; i < r; ++i)
+          for (int j = 0; j < r; ++j) {
+            if (pass == 0) {
+              Rs[i * ldm + j] = Gs[i * ldm + j];
+            } else if (i <= j) {  // R = R2 R1 in place, rows top-down: row i reads rows >= i of R1
+              double v = 0.0;
+              for (int k = i; k <= j; ++k) v += Gs[i * ldm + k] * Rs[k * ldm + j];
+              Rs[i * ldm + j] = v;
+            }
+          }
+      }
+      __syncthreads();
+    } else {
+      for (int sd = 0; sd < 2; ++sd) {
+        double* Gs = sd ? Gm2 : Gm;
+        double* Rs = sd ? RV : RU;
+        ok = blk_chol_upper(Gs, ldm, r, iflag, clamp_gram<T>()) && ok;
+        blk_triinv_upper(Gs, ldm, sd ? Ri2 : Ri, ldm, r);
+        if (pass == 0) {
+          for (int t = threadIdx.x; t < cc2; t += blockDim.x) Rs[t] = Gs[t];
+        } else {
+          // R = R2 R1 in place, one thread per column, rows top-down
+          for (int j = threadIdx.x; j < r; j += blockDim.x)
+            for (int i = 0; i <= j; ++i) {
+              double v = 0.0;
+              for (int k = i; k <= j; ++k) v += Gs[i * ldm + k] * Rs[k * ldm + j];
+              Rs[i * ldm + j] = v;
+            }
+        }
+        __syncthreads();
+      }
     }
-    __syncthreads();
-    rowmul_pass<T>(Qb, n, r, a0, a1, Ri, ldm);
+    rowmul_pass<T>(Qb, n, r, sa0, sa1, Ri, ldm);
+    rowmul_pass<T>(Qb, n, r, sb0, sb1, Ri2, ldm);
   }
+  ok = ok && iflag[2] == 0;
   if (!ok && g == 0 && threadIdx.x == 0) atomicOr(status, FIFA_DEV_NOT_SPD);
 
   // capacitance: S = I + R X R^T, L_S = chol(S) (computed by the group's first CTA)
@@ -773,42 +839,6 @@ __global__ void __launch_bounds__(128) k_level_small(const FactDesc* __restrict_
 // ---------------------------------------------------------------------------
 #define LM_W 8  // ancestor columns per chunk
 
-// Serial upper Cholesky of A (r x r, ld) in place by one thread, pivots from
-// one rsqrt each (as blk_chol_upper); rinv receives the reciprocal pivots.
-__device__ inline bool thr_chol_upper(double* A, int ld, int r, double* rinv, double clamp) {
-  double dmax = 0.0;
-  for (int k = 0; k < r; ++k) dmax = fmax(dmax, A[k * ld + k]);
-  const double floor_v = clamp * dmax;
-  bool ok = true;
-  for (int k = 0; k < r; ++k) {
-    double d = A[k * ld + k];
-    if (clamp > 0.0 && !(d > floor_v)) d = floor_v > 0.0 ? floor_v : 1.0;
-    if (!(d > 0.0)) {
-      ok = false;
-      d = 1.0;
-    }
-    const double rs = rsqrt(d);
-    A[k * ld + k] = d * rs;
-    rinv[k] = rs;
-    for (int j = k + 1; j < r; ++j) A[k * ld + j] *= rs;
-    for (int i = k + 1; i < r; ++i)
-      for (int j = i; j < r; ++j) A[i * ld + j] -= A[k * ld + i] * A[k * ld + j];
-  }
-  for (int i = 0; i < r; ++i)
-    for (int j = 0; j < i; ++j) A[i * ld + j] = 0.0;
-  return ok;
-}
-
-// Ri = R^-1 (upper, r x r) by one thread, with the reciprocal pivots rinv.
-__device__ inline void thr_triinv_upper(const double* R, int ldr, const double* rinv, double* Ri, int ldi, int r) {
-  for (int j = 0; j < r; ++j)
-    for (int i = r - 1; i >= 0; --i) {
-      double acc = (i == j) ? 1.0 : 0.0;
-      for (int k = i + 1; k <= j; ++k) acc -= R[i * ldr + k] * Ri[k * ldi + j];
-      Ri[i * ldi + j] = (i <= j) ? acc * rinv[i] : 0.0;
-    }
-}
-
 template <int R, int MS, int NPC>
 struct LmLayout {
   static constexpr int R2 = 2 * R;
@@ -1119,7 +1149,7 @@ size_t leaf_factor_smem(int Bm, int L, int cap, int prec) {
 }
 size_t level_smem(int ldm, int cap) {
   const size_t W = LEVEL_W(ldm);
-  return ((size_t)5 * ldm * ldm + (size_t)(ldm + W) * LV_TRP + 256 + LV_RED + 4 * (size_t)ldm * W) * sizeof(double) +
+  return ((size_t)6 * ldm * ldm + 16 + (size_t)(ldm + W) * LV_TRP + 256 + LV_RED + 4 * (size_t)ldm * W) * sizeof(double) +
          W * sizeof(void*) + (4 + (size_t)FIFA_LEVELS_MAX * cap) * sizeof(int);
 }
 
@@ -1186,9 +1216,9 @@ static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, const 
     // small nodes: rank <= 4 several nodes per CTA, rank 5..8 one node per CTA
     // (static shared memory); larger nodes take the tiled bucket kernels below,
     // whose output-major Gram and projection passes use the lanes better
-    cudaError_t e0 = side_max <= 32   ? launch_level_multi<T, 4, 32, 8>(Fd, lvl, nodes, st, nprob)
-                     : side_max <= 64 ? launch_level_multi<T, 4, 64, 4>(Fd, lvl, nodes, st, nprob)
-                                      : launch_level_multi<T, 4, 128, 2>(Fd, lvl, nodes, st, nprob);
+    cudaError_t e0 = side_max <= 32   ? launch_level_multi<T, 4, 32, 4>(Fd, lvl, nodes, st, nprob)
+                     : side_max <= 64 ? launch_level_multi<T, 4, 64, 2>(Fd, lvl, nodes, st, nprob)
+                                      : launch_level_multi<T, 4, 128, 1>(Fd, lvl, nodes, st, nprob);
     if (e0 != cudaSuccess) return e0;
     k_level_small<T, 8, 4, 128, 8><<<dim3(nodes, nprob), 128, 0, st>>>(Fd, lvl);
     skip = 8;
