@@ -956,6 +956,10 @@ extern "C" fifa_status fifa_fact_export(fifa_ctx* ctx, const fifa_fact* F, doubl
   };
   CK(fetch(bases_host, F->host.Q, nb));
   CK(fetch(leaves_host, F->host.Lleaf, nl));
+  if (leaves_host)  // the device copy mirrors L^T into the upper triangle; export L alone
+    for (size_t lf = 0; lf < (size_t)P->nleaf; ++lf)
+      for (int k = 1; k < P->Bm; ++k)
+        for (int j = 0; j < k; ++j) leaves_host[(lf * P->Bm + k) * P->Bm + j] = 0.0;
   const size_t nz = (size_t)std::max(1, P->nnodes) * 4 * cap * cap;
   if (Zf_host && P->nnodes) CK(cudaMemcpy(Zf_host, F->host.Zf, sizeof(double) * nz, cudaMemcpyDeviceToHost));
   if (Zi_host && P->nnodes) CK(cudaMemcpy(Zi_host, F->host.Zi, sizeof(double) * nz, cudaMemcpyDeviceToHost));

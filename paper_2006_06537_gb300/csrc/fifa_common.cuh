@@ -51,7 +51,7 @@ struct FactDesc {
   int64_t n;
   int L, nleaf, Bm, cap, prec;  // prec: 0 = f64 storage, 1 = f32 storage
   const int* bnd;
-  void* Lleaf;                  // nleaf x Bm x Bm lower Cholesky factors
+  void* Lleaf;                  // nleaf x Bm x Bm Cholesky factors L, L^T mirrored into the upper triangle
   double* Ldinv;                // nleaf x Bm reciprocals of their diagonals
   void* Q;                      // L x cap x n orthonormal bases
   double* Zf;                   // nnodes x (2cap)^2 : L_S - I

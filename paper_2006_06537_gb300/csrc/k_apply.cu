@@ -101,7 +101,9 @@ __device__ __forceinline__ double reg_sel(const double (&a)[N], int q) {
 // ---------------------------------------------------------------------------
 // Leaf step of one leaf by one warp, on m entries at vj (global or shared
 // memory).  mode 0: v <- L v, 1: v <- L^-1 v, 2: v <- L^T v, 3: v <- L^-T v.
-// L column-major (L[i][k] at k*Bm + i).
+// L column-major (L[i][k] at k*Bm + i, i >= k) with L^T mirrored into the
+// upper triangle (L[k][j] at k*Bm + j, j < k): every step reads one contiguous
+// column, L's for modes 0 / 1 and L^T's for modes 2 / 3.
 // ---------------------------------------------------------------------------
 template <typename T, int RPL>  // RPL: rows per lane, 32 RPL >= m; dinv: reciprocal pivots
 __device__ __forceinline__ void leaf_warp_apply_r(const T* __restrict__ Lm, const double* __restrict__ dinv, int Bm,
@@ -139,34 +141,33 @@ __device__ __forceinline__ void leaf_warp_apply_r(const T* __restrict__ Lm, cons
         else if (i > k && i < m) o[q] -= to_d(Lm[(size_t)k * Bm + i]) * xk;
       }
     }
-  } else if (mode == 2) {  // o_j = sum_{k>=j} L[k][j] x_k (column j contiguous)
-    for (int jj = 0; jj < m; ++jj) {
-      double part = 0.0;
+  } else if (mode == 2) {  // o_j = sum_{k>=j} L[k][j] x_k, right-looking over k
+    // row k of L is column k of the stored upper triangle (L^T mirrored there):
+    // coalesced, and no cross-lane sums
+    for (int k = 0; k < m; ++k) {
+      const double xk = __shfl_sync(0xffffffffu, reg_sel<RPL>(x, k >> 5), k & 31);
 #pragma unroll
       for (int q = 0; q < RPL; ++q) {
-        int k = lane + 32 * q;
-        if (k >= jj && k < m) part += to_d(Lm[(size_t)jj * Bm + k]) * x[q];
+        const int j = lane + 32 * q;
+        if (j <= k) o[q] += to_d(Lm[(size_t)k * Bm + j]) * xk;
       }
-      part = warp_sum(part);
-      part = __shfl_sync(0xffffffffu, part, 0);
-#pragma unroll
-      for (int q = 0; q < RPL; ++q)
-        if (lane + 32 * q == jj) o[q] = part;
     }
-  } else {  // backward substitution L^T x = v
-    for (int jj = m - 1; jj >= 0; --jj) {
-      double part = 0.0;
+  } else {  // backward substitution L^T x = v, column-oriented (x_k, then o_j -= L[k][j] x_k for j < k)
 #pragma unroll
-      for (int q = 0; q < RPL; ++q) {
-        int k = lane + 32 * q;
-        if (k > jj && k < m) part += to_d(Lm[(size_t)jj * Bm + k]) * o[q];
-      }
-      part = warp_sum(part);
-      part = __shfl_sync(0xffffffffu, part, 0);
-      const double xj = (__shfl_sync(0xffffffffu, reg_sel<RPL>(x, jj >> 5), jj & 31) - part) * dinv[jj];
+    for (int q = 0; q < RPL; ++q) o[q] = x[q];
+    for (int k = m - 1; k >= 0; --k) {
+      const int qk = k >> 5;
+      double ok = 0.0;
 #pragma unroll
       for (int q = 0; q < RPL; ++q)
-        if (lane + 32 * q == jj) o[q] = xj;
+        if (q == qk) ok = o[q];
+      const double xk = __shfl_sync(0xffffffffu, ok, k & 31) * dinv[k];
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        const int j = lane + 32 * q;
+        if (j == k) o[q] = xk;
+        else if (j < k) o[q] -= to_d(Lm[(size_t)k * Bm + j]) * xk;
+      }
     }
   }
 #pragma unroll
@@ -317,14 +318,15 @@ __device__ void fs_local_level(const FactDesc* __restrict__ Fd, int l, int ls, i
       int s0, h0, e0;
       node_range(bnd, l, gi, s0, h0, e0);
       const double* tn = sh.tv + node * per + (p < h0 ? 0 : rmax) * nrhs;
-      double acc0 = 0.0, acc1 = 0.0;
+      // the products accumulate onto v itself (no separate add per row)
+      double acc0 = vs[p - S], acc1 = nrhs > 1 ? vs[rows + p - S] : 0.0;
       for (int a = 0; a < r; ++a) {
         const double q = to_d(Qb[(size_t)a * n + p]);
         acc0 += q * tn[a * nrhs];
         if (nrhs > 1) acc1 += q * tn[a * nrhs + 1];
       }
-      vs[p - S] += acc0;
-      if (nrhs > 1) vs[rows + p - S] += acc1;
+      vs[p - S] = acc0;
+      if (nrhs > 1) vs[rows + p - S] = acc1;
     }
     __syncthreads();
   }
@@ -394,14 +396,14 @@ __device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, 
   __syncthreads();
   const int off = side * r;
   for (int p = S + (int)threadIdx.x; p < E; p += blockDim.x) {
-    double acc0 = 0.0, acc1 = 0.0;
+    double acc0 = vs[p - S], acc1 = nrhs > 1 ? vs[rows + p - S] : 0.0;
     for (int a = 0; a < r; ++a) {
       const double q = to_d(Qb[(size_t)a * n + p]);
       acc0 += q * sh.tv[(off + a) * nrhs];
       if (nrhs > 1) acc1 += q * sh.tv[(off + a) * nrhs + 1];
     }
-    vs[p - S] += acc0;
-    if (nrhs > 1) vs[rows + p - S] += acc1;
+    vs[p - S] = acc0;
+    if (nrhs > 1) vs[rows + p - S] = acc1;
   }
   __syncthreads();
   return true;
@@ -615,14 +617,14 @@ __global__ void __launch_bounds__(256, RPT <= 8 ? 4 : 2) k_mv_fused(const HmatDe
             node_range(bnd, l, gi, s0, h0, e0);
             const int other = p < h0 ? 1 : 0;
             const double* pr = pj + node * per + other * rmax * nrhs;
-            double a0 = 0.0, a1 = 0.0;
+            double a0 = acc[i][0], a1 = acc[i][1];  // products accumulate onto the row sums
             for (int cc = 0; cc < r; ++cc) {
               const double bv = Bl[(size_t)cc * n + p];
               a0 += bv * pr[cc * nrhs];
               if (nrhs > 1) a1 += bv * pr[cc * nrhs + 1];
             }
-            acc[i][0] += a0;
-            acc[i][1] += a1;
+            acc[i][0] = a0;
+            acc[i][1] = a1;
           }
         }
       }
@@ -674,14 +676,14 @@ __global__ void __launch_bounds__(256, RPT <= 8 ? 4 : 2) k_mv_fused(const HmatDe
     for (int ii = 0; ii < RPT; ++ii) {
       const int p = S + tid + ii * (int)blockDim.x;
       if (p < E) {
-        double a0 = 0.0, a1 = 0.0;
+        double a0 = acc[ii][0], a1 = acc[ii][1];
         for (int cc = 0; cc < r; ++cc) {
           const double bv = Bl[(size_t)cc * n + p];
           a0 += bv * pj[cc * nrhs];
           if (nrhs > 1) a1 += bv * pj[cc * nrhs + 1];
         }
-        acc[ii][0] += a0;
-        acc[ii][1] += a1;
+        acc[ii][0] = a0;
+        acc[ii][1] = a1;
       }
     }
     __syncthreads();

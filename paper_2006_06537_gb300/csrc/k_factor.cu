@@ -85,7 +85,9 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
   T* Lout = (T*)Fd->Lleaf + (size_t)leaf * Bm * Bm;
   for (int t = threadIdx.x; t < Bm * Bm; t += blockDim.x) {
     int i = t % Bm, j = t / Bm;
-    double v = (i < m && j < m && i >= j) ? A[j * ld + i] : 0.0;
+    // L in the lower triangle, L^T mirrored into the upper one (transposed
+    // solves then read contiguous columns as well)
+    double v = (i < m && j < m) ? (i >= j ? A[j * ld + i] : A[i * ld + j]) : 0.0;
     Lout[t] = (T)v;
   }
   if (sizeof(T) != sizeof(double)) {
