@@ -18,7 +18,10 @@
 #include "fifa_common.cuh"
 #include "fifa_launch.h"
 
-#define LF_NCH 32
+// Ancestor columns per right-hand-side chunk of the leaf TRSM: the first chunk
+// is eliminated together with the Cholesky steps, later chunks (more ancestor
+// columns than this) by a separate triangular solve.
+__host__ __device__ inline int lf_nch(int Bm) { return Bm <= 64 ? 64 : 32; }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict__ Hd, const FactDesc* __restrict__ Fd) {
@@ -31,11 +34,11 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
   const double sc = Hd->scale, shf = Hd->shift;
   const int* bnd = Fd->bnd;
   const int s = bnd[bnd_off(L) + leaf], e = bnd[bnd_off(L) + leaf + 1], m = e - s;
-  const int ld = Bm + 1;
+  const int ld = Bm + 1, NCH = lf_nch(Bm);
   double* A = sm;                          // FP64 Cholesky, column-major A[j*ld + i]
   T* La = sizeof(T) == sizeof(double) ? (T*)A : (T*)(A + (size_t)Bm * ld);  // L in the TRSM precision
   T* X = (T*)(A + (size_t)Bm * ld + (sizeof(T) == sizeof(double) ? 0 : ((size_t)Bm * ld + 1) / 2));
-  double* red = (double*)(X + (size_t)LF_NCH * ld) + 1;  // 40 doubles (8-byte aligned past X)
+  double* red = (double*)(X + (size_t)NCH * ld) + 1;  // 40 doubles (8-byte aligned past X)
   red = (double*)(((uintptr_t)red) & ~(uintptr_t)7);
   int* flag = (int*)(red + 40);
   int* clist = flag + 4;                   // L * cap entries: (level << 8) | col
@@ -45,53 +48,6 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
     double v = __dmul_rn(sc, D[(size_t)j * Bm + i]);
     if (i == j) v = __dadd_rn(v, shf);
     A[j * ld + i] = v;
-  }
-  // reciprocals of the pivots: one division per column, products elsewhere
-  __shared__ double rinv[FIFA_LEAF_MAX];
-  if (threadIdx.x == 0) flag[0] = 0;
-  __syncthreads();
-  for (int k = 0; k < m; ++k) {
-    if (threadIdx.x == 0) {
-      double d = A[k * ld + k];
-      if (!(d > 0.0)) { flag[0] = 1; d = 1.0; }
-      const double rs = rsqrt(d);  // the pivot and its reciprocal from one reciprocal square root
-      A[k * ld + k] = d * rs;
-      rinv[k] = rs;
-    }
-    __syncthreads();
-    const double dinv = rinv[k];
-    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[k * ld + i] *= dinv;
-    __syncthreads();
-    // trailing update on the lower triangle only: t -> (a, b), b <= a, t = a(a+1)/2 + b
-    const int w = m - k - 1;
-    for (int t = threadIdx.x; t < w * (w + 1) / 2; t += blockDim.x) {
-      int a = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-      if ((a + 1) * (a + 2) / 2 <= t) ++a;
-      if (a * (a + 1) / 2 > t) --a;
-      const int b = t - a * (a + 1) / 2;
-      const int i = k + 1 + a, j = k + 1 + b;
-      A[j * ld + i] -= A[k * ld + i] * A[k * ld + j];
-    }
-    __syncthreads();
-  }
-  double lsum = 0.0;
-  for (int k = threadIdx.x; k < m; k += blockDim.x) lsum += log(A[k * ld + k]);
-  lsum = block_sum(lsum, red);
-  if (threadIdx.x == 0) {
-    Fd->ld_parts[leaf] = lsum;
-    if (flag[0]) atomicOr(Fd->status, FIFA_DEV_NOT_SPD);
-  }
-  for (int k = threadIdx.x; k < m; k += blockDim.x) Fd->Ldinv[(size_t)leaf * Bm + k] = rinv[k];
-  T* Lout = (T*)Fd->Lleaf + (size_t)leaf * Bm * Bm;
-  for (int t = threadIdx.x; t < Bm * Bm; t += blockDim.x) {
-    int i = t % Bm, j = t / Bm;
-    // L in the lower triangle, L^T mirrored into the upper one (transposed
-    // solves then read contiguous columns as well)
-    double v = (i < m && j < m) ? (i >= j ? A[j * ld + i] : A[i * ld + j]) : 0.0;
-    Lout[t] = (T)v;
-  }
-  if (sizeof(T) != sizeof(double)) {
-    for (int t = threadIdx.x; t < m * ld; t += blockDim.x) La[t] = (T)A[t];
   }
   // column list of all ancestor bases restricted to this leaf: the level-l
   // ancestor of leaf i is node i >> (L - l); the leaf lies in its left child
@@ -112,8 +68,8 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
   }
   __syncthreads();
   const int nc = ncols;
-  for (int c0 = 0; c0 < nc; c0 += LF_NCH) {
-    const int w = min(LF_NCH, nc - c0);
+  T* Q = (T*)Fd->Q;
+  auto load_chunk = [&](int c0, int w) {
     for (int t = threadIdx.x; t < w * m; t += blockDim.x) {
       int cc = t / m, i = t % m;
       int code = clist[c0 + cc], l = code >> 8, q = code & 255;
@@ -121,9 +77,86 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
       double v = Hd->bases[((size_t)l * cap + q) * n + s + i];
       X[cc * ld + i] = (T)((scl == 1.0) ? v : __dmul_rn(scl, v));
     }
+  };
+  auto store_chunk = [&](int c0, int w) {
+    for (int t = threadIdx.x; t < w * m; t += blockDim.x) {
+      int cc = t / m, i = t % m;
+      int code = clist[c0 + cc], l = code >> 8, q = code & 255;
+      Q[((size_t)l * cap + q) * n + s + i] = X[cc * ld + i];
+    }
+  };
+  const int w0 = min(NCH, nc);
+  load_chunk(0, w0);
+  // reciprocals of the pivots: one reciprocal square root per column, products elsewhere
+  __shared__ double rinv[FIFA_LEAF_MAX];
+  auto pivot = [&](int k) {  // by one thread
+    double d = A[k * ld + k];
+    if (!(d > 0.0)) { flag[0] = 1; d = 1.0; }
+    const double rs = rsqrt(d);
+    A[k * ld + k] = d * rs;
+    rinv[k] = rs;
+  };
+  if (threadIdx.x == 0) {
+    flag[0] = 0;
+    if (m > 0) pivot(0);
+  }
+  __syncthreads();
+  // right-looking Cholesky with the first chunk of right-hand sides eliminated
+  // in the same steps (L^-1 X): per column k, one pass scales column k of L and
+  // row k of X, the next updates the trailing triangle and the rows of X below
+  // k, and the thread owning the next diagonal entry takes its pivot at once
+  for (int k = 0; k < m; ++k) {
+    const double dinv = rinv[k];
+    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[k * ld + i] *= dinv;
+    for (int cc = threadIdx.x; cc < w0; cc += blockDim.x) X[cc * ld + k] *= (T)dinv;
+    __syncthreads();
+    // trailing update on the lower triangle only: t -> (a, b), b <= a, t = a(a+1)/2 + b
+    // (thread 0 owns t = 0, the next diagonal entry)
+    const int w = m - k - 1;
+    for (int t = threadIdx.x; t < w * (w + 1) / 2; t += blockDim.x) {
+      int a = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+      if ((a + 1) * (a + 2) / 2 <= t) ++a;
+      if (a * (a + 1) / 2 > t) --a;
+      const int b = t - a * (a + 1) / 2;
+      const int i = k + 1 + a, j = k + 1 + b;
+      A[j * ld + i] -= A[k * ld + i] * A[k * ld + j];
+    }
+    for (int t = threadIdx.x; t < w * w0; t += blockDim.x) {
+      const int cc = t / w, i = k + 1 + t % w;
+      X[cc * ld + i] -= (T)A[k * ld + i] * X[cc * ld + k];
+    }
+    if (threadIdx.x == 0 && k + 1 < m) pivot(k + 1);
+    __syncthreads();
+  }
+  double lsum = 0.0;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) lsum += log(A[k * ld + k]);
+  lsum = block_sum(lsum, red);
+  if (threadIdx.x == 0) {
+    Fd->ld_parts[leaf] = lsum;
+    if (flag[0]) atomicOr(Fd->status, FIFA_DEV_NOT_SPD);
+  }
+  for (int k = threadIdx.x; k < m; k += blockDim.x) Fd->Ldinv[(size_t)leaf * Bm + k] = rinv[k];
+  T* Lout = (T*)Fd->Lleaf + (size_t)leaf * Bm * Bm;
+  for (int t = threadIdx.x; t < Bm * Bm; t += blockDim.x) {
+    int i = t % Bm, j = t / Bm;
+    // L in the lower triangle, L^T mirrored into the upper one (transposed
+    // solves then read contiguous columns as well)
+    double v = (i < m && j < m) ? (i >= j ? A[j * ld + i] : A[i * ld + j]) : 0.0;
+    Lout[t] = (T)v;
+  }
+  store_chunk(0, w0);
+  if (nc <= w0) return;
+  if (sizeof(T) != sizeof(double)) {
+    for (int t = threadIdx.x; t < m * ld; t += blockDim.x) La[t] = (T)A[t];
+  }
+  __syncthreads();
+  // further chunks: forward substitution with the finished factor
+  for (int c0 = w0; c0 < nc; c0 += NCH) {
+    const int w = min(NCH, nc - c0);
+    load_chunk(c0, w);
     __syncthreads();
     for (int k = 0; k < m; ++k) {
-      if (threadIdx.x < w) X[threadIdx.x * ld + k] *= (T)rinv[k];
+      for (int cc = threadIdx.x; cc < w; cc += blockDim.x) X[cc * ld + k] *= (T)rinv[k];
       __syncthreads();
       const int rem = m - k - 1;
       for (int t = threadIdx.x; t < rem * w; t += blockDim.x) {
@@ -132,12 +165,7 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
       }
       __syncthreads();
     }
-    T* Q = (T*)Fd->Q;
-    for (int t = threadIdx.x; t < w * m; t += blockDim.x) {
-      int cc = t / m, i = t % m;
-      int code = clist[c0 + cc], l = code >> 8, q = code & 255;
-      Q[((size_t)l * cap + q) * n + s + i] = X[cc * ld + i];
-    }
+    store_chunk(c0, w);
     __syncthreads();
   }
 }
@@ -1145,7 +1173,7 @@ size_t leaf_factor_smem(int Bm, int L, int cap, int prec) {
   const size_t ld = Bm + 1;
   size_t b = (size_t)Bm * ld * sizeof(double);                   // FP64 Cholesky
   if (prec) b += ((size_t)Bm * ld + 1) / 2 * sizeof(double);      // FP32 copy of L
-  b += (size_t)LF_NCH * ld * (prec ? sizeof(float) : sizeof(double));  // right-hand sides
+  b += (size_t)lf_nch(Bm) * ld * (prec ? sizeof(float) : sizeof(double));  // right-hand sides
   b += 16 + 40 * sizeof(double) + (4 + (size_t)L * cap) * sizeof(int);
   return b;
 }
