@@ -323,13 +323,14 @@ __device__ inline bool group_reduce(double* dst, const double* src_local, int co
 
 
 // ---------------------------------------------------------------------------
-// Tiled, output-major reductions for the general level kernel: a tile of rows
-// is staged in shared memory (coalesced loads), each output entry is owned by a
-// group of threads that walk disjoint rows of the tile, and the groups' partial
-// sums are combined by one short shared-memory loop per output.  FP64
-// instructions go to products of nonzero entries only.
+// Tiled, output-major reductions for the general level kernel: tiles of rows
+// are staged in shared memory (coalesced loads, two buffers: the next tile's
+// asynchronous copies are in flight while the current one is reduced), each
+// output entry is owned by a group of threads that walk disjoint rows of the
+// tile, and the groups' partial sums are combined by a short pairwise tree.
+// FP64 instructions go to products of nonzero entries only.
 // ---------------------------------------------------------------------------
-#define LV_TR 256  // rows per staged tile (fewer barriers per row)
+#define LV_TR 128  // rows per staged tile
 #define LV_TRP (LV_TR + 1)
 
 __device__ __forceinline__ void pair_decode(int o, int r, int& a, int& b) {
@@ -342,12 +343,51 @@ __device__ __forceinline__ void pair_decode(int o, int r, int& a, int& b) {
   b = a + rem;
 }
 
+// 8-byte asynchronous global -> shared copy (cp.async), its group commit and wait.
+__device__ __forceinline__ void cp_async8(double* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Stage rows [p0, p0 + tr) of ncol columns (column c at col(c)) into a tile
+// (column c at c * LV_TRP): asynchronous copies for FP64 storage, converting
+// loads for FP32 storage.
+template <typename T, typename ColF>
+__device__ __forceinline__ void stage_tile(double* tile, int ncol, int p0, int tr, ColF col) {
+  for (int i = threadIdx.x; i < ncol * tr; i += blockDim.x) {
+    const int c = i / tr, p = i - c * tr;
+    const T* src = col(c) + p0 + p;
+    if constexpr (sizeof(T) == sizeof(double)) cp_async8(tile + c * LV_TRP + p, src);
+    else tile[c * LV_TRP + p] = to_d(*src);
+  }
+}
+
+// Walk the tiles of rows [a0, a1) with double buffering: body(tile, tr) runs on
+// each staged tile by every thread (tbuf: doubles per buffer).
+template <typename T, typename ColF, typename BodyF>
+__device__ __forceinline__ void tile_walk(double* tile, int tbuf, int ncol, int a0, int a1, ColF col, BodyF body) {
+  const int nt = a1 > a0 ? (a1 - a0 + LV_TR - 1) / LV_TR : 0;
+  if (nt > 0) stage_tile<T>(tile, ncol, a0, min(LV_TR, a1 - a0), col);
+  cp_async_commit();
+  for (int k = 0; k < nt; ++k) {
+    const int pn = a0 + (k + 1) * LV_TR;
+    if (k + 1 < nt) stage_tile<T>(tile + ((k + 1) & 1) * tbuf, ncol, pn, min(LV_TR, a1 - pn), col);
+    cp_async_commit();
+    cp_async_wait_prev();  // this thread's copies of tile k have landed
+    __syncthreads();       // ... and every thread's
+    body(tile + (k & 1) * tbuf, min(LV_TR, a1 - (a0 + k * LV_TR)));
+    __syncthreads();       // the buffer is free for tile k + 2
+  }
+}
+
 // Packed Gram matrix: Gp[q] = sum over rows [a0, a1) of X[a][p] X[b][p] for the
 // pair (a, b), a <= b < r, q = pair index (row-major upper triangle).  More
 // pairs than threads are taken in chunks of blockDim.x pairs.
 template <typename T>
-__device__ void gram_tiled(const T* __restrict__ Xb, int64_t n, int r, int a0, int a1, double* tile, double* part,
-                           double* Gp) {
+__device__ void gram_tiled(const T* __restrict__ Xb, int64_t n, int r, int a0, int a1, double* tile, int tbuf,
+                           double* part, double* Gp) {
   const int np_all = r * (r + 1) / 2;
   const int t = threadIdx.x;
   for (int q0 = 0; q0 < np_all; q0 += blockDim.x) {
@@ -358,18 +398,11 @@ __device__ void gram_tiled(const T* __restrict__ Xb, int64_t n, int r, int a0, i
     int a = 0, b = 0;
     pair_decode(q0 + o, r, a, b);
     double acc = 0.0;
-    for (int p0 = a0; p0 < a1; p0 += LV_TR) {
-      const int tr = min(LV_TR, a1 - p0);
-      __syncthreads();
-      for (int i = t; i < r * tr; i += blockDim.x) {
-        const int c = i / tr, p = i % tr;
-        tile[c * LV_TRP + p] = to_d(Xb[(size_t)c * n + p0 + p]);
-      }
-      __syncthreads();
-      if (active)
-        for (int p = gidx; p < tr; p += ng) acc += tile[a * LV_TRP + p] * tile[b * LV_TRP + p];
-    }
-    __syncthreads();
+    tile_walk<T>(tile, tbuf, r, a0, a1, [&](int c) { return Xb + (size_t)c * n; },
+                 [&](const double* tl, int tr) {
+                   if (active)
+                     for (int p = gidx; p < tr; p += ng) acc += tl[a * LV_TRP + p] * tl[b * LV_TRP + p];
+                 });
     if (active) part[gidx * np + o] = acc;
     __syncthreads();
     // pairwise tree over the ng group partials, all outputs at once (few FP64
@@ -402,7 +435,7 @@ __device__ void gram_unpack(const double* Gp, int r, double* G, int ldg) {
 // Pm[a * W + j] = sum over rows [a0, a1) of Q[a][p] B_j[p], products in the storage precision.
 template <typename T, int W>
 __device__ void proj_tiled(const T* __restrict__ Qb, T* const* Bp, int w, int64_t n, int r, int a0, int a1,
-                           double* tile, double* part, double* Pm) {
+                           double* tile, int tbuf, double* part, double* Pm) {
   const int np = r * w;
   const int ng = max(1, (int)blockDim.x / np);
   const int t = threadIdx.x;
@@ -410,18 +443,11 @@ __device__ void proj_tiled(const T* __restrict__ Qb, T* const* Bp, int w, int64_
   const int o = active ? t % np : 0, gidx = active ? t / np : 0;
   const int a = o / w, j = o % w;
   T acc = (T)0;
-  for (int p0 = a0; p0 < a1; p0 += LV_TR) {
-    const int tr = min(LV_TR, a1 - p0);
-    __syncthreads();
-    for (int i = t; i < (r + w) * tr; i += blockDim.x) {
-      const int c = i / tr, p = i % tr;
-      tile[c * LV_TRP + p] = c < r ? to_d(Qb[(size_t)c * n + p0 + p]) : to_d(Bp[c - r][p0 + p]);
-    }
-    __syncthreads();
-    if (active)
-      for (int p = gidx; p < tr; p += ng) acc += (T)tile[a * LV_TRP + p] * (T)tile[(r + j) * LV_TRP + p];
-  }
-  __syncthreads();
+  tile_walk<T>(tile, tbuf, r + w, a0, a1, [&](int c) { return c < r ? Qb + (size_t)c * n : (const T*)Bp[c - r]; },
+               [&](const double* tl, int tr) {
+                 if (active)
+                   for (int p = gidx; p < tr; p += ng) acc += (T)tl[a * LV_TRP + p] * (T)tl[(r + j) * LV_TRP + p];
+               });
   if (active) part[gidx * np + o] = (double)acc;
   __syncthreads();
   for (int gw = ng; gw > 1;) {  // pairwise tree over the group partials
@@ -478,8 +504,9 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
   double* RU = Ri2 + cc2;                 // R1, then R = R2 R1 of the left side
   double* RV = RU + cc2;                  // ... of the right side
   double* rvs = RV + cc2;                 // 2 x 8 reciprocal pivots (serial small factorizations)
-  double* tile = rvs + 16;                // (ldm + W) x LV_TRP row tile
-  double* part = tile + (ldm + W) * LV_TRP;  // 256 group partial sums
+  const int tbuf = (ldm + W) * LV_TRP;    // doubles per row tile
+  double* tile = rvs + 16;                // two (ldm + W) x LV_TRP row tiles
+  double* part = tile + 2 * tbuf;         // 256 group partial sums
   double* tmp = part + 256;               // LV_RED
   double* Pm = tmp + LV_RED;              // 2ldm x W
   T* Tm = (T*)(Pm + 2 * ldm * W);      // 2ldm x W, storage precision
@@ -498,8 +525,8 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
   const int sa0 = max(r0, s), sa1 = min(r1, h), sb0 = max(r0, h), sb1 = min(r1, e);
   if (threadIdx.x == 0) iflag[2] = 0;
   for (int pass = 0; pass < 2; ++pass) {
-    gram_tiled<T>(Qb, n, r, sa0, sa1, tile, part, Ri);
-    gram_tiled<T>(Qb, n, r, sb0, sb1, tile, part, Ri + npk);
+    gram_tiled<T>(Qb, n, r, sa0, sa1, tile, tbuf, part, Ri);
+    gram_tiled<T>(Qb, n, r, sb0, sb1, tile, tbuf, part, Ri + npk);
     if (!group_reduce(Ri, Ri, 2 * npk, G, g, base, gpart, pstride, bar, phase, status, abort_flag, part)) return;
     gram_unpack(Ri, r, Gm, ldm);
     gram_unpack(Ri + npk, r, Gm2, ldm);
@@ -554,7 +581,7 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
   const int r2 = 2 * r, ld2 = 2 * cap;
   double* Zf = Fd->Zf + (size_t)nid * ld2 * ld2;
   double* Zi = Fd->Zi + (size_t)nid * ld2 * ld2;
-  if (g == 0 && 8 * ldm * ldm <= (ldm + W) * LV_TRP) {
+  if (g == 0 && 8 * ldm * ldm <= 2 * tbuf) {
     // S and its inverse factor in shared memory (the row tile is free here),
     // so the serial pivot chain never waits on global memory
     double* Sm = tile;
@@ -655,8 +682,8 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
     }
     for (int t = threadIdx.x; t < 2 * ldm * W; t += blockDim.x) Pm[t] = 0.0;
     __syncthreads();
-    proj_tiled<T, W>(Qb, Bp, w, n, r, max(r0, s), min(r1, h), tile, part, Pm);
-    proj_tiled<T, W>(Qb, Bp, w, n, r, max(r0, h), min(r1, e), tile, part, Pm + r * W);
+    proj_tiled<T, W>(Qb, Bp, w, n, r, max(r0, s), min(r1, h), tile, tbuf, part, Pm);
+    proj_tiled<T, W>(Qb, Bp, w, n, r, max(r0, h), min(r1, e), tile, tbuf, part, Pm + r * W);
     if (!group_reduce(Pm, Pm, r2 * W, G, g, base, gpart, pstride, bar, phase, status, abort_flag, part)) return;
     for (int t = threadIdx.x; t < r2 * W; t += blockDim.x) {
       const int a = t / W, j = t % W;
@@ -1179,7 +1206,7 @@ size_t leaf_factor_smem(int Bm, int L, int cap, int prec) {
 }
 size_t level_smem(int ldm, int cap) {
   const size_t W = LEVEL_W(ldm);
-  return ((size_t)6 * ldm * ldm + 16 + (size_t)(ldm + W) * LV_TRP + 256 + LV_RED + 4 * (size_t)ldm * W) * sizeof(double) +
+  return ((size_t)6 * ldm * ldm + 16 + 2 * (size_t)(ldm + W) * LV_TRP + 256 + LV_RED + 4 * (size_t)ldm * W) * sizeof(double) +
          W * sizeof(void*) + (4 + (size_t)FIFA_LEVELS_MAX * cap) * sizeof(int);
 }
 
