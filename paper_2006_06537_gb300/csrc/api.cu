@@ -164,19 +164,26 @@ static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, const int*
       if (Gl[l] < 2) Gl[l] = 1;
     }
   }
-  std::vector<int4> coop, solo;
+  // blocks whose node spans <= 2 ACA_WARP_MAX rows take one warp each
+  std::vector<int4> coop, solo, warp;
   for (int l = 0; l < P->L; ++l) {
+    const int off = (1 << l) - 1 + l;
     for (int i = 0; i < (1 << l); ++i) {
+      const int len = P->bnd_host[off + i + 1] - P->bnd_host[off + i];
       if (Gl[l] > 1)
         for (int g = 0; g < Gl[l]; ++g) coop.push_back(make_int4(l, i, g, Gl[l]));
+      else if (len <= 2 * ACA_WARP_MAX)
+        warp.push_back(make_int4(l, i, 0, 1));
       else
         solo.push_back(make_int4(l, i, 0, 1));
     }
   }
   P->aca_ncoop = (int)coop.size();
   P->aca_nsolo = (int)solo.size();
+  P->aca_nwarp = (int)warp.size();
   P->work_host = coop;
   P->work_host.insert(P->work_host.end(), solo.begin(), solo.end());
+  P->work_host.insert(P->work_host.end(), warp.begin(), warp.end());
   // factor / sweep groups per level: levels with fewer nodes than the
   // co-resident CTAs split each node's rows over a group of CTAs (>= 1024 rows
   // each) that fills the GPU; each rank bucket's kernel has its own CTAs per SM
@@ -507,6 +514,7 @@ fifa_status hmat_assemble_enqueue(fifa_ctx* ctx, fifa_hmat* H) {
     CK(launch_aca(H->dev, P->aca_work, P->aca_ncoop, true, S.aca_part, S.aca_bar, S.flags, s));
   }
   if (P->aca_nsolo > 0) CK(launch_aca(H->dev, P->aca_work + P->aca_ncoop, P->aca_nsolo, false, S.aca_part, S.aca_bar, S.flags, s));
+  if (P->aca_nwarp > 0) CK(launch_aca_warp(H->dev, P->aca_work + P->aca_ncoop + P->aca_nsolo, P->aca_nwarp, s));
   return FIFA_OK;
 }
 

@@ -24,7 +24,7 @@ struct Plan {
   std::vector<int> bnd_host;
   int* bnd_dev = nullptr;
   int4* aca_work = nullptr;  // coop entries first, then solo entries
-  int aca_ncoop = 0, aca_nsolo = 0;
+  int aca_ncoop = 0, aca_nsolo = 0, aca_nwarp = 0;
   std::vector<int4> work_host;
   size_t work_off = 0, dev_bytes = 0;  // device block: bounds, then the work list at work_off
   std::vector<int> lvl_G[3], sweep_G;  // lvl_G[b]: group size of the level kernel of rank bucket b

@@ -163,14 +163,22 @@ __device__ inline double block_sum(double v, double* sh) {
 }
 
 // (value, index) argmax with ties to the lowest index; value -1 = none.
+// Values are absolute values (>= 0, never NaN) or exactly -1, so their IEEE
+// bit patterns read as signed 64-bit integers order the same way: the
+// comparisons run on the integer pipe, not the FP64 one.
 struct ArgMax {
   double v;
   int i;
   double sv;  // signed value carried along
 };
 __device__ __forceinline__ ArgMax am_better(ArgMax a, ArgMax b) {
-  if (b.v > a.v || (b.v == a.v && b.i < a.i)) return b;
+  const long long av = __double_as_longlong(a.v), bv = __double_as_longlong(b.v);
+  if (bv > av || (bv == av && b.i < a.i)) return b;
   return a;
+}
+// max of two values >= 0 or -1 (same ordering argument)
+__device__ __forceinline__ double nn_max(double a, double b) {
+  return __double_as_longlong(b) > __double_as_longlong(a) ? b : a;
 }
 __device__ __forceinline__ ArgMax warp_argmax(ArgMax a) {
   for (int o = 16; o > 0; o >>= 1) {
@@ -199,15 +207,16 @@ __device__ inline ArgMax block_argmax(ArgMax a, ArgMax* sh) {
   __syncthreads();
   return r;
 }
+// Block max of values >= 0 (or -1); result valid in every thread.
 __device__ __forceinline__ double block_max(double v, double* sh) {
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = nn_max(v, __shfl_down_sync(0xffffffffu, v, o));
   __syncthreads();
   if (lane == 0) sh[w] = v;
   __syncthreads();
   if (w == 0) {
     double t = lane < nw ? sh[lane] : -1.0;
-    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
+    for (int o = 16; o > 0; o >>= 1) t = nn_max(t, __shfl_down_sync(0xffffffffu, t, o));
     if (lane == 0) sh[32] = t;
   }
   __syncthreads();

@@ -5,6 +5,8 @@
 #include "fifa_common.cuh"
 
 cudaError_t launch_leaf_assemble(const HmatDesc* Hd, int nleaf, cudaStream_t st);
+#define ACA_WARP_MAX 128  // largest side of a block that the warp-per-block ACA takes
+cudaError_t launch_aca_warp(const HmatDesc* Hd, const int4* work, int nwork, cudaStream_t st);
 cudaError_t launch_aca(const HmatDesc* Hd, const int4* work, int ncta, bool cooperative, ArgMax* part,
                        unsigned int* bar, int* abort_flag, cudaStream_t st);
 int aca_max_coresident_ctas();

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256, 3) k_aca(const HmatDesc* __restrict__ Hd,
         for (int l = 0; l < k; ++l)
           acc = __dsub_rn(acc, __dmul_rn(Bs[(size_t)l * n + s + ii], __ldcg(Bs + (size_t)l * n + h + js)));
         Bs[(size_t)k * n + s + ii] = acc;
-        umax = fmax(umax, fabs(acc));
+        umax = nn_max(umax, fabs(acc));
         bool used = (ii == i);
         for (int l = 0; l < k; ++l) used |= (rowp[l] == ii);
         if (!used) nb = am_better(nb, ArgMax{fabs(acc), ii, acc});
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256, 3) k_aca(const HmatDesc* __restrict__ Hd,
         ArgMax t{-1.0, 0x7fffffff, 0.0};
         for (int q = threadIdx.x; q < G; q += blockDim.x) {
           const ArgMax* pq = part + 3 * (base + q);
-          tm = fmax(tm, __ldcg(&pq[1].v));
+          tm = nn_max(tm, __ldcg(&pq[1].v));
           t = am_better(t, ArgMax{__ldcg(&pq[2].v), __ldcg(&pq[2].i), __ldcg(&pq[2].sv)});
         }
         umax = block_max(tm, shD);
@@ -191,8 +191,113 @@ __global__ void __launch_bounds__(256, 3) k_aca(const HmatDesc* __restrict__ Hd,
 }
 
 // ---------------------------------------------------------------------------
+// ACA of small blocks (both sides <= ACA_WARP_MAX rows): one warp per block,
+// eight independent blocks per CTA.  Same arithmetic and pivot rules as k_aca
+// with G = 1 (so the same bases, bit for bit); the reductions are warp
+// shuffles, with no CTA barrier and no idle warps in them.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ ArgMax warp_argmax_all(ArgMax a) {
+  for (int o = 16; o > 0; o >>= 1) {
+    ArgMax b;
+    b.v = __shfl_xor_sync(0xffffffffu, a.v, o);
+    b.i = __shfl_xor_sync(0xffffffffu, a.i, o);
+    b.sv = __shfl_xor_sync(0xffffffffu, a.sv, o);
+    a = am_better(a, b);
+  }
+  return a;
+}
+
+__global__ void __launch_bounds__(256) k_aca_warp(const HmatDesc* __restrict__ Hd, const int4* __restrict__ work,
+                                                  int nwork) {
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int item = blockIdx.x * 8 + wl;
+  if (item >= nwork) return;  // whole warp
+  const int4 w = work[item];
+  const int lvl = w.x, bi = w.y;
+  const int64_t n = Hd->n;
+  const int cap = Hd->cap, kind = Hd->kind;
+  const double kc = Hd->kc, eps = Hd->eps;
+  const double* __restrict__ x = Hd->x;
+  double* Bs = Hd->bases + (size_t)lvl * cap * n;
+  int s, h, e;
+  node_range(Hd->bnd, lvl, bi, s, h, e);
+  const int m = h - s, p = e - h;
+  const int nid = node_id(lvl, bi);
+  __shared__ int rowp_all[8][FIFA_CAP_MAX], colp_all[8][FIFA_CAP_MAX];
+  int* rowp = rowp_all[wl];
+  int* colp = colp_all[wl];
+
+  int i = m - 1, k = 0;
+  bool hit = false;
+  if (m > 0 && p > 0)
+    while (true) {
+      if (k == cap) { hit = true; break; }
+      // residual of row i, stored unnormalised in V[:, k]
+      const double xi = x[s + i];
+      ArgMax best{-1.0, 0x7fffffff, 0.0};
+      for (int j = lane; j < p; j += 32) {
+        double acc = kern_entry(kind, kc, xi, x[h + j]);
+        for (int l = 0; l < k; ++l)
+          acc = __dsub_rn(acc, __dmul_rn(__ldcg(Bs + (size_t)l * n + s + i), __ldcg(Bs + (size_t)l * n + h + j)));
+        Bs[(size_t)k * n + h + j] = acc;
+        bool used = false;
+        for (int l = 0; l < k; ++l) used |= (colp[l] == j);
+        if (!used) best = am_better(best, ArgMax{fabs(acc), j, acc});
+      }
+      best = warp_argmax_all(best);
+      if (!(best.v > 0.0)) break;
+      const int js = best.i;
+      const double piv = best.sv;
+      for (int j = lane; j < p; j += 32) {
+        double* vp = Bs + (size_t)k * n + h + j;
+        *vp = __ddiv_rn(*vp, piv);
+      }
+      __syncwarp();
+      // residual of column js, stored in U[:, k]
+      const double xj = x[h + js];
+      double umax = 0.0;
+      ArgMax nb{-1.0, 0x7fffffff, 0.0};
+      for (int ii = lane; ii < m; ii += 32) {
+        double acc = kern_entry(kind, kc, x[s + ii], xj);
+        for (int l = 0; l < k; ++l)
+          acc = __dsub_rn(acc, __dmul_rn(__ldcg(Bs + (size_t)l * n + s + ii), __ldcg(Bs + (size_t)l * n + h + js)));
+        Bs[(size_t)k * n + s + ii] = acc;
+        umax = nn_max(umax, fabs(acc));
+        bool used = (ii == i);
+        for (int l = 0; l < k; ++l) used |= (rowp[l] == ii);
+        if (!used) nb = am_better(nb, ArgMax{fabs(acc), ii, acc});
+      }
+      for (int o = 16; o > 0; o >>= 1) umax = nn_max(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+      nb = warp_argmax_all(nb);
+      if (umax <= eps) break;
+      if (lane == 0) {
+        rowp[k] = i;
+        colp[k] = js;
+      }
+      __syncwarp();
+      ++k;
+      if (nb.v < 0.0) break;
+      i = nb.i;
+    }
+  if (lane == 0) {
+    Hd->rank[nid] = k;
+    for (int l = 0; l < cap; ++l) {
+      Hd->row_piv[nid * cap + l] = l < k ? rowp[l] : -1;
+      Hd->col_piv[nid * cap + l] = l < k ? colp[l] : -1;
+    }
+    if (hit) atomicOr(Hd->status, FIFA_DEV_RANK_CAP);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
+cudaError_t launch_aca_warp(const HmatDesc* Hd, const int4* work, int nwork, cudaStream_t st) {
+  if (nwork <= 0) return cudaSuccess;
+  k_aca_warp<<<(nwork + 7) / 8, 256, 0, st>>>(Hd, work, nwork);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_leaf_assemble(const HmatDesc* Hd, int nleaf, cudaStream_t st) {
   k_leaf_assemble<<<nleaf, 256, 0, st>>>(Hd);
   return cudaGetLastError();
