@@ -350,6 +350,7 @@ __device__ __forceinline__ void cp_async8(double* sdst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Stage rows [p0, p0 + tr) of ncol columns (column c at col(c)) into a tile
 // (column c at c * LV_TRP): asynchronous copies for FP64 storage, converting
@@ -896,6 +897,10 @@ __global__ void __launch_bounds__(128) k_level_small(const FactDesc* __restrict_
 // ---------------------------------------------------------------------------
 #define LM_W 8  // ancestor columns per chunk
 
+// Double-buffered ancestor chunks only for one node per CTA: with several
+// nodes the second buffer costs a co-resident CTA per SM (measured slower).
+template <int NPC> struct LmDB { static constexpr int nbuf = NPC == 1 ? 2 : 1; };
+
 template <int R, int MS, int NPC>
 struct LmLayout {
   static constexpr int R2 = 2 * R;
@@ -906,8 +911,8 @@ struct LmLayout {
   static constexpr size_t pm = (size_t)NPC * R2 * LM_W;    // Pm / Tm
   static constexpr size_t doubles = xs + 3 * mats + (size_t)NPC * 2 * R + 2 * ruv + 2 * sm + pm;
   static size_t bytes(int elt) {
-    return doubles * sizeof(double) + (size_t)NPC * LM_W * 2 * MS * elt + pm * elt +
-           (size_t)NPC * (FIFA_LEVELS_MAX + 1 + LM_W + 8) * sizeof(int) + 64;
+    return doubles * sizeof(double) + (size_t)LmDB<NPC>::nbuf * NPC * LM_W * 2 * MS * elt + pm * elt +
+           (size_t)NPC * (FIFA_LEVELS_MAX + 1 + LmDB<NPC>::nbuf * LM_W + 8) * sizeof(int) + 64;
   }
 };
 
@@ -927,12 +932,13 @@ __global__ void __launch_bounds__(256) k_level_multi(const FactDesc* __restrict_
   double* S = RV + LY::ruv;               // [j][R2*R2]
   double* Si = S + LY::sm;
   double* Pm = Si + LY::sm;               // [j][R2][LM_W]
-  T* Bs = (T*)(Pm + LY::pm);              // [j][LM_W][2 MS]
-  T* Tm = Bs + (size_t)NPC * LM_W * 2 * MS;  // [j][R2][LM_W]
+  constexpr int NB = LmDB<NPC>::nbuf;
+  T* Bs2 = (T*)(Pm + LY::pm);             // NB buffers of [j][LM_W][2 MS]
+  T* Tm = Bs2 + NB * (size_t)NPC * LM_W * 2 * MS;  // [j][R2][LM_W]
   int* ib = (int*)(Tm + LY::pm);
   int* rpre = ib;                          // [j][LEVELS_MAX + 1]
-  int* ccode = rpre + NPC * (FIFA_LEVELS_MAX + 1);  // [j][LM_W]
-  int* info = ccode + NPC * LM_W;          // [j][8]: r, s, h, e, active, ok
+  int* ccode2 = rpre + NPC * (FIFA_LEVELS_MAX + 1);  // NB buffers of [j][LM_W]
+  int* info = ccode2 + NB * NPC * LM_W;    // [j][8]: r, s, h, e, active, ok
 
   const int cap = Fd->cap, nleaf = Fd->nleaf;
   const int64_t n = Fd->n;
@@ -1069,8 +1075,17 @@ __global__ void __launch_bounds__(256) k_level_multi(const FactDesc* __restrict_
         }
       double srv[R2];
       if (!thr_chol_upper(Sj, R2, r2, srv, clamp_cap<T>())) in[5] = 0;
+      // log det L_S from one logarithm of the pivots' product (a serial chain
+      // of r2 logarithms here costs more than the rest of the node's algebra);
+      // a product out of range falls back to the sum of logarithms
+      double prod = 1.0;
+      for (int k = 0; k < r2; ++k) prod *= Sj[k * R2 + k];
       double ls = 0.0;
-      for (int k = 0; k < r2; ++k) ls += log(Sj[k * R2 + k]);
+      if (prod > 0.0 && prod < INFINITY && prod > 1e-300) {
+        ls = log(prod);
+      } else {
+        for (int k = 0; k < r2; ++k) ls += log(Sj[k * R2 + k]);
+      }
       thr_triinv_upper(Sj, R2, srv, Si + j * R2 * R2, R2, r2);
       const int nid = node_id(lvl, b0 + j), ld2 = 2 * cap;
       double* Zf = Fd->Zf + (size_t)nid * ld2 * ld2;
@@ -1098,8 +1113,10 @@ __global__ void __launch_bounds__(256) k_level_multi(const FactDesc* __restrict_
   int nmax = 0;
   for (int j = 0; j < NPC; ++j)
     if (info[j * 8 + 4]) nmax = max(nmax, rpre[j * (FIFA_LEVELS_MAX + 1) + lvl]);
-  // B <- B + Q (L_S^-1 - I) Q^T B for every ancestor column, LM_W at a time
-  for (int c0 = 0; c0 < nmax; c0 += LM_W) {
+  // B <- B + Q (L_S^-1 - I) Q^T B for every ancestor column, LM_W at a time;
+  // the next chunk's columns are copied in (asynchronously for FP64 storage)
+  // while the current chunk is projected and updated
+  auto chunk_codes = [&](int c0, int* cc) {
     if (tid < NPC * LM_W) {
       const int j = tid / LM_W, w = tid % LM_W;
       const int* rp = rpre + j * (FIFA_LEVELS_MAX + 1);
@@ -1110,17 +1127,48 @@ __global__ void __launch_bounds__(256) k_level_multi(const FactDesc* __restrict_
         while (rp[a + 1] <= c) ++a;
         code = (a << 8) | (c - rp[a]);
       }
-      ccode[tid] = code;
+      cc[tid] = code;
     }
-    __syncthreads();
+  };
+  auto chunk_stage = [&](const int* cc, T* B) {
     for (int t = tid; t < NPC * LM_W * 2 * MS; t += nt) {
       const int j = t / (LM_W * 2 * MS), w = (t / (2 * MS)) % LM_W, p = t % (2 * MS);
-      const int code = ccode[j * LM_W + w];
+      const int code = cc[j * LM_W + w];
       const int* in = info + j * 8;
-      T v = (T)0;
-      if (code >= 0 && p < in[3] - in[1])
-        v = Qall[((size_t)(code >> 8) * cap + (code & 255)) * n + in[1] + p];
-      Bs[t] = v;
+      if (code >= 0 && p < in[3] - in[1]) {
+        const T* src = Qall + ((size_t)(code >> 8) * cap + (code & 255)) * n + in[1] + p;
+        if constexpr (sizeof(T) == sizeof(double)) cp_async8((double*)(B + t), src);
+        else B[t] = *src;
+      } else {
+        B[t] = (T)0;
+      }
+    }
+  };
+  if (NB == 2) {
+    chunk_codes(0, ccode2);
+    __syncthreads();
+    chunk_stage(ccode2, Bs2);
+    cp_async_commit();
+  }
+  for (int c0 = 0, k = 0; c0 < nmax; c0 += LM_W, ++k) {
+    const int cur = NB == 2 ? (k & 1) : 0;
+    const int* ccode = ccode2 + cur * NPC * LM_W;
+    const T* Bs = Bs2 + (size_t)cur * NPC * LM_W * 2 * MS;
+    if (NB == 2) {
+      int* cnext = ccode2 + (cur ^ 1) * NPC * LM_W;
+      T* bnext = Bs2 + (size_t)(cur ^ 1) * NPC * LM_W * 2 * MS;
+      const bool more = c0 + LM_W < nmax;
+      if (more) chunk_codes(c0 + LM_W, cnext);
+      __syncthreads();
+      if (more) chunk_stage(cnext, bnext);
+      cp_async_commit();
+      cp_async_wait_prev();  // this chunk's copies have landed
+    } else {
+      chunk_codes(c0, ccode2);
+      __syncthreads();
+      chunk_stage(ccode2, Bs2);
+      cp_async_commit();
+      cp_async_wait_all();
     }
     __syncthreads();
     // P[a][w] = Q^T B (rows a < r from the left child, r <= a < 2r from the right)
