@@ -171,11 +171,11 @@ struct ArgMax {
   int i;
   double sv;  // signed value carried along
 };
-__device__ __forceinline__ ArgMax am_better(ArgMax a, ArgMax b) {
+__device__ __forceinline__ bool am_wins(const ArgMax& a, const ArgMax& b) {  // b beats a
   const long long av = __double_as_longlong(a.v), bv = __double_as_longlong(b.v);
-  if (bv > av || (bv == av && b.i < a.i)) return b;
-  return a;
+  return bv > av || (bv == av && b.i < a.i);
 }
+__device__ __forceinline__ ArgMax am_better(ArgMax a, ArgMax b) { return am_wins(a, b) ? b : a; }
 // max of two values >= 0 or -1 (same ordering argument)
 __device__ __forceinline__ double nn_max(double a, double b) {
   return __double_as_longlong(b) > __double_as_longlong(a) ? b : a;

@@ -112,9 +112,14 @@ __global__ void __launch_bounds__(256, 3) k_aca(const HmatDesc* __restrict__ Hd,
         for (int l = 0; l < k; ++l)
           acc = __dsub_rn(acc, __dmul_rn(__ldcg(Bs + (size_t)l * n + s + i), Bs[(size_t)l * n + h + j]));
         Bs[(size_t)k * n + h + j] = acc;
-        bool used = false;
-        for (int l = 0; l < k; ++l) used |= (colp[l] == j);
-        if (!used) best = am_better(best, ArgMax{fabs(acc), j, acc});
+        // an entry that would win is checked against the used columns (the
+        // check runs only then: same result as checking every entry)
+        const ArgMax cand{fabs(acc), j, acc};
+        if (am_wins(best, cand)) {
+          bool used = false;
+          for (int l = 0; l < k; ++l) used |= (colp[l] == j);
+          if (!used) best = cand;
+        }
       }
       best = block_argmax(best, shA);
       if (G > 1) {
@@ -145,9 +150,12 @@ __global__ void __launch_bounds__(256, 3) k_aca(const HmatDesc* __restrict__ Hd,
           acc = __dsub_rn(acc, __dmul_rn(Bs[(size_t)l * n + s + ii], __ldcg(Bs + (size_t)l * n + h + js)));
         Bs[(size_t)k * n + s + ii] = acc;
         umax = nn_max(umax, fabs(acc));
-        bool used = (ii == i);
-        for (int l = 0; l < k; ++l) used |= (rowp[l] == ii);
-        if (!used) nb = am_better(nb, ArgMax{fabs(acc), ii, acc});
+        const ArgMax cand{fabs(acc), ii, acc};
+        if (am_wins(nb, cand)) {
+          bool used = (ii == i);
+          for (int l = 0; l < k; ++l) used |= (rowp[l] == ii);
+          if (!used) nb = cand;
+        }
       }
       umax = block_max(umax, shD);
       nb = block_argmax(nb, shA);
@@ -207,7 +215,7 @@ __device__ __forceinline__ ArgMax warp_argmax_all(ArgMax a) {
   return a;
 }
 
-__global__ void __launch_bounds__(256) k_aca_warp(const HmatDesc* __restrict__ Hd, const int4* __restrict__ work,
+__global__ void __launch_bounds__(256, 3) k_aca_warp(const HmatDesc* __restrict__ Hd, const int4* __restrict__ work,
                                                   int nwork) {
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.x * 8 + wl;
@@ -240,9 +248,14 @@ __global__ void __launch_bounds__(256) k_aca_warp(const HmatDesc* __restrict__ H
         for (int l = 0; l < k; ++l)
           acc = __dsub_rn(acc, __dmul_rn(__ldcg(Bs + (size_t)l * n + s + i), __ldcg(Bs + (size_t)l * n + h + j)));
         Bs[(size_t)k * n + h + j] = acc;
-        bool used = false;
-        for (int l = 0; l < k; ++l) used |= (colp[l] == j);
-        if (!used) best = am_better(best, ArgMax{fabs(acc), j, acc});
+        // an entry that would win is checked against the used columns (the
+        // check runs only then: same result as checking every entry)
+        const ArgMax cand{fabs(acc), j, acc};
+        if (am_wins(best, cand)) {
+          bool used = false;
+          for (int l = 0; l < k; ++l) used |= (colp[l] == j);
+          if (!used) best = cand;
+        }
       }
       best = warp_argmax_all(best);
       if (!(best.v > 0.0)) break;
@@ -263,9 +276,12 @@ __global__ void __launch_bounds__(256) k_aca_warp(const HmatDesc* __restrict__ H
           acc = __dsub_rn(acc, __dmul_rn(__ldcg(Bs + (size_t)l * n + s + ii), __ldcg(Bs + (size_t)l * n + h + js)));
         Bs[(size_t)k * n + s + ii] = acc;
         umax = nn_max(umax, fabs(acc));
-        bool used = (ii == i);
-        for (int l = 0; l < k; ++l) used |= (rowp[l] == ii);
-        if (!used) nb = am_better(nb, ArgMax{fabs(acc), ii, acc});
+        const ArgMax cand{fabs(acc), ii, acc};
+        if (am_wins(nb, cand)) {
+          bool used = (ii == i);
+          for (int l = 0; l < k; ++l) used |= (rowp[l] == ii);
+          if (!used) nb = cand;
+        }
       }
       for (int o = 16; o > 0; o >>= 1) umax = nn_max(umax, __shfl_xor_sync(0xffffffffu, umax, o));
       nb = warp_argmax_all(nb);

@@ -37,7 +37,14 @@ def make_ctx(B=64, eps=1e-12, cap=32, prec=fifa.FIFA_FP64, refine_max=3, indep=0
 def test_det_exp_bitwise():
     ctx = make_ctx()
     g = np.random.default_rng(0)
-    x = np.concatenate([-g.uniform(0, 708, 200000), -g.uniform(0, 1, 50000), [0.0, -708.0, -708.5, -1e-300]])
+    # inputs whose x 32/ln2 is exactly a half-integer: the range reduction's
+    # rounding ties (to even) must agree too
+    inv = float.fromhex("0x1.71547652b82fep+5")
+    m = np.arange(-32000, 0, 7, dtype=np.float64)
+    xt = (m + 0.5) / inv
+    ties = xt[(xt * inv) == (m + 0.5)]
+    assert len(ties) > 100
+    x = np.concatenate([-g.uniform(0, 708, 200000), -g.uniform(0, 1, 50000), ties, [0.0, -708.0, -708.5, -1e-300]])
     xd = dev(x, torch)
     out = torch.empty_like(xd)
     fifa.fifa_det_exp(ctx.h, xd, out, len(x))
