@@ -24,7 +24,7 @@
 __host__ __device__ inline int lf_nch(int Bm) { return Bm <= 64 ? 64 : 32; }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict__ Hd, const FactDesc* __restrict__ Fd) {
+__global__ void __launch_bounds__(256, 7) k_leaf_factor(const HmatDesc* __restrict__ Hd, const FactDesc* __restrict__ Fd) {
   extern __shared__ double sm[];
   Hd += blockIdx.y;  // problem of a batched launch (descriptor arrays)
   Fd += blockIdx.y;
@@ -96,36 +96,52 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const HmatDesc* __restrict_
     A[k * ld + k] = d * rs;
     rinv[k] = rs;
   };
-  if (threadIdx.x == 0) {
-    flag[0] = 0;
-    if (m > 0) pivot(0);
-  }
+  if (threadIdx.x == 0) flag[0] = 0;
+  // column k ready for its step: pivot, column k of L and row k of X scaled
+  // (warp 0 alone)
+  auto prep_column = [&](int k) {
+    const int lane = threadIdx.x;
+    if (lane == 0) pivot(k);
+    __syncwarp();
+    const double dinv = rinv[k];
+    for (int i = k + 1 + lane; i < m; i += 32) A[k * ld + i] *= dinv;
+    for (int cc = lane; cc < w0; cc += 32) X[cc * ld + k] *= (T)dinv;
+  };
+  __syncthreads();  // the first chunk of X is loaded
+  if (threadIdx.x < 32 && m > 0) prep_column(0);
   __syncthreads();
   // right-looking Cholesky with the first chunk of right-hand sides eliminated
-  // in the same steps (L^-1 X): per column k, one pass scales column k of L and
-  // row k of X, the next updates the trailing triangle and the rows of X below
-  // k, and the thread owning the next diagonal entry takes its pivot at once
+  // in the same steps (L^-1 X), one barrier per column: in step k warp 0
+  // updates column k + 1 and row k + 1 of X first and prepares column k + 1
+  // (pivot and scaling) for the next step, while the other warps update the
+  // rest of the trailing triangle and of X
   for (int k = 0; k < m; ++k) {
-    const double dinv = rinv[k];
-    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[k * ld + i] *= dinv;
-    for (int cc = threadIdx.x; cc < w0; cc += blockDim.x) X[cc * ld + k] *= (T)dinv;
-    __syncthreads();
-    // trailing update on the lower triangle only: t -> (a, b), b <= a, t = a(a+1)/2 + b
-    // (thread 0 owns t = 0, the next diagonal entry)
     const int w = m - k - 1;
-    for (int t = threadIdx.x; t < w * (w + 1) / 2; t += blockDim.x) {
-      int a = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-      if ((a + 1) * (a + 2) / 2 <= t) ++a;
-      if (a * (a + 1) / 2 > t) --a;
-      const int b = t - a * (a + 1) / 2;
-      const int i = k + 1 + a, j = k + 1 + b;
-      A[j * ld + i] -= A[k * ld + i] * A[k * ld + j];
+    if (threadIdx.x < 32) {
+      if (w > 0) {
+        const int lane = threadIdx.x;
+        const double lk1 = A[k * ld + k + 1];  // L[k+1][k]
+        for (int i = k + 1 + lane; i < m; i += 32) A[(k + 1) * ld + i] -= A[k * ld + i] * lk1;
+        for (int cc = lane; cc < w0; cc += 32) X[cc * ld + k + 1] -= (T)lk1 * X[cc * ld + k];
+        __syncwarp();
+        prep_column(k + 1);
+      }
+    } else {
+      const int t0 = threadIdx.x - 32, nt2 = blockDim.x - 32, w1 = w - 1;
+      // trailing triangle beyond column k + 1: t -> (a, b), b <= a, t = a(a+1)/2 + b
+      for (int t = t0; t < w1 * (w1 + 1) / 2; t += nt2) {
+        int a = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        if ((a + 1) * (a + 2) / 2 <= t) ++a;
+        if (a * (a + 1) / 2 > t) --a;
+        const int b = t - a * (a + 1) / 2;
+        const int i = k + 2 + a, j = k + 2 + b;
+        A[j * ld + i] -= A[k * ld + i] * A[k * ld + j];
+      }
+      for (int t = t0; t < w1 * w0; t += nt2) {
+        const int cc = t / w1, i = k + 2 + t % w1;
+        X[cc * ld + i] -= (T)A[k * ld + i] * X[cc * ld + k];
+      }
     }
-    for (int t = threadIdx.x; t < w * w0; t += blockDim.x) {
-      const int cc = t / w, i = k + 1 + t % w;
-      X[cc * ld + i] -= (T)A[k * ld + i] * X[cc * ld + k];
-    }
-    if (threadIdx.x == 0 && k + 1 < m) pivot(k + 1);
     __syncthreads();
   }
   double lsum = 0.0;
