@@ -313,6 +313,10 @@ fifa_status fifa_server_submit(fifa_server* server, const fifa_request* req, uin
 fifa_status fifa_server_wait(fifa_server* server, uint64_t id, double* mean_host, double* draws_host,
                              fifa_result* res);
 
+/* Non-blocking: *done_out = 1 if request `id` has finished (fifa_server_wait
+ * then returns at once), else 0.  INVALID_ARG for an unknown or collected id. */
+fifa_status fifa_server_poll(fifa_server* server, uint64_t id, int* done_out);
+
 fifa_status fifa_server_stats(fifa_server* server, fifa_server_counters* out);
 
 /* Finish the requests in flight, drop the queued ones, free the budget.  Call

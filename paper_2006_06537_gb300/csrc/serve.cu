@@ -281,6 +281,15 @@ extern "C" fifa_status fifa_server_wait(fifa_server* S, uint64_t id, double* mea
   return st;
 }
 
+extern "C" fifa_status fifa_server_poll(fifa_server* S, uint64_t id, int* done_out) {
+  if (!S || !done_out) return FIFA_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return FIFA_ERR_INVALID_ARG;
+  *done_out = it->second->done ? 1 : 0;
+  return FIFA_OK;
+}
+
 extern "C" fifa_status fifa_server_stats(fifa_server* S, fifa_server_counters* out) {
   if (!S || !out) return FIFA_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(S->mu);

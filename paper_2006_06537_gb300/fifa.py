@@ -100,6 +100,7 @@ def lib():
         "fifa_server_create": (C.c_int, [C.POINTER(fifa_server_opts), C.POINTER(_P)]),
         "fifa_server_submit": (C.c_int, [_P, C.POINTER(fifa_request), C.POINTER(C.c_uint64)]),
         "fifa_server_wait": (C.c_int, [_P, C.c_uint64, _P, _P, C.POINTER(fifa_result)]),
+        "fifa_server_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(C.c_int)]),
         "fifa_server_stats": (C.c_int, [_P, C.POINTER(fifa_server_counters)]),
         "fifa_server_destroy": (None, [_P]),
         "fifa_additive_create": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, C.POINTER(fifa_hyper),
@@ -300,6 +301,12 @@ def fifa_server_wait(server, rid: int, mean: np.ndarray | None = None, draws: np
     dp = draws.ctypes.data_as(C.c_void_p) if draws is not None else None
     st = _check(lib().fifa_server_wait(server, C.c_uint64(rid), mp, dp, C.byref(res)), "fifa_server_wait", allow)
     return st, res
+
+
+def fifa_server_poll(server, rid: int) -> bool:
+    done = C.c_int(0)
+    _check(lib().fifa_server_poll(server, C.c_uint64(rid), C.byref(done)), "fifa_server_poll")
+    return bool(done.value)
 
 
 def fifa_server_stats(server) -> fifa_server_counters:

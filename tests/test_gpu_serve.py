@@ -10,6 +10,7 @@
 * Admission never lets the requests in flight exceed the HBM budget.
 """
 import math
+import time
 
 import numpy as np
 import pytest
@@ -79,8 +80,18 @@ def test_server_request_matches_oracle():
     x, y = uniform_sine(n, 0)
     vy = float(np.var(y))
     srv = fifa.fifa_server_create(_opts(), 1 << 30, 2)
-    (mean, draws, res), = _run(srv, [(x, y, fifa.fifa_hyper(0, vy, 0.1, 0.5 * vy, 1e-6), _prior(), 0, 0, iters, burn,
-                                      nd)])
+    # non-blocking poll until the request is done, then collect it
+    rid = fifa.fifa_server_submit(srv, x, y, fifa.fifa_hyper(0, vy, 0.1, 0.5 * vy, 1e-6), _prior(), 0, 0, iters, burn,
+                                  nd)
+    deadline = time.monotonic() + 600
+    while not fifa.fifa_server_poll(srv, rid):
+        assert time.monotonic() < deadline
+        time.sleep(0.01)
+    mean, draws = np.empty(n), np.empty((nd, n))
+    st, res = fifa.fifa_server_wait(srv, rid, mean, draws)
+    with pytest.raises(fifa.FifaError) as e:  # collected: the id is gone
+        fifa.fifa_server_poll(srv, rid)
+    assert e.value.code == fifa.FIFA_ERR_INVALID_ARG
     fifa.fifa_server_destroy(srv)
     assert res.status == fifa.FIFA_OK
     assert res.t_submit <= res.t_start <= res.t_done
