@@ -331,6 +331,12 @@ void fifa_server_destroy(fifa_server* server);
  *   leaves[(leaf * Bm + b) * Bm + a] = C~ leaf entry (a, b), Bm = max leaf size. */
 fifa_status fifa_hmat_dims(const fifa_hmat* H, int64_t* n, int* levels, int* nleaf, int* leaf_max,
                            int* rank_cap);
+/* Rows [row0, row0 + nrows) of the level-l bases only (for sampled checks of
+ * large problems): out_host[k * nrows + (p - row0)] = bases[(l * rank_cap + k)
+ * * n + p], k < rank_cap.  Errors: INVALID_ARG (level or row range outside
+ * the H-matrix). */
+fifa_status fifa_hmat_level_rows(fifa_ctx* ctx, const fifa_hmat* H, int level, int64_t row0, int64_t nrows,
+                                 double* out_host);
 fifa_status fifa_hmat_export(fifa_ctx* ctx, const fifa_hmat* H, int* ranks_host, int* row_piv_host,
                              int* col_piv_host, double* bases_host, double* leaves_host);
 /* Factor pieces in the same layouts: bases are the orthonormal Q_U / Q_V,

@@ -926,6 +926,18 @@ extern "C" fifa_status fifa_hmat_dims(const fifa_hmat* H, int64_t* n, int* level
   return FIFA_OK;
 }
 
+extern "C" fifa_status fifa_hmat_level_rows(fifa_ctx* ctx, const fifa_hmat* H, int level, int64_t row0,
+                                            int64_t nrows, double* out_host) {
+  if (!ctx || !H || !out_host) return FIFA_ERR_INVALID_ARG;
+  Plan* P = H->plan;
+  if (level < 0 || level >= P->L || row0 < 0 || nrows < 1 || row0 + nrows > P->n) return FIFA_ERR_INVALID_ARG;
+  const int cap = H->host.cap;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy2D(out_host, sizeof(double) * (size_t)nrows, H->host.bases + ((size_t)level * cap) * P->n + row0,
+                  sizeof(double) * (size_t)P->n, sizeof(double) * (size_t)nrows, (size_t)cap, cudaMemcpyDeviceToHost));
+  return FIFA_OK;
+}
+
 extern "C" fifa_status fifa_hmat_export(fifa_ctx* ctx, const fifa_hmat* H, int* ranks_host, int* row_piv_host,
                                         int* col_piv_host, double* bases_host, double* leaves_host) {
   if (!ctx || !H) return FIFA_ERR_INVALID_ARG;

@@ -111,6 +111,7 @@ def lib():
         "fifa_destroy_additive": (None, [_P, _P]),
         "fifa_hmat_dims": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "fifa_hmat_level_rows": (C.c_int, [_P, _P, C.c_int, C.c_int64, C.c_int64, _P]),
         "fifa_hmat_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
         "fifa_fact_export": (C.c_int, [_P, _P, _P, _P, _P, _P]),
         "fifa_destroy_hmat": (None, [_P, _P]),
@@ -327,6 +328,14 @@ def fifa_hmat_dims(H):
 
 def _np_ptr(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def fifa_hmat_level_rows(ctx, H, level: int, row0: int, nrows: int) -> np.ndarray:
+    """(rank_cap, nrows) array: the level's basis columns on rows [row0, row0 + nrows)."""
+    cap = fifa_hmat_dims(H)[4]
+    out = np.zeros((cap, nrows))
+    _check(lib().fifa_hmat_level_rows(ctx, H, int(level), int(row0), int(nrows), _np_ptr(out)), "fifa_hmat_level_rows")
+    return out
 
 
 def fifa_hmat_export(ctx, H, allow=(FIFA_ERR_RANK_CAP,), bases=True, leaves=True):
