@@ -168,7 +168,11 @@ def reference_arm(args):
     if rank != 0:
         return
     n_s = 1 << 15
-    leaf = args.leaf or 64
+    # the GPU arm's leaf size (the autotuner's cached choice, else 32)
+    from paper_2006_06537_gb300 import autotune
+
+    entry = autotune.load(autotune.workload_key("clustered_se", args.n))
+    leaf = args.leaf or (entry["leaf"] if entry else 32)
     times = []
     for _ in range(args.warmup):
         oracle_sample(n_s, leaf, args.nugget, 1)
@@ -181,7 +185,8 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"clustered SE n={args.n}", "n": args.n, "leaf": leaf, "aca_tol": EPS,
+            "config": {"workload": f"clustered SE n={args.n}, 8 clusters, rho0={RHO0}, sigma={NOISE}", "n": args.n,
+                       "leaf": leaf, "aca_tol": EPS, "rank_cap": CAP, "nugget": args.nugget, "precision": "fp64",
                        "sample_n": n_s},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
                              "sample": f"oracle Gibbs iterations at n={n_s}, scaled by n log2(n)^2 (x{scale:.1f})"},
