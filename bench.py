@@ -74,6 +74,23 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(values, world, device):
+    """Element-wise max of per-rank timings over the process group (the
+    slowest replica bounds the job); the values themselves when world == 1."""
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def job_rates(per_step_ms, e2e_s_per_step, world):
+    """Whole-job iterations/s of `world` replicas, one chain each, from the
+    slowest rank's device time per step (ms) and end-to-end time per step (s)."""
+    return world * 1e3 / per_step_ms, world / e2e_s_per_step
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
 
@@ -320,10 +337,8 @@ def gpu_arm(args):
     if rank == 0 and args.additive_sweeps > 0:
         additive = additive_leg(fifa, torch, args.additive_sweeps, 32)
 
-    vals = torch.tensor([per_head, e2e_s], device="cuda", dtype=torch.float64)
-    if world > 1:
-        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
-    per_head, e2e_s = [float(v) for v in vals.cpu()]
+    per_head, e2e_s = max_over_ranks([per_head, e2e_s], world, "cuda")
+    value, e2e_value = job_rates(per_head, e2e_s, world)
     if rank != 0:
         return
     cpu = None
@@ -337,7 +352,7 @@ def gpu_arm(args):
                  "valid": v["ok"], "note": v["why"], "refine_residual": v["refine_res"],
                  "kernels_per_step": v["kernels"]} for k, v in results.items()}
     line = {
-        "metric": METRIC, "value": world * 1e3 / per_head, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_head, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": f"clustered SE n={n}, 8 clusters, rho0={RHO0}, sigma={NOISE}", "n": n, "leaf": leaf,
@@ -345,7 +360,7 @@ def gpu_arm(args):
                    "precision": head, "l2": "inputs and H-matrices (>> 129 MB L2) resident; no flush needed",
                    "parallelism": f"replicas x{world}"},
         "paths": paths,
-        "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
                 "d2h_bytes_per_step": 8 * n + 8 * fifa.FIFA_TRACE_FIELDS},
         "chain": {"rho": float(tr[-1, 3]), "sigma2": float(tr[-1, 1]), "tau2": float(tr[-1, 2]),
                   "accept_rate": float(tr[:, 4].mean())},
