@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(const HmatDesc* __restric
 // The arithmetic (products then differences, l ascending, IEEE division)
 // matches the CPU reference operation for operation.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 3) k_aca(const HmatDesc* __restrict__ Hd, const int4* __restrict__ work,
+__global__ void __launch_bounds__(256, 4) k_aca(const HmatDesc* __restrict__ Hd, const int4* __restrict__ work,
                                               ArgMax* __restrict__ part, unsigned int* __restrict__ bar,
                                               int* __restrict__ abort_flag) {
   const int4 w = work[blockIdx.x];
