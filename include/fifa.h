@@ -331,6 +331,25 @@ void fifa_server_destroy(fifa_server* server);
  *   leaves[(leaf * Bm + b) * Bm + a] = C~ leaf entry (a, b), Bm = max leaf size. */
 fifa_status fifa_hmat_dims(const fifa_hmat* H, int64_t* n, int* levels, int* nleaf, int* leaf_max,
                            int* rank_cap);
+/* The plan the library builds for n points (host only: no GPU needed), given
+ * the co-resident CTA budgets it queries on a GPU: aca_cores for the ACA
+ * kernel, lvl_cores[3] for the level kernel's rank buckets (<= 4, 5..16,
+ * > 16).  Optional outputs: bounds_out, the tree bounds with level l at offset
+ * 2^l - 1 + l (2^(L+1) + L ints; node i of level l spans
+ * [b[l][i], b[l][i + 1]) with its split at b[l + 1][2 i + 1]); aca_work_out,
+ * 4 ints per entry {level, node, g, G}: the grouped entries (G CTAs per
+ * block), then one CTA per block, then one warp per block; lvl_groups_out,
+ * the CTA group size per rank bucket and level (3 x L ints, bucket-major).
+ * Call with null outputs first to size them.  Errors: INVALID_ARG,
+ * UNSUPPORTED (more levels than the library supports), OOM. */
+typedef struct {
+  int levels, nleaf, leaf_max;
+  int aca_grouped_ctas, aca_solo_blocks, aca_warp_blocks;
+  int64_t scratch_bytes;
+} fifa_plan_info;
+fifa_status fifa_plan_describe(const fifa_opts* opts, int64_t n, int aca_cores, const int* lvl_cores,
+                               fifa_plan_info* info, int* bounds_out, int* aca_work_out, int* lvl_groups_out);
+
 /* Rows [row0, row0 + nrows) of the level-l bases only (for sampled checks of
  * large problems): out_host[k * nrows + (p - row0)] = bases[(l * rank_cap + k)
  * * n + p], k < rank_cap.  Errors: INVALID_ARG (level or row range outside

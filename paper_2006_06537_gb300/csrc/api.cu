@@ -230,6 +230,40 @@ static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, const int*
   return P;
 }
 
+extern "C" fifa_status fifa_plan_describe(const fifa_opts* opts, int64_t n, int aca_cores, const int* lvl_cores,
+                                          fifa_plan_info* info, int* bounds_out, int* aca_work_out,
+                                          int* lvl_groups_out) {
+  if (!opts || !lvl_cores || !info || n < 1 || opts->leaf_size < 1 || opts->rank_cap < 1 ||
+      opts->rank_cap > FIFA_CAP_MAX || aca_cores < 1)
+    return FIFA_ERR_INVALID_ARG;
+  for (int b = 0; b < LEVEL_BUCKETS; ++b)
+    if (lvl_cores[b] < 1) return FIFA_ERR_INVALID_ARG;
+  fifa_status st = FIFA_OK;
+  Plan* P = plan_build(n, *opts, aca_cores, lvl_cores, &st);
+  if (!P) return st;
+  info->levels = P->L;
+  info->nleaf = P->nleaf;
+  info->leaf_max = P->Bm;
+  info->aca_grouped_ctas = P->aca_ncoop;
+  info->aca_solo_blocks = P->aca_nsolo;
+  info->aca_warp_blocks = P->aca_nwarp;
+  info->scratch_bytes = (int64_t)P->scratch_bytes;
+  if (bounds_out) std::copy(P->bnd_host.begin(), P->bnd_host.end(), bounds_out);
+  if (aca_work_out)
+    for (size_t k = 0; k < P->work_host.size(); ++k) {
+      const int4 w = P->work_host[k];
+      aca_work_out[4 * k] = w.x;
+      aca_work_out[4 * k + 1] = w.y;
+      aca_work_out[4 * k + 2] = w.z;
+      aca_work_out[4 * k + 3] = w.w;
+    }
+  if (lvl_groups_out)
+    for (int b = 0; b < LEVEL_BUCKETS; ++b)
+      for (int l = 0; l < P->L; ++l) lvl_groups_out[b * P->L + l] = P->lvl_G[b][l];
+  delete P;
+  return FIFA_OK;
+}
+
 Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st) {
   auto key = std::make_pair(n, ctx->opts.leaf_size);
   auto it = ctx->plans.find(key);

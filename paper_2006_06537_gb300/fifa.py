@@ -34,6 +34,11 @@ class fifa_opts(C.Structure):
                 ("refine_tol", C.c_double), ("refine_max", C.c_int), ("independent_ctas", C.c_int)]
 
 
+class fifa_plan_info(C.Structure):
+    _fields_ = [("levels", C.c_int), ("nleaf", C.c_int), ("leaf_max", C.c_int), ("aca_grouped_ctas", C.c_int),
+                ("aca_solo_blocks", C.c_int), ("aca_warp_blocks", C.c_int), ("scratch_bytes", C.c_int64)]
+
+
 class fifa_prior(C.Structure):
     _fields_ = [("a_tau2", C.c_double), ("b_tau2", C.c_double), ("a_sigma2", C.c_double), ("b_sigma2", C.c_double),
                 ("logrho_mu", C.c_double), ("logrho_sd", C.c_double), ("prop_sd", C.c_double)]
@@ -111,6 +116,7 @@ def lib():
         "fifa_destroy_additive": (None, [_P, _P]),
         "fifa_hmat_dims": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "fifa_plan_describe": (C.c_int, [C.POINTER(fifa_opts), C.c_int64, C.c_int, _P, C.POINTER(fifa_plan_info), _P, _P, _P]),
         "fifa_hmat_level_rows": (C.c_int, [_P, _P, C.c_int, C.c_int64, C.c_int64, _P]),
         "fifa_hmat_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
         "fifa_fact_export": (C.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -328,6 +334,23 @@ def fifa_hmat_dims(H):
 
 def _np_ptr(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def fifa_plan_describe(opts, n: int, aca_cores: int, lvl_cores) -> dict:
+    """Host-only plan for n points: info, tree bounds, ACA work list (k x 4) and level group sizes (3 x L)."""
+    lc = np.ascontiguousarray(lvl_cores, dtype=np.int32)
+    info = fifa_plan_info()
+    _check(lib().fifa_plan_describe(C.byref(opts), int(n), int(aca_cores), _np_ptr(lc), C.byref(info), None, None,
+                                    None), "fifa_plan_describe")
+    L = info.levels
+    nb = (1 << (L + 1)) + L  # levels 0..L, 2^l + 1 bounds each
+    nw = info.aca_grouped_ctas + info.aca_solo_blocks + info.aca_warp_blocks
+    bounds = np.zeros(nb, np.int32)
+    work = np.zeros(max(1, 4 * nw), np.int32)
+    groups = np.zeros(max(1, 3 * L), np.int32)
+    _check(lib().fifa_plan_describe(C.byref(opts), int(n), int(aca_cores), _np_ptr(lc), C.byref(info),
+                                    _np_ptr(bounds), _np_ptr(work), _np_ptr(groups)), "fifa_plan_describe")
+    return dict(info=info, bounds=bounds, work=work[:4 * nw].reshape(nw, 4), groups=groups[:3 * L].reshape(3, L))
 
 
 def fifa_hmat_level_rows(ctx, H, level: int, row0: int, nrows: int) -> np.ndarray:
