@@ -7,16 +7,19 @@ ACA tolerance 1e-10, rank cap 32, IG(1,1) priors, random-walk Metropolis on
 log rho.  One step = one full Gibbs iteration (M~ factor, Algorithm 1 draw,
 sigma2, tau2, proposal assembly + FP64 factor + Metropolis).
 
-value      = iterations/s of the MIXED path (M~ factor in FP32, FP64 refinement),
-             data resident on the device, timed with CUDA events over K graph
-             replays (the inputs exceed L2 many times over: no flush needed).
-fp64       = the same for the all-FP64 path.
-e2e        = the MIXED path through the public API with host buffers: every step
+value      = iterations/s of the fastest valid path (all-FP64, or the mixed path:
+             M~ factor in FP32 with FP64 refinement, valid when its refined
+             residual meets the target), data resident on the device, timed
+             with CUDA events over K graph replays (the inputs exceed L2 many
+             times over: no flush needed); `paths` reports both.
+e2e        = the same path through the public API with host buffers: every step
              copies x, y from pinned host memory to the device, runs
              fifa_gibbs_step(1) with its trace row read back, and copies the draw f
              back to pinned host memory.
-roofline   = the dominant operation, timed live with CUDA events on the library's
-             stream (see the design doc for its algorithmic flop / byte counts).
+roofline   = the dominant operation (the FP64 factorization), timed live with
+             CUDA events on the library's stream: algorithmic flops from the
+             actual per-node ranks (factor_work) over the measured FP64 peak,
+             and the fused W^-1 sweep's bytes over the measured HBM bandwidth.
 cpu_baseline = the CPU oracle (numpy, FP64) timed on this host on a bounded
              sample of the same workload.
 
