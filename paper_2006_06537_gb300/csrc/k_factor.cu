@@ -4,15 +4,19 @@
 //
 //  k_leaf_factor : per leaf, L_i = chol(scale * D_i + shift * I) in FP64 shared
 //                  memory, log-det partial, and L_i^-1 applied to the rows of
-//                  every ancestor basis lying in the leaf (the first transform).
+//                  every ancestor basis lying in the leaf (the first transform),
+//                  the first chunk of those columns inside the Cholesky steps.
 //  k_level       : per node of one level (bottom-up), the orthonormal bases
 //                  Q_U, Q_V of the transformed U~, V~ by CholeskyQR2 (two Gram
 //                  passes; stable here because the column-scaled bases are
 //                  well conditioned), R = R2 R1, L_S = chol(I + R X R^T),
 //                  Zf = L_S - I, Zi = L_S^-1 - I, and the inverse node factor
 //                  I + Q Zi Q^T applied to every ancestor basis on the node's rows.
-//                  Small nodes: one CTA each.  Large nodes: G CTAs split the rows
-//                  and exchange partial sums through bounded-spin group barriers.
+//                  Large nodes: G CTAs split the rows and exchange partial sums
+//                  through bounded-spin group barriers.
+//  k_level_multi : the same for the deepest levels (sides of <= 128 rows,
+//                  rank <= 4), several nodes per CTA staged in shared memory;
+//  k_level_small : rank 5..8 nodes of those levels, one CTA each.
 #include <algorithm>
 #include <atomic>
 #include "fifa_common.cuh"
