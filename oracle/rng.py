@@ -13,6 +13,9 @@ W0 = floor(2**32 (phi - 1)) and W1 = floor(2**32 (sqrt(3) - 1)).
 The multipliers M0 = 0xD2511F53 and M1 = 0xCD9E8D57 are the ones the paper
 chose for the 4x32 variant.
 
+Pinned against cuRAND's curand_Philox4x32_10 (known answers in
+tests/test_oracle_philox_kat.py).
+
 Counter layout used by the sampler (one call yields four 32-bit words):
     word 0: element-pair or attempt index, word 1: stream tag,
     word 2: Gibbs iteration (low 32 bits), word 3: chain id (low 32 bits);
