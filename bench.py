@@ -4,24 +4,32 @@ Workload (the headline configuration): n = 2^20 sorted inputs drawn from a
 mixture of 8 narrow uniforms (half-width 0.01, centres (2j+1)/16),
 y = sin(2 pi x) + N(0, 0.05^2), squared-exponential kernel, rho_0 = 0.01,
 ACA tolerance 1e-10, rank cap 32, IG(1,1) priors, random-walk Metropolis on
-log rho.  One step = one full Gibbs iteration (M~ factor, Algorithm 1 draw,
-sigma2, tau2, proposal assembly + FP64 factor + Metropolis).
+log rho.  One step = one full Gibbs iteration (M~ factor or its kept factor,
+Algorithm 1 draw, sigma2, tau2, proposal assembly + FP64 factor + Metropolis).
 
-value      = iterations/s of the fastest valid path (all-FP64, or the mixed path:
-             M~ factor in FP32 with FP64 refinement, valid when its refined
-             residual meets the target), data resident on the device, timed
-             with CUDA events over K graph replays (the inputs exceed L2 many
-             times over: no flush needed); `paths` reports both.
-e2e        = the same path through the public API with host buffers: every step
-             copies x, y from pinned host memory to the device, runs
-             fifa_gibbs_step(1) with its trace row read back, and copies the draw f
-             back to pinned host memory.
-roofline   = the dominant operation (the FP64 factorization), timed live with
-             CUDA events on the library's stream: algorithmic flops from the
-             actual per-node ranks (factor_work) over the measured FP64 peak,
-             and the fused W^-1 sweep's bytes over the measured HBM bandwidth.
+paths      = the FP64 chain (M~ factored and solved directly every iteration,
+             as Algorithm 1 is written) and the mixed chain (FP64 factor of M~
+             kept between iterations and refreshed when rho moves or the
+             solves slow down, applied in FP32 as the preconditioner of
+             conjugate gradients with FP64 residuals), both from the same
+             state and Philox streams, timed with CUDA events over K graph
+             replays; `mixed_vs_fp64` compares the two chains step by step.
+value      = iterations/s of the fastest valid path (mixed is valid when its
+             M~ solves meet a 1e-8 true residual and its draws stay within
+             1e-8 of the FP64 chain's).  Inputs and H-matrices exceed the
+             129 MB L2 many times over: no flush is needed.
+e2e        = the same path through the public API with host buffers: every
+             step copies y from pinned host memory into the chain
+             (fifa_chain_set_y), runs fifa_gibbs_step(1) with its trace row
+             read back, and copies the draw f back to pinned host memory.
+roofline   = the dominant operation (the FP64 factorization of C~), timed live
+             with CUDA events on the library's stream: algorithmic flops from
+             the actual per-node ranks (factor_work) over the FP64 FMA peak
+             measured in the same run (fifa_probe_fp64_fma); secondary entries
+             for the fused H-matrix product, the FP64 W^-1 sweep and the FP32
+             preconditioner solve against the measured HBM bandwidth.
 cpu_baseline = the CPU oracle (numpy, FP64) timed on this host on a bounded
-             sample of the same workload.
+             sample of the same workload (one iteration at n = 2^17, scaled).
 
 --impl reference runs the CPU oracle itself as the reference arm.
 """
@@ -147,20 +155,7 @@ def peaks():
 # ---------------------------------------------------------------------------
 # CPU oracle leg (bounded sample)
 # ---------------------------------------------------------------------------
-def oracle_sample(n_sample: int, leaf: int, nugget: float, iters: int = 1):
-    """One oracle Gibbs iteration on the first n_sample points' recipe (same
-    generator, smaller n); returns (seconds per iteration, threads used)."""
-    from oracle import sampler
-
-    x, y = clustered(n_sample, 2, noise=NOISE)
-    opts = sampler.Opts(B=leaf, eps=EPS, cap=CAP, kind=0, nugget=nugget)
-    prior = sampler.Prior(logrho_mu=math.log(RHO0))
-    st = sampler.init_state(x, y, RHO0, opts)
-    t0 = time.perf_counter()
-    for _ in range(iters):
-        sampler.gibbs_step(st, x, y, prior, opts, seed=0, chain=0)
-    dt = (time.perf_counter() - t0) / iters
-    return dt, threads_used()
+REF_SAMPLE_N = 1 << 17  # oracle sample size: one iteration takes seconds on the host cores
 
 
 def threads_used():
@@ -172,44 +167,90 @@ def threads_used():
         return os.cpu_count() or 1
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), and its core count."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                name = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not name:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    name = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+
+    return {"model": name or platform.processor() or "unknown", "arch": platform.machine(), "cpus": os.cpu_count()}
+
+
+def oracle_chain(n_sample: int, leaf: int, nugget: float, warmup: int, steps: int):
+    """The oracle's Gibbs chain on the clustered recipe at n_sample points:
+    set-up (assembly + factorization of C~(rho0)) untimed, `warmup` untimed
+    iterations, then `steps` timed ones.  Returns (seconds per iteration, threads)."""
+    from oracle import sampler
+
+    x, y = clustered(n_sample, 2, noise=NOISE)
+    opts = sampler.Opts(B=leaf, eps=EPS, cap=CAP, kind=0, nugget=nugget)
+    prior = sampler.Prior(logrho_mu=math.log(RHO0))
+    st = sampler.init_state(x, y, RHO0, opts)
+    for _ in range(warmup):
+        sampler.gibbs_step(st, x, y, prior, opts, seed=0, chain=0)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sampler.gibbs_step(st, x, y, prior, opts, seed=0, chain=0)
+    return (time.perf_counter() - t0) / max(1, steps), threads_used()
+
+
+def nlog2(n):
+    return n * math.log2(n) ** 2
+
+
 def cpu_baseline(n_full: int, leaf: int, nugget: float):
     """Oracle per-iteration time at a sample size, scaled to n_full by n log^2 n
     (the method's factorization cost, Sec. 4.1.1)."""
-    n_s = 1 << 17
-    dt, thr = oracle_sample(n_s, leaf, nugget, iters=1)
-    scale = (n_full * math.log2(n_full) ** 2) / (n_s * math.log2(n_s) ** 2)
-    return {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": thr, "kind": "oracle",
+    n_s = min(n_full, REF_SAMPLE_N)
+    dt, thr = oracle_chain(n_s, leaf, nugget, 0, 1)
+    scale = nlog2(n_full) / nlog2(n_s)
+    return {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": thr, "kind": "oracle", "cpu": cpu_model(),
             "sample": f"1 oracle Gibbs iteration at n={n_s} of the same clustered recipe ({dt:.2f} s), "
-                      f"scaled to n={n_full} by n log2(n)^2 (x{scale:.1f})"}
+                      f"scaled to n={n_full} by n log2(n)^2 (x{scale:.2f})"}
 
 
 def reference_arm(args):
+    """The oracle as the reference arm: every step one oracle Gibbs iteration on
+    the clustered recipe at n = 2^17 (a bounded sample of the 2^20 workload),
+    measured; the line's n is the sample's, and the n log^2 n extrapolation to
+    the workload size is reported in its own field."""
     rank, world, _ = dist_info()
     if rank != 0:
         return
-    n_s = 1 << 15
-    # the GPU arm's leaf size (the autotuner's cached choice, else 32)
     from paper_2006_06537_gb300 import autotune
 
     entry = autotune.load(autotune.workload_key("clustered_se", args.n))
     leaf = args.leaf or (entry["leaf"] if entry else 32)
-    times = []
-    for _ in range(args.warmup):
-        oracle_sample(n_s, leaf, args.nugget, 1)
-    for _ in range(args.steps):
-        dt, thr = oracle_sample(n_s, leaf, args.nugget, 1)
-        times.append(dt)
-    scale = (args.n * math.log2(args.n) ** 2) / (n_s * math.log2(n_s) ** 2)
-    per = float(np.mean(times)) * scale
+    n_s = min(args.n, REF_SAMPLE_N)
+    per, thr = oracle_chain(n_s, leaf, args.nugget, args.warmup, args.steps)
     v = 1.0 / per
+    scale = nlog2(args.n) / nlog2(n_s)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"clustered SE n={args.n}, 8 clusters, rho0={RHO0}, sigma={NOISE}", "n": args.n,
-                       "leaf": leaf, "aca_tol": EPS, "rank_cap": CAP, "nugget": args.nugget, "precision": "fp64",
-                       "sample_n": n_s},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
-                             "sample": f"oracle Gibbs iterations at n={n_s}, scaled by n log2(n)^2 (x{scale:.1f})"},
+            "config": {"workload": f"clustered SE n={n_s} (sample of the n={args.n} workload), 8 clusters, "
+                                   f"rho0={RHO0}, sigma={NOISE}", "n": n_s, "workload_n": args.n,
+                       "leaf": leaf, "aca_tol": EPS, "rank_cap": CAP, "nugget": args.nugget, "precision": "fp64"},
+            "extrapolated_to_workload_n": {"n": args.n, "value": v / scale, "unit": UNIT,
+                                           "scaling": "n log2(n)^2 (the factorization's cost)", "factor": scale},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle", "cpu": cpu_model(),
+                             "sample": f"{args.steps} oracle Gibbs iterations at n={n_s} after {args.warmup} "
+                                       f"untimed ones (measured, not scaled)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -245,11 +286,11 @@ def gpu_arm(args):
             pr = fifa.fifa_prior(1.0, 1.0, 1.0, 1.0, prior_mu, 1.0, 0.2)
             ch = fifa.fifa_chain_create(ctx.h, xd, yd, n, fifa.fifa_hyper(0, vy, RHO0, 0.5 * vy, args.nugget), pr,
                                         0, rank)
-        return ctx, ch, xd, yd
+        return ctx, ch
 
     def time_chain(ctx, ch, steps, warmup):
-        tr = np.zeros((max(warmup, 1), fifa.FIFA_TRACE_FIELDS))
-        fifa.fifa_gibbs_step(ctx.h, ch, warmup, tr[:warmup] if warmup else None)
+        wtr = np.zeros((max(warmup, 1), fifa.FIFA_TRACE_FIELDS))
+        fifa.fifa_gibbs_step(ctx.h, ch, warmup, wtr[:warmup] if warmup else None)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         if world > 1:
@@ -260,7 +301,11 @@ def gpu_arm(args):
         fifa.fifa_gibbs_step(ctx.h, ch, steps, trace)
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1), trace
+        f = torch.empty(n, dtype=torch.float64, device="cuda")
+        mean = torch.empty_like(f)
+        fifa.fifa_chain_get(ctx.h, ch, f, mean)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), np.vstack([wtr[:warmup], trace]), f.cpu().numpy(), mean.cpu().numpy()
 
     def close(ctx, ch):
         fifa.fifa_destroy_chain(ctx.h, ch)
@@ -268,8 +313,8 @@ def gpu_arm(args):
         torch.cuda.synchronize()
 
     # leaf size: the autotuner's cached choice for this workload (tuned.json),
-    # measured once by `python -m paper_2006_06537_gb300.autotune`; tuned here
-    # (and cached) only if no entry exists yet
+    # measured by `python -m paper_2006_06537_gb300.autotune`; tuned here (and
+    # cached) only if no entry exists yet
     from paper_2006_06537_gb300 import autotune
 
     if args.leaf:
@@ -285,41 +330,64 @@ def gpu_arm(args):
     for name, prec in (("fp64", fifa.FIFA_FP64), ("mixed", fifa.FIFA_MIXED)):
         if name not in wanted:
             continue
-        ctx, ch, xd, yd = make(prec, leaf)
+        ctx, ch = make(prec, leaf)
         try:
             clocks = ClockSampler(local)
             clocks.start()
-            ms, trace = time_chain(ctx, ch, args.steps, args.warmup)
+            ms, trace, f_end, m_end = time_chain(ctx, ch, args.steps, args.warmup)
             clk = clocks.stop()
             ok, why = True, ""
         except fifa.FifaError as exc:
-            ms, trace, clk, ok, why = float("nan"), None, None, False, str(exc)
-        res = float(np.nanmax(trace[:, 9])) if trace is not None else float("nan")
+            ms, trace, f_end, m_end, clk, ok, why = float("nan"), None, None, None, None, False, str(exc)
+        timed = trace[args.warmup:] if trace is not None else None
+        res = float(np.nanmax(timed[:, 9])) if timed is not None else float("nan")
         if ok and prec == fifa.FIFA_MIXED and not (res <= 1e-8):
-            ok, why = False, f"M~ refinement residual {res:.2e} above 1e-8"
+            ok, why = False, f"M~ solve residual {res:.2e} above 1e-8"
         results[name] = dict(ms=ms / args.steps if ok else float("nan"), ok=ok, why=why, clocks=clk, trace=trace,
-                             kernels=fifa.fifa_chain_kernel_nodes(ch), refine_res=res)
+                             kernels=fifa.fifa_chain_kernel_nodes(ch), refine_res=res, f=f_end, mean=m_end)
         close(ctx, ch)
+    # the mixed chain against the FP64 chain (same state, data and Philox streams)
+    cmp = None
+    if "fp64" in results and "mixed" in results and results["fp64"]["ok"] and results["mixed"]["ok"]:
+        t6, tm = results["fp64"]["trace"], results["mixed"]["trace"]
+        same = bool(np.array_equal(t6[:, 4], tm[:, 4]))
+
+        def rmax(a, b):
+            return float(np.max(np.abs(a - b) / np.abs(b)))
+
+        rf = float(np.linalg.norm(results["mixed"]["f"] - results["fp64"]["f"]) / np.linalg.norm(results["fp64"]["f"]))
+        rm = float(np.linalg.norm(results["mixed"]["mean"] - results["fp64"]["mean"]) /
+                   np.linalg.norm(results["fp64"]["mean"]))
+        fin = np.isfinite(t6[:, 5]) & np.isfinite(tm[:, 5])
+        cmp = {"steps_compared": int(len(t6)), "accept_decisions_equal": same,
+               "sigma2_max_rel": rmax(tm[:, 1], t6[:, 1]), "tau2_max_rel": rmax(tm[:, 2], t6[:, 2]),
+               "log_alpha_max_abs": float(np.max(np.abs(tm[fin, 5] - t6[fin, 5]))) if fin.any() else None,
+               "f_final_rel": rf, "mean_final_rel": rm,
+               "mixed_refactor_fraction": float(tm[args.warmup:, 11].mean()),
+               "mixed_cg_iters_mean": float(tm[args.warmup:, 12].mean()),
+               "mixed_cg_iters_max": int(tm[args.warmup:, 12].max())}
+        if same and not (rf <= 1e-8 and rm <= 1e-8):
+            results["mixed"]["ok"] = False
+            results["mixed"]["why"] = f"draw / mean differ from the FP64 chain by {rf:.1e} / {rm:.1e} (> 1e-8)"
     valid = [k for k in results if results[k]["ok"]]
     head = min(valid, key=lambda k: results[k]["ms"])
     per_head = results[head]["ms"]
     hprec = fifa.FIFA_FP64 if head == "fp64" else fifa.FIFA_MIXED
 
-    # end-to-end through the public API with pinned host buffers
-    ctx, ch, xd, yd = make(hprec, leaf)
-    xh = torch.tensor(x).pin_memory()
+    # end-to-end through the public API with pinned host buffers: each step
+    # streams y into the chain, runs one iteration, reads f and the trace row back
+    ctx, ch = make(hprec, leaf)
     yh = torch.tensor(y).pin_memory()
     fh = torch.empty(n, dtype=torch.float64).pin_memory()
     fd = torch.empty(n, dtype=torch.float64, device="cuda")
     row = np.zeros((1, fifa.FIFA_TRACE_FIELDS))
-    fifa.fifa_gibbs_step(ctx.h, ch, 2, None)
+    fifa.fifa_gibbs_step(ctx.h, ch, args.warmup, None)
     e2e_steps = max(3, min(args.steps, 10))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         with torch.cuda.stream(stream):
-            xd.copy_(xh, non_blocking=True)
-            yd.copy_(yh, non_blocking=True)
+            fifa.fifa_chain_set_y(ctx.h, ch, yh)
             fifa.fifa_gibbs_step(ctx.h, ch, 1, row)
             fifa.fifa_chain_get(ctx.h, ch, fd, None)
             fh.copy_(fd, non_blocking=True)
@@ -327,8 +395,9 @@ def gpu_arm(args):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     close(ctx, ch)
     with torch.cuda.stream(stream):
-        pctx = fifa.Context(leaf_size=leaf, aca_tol=EPS, rank_cap=CAP, prec=fifa.FIFA_FP64,
-                            arena_bytes=24 << 30, stream=stream)
+        pctx = fifa.Context(leaf_size=leaf, aca_tol=EPS, rank_cap=CAP, prec=fifa.FIFA_MIXED, refine_max=8,
+                            refine_tol=1e-12, arena_bytes=24 << 30, stream=stream)
+        xd = torch.tensor(x, device="cuda")
     roof = roofline_probe(pctx, fifa, torch, stream, xd, n, leaf, args.nugget)
     pctx.close()
 
@@ -336,7 +405,7 @@ def gpu_arm(args):
     # measured after the headline, outside its timed region
     serving = additive = None
     if rank == 0 and args.serve_requests > 0:
-        serving = serving_leg(fifa, args.serve_requests, args.serve_slots, fifa.FIFA_FP64, 32)
+        serving = serving_leg(fifa, args.serve_requests, args.serve_slots, fifa.FIFA_MIXED, 32)
     if rank == 0 and args.additive_sweeps > 0:
         additive = additive_leg(fifa, torch, args.additive_sweeps, 32)
 
@@ -350,7 +419,7 @@ def gpu_arm(args):
             cpu = cpu_baseline(n, leaf, args.nugget)
         except Exception as exc:  # the baseline must not hide the GPU line
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {exc}"}
-    tr = results[head]["trace"]
+    tr = results[head]["trace"][args.warmup:]
     paths = {k: {"value": (1e3 / v["ms"]) if v["ok"] else None, "ms_per_step": v["ms"] if v["ok"] else None,
                  "valid": v["ok"], "note": v["why"], "refine_residual": v["refine_res"],
                  "kernels_per_step": v["kernels"]} for k, v in results.items()}
@@ -363,8 +432,10 @@ def gpu_arm(args):
                    "precision": head, "l2": "inputs and H-matrices (>> 129 MB L2) resident; no flush needed",
                    "parallelism": f"replicas x{world}"},
         "paths": paths,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
-                "d2h_bytes_per_step": 8 * n + 8 * fifa.FIFA_TRACE_FIELDS},
+        "mixed_vs_fp64": cmp,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * n + 8 * fifa.FIFA_TRACE_FIELDS,
+                "step": "y pinned host -> chain (fifa_chain_set_y), fifa_gibbs_step(1) + trace row, f -> pinned host"},
         "chain": {"rho": float(tr[-1, 3]), "sigma2": float(tr[-1, 1]), "tau2": float(tr[-1, 2]),
                   "accept_rate": float(tr[:, 4].mean())},
         "roofline": roof,
@@ -489,28 +560,10 @@ def additive_leg(fifa, torch, sweeps, leaf, n=65536, d=4):
     return out
 
 
-def count_launches(L: int, mixed: bool, refine_max: int, grouped_aca: bool) -> int:
-    """Kernel launches of one Gibbs iteration, counted from the plan shape:
-    factor = prep + leaf + L levels + logdet; sweep = 2 L + 1; matvec = 3;
-    assembly = prep + leaves + ACA (1 or 2 launches)."""
-    factor = 3 + L
-    sweep = 2 * L + 1
-    mv = 3 if L > 0 else 1
-    it = 1 + factor                                  # M~ view + factor
-    it += 2 + mv + sweep + 1 + 2 * sweep + mv + 1     # Algorithm 1 (normals, C~a, W_C b, rhs, solve, C~r, finish)
-    if mixed:
-        it += refine_max * (mv + 1 + 2 * sweep + 1)   # refinement steps
-        it += mv + 1 + 4 + 1                          # final residual norm
-    it += 2 + 1                                       # ||y - f||^2, sigma2
-    it += sweep + 2 + 1                               # q, tau2
-    it += 1 + 2 + (2 if grouped_aca else 1)           # propose, assemble C~(rho')
-    it += factor + sweep + 2 + 1                      # factor, q', Metropolis
-    return it
-
-
 def factor_work(n, leaf, ranks):
-    """Algorithmic FP64 flops of one HODLR factorization and bytes of one W^-1
-    sweep with two right-hand sides, from the per-node ranks (heap order)."""
+    """Algorithmic FP64 flops of one HODLR factorization (per level too), from
+    the per-node ranks (heap order): leaf m^3/3 + m^2 C_anc, levels 4 r^2 m
+    (CholeskyQR2) + 4 r C_anc m (ancestor update)."""
     L = 0
     while (n + (1 << L) - 1) >> L > leaf:
         L += 1
@@ -522,7 +575,6 @@ def factor_work(n, leaf, ranks):
             nxt += [[s_, h_], [h_, e_]]
         b = nxt if nxt else b
     leaves_m = np.array([e_ - s_ for s_, e_ in b], dtype=np.float64)
-    # per-leaf ancestor columns
     nl = len(leaves_m)
     canc_leaf = np.zeros(nl)
     for l in range(L):
@@ -530,7 +582,6 @@ def factor_work(n, leaf, ranks):
         canc_leaf += np.repeat(r_l, nl >> l)
     flops = float(np.sum(leaves_m ** 3) / 3.0 + np.sum(leaves_m ** 2 * canc_leaf))
     per_level = [flops]  # leaves first, then levels L-1 .. 0
-    # levels: CholeskyQR2 (two Gram passes + two row transforms) and the ancestor update
     lv = []
     for l in range(L):
         r_l = ranks[(1 << l) - 1:(1 << (l + 1)) - 1].astype(np.float64)
@@ -542,26 +593,62 @@ def factor_work(n, leaf, ranks):
         lv.append(f)
         flops += f
     per_level += lv[::-1]
-    # one fused W^-1 sweep with two right-hand sides: the leaf factors (lower
-    # triangles), the bases once, v read and written once
-    sweep_bytes = 8.0 * (np.sum(leaves_m ** 2) / 2.0 + n * float(sum(
-        ranks[(1 << l) - 1:(1 << (l + 1)) - 1].mean() for l in range(L)))) + 2 * 8.0 * n * 2
-    return flops, sweep_bytes, L, per_level
+    return flops, L, per_level, leaves_m
+
+
+def apply_work(n, leaves_m, ranks, L, nrhs=2):
+    """Algorithmic bytes of the application kernels for nrhs right-hand sides:
+    rank_rows = sum over levels of the level's mean rank times n (basis entries
+    one pass reads).
+      FP64 W^-1 sweep: the leaf factors' lower triangles and the bases once
+        (8 bytes), v read and written once.
+      FP32 preconditioner solve W32^-T W32^-1: both triangles of the leaf
+        factors and the bases twice (4 bytes), v read and written once (FP64).
+      FP64 H-matrix product: the dense leaves and the bases once (8 bytes), x
+        read and y written once; flops 2 (m + 2 rank_rows / n) n nrhs."""
+    rank_rows = n * float(sum(ranks[(1 << l) - 1:(1 << (l + 1)) - 1].mean() for l in range(L)))
+    vec = 2 * 8.0 * n * nrhs
+    sweep = 8.0 * (np.sum(leaves_m ** 2) / 2.0 + rank_rows) + vec
+    precond = 4.0 * (np.sum(leaves_m ** 2) + 2 * rank_rows) + vec
+    mv_bytes = 8.0 * (np.sum(leaves_m ** 2) + rank_rows) + vec
+    mv_flops = 2.0 * (np.sum(leaves_m ** 2) + 2 * rank_rows) * nrhs
+    return float(sweep), float(precond), float(mv_bytes), float(mv_flops)
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, summed over every
+# launch of one FP64 factorization of C~(rho0) of this workload at n = 2^20,
+# leaf 32) from one ncu capture; None until the current kernels are captured.
+FACTOR_TRAFFIC_BYTES = None
 
 
 def roofline_probe(ctx, fifa, torch, stream, xd, n, leaf, nugget):
-    """FP64 factorization of C~(rho0) of this workload and a W^-1 sweep, each
-    timed alone with CUDA events on the library stream."""
+    """The FP64 factorization of C~(rho0) of this workload (the dominant
+    operation) and the application kernels, each timed alone with CUDA events
+    on the library stream; peaks: the FP64 FMA probe of this run and the
+    measured HBM copy bandwidth."""
     hbm, src = peaks()
+    peak_fp64, probe_ms = fifa.fifa_probe_fp64_fma(ctx.h, 20000)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        fn()  # warm-up
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
     with torch.cuda.stream(stream):
         H = fifa.fifa_assemble(ctx.h, xd, n, fifa.fifa_hyper(0, 1.0, RHO0, 1.0, nugget))
         ranks = fifa.fifa_hmat_export(ctx.h, H, bases=False, leaves=False)["ranks"].astype(np.float64)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        ms = 0.0
         F = fifa.fifa_factor(ctx.h, H)  # warm-up
         torch.cuda.synchronize()
         fifa.fifa_destroy_fact(ctx.h, F)
-        ms, reps = 0.0, 3
+        reps = 3
         for _ in range(reps):
             torch.cuda.synchronize()
             e0.record(stream)
@@ -572,30 +659,43 @@ def roofline_probe(ctx, fifa, torch, stream, xd, n, leaf, nugget):
             fifa.fifa_destroy_fact(ctx.h, F)
         F = fifa.fifa_factor(ctx.h, H)
         v = torch.randn(2, n, dtype=torch.float64, device="cuda")
-        fifa.fifa_apply_W(ctx.h, F, 0, 1, v, v, 2)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(5):
-            fifa.fifa_apply_W(ctx.h, F, 0, 1, v, v, 2)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_sw = e0.elapsed_time(e1) / 5
+        w = torch.empty_like(v)
+        ms_sw = timed(lambda: fifa.fifa_apply_W(ctx.h, F, 0, 1, v, v, 2), 5)
+        ms_mv = timed(lambda: fifa.fifa_matvec(ctx.h, H, v, w, 2), 5)
+        # M~ = s C~ + I at the chain's s (tau2 / sigma2 ~ 0.5 / 0.05^2) and its
+        # mixed factor: the FP32 preconditioner solve and a whole mixed solve
+        M = fifa.fifa_shift_scale(ctx.h, H, 200.0)
+        FM = fifa.fifa_factor(ctx.h, M)
+        ms_pc = timed(lambda: fifa.fifa_apply_precond(ctx.h, FM, v, w, 2), 5)
+        ms_solve = timed(lambda: fifa.fifa_solve(ctx.h, FM, v, w, 2), 3)
+        fifa.fifa_destroy_fact(ctx.h, FM)
+        fifa.fifa_destroy_hmat(ctx.h, M)
         fifa.fifa_destroy_fact(ctx.h, F)
         fifa.fifa_destroy_hmat(ctx.h, H)
-    flops, sweep_bytes, L, per_level = factor_work(n, leaf, ranks)
-    peak_fp64 = 1.20  # measured FP64 FMA throughput of this GB300 (independent DFMA chains)
+    flops, L, per_level, leaves_m = factor_work(n, leaf, ranks)
+    sweep_b, pc_b, mv_b, mv_f = apply_work(n, leaves_m, ranks, L)
     achieved = flops / (ms * 1e-3) / 1e12
+
+    def hbm_entry(op, ms_, bytes_):
+        a = bytes_ / (ms_ * 1e-3) / 1e9
+        return {"bound": "hbm", "op": op, "ms": ms_, "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                "bytes": bytes_, "peak_source": src}
+
+    mv = hbm_entry("fused H-matrix product C~ x, FP64, 2 right-hand sides", ms_mv, mv_b)
+    mv["fp64"] = {"flops": mv_f, "achieved": mv_f / (ms_mv * 1e-3) / 1e12, "peak": peak_fp64, "unit": "TFLOP/s",
+                  "frac": mv_f / (ms_mv * 1e-3) / 1e12 / peak_fp64}
     return {"bound": "alu", "op": "FP64 HODLR factorization of C~ (leaf Cholesky + TRSM, per-level CholeskyQR2, "
                                   "capacitance, ancestor update)",
             "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s", "frac": achieved / peak_fp64,
-            "traffic": None, "ms": ms, "flops": flops, "rank_mean": float(ranks.mean()), "levels": L,
+            "traffic": FACTOR_TRAFFIC_BYTES, "ms": ms, "flops": flops, "rank_mean": float(ranks.mean()), "levels": L,
             "gflops_leaves_then_levels_deep_to_top": [round(f / 1e9, 4) for f in per_level],
             "rank_mean_per_level": [round(float(ranks[(1 << l) - 1:(1 << (l + 1)) - 1].mean()), 2) for l in range(L)],
-            "peak_source": "measured FP64 FMA throughput",
-            "sweep": {"bound": "hbm", "op": "W^-1 sweep, 2 right-hand sides", "ms": ms_sw,
-                      "achieved": sweep_bytes / (ms_sw * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                      "frac": sweep_bytes / (ms_sw * 1e-3) / 1e9 / hbm, "bytes": sweep_bytes,
-                      "peak_source": src}}
+            "peak_source": f"FP64 FMA throughput measured in this run (fifa_probe_fp64_fma, {probe_ms:.1f} ms)",
+            "sweep": hbm_entry("fused W^-1 sweep, FP64, 2 right-hand sides", ms_sw, sweep_b),
+            "matvec": mv,
+            "precond_fp32": hbm_entry("FP32 preconditioner solve W32^-T W32^-1 (one fused launch), 2 right-hand sides",
+                                      ms_pc, pc_b),
+            "mixed_solve_ms": ms_solve}
 
 
 def main():

@@ -70,9 +70,10 @@ typedef struct {
   int leaf_size;      /* B: leaves hold at most B points; 1..128 */
   double aca_tol;     /* absolute max-norm tolerance of every ACA block of C */
   int rank_cap;       /* maximum ACA rank per block; 1..64 */
-  int prec;           /* fifa_precision: FP64, or MIXED (M~ factor in FP32 + FP64 refinement) */
-  double refine_tol;  /* MIXED: stop refining when ||b - M~ x|| <= refine_tol ||b|| */
-  int refine_max;     /* MIXED: refinement steps captured per solve (fixed; converged steps are no-ops) */
+  int prec;           /* fifa_precision: FP64, or MIXED (see below) */
+  double refine_tol;  /* MIXED: stop iterating when ||b - M~ x|| <= refine_tol ||b|| */
+  int refine_max;     /* MIXED: conjugate-gradient steps captured per solve (fixed; once every system
+                         has converged the remaining steps' launches return at once) */
   int independent_ctas; /* 1: no kernel splits a tree node over a group of CTAs that wait on each
                            other (every CTA runs independently); required when several contexts
                            launch work concurrently on one GPU, since grouped kernels size their
@@ -128,8 +129,10 @@ fifa_status fifa_shift_scale(fifa_ctx* ctx, const fifa_hmat* C, double s, fifa_h
  *   Scratch: a file-scope static device array of 2^20 doubles (8 MiB) that every
  *   GPU loading the library holds until exit; no allocation routine is called.
  *   The first call on each device looks up the array's address with
- *   cudaGetSymbolAddress while that device is current and caches it; make that
- *   first call before any stream capture begins.
+ *   cudaGetSymbolAddress while that device is current and caches it together
+ *   with the id of the device's context; make that first call before any
+ *   stream capture begins.  After a device reset (a new context) the next call
+ *   looks the address up again, so make it outside stream capture as well.
  *   All calls share the array: calls that overlap on the GPU race on it and must
  *   be ordered by the caller.  Each call writes every scratch entry it reads.
  *   Limit: nleaf * levels * rank_cap * 2 + (2^levels - 1) * 4 * rank_cap doubles
@@ -139,9 +142,11 @@ fifa_status fifa_shift_scale(fifa_ctx* ctx, const fifa_hmat* C, double s, fifa_h
 fifa_status fifa_matvec_static(fifa_ctx* ctx, const fifa_hmat* A, const double* in_dev, double* out_dev, int nrhs);
 
 /* Symmetric factorization A = W W^T, W = A_L ... A_0 (SI, Ambikasaran Thm 3.1)
- * and log det A.  Precision: FP64, or FP32 storage and bulk arithmetic when the
- * context is MIXED and A is a shift_scale view (the M~ of Algorithm 1); leaf
- * and capacitance Cholesky factors and the log-determinant stay FP64.
+ * and log det A, computed in FP64.  When the context is MIXED and A is a
+ * shift_scale view (the M~ of Algorithm 1), the factor also carries an FP32
+ * copy of W (leaf factors, reciprocal pivots and bases rounded to FP32) that
+ * fifa_solve applies in FP32 arithmetic as the preconditioner of conjugate
+ * gradients on the FP64 operator.
  * Errors: OOM, CUDA; NOT_SPD is reported through fifa_fact_status/logdet. */
 fifa_status fifa_factor(fifa_ctx* ctx, const fifa_hmat* A, fifa_fact** out);
 
@@ -150,9 +155,18 @@ fifa_status fifa_factor(fifa_ctx* ctx, const fifa_hmat* A, fifa_fact** out);
 fifa_status fifa_logdet(fifa_ctx* ctx, const fifa_fact* F, double* out_host);
 
 /* x = A^-1 b = W^-T W^-1 b for nrhs column-major vectors of length n.
- * b_dev and x_dev may alias.  For an FP32 factor the solve is refined with
- * the FP64 operator (see fifa_opts).  Errors: INVALID_ARG. */
+ * b_dev and x_dev may alias.  For a MIXED factor: conjugate gradients on the
+ * FP64 operator A preconditioned by the factor's FP32 copy (applied in FP32
+ * arithmetic), x0 = that preconditioner applied to b, at most refine_max steps
+ * to ||b - A x|| <= refine_tol ||b|| (fifa_opts).  Errors: INVALID_ARG. */
 fifa_status fifa_solve(fifa_ctx* ctx, const fifa_fact* F, const double* b_dev, double* x_dev, int nrhs);
+
+/* out = W32^-T W32^-1 in for a MIXED factor F of M~ (fifa_factor on a
+ * shift_scale view in a MIXED context): the preconditioner of its solves, the
+ * FP32 copy of W applied in FP32 arithmetic (in and out stay FP64).  Agrees
+ * with A^-1 in to about sqrt(kappa(A)) u32.  in_dev and out_dev may alias.
+ * Errors: INVALID_ARG (also for a factor without an FP32 copy). */
+fifa_status fifa_apply_precond(fifa_ctx* ctx, const fifa_fact* F, const double* in_dev, double* out_dev, int nrhs);
 
 /* out = op(W) in, op = W, W^T, W^-1 or W^-T (trans, inverse in {0,1});
  * in_dev and out_dev may alias.  Errors: INVALID_ARG. */
@@ -183,17 +197,35 @@ fifa_status fifa_chain_create(fifa_ctx* ctx, const double* x_dev, const double* 
 /* Run `iters` Gibbs iterations (Eqs. posterior_gibs1-4 in order: f by
  * Algorithm 1, sigma2, tau2, then the Metropolis step on log rho).  The
  * whole iteration is captured once in a CUDA graph and replayed; nothing
- * returns to the host in between.  trace_host (nullable): iters rows of
- * FIFA_TRACE_FIELDS doubles (written after the last iteration, synchronizes):
- * iteration, sigma2, tau2, rho, accepted, log alpha, logdet C~(rho), q = f^T C~^-1 f,
- * ||y - f||^2, refinement residual, status.  Errors: the chain's device status. */
-#define FIFA_TRACE_FIELDS 11
+ * returns to the host in between.
+ * Precision: an FP64 chain factors M~ = (tau2/sigma2) C~ + I every iteration
+ * and solves with it directly.  A MIXED chain keeps its FP64 factor of M~
+ * between iterations and refactors only when the Metropolis step accepted a
+ * new rho, when tau2/sigma2 moved by more than 5% from the value it was
+ * factored at, or when the last solve needed more than 6 conjugate-gradient
+ * steps; its M~ solves are conjugate gradients on the current FP64 M~
+ * preconditioned by the FP32 copy of the kept factor.  C~ factors, log
+ * determinants and W_C products stay FP64 in both.
+ * trace_host (nullable): iters rows of FIFA_TRACE_FIELDS doubles (written after
+ * the last iteration, synchronizes): iteration, sigma2, tau2, rho, accepted,
+ * log alpha, logdet C~(rho), q = f^T C~^-1 f, ||y - f||^2, relative residual of
+ * the M~ solves (MIXED; 0 for FP64), status, M~ refactored this iteration (1/0),
+ * conjugate-gradient steps of the M~ solves.  Errors: the chain's device status. */
+#define FIFA_TRACE_FIELDS 13
 fifa_status fifa_gibbs_step(fifa_ctx* ctx, fifa_chain* chain, int iters, double* trace_host);
 
 /* Kernel launches of one Gibbs iteration: the kernel nodes of the captured
  * iteration graph (built by the first fifa_gibbs_step), or -1 if the chain
  * runs without a graph.  Synchronizes nothing. */
 fifa_status fifa_chain_kernel_nodes(const fifa_chain* chain, int* out_host);
+
+/* Replace the chain's observations y (n doubles, same inputs x) before its
+ * next iteration: y may be host memory (pinned for an asynchronous copy) or
+ * device memory; the copy is enqueued on the context's stream (no
+ * synchronization), so the caller keeps y unchanged until the stream reaches
+ * it.  For data streamed into a resident chain (the model of Sec. 2.1 with
+ * fixed inputs).  Errors: INVALID_ARG (also during stream capture), CUDA. */
+fifa_status fifa_chain_set_y(fifa_ctx* ctx, fifa_chain* chain, const double* y);
 
 /* Current state: f (and the last posterior mean tau2 C~ r) to device buffers
  * (nullable), hyperparameters to h_host (nullable); synchronizes. */
@@ -386,6 +418,14 @@ fifa_status fifa_normals(fifa_ctx* ctx, uint64_t seed, uint32_t tag, uint64_t it
 /* Raw Philox4x32-10 words: out[4i..4i+3] = Philox(ctr[4i..4i+3], key = seed),
  * for `count` counters (device uint32 arrays).  Exposed for parity tests. */
 fifa_status fifa_philox(fifa_ctx* ctx, uint64_t seed, const uint32_t* ctr_dev, uint32_t* out_dev, int64_t count);
+
+/* Measurement only (not part of the method): FP64 fused multiply-add
+ * throughput of this GPU, the roofline denominator of the FP64-issue-bound
+ * kernels.  Runs 8 independent FMA chains of `iters` steps in every thread of
+ * 8 CTAs x 256 threads per SM, timed with CUDA events on the context's stream
+ * (synchronizes): tflops_host = 16 iters threads / time; ms_host (nullable) the
+ * kernel time.  Errors: INVALID_ARG, CUDA. */
+fifa_status fifa_probe_fp64_fma(fifa_ctx* ctx, int iters, double* tflops_host, double* ms_host);
 
 #ifdef __cplusplus
 }

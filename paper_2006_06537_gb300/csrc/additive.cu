@@ -64,6 +64,7 @@ struct fifa_additive {
   // batched factorization of the blocks' M~ (all blocks share one plan): the
   // blocks' M~ factor and view descriptors and their scratch are contiguous
   FactDesc* fm_desc = nullptr;  // d
+  FactDesc* fm32_desc = nullptr;  // d: their FP32 copies (mixed precision), else null
   HmatDesc* mv_desc = nullptr;  // d
   FactDesc* f_desc[2] = {nullptr, nullptr};  // d each: current / proposal factor of C~
   HmatDesc* h_desc[2] = {nullptr, nullptr};  // d each: current / proposal C~
@@ -114,8 +115,8 @@ static fifa_status additive_sweep_enqueue(fifa_ctx* ctx, fifa_additive* A) {
       if (launch_chain_make_view(ch->H[0]->dev, ch->Mv->dev, ch->dev, ctx->stream) != cudaSuccess) st = FIFA_ERR_CUDA;
     }
     if (st == FIFA_OK)
-      st = fact_enqueue_batched(ctx, A->blk[0]->plan, A->blk[0]->FM->host.prec, A->fm_desc, A->mv_desc, d, A->scratch,
-                                A->scratch_stride);
+      st = fact_enqueue_batched(ctx, A->blk[0]->plan, A->fm_desc, A->mv_desc, d, A->scratch, A->scratch_stride,
+                                A->fm32_desc);
   } else {
     st = for_blocks(ctx, A, [&](int k) {
       ctx->active_scratch = A->blk[k]->scratch;
@@ -153,7 +154,7 @@ static fifa_status additive_sweep_enqueue(fifa_ctx* ctx, fifa_additive* A) {
       st = chain_phase_hyper_pre(ctx, ch, S);
     }
     if (st == FIFA_OK)
-      st = fact_enqueue_batched(ctx, A->blk[0]->plan, 0, A->f_desc[1], A->h_desc[1], d, A->scratch, A->scratch_stride);
+      st = fact_enqueue_batched(ctx, A->blk[0]->plan, A->f_desc[1], A->h_desc[1], d, A->scratch, A->scratch_stride);
     for (int k = 0; k < d && st == FIFA_OK; ++k) {
       fifa_chain* ch = A->blk[k];
       ctx->active_scratch = ch->scratch;
@@ -240,6 +241,8 @@ extern "C" fifa_status fifa_additive_create(fifa_ctx* ctx, const double* X_dev, 
     A->scratch = (char*)ctx->arena.alloc(A->scratch_stride * d);
     if (!A->fm_desc || !A->mv_desc || !A->f_desc[0] || !A->f_desc[1] || !A->h_desc[0] || !A->h_desc[1] || !A->scratch)
       return fail(FIFA_ERR_OOM);
+    if (A->blk[0]->FM->has32 && !(A->fm32_desc = (FactDesc*)ctx->arena.alloc(sizeof(FactDesc) * d)))
+      return fail(FIFA_ERR_OOM);
     for (int k = 0; k < d; ++k) {
       fifa_chain* ch = A->blk[k];
       CK(cudaMemcpyAsync(A->fm_desc + k, ch->FM->dev, sizeof(FactDesc), cudaMemcpyDeviceToDevice, s));
@@ -248,10 +251,16 @@ extern "C" fifa_status fifa_additive_create(fifa_ctx* ctx, const double* X_dev, 
         CK(cudaMemcpyAsync(A->f_desc[q] + k, ch->F[q]->dev, sizeof(FactDesc), cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(A->h_desc[q] + k, ch->H[q]->dev, sizeof(HmatDesc), cudaMemcpyDeviceToDevice, s));
       }
+      if (A->fm32_desc)
+        CK(cudaMemcpyAsync(A->fm32_desc + k, ch->FM->dev32, sizeof(FactDesc), cudaMemcpyDeviceToDevice, s));
       CK(cudaStreamSynchronize(s));
       ctx->arena.release(ch->FM->dev);
       ctx->arena.release(ch->Mv->dev);
       ctx->arena.release(ch->scratch);
+      if (A->fm32_desc) {
+        ctx->arena.release(ch->FM->dev32);
+        ch->FM->dev32 = A->fm32_desc + k;
+      }
       ch->FM->dev = A->fm_desc + k;
       ch->Mv->dev = A->mv_desc + k;
       for (int q = 0; q < 2; ++q) {
@@ -415,6 +424,7 @@ extern "C" void fifa_destroy_additive(fifa_ctx* ctx, fifa_additive* A) {
     if (A->blk[k]) {
       if (A->fm_desc) {  // these point into the model's shared arrays, released below
         A->blk[k]->FM->dev = nullptr;
+        if (A->fm32_desc) A->blk[k]->FM->dev32 = nullptr;
         A->blk[k]->Mv->dev = nullptr;
         for (int q = 0; q < 2; ++q) {
           A->blk[k]->F[q]->dev = nullptr;
@@ -425,6 +435,7 @@ extern "C" void fifa_destroy_additive(fifa_ctx* ctx, fifa_additive* A) {
       fifa_destroy_chain(ctx, A->blk[k]);
     }
   ctx->arena.release(A->fm_desc);
+  ctx->arena.release(A->fm32_desc);
   ctx->arena.release(A->mv_desc);
   for (int q = 0; q < 2; ++q) {
     ctx->arena.release(A->f_desc[q]);

@@ -14,6 +14,7 @@
 #include "fifa_chain.h"
 #include "fifa_common.cuh"
 #include "fifa_launch.h"
+#include "fifa_mixed.h"
 
 // ---------------------------------------------------------------------------
 // Arena: first-fit sub-allocator over one device buffer (256-byte granules).
@@ -226,6 +227,7 @@ static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, const int*
   add(256);                                                               // fused sweep barrier
   add(sizeof(double) * fused_mv_part_doubles(P, o));                      // fused matvec partials
   add(256);                                                               // fused matvec barrier
+  add(sizeof(double) * PCG_SCRATCH_DOUBLES);                              // mixed-precision solve state
   P->scratch_bytes = need;
   return P;
 }
@@ -335,14 +337,19 @@ size_t hmat_bytes(const Plan* P, int cap) {
          2 * arena_round(sizeof(int) * nn * cap) + arena_round(sizeof(int)) + arena_round(sizeof(HmatDesc));
 }
 
-size_t fact_bytes(const Plan* P, int cap, int prec) {
+size_t fact_bytes(const Plan* P, int cap, int with32) {
   const size_t nn = std::max(1, P->nnodes);
-  const size_t esz = prec ? sizeof(float) : sizeof(double);
-  return arena_round(esz * (size_t)P->nleaf * P->Bm * P->Bm) + arena_round(sizeof(double) * (size_t)P->nleaf * P->Bm) +
-         arena_round(esz * (size_t)std::max(1, P->L) * cap * P->n) +
-         2 * arena_round(sizeof(double) * nn * 4 * cap * cap) + arena_round(sizeof(int) * nn) +
-         arena_round(sizeof(double) * (P->nleaf + nn)) + arena_round(sizeof(double)) + arena_round(sizeof(int)) +
-         arena_round(sizeof(FactDesc));
+  size_t b = arena_round(sizeof(double) * (size_t)P->nleaf * P->Bm * P->Bm) +
+             arena_round(sizeof(double) * (size_t)P->nleaf * P->Bm) +
+             arena_round(sizeof(double) * (size_t)std::max(1, P->L) * cap * P->n) +
+             2 * arena_round(sizeof(double) * nn * 4 * cap * cap) + arena_round(sizeof(int) * nn) +
+             arena_round(sizeof(double) * (P->nleaf + nn)) + arena_round(sizeof(double)) + arena_round(sizeof(int)) +
+             arena_round(sizeof(FactDesc));
+  if (with32)  // the FP32 copy: leaf factors, reciprocal pivots, bases, descriptor
+    b += arena_round(sizeof(float) * (size_t)P->nleaf * P->Bm * P->Bm) +
+         arena_round(sizeof(float) * (size_t)P->nleaf * P->Bm) +
+         arena_round(sizeof(float) * (size_t)std::max(1, P->L) * cap * P->n) + arena_round(sizeof(FactDesc));
+  return b;
 }
 
 extern "C" fifa_status fifa_chain_bytes(const fifa_opts* opts, int64_t n, size_t* bytes_out) {
@@ -386,6 +393,7 @@ Scratch carve(fifa_ctx* ctx, Plan* P) {
   S.fs_bar = (unsigned int*)take(256);
   S.mv_fpart = (double*)take(sizeof(double) * fused_mv_part_doubles(P, ctx->opts));
   S.mv_bar = (unsigned int*)take(256);
+  S.pcg = (double*)take(sizeof(double) * PCG_SCRATCH_DOUBLES);
   return S;
 }
 
@@ -631,13 +639,12 @@ extern "C" void fifa_destroy_hmat(fifa_ctx* ctx, fifa_hmat* H) {
 // ---------------------------------------------------------------------------
 // Factor
 // ---------------------------------------------------------------------------
-fifa_status fact_alloc(fifa_ctx* ctx, Plan* P, int prec, fifa_fact** out) {
+fifa_status fact_alloc(fifa_ctx* ctx, Plan* P, int with32, fifa_fact** out) {
   fifa_fact* F = new (std::nothrow) fifa_fact();
   if (!F) return FIFA_ERR_OOM;
   F->plan = P;
   const int cap = ctx->opts.rank_cap;
   const size_t nn = std::max(1, P->nnodes);
-  const size_t esz = prec ? sizeof(float) : sizeof(double);
   FactDesc& d = F->host;
   memset(&d, 0, sizeof(d));
   d.n = P->n;
@@ -645,11 +652,12 @@ fifa_status fact_alloc(fifa_ctx* ctx, Plan* P, int prec, fifa_fact** out) {
   d.nleaf = P->nleaf;
   d.Bm = P->Bm;
   d.cap = cap;
-  d.prec = prec;
+  d.prec = 0;
   d.bnd = P->bnd_dev;
-  d.Lleaf = ctx->arena.alloc(esz * (size_t)P->nleaf * P->Bm * P->Bm);
-  d.Ldinv = (double*)ctx->arena.alloc(sizeof(double) * (size_t)P->nleaf * P->Bm);
-  d.Q = ctx->arena.alloc(esz * (size_t)std::max(1, P->L) * cap * P->n);
+  d.skip = nullptr;
+  d.Lleaf = ctx->arena.alloc(sizeof(double) * (size_t)P->nleaf * P->Bm * P->Bm);
+  d.Ldinv = ctx->arena.alloc(sizeof(double) * (size_t)P->nleaf * P->Bm);
+  d.Q = ctx->arena.alloc(sizeof(double) * (size_t)std::max(1, P->L) * cap * P->n);
   d.Zf = (double*)ctx->arena.alloc(sizeof(double) * nn * 4 * cap * cap);
   d.Zi = (double*)ctx->arena.alloc(sizeof(double) * nn * 4 * cap * cap);
   d.rank = (int*)ctx->arena.alloc(sizeof(int) * nn);
@@ -661,8 +669,30 @@ fifa_status fact_alloc(fifa_ctx* ctx, Plan* P, int prec, fifa_fact** out) {
     fifa_destroy_fact(ctx, F);
     return FIFA_ERR_OOM;
   }
+  if (with32) {
+    F->has32 = true;
+    FactDesc& h = F->host32;
+    h = d;  // Zf, Zi, ranks, log-determinant and status are the FP64 factor's
+    h.prec = 1;
+    h.skip = nullptr;
+    h.Lleaf = ctx->arena.alloc(sizeof(float) * (size_t)P->nleaf * P->Bm * P->Bm);
+    h.Ldinv = ctx->arena.alloc(sizeof(float) * (size_t)P->nleaf * P->Bm);
+    h.Q = ctx->arena.alloc(sizeof(float) * (size_t)std::max(1, P->L) * cap * P->n);
+    F->dev32 = (FactDesc*)ctx->arena.alloc(sizeof(FactDesc));
+    if (!h.Lleaf || !h.Ldinv || !h.Q || !F->dev32) {
+      fifa_destroy_fact(ctx, F);
+      return FIFA_ERR_OOM;
+    }
+    CK(cudaMemcpyAsync(F->dev32, &F->host32, sizeof(FactDesc), cudaMemcpyHostToDevice, ctx->stream));
+  }
   CK(cudaMemcpyAsync(F->dev, &F->host, sizeof(FactDesc), cudaMemcpyHostToDevice, ctx->stream));
   *out = F;
+  return FIFA_OK;
+}
+
+fifa_status fact_set_skip(fifa_ctx* ctx, fifa_fact* F, const int* skip_dev) {
+  F->host.skip = skip_dev;
+  CK(cudaMemcpyAsync(F->dev, &F->host, sizeof(FactDesc), cudaMemcpyHostToDevice, ctx->stream));
   return FIFA_OK;
 }
 
@@ -686,14 +716,16 @@ fifa_status fact_enqueue(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev) {
     CK(launch_level(F->dev, prec, l, 1 << l, Gb, cap, S.lvl_part, S.lvl_bar, P->lvl_ctas_max, S.flags, side_max, s));
   }
   CK(launch_logdet_reduce(F->dev, s));
+  if (F->has32) CK(launch_demote(F->dev, F->dev32, P->n, s));
   return FIFA_OK;
 }
 
 // Factor nprob matrices of one plan in one launch per step and tree level:
 // F0[q] from H0[q] (contiguous descriptor arrays), problem q's scratch at
 // scratch0 + q * sstride bytes.  Groups shrink to fit all problems' CTAs.
-fifa_status fact_enqueue_batched(fifa_ctx* ctx, Plan* P, int prec, FactDesc* F0, const HmatDesc* H0, int nprob,
-                                 void* scratch0, size_t sstride) {
+fifa_status fact_enqueue_batched(fifa_ctx* ctx, Plan* P, FactDesc* F0, const HmatDesc* H0, int nprob,
+                                 void* scratch0, size_t sstride, const FactDesc* F32_0) {
+  const int prec = 0;
   void* saved = ctx->active_scratch;
   ctx->active_scratch = scratch0;
   Scratch S = carve(ctx, P);
@@ -714,15 +746,16 @@ fifa_status fact_enqueue_batched(fifa_ctx* ctx, Plan* P, int prec, FactDesc* F0,
                     sstride));
   }
   CK(launch_logdet_reduce(F0, s, nprob));
+  if (F32_0) CK(launch_demote(F0, F32_0, P->n, s, nprob));
   return FIFA_OK;
 }
 
 extern "C" fifa_status fifa_factor(fifa_ctx* ctx, const fifa_hmat* A, fifa_fact** out) {
   if (!ctx || !A || !out) return FIFA_ERR_INVALID_ARG;
   *out = nullptr;
-  const int prec = (ctx->opts.prec == FIFA_MIXED && A->host.shift != 0.0) ? 1 : 0;
+  const int with32 = (ctx->opts.prec == FIFA_MIXED && A->host.shift != 0.0) ? 1 : 0;
   fifa_fact* F = nullptr;
-  fifa_status st = fact_alloc(ctx, A->plan, prec, &F);
+  fifa_status st = fact_alloc(ctx, A->plan, with32, &F);
   if (st != FIFA_OK) return st;
   F->src = A;
   st = fact_enqueue(ctx, F, A->dev);
@@ -748,6 +781,12 @@ extern "C" void fifa_destroy_fact(fifa_ctx* ctx, fifa_fact* F) {
   ctx->arena.release(d.logdet);
   ctx->arena.release(d.status);
   ctx->arena.release(F->dev);
+  if (F->has32) {
+    ctx->arena.release(F->host32.Lleaf);
+    ctx->arena.release(F->host32.Ldinv);
+    ctx->arena.release(F->host32.Q);
+    ctx->arena.release(F->dev32);
+  }
   delete F;
 }
 
@@ -764,36 +803,49 @@ extern "C" fifa_status fifa_logdet(fifa_ctx* ctx, const fifa_fact* F, double* ou
 // ---------------------------------------------------------------------------
 // Sweeps, solve, matvec
 // ---------------------------------------------------------------------------
-fifa_status sweep_enqueue(fifa_ctx* ctx, const fifa_fact* F, int trans, int inverse, double* v, int nrhs) {
-  Plan* P = F->plan;
+fifa_status sweep_enqueue_desc(fifa_ctx* ctx, Plan* P, const FactDesc* Fdev, int prec, int mode, double* v, int nrhs,
+                               const int* active) {
   Scratch S = carve(ctx, P);
   cudaStream_t s = ctx->stream;
-  const int prec = F->host.prec;
   if (P->fs_ls >= 0) {
-    const int mode = trans ? (inverse ? 3 : 2) : (inverse ? 1 : 0);
     CK(cudaMemsetAsync(S.fs_bar, 0, sizeof(unsigned int), s));
     CK(cudaMemsetAsync(S.flags, 0, sizeof(int), s));
-    CK(launch_sweep_fused(F->dev, prec, P->fs_ls, P->fs_rows, ctx->opts.rank_cap, v, nrhs, mode, S.fs_part, S.fs_bar,
-                          S.flags, s));
+    CK(launch_sweep_fused(Fdev, prec, P->fs_ls, P->fs_rows, ctx->opts.rank_cap, v, nrhs, mode, S.fs_part, S.fs_bar,
+                          S.flags, s, active));
     return FIFA_OK;
   }
   auto level = [&](int l, int zsel, int zt) -> cudaError_t {
-    return launch_sweep_level(F->dev, prec, l, 1 << l, P->sweep_G[l], v, nrhs, S.sweep_part, zsel, zt, s);
+    return launch_sweep_level(Fdev, prec, l, 1 << l, P->sweep_G[l], v, nrhs, S.sweep_part, zsel, zt, s, active);
   };
-  if (!trans && !inverse) {
-    for (int l = 0; l < P->L; ++l) CK(level(l, 0, 0));
-    CK(launch_sweep_leaf(F->dev, prec, P->nleaf, v, nrhs, 0, s));
-  } else if (!trans && inverse) {
-    CK(launch_sweep_leaf(F->dev, prec, P->nleaf, v, nrhs, 1, s));
-    for (int l = P->L - 1; l >= 0; --l) CK(level(l, 1, 0));
-  } else if (trans && !inverse) {
-    CK(launch_sweep_leaf(F->dev, prec, P->nleaf, v, nrhs, 2, s));
-    for (int l = P->L - 1; l >= 0; --l) CK(level(l, 0, 1));
+  auto one = [&](int md) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    if (md == 0) {
+      for (int l = 0; l < P->L && e == cudaSuccess; ++l) e = level(l, 0, 0);
+      if (e == cudaSuccess) e = launch_sweep_leaf(Fdev, prec, P->nleaf, v, nrhs, 0, s, active);
+    } else if (md == 1) {
+      e = launch_sweep_leaf(Fdev, prec, P->nleaf, v, nrhs, 1, s, active);
+      for (int l = P->L - 1; l >= 0 && e == cudaSuccess; --l) e = level(l, 1, 0);
+    } else if (md == 2) {
+      e = launch_sweep_leaf(Fdev, prec, P->nleaf, v, nrhs, 2, s, active);
+      for (int l = P->L - 1; l >= 0 && e == cudaSuccess; --l) e = level(l, 0, 1);
+    } else {
+      for (int l = 0; l < P->L && e == cudaSuccess; ++l) e = level(l, 1, 1);
+      if (e == cudaSuccess) e = launch_sweep_leaf(Fdev, prec, P->nleaf, v, nrhs, 3, s, active);
+    }
+    return e;
+  };
+  if (mode == 4) {
+    CK(one(1));
+    CK(one(3));
   } else {
-    for (int l = 0; l < P->L; ++l) CK(level(l, 1, 1));
-    CK(launch_sweep_leaf(F->dev, prec, P->nleaf, v, nrhs, 3, s));
+    CK(one(mode));
   }
   return FIFA_OK;
+}
+
+fifa_status sweep_enqueue(fifa_ctx* ctx, const fifa_fact* F, int trans, int inverse, double* v, int nrhs) {
+  const int mode = trans ? (inverse ? 3 : 2) : (inverse ? 1 : 0);
+  return sweep_enqueue_desc(ctx, F->plan, F->dev, F->host.prec, mode, v, nrhs);
 }
 
 extern "C" fifa_status fifa_apply_W(fifa_ctx* ctx, const fifa_fact* F, int trans, int inverse, const double* in_dev,
@@ -806,16 +858,28 @@ extern "C" fifa_status fifa_apply_W(fifa_ctx* ctx, const fifa_fact* F, int trans
   return sweep_enqueue(ctx, F, trans ? 1 : 0, inverse ? 1 : 0, out_dev, nrhs);
 }
 
-fifa_status matvec_enqueue(fifa_ctx* ctx, const fifa_hmat* A, const double* in, double* out, int nrhs) {
+extern "C" fifa_status fifa_apply_precond(fifa_ctx* ctx, const fifa_fact* F, const double* in_dev, double* out_dev,
+                                          int nrhs) {
+  if (!ctx || !F || !F->has32 || !in_dev || !out_dev || nrhs < 1 || nrhs > SWEEP_RHS_MAX) return FIFA_ERR_INVALID_ARG;
+  fifa_status st = ensure_scratch(ctx, F->plan);
+  if (st != FIFA_OK) return st;
+  if (in_dev != out_dev)
+    CK(cudaMemcpyAsync(out_dev, in_dev, sizeof(double) * F->plan->n * nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
+  return sweep_enqueue_desc(ctx, F->plan, F->dev32, 1, 4, out_dev, nrhs);
+}
+
+fifa_status matvec_enqueue(fifa_ctx* ctx, const fifa_hmat* A, const double* in, double* out, int nrhs,
+                           const int* active) {
   Plan* P = A->plan;
   Scratch S = carve(ctx, P);
   if (P->mv_ls >= 0) {
     CK(cudaMemsetAsync(S.mv_bar, 0, sizeof(unsigned int), ctx->stream));
     CK(cudaMemsetAsync(S.flags, 0, sizeof(int), ctx->stream));
-    CK(launch_mv_fused(A->dev, P->mv_ls, P->mv_rows, in, nrhs, out, S.mv_fpart, S.mv_bar, S.flags, ctx->stream));
+    CK(launch_mv_fused(A->dev, P->mv_ls, P->mv_rows, in, nrhs, out, S.mv_fpart, S.mv_bar, S.flags, ctx->stream,
+                       active));
     return FIFA_OK;
   }
-  CK(launch_matvec(A->dev, P->nleaf, P->L, in, nrhs, S.mv_part, S.mv_proj, out, ctx->stream));
+  CK(launch_matvec(A->dev, P->nleaf, P->L, in, nrhs, S.mv_part, S.mv_proj, out, ctx->stream, active));
   return FIFA_OK;
 }
 
@@ -827,59 +891,54 @@ extern "C" fifa_status fifa_matvec(fifa_ctx* ctx, const fifa_hmat* A, const doub
   return matvec_enqueue(ctx, A, in_dev, out_dev, nrhs);
 }
 
-// x = A^-1 b, refined against the FP64 operator when the factor is FP32.
-// x = A^-1 b.  FP64 factor: W^-T W^-1 b.  FP32 factor: preconditioned conjugate
-// gradients on the FP64 operator F->src with W32 W32^T as preconditioner,
-// refine_max steps captured (a converged system's steps are no-ops); work
-// holds 4 n nrhs doubles.
+// x = A^-1 b.  FP64 factor: W^-T W^-1 b (two sweeps, or one fused launch).
+// Mixed factor: conjugate gradients on the FP64 operator (op, default the
+// factored matrix) preconditioned by W32 W32^T, the FP32 copy of the factor
+// applied in FP32 arithmetic: x0 = P^-1 b, then refine_max captured
+// iterations; once every system meets ||r|| <= refine_tol ||b|| the remaining
+// iterations' launches return at once.  work holds 4 n nrhs doubles (r, z, p,
+// q); b must not alias x for a mixed factor.
 fifa_status solve_enqueue(fifa_ctx* ctx, const fifa_fact* F, const double* b, double* x, int nrhs, double* work,
-                          double* res_dev) {
-  const int64_t n = F->plan->n;
+                          double* res_dev, int* iters_dev, const fifa_hmat* op) {
+  Plan* P = F->plan;
+  const int64_t n = P->n;
   const int64_t nn = n * nrhs;
   cudaStream_t s = ctx->stream;
   if (x != b) CK(cudaMemcpyAsync(x, b, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-  fifa_status st = sweep_enqueue(ctx, F, 0, 1, x, nrhs);
-  if (st == FIFA_OK) st = sweep_enqueue(ctx, F, 1, 1, x, nrhs);
-  if (st != FIFA_OK || F->host.prec == 0 || !F->src) return st;
-  Scratch S = carve(ctx, F->plan);
-  double* part = S.red;        // DOT_BLOCKS * nrhs partial sums
-  double* pst = S.red + 256;   // PCG state, 8 per right-hand side
+  if (!F->has32) return sweep_enqueue_desc(ctx, P, F->dev, 0, 4, x, nrhs);
+  if (!op) op = F->src;
+  if (!op || x == b) return FIFA_ERR_INVALID_ARG;
+  Scratch S = carve(ctx, P);
+  double* part = S.pcg;
+  double* st = S.pcg + PCG_OFF_STATE;  // two parity slots of PCG_RHS_MAX * PCG_SLOT doubles
+  int* ints = (int*)(S.pcg + PCG_OFF_INTS);
+  int* act = ints;        // act[2]
+  int* iters = ints + 2;  // iterations taken
   double* r = work;
   double* z = work + nn;
   double* p = work + 2 * nn;
   double* q = work + 3 * nn;
   const double tol = ctx->opts.refine_tol > 0.0 ? ctx->opts.refine_tol : 1e-12;
-  auto prec_solve = [&](double* v) -> fifa_status {
-    fifa_status e = sweep_enqueue(ctx, F, 0, 1, v, nrhs);
-    return e == FIFA_OK ? sweep_enqueue(ctx, F, 1, 1, v, nrhs) : e;
-  };
-  st = matvec_enqueue(ctx, F->src, x, r, nrhs);
-  if (st != FIFA_OK) return st;
-  CK(launch_residual_axpy(b, r, nn, s));  // r = b - A x0
-  CK(launch_dot(b, b, n, nrhs, part, pst, 4, s));
-  CK(cudaMemcpyAsync(z, r, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-  if ((st = prec_solve(z)) != FIFA_OK) return st;
-  CK(launch_dot(r, z, n, nrhs, part, pst, 0, s));
-  CK(cudaMemcpyAsync(p, z, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  const double tol2 = tol * tol;
+  fifa_status e = sweep_enqueue_desc(ctx, P, F->dev32, 1, 4, x, nrhs);  // x0 = P^-1 b
+  if (e != FIFA_OK) return e;
+  if ((e = matvec_enqueue(ctx, op, x, r, nrhs)) != FIFA_OK) return e;
+  CK(launch_pcg_residual0(b, r, z, n, nrhs, part, s));  // r = b - A x0, z = r
+  if ((e = sweep_enqueue_desc(ctx, P, F->dev32, 1, 4, z, nrhs)) != FIFA_OK) return e;
+  CK(launch_pcg_start(r, z, p, n, nrhs, part, st, act, iters, tol2, s));
+  const int slot = PCG_RHS_MAX * PCG_SLOT;
   for (int it = 0; it < ctx->opts.refine_max; ++it) {
-    if ((st = matvec_enqueue(ctx, F->src, p, q, nrhs)) != FIFA_OK) return st;
-    CK(launch_dot(p, q, n, nrhs, part, pst, 1, s));
-    CK(launch_dot(r, r, n, nrhs, part, pst, 3, s));
-    CK(launch_pcg_alpha(pst, nrhs, tol * tol, s));
-    CK(launch_pcg_xr(x, r, p, q, pst, n, nrhs, s));
-    CK(cudaMemcpyAsync(z, r, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-    if ((st = prec_solve(z)) != FIFA_OK) return st;
-    CK(launch_dot(r, z, n, nrhs, part, pst, 5, s));
-    CK(launch_pcg_beta(pst, nrhs, s));
-    CK(launch_pcg_p(p, z, pst, n, nrhs, s));
+    const int cur = it & 1, nxt = cur ^ 1;
+    if ((e = matvec_enqueue(ctx, op, p, q, nrhs, act + cur)) != FIFA_OK) return e;
+    CK(launch_pcg_pq(p, q, n, nrhs, part, act + cur, s));
+    CK(launch_pcg_update(x, r, z, p, q, n, nrhs, st + cur * slot, part, act + cur, s));
+    if ((e = sweep_enqueue_desc(ctx, P, F->dev32, 1, 4, z, nrhs, act + cur)) != FIFA_OK) return e;
+    CK(launch_pcg_direction(r, p, z, n, nrhs, st + cur * slot, st + nxt * slot, act + cur, act + nxt, iters, part,
+                            tol2, s));
   }
-  if (res_dev) {  // true relative residual ||b - A x|| / ||b|| in FP64
-    st = matvec_enqueue(ctx, F->src, x, r, nrhs);
-    if (st != FIFA_OK) return st;
-    CK(launch_residual_axpy(b, r, nn, s));
-    CK(launch_sumsq(r, nullptr, nn, S.red, S.red + 300, s));
-    CK(launch_sumsq(b, nullptr, nn, S.red, S.red + 301, s));
-    CK(launch_ratio_sqrt(S.red + 300, S.red + 301, res_dev, s));
+  if (res_dev || iters_dev) {  // the true relative residual ||b - A x|| / ||b||, in FP64
+    if ((e = matvec_enqueue(ctx, op, x, q, nrhs)) != FIFA_OK) return e;
+    CK(launch_pcg_true_residual(b, q, n, nrhs, part, res_dev, iters, iters_dev, s));
   }
   return FIFA_OK;
 }
@@ -891,7 +950,7 @@ extern "C" fifa_status fifa_solve(fifa_ctx* ctx, const fifa_fact* F, const doubl
   Scratch S = carve(ctx, F->plan);
   const int64_t n = F->plan->n;
   const double* b = b_dev;
-  if (b_dev == x_dev && F->host.prec) {  // the iteration needs the original right-hand side
+  if (b_dev == x_dev && F->has32) {  // the iteration needs the original right-hand side
     CK(cudaMemcpyAsync(S.vec + 8 * n, b_dev, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
     b = S.vec + 8 * n;
   }
@@ -903,7 +962,8 @@ extern "C" fifa_status fifa_solve(fifa_ctx* ctx, const fifa_fact* F, const doubl
 // ---------------------------------------------------------------------------
 fifa_status sample_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, const fifa_fact* WM, const double* y,
                            double tau2, double sigma2, uint64_t seed, uint64_t sid, const uint64_t* iter_dev,
-                           uint64_t iter_host, double* f, double* mean, const double* scal_dev, double* res_dev) {
+                           uint64_t iter_host, double* f, double* mean, const double* scal_dev, double* res_dev,
+                           int* iters_dev, const fifa_hmat* op) {
   Plan* P = C->plan;
   const int64_t n = P->n;
   Scratch S = carve(ctx, P);
@@ -923,9 +983,9 @@ fifa_status sample_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* W
   if (st != FIFA_OK) return st;
   // rhs0 = (tau2/sigma) Ca + tau Wb ; rhs1 = y / sigma2
   CK(launch_alg1_rhs(Ca, b, y, rhs, n, tau2, sigma2, scal_dev, s));
-  if (WM->host.prec) {
+  if (WM->has32) {
     CK(cudaMemcpyAsync(bsave, rhs, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, s));
-    st = solve_enqueue(ctx, WM, bsave, rhs, 2, work, res_dev);
+    st = solve_enqueue(ctx, WM, bsave, rhs, 2, work, res_dev, iters_dev, op);
   } else {
     st = solve_enqueue(ctx, WM, rhs, rhs, 2, work);
   }
@@ -1043,6 +1103,37 @@ extern "C" fifa_status fifa_philox(fifa_ctx* ctx, uint64_t seed, const uint32_t*
   if (count == 0) return FIFA_OK;
   CK(launch_philox(seed, ctr_dev, out_dev, count, ctx->stream));
   return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_probe_fp64_fma(fifa_ctx* ctx, int iters, double* tflops_host, double* ms_host) {
+  if (!ctx || iters < 1 || !tflops_host) return FIFA_ERR_INVALID_ARG;
+  cudaStream_t s = ctx->stream;
+  const int blocks = ctx->num_sms * 8;  // 8 CTAs of 256 threads per SM: 64 warps, full occupancy
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return FIFA_ERR_CUDA;
+  }
+  fifa_status st = FIFA_OK;
+  float ms = 0.0f;
+  cudaError_t e = launch_dfma_probe((double*)ctx->flags, 1000, blocks, s);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess) e = launch_dfma_probe((double*)ctx->flags, iters, blocks, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e != cudaSuccess) {
+    ctx->last_cuda = e;
+    st = FIFA_ERR_CUDA;
+  } else {
+    const double flops = 2.0 * 8.0 * (double)iters * 256.0 * (double)blocks;
+    *tflops_host = flops / ((double)ms * 1e-3) / 1e12;
+    if (ms_host) *ms_host = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
 }
 
 extern "C" const char* fifa_last_cuda_error(const fifa_ctx* ctx) {

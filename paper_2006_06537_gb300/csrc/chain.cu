@@ -1,7 +1,8 @@
 // Gibbs chain: device-resident state and one iteration captured in a CUDA graph.
 //
 // Per iteration (Sec. 4.1, in the order of Eqs. posterior_gibs1-4):
-//   M~ = s C~ + I view (s = tau2 / sigma2), factor M~ (FP64, or FP32 + refinement)
+//   M~ = s C~ + I view (s = tau2 / sigma2) and its FP64 factor (mixed: kept from
+//   an earlier iteration unless it must be refreshed, plus its FP32 copy)
 //   f by Algorithm 1 (Philox a, b; C~ a, W_C b, two-right-hand-side solve, C~ r)
 //   sigma2 | y, f ;  q = ||W_C^-1 f||^2 ;  tau2 | f
 //   propose rho', assemble C~(rho') (leaves + ACA), factor it, q' = ||W'^-1 f||^2
@@ -35,11 +36,12 @@ fifa_status chain_phase_factor_m(fifa_ctx* ctx, fifa_chain* ch) {
   return fact_enqueue(ctx, ch->FM, ch->Mv->dev);
 }
 
-// Phase 1b: f | y by Algorithm 1 (after phase 1a).
+// Phase 1b: f | y by Algorithm 1 (after phase 1a).  A mixed chain's M~ solves
+// iterate on the current M~ view with its kept factor as preconditioner.
 fifa_status chain_phase_sample(fifa_ctx* ctx, fifa_chain* ch) {
   ChainDev* c = ch->dev;
   return sample_enqueue(ctx, ch->H[0], ch->F[0], ch->FM, ch->y, 0.0, 0.0, ch->init.seed, ch->init.chain_id, &c->iter,
-                        0, ch->f, ch->mean, &c->tau2, &c->refine_res);
+                        0, ch->f, ch->mean, &c->tau2, &c->refine_res, &c->pcg_iters, ch->Mv);
 }
 
 // Phase 1: phases 1a and 1b.
@@ -184,6 +186,8 @@ extern "C" fifa_status fifa_chain_create(fifa_ctx* ctx, const double* x_dev, con
   st = fact_alloc(ctx, P, ctx->opts.prec == FIFA_MIXED ? 1 : 0, &ch->FM);
   if (st != FIFA_OK) return fail(st);
   ch->FM->src = ch->Mv;
+  // the M~ factorization kernels read the chain's keep flag (set every iteration)
+  if (ctx->opts.prec == FIFA_MIXED && (st = fact_set_skip(ctx, ch->FM, &ch->dev->fm_skip)) != FIFA_OK) return fail(st);
   ChainDev& c = ch->init;
   memset(&c, 0, sizeof(c));
   c.tau2 = init->tau2;
@@ -204,6 +208,9 @@ extern "C" fifa_status fifa_chain_create(fifa_ctx* ctx, const double* x_dev, con
   c.kind = init->kernel;
   c.trace_cap = CHAIN_TRACE_CAP;
   c.trace = ch->trace;
+  c.mixed = ctx->opts.prec == FIFA_MIXED ? 1 : 0;
+  c.fm_skip = 0;
+  c.s_ref = 0.0;
   CK(cudaMemcpyAsync(ch->dev, &c, sizeof(ChainDev), cudaMemcpyHostToDevice, s));
   // C~(rho_0) and its factor
   ctx->active_scratch = ch->scratch;
@@ -329,6 +336,12 @@ fifa_status chain_run_collect(fifa_ctx* ctx, fifa_chain* ch, int iters, int burn
 fifa_status chain_state(fifa_ctx* ctx, const fifa_chain* ch, ChainDev* out) {
   CK(cudaMemcpyAsync(out, ch->dev, sizeof(ChainDev), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_chain_set_y(fifa_ctx* ctx, fifa_chain* ch, const double* y) {
+  if (!ctx || !ch || !y || ctx->capturing) return FIFA_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(ch->y, y, sizeof(double) * ch->plan->n, cudaMemcpyDefault, ctx->stream));
   return FIFA_OK;
 }
 

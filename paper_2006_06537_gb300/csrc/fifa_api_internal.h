@@ -49,6 +49,7 @@ struct Scratch {
   unsigned int* fs_bar;   // fused sweep grid barrier
   double* mv_fpart;       // fused H-matvec partials
   unsigned int* mv_bar;   // fused H-matvec grid barrier
+  double* pcg;            // PCG_SCRATCH_DOUBLES: partial sums and state of a mixed-precision solve
 };
 
 struct fifa_ctx {
@@ -81,7 +82,13 @@ struct fifa_fact {
   Plan* plan = nullptr;
   FactDesc host{};
   FactDesc* dev = nullptr;
-  const fifa_hmat* src = nullptr;  // operator used for refinement (FP32 factors)
+  const fifa_hmat* src = nullptr;  // the factored operator (the one a mixed solve iterates on)
+  // Mixed precision: an FP32 copy of this FP64 factor (prec 1; Zf, Zi, ranks,
+  // log-determinant and status shared), refreshed after every factorization
+  // and applied as the preconditioner of the FP64-residual iteration.
+  bool has32 = false;
+  FactDesc host32{};
+  FactDesc* dev32 = nullptr;
 };
 
 Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st);
@@ -90,37 +97,43 @@ Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st);
 fifa_status ctx_rebind_arena(fifa_ctx* ctx, void* base, size_t bytes);
 // Arena bytes of one hmat / fact / chain (every allocation rounded as the arena does).
 size_t hmat_bytes(const Plan* P, int cap);
-size_t fact_bytes(const Plan* P, int cap, int prec);
+size_t fact_bytes(const Plan* P, int cap, int with32);
 size_t chain_bytes(const Plan* P, const fifa_opts& o);
 Scratch carve(fifa_ctx* ctx, Plan* P);
 fifa_status ensure_scratch(fifa_ctx* ctx, Plan* P);
 fifa_status hmat_alloc(fifa_ctx* ctx, Plan* P, int kind, fifa_hmat** out);
 fifa_status hmat_assemble_enqueue(fifa_ctx* ctx, fifa_hmat* H);
-fifa_status fact_alloc(fifa_ctx* ctx, Plan* P, int prec, fifa_fact** out);
+// with32: also allocate the FP32 copy (a mixed-precision factor of M~).
+fifa_status fact_alloc(fifa_ctx* ctx, Plan* P, int with32, fifa_fact** out);
+// Point the factor's skip flag at a device int (nullable) and upload its descriptor.
+fifa_status fact_set_skip(fifa_ctx* ctx, fifa_fact* F, const int* skip_dev);
 fifa_status fact_enqueue(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev);
-fifa_status fact_enqueue_batched(fifa_ctx* ctx, Plan* P, int prec, FactDesc* F0, const HmatDesc* H0, int nprob,
-                                 void* scratch0, size_t sstride);
+// F32_0 (nullable): the problems' FP32 copies, refreshed after the factorization.
+fifa_status fact_enqueue_batched(fifa_ctx* ctx, Plan* P, FactDesc* F0, const HmatDesc* H0, int nprob,
+                                 void* scratch0, size_t sstride, const FactDesc* F32_0 = nullptr);
 fifa_status sweep_enqueue(fifa_ctx* ctx, const fifa_fact* F, int trans, int inverse, double* v, int nrhs);
-fifa_status matvec_enqueue(fifa_ctx* ctx, const fifa_hmat* A, const double* in, double* out, int nrhs);
+// Sweep with a factor descriptor of either precision; mode as launch_sweep_fused
+// (4: W^-T W^-1); active (nullable) as there.
+fifa_status sweep_enqueue_desc(fifa_ctx* ctx, Plan* P, const FactDesc* Fdev, int prec, int mode, double* v, int nrhs,
+                               const int* active = nullptr);
+fifa_status matvec_enqueue(fifa_ctx* ctx, const fifa_hmat* A, const double* in, double* out, int nrhs,
+                           const int* active = nullptr);
+// x = A^-1 b.  FP64 factor: W^-T W^-1 b.  Mixed factor: conjugate gradients on
+// the FP64 operator op (default F->src) preconditioned by the FP32 copy.
+// res_dev (nullable): the final true relative residual; iters_dev (nullable):
+// conjugate-gradient iterations taken.
 fifa_status solve_enqueue(fifa_ctx* ctx, const fifa_fact* F, const double* b, double* x, int nrhs, double* work,
-                          double* res_dev = nullptr);
+                          double* res_dev = nullptr, int* iters_dev = nullptr, const fifa_hmat* op = nullptr);
 fifa_status sample_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, const fifa_fact* WM, const double* y,
                            double tau2, double sigma2, uint64_t seed, uint64_t sid, const uint64_t* iter_dev,
-                           uint64_t iter_host, double* f, double* mean, const double* scal_dev, double* res_dev = nullptr);
+                           uint64_t iter_host, double* f, double* mean, const double* scal_dev, double* res_dev = nullptr,
+                           int* iters_dev = nullptr, const fifa_hmat* op = nullptr);
 
 // vector kernels (k_vec.cu)
 cudaError_t launch_prep_hmat(HmatDesc* H, int nnodes, cudaStream_t st);
 cudaError_t launch_prep_fact(FactDesc* F, const HmatDesc* H, int nnodes, cudaStream_t st, int nprob = 1);
 cudaError_t launch_sumsq(const double* a, const double* b, int64_t n, double* part, double* out, cudaStream_t st);
 cudaError_t launch_axpy(double a, const double* x, double* y, int64_t n, cudaStream_t st);
-cudaError_t launch_dot(const double* a, const double* b, int64_t n, int nrhs, double* part, double* st, int slot,
-                       cudaStream_t stream);
-cudaError_t launch_pcg_alpha(double* st, int nrhs, double tol2, cudaStream_t stream);
-cudaError_t launch_pcg_beta(double* st, int nrhs, cudaStream_t stream);
-cudaError_t launch_pcg_xr(double* x, double* r, const double* p, const double* q, const double* st, int64_t n, int nrhs,
-                          cudaStream_t stream);
-cudaError_t launch_pcg_p(double* p, const double* z, const double* st, int64_t n, int nrhs, cudaStream_t stream);
-cudaError_t launch_residual_axpy(const double* b, double* r, int64_t n, cudaStream_t st);
 cudaError_t launch_alg1_rhs(const double* Ca, const double* Wb, const double* y, double* rhs, int64_t n, double tau2,
                             double sigma2, const double* scal_dev, cudaStream_t st);
 cudaError_t launch_alg1_finish(const double* wr, const double* Cr, double* f, double* mean, int64_t n, double tau2,

@@ -49,10 +49,11 @@ struct HmatDesc {
 
 struct FactDesc {
   int64_t n;
-  int L, nleaf, Bm, cap, prec;  // prec: 0 = f64 storage, 1 = f32 storage
+  int L, nleaf, Bm, cap, prec;  // prec: 0 = f64 storage, 1 = f32 storage (a rounded copy of an FP64
+                                // factor, applied in FP32 arithmetic; Zf, Zi and the rest shared with it)
   const int* bnd;
   void* Lleaf;                  // nleaf x Bm x Bm Cholesky factors L, L^T mirrored into the upper triangle
-  double* Ldinv;                // nleaf x Bm reciprocals of their diagonals
+  void* Ldinv;                  // nleaf x Bm reciprocals of their diagonals (storage precision)
   void* Q;                      // L x cap x n orthonormal bases
   double* Zf;                   // nnodes x (2cap)^2 : L_S - I
   double* Zi;                   // nnodes x (2cap)^2 : L_S^-1 - I
@@ -61,6 +62,8 @@ struct FactDesc {
   double* ld_parts;             // nleaf + nnodes partial log-determinants
   double* logdet;               // [1]
   int* status;                  // [1]
+  const int* skip;              // nullable: while *skip != 0 the factorization kernels leave this
+                                // factor as it is (a factor kept from an earlier iteration)
 };
 
 __host__ __device__ inline int bnd_off(int l) { return (1 << l) - 1 + l; }

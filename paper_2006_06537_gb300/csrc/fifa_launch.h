@@ -34,24 +34,30 @@ int level_bucket_coresident(int prec, int b, int cap);
 cudaError_t launch_logdet_reduce(const FactDesc* Fd, cudaStream_t st, int nprob = 1);
 
 #define SWEEP_RHS_MAX 2
+// active (nullable): when *active == 0 the application / product kernels return at
+// once (iterations of a solve that has converged).
 cudaError_t launch_sweep_level(const FactDesc* Fd, int prec, int lvl, int nodes, int G, double* v, int nrhs, double* part,
-                               int zsel, int ztrans, cudaStream_t st);
+                               int zsel, int ztrans, cudaStream_t st, const int* active = nullptr);
 // Fused sweep (one cooperative launch of 2^ls CTAs; rows >= the longest
 // level-ls node).  part: 2 * 2^ls * FS_PART_STRIDE doubles; bar zeroed before.
 #define FS_PART_STRIDE (2 * FIFA_CAP_MAX * SWEEP_RHS_MAX)
 #define FS_CTAS_MAX 1024
 int sweep_fused_coresident(int prec, int rows, int cap);
+// mode 0: W v, 1: W^-1 v, 2: W^T v, 3: W^-T v, 4: W^-T W^-1 v (both inverse sweeps
+// in one launch).  Arithmetic in the factor's storage precision (prec 1: FP32).
 cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, int cap, double* v, int nrhs,
-                               int mode, double* part, unsigned int* bar, int* abort_flag, cudaStream_t st);
+                               int mode, double* part, unsigned int* bar, int* abort_flag, cudaStream_t st,
+                               const int* active = nullptr);
 // Fused H-matrix product (one cooperative launch of 2^ls CTAs, rows <= 4096).
 // part: 2^ls * ls * MV_PART_STRIDE doubles; bar zeroed before.
 #define MV_FUSED_ROWS_MAX 4096
 int mv_fused_coresident(int rows);
 cudaError_t launch_mv_fused(const HmatDesc* Hd, int ls, int rows, const double* x, int nrhs, double* y, double* part,
-                            unsigned int* bar, int* abort_flag, cudaStream_t st);
-cudaError_t launch_sweep_leaf(const FactDesc* Fd, int prec, int nleaf, double* v, int nrhs, int mode, cudaStream_t st);
+                            unsigned int* bar, int* abort_flag, cudaStream_t st, const int* active = nullptr);
+cudaError_t launch_sweep_leaf(const FactDesc* Fd, int prec, int nleaf, double* v, int nrhs, int mode, cudaStream_t st,
+                              const int* active = nullptr);
 cudaError_t launch_matvec(const HmatDesc* Hd, int nleaf, int L, const double* x, int nrhs, double* part, double* proj,
-                          double* y, cudaStream_t st);
+                          double* y, cudaStream_t st, const int* active = nullptr);
 
 // vector / random / scalar kernels (k_gibbs.cu)
 cudaError_t launch_det_exp(const double* in, double* out, int64_t n, cudaStream_t st);
@@ -59,3 +65,5 @@ cudaError_t launch_normals(uint64_t seed, uint32_t tag, const uint64_t* iter_dev
                            double* out, int64_t n, cudaStream_t st);
 cudaError_t launch_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64_t cnt, cudaStream_t st);
 cudaError_t launch_check_sorted(const double* x, int64_t n, int* flag, cudaStream_t st);
+// FP64 FMA throughput probe: 16 iters flops per thread, 256 threads per block.
+cudaError_t launch_dfma_probe(double* out, int iters, int blocks, cudaStream_t st);

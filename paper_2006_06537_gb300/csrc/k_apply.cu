@@ -14,7 +14,9 @@
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_sweep_proj(const FactDesc* __restrict__ Fd, int lvl, int G,
-                                                    const double* __restrict__ v, int nrhs, double* __restrict__ part) {
+                                                    const double* __restrict__ v, int nrhs, double* __restrict__ part,
+                                                    const int* __restrict__ active) {
+  if (active && *active == 0) return;
   const int bi = blockIdx.x / G, g = blockIdx.x % G;
   const int nid = node_id(lvl, bi);
   const int r = Fd->rank[nid];
@@ -48,7 +50,9 @@ __global__ void __launch_bounds__(256) k_sweep_proj(const FactDesc* __restrict__
 // zsel: 0 -> Zf, 1 -> Zi; ztrans: use the transpose.
 template <typename T>
 __global__ void __launch_bounds__(256) k_sweep_upd(const FactDesc* __restrict__ Fd, int lvl, int G, double* __restrict__ v,
-                                                   int nrhs, const double* __restrict__ part, int zsel, int ztrans) {
+                                                   int nrhs, const double* __restrict__ part, int zsel, int ztrans,
+                                                   const int* __restrict__ active) {
+  if (active && *active == 0) return;
   const int bi = blockIdx.x / G, g = blockIdx.x % G, base = blockIdx.x - g;
   const int nid = node_id(lvl, bi);
   const int r = Fd->rank[nid];
@@ -89,9 +93,9 @@ __global__ void __launch_bounds__(256) k_sweep_upd(const FactDesc* __restrict__ 
   }
 }
 
-template <int N>
-__device__ __forceinline__ double reg_sel(const double (&a)[N], int q) {
-  double r = a[0];
+template <typename T, int N>
+__device__ __forceinline__ T reg_sel(const T (&a)[N], int q) {
+  T r = a[0];
 #pragma unroll
   for (int t = 1; t < N; ++t)
     if (q == t) r = a[t];
@@ -100,28 +104,29 @@ __device__ __forceinline__ double reg_sel(const double (&a)[N], int q) {
 
 // ---------------------------------------------------------------------------
 // Leaf step of one leaf by one warp, on m entries at vj (global or shared
-// memory).  mode 0: v <- L v, 1: v <- L^-1 v, 2: v <- L^T v, 3: v <- L^-T v.
+// memory, element type V), in the factor's precision T (FP64, or FP32 for an
+// FP32 copy of a factor: every product and sum in T).  mode 0: v <- L v, 1: v <- L^-1 v, 2: v <- L^T v, 3: v <- L^-T v.
 // L column-major (L[i][k] at k*Bm + i, i >= k) with L^T mirrored into the
 // upper triangle (L[k][j] at k*Bm + j, j < k): every step reads one contiguous
 // column, L's for modes 0 / 1 and L^T's for modes 2 / 3.
 // ---------------------------------------------------------------------------
-template <typename T, int RPL>  // RPL: rows per lane, 32 RPL >= m; dinv: reciprocal pivots
-__device__ __forceinline__ void leaf_warp_apply_r(const T* __restrict__ Lm, const double* __restrict__ dinv, int Bm,
-                                                  int m, double* vj, int mode, int lane) {
-  double x[RPL], o[RPL];
+template <typename T, typename V, int RPL>  // RPL: rows per lane, 32 RPL >= m; dinv: reciprocal pivots
+__device__ __forceinline__ void leaf_warp_apply_r(const T* __restrict__ Lm, const T* __restrict__ dinv, int Bm,
+                                                  int m, V* vj, int mode, int lane) {
+  T x[RPL], o[RPL];
 #pragma unroll
   for (int q = 0; q < RPL; ++q) {
     int i = lane + 32 * q;
-    x[q] = i < m ? vj[i] : 0.0;
-    o[q] = 0.0;
+    x[q] = i < m ? (T)vj[i] : (T)0;
+    o[q] = (T)0;
   }
   if (mode == 0) {  // o_i = sum_{k<=i} L[i][k] x_k
     for (int k = 0; k < m; ++k) {
-      double xk = __shfl_sync(0xffffffffu, reg_sel<RPL>(x, k >> 5), k & 31);
+      T xk = __shfl_sync(0xffffffffu, reg_sel<T, RPL>(x, k >> 5), k & 31);
 #pragma unroll
       for (int q = 0; q < RPL; ++q) {
         int i = lane + 32 * q;
-        if (i >= k && i < m) o[q] += to_d(Lm[(size_t)k * Bm + i]) * xk;
+        if (i >= k && i < m) o[q] += Lm[(size_t)k * Bm + i] * xk;
       }
     }
   } else if (mode == 1) {  // forward substitution
@@ -129,27 +134,27 @@ __device__ __forceinline__ void leaf_warp_apply_r(const T* __restrict__ Lm, cons
     for (int q = 0; q < RPL; ++q) o[q] = x[q];
     for (int k = 0; k < m; ++k) {
       const int qk = k >> 5;
-      double ok = 0.0;
+      T ok = (T)0;
 #pragma unroll
       for (int q = 0; q < RPL; ++q)
         if (q == qk) ok = o[q];
-      double xk = __shfl_sync(0xffffffffu, ok, k & 31) * dinv[k];
+      T xk = __shfl_sync(0xffffffffu, ok, k & 31) * dinv[k];
 #pragma unroll
       for (int q = 0; q < RPL; ++q) {
         int i = lane + 32 * q;
         if (i == k) o[q] = xk;
-        else if (i > k && i < m) o[q] -= to_d(Lm[(size_t)k * Bm + i]) * xk;
+        else if (i > k && i < m) o[q] -= Lm[(size_t)k * Bm + i] * xk;
       }
     }
   } else if (mode == 2) {  // o_j = sum_{k>=j} L[k][j] x_k, right-looking over k
     // row k of L is column k of the stored upper triangle (L^T mirrored there):
     // coalesced, and no cross-lane sums
     for (int k = 0; k < m; ++k) {
-      const double xk = __shfl_sync(0xffffffffu, reg_sel<RPL>(x, k >> 5), k & 31);
+      const T xk = __shfl_sync(0xffffffffu, reg_sel<T, RPL>(x, k >> 5), k & 31);
 #pragma unroll
       for (int q = 0; q < RPL; ++q) {
         const int j = lane + 32 * q;
-        if (j <= k) o[q] += to_d(Lm[(size_t)k * Bm + j]) * xk;
+        if (j <= k) o[q] += Lm[(size_t)k * Bm + j] * xk;
       }
     }
   } else {  // backward substitution L^T x = v, column-oriented (x_k, then o_j -= L[k][j] x_k for j < k)
@@ -157,37 +162,39 @@ __device__ __forceinline__ void leaf_warp_apply_r(const T* __restrict__ Lm, cons
     for (int q = 0; q < RPL; ++q) o[q] = x[q];
     for (int k = m - 1; k >= 0; --k) {
       const int qk = k >> 5;
-      double ok = 0.0;
+      T ok = (T)0;
 #pragma unroll
       for (int q = 0; q < RPL; ++q)
         if (q == qk) ok = o[q];
-      const double xk = __shfl_sync(0xffffffffu, ok, k & 31) * dinv[k];
+      const T xk = __shfl_sync(0xffffffffu, ok, k & 31) * dinv[k];
 #pragma unroll
       for (int q = 0; q < RPL; ++q) {
         const int j = lane + 32 * q;
         if (j == k) o[q] = xk;
-        else if (j < k) o[q] -= to_d(Lm[(size_t)k * Bm + j]) * xk;
+        else if (j < k) o[q] -= Lm[(size_t)k * Bm + j] * xk;
       }
     }
   }
 #pragma unroll
   for (int q = 0; q < RPL; ++q) {
     int i = lane + 32 * q;
-    if (i < m) vj[i] = o[q];
+    if (i < m) vj[i] = (V)o[q];
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void leaf_warp_apply(const T* __restrict__ Lm, const double* __restrict__ dinv, int Bm, int m,
-                                                double* vj, int mode, int lane) {
-  if (Bm <= 32) leaf_warp_apply_r<T, 1>(Lm, dinv, Bm, m, vj, mode, lane);
-  else if (Bm <= 64) leaf_warp_apply_r<T, 2>(Lm, dinv, Bm, m, vj, mode, lane);
-  else leaf_warp_apply_r<T, FIFA_LEAF_MAX / 32>(Lm, dinv, Bm, m, vj, mode, lane);
+template <typename T, typename V>
+__device__ __forceinline__ void leaf_warp_apply(const T* __restrict__ Lm, const T* __restrict__ dinv, int Bm, int m,
+                                                V* vj, int mode, int lane) {
+  if (Bm <= 32) leaf_warp_apply_r<T, V, 1>(Lm, dinv, Bm, m, vj, mode, lane);
+  else if (Bm <= 64) leaf_warp_apply_r<T, V, 2>(Lm, dinv, Bm, m, vj, mode, lane);
+  else leaf_warp_apply_r<T, V, FIFA_LEAF_MAX / 32>(Lm, dinv, Bm, m, vj, mode, lane);
 }
 
 // Leaf step over all leaves: one warp per leaf.
 template <typename T>
-__global__ void __launch_bounds__(256) k_sweep_leaf(const FactDesc* __restrict__ Fd, double* __restrict__ v, int nrhs, int mode) {
+__global__ void __launch_bounds__(256) k_sweep_leaf(const FactDesc* __restrict__ Fd, double* __restrict__ v, int nrhs,
+                                                    int mode, const int* __restrict__ active) {
+  if (active && *active == 0) return;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int L = Fd->L, Bm = Fd->Bm, nleaf = Fd->nleaf;
@@ -195,8 +202,8 @@ __global__ void __launch_bounds__(256) k_sweep_leaf(const FactDesc* __restrict__
   const int64_t n = Fd->n;
   const int s = Fd->bnd[bnd_off(L) + warp], e = Fd->bnd[bnd_off(L) + warp + 1];
   const T* Lm = (const T*)Fd->Lleaf + (size_t)warp * Bm * Bm;
-  const double* dinv = Fd->Ldinv + (size_t)warp * Bm;
-  for (int j = 0; j < nrhs; ++j) leaf_warp_apply<T>(Lm, dinv, Bm, e - s, v + (size_t)j * n + s, mode, lane);
+  const T* dinv = (const T*)Fd->Ldinv + (size_t)warp * Bm;
+  for (int j = 0; j < nrhs; ++j) leaf_warp_apply<T, double>(Lm, dinv, Bm, e - s, v + (size_t)j * n + s, mode, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -212,27 +219,33 @@ __global__ void __launch_bounds__(256) k_sweep_leaf(const FactDesc* __restrict__
 #define FS_WARPS 8
 #define FS_K (2 * FIFA_CAP_MAX * SW_RHS_MAX)  // stride of one CTA's partial in `part`
 
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Sum over rows [a0, a1) of Bl[col][p] * xs[j][p - S] for K outputs
 // o = (unit, c, j) described by fn(o, &a0, &a1, &col, &j) (col < 0: skip);
-// results to out[o].  Threads take (output, row chunk) pairs; chunk partials
-// are combined in a fixed order.
-template <typename TB, typename F>
-__device__ void tile_dots(int K, const TB* __restrict__ Bl, int64_t n, const double* xs, int rows, int S, F fn,
-                        double* red, double* out) {
+// results to out[o], accumulated in TX.  Threads take (output, row chunk)
+// pairs; chunk partials are combined in a fixed order.
+template <typename TB, typename TX, typename F>
+__device__ void tile_dots(int K, const TB* __restrict__ Bl, int64_t n, const TX* xs, int rows, int S, F fn,
+                          TX* red, TX* out) {
   const int nt = blockDim.x;
   const int nch = K >= nt ? 1 : nt / K;
   for (int o0 = 0; o0 < K; o0 += nt) {
     const int kk = min(nt, K - o0);
     const int ch = nch == 1 ? 0 : threadIdx.x / kk;
     const int o = o0 + (nch == 1 ? threadIdx.x : threadIdx.x % kk);
-    double acc = 0.0;
+    TX acc = (TX)0;
     if ((nch == 1 && threadIdx.x < kk) || (nch > 1 && ch < nch)) {
       int a0, a1, col, j;
       fn(o, a0, a1, col, j);
       if (col >= 0) {
         const TB* b = Bl + (size_t)col * n;
-        const double* xj = xs + (size_t)j * rows - S;
-        for (int p = a0 + ch; p < a1; p += nch) acc += to_d(b[p]) * xj[p];
+        const TX* xj = xs + (size_t)j * rows - S;
+        for (int p = a0 + ch; p < a1; p += nch) acc += (TX)b[p] * xj[p];
       }
     }
     __syncthreads();
@@ -240,7 +253,7 @@ __device__ void tile_dots(int K, const TB* __restrict__ Bl, int64_t n, const dou
       if (ch < nch) red[ch * kk + (threadIdx.x % kk)] = acc;
       __syncthreads();
       if ((int)threadIdx.x < kk) {
-        double v = 0.0;
+        TX v = (TX)0;
         for (int q = 0; q < nch; ++q) v += red[q * kk + threadIdx.x];
         out[o0 + threadIdx.x] = v;
       }
@@ -251,23 +264,24 @@ __device__ void tile_dots(int K, const TB* __restrict__ Bl, int64_t n, const dou
   }
 }
 
-#define FS_BUF 512  // doubles of node projections (and of op(Z) p) per batch
+#define FS_BUF 512  // entries of node projections (and of op(Z) p) per batch
 
-// Shared scratch carved after v.
+// Shared scratch carved after v; T is the arithmetic type of the sweep.
+template <typename T>
 struct FsShared {
-  double* pj;             // FS_BUF: projections p of a batch of nodes
-  double* tv;             // FS_BUF: t = op(Z) p of the batch
-  double* red;            // 256 reduction partials
+  T* pj;                  // FS_BUF: projections p of a batch of nodes
+  T* tv;                  // FS_BUF: t = op(Z) p of the batch
+  T* red;                 // 256 reduction partials
   unsigned short* lmap;   // rows: local leaf of each row
 };
 
 // One level >= ls inside CTA c (rows [S, S + R)): the level's nodes in c's
 // subtree in batches whose projections fit FS_BUF; each batch takes one pass of
-// dot products (output-major, no cross-lane FP64 reductions), t = op(Z) p per
-// node, and the row update v += Q t.
+// dot products (output-major, no cross-lane reductions), t = op(Z) p per
+// node, and the row update v += Q t.  All arithmetic in T.
 template <typename T>
-__device__ void fs_local_level(const FactDesc* __restrict__ Fd, int l, int ls, int c, double* vs, int rows, int S,
-                               int R, int nrhs, int zsel, int zt, FsShared& sh) {
+__device__ void fs_local_level(const FactDesc* __restrict__ Fd, int l, int ls, int c, T* vs, int rows, int S,
+                               int R, int nrhs, int zsel, int zt, FsShared<T>& sh) {
   const int L = Fd->L, cap = Fd->cap, ld2 = 2 * cap;
   const int64_t n = Fd->n;
   const int* bnd = Fd->bnd;
@@ -280,31 +294,31 @@ __device__ void fs_local_level(const FactDesc* __restrict__ Fd, int l, int ls, i
   const int nb = max(1, FS_BUF / per);
   for (int b0 = 0; b0 < nsub; b0 += nb) {
     const int bn = min(nb, nsub - b0);
-    tile_dots(bn * per, Qb, n, vs, rows, S,
-              [&](int o, int& a0, int& a1, int& col, int& j) {
-                const int node = o / per, rem = o % per, side = rem / (rmax * nrhs), aj = rem % (rmax * nrhs);
-                const int a = aj / nrhs;
-                j = aj % nrhs;
-                int s0, h0, e0;
-                node_range(bnd, l, i0 + b0 + node, s0, h0, e0);
-                a0 = side ? h0 : s0;
-                a1 = side ? e0 : h0;
-                col = a < Fd->rank[node_id(l, i0 + b0 + node)] ? a : -1;
-              },
-              sh.red, sh.pj);
+    tile_dots<T, T>(bn * per, Qb, n, vs, rows, S,
+                    [&](int o, int& a0, int& a1, int& col, int& j) {
+                      const int node = o / per, rem = o % per, side = rem / (rmax * nrhs), aj = rem % (rmax * nrhs);
+                      const int a = aj / nrhs;
+                      j = aj % nrhs;
+                      int s0, h0, e0;
+                      node_range(bnd, l, i0 + b0 + node, s0, h0, e0);
+                      a0 = side ? h0 : s0;
+                      a1 = side ? e0 : h0;
+                      col = a < Fd->rank[node_id(l, i0 + b0 + node)] ? a : -1;
+                    },
+                    sh.red, sh.pj);
     for (int k = threadIdx.x; k < bn * per; k += blockDim.x) {
       const int node = k / per, rem = k % per, sa = rem / nrhs, j = rem % nrhs;
       const int side = sa / rmax, a = sa % rmax;
       const int nid = node_id(l, i0 + b0 + node);
       const int r = Fd->rank[nid];
-      double acc = 0.0;
+      T acc = (T)0;
       if (a < r) {
         const double* Z = (zsel ? Fd->Zi : Fd->Zf) + (size_t)nid * ld2 * ld2;
         const int row = side * r + a;
-        const double* pn = sh.pj + node * per;
+        const T* pn = sh.pj + node * per;
         for (int bb = 0; bb < 2 * r; ++bb) {
           const int bs = bb >= r ? 1 : 0, ba = bb - bs * r;
-          acc += (zt ? Z[bb * ld2 + row] : Z[row * ld2 + bb]) * pn[(bs * rmax + ba) * nrhs + j];
+          acc += (T)(zt ? Z[bb * ld2 + row] : Z[row * ld2 + bb]) * pn[(bs * rmax + ba) * nrhs + j];
         }
       }
       sh.tv[k] = acc;
@@ -317,11 +331,11 @@ __device__ void fs_local_level(const FactDesc* __restrict__ Fd, int l, int ls, i
       const int r = Fd->rank[node_id(l, gi)];
       int s0, h0, e0;
       node_range(bnd, l, gi, s0, h0, e0);
-      const double* tn = sh.tv + node * per + (p < h0 ? 0 : rmax) * nrhs;
+      const T* tn = sh.tv + node * per + (p < h0 ? 0 : rmax) * nrhs;
       // the products accumulate onto v itself (no separate add per row)
-      double acc0 = vs[p - S], acc1 = nrhs > 1 ? vs[rows + p - S] : 0.0;
+      T acc0 = vs[p - S], acc1 = nrhs > 1 ? vs[rows + p - S] : (T)0;
       for (int a = 0; a < r; ++a) {
-        const double q = to_d(Qb[(size_t)a * n + p]);
+        const T q = Qb[(size_t)a * n + p];
         acc0 += q * tn[a * nrhs];
         if (nrhs > 1) acc1 += q * tn[a * nrhs + 1];
       }
@@ -333,11 +347,12 @@ __device__ void fs_local_level(const FactDesc* __restrict__ Fd, int l, int ls, i
 }
 
 // One level < ls: node i = c >> (ls - l) spans 2^(ls - l) CTAs; c's rows lie in
-// one child (side).  Returns false if the grid barrier gave up.
+// one child (side).  The CTAs exchange their partial projections in FP64
+// (`part`).  Returns false if the grid barrier gave up.
 template <typename T>
-__device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, int c, double* vs, int rows, int S,
+__device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, int c, T* vs, int rows, int S,
                                 int E, int nrhs, int zsel, int zt, double* __restrict__ part, int buf,
-                                unsigned int* bar, unsigned int& phase, int* abort_flag, FsShared& sh) {
+                                unsigned int* bar, unsigned int& phase, int* abort_flag, FsShared<T>& sh) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int C = gridDim.x;
   const int cap = Fd->cap, ld2 = 2 * cap;
@@ -350,17 +365,17 @@ __device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, 
   // partial projection of this CTA's rows onto its side's r columns
   for (int a = warp; a < r; a += FS_WARPS) {
     const T* Qc = Qb + (size_t)a * n;
-    double acc0 = 0.0, acc1 = 0.0;
+    T acc0 = (T)0, acc1 = (T)0;
     for (int p = S + lane; p < E; p += 32) {
-      const double q = to_d(Qc[p]);
+      const T q = Qc[p];
       acc0 += q * vs[p - S];
       if (nrhs > 1) acc1 += q * vs[rows + p - S];
     }
-    acc0 = warp_sum(acc0);
-    if (nrhs > 1) acc1 = warp_sum(acc1);
+    acc0 = warp_sum_t(acc0);
+    if (nrhs > 1) acc1 = warp_sum_t(acc1);
     if (lane == 0) {
-      __stcg(mine + a * nrhs, acc0);
-      if (nrhs > 1) __stcg(mine + a * nrhs + 1, acc1);
+      __stcg(mine + a * nrhs, (double)acc0);
+      if (nrhs > 1) __stcg(mine + a * nrhs + 1, (double)acc1);
     }
   }
   ++phase;
@@ -370,18 +385,18 @@ __device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, 
   // right half for the right child, summed in a fixed order
   const int K = 2 * r * nrhs, half = 1 << (span - 1), c0 = i << span;
   const int nch = blockDim.x / K;
-  double* red = sh.red;
+  T* red = sh.red;
   if ((int)threadIdx.x < nch * K) {
     const int k = threadIdx.x % K, ch = threadIdx.x / K;
     const int sd = (k / nrhs) >= r ? 1 : 0, kk = k - sd * r * nrhs;
     const double* src = part + ((size_t)buf * C + c0 + sd * half) * FS_K + kk;
     double acc = 0.0;
     for (int q = ch; q < half; q += nch) acc += __ldcg(src + (size_t)q * FS_K);
-    red[ch * K + k] = acc;
+    red[ch * K + k] = (T)acc;
   }
   __syncthreads();
   if ((int)threadIdx.x < K) {
-    double acc = 0.0;
+    T acc = (T)0;
     for (int ch = 0; ch < nch; ++ch) acc += red[ch * K + threadIdx.x];
     sh.pj[threadIdx.x] = acc;
   }
@@ -389,16 +404,16 @@ __device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, 
   if ((int)threadIdx.x < K) {
     const int a = threadIdx.x / nrhs, j = threadIdx.x % nrhs;
     const double* Z = (zsel ? Fd->Zi : Fd->Zf) + (size_t)nid * ld2 * ld2;
-    double acc = 0.0;
-    for (int b = 0; b < 2 * r; ++b) acc += (zt ? Z[b * ld2 + a] : Z[a * ld2 + b]) * sh.pj[b * nrhs + j];
+    T acc = (T)0;
+    for (int b = 0; b < 2 * r; ++b) acc += (T)(zt ? Z[b * ld2 + a] : Z[a * ld2 + b]) * sh.pj[b * nrhs + j];
     sh.tv[threadIdx.x] = acc;
   }
   __syncthreads();
   const int off = side * r;
   for (int p = S + (int)threadIdx.x; p < E; p += blockDim.x) {
-    double acc0 = vs[p - S], acc1 = nrhs > 1 ? vs[rows + p - S] : 0.0;
+    T acc0 = vs[p - S], acc1 = nrhs > 1 ? vs[rows + p - S] : (T)0;
     for (int a = 0; a < r; ++a) {
-      const double q = to_d(Qb[(size_t)a * n + p]);
+      const T q = Qb[(size_t)a * n + p];
       acc0 += q * sh.tv[(off + a) * nrhs];
       if (nrhs > 1) acc1 += q * sh.tv[(off + a) * nrhs + 1];
     }
@@ -410,7 +425,7 @@ __device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, 
 }
 
 template <typename T>
-__device__ void fs_leaves(const FactDesc* __restrict__ Fd, int ls, int c, double* vs, int rows, int S, int nrhs,
+__device__ void fs_leaves(const FactDesc* __restrict__ Fd, int ls, int c, T* vs, int rows, int S, int nrhs,
                           int mode) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int L = Fd->L, Bm = Fd->Bm;
@@ -419,22 +434,29 @@ __device__ void fs_leaves(const FactDesc* __restrict__ Fd, int ls, int c, double
     const int leaf = first + q;
     const int s = Fd->bnd[bnd_off(L) + leaf], e = Fd->bnd[bnd_off(L) + leaf + 1];
     const T* Lm = (const T*)Fd->Lleaf + (size_t)leaf * Bm * Bm;
-    const double* dinv = Fd->Ldinv + (size_t)leaf * Bm;
+    const T* dinv = (const T*)Fd->Ldinv + (size_t)leaf * Bm;
     for (int j = 0; j < nrhs; ++j)
-      leaf_warp_apply<T>(Lm, dinv, Bm, e - s, vs + (size_t)j * rows + (s - S), mode, lane);
+      leaf_warp_apply<T, T>(Lm, dinv, Bm, e - s, vs + (size_t)j * rows + (s - S), mode, lane);
   }
   __syncthreads();
 }
 
-// mode 0: v <- W v, 1: W^-1 v, 2: W^T v, 3: W^-T v.  Dynamic shared memory:
-// nrhs * rows doubles (rows >= the longest level-ls node), then the FsShared
-// arrays.
+// mode 0: v <- W v, 1: W^-1 v, 2: W^T v, 3: W^-T v; mode 4: v <- W^-T W^-1 v
+// (both inverse sweeps, v kept in shared memory in between: a full solve with
+// the factor).  Arithmetic in T: FP64 for an FP64 factor, FP32 for an FP32
+// copy (the global v stays FP64, converted on load and store).  active
+// (nullable): when *active == 0 the launch does nothing (a converged
+// iteration).  Dynamic shared memory: nrhs * rows entries of T (rows >= the
+// longest level-ls node), then the FsShared arrays.
 template <typename T>
 __global__ void __launch_bounds__(256) k_sweep_fused(const FactDesc* __restrict__ Fd, double* __restrict__ v, int nrhs,
                                                      int mode, int ls, int rows, double* __restrict__ part,
-                                                     unsigned int* __restrict__ bar, int* __restrict__ abort_flag) {
-  extern __shared__ double vs[];
-  FsShared sh;
+                                                     unsigned int* __restrict__ bar, int* __restrict__ abort_flag,
+                                                     const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  extern __shared__ __align__(16) unsigned char fs_smem[];
+  T* vs = (T*)fs_smem;
+  FsShared<T> sh;
   sh.pj = vs + (size_t)rows * nrhs;
   sh.tv = sh.pj + FS_BUF;
   sh.red = sh.tv + FS_BUF;
@@ -444,7 +466,7 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const FactDesc* __restrict_
   const int64_t n = Fd->n;
   const int S = Fd->bnd[bnd_off(ls) + c], E = Fd->bnd[bnd_off(ls) + c + 1];
   for (int j = 0; j < nrhs; ++j)
-    for (int p = threadIdx.x; p < E - S; p += blockDim.x) vs[(size_t)j * rows + p] = v[(size_t)j * n + S + p];
+    for (int p = threadIdx.x; p < E - S; p += blockDim.x) vs[(size_t)j * rows + p] = (T)v[(size_t)j * n + S + p];
   {
     const int nl = 1 << (L - ls), first = c << (L - ls);
     for (int q = threadIdx.x; q < nl; q += blockDim.x) {
@@ -453,37 +475,50 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const FactDesc* __restrict_
     }
   }
   __syncthreads();
-  const int zsel = (mode == 1 || mode == 3) ? 1 : 0, zt = (mode == 2 || mode == 3) ? 1 : 0;
   unsigned int phase = 0;
   bool ok = true;
-  if (mode == 1 || mode == 2) {  // leaves first, then the levels upward
-    fs_leaves<T>(Fd, ls, c, vs, rows, S, nrhs, mode);
+  auto up = [&](int md) {  // leaves first, then the levels upward (W^-1, W^T)
+    const int zsel = md == 1 ? 1 : 0, zt = md == 2 ? 1 : 0;
+    fs_leaves<T>(Fd, ls, c, vs, rows, S, nrhs, md);
     for (int l = L - 1; l >= ls; --l) fs_local_level<T>(Fd, l, ls, c, vs, rows, S, E - S, nrhs, zsel, zt, sh);
     for (int l = ls - 1; l >= 0 && ok; --l)
-      ok = fs_global_level<T>(Fd, l, ls, c, vs, rows, S, E, nrhs, zsel, zt, part, l & 1, bar, phase, abort_flag, sh);
-  } else {  // the levels downward, then the leaves
+      ok = fs_global_level<T>(Fd, l, ls, c, vs, rows, S, E, nrhs, zsel, zt, part, phase & 1, bar, phase, abort_flag,
+                              sh);
+  };
+  auto down = [&](int md) {  // the levels downward, then the leaves (W, W^-T)
+    const int zsel = md == 3 ? 1 : 0, zt = md == 3 ? 1 : 0;
     for (int l = 0; l < ls && ok; ++l)
-      ok = fs_global_level<T>(Fd, l, ls, c, vs, rows, S, E, nrhs, zsel, zt, part, l & 1, bar, phase, abort_flag, sh);
+      ok = fs_global_level<T>(Fd, l, ls, c, vs, rows, S, E, nrhs, zsel, zt, part, phase & 1, bar, phase, abort_flag,
+                              sh);
     if (ok) {
       for (int l = ls; l < L; ++l) fs_local_level<T>(Fd, l, ls, c, vs, rows, S, E - S, nrhs, zsel, zt, sh);
-      fs_leaves<T>(Fd, ls, c, vs, rows, S, nrhs, mode);
+      fs_leaves<T>(Fd, ls, c, vs, rows, S, nrhs, md);
     }
+  };
+  if (mode == 1 || mode == 2) {
+    up(mode);
+  } else if (mode == 4) {
+    up(1);
+    if (ok) down(3);
+  } else {
+    down(mode);
   }
   if (!ok) return;  // the status word carries TIMEOUT; v is left as it was
   for (int j = 0; j < nrhs; ++j)
-    for (int p = threadIdx.x; p < E - S; p += blockDim.x) v[(size_t)j * n + S + p] = vs[(size_t)j * rows + p];
+    for (int p = threadIdx.x; p < E - S; p += blockDim.x) v[(size_t)j * n + S + p] = (double)vs[(size_t)j * rows + p];
 }
 
-size_t sweep_fused_smem(int rows, int nrhs, int cap) {
-  (void)cap;
-  return sizeof(double) * ((size_t)rows * nrhs + 2 * FS_BUF + 256) + sizeof(unsigned short) * (size_t)rows;
+size_t sweep_fused_smem(int rows, int nrhs, int prec) {
+  const size_t esz = prec ? sizeof(float) : sizeof(double);
+  return esz * ((size_t)rows * nrhs + 2 * FS_BUF + 256) + sizeof(unsigned short) * (size_t)rows;
 }
 
 int sweep_fused_coresident(int prec, int rows, int cap) {
+  (void)cap;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = sweep_fused_smem(rows, SW_RHS_MAX, cap);
+  const size_t smem = sweep_fused_smem(rows, SW_RHS_MAX, prec);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (smem > (size_t)optin) return 0;
@@ -500,11 +535,13 @@ int sweep_fused_coresident(int prec, int rows, int cap) {
 }
 
 cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, int cap, double* v, int nrhs,
-                               int mode, double* part, unsigned int* bar, int* abort_flag, cudaStream_t st) {
+                               int mode, double* part, unsigned int* bar, int* abort_flag, cudaStream_t st,
+                               const int* active) {
+  (void)cap;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(1u << ls);
   cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = sweep_fused_smem(rows, nrhs, cap);
+  cfg.dynamicSmemBytes = sweep_fused_smem(rows, nrhs, prec);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -513,12 +550,12 @@ cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, i
   cfg.numAttrs = 1;
   if (prec) {
     cudaFuncSetAttribute(k_sweep_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sweep_fused_smem(rows, SW_RHS_MAX, cap));
-    return cudaLaunchKernelEx(&cfg, k_sweep_fused<float>, Fd, v, nrhs, mode, ls, rows, part, bar, abort_flag);
+                         (int)sweep_fused_smem(rows, SW_RHS_MAX, 1));
+    return cudaLaunchKernelEx(&cfg, k_sweep_fused<float>, Fd, v, nrhs, mode, ls, rows, part, bar, abort_flag, active);
   }
   cudaFuncSetAttribute(k_sweep_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sweep_fused_smem(rows, SW_RHS_MAX, cap));
-  return cudaLaunchKernelEx(&cfg, k_sweep_fused<double>, Fd, v, nrhs, mode, ls, rows, part, bar, abort_flag);
+                       (int)sweep_fused_smem(rows, SW_RHS_MAX, 0));
+  return cudaLaunchKernelEx(&cfg, k_sweep_fused<double>, Fd, v, nrhs, mode, ls, rows, part, bar, abort_flag, active);
 }
 
 // ---------------------------------------------------------------------------
@@ -540,7 +577,9 @@ cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, i
 template <int RPT>
 __global__ void __launch_bounds__(256, RPT <= 8 ? 4 : 2) k_mv_fused(const HmatDesc* __restrict__ Hd, const double* __restrict__ x, int nrhs,
                                                   double* __restrict__ y, int ls, int rows, double* __restrict__ part,
-                                                  unsigned int* __restrict__ bar, int* __restrict__ abort_flag) {
+                                                  unsigned int* __restrict__ bar, int* __restrict__ abort_flag,
+                                                  const int* __restrict__ active) {
+  if (active && *active == 0) return;  // a converged iteration: nothing to compute
   extern __shared__ double sm[];
   double* xs = sm;                                   // nrhs x rows
   double* pj = xs + (size_t)rows * nrhs;             // MV_PROJ_BUF node projections
@@ -739,7 +778,8 @@ int mv_fused_coresident(int rows) {
 
 template <int RPT>
 static cudaError_t launch_mv_fused_t(const HmatDesc* Hd, int ls, int rows, const double* x, int nrhs, double* y,
-                                     double* part, unsigned int* bar, int* abort_flag, cudaStream_t st) {
+                                     double* part, unsigned int* bar, int* abort_flag, cudaStream_t st,
+                                     const int* active) {
   const size_t smem = mv_fused_smem(rows);
   cudaFuncSetAttribute(k_mv_fused<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaLaunchConfig_t cfg = {};
@@ -752,17 +792,17 @@ static cudaError_t launch_mv_fused_t(const HmatDesc* Hd, int ls, int rows, const
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_mv_fused<RPT>, Hd, x, nrhs, y, ls, rows, part, bar, abort_flag);
+  return cudaLaunchKernelEx(&cfg, k_mv_fused<RPT>, Hd, x, nrhs, y, ls, rows, part, bar, abort_flag, active);
 }
 
 cudaError_t launch_mv_fused(const HmatDesc* Hd, int ls, int rows, const double* x, int nrhs, double* y, double* part,
-                            unsigned int* bar, int* abort_flag, cudaStream_t st) {
+                            unsigned int* bar, int* abort_flag, cudaStream_t st, const int* active) {
   switch (mv_rpt(rows)) {
-    case 1: return launch_mv_fused_t<1>(Hd, ls, rows, x, nrhs, y, part, bar, abort_flag, st);
-    case 2: return launch_mv_fused_t<2>(Hd, ls, rows, x, nrhs, y, part, bar, abort_flag, st);
-    case 4: return launch_mv_fused_t<4>(Hd, ls, rows, x, nrhs, y, part, bar, abort_flag, st);
-    case 8: return launch_mv_fused_t<8>(Hd, ls, rows, x, nrhs, y, part, bar, abort_flag, st);
-    case 16: return launch_mv_fused_t<16>(Hd, ls, rows, x, nrhs, y, part, bar, abort_flag, st);
+    case 1: return launch_mv_fused_t<1>(Hd, ls, rows, x, nrhs, y, part, bar, abort_flag, st, active);
+    case 2: return launch_mv_fused_t<2>(Hd, ls, rows, x, nrhs, y, part, bar, abort_flag, st, active);
+    case 4: return launch_mv_fused_t<4>(Hd, ls, rows, x, nrhs, y, part, bar, abort_flag, st, active);
+    case 8: return launch_mv_fused_t<8>(Hd, ls, rows, x, nrhs, y, part, bar, abort_flag, st, active);
+    case 16: return launch_mv_fused_t<16>(Hd, ls, rows, x, nrhs, y, part, bar, abort_flag, st, active);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -776,7 +816,8 @@ cudaError_t launch_mv_fused(const HmatDesc* Hd, int ls, int rows, const double* 
 // Pass 3 (one CTA per leaf): y = scale (D x + sum_l basis_l proj_other) + shift x.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_mv_proj(const HmatDesc* __restrict__ Hd, const double* __restrict__ x, int nrhs,
-                                                 double* __restrict__ part) {
+                                                 double* __restrict__ part, const int* __restrict__ active) {
+  if (active && *active == 0) return;
   const int leaf = blockIdx.x;
   const int L = Hd->L, cap = Hd->cap;
   const int64_t n = Hd->n;
@@ -798,7 +839,8 @@ __global__ void __launch_bounds__(256) k_mv_proj(const HmatDesc* __restrict__ Hd
 }
 
 __global__ void __launch_bounds__(256) k_mv_sum(const HmatDesc* __restrict__ Hd, int nrhs, const double* __restrict__ part,
-                                                double* __restrict__ proj) {
+                                                double* __restrict__ proj, const int* __restrict__ active) {
+  if (active && *active == 0) return;
   // blockIdx.x enumerates (level node, side) pairs in heap order: 2 * node + side
   const int L = Hd->L, cap = Hd->cap;
   const int nid = blockIdx.x >> 1, side = blockIdx.x & 1;
@@ -820,7 +862,9 @@ __global__ void __launch_bounds__(256) k_mv_sum(const HmatDesc* __restrict__ Hd,
 }
 
 __global__ void __launch_bounds__(128) k_mv_expand(const HmatDesc* __restrict__ Hd, const double* __restrict__ x, int nrhs,
-                                                   const double* __restrict__ proj, double* __restrict__ y) {
+                                                   const double* __restrict__ proj, double* __restrict__ y,
+                                                   const int* __restrict__ active) {
+  if (active && *active == 0) return;
   const int leaf = blockIdx.x;
   const int L = Hd->L, cap = Hd->cap, Bm = Hd->Bm;
   const int64_t n = Hd->n;
@@ -866,31 +910,32 @@ __global__ void __launch_bounds__(128) k_mv_expand(const HmatDesc* __restrict__ 
 
 // ---------------------------------------------------------------------------
 cudaError_t launch_sweep_level(const FactDesc* Fd, int prec, int lvl, int nodes, int G, double* v, int nrhs, double* part,
-                               int zsel, int ztrans, cudaStream_t st) {
+                               int zsel, int ztrans, cudaStream_t st, const int* active) {
   const int grid = nodes * G;
   if (prec) {
-    k_sweep_proj<float><<<grid, 256, 0, st>>>(Fd, lvl, G, v, nrhs, part);
-    k_sweep_upd<float><<<grid, 256, 0, st>>>(Fd, lvl, G, v, nrhs, part, zsel, ztrans);
+    k_sweep_proj<float><<<grid, 256, 0, st>>>(Fd, lvl, G, v, nrhs, part, active);
+    k_sweep_upd<float><<<grid, 256, 0, st>>>(Fd, lvl, G, v, nrhs, part, zsel, ztrans, active);
   } else {
-    k_sweep_proj<double><<<grid, 256, 0, st>>>(Fd, lvl, G, v, nrhs, part);
-    k_sweep_upd<double><<<grid, 256, 0, st>>>(Fd, lvl, G, v, nrhs, part, zsel, ztrans);
+    k_sweep_proj<double><<<grid, 256, 0, st>>>(Fd, lvl, G, v, nrhs, part, active);
+    k_sweep_upd<double><<<grid, 256, 0, st>>>(Fd, lvl, G, v, nrhs, part, zsel, ztrans, active);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_leaf(const FactDesc* Fd, int prec, int nleaf, double* v, int nrhs, int mode, cudaStream_t st) {
+cudaError_t launch_sweep_leaf(const FactDesc* Fd, int prec, int nleaf, double* v, int nrhs, int mode, cudaStream_t st,
+                              const int* active) {
   const int grid = (nleaf * 32 + 255) / 256;
-  if (prec) k_sweep_leaf<float><<<grid, 256, 0, st>>>(Fd, v, nrhs, mode);
-  else k_sweep_leaf<double><<<grid, 256, 0, st>>>(Fd, v, nrhs, mode);
+  if (prec) k_sweep_leaf<float><<<grid, 256, 0, st>>>(Fd, v, nrhs, mode, active);
+  else k_sweep_leaf<double><<<grid, 256, 0, st>>>(Fd, v, nrhs, mode, active);
   return cudaGetLastError();
 }
 
 cudaError_t launch_matvec(const HmatDesc* Hd, int nleaf, int L, const double* x, int nrhs, double* part, double* proj,
-                          double* y, cudaStream_t st) {
+                          double* y, cudaStream_t st, const int* active) {
   if (L > 0) {
-    k_mv_proj<<<nleaf, 256, 0, st>>>(Hd, x, nrhs, part);
-    k_mv_sum<<<2 * ((1 << L) - 1), 256, 0, st>>>(Hd, nrhs, part, proj);
+    k_mv_proj<<<nleaf, 256, 0, st>>>(Hd, x, nrhs, part, active);
+    k_mv_sum<<<2 * ((1 << L) - 1), 256, 0, st>>>(Hd, nrhs, part, proj, active);
   }
-  k_mv_expand<<<nleaf, 128, 0, st>>>(Hd, x, nrhs, proj, y);
+  k_mv_expand<<<nleaf, 128, 0, st>>>(Hd, x, nrhs, proj, y, active);
   return cudaGetLastError();
 }

@@ -13,12 +13,26 @@
 #include "fifa_common.cuh"
 #include "fifa_rng.cuh"
 
-__global__ void k_chain_make_view(const HmatDesc* __restrict__ Hc, HmatDesc* __restrict__ Mv, const ChainDev* __restrict__ c) {
+// M~ = s C~ + I with s = tau2 / sigma2, and whether its factor is refreshed
+// this iteration (always for an FP64 chain; see CHAIN_REFRESH_* for mixed).
+__global__ void k_chain_make_view(const HmatDesc* __restrict__ Hc, HmatDesc* __restrict__ Mv, ChainDev* __restrict__ c) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     HmatDesc d = *Hc;
-    d.scale = c->tau2 / c->sigma2;
+    const double sv = c->tau2 / c->sigma2;
+    d.scale = sv;
     d.shift = 1.0;
     *Mv = d;
+    int refresh = 1;
+    if (c->mixed)
+      refresh = c->force_refresh || !(c->s_ref > 0.0) || !(fabs(sv / c->s_ref - 1.0) <= CHAIN_REFRESH_REL) ||
+                c->pcg_iters > CHAIN_REFRESH_ITERS;
+    if (refresh) {
+      c->s_ref = sv;
+      c->force_refresh = 0;
+      c->n_refresh += 1;
+    }
+    c->fm_skip = refresh ? 0 : 1;
+    c->refreshed = refresh;
   }
 }
 
@@ -76,6 +90,7 @@ __global__ void k_chain_mh(ChainDev* __restrict__ c, HmatDesc* __restrict__ Hc, 
   c->n_accept += (uint64_t)acc;
   c->log_alpha = la;
   if (acc) {
+    if (c->eta_prop != c->eta) c->force_refresh = 1;  // C~ changed: the kept M~ factor no longer fits
     swap_desc(Hc, Hp);
     swap_desc(Fc, Fp);
     c->eta = c->eta_prop;
@@ -94,15 +109,14 @@ __global__ void k_chain_mh(ChainDev* __restrict__ c, HmatDesc* __restrict__ Hc, 
     row[8] = c->rss;
     row[9] = c->refine_res;
     row[10] = (double)c->status;
+    row[11] = (double)c->refreshed;
+    row[12] = (double)c->pcg_iters;
   }
   c->iter += 1;
 }
 
-__global__ void k_ratio_sqrt(const double* __restrict__ num, const double* __restrict__ den, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *out = (*den > 0.0) ? sqrt(*num / *den) : 0.0;
-}
 
-cudaError_t launch_chain_make_view(const HmatDesc* Hc, HmatDesc* Mv, const ChainDev* c, cudaStream_t st) {
+cudaError_t launch_chain_make_view(const HmatDesc* Hc, HmatDesc* Mv, ChainDev* c, cudaStream_t st) {
   k_chain_make_view<<<1, 32, 0, st>>>(Hc, Mv, c);
   return cudaGetLastError();
 }
@@ -121,10 +135,6 @@ cudaError_t launch_chain_propose(ChainDev* c, HmatDesc* Hp, cudaStream_t st) {
 cudaError_t launch_chain_mh(ChainDev* c, HmatDesc* Hc, HmatDesc* Hp, FactDesc* Fc, FactDesc* Fp, const FactDesc* Fm,
                             cudaStream_t st) {
   k_chain_mh<<<1, 32, 0, st>>>(c, Hc, Hp, Fc, Fp, Fm);
-  return cudaGetLastError();
-}
-cudaError_t launch_ratio_sqrt(const double* num, const double* den, double* out, cudaStream_t st) {
-  k_ratio_sqrt<<<1, 32, 0, st>>>(num, den, out);
   return cudaGetLastError();
 }
 

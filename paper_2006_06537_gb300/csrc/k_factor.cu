@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(256, 7) k_leaf_factor(const HmatDesc* __restri
   extern __shared__ double sm[];
   Hd += blockIdx.y;  // problem of a batched launch (descriptor arrays)
   Fd += blockIdx.y;
+  if (Fd->skip && *Fd->skip) return;  // this factor is kept as it is
   const int leaf = blockIdx.x;
   const int L = Fd->L, Bm = Fd->Bm, cap = Fd->cap;
   const int64_t n = Fd->n;
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(256, 7) k_leaf_factor(const HmatDesc* __restri
     Fd->ld_parts[leaf] = lsum;
     if (flag[0]) atomicOr(Fd->status, FIFA_DEV_NOT_SPD);
   }
-  for (int k = threadIdx.x; k < m; k += blockDim.x) Fd->Ldinv[(size_t)leaf * Bm + k] = rinv[k];
+  for (int k = threadIdx.x; k < m; k += blockDim.x) ((double*)Fd->Ldinv)[(size_t)leaf * Bm + k] = rinv[k];
   T* Lout = (T*)Fd->Lleaf + (size_t)leaf * Bm * Bm;
   for (int t = threadIdx.x; t < Bm * Bm; t += blockDim.x) {
     int i = t % Bm, j = t / Bm;
@@ -494,6 +495,7 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
   extern __shared__ double sm[];
   // problem of a batched launch: its descriptor, and its scratch sstride bytes on
   Fd += blockIdx.y;
+  if (Fd->skip && *Fd->skip) return;  // the same for every CTA: no group waits on a missing one
   gpart = (double*)((char*)gpart + blockIdx.y * sstride);
   bar = (unsigned int*)((char*)bar + blockIdx.y * sstride);
   abort_flag = (int*)((char*)abort_flag + blockIdx.y * sstride);
@@ -730,6 +732,7 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
 template <typename T, int R, int RLO, int MS, int W>
 __global__ void __launch_bounds__(128) k_level_small(const FactDesc* __restrict__ Fd, int lvl) {
   Fd += blockIdx.y;  // problem of a batched launch
+  if (Fd->skip && *Fd->skip) return;
   constexpr int R2 = 2 * R;
   __shared__ double Xs[2][R][MS];   // side-major basis rows (FP64 during the QR)
   __shared__ T Bs[W][2 * MS];       // ancestor-column chunk on the node's rows
@@ -939,6 +942,7 @@ struct LmLayout {
 template <typename T, int R, int MS, int NPC>
 __global__ void __launch_bounds__(256) k_level_multi(const FactDesc* __restrict__ Fd, int lvl, int nodes) {
   Fd += blockIdx.y;  // problem of a batched launch
+  if (Fd->skip && *Fd->skip) return;
   using LY = LmLayout<R, MS, NPC>;
   constexpr int R2 = 2 * R;
   extern __shared__ double smd[];
@@ -1255,6 +1259,7 @@ static cudaError_t launch_level_multi(const FactDesc* Fd, int lvl, int nodes, cu
 
 __global__ void k_logdet_reduce(const FactDesc* __restrict__ Fd) {
   Fd += blockIdx.y;  // problem of a batched launch
+  if (Fd->skip && *Fd->skip) return;
   __shared__ double red[40];
   const int cnt = Fd->nleaf + (1 << Fd->L) - 1;
   double v = 0.0;
@@ -1302,11 +1307,13 @@ static cudaError_t launch_leaf_factor_t(const HmatDesc* Hd, const FactDesc* Fd, 
   return cudaGetLastError();
 }
 
+// Factorizations are computed in FP64 (prec 0); an FP32 factor is only ever a
+// rounded copy of an FP64 one (k_mixed.cu), never factored directly.
 cudaError_t launch_leaf_factor(const HmatDesc* Hd, const FactDesc* Fd, int prec, int nleaf, int Bm, int L, int cap,
                                cudaStream_t st, int nprob) {
-  size_t smem = leaf_factor_smem(Bm, L, cap, prec);
-  return prec ? launch_leaf_factor_t<float>(Hd, Fd, nleaf, smem, st, nprob)
-              : launch_leaf_factor_t<double>(Hd, Fd, nleaf, smem, st, nprob);
+  if (prec != 0) return cudaErrorInvalidValue;
+  size_t smem = leaf_factor_smem(Bm, L, cap, 0);
+  return launch_leaf_factor_t<double>(Hd, Fd, nleaf, smem, st, nprob);
 }
 
 template <typename T, int RB, int RLO>
@@ -1375,10 +1382,9 @@ static cudaError_t launch_level_t(const FactDesc* Fd, int lvl, int nodes, const 
 cudaError_t launch_level(const FactDesc* Fd, int prec, int lvl, int nodes, const int* G, int cap, double* part,
                          unsigned int* bar, int bar_stride, int* abort_flag, int side_max, cudaStream_t st, int nprob,
                          size_t sstride) {
-  return prec ? launch_level_t<float>(Fd, lvl, nodes, G, cap, part, bar, bar_stride, abort_flag, side_max, st, nprob,
-                                      sstride)
-              : launch_level_t<double>(Fd, lvl, nodes, G, cap, part, bar, bar_stride, abort_flag, side_max, st, nprob,
-                                       sstride);
+  if (prec != 0) return cudaErrorInvalidValue;
+  return launch_level_t<double>(Fd, lvl, nodes, G, cap, part, bar, bar_stride, abort_flag, side_max, st, nprob,
+                                sstride);
 }
 
 template <typename T, int RB, int RLO>
@@ -1396,12 +1402,12 @@ int level_bucket_coresident(int prec, int b, int cap) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  (void)prec;  // factorizations run in FP64 only
   int per_sm = 0;
-  if (b == 0) per_sm = prec ? level_bucket_per_sm<float, 4, -1>(cap) : level_bucket_per_sm<double, 4, -1>(cap);
+  if (b == 0) per_sm = level_bucket_per_sm<double, 4, -1>(cap);
   else if (b == 1)  // also launched as <16, -1> at levels with CTA groups
-    per_sm = prec ? std::min(level_bucket_per_sm<float, 16, 4>(cap), level_bucket_per_sm<float, 16, -1>(cap))
-                  : std::min(level_bucket_per_sm<double, 16, 4>(cap), level_bucket_per_sm<double, 16, -1>(cap));
-  else per_sm = prec ? level_bucket_per_sm<float, 0, 16>(cap) : level_bucket_per_sm<double, 0, 16>(cap);
+    per_sm = std::min(level_bucket_per_sm<double, 16, 4>(cap), level_bucket_per_sm<double, 16, -1>(cap));
+  else per_sm = level_bucket_per_sm<double, 0, 16>(cap);
   return sms * per_sm;
 }
 

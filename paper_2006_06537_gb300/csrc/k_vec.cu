@@ -85,10 +85,6 @@ __global__ void k_axpy(double a, const double* __restrict__ x, double* __restric
     y[i] += a * x[i];
 }
 
-__global__ void k_residual(const double* __restrict__ b, double* __restrict__ r, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    r[i] = b[i] - r[i];
-}
 
 // rhs[0:n] = (tau2 / sigma) Ca + tau Wb ; rhs[n:2n] = y / sigma2
 __global__ void k_alg1_rhs(const double* __restrict__ Ca, const double* __restrict__ Wb, const double* __restrict__ y,
@@ -119,10 +115,6 @@ cudaError_t launch_axpy(double a, const double* x, double* y, int64_t n, cudaStr
   k_axpy<<<grid_for(n), 256, 0, st>>>(a, x, y, n);
   return cudaGetLastError();
 }
-cudaError_t launch_residual_axpy(const double* b, double* r, int64_t n, cudaStream_t st) {
-  k_residual<<<grid_for(n), 256, 0, st>>>(b, r, n);
-  return cudaGetLastError();
-}
 cudaError_t launch_alg1_rhs(const double* Ca, const double* Wb, const double* y, double* rhs, int64_t n, double tau2,
                             double sigma2, const double* scal_dev, cudaStream_t st) {
   k_alg1_rhs<<<grid_for(n), 256, 0, st>>>(Ca, Wb, y, rhs, n, tau2, sigma2, scal_dev);
@@ -148,6 +140,7 @@ __global__ void k_prep_hmat(HmatDesc* __restrict__ H, int nnodes) {
 __global__ void k_prep_fact(FactDesc* __restrict__ F, const HmatDesc* __restrict__ H, int nnodes) {
   F += blockIdx.y;  // problem of a batched launch (descriptor arrays)
   H += blockIdx.y;
+  if (F->skip && *F->skip) return;  // the factor is kept: its ranks and status stay
   int* dst = F->rank;
   const int* src = H->rank;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nnodes; i += gridDim.x * blockDim.x) dst[i] = src[i];
@@ -188,97 +181,27 @@ cudaError_t launch_sumsq(const double* a, const double* b, int64_t n, double* pa
   return cudaGetLastError();
 }
 
+
 // ---------------------------------------------------------------------------
-// Preconditioned conjugate gradients for nrhs independent systems, scalars on
-// the device.  State per right-hand side j at st[8 j + k]:
-//   k = 0 rho = r^T z, 1 p^T q, 2 alpha, 3 r^T r, 4 b^T b, 5 new rho, 6 beta.
-// A system whose residual has reached tol^2 b^T b takes alpha = 0 (no-op).
+// FP64 FMA throughput probe (the roofline denominator of the FP64-issue-bound
+// kernels): every thread advances 8 independent chains x <- x a + b of fused
+// multiply-adds in registers, no memory traffic; the grid fills every SM.
 // ---------------------------------------------------------------------------
-#define DOT_BLOCKS 120
-
-__global__ void k_dot_part(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
-                           double* __restrict__ part) {
-  __shared__ double red[40];
-  const int j = blockIdx.y;
-  const double* aj = a + (size_t)j * n;
-  const double* bj = b + (size_t)j * n;
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    acc += aj[i] * bj[i];
-  acc = block_sum(acc, red);
-  if (threadIdx.x == 0) part[j * DOT_BLOCKS + blockIdx.x] = acc;
-}
-
-__global__ void k_dot_final(const double* __restrict__ part, double* __restrict__ st, int slot) {
-  __shared__ double red[40];
-  const int j = blockIdx.x;
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < DOT_BLOCKS; i += blockDim.x) acc += part[j * DOT_BLOCKS + i];
-  acc = block_sum(acc, red);
-  if (threadIdx.x == 0) st[8 * j + slot] = acc;
-}
-
-__global__ void k_pcg_alpha(double* __restrict__ st, int nrhs, double tol2) {
-  const int j = threadIdx.x;
-  if (j >= nrhs) return;
-  double* s = st + 8 * j;
-  const double pq = s[1], rho = s[0];
-  double alpha = 0.0;
-  if (s[3] > tol2 * s[4] && pq > 0.0 && rho > 0.0 && isfinite(rho / pq)) alpha = rho / pq;
-  s[2] = alpha;
-}
-
-__global__ void k_pcg_beta(double* __restrict__ st, int nrhs) {
-  const int j = threadIdx.x;
-  if (j >= nrhs) return;
-  double* s = st + 8 * j;
-  const double beta = (s[2] != 0.0 && s[0] > 0.0 && isfinite(s[5] / s[0])) ? s[5] / s[0] : 0.0;
-  s[6] = beta;
-  if (s[2] != 0.0) s[0] = s[5];
-}
-
-__global__ void k_pcg_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                         const double* __restrict__ q, const double* __restrict__ st, int64_t n, int nrhs) {
-  const int64_t tot = n * nrhs;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
-    const double a = st[8 * (i / n) + 2];
-    if (a != 0.0) {
-      x[i] += a * p[i];
-      r[i] -= a * q[i];
-    }
+__global__ void __launch_bounds__(256) k_dfma_probe(double* __restrict__ out, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = 1e-3 * (threadIdx.x + k);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
   }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  if (s == -1.0) out[0] = s;  // never true (the chains stay near b / (1 - a) > 0); keeps the work
 }
 
-// p <- z + beta p for systems still iterating (alpha != 0)
-__global__ void k_pcg_p(double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ st, int64_t n,
-                        int nrhs) {
-  const int64_t tot = n * nrhs;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
-    const double* s = st + 8 * (i / n);
-    if (s[2] != 0.0) p[i] = z[i] + s[6] * p[i];
-  }
-}
-
-cudaError_t launch_dot(const double* a, const double* b, int64_t n, int nrhs, double* part, double* st, int slot,
-                       cudaStream_t stream) {
-  k_dot_part<<<dim3(DOT_BLOCKS, nrhs), 256, 0, stream>>>(a, b, n, part);
-  k_dot_final<<<nrhs, 128, 0, stream>>>(part, st, slot);
-  return cudaGetLastError();
-}
-cudaError_t launch_pcg_alpha(double* st, int nrhs, double tol2, cudaStream_t stream) {
-  k_pcg_alpha<<<1, 32, 0, stream>>>(st, nrhs, tol2);
-  return cudaGetLastError();
-}
-cudaError_t launch_pcg_beta(double* st, int nrhs, cudaStream_t stream) {
-  k_pcg_beta<<<1, 32, 0, stream>>>(st, nrhs);
-  return cudaGetLastError();
-}
-cudaError_t launch_pcg_xr(double* x, double* r, const double* p, const double* q, const double* st, int64_t n, int nrhs,
-                          cudaStream_t stream) {
-  k_pcg_xr<<<grid_for(n * nrhs), 256, 0, stream>>>(x, r, p, q, st, n, nrhs);
-  return cudaGetLastError();
-}
-cudaError_t launch_pcg_p(double* p, const double* z, const double* st, int64_t n, int nrhs, cudaStream_t stream) {
-  k_pcg_p<<<grid_for(n * nrhs), 256, 0, stream>>>(p, z, st, n, nrhs);
+cudaError_t launch_dfma_probe(double* out, int iters, int blocks, cudaStream_t st) {
+  k_dfma_probe<<<blocks, 256, 0, st>>>(out, iters, 0.999999, 1e-6);
   return cudaGetLastError();
 }

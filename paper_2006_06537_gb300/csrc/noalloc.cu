@@ -15,6 +15,7 @@
 // written by that same call (leaf partial projections, then their per-node
 // sums), so stale contents from a previous call are never used and nothing
 // needs clearing.
+#include <cuda.h>  // types of the two driver entry points looked up at run time (no link to the driver)
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -28,18 +29,47 @@
 
 static __device__ __align__(256) double g_matvec_scratch[FIFA_STATIC_SCRATCH_DOUBLES];
 
-// Device address of g_matvec_scratch per device, looked up once with that
-// device current.  In host code the symbol itself is only a host-side stand-in.
+// Device address of g_matvec_scratch per device, looked up with that device
+// current and kept together with the unique id of the context it belongs to:
+// a device reset (or any re-creation of the context) makes the next call look
+// the address up again instead of using a stale one.  In host code the symbol
+// itself is only a host-side stand-in.
 static double* g_scratch_addr[FIFA_STATIC_MAX_DEVICES];
+static unsigned long long g_scratch_ctx[FIFA_STATIC_MAX_DEVICES];
 static std::mutex g_scratch_mu;
+
+// Unique id of the calling thread's current context, 0 if unknown.
+static unsigned long long current_context_id() {
+  typedef CUresult (*get_current_t)(CUcontext*);
+  typedef CUresult (*get_id_t)(CUcontext, unsigned long long*);
+  static get_current_t get_current = nullptr;
+  static get_id_t get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {  // called with g_scratch_mu held
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, nullptr) == cudaSuccess)
+      get_current = (get_current_t)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, nullptr) == cudaSuccess)
+      get_id = (get_id_t)f;
+    cudaGetLastError();
+    looked_up = true;
+  }
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 static cudaError_t scratch_address(int dev, double** out) {
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  const unsigned long long id = current_context_id();
+  if (!g_scratch_addr[dev] || id == 0 || id != g_scratch_ctx[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_matvec_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_addr[dev] = (double*)p;
+    g_scratch_ctx[dev] = current_context_id();
   }
   *out = g_scratch_addr[dev];
   return cudaSuccess;

@@ -20,8 +20,9 @@ FIFA_OK, FIFA_ERR_INVALID_ARG, FIFA_ERR_UNSORTED, FIFA_ERR_NOT_SPD = 0, 1, 2, 3
 FIFA_ERR_RANK_CAP, FIFA_ERR_OOM, FIFA_ERR_CUDA, FIFA_ERR_TIMEOUT, FIFA_ERR_UNSUPPORTED = 4, 5, 6, 7, 8
 FIFA_KERNEL_SE, FIFA_KERNEL_MATERN52 = 0, 1
 FIFA_FP64, FIFA_MIXED = 0, 1
-FIFA_TRACE_FIELDS = 11
-TRACE_COLUMNS = ["iter", "sigma2", "tau2", "rho", "accept", "log_alpha", "logdet", "q", "rss", "refine_res", "status"]
+FIFA_TRACE_FIELDS = 13
+TRACE_COLUMNS = ["iter", "sigma2", "tau2", "rho", "accept", "log_alpha", "logdet", "q", "rss", "refine_res", "status",
+                 "refactored", "cg_iters"]
 
 
 class fifa_hyper(C.Structure):
@@ -92,6 +93,7 @@ def lib():
         "fifa_logdet": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
         "fifa_solve": (C.c_int, [_P, _P, _P, _P, C.c_int]),
         "fifa_apply_W": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, C.c_int]),
+        "fifa_apply_precond": (C.c_int, [_P, _P, _P, _P, C.c_int]),
         "fifa_matvec": (C.c_int, [_P, _P, _P, _P, C.c_int]),
         "fifa_matvec_static": (C.c_int, [_P, _P, _P, _P, C.c_int]),
         "fifa_sample": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_double, C.c_uint64, C.c_uint64, C.c_uint64,
@@ -100,6 +102,7 @@ def lib():
                                         C.c_uint64, C.c_uint64, C.POINTER(_P)]),
         "fifa_gibbs_step": (C.c_int, [_P, _P, C.c_int, _P]),
         "fifa_chain_get": (C.c_int, [_P, _P, _P, _P, C.POINTER(fifa_hyper)]),
+        "fifa_chain_set_y": (C.c_int, [_P, _P, _P]),
         "fifa_chain_kernel_nodes": (C.c_int, [_P, C.POINTER(C.c_int)]),
         "fifa_chain_bytes": (C.c_int, [C.POINTER(fifa_opts), C.c_int64, C.POINTER(C.c_size_t)]),
         "fifa_server_create": (C.c_int, [C.POINTER(fifa_server_opts), C.POINTER(_P)]),
@@ -128,6 +131,7 @@ def lib():
         "fifa_det_exp": (C.c_int, [_P, _P, _P, C.c_int64]),
         "fifa_normals": (C.c_int, [_P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint64, _P, C.c_int64]),
         "fifa_philox": (C.c_int, [_P, C.c_uint64, _P, _P, C.c_int64]),
+        "fifa_probe_fp64_fma": (C.c_int, [_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -200,6 +204,10 @@ def fifa_apply_W(ctx, F, trans: int, inverse: int, x_in, x_out, nrhs: int = 1):
     _check(lib().fifa_apply_W(ctx, F, int(trans), int(inverse), _ptr(x_in), _ptr(x_out), int(nrhs)), "fifa_apply_W", ctx=ctx)
 
 
+def fifa_apply_precond(ctx, F, x_in, x_out, nrhs: int = 1):
+    _check(lib().fifa_apply_precond(ctx, F, _ptr(x_in), _ptr(x_out), int(nrhs)), "fifa_apply_precond", ctx=ctx)
+
+
 def fifa_matvec(ctx, A, x_in, x_out, nrhs: int = 1):
     _check(lib().fifa_matvec(ctx, A, _ptr(x_in), _ptr(x_out), int(nrhs)), "fifa_matvec", ctx=ctx)
 
@@ -230,6 +238,11 @@ def fifa_chain_get(ctx, chain, f=None, mean=None):
     h = fifa_hyper()
     _check(lib().fifa_chain_get(ctx, chain, _ptr(f), _ptr(mean), C.byref(h)), "fifa_chain_get", ctx=ctx)
     return h
+
+
+def fifa_chain_set_y(ctx, chain, y):
+    """y: a torch tensor on the device or in (pinned) host memory; copied on the context's stream."""
+    _check(lib().fifa_chain_set_y(ctx, chain, _ptr(y)), "fifa_chain_set_y", ctx=ctx)
 
 
 def fifa_chain_kernel_nodes(chain):
@@ -412,6 +425,13 @@ def fifa_normals(ctx, seed, tag, it, stream_id, out, n):
 
 def fifa_philox(ctx, seed, ctr, out, count):
     _check(lib().fifa_philox(ctx, C.c_uint64(seed), _ptr(ctr), _ptr(out), C.c_int64(count)), "fifa_philox", ctx=ctx)
+
+
+def fifa_probe_fp64_fma(ctx, iters: int = 200000):
+    """(TFLOP/s, ms) of the FP64 fused multiply-add probe (synchronizes)."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(lib().fifa_probe_fp64_fma(ctx, int(iters), C.byref(tf), C.byref(ms)), "fifa_probe_fp64_fma", ctx=ctx)
+    return tf.value, ms.value
 
 
 # ---------------------------------------------------------------------------

@@ -31,4 +31,9 @@ def test_reference_arm_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert d["config"]["n"] == 1 << 20 and d["config"]["workload"].startswith("clustered SE n=1048576")
+    # every step is one measured oracle iteration on a bounded sample of the 2^20 workload
+    assert d["config"]["n"] == bench.REF_SAMPLE_N and d["config"]["workload_n"] == 1 << 20
+    assert d["config"]["workload"].startswith(f"clustered SE n={bench.REF_SAMPLE_N}")
+    ex = d["extrapolated_to_workload_n"]
+    assert ex["n"] == 1 << 20 and 0 < ex["value"] < d["value"] and ex["unit"] == d["unit"]
+    assert cb["cpu"]["cpus"] >= 1

@@ -33,15 +33,15 @@ def _prior():
                          prop_sd=0.2)
 
 
-def _gpu_chain(x, y, nugget, prec=fifa.FIFA_FP64, sigma2=None, tau2=None):
+def _gpu_chain(x, y, nugget, prec=fifa.FIFA_FP64, sigma2=None, tau2=None, refine_max=8, prior=None):
     # a stream of its own, so the iteration runs as a captured graph (the
     # legacy default stream cannot be captured)
-    ctx = fifa.Context(leaf_size=B, aca_tol=EPS, rank_cap=32, prec=prec, refine_max=3, arena_bytes=1 << 30,
-                       stream=torch.cuda.Stream())
+    ctx = fifa.Context(leaf_size=B, aca_tol=EPS, rank_cap=32, prec=prec, refine_max=refine_max, refine_tol=1e-13,
+                       arena_bytes=1 << 30, stream=torch.cuda.Stream())
     vy = float(np.var(y))
     s2 = 0.5 * vy if sigma2 is None else sigma2
     t2 = vy if tau2 is None else tau2
-    p = _prior()
+    p = _prior() if prior is None else prior
     pr = fifa.fifa_prior(p.a_tau2, p.b_tau2, p.a_sigma2, p.b_sigma2, p.logrho_mu, p.logrho_sd, p.prop_sd)
     xd, yd = dev(x, torch), dev(y, torch)
     torch.cuda.synchronize()
@@ -98,11 +98,46 @@ def test_mixed_chain_refines_to_fp64_tolerance():
     mean = torch.empty(N, dtype=torch.float64, device="cuda")
     fifa.fifa_chain_get(ctx.h, ch, None, mean)
     st = _oracle_chain(x, y, 1e-6, iters)
-    assert np.all(tr[:, 9] <= 1e-10), tr[:, 9]  # refined relative residual of the M~ solves
+    assert np.all(tr[:, 9] <= 1e-10), tr[:, 9]  # true relative residual of the M~ solves
+    assert tr[0, 11] == 1.0                     # the first iteration factors M~
+    assert np.all(tr[:, 12] <= 8)
     for t, o in zip(tr, st.trace):
         assert abs(t[1] - o["sigma2"]) <= 1e-8 * o["sigma2"]
         assert bool(t[4]) == o["accept"]
+        if o["accept"] and t[0] + 1 < iters:    # a new length-scale: M~ is refactored next
+            assert tr[int(t[0]) + 1, 11] == 1.0
     assert rel(host(mean), st.mean) <= 1e-8
+
+
+def test_mixed_chain_reuses_its_factor_and_tracks_the_fp64_chain():
+    # fixed length-scale (a zero-step proposal is accepted without changing C~)
+    # and variances started near the posterior: s = tau2 / sigma2 moves by well
+    # under 5% per iteration, so the kept FP64 factor of M~ preconditions the
+    # later iterations' solves; the chain must still follow the FP64 chain
+    x, y = uniform_sine(N, 0)
+    iters = 8
+    p = _prior()
+    p.prop_sd = 0.0
+    cm, chm = _gpu_chain(x, y, 1e-6, prec=fifa.FIFA_MIXED, sigma2=0.01, tau2=0.5, prior=p)
+    c6, ch6 = _gpu_chain(x, y, 1e-6, sigma2=0.01, tau2=0.5, prior=p)
+    tm = np.zeros((iters, fifa.FIFA_TRACE_FIELDS))
+    t6 = np.zeros((iters, fifa.FIFA_TRACE_FIELDS))
+    fifa.fifa_gibbs_step(cm.h, chm, iters, tm)
+    fifa.fifa_gibbs_step(c6.h, ch6, iters, t6)
+    assert tm[0, 11] == 1.0 and np.any(tm[1:, 11] == 0.0), tm[:, 11]
+    assert np.all(t6[:, 11] == 1.0) and np.all(t6[:, 12] == 0.0)  # FP64: refactored every iteration
+    kept = tm[:, 11] == 0.0
+    assert np.all(tm[kept, 12] >= 1) and np.all(tm[:, 12] <= 8)
+    assert np.all(tm[:, 9] <= 1e-10), tm[:, 9]
+    for a, b in zip(tm, t6):
+        assert abs(a[1] - b[1]) <= 1e-9 * b[1] and abs(a[2] - b[2]) <= 1e-9 * b[2]
+        assert abs(a[8] - b[8]) <= 1e-9 * b[8]
+    f_m, f_6 = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(2))
+    m_m, m_6 = torch.empty_like(f_m), torch.empty_like(f_m)
+    fifa.fifa_chain_get(cm.h, chm, f_m, m_m)
+    fifa.fifa_chain_get(c6.h, ch6, f_6, m_6)
+    assert rel(host(f_m), host(f_6)) <= 1e-8
+    assert rel(host(m_m), host(m_6)) <= 1e-9
 
 
 def test_graph_replay_is_deterministic_and_chunking_invariant():

@@ -209,11 +209,28 @@ def test_mixed_precision_solve_refines_to_fp64():
     fifa.fifa_solve(ctx.h, F, vd, out, 2)
     torch.cuda.synchronize()
     ref = factor.solve(Fo, v.T).T
-    assert rel(host(out), ref) <= 1e-8
-    # the FP32 factor's log-determinant is FP32-accurate only; the sampler never
-    # uses it (the Metropolis step takes log det C~ from the FP64 factor)
+    assert rel(host(out), ref) <= 1e-10
+    # a mixed factor is an FP64 factor with an FP32 copy: its log-determinant is FP64
     ld, code = fifa.fifa_logdet(ctx.h, F)
-    assert abs(ld - Fo.logdet) <= 1e-4 * abs(Fo.logdet)
+    assert abs(ld - Fo.logdet) <= 1e-10 * abs(Fo.logdet)
+
+
+def test_fp32_preconditioner_solve_within_its_precision():
+    # the mixed factor's FP32 copy, applied in FP32 arithmetic, solves M~ to
+    # about sqrt(kappa) u32 (W's condition number times the FP32 unit roundoff)
+    # -- and no better: it really is FP32 work
+    n, B = 2048, 64
+    s = 250.0
+    ctx, x, y, xd, H, Ho, A, Ao, F, Fo = _factor_setup(n, B, 0, 0.1, 1e-8, 1e-12, s, prec=fifa.FIFA_MIXED)
+    v = np.random.default_rng(5).standard_normal((2, n))
+    vd = dev(v, torch)
+    out = torch.empty_like(vd)
+    fifa.fifa_apply_precond(ctx.h, F, vd, out, 2)
+    torch.cuda.synchronize()
+    ref = factor.solve(Fo, v.T).T
+    kappa = np.linalg.cond(hodlr.dense(Ao))
+    err = rel(host(out), ref)
+    assert 1e-10 < err <= 64 * math.sqrt(kappa) * 2.0 ** -24, (err, kappa)
 
 
 def test_rejects_bad_inputs():
