@@ -75,6 +75,11 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--paths", default="fp64,mixed", help="chain precisions to time (comma list of fp64, mixed)")
     ap.add_argument("--additive-sweeps", type=int, default=10, help="0 = skip the d-block additive leg")
+    ap.add_argument("--arena-gb", type=int, default=40, help="device arena of each chain context (GB)")
+    ap.add_argument("--cap", type=int, default=CAP, help="ACA rank cap (profiling runs: a smaller arena)")
+    ap.add_argument("--refine-tol", type=float, default=1e-10,
+                    help="mixed path: conjugate gradients stop at ||b - M~ x|| <= tol ||b||")
+    ap.add_argument("--no-roofline", action="store_true", help="skip the roofline probe")
     return ap.parse_args()
 
 
@@ -277,10 +282,10 @@ def gpu_arm(args):
     prior_mu = math.log(RHO0)
     vy = float(np.var(y))
 
-    def make(prec, leaf, refine_max=8, arena_gb=40):
+    def make(prec, leaf, refine_max=8, arena_gb=args.arena_gb):
         with torch.cuda.stream(stream):
-            ctx = fifa.Context(leaf_size=leaf, aca_tol=EPS, rank_cap=CAP, prec=prec, refine_max=refine_max,
-                               refine_tol=1e-12, arena_bytes=int(arena_gb) << 30, stream=stream)
+            ctx = fifa.Context(leaf_size=leaf, aca_tol=EPS, rank_cap=args.cap, prec=prec, refine_max=refine_max,
+                               refine_tol=args.refine_tol, arena_bytes=int(arena_gb) << 30, stream=stream)
             xd = torch.tensor(x, device="cuda")
             yd = torch.tensor(y, device="cuda")
             pr = fifa.fifa_prior(1.0, 1.0, 1.0, 1.0, prior_mu, 1.0, 0.2)
@@ -394,12 +399,14 @@ def gpu_arm(args):
         stream.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     close(ctx, ch)
-    with torch.cuda.stream(stream):
-        pctx = fifa.Context(leaf_size=leaf, aca_tol=EPS, rank_cap=CAP, prec=fifa.FIFA_MIXED, refine_max=8,
-                            refine_tol=1e-12, arena_bytes=24 << 30, stream=stream)
-        xd = torch.tensor(x, device="cuda")
-    roof = roofline_probe(pctx, fifa, torch, stream, xd, n, leaf, args.nugget)
-    pctx.close()
+    roof = None
+    if not args.no_roofline:
+        with torch.cuda.stream(stream):
+            pctx = fifa.Context(leaf_size=leaf, aca_tol=EPS, rank_cap=CAP, prec=fifa.FIFA_MIXED, refine_max=8,
+                                refine_tol=1e-12, arena_bytes=min(24, args.arena_gb) << 30, stream=stream)
+            xd = torch.tensor(x, device="cuda")
+        roof = roofline_probe(pctx, fifa, torch, stream, xd, n, leaf, args.nugget)
+        pctx.close()
 
     # serving (continuous batching, p50/p99) and the d-block additive model:
     # measured after the headline, outside its timed region

@@ -120,6 +120,15 @@ fifa_status fifa_assemble(fifa_ctx* ctx, const double* x_dev, int64_t n, const f
  * outlive M.  Errors: INVALID_ARG, OOM. */
 fifa_status fifa_shift_scale(fifa_ctx* ctx, const fifa_hmat* C, double s, fifa_hmat** M);
 
+/* P~ = s C~ + diag(diag_dev) (Appendix "Heteroskedastic noise derivation":
+ * P~ = K~ + D^-1 with K~ = tau2 C~, s = tau2 and diag_dev = 1/d, the inverse
+ * noise precisions), as a view sharing C's storage: leaves s D_i + diag, U
+ * scaled by s, V shared.  diag_dev: n device doubles, read by the kernels that
+ * use the view (the caller keeps them alive and unchanged meanwhile); C must
+ * outlive P.  fifa_factor, fifa_matvec and fifa_solve accept the view.
+ * Errors: INVALID_ARG (C itself a view), OOM. */
+fifa_status fifa_add_diagonal(fifa_ctx* ctx, const fifa_hmat* C, double s, const double* diag_dev, fifa_hmat** P);
+
 /* The same product as fifa_matvec, for callers that cannot allocate device
  * memory themselves: a plug-in whose host framework owns all device memory,
  * a process whose memory is fully reserved by a pooling allocator, or a
@@ -186,6 +195,18 @@ fifa_status fifa_sample(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, 
                         const double* y_dev, double tau2, double sigma2, uint64_t seed,
                         uint64_t stream_id, uint64_t iter, double* f_dev, double* mean_dev);
 
+/* Algorithm 1.h (Appendix "Heteroskedastic noise derivation"): the draw of
+ * f | y for y = f + e, e_i ~ N(0, 1/d_i), f ~ N(0, tau2 C~).  a0, b ~ N(0, I)
+ * from Philox4x32-10 (streams as fifa_sample: tags 0 / 1, iter, stream_id);
+ * a = sqrt(d) a0; Z = tau2 C~ a + tau W_C b; Z* = P~^-1 Z; R = tau2 C~ P~^-1 y;
+ * f = R + D^-1 Z*, with P~ = tau2 C~ + D^-1 (fifa_add_diagonal with diag 1/d).
+ * C: C~; WC: factor of C~; WP: factor of P~ (MIXED: solved by conjugate
+ * gradients as fifa_solve).  d_dev: n precisions > 0.  R_dev (nullable)
+ * receives R, the posterior mean.  Errors: INVALID_ARG. */
+fifa_status fifa_sample_hetero(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, const fifa_fact* WP,
+                               const double* y_dev, double tau2, const double* d_dev, uint64_t seed,
+                               uint64_t stream_id, uint64_t iter, double* f_dev, double* R_dev);
+
 /* A Gibbs chain: copies x, y to the device arena, assembles and factors
  * C~(init->rho); state sigma2 = init->sigma2, tau2 = init->tau2, f = 0.
  * init->nugget and ->kernel fix those settings for the chain.  Errors as
@@ -209,7 +230,8 @@ fifa_status fifa_chain_create(fifa_ctx* ctx, const double* x_dev, const double* 
  * trace_host (nullable): iters rows of FIFA_TRACE_FIELDS doubles (written after
  * the last iteration, synchronizes): iteration, sigma2, tau2, rho, accepted,
  * log alpha, logdet C~(rho), q = f^T C~^-1 f, ||y - f||^2, relative residual of
- * the M~ solves (MIXED; 0 for FP64), status, M~ refactored this iteration (1/0),
+ * the M~ solves (MIXED: the conjugate gradients' recursive residual, the larger
+ * of the two systems; 0 for FP64), status, M~ refactored this iteration (1/0),
  * conjugate-gradient steps of the M~ solves.  Errors: the chain's device status. */
 #define FIFA_TRACE_FIELDS 13
 fifa_status fifa_gibbs_step(fifa_ctx* ctx, fifa_chain* chain, int iters, double* trace_host);

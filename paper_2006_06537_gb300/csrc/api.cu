@@ -621,6 +621,33 @@ extern "C" fifa_status fifa_shift_scale(fifa_ctx* ctx, const fifa_hmat* C, doubl
   return FIFA_OK;
 }
 
+extern "C" fifa_status fifa_add_diagonal(fifa_ctx* ctx, const fifa_hmat* C, double s, const double* diag_dev,
+                                         fifa_hmat** P) {
+  if (!ctx || !C || !P || !diag_dev || !isfinite(s)) return FIFA_ERR_INVALID_ARG;
+  if (C->host.shift != 0.0 || C->host.scale != 1.0 || C->host.diag) return FIFA_ERR_INVALID_ARG;
+  fifa_hmat* H = new (std::nothrow) fifa_hmat();
+  if (!H) return FIFA_ERR_OOM;
+  H->plan = C->plan;
+  H->host = C->host;
+  H->host.scale = s;
+  H->host.shift = 0.0;
+  H->host.diag = diag_dev;
+  H->owns = false;
+  H->base = C;
+  H->dev = (HmatDesc*)ctx->arena.alloc(sizeof(HmatDesc));
+  if (!H->dev) {
+    delete H;
+    return FIFA_ERR_OOM;
+  }
+  fifa_status st = upload_desc(ctx, H);
+  if (st != FIFA_OK) {
+    fifa_destroy_hmat(ctx, H);
+    return st;
+  }
+  *P = H;
+  return FIFA_OK;
+}
+
 extern "C" void fifa_destroy_hmat(fifa_ctx* ctx, fifa_hmat* H) {
   if (!ctx || !H) return;
   cudaStreamSynchronize(ctx->stream);
@@ -753,7 +780,7 @@ fifa_status fact_enqueue_batched(fifa_ctx* ctx, Plan* P, FactDesc* F0, const Hma
 extern "C" fifa_status fifa_factor(fifa_ctx* ctx, const fifa_hmat* A, fifa_fact** out) {
   if (!ctx || !A || !out) return FIFA_ERR_INVALID_ARG;
   *out = nullptr;
-  const int with32 = (ctx->opts.prec == FIFA_MIXED && A->host.shift != 0.0) ? 1 : 0;
+  const int with32 = (ctx->opts.prec == FIFA_MIXED && (A->host.shift != 0.0 || A->host.diag)) ? 1 : 0;
   fifa_fact* F = nullptr;
   fifa_status st = fact_alloc(ctx, A->plan, with32, &F);
   if (st != FIFA_OK) return st;
@@ -899,7 +926,7 @@ extern "C" fifa_status fifa_matvec(fifa_ctx* ctx, const fifa_hmat* A, const doub
 // iterations' launches return at once.  work holds 4 n nrhs doubles (r, z, p,
 // q); b must not alias x for a mixed factor.
 fifa_status solve_enqueue(fifa_ctx* ctx, const fifa_fact* F, const double* b, double* x, int nrhs, double* work,
-                          double* res_dev, int* iters_dev, const fifa_hmat* op) {
+                          double* res_dev, int* iters_dev, const fifa_hmat* op, bool true_res) {
   Plan* P = F->plan;
   const int64_t n = P->n;
   const int64_t nn = n * nrhs;
@@ -936,9 +963,13 @@ fifa_status solve_enqueue(fifa_ctx* ctx, const fifa_fact* F, const double* b, do
     CK(launch_pcg_direction(r, p, z, n, nrhs, st + cur * slot, st + nxt * slot, act + cur, act + nxt, iters, part,
                             tol2, s));
   }
-  if (res_dev || iters_dev) {  // the true relative residual ||b - A x|| / ||b||, in FP64
-    if ((e = matvec_enqueue(ctx, op, x, q, nrhs)) != FIFA_OK) return e;
-    CK(launch_pcg_true_residual(b, q, n, nrhs, part, res_dev, iters, iters_dev, s));
+  if (res_dev || iters_dev) {
+    if (true_res) {  // ||b - A x|| / ||b|| with one more FP64 product
+      if ((e = matvec_enqueue(ctx, op, x, q, nrhs)) != FIFA_OK) return e;
+      CK(launch_pcg_true_residual(b, q, n, nrhs, part, res_dev, iters, iters_dev, s));
+    } else {  // the iteration's own (recursive) residual
+      CK(launch_pcg_recursive_residual(st + (ctx->opts.refine_max & 1) * slot, nrhs, res_dev, iters, iters_dev, s));
+    }
   }
   return FIFA_OK;
 }
@@ -985,7 +1016,7 @@ fifa_status sample_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* W
   CK(launch_alg1_rhs(Ca, b, y, rhs, n, tau2, sigma2, scal_dev, s));
   if (WM->has32) {
     CK(cudaMemcpyAsync(bsave, rhs, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, s));
-    st = solve_enqueue(ctx, WM, bsave, rhs, 2, work, res_dev, iters_dev, op);
+    st = solve_enqueue(ctx, WM, bsave, rhs, 2, work, res_dev, iters_dev, op, false);
   } else {
     st = solve_enqueue(ctx, WM, rhs, rhs, 2, work);
   }
@@ -994,6 +1025,51 @@ fifa_status sample_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* W
   if (st != FIFA_OK) return st;
   CK(launch_alg1_finish(rhs, Cr, f, mean, n, tau2, scal_dev, s));
   return FIFA_OK;
+}
+
+// Algorithm 1.h (Appendix "Heteroskedastic noise derivation"), noise precisions d.
+fifa_status sample_hetero_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, const fifa_fact* WP,
+                                  const double* y, double tau2, const double* d, uint64_t seed, uint64_t sid,
+                                  const uint64_t* iter_dev, uint64_t iter_host, double* f, double* R,
+                                  double* res_dev, int* iters_dev) {
+  Plan* P = C->plan;
+  const int64_t n = P->n;
+  Scratch S = carve(ctx, P);
+  cudaStream_t s = ctx->stream;
+  double* a = S.vec;              // n: a0, then a = sqrt(d) a0
+  double* b = S.vec + n;          // n: b, then W_C b
+  double* Ca = S.vec + 2 * n;     // n
+  double* rhs = S.vec + 3 * n;    // 2n: [Z, y] -> [Z*, P~^-1 y]
+  double* Cr = S.vec + 5 * n;     // n
+  double* bsave = S.vec + 6 * n;  // 2n
+  double* work = S.vec + 8 * n;   // 8n
+  CK(launch_normals(seed, 0, iter_dev, iter_host, sid, a, n, s));
+  CK(launch_normals(seed, 1, iter_dev, iter_host, sid, b, n, s));
+  CK(launch_alg1h_scale(d, a, n, s));
+  fifa_status st = matvec_enqueue(ctx, C, a, Ca, 1);
+  if (st != FIFA_OK) return st;
+  if ((st = sweep_enqueue(ctx, WC, 0, 0, b, 1)) != FIFA_OK) return st;
+  CK(launch_alg1h_rhs(Ca, b, y, rhs, n, tau2, s));
+  if (WP->has32) {
+    CK(cudaMemcpyAsync(bsave, rhs, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, s));
+    st = solve_enqueue(ctx, WP, bsave, rhs, 2, work, res_dev, iters_dev);
+  } else {
+    st = solve_enqueue(ctx, WP, rhs, rhs, 2, work);
+  }
+  if (st != FIFA_OK) return st;
+  if ((st = matvec_enqueue(ctx, C, rhs + n, Cr, 1)) != FIFA_OK) return st;
+  CK(launch_alg1h_finish(rhs, Cr, d, f, R, n, tau2, s));
+  return FIFA_OK;
+}
+
+extern "C" fifa_status fifa_sample_hetero(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, const fifa_fact* WP,
+                                          const double* y_dev, double tau2, const double* d_dev, uint64_t seed,
+                                          uint64_t stream_id, uint64_t iter, double* f_dev, double* R_dev) {
+  if (!ctx || !C || !WC || !WP || !y_dev || !d_dev || !f_dev || !(tau2 > 0.0)) return FIFA_ERR_INVALID_ARG;
+  if (C->plan != WC->plan || C->plan != WP->plan || C->host.diag || C->host.shift != 0.0) return FIFA_ERR_INVALID_ARG;
+  fifa_status st = ensure_scratch(ctx, C->plan);
+  if (st != FIFA_OK) return st;
+  return sample_hetero_enqueue(ctx, C, WC, WP, y_dev, tau2, d_dev, seed, stream_id, nullptr, iter, f_dev, R_dev);
 }
 
 extern "C" fifa_status fifa_sample(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, const fifa_fact* WM,

@@ -120,10 +120,12 @@ fifa_status matvec_enqueue(fifa_ctx* ctx, const fifa_hmat* A, const double* in, 
                            const int* active = nullptr);
 // x = A^-1 b.  FP64 factor: W^-T W^-1 b.  Mixed factor: conjugate gradients on
 // the FP64 operator op (default F->src) preconditioned by the FP32 copy.
-// res_dev (nullable): the final true relative residual; iters_dev (nullable):
-// conjugate-gradient iterations taken.
+// res_dev (nullable): the final relative residual, the true ||b - A x|| / ||b||
+// (one more FP64 product) if true_res, else the iteration's recursive one;
+// iters_dev (nullable): conjugate-gradient iterations taken.
 fifa_status solve_enqueue(fifa_ctx* ctx, const fifa_fact* F, const double* b, double* x, int nrhs, double* work,
-                          double* res_dev = nullptr, int* iters_dev = nullptr, const fifa_hmat* op = nullptr);
+                          double* res_dev = nullptr, int* iters_dev = nullptr, const fifa_hmat* op = nullptr,
+                          bool true_res = true);
 fifa_status sample_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, const fifa_fact* WM, const double* y,
                            double tau2, double sigma2, uint64_t seed, uint64_t sid, const uint64_t* iter_dev,
                            uint64_t iter_host, double* f, double* mean, const double* scal_dev, double* res_dev = nullptr,
@@ -138,3 +140,12 @@ cudaError_t launch_alg1_rhs(const double* Ca, const double* Wb, const double* y,
                             double sigma2, const double* scal_dev, cudaStream_t st);
 cudaError_t launch_alg1_finish(const double* wr, const double* Cr, double* f, double* mean, int64_t n, double tau2,
                                const double* scal_dev, cudaStream_t st);
+cudaError_t launch_alg1h_scale(const double* d, double* a, int64_t n, cudaStream_t st);
+cudaError_t launch_alg1h_rhs(const double* Ca, const double* Wb, const double* y, double* rhs, int64_t n, double tau2,
+                             cudaStream_t st);
+cudaError_t launch_alg1h_finish(const double* Zs, const double* Cr, const double* d, double* f, double* R, int64_t n,
+                                double tau2, cudaStream_t st);
+fifa_status sample_hetero_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, const fifa_fact* WP,
+                                  const double* y, double tau2, const double* d, uint64_t seed, uint64_t sid,
+                                  const uint64_t* iter_dev, uint64_t iter_host, double* f, double* R,
+                                  double* res_dev = nullptr, int* iters_dev = nullptr);

@@ -45,6 +45,7 @@ struct HmatDesc {
   double eps;
   double scale;   // view: A = scale * C~ + shift * I (U scaled by `scale`)
   double shift;
+  const double* diag;  // nullable: per-row diagonal, A = scale * C~ + diag(diag) (replaces shift)
 };
 
 struct FactDesc {

@@ -32,3 +32,6 @@ cudaError_t launch_pcg_direction(const double* r, double* p, const double* z, in
                                  double* part, double tol2, cudaStream_t st);
 cudaError_t launch_pcg_true_residual(const double* b, const double* q, int64_t n, int nrhs, double* part,
                                      double* res, const int* iters, int* iters_out, cudaStream_t st);
+// res = max_j ||r_j|| / ||b_j|| from the recursive residuals of the final state slot.
+cudaError_t launch_pcg_recursive_residual(const double* st_final, int nrhs, double* res, const int* iters,
+                                          int* iters_out, cudaStream_t st);

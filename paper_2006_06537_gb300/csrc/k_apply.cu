@@ -182,6 +182,74 @@ __device__ __forceinline__ void leaf_warp_apply_r(const T* __restrict__ Lm, cons
   }
 }
 
+// Leaves of at most 32 rows, both right-hand sides at once (v1 nullable).  Lane
+// i holds the entries Lm[k Bm + i] of every column k it needs (L[i][k] below
+// the diagonal, L[k][i] = L^T mirrored above it), loaded in chunks of CH
+// columns before any of them is used, so a chunk's loads are in flight
+// together instead of one dependent load per substitution step.  MODE as
+// leaf_warp_apply_r.
+template <typename T, typename V, int CH, int MODE>
+__device__ __forceinline__ void leaf_warp_apply32_m(const T* __restrict__ Lm, const T* __restrict__ dinv, int Bm, int m,
+                                                    V* v0, V* v1, int lane) {
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr bool subst = MODE == 1 || MODE == 3;
+  const bool in = lane < Bm;
+  const bool two = v1 != nullptr;
+  const T x0 = lane < m ? (T)v0[lane] : (T)0;
+  const T x1 = (two && lane < m) ? (T)v1[lane] : (T)0;
+  const T dl = (subst && in) ? dinv[lane] : (T)1;
+  T o0 = subst ? x0 : (T)0, o1 = subst ? x1 : (T)0;
+  for (int t0 = 0; t0 < m; t0 += CH) {
+    T Lc[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int k = MODE == 3 ? m - 1 - (t0 + u) : t0 + u;
+      Lc[u] = (in && t0 + u < m) ? Lm[(size_t)k * Bm + lane] : (T)0;
+    }
+    const int cnt = min(CH, m - t0);
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      if (u < cnt) {
+        const int k = MODE == 3 ? m - 1 - (t0 + u) : t0 + u;
+        const T a = Lc[u];
+        if (!subst) {  // mode 0: o_i += L[i][k] x_k (i >= k);  mode 2: o_j += L[k][j] x_k (j <= k)
+          const T xk0 = __shfl_sync(FULL, x0, k), xk1 = __shfl_sync(FULL, x1, k);
+          if (MODE == 0 ? (lane >= k && lane < m) : (lane <= k)) {
+            o0 += a * xk0;
+            o1 += a * xk1;
+          }
+        } else {  // mode 1: forward, mode 3: backward substitution with the reciprocal pivots
+          const T dk = __shfl_sync(FULL, dl, k);
+          const T xk0 = __shfl_sync(FULL, o0, k) * dk, xk1 = __shfl_sync(FULL, o1, k) * dk;
+          if (lane == k) {
+            o0 = xk0;
+            o1 = xk1;
+          } else if (MODE == 1 ? (lane > k && lane < m) : (lane < k)) {
+            o0 -= a * xk0;
+            o1 -= a * xk1;
+          }
+        }
+      }
+    }
+  }
+  if (lane < m) {
+    v0[lane] = (V)o0;
+    if (two) v1[lane] = (V)o1;
+  }
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ void leaf_warp_apply32(const T* __restrict__ Lm, const T* __restrict__ dinv, int Bm, int m,
+                                                  V* v0, V* v1, int mode, int lane) {
+  constexpr int CH = sizeof(T) == 4 ? 16 : 8;  // register budget of the fused sweep (64 per thread)
+  switch (mode) {
+    case 0: leaf_warp_apply32_m<T, V, CH, 0>(Lm, dinv, Bm, m, v0, v1, lane); break;
+    case 1: leaf_warp_apply32_m<T, V, CH, 1>(Lm, dinv, Bm, m, v0, v1, lane); break;
+    case 2: leaf_warp_apply32_m<T, V, CH, 2>(Lm, dinv, Bm, m, v0, v1, lane); break;
+    default: leaf_warp_apply32_m<T, V, CH, 3>(Lm, dinv, Bm, m, v0, v1, lane); break;
+  }
+}
+
 template <typename T, typename V>
 __device__ __forceinline__ void leaf_warp_apply(const T* __restrict__ Lm, const T* __restrict__ dinv, int Bm, int m,
                                                 V* vj, int mode, int lane) {
@@ -203,6 +271,11 @@ __global__ void __launch_bounds__(256) k_sweep_leaf(const FactDesc* __restrict__
   const int s = Fd->bnd[bnd_off(L) + warp], e = Fd->bnd[bnd_off(L) + warp + 1];
   const T* Lm = (const T*)Fd->Lleaf + (size_t)warp * Bm * Bm;
   const T* dinv = (const T*)Fd->Ldinv + (size_t)warp * Bm;
+  if (Bm <= 32) {
+    leaf_warp_apply32<T, double>(Lm, dinv, Bm, e - s, v + s, nrhs > 1 ? v + n + s : nullptr,
+                                                           mode, lane);
+    return;
+  }
   for (int j = 0; j < nrhs; ++j) leaf_warp_apply<T, double>(Lm, dinv, Bm, e - s, v + (size_t)j * n + s, mode, lane);
 }
 
@@ -245,6 +318,7 @@ __device__ void tile_dots(int K, const TB* __restrict__ Bl, int64_t n, const TX*
       if (col >= 0) {
         const TB* b = Bl + (size_t)col * n;
         const TX* xj = xs + (size_t)j * rows - S;
+#pragma unroll 8
         for (int p = a0 + ch; p < a1; p += nch) acc += (TX)b[p] * xj[p];
       }
     }
@@ -275,13 +349,39 @@ struct FsShared {
   unsigned short* lmap;   // rows: local leaf of each row
 };
 
+// basis columns whose loads a thread issues together (fewer FP64 ones: the
+// register budget of the fused sweep is 64 per thread)
+#define FS_RG_OF(T) (sizeof(T) == 4 ? 4 : 2)
+
+// v_p += sum_{a < r} Q[a][p] t[a] for one row p (two right-hand sides in acc0,
+// acc1; t interleaved by right-hand side), FS_RG_OF(T) loads in flight at a time.
+template <typename T, int NR>
+__device__ __forceinline__ void fs_row_update(const T* __restrict__ Qb, int64_t n, int p, int r, const T* tn, T& acc0,
+                                              T& acc1) {
+  constexpr int nrhs = NR;
+  constexpr int RG = FS_RG_OF(T);
+  for (int a0 = 0; a0 < r; a0 += RG) {
+    T q[RG];
+#pragma unroll
+    for (int u = 0; u < RG; ++u) q[u] = a0 + u < r ? Qb[(size_t)(a0 + u) * n + p] : (T)0;
+#pragma unroll
+    for (int u = 0; u < RG; ++u) {
+      if (a0 + u < r) {
+        acc0 += q[u] * tn[(a0 + u) * nrhs];
+        if (nrhs > 1) acc1 += q[u] * tn[(a0 + u) * nrhs + 1];
+      }
+    }
+  }
+}
+
 // One level >= ls inside CTA c (rows [S, S + R)): the level's nodes in c's
 // subtree in batches whose projections fit FS_BUF; each batch takes one pass of
 // dot products (output-major, no cross-lane reductions), t = op(Z) p per
 // node, and the row update v += Q t.  All arithmetic in T.
-template <typename T>
+template <typename T, int NR>
 __device__ void fs_local_level(const FactDesc* __restrict__ Fd, int l, int ls, int c, T* vs, int rows, int S,
-                               int R, int nrhs, int zsel, int zt, FsShared<T>& sh) {
+                               int R, int zsel, int zt, FsShared<T>& sh) {
+  constexpr int nrhs = NR;
   const int L = Fd->L, cap = Fd->cap, ld2 = 2 * cap;
   const int64_t n = Fd->n;
   const int* bnd = Fd->bnd;
@@ -334,11 +434,7 @@ __device__ void fs_local_level(const FactDesc* __restrict__ Fd, int l, int ls, i
       const T* tn = sh.tv + node * per + (p < h0 ? 0 : rmax) * nrhs;
       // the products accumulate onto v itself (no separate add per row)
       T acc0 = vs[p - S], acc1 = nrhs > 1 ? vs[rows + p - S] : (T)0;
-      for (int a = 0; a < r; ++a) {
-        const T q = Qb[(size_t)a * n + p];
-        acc0 += q * tn[a * nrhs];
-        if (nrhs > 1) acc1 += q * tn[a * nrhs + 1];
-      }
+      fs_row_update<T, NR>(Qb, n, p, r, tn, acc0, acc1);
       vs[p - S] = acc0;
       if (nrhs > 1) vs[rows + p - S] = acc1;
     }
@@ -349,10 +445,12 @@ __device__ void fs_local_level(const FactDesc* __restrict__ Fd, int l, int ls, i
 // One level < ls: node i = c >> (ls - l) spans 2^(ls - l) CTAs; c's rows lie in
 // one child (side).  The CTAs exchange their partial projections in FP64
 // (`part`).  Returns false if the grid barrier gave up.
-template <typename T>
+template <typename T, int NR>
 __device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, int c, T* vs, int rows, int S,
-                                int E, int nrhs, int zsel, int zt, double* __restrict__ part, int buf,
+                                int E, int zsel, int zt, double* __restrict__ part, int buf,
                                 unsigned int* bar, unsigned int& phase, int* abort_flag, FsShared<T>& sh) {
+  constexpr int nrhs = NR;
+  constexpr int RG = FS_RG_OF(T);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int C = gridDim.x;
   const int cap = Fd->cap, ld2 = 2 * cap;
@@ -362,22 +460,52 @@ __device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, 
   const int r = Fd->rank[nid];
   const T* Qb = (const T*)Fd->Q + (size_t)l * cap * n;
   double* mine = part + ((size_t)buf * C + c) * FS_K;
-  // partial projection of this CTA's rows onto its side's r columns
-  for (int a = warp; a < r; a += FS_WARPS) {
-    const T* Qc = Qb + (size_t)a * n;
-    T acc0 = (T)0, acc1 = (T)0;
-    for (int p = S + lane; p < E; p += 32) {
-      const T q = Qc[p];
-      acc0 += q * vs[p - S];
-      if (nrhs > 1) acc1 += q * vs[rows + p - S];
+  // partial projection of this CTA's rows onto its side's r columns: every
+  // thread takes rows p = S + tid + 256 i and RG columns at a time (their
+  // loads issued together), then a fixed-order block reduction
+  for (int a0 = 0; a0 < r; a0 += RG) {
+    T acc0[RG], acc1[RG];
+#pragma unroll
+    for (int u = 0; u < RG; ++u) acc0[u] = acc1[u] = (T)0;
+#pragma unroll 2
+    for (int p = S + (int)threadIdx.x; p < E; p += blockDim.x) {
+      const T v0 = vs[p - S], v1 = nrhs > 1 ? vs[rows + p - S] : (T)0;
+      T q[RG];
+#pragma unroll
+      for (int u = 0; u < RG; ++u) q[u] = a0 + u < r ? Qb[(size_t)(a0 + u) * n + p] : (T)0;
+#pragma unroll
+      for (int u = 0; u < RG; ++u) {
+        if (a0 + u < r) {  // uniform over the CTA: no arithmetic on the columns past the rank
+          acc0[u] += q[u] * v0;
+          if (nrhs > 1) acc1[u] += q[u] * v1;
+        }
+      }
     }
-    acc0 = warp_sum_t(acc0);
-    if (nrhs > 1) acc1 = warp_sum_t(acc1);
-    if (lane == 0) {
-      __stcg(mine + a * nrhs, (double)acc0);
-      if (nrhs > 1) __stcg(mine + a * nrhs + 1, (double)acc1);
+#pragma unroll
+    for (int u = 0; u < RG; ++u) {
+      if (a0 + u < r) {  // uniform: no reduction for the columns past the rank
+        acc0[u] = warp_sum_t(acc0[u]);
+        if (nrhs > 1) acc1[u] = warp_sum_t(acc1[u]);
+      }
     }
+    if (lane == 0)
+#pragma unroll
+      for (int u = 0; u < RG; ++u) {
+        sh.red[(warp * RG + u) * 2] = acc0[u];
+        sh.red[(warp * RG + u) * 2 + 1] = acc1[u];
+      }
+    __syncthreads();
+    if ((int)threadIdx.x < RG * nrhs) {
+      const int u = threadIdx.x / nrhs, j = threadIdx.x % nrhs;
+      if (a0 + u < r) {
+        T t = (T)0;
+        for (int w = 0; w < FS_WARPS; ++w) t += sh.red[(w * RG + u) * 2 + j];
+        __stcg(mine + (a0 + u) * nrhs + j, (double)t);
+      }
+    }
+    __syncthreads();
   }
+  (void)lane;
   ++phase;
   if (!group_barrier(bar, (unsigned)C * phase, Fd->status, abort_flag)) return false;
   if (r == 0) return true;
@@ -410,13 +538,10 @@ __device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, 
   }
   __syncthreads();
   const int off = side * r;
+#pragma unroll 2
   for (int p = S + (int)threadIdx.x; p < E; p += blockDim.x) {
     T acc0 = vs[p - S], acc1 = nrhs > 1 ? vs[rows + p - S] : (T)0;
-    for (int a = 0; a < r; ++a) {
-      const T q = Qb[(size_t)a * n + p];
-      acc0 += q * sh.tv[(off + a) * nrhs];
-      if (nrhs > 1) acc1 += q * sh.tv[(off + a) * nrhs + 1];
-    }
+    fs_row_update<T, NR>(Qb, n, p, r, sh.tv + off * nrhs, acc0, acc1);
     vs[p - S] = acc0;
     if (nrhs > 1) vs[rows + p - S] = acc1;
   }
@@ -424,9 +549,9 @@ __device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, 
   return true;
 }
 
-template <typename T>
-__device__ void fs_leaves(const FactDesc* __restrict__ Fd, int ls, int c, T* vs, int rows, int S, int nrhs,
-                          int mode) {
+template <typename T, int NR>
+__device__ void fs_leaves(const FactDesc* __restrict__ Fd, int ls, int c, T* vs, int rows, int S, int mode) {
+  constexpr int nrhs = NR;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int L = Fd->L, Bm = Fd->Bm;
   const int nl = 1 << (L - ls), first = c << (L - ls);
@@ -435,6 +560,11 @@ __device__ void fs_leaves(const FactDesc* __restrict__ Fd, int ls, int c, T* vs,
     const int s = Fd->bnd[bnd_off(L) + leaf], e = Fd->bnd[bnd_off(L) + leaf + 1];
     const T* Lm = (const T*)Fd->Lleaf + (size_t)leaf * Bm * Bm;
     const T* dinv = (const T*)Fd->Ldinv + (size_t)leaf * Bm;
+    if (Bm <= 32) {
+      leaf_warp_apply32<T, T>(Lm, dinv, Bm, e - s, vs + (s - S),
+                                                        nrhs > 1 ? vs + rows + (s - S) : nullptr, mode, lane);
+      continue;
+    }
     for (int j = 0; j < nrhs; ++j)
       leaf_warp_apply<T, T>(Lm, dinv, Bm, e - s, vs + (size_t)j * rows + (s - S), mode, lane);
   }
@@ -448,11 +578,12 @@ __device__ void fs_leaves(const FactDesc* __restrict__ Fd, int ls, int c, T* vs,
 // (nullable): when *active == 0 the launch does nothing (a converged
 // iteration).  Dynamic shared memory: nrhs * rows entries of T (rows >= the
 // longest level-ls node), then the FsShared arrays.
-template <typename T>
-__global__ void __launch_bounds__(256) k_sweep_fused(const FactDesc* __restrict__ Fd, double* __restrict__ v, int nrhs,
-                                                     int mode, int ls, int rows, double* __restrict__ part,
-                                                     unsigned int* __restrict__ bar, int* __restrict__ abort_flag,
-                                                     const int* __restrict__ active) {
+template <typename T, int NR>
+__global__ void __launch_bounds__(256, 4) k_sweep_fused(const FactDesc* __restrict__ Fd, double* __restrict__ v,
+                                                        int mode, int ls, int rows, double* __restrict__ part,
+                                                        unsigned int* __restrict__ bar, int* __restrict__ abort_flag,
+                                                        const int* __restrict__ active) {
+  constexpr int nrhs = NR;
   if (active && *active == 0) return;
   extern __shared__ __align__(16) unsigned char fs_smem[];
   T* vs = (T*)fs_smem;
@@ -479,20 +610,20 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const FactDesc* __restrict_
   bool ok = true;
   auto up = [&](int md) {  // leaves first, then the levels upward (W^-1, W^T)
     const int zsel = md == 1 ? 1 : 0, zt = md == 2 ? 1 : 0;
-    fs_leaves<T>(Fd, ls, c, vs, rows, S, nrhs, md);
-    for (int l = L - 1; l >= ls; --l) fs_local_level<T>(Fd, l, ls, c, vs, rows, S, E - S, nrhs, zsel, zt, sh);
+    fs_leaves<T, NR>(Fd, ls, c, vs, rows, S, md);
+    for (int l = L - 1; l >= ls; --l) fs_local_level<T, NR>(Fd, l, ls, c, vs, rows, S, E - S, zsel, zt, sh);
     for (int l = ls - 1; l >= 0 && ok; --l)
-      ok = fs_global_level<T>(Fd, l, ls, c, vs, rows, S, E, nrhs, zsel, zt, part, phase & 1, bar, phase, abort_flag,
+      ok = fs_global_level<T, NR>(Fd, l, ls, c, vs, rows, S, E, zsel, zt, part, phase & 1, bar, phase, abort_flag,
                               sh);
   };
   auto down = [&](int md) {  // the levels downward, then the leaves (W, W^-T)
     const int zsel = md == 3 ? 1 : 0, zt = md == 3 ? 1 : 0;
     for (int l = 0; l < ls && ok; ++l)
-      ok = fs_global_level<T>(Fd, l, ls, c, vs, rows, S, E, nrhs, zsel, zt, part, phase & 1, bar, phase, abort_flag,
+      ok = fs_global_level<T, NR>(Fd, l, ls, c, vs, rows, S, E, zsel, zt, part, phase & 1, bar, phase, abort_flag,
                               sh);
     if (ok) {
-      for (int l = ls; l < L; ++l) fs_local_level<T>(Fd, l, ls, c, vs, rows, S, E - S, nrhs, zsel, zt, sh);
-      fs_leaves<T>(Fd, ls, c, vs, rows, S, nrhs, md);
+      for (int l = ls; l < L; ++l) fs_local_level<T, NR>(Fd, l, ls, c, vs, rows, S, E - S, zsel, zt, sh);
+      fs_leaves<T, NR>(Fd, ls, c, vs, rows, S, md);
     }
   };
   if (mode == 1 || mode == 2) {
@@ -513,25 +644,36 @@ size_t sweep_fused_smem(int rows, int nrhs, int prec) {
   return esz * ((size_t)rows * nrhs + 2 * FS_BUF + 256) + sizeof(unsigned short) * (size_t)rows;
 }
 
+template <typename T, int NR>
+static int sweep_fused_per_sm(size_t smem) {
+  int per_sm = 0;
+  cudaFuncSetAttribute(k_sweep_fused<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_fused<T, NR>, 256, smem) != cudaSuccess) per_sm = 0;
+  cudaGetLastError();
+  return per_sm;
+}
+
 int sweep_fused_coresident(int prec, int rows, int cap) {
   (void)cap;
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = sweep_fused_smem(rows, SW_RHS_MAX, prec);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (smem > (size_t)optin) return 0;
-  cudaError_t e;
-  if (prec) {
-    cudaFuncSetAttribute(k_sweep_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_fused<float>, 256, smem);
-  } else {
-    cudaFuncSetAttribute(k_sweep_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_fused<double>, 256, smem);
-  }
-  cudaGetLastError();
-  return e == cudaSuccess ? sms * per_sm : 0;
+  const int per_sm = prec ? std::min(sweep_fused_per_sm<float, 1>(smem), sweep_fused_per_sm<float, 2>(smem))
+                          : std::min(sweep_fused_per_sm<double, 1>(smem), sweep_fused_per_sm<double, 2>(smem));
+  return sms * per_sm;
+}
+
+template <typename T, int NR>
+static cudaError_t launch_sweep_fused_t(cudaLaunchConfig_t& cfg, const FactDesc* Fd, double* v, int mode, int ls,
+                                        int rows, double* part, unsigned int* bar, int* abort_flag,
+                                        const int* active, int prec) {
+  cudaFuncSetAttribute(k_sweep_fused<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sweep_fused_smem(rows, SW_RHS_MAX, prec));
+  return cudaLaunchKernelEx(&cfg, k_sweep_fused<T, NR>, Fd, v, mode, ls, rows, part, bar, abort_flag, active);
 }
 
 cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, int cap, double* v, int nrhs,
@@ -548,14 +690,11 @@ cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, i
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (prec) {
-    cudaFuncSetAttribute(k_sweep_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sweep_fused_smem(rows, SW_RHS_MAX, 1));
-    return cudaLaunchKernelEx(&cfg, k_sweep_fused<float>, Fd, v, nrhs, mode, ls, rows, part, bar, abort_flag, active);
-  }
-  cudaFuncSetAttribute(k_sweep_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sweep_fused_smem(rows, SW_RHS_MAX, 0));
-  return cudaLaunchKernelEx(&cfg, k_sweep_fused<double>, Fd, v, nrhs, mode, ls, rows, part, bar, abort_flag, active);
+  if (prec)
+    return nrhs > 1 ? launch_sweep_fused_t<float, 2>(cfg, Fd, v, mode, ls, rows, part, bar, abort_flag, active, prec)
+                    : launch_sweep_fused_t<float, 1>(cfg, Fd, v, mode, ls, rows, part, bar, abort_flag, active, prec);
+  return nrhs > 1 ? launch_sweep_fused_t<double, 2>(cfg, Fd, v, mode, ls, rows, part, bar, abort_flag, active, prec)
+                  : launch_sweep_fused_t<double, 1>(cfg, Fd, v, mode, ls, rows, part, bar, abort_flag, active, prec);
 }
 
 // ---------------------------------------------------------------------------
@@ -728,13 +867,15 @@ __global__ void __launch_bounds__(256, RPT <= 8 ? 4 : 2) k_mv_fused(const HmatDe
     __syncthreads();
   }
   const double sc = Hd->scale, shf = Hd->shift;
+  const double* dg = Hd->diag;
 #pragma unroll
   for (int i = 0; i < RPT; ++i) {
     const int p = S + tid + i * (int)blockDim.x;
     if (p < E) {
-      const bool plain = shf == 0.0 && sc == 1.0;
-      y[p] = plain ? acc[i][0] : sc * acc[i][0] + shf * xs[p - S];
-      if (nrhs > 1) y[n + p] = plain ? acc[i][1] : sc * acc[i][1] + shf * xs[rows + p - S];
+      const bool plain = !dg && shf == 0.0 && sc == 1.0;
+      const double sh = dg ? dg[p] : shf;
+      y[p] = plain ? acc[i][0] : sc * acc[i][0] + sh * xs[p - S];
+      if (nrhs > 1) y[n + p] = plain ? acc[i][1] : sc * acc[i][1] + sh * xs[rows + p - S];
     }
   }
 }
@@ -903,7 +1044,8 @@ __global__ void __launch_bounds__(128) k_mv_expand(const HmatDesc* __restrict__ 
     }
     for (int j = 0; j < nrhs; ++j) {
       double xv = xs[j * FIFA_LEAF_MAX + i];
-      y[(size_t)j * n + s + i] = (shf == 0.0 && sc == 1.0) ? acc[j] : sc * acc[j] + shf * xv;
+      const double sh = Hd->diag ? Hd->diag[s + i] : shf;
+      y[(size_t)j * n + s + i] = (!Hd->diag && shf == 0.0 && sc == 1.0) ? acc[j] : sc * acc[j] + sh * xv;
     }
   }
 }

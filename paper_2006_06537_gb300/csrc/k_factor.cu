@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256, 7) k_leaf_factor(const HmatDesc* __restri
   for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
     int i = t % m, j = t / m;
     double v = __dmul_rn(sc, D[(size_t)j * Bm + i]);
-    if (i == j) v = __dadd_rn(v, shf);
+    if (i == j) v = __dadd_rn(v, Hd->diag ? Hd->diag[s + i] : shf);
     A[j * ld + i] = v;
   }
   // column list of all ancestor bases restricted to this leaf: the level-l

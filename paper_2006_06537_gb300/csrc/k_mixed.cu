@@ -271,6 +271,21 @@ __global__ void k_pcg_res(const double* __restrict__ part, int nrhs, double* __r
   if (iters_out) *iters_out = *iters;
 }
 
+// The same report from the recursive residual of the final state slot:
+// res = max_j sqrt(r_j^T r_j / b_j^T b_j) (no extra product with A).
+__global__ void k_pcg_res_recursive(const double* __restrict__ st, int nrhs, double* __restrict__ res,
+                                    const int* __restrict__ iters, int* __restrict__ iters_out) {
+  if (threadIdx.x != 0) return;
+  double m = 0.0;
+  for (int j = 0; j < nrhs; ++j) {
+    const double* s = st + j * PCG_SLOT;
+    const double v = s[1] > 0.0 ? sqrt(fmax(s[3], 0.0) / s[1]) : sqrt(fmax(s[3], 0.0));
+    m = fmax(m, v);
+  }
+  if (res) *res = m;
+  if (iters_out) *iters_out = *iters;
+}
+
 cudaError_t launch_pcg_residual0(const double* b, double* r, double* z, int64_t n, int nrhs, double* part,
                                  cudaStream_t st) {
   k_pcg_residual0<<<dim3(PCG_NB, nrhs), 256, 0, st>>>(b, r, z, n, part);
@@ -303,5 +318,10 @@ cudaError_t launch_pcg_true_residual(const double* b, const double* q, int64_t n
                                      double* res, const int* iters, int* iters_out, cudaStream_t st) {
   k_pcg_true<<<dim3(PCG_NB, nrhs), 256, 0, st>>>(b, q, n, part);
   k_pcg_res<<<1, 32, 0, st>>>(part, nrhs, res, iters, iters_out);
+  return cudaGetLastError();
+}
+cudaError_t launch_pcg_recursive_residual(const double* st_final, int nrhs, double* res, const int* iters,
+                                          int* iters_out, cudaStream_t st) {
+  k_pcg_res_recursive<<<1, 32, 0, st>>>(st_final, nrhs, res, iters, iters_out);
   return cudaGetLastError();
 }

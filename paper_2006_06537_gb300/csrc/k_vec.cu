@@ -205,3 +205,43 @@ cudaError_t launch_dfma_probe(double* out, int iters, int blocks, cudaStream_t s
   k_dfma_probe<<<blocks, 256, 0, st>>>(out, iters, 0.999999, 1e-6);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Algorithm 1.h (heteroskedastic noise, precisions d_i): a = sqrt(d) a0;
+// rhs = [tau2 C~ a + tau W_C b, y]; after the solves with P~ = tau2 C~ + D^-1:
+// R = tau2 C~ P~^-1 y and f = R + D^-1 P~^-1 Z.
+// ---------------------------------------------------------------------------
+__global__ void k_alg1h_scale(const double* __restrict__ d, double* __restrict__ a, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] *= sqrt(d[i]);
+}
+__global__ void k_alg1h_rhs(const double* __restrict__ Ca, const double* __restrict__ Wb, const double* __restrict__ y,
+                            double* __restrict__ rhs, int64_t n, double tau2) {
+  const double tau = sqrt(tau2);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    rhs[i] = tau2 * Ca[i] + tau * Wb[i];
+    rhs[n + i] = y[i];
+  }
+}
+__global__ void k_alg1h_finish(const double* __restrict__ Zs, const double* __restrict__ Cr, const double* __restrict__ d,
+                               double* __restrict__ f, double* __restrict__ R, int64_t n, double tau2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double r = tau2 * Cr[i];
+    f[i] = r + Zs[i] / d[i];
+    if (R) R[i] = r;
+  }
+}
+cudaError_t launch_alg1h_scale(const double* d, double* a, int64_t n, cudaStream_t st) {
+  k_alg1h_scale<<<grid_for(n), 256, 0, st>>>(d, a, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_alg1h_rhs(const double* Ca, const double* Wb, const double* y, double* rhs, int64_t n, double tau2,
+                             cudaStream_t st) {
+  k_alg1h_rhs<<<grid_for(n), 256, 0, st>>>(Ca, Wb, y, rhs, n, tau2);
+  return cudaGetLastError();
+}
+cudaError_t launch_alg1h_finish(const double* Zs, const double* Cr, const double* d, double* f, double* R, int64_t n,
+                                double tau2, cudaStream_t st) {
+  k_alg1h_finish<<<grid_for(n), 256, 0, st>>>(Zs, Cr, d, f, R, n, tau2);
+  return cudaGetLastError();
+}

@@ -89,6 +89,9 @@ def lib():
         "fifa_destroy_ctx": (None, [_P]),
         "fifa_assemble": (C.c_int, [_P, _P, C.c_int64, C.POINTER(fifa_hyper), C.POINTER(_P)]),
         "fifa_shift_scale": (C.c_int, [_P, _P, C.c_double, C.POINTER(_P)]),
+        "fifa_add_diagonal": (C.c_int, [_P, _P, C.c_double, _P, C.POINTER(_P)]),
+        "fifa_sample_hetero": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, _P, C.c_uint64, C.c_uint64, C.c_uint64,
+                                         _P, _P]),
         "fifa_factor": (C.c_int, [_P, _P, C.POINTER(_P)]),
         "fifa_logdet": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
         "fifa_solve": (C.c_int, [_P, _P, _P, _P, C.c_int]),
@@ -182,6 +185,18 @@ def fifa_shift_scale(ctx, Cm, s: float):
     h = C.c_void_p()
     _check(lib().fifa_shift_scale(ctx, Cm, C.c_double(s), C.byref(h)), "fifa_shift_scale", ctx=ctx)
     return h
+
+
+def fifa_add_diagonal(ctx, Cm, s: float, diag):
+    h = C.c_void_p()
+    _check(lib().fifa_add_diagonal(ctx, Cm, C.c_double(s), _ptr(diag), C.byref(h)), "fifa_add_diagonal", ctx=ctx)
+    return h
+
+
+def fifa_sample_hetero(ctx, Cm, WC, WP, y, tau2, d, seed, stream_id, it, f, R=None):
+    _check(lib().fifa_sample_hetero(ctx, Cm, WC, WP, _ptr(y), C.c_double(tau2), _ptr(d), C.c_uint64(seed),
+                                    C.c_uint64(stream_id), C.c_uint64(it), _ptr(f), _ptr(R)), "fifa_sample_hetero",
+           ctx=ctx)
 
 
 def fifa_factor(ctx, A):
