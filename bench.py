@@ -387,7 +387,7 @@ def gpu_arm(args):
     fd = torch.empty(n, dtype=torch.float64, device="cuda")
     row = np.zeros((1, fifa.FIFA_TRACE_FIELDS))
     fifa.fifa_gibbs_step(ctx.h, ch, args.warmup, None)
-    e2e_steps = max(3, min(args.steps, 10))
+    e2e_steps = args.steps  # the same iterations of the chain as the device-timed region
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):

@@ -78,6 +78,10 @@ typedef struct {
                            other (every CTA runs independently); required when several contexts
                            launch work concurrently on one GPU, since grouped kernels size their
                            groups to the whole GPU.  0: groups fill the GPU for the top levels. */
+  int wait_polls;     /* a CTA waiting for the rest of its group gives up after this many polls
+                         (each followed by a 64 ns sleep), sets FIFA_ERR_TIMEOUT in the object's
+                         status and makes the whole launch return; 0: the default 2^26 polls
+                         (seconds).  Objects take the value of the context that created them. */
 } fifa_opts;
 
 /* Priors: inverse-gamma IG(shape, scale) on tau2 and sigma2 (the conjugate
@@ -207,6 +211,47 @@ fifa_status fifa_sample_hetero(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fac
                                const double* y_dev, double tau2, const double* d_dev, uint64_t seed,
                                uint64_t stream_id, uint64_t iter, double* f_dev, double* R_dev);
 
+/* Function posterior at new inputs (Sec. "Function posterior at new inputs",
+ * Eq. gp_posterior_newx), given f at the training inputs: with K~ = tau2 C~,
+ *   mu*_j      = c(x*_j, x)^T C~^-1 f,
+ *   sigma*^2_j = tau2 (1 - c(x*_j, x)^T C~^-1 c(x, x*_j)),
+ * c the unit-variance kernel of C (its kind and length-scale; no nugget on the
+ * cross entries; k(x*, x*) = tau2).  C: an assembled C~ (not a view) of the
+ * sorted training inputs x_dev (n doubles); WC: its factor; f_dev: n values;
+ * xstar_dev: nstar new inputs in any order.  mu_dev, var_dev (nstar doubles
+ * each, either nullable) receive the two results.  Costs one W_C^-T W_C^-1
+ * solve and nstar n kernel entries for the means, and one W_C^-1 sweep per two
+ * new inputs for the variances.  Errors: INVALID_ARG, UNSUPPORTED. */
+fifa_status fifa_predict(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, const double* x_dev,
+                         const double* f_dev, const double* xstar_dev, int64_t nstar, double tau2, double* mu_dev,
+                         double* var_dev);
+
+/* Length-scale on a discrete grid (Eq. posterior_gibs4, the sampler the paper
+ * times, with its factorizations computed once): C~(s_h) assembled and
+ * factored in FP64 for every grid value s_h = rho_host[h] (h < G) of the
+ * sorted inputs x_dev (copied), kernel and nugget as fifa_hyper.
+ * log_prior_host (nullable, G values): log prior weight of each grid value
+ * (uniform when null).  Holds G H-matrices and factors in the arena.
+ * Errors: INVALID_ARG, UNSORTED, OOM, NOT_SPD (a grid matrix that does not
+ * factor), those of fifa_assemble. */
+typedef struct fifa_grid fifa_grid;
+fifa_status fifa_grid_create(fifa_ctx* ctx, const double* x_dev, int64_t n, int kernel, double nugget,
+                             const double* rho_host, int G, const double* log_prior_host, fifa_grid** out);
+
+/* Draw the grid index of rho | f, tau2: log w_h = log prior_h - logdet C~_h / 2
+ * - ||W_h^-1 f||^2 / (2 tau2); probabilities normalised after subtracting the
+ * largest log weight; index = the first h whose cumulative probability
+ * exceeds u, u the Philox uniform of (seed, tag 5, iter, stream_id) (the last
+ * index if rounding leaves the total below u).  Synchronizes.  probs_host
+ * (nullable) receives the G probabilities.  Errors: INVALID_ARG. */
+fifa_status fifa_grid_draw(fifa_ctx* ctx, fifa_grid* grid, const double* f_dev, double tau2, uint64_t seed,
+                           uint64_t stream_id, uint64_t iter, int* index_host, double* probs_host);
+
+/* The H-matrix C~(s_h) and its factor (owned by the grid; usable with
+ * fifa_sample, fifa_shift_scale, fifa_matvec ...).  Errors: INVALID_ARG. */
+fifa_status fifa_grid_get(const fifa_grid* grid, int h, const fifa_hmat** C, const fifa_fact** W);
+void fifa_destroy_grid(fifa_ctx* ctx, fifa_grid* grid);
+
 /* A Gibbs chain: copies x, y to the device arena, assembles and factors
  * C~(init->rho); state sigma2 = init->sigma2, tau2 = init->tau2, f = 0.
  * init->nugget and ->kernel fix those settings for the chain.  Errors as
@@ -300,6 +345,41 @@ fifa_status fifa_additive_get(fifa_ctx* ctx, const fifa_additive* model, double*
 fifa_status fifa_additive_kernel_nodes(const fifa_additive* model, int* out_host);
 
 void fifa_destroy_additive(fifa_ctx* ctx, fifa_additive* model);
+
+/* Tensor product of d one-dimensional GPs (Sec. 4.2, Eq. tensor_prod):
+ *   y_i = beta f_1(x_{1,i}) ... f_d(x_{d,i}) + e_i,  e_i ~ N(0, sigma2),
+ *   f_h ~ GP(1, C(rho_h)) (unit variance, prior mean 1), beta ~ N(beta_mu, beta_sd^2).
+ * X_dev: d columns of n doubles (coordinate h of point i at X_dev[h n + i]),
+ * any order; y_dev: n doubles (copied; both may be freed after the call).
+ * init: kernel, nugget, starting rho of every block and sigma2 (init->tau2 is
+ * not used: the blocks have unit variance); prior: IG on sigma2, normal prior
+ * and random-walk step on every log rho_h.  Every f_h starts at 1, beta at
+ * beta0.  Block h draws from Philox stream id h, sigma2 from d, beta from d + 1.
+ * Errors: INVALID_ARG (d outside 1..FIFA_ADDITIVE_MAX_D, non-finite x, beta_sd
+ * <= 0), OOM, those of fifa_chain_create. */
+typedef struct fifa_tensor fifa_tensor;
+fifa_status fifa_tensor_create(fifa_ctx* ctx, const double* X_dev, const double* y_dev, int64_t n, int d,
+                               const fifa_hyper* init, const fifa_prior* prior, double beta0, double beta_mu,
+                               double beta_sd, uint64_t seed, fifa_tensor** out);
+
+/* Run `sweeps` sweeps: for h = 0..d-1, f_h - 1 by Algorithm 1.h on the sorted
+ * x_h with data y / g - 1 and precisions g^2 / sigma2, g = beta prod_{k != h} f_k
+ * (the block's P~ = C~ + D^-1 refactored each sweep); beta | y, F (its normal
+ * conditional); sigma2 | y, F, beta; then the Metropolis step on every log
+ * rho_h with tau2 = 1.  One sweep is captured in a CUDA graph.  trace_host
+ * (nullable): sweeps rows of FIFA_TENSOR_TRACE_FIELDS(d) doubles: sweep, beta,
+ * sigma2, ||y - beta prod_h f_h||^2, status, rho[d], accepted[d].
+ * Errors: INVALID_ARG (a zero product g_i: no information on f_h), the blocks'
+ * device status (NOT_SPD, TIMEOUT). */
+#define FIFA_TENSOR_TRACE_FIELDS(d) (5 + 2 * (d))
+fifa_status fifa_tensor_sweep(fifa_ctx* ctx, fifa_tensor* model, int sweeps, double* trace_host);
+
+/* Current state (synchronizes): F_dev (nullable) receives f_1..f_d as d columns
+ * of n doubles in the original point order; beta_host, sigma2_host (nullable);
+ * blocks_host (nullable): d entries with each block's rho. */
+fifa_status fifa_tensor_get(fifa_ctx* ctx, const fifa_tensor* model, double* F_dev, double* beta_host,
+                            double* sigma2_host, fifa_hyper* blocks_host);
+void fifa_destroy_tensor(fifa_ctx* ctx, fifa_tensor* model);
 
 /* Serving: independent 1-D GP regression requests (each a Gibbs chain on its
  * own sorted inputs) with continuous batching on the current GPU.  The server

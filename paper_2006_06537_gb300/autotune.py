@@ -1,9 +1,18 @@
 """Leaf-size autotuner for the Gibbs chain (results cached in tuned.json).
 
-For a workload key (kernel, input recipe, n) it times a few Gibbs iterations of
-the FP64 chain for every candidate leaf size B and stores the per-B times and
-the fastest B.  bench.py and users read the cached choice, so repeated runs
-(and profiled runs, whose timings are distorted) use the same configuration.
+For a workload key (kernel, input recipe, n) it times Gibbs iterations of the
+mixed-precision chain and of the FP64 chain for every candidate leaf size B and
+stores the per-B times and the B that is fastest for the mixed chain (the
+benchmark's headline path; bench.py runs both paths with it).  bench.py and
+users read the cached choice, so repeated runs (and profiled runs, whose
+timings are distorted) use the same configuration.
+
+Candidates: B in {32, 64, 128}.  B = 256 is out of reach of this library: a
+leaf's FP64 Cholesky and triangular solves run in one CTA's shared memory,
+which holds at most 227 KB, and a 256 x 256 FP64 leaf alone is 512 KB
+(FIFA_LEAF_MAX = 128).  The rank cap only bounds memory (the clustered
+workload's ranks stay at or below 7 of 32), and the kernels' tile shapes are
+fixed at compile time, so neither is searched.
 
     python -m paper_2006_06537_gb300.autotune [--n 1048576] [--leaves 32 64 128]
 """
@@ -37,7 +46,7 @@ def store(key: str, entry: dict):
         json.dump(data, fh, indent=1, sort_keys=True)
 
 
-def time_leaf(x, y, leaf, rho0, eps, cap, nugget, iters=3, warmup=1):
+def time_leaf(x, y, leaf, rho0, eps, cap, nugget, iters=5, warmup=3, prec=0, refine_tol=1e-10):
     import torch
 
     from . import fifa
@@ -45,8 +54,8 @@ def time_leaf(x, y, leaf, rho0, eps, cap, nugget, iters=3, warmup=1):
     stream = torch.cuda.Stream()
     vy = float(np.var(y))
     with torch.cuda.stream(stream):
-        ctx = fifa.Context(leaf_size=leaf, aca_tol=eps, rank_cap=cap, prec=fifa.FIFA_FP64, arena_bytes=40 << 30,
-                           stream=stream)
+        ctx = fifa.Context(leaf_size=leaf, aca_tol=eps, rank_cap=cap, prec=prec, refine_max=8, refine_tol=refine_tol,
+                           arena_bytes=40 << 30, stream=stream)
         xd = torch.tensor(x, device="cuda")
         yd = torch.tensor(y, device="cuda")
         pr = fifa.fifa_prior(1.0, 1.0, 1.0, 1.0, math.log(rho0), 1.0, 0.2)
@@ -71,9 +80,11 @@ def tune_clustered(n: int, leaves=(32, 64, 128), rho0=0.01, eps=1e-10, cap=32, n
 
     build()
     x, y = clustered(n, 2, noise=noise)
-    times = {str(b): time_leaf(x, y, b, rho0, eps, cap, nugget) for b in leaves}
-    best = int(min(times, key=times.get))
-    entry = {"leaf": best, "ms_per_iter": times, "rho0": rho0, "eps": eps, "cap": cap, "nugget": nugget}
+    mixed = {str(b): time_leaf(x, y, b, rho0, eps, cap, nugget, prec=1) for b in leaves}
+    fp64 = {str(b): time_leaf(x, y, b, rho0, eps, cap, nugget, prec=0) for b in leaves}
+    best = int(min(mixed, key=mixed.get))
+    entry = {"leaf": best, "ms_per_iter": mixed, "ms_per_iter_fp64": fp64, "rho0": rho0, "eps": eps, "cap": cap,
+             "nugget": nugget, "refine_tol": 1e-10, "iters_timed": 5, "warmup": 3}
     store(workload_key("clustered_se", n), entry)
     return entry
 

@@ -423,6 +423,7 @@ extern "C" fifa_status fifa_create(fifa_ctx** out, const fifa_opts* opts, void* 
   if (opts->leaf_size > FIFA_LEAF_MAX || opts->rank_cap > FIFA_CAP_MAX) return FIFA_ERR_UNSUPPORTED;
   if (opts->prec != FIFA_FP64 && opts->prec != FIFA_MIXED) return FIFA_ERR_INVALID_ARG;
   if (opts->independent_ctas != 0 && opts->independent_ctas != 1) return FIFA_ERR_INVALID_ARG;
+  if (opts->wait_polls < 0) return FIFA_ERR_INVALID_ARG;
   if (arena_bytes < (1u << 20)) return FIFA_ERR_INVALID_ARG;
   fifa_ctx* ctx = new (std::nothrow) fifa_ctx();
   if (!ctx) return FIFA_ERR_OOM;
@@ -525,6 +526,7 @@ fifa_status hmat_alloc(fifa_ctx* ctx, Plan* P, int kind, fifa_hmat** out) {
   d.scale = 1.0;
   d.shift = 0.0;
   d.eps = ctx->opts.aca_tol;
+  d.spin = ctx->opts.wait_polls > 0 ? (unsigned int)ctx->opts.wait_polls : 0u;
   d.leaves = (double*)ctx->arena.alloc(sizeof(double) * (size_t)P->nleaf * P->Bm * P->Bm);
   d.bases = (double*)ctx->arena.alloc(sizeof(double) * (size_t)std::max(1, P->L) * cap * P->n);
   d.rank = (int*)ctx->arena.alloc(sizeof(int) * nn);
@@ -682,6 +684,7 @@ fifa_status fact_alloc(fifa_ctx* ctx, Plan* P, int with32, fifa_fact** out) {
   d.prec = 0;
   d.bnd = P->bnd_dev;
   d.skip = nullptr;
+  d.spin = ctx->opts.wait_polls > 0 ? (unsigned int)ctx->opts.wait_polls : 0u;
   d.Lleaf = ctx->arena.alloc(sizeof(double) * (size_t)P->nleaf * P->Bm * P->Bm);
   d.Ldinv = ctx->arena.alloc(sizeof(double) * (size_t)P->nleaf * P->Bm);
   d.Q = ctx->arena.alloc(sizeof(double) * (size_t)std::max(1, P->L) * cap * P->n);

@@ -46,6 +46,7 @@ struct HmatDesc {
   double scale;   // view: A = scale * C~ + shift * I (U scaled by `scale`)
   double shift;
   const double* diag;  // nullable: per-row diagonal, A = scale * C~ + diag(diag) (replaces shift)
+  unsigned int spin;   // polls before a group wait gives up (0: FIFA_SPIN_LIMIT)
 };
 
 struct FactDesc {
@@ -65,6 +66,7 @@ struct FactDesc {
   int* status;                  // [1]
   const int* skip;              // nullable: while *skip != 0 the factorization kernels leave this
                                 // factor as it is (a factor kept from an earlier iteration)
+  unsigned int spin;            // polls before a group wait gives up (0: FIFA_SPIN_LIMIT)
 };
 
 __host__ __device__ inline int bnd_off(int l) { return (1 << l) - 1 + l; }
@@ -316,7 +318,8 @@ template <typename T> __device__ __forceinline__ double to_d(T v) { return (doub
 // Returns false (in every thread) if the wait gave up; *err then has the
 // TIMEOUT bit set.
 __device__ inline bool group_barrier(unsigned int* counter, unsigned int target, int* err,
-                                     volatile int* abort_flag) {
+                                     volatile int* abort_flag, unsigned int limit) {
+  if (limit == 0) limit = FIFA_SPIN_LIMIT;
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -328,7 +331,7 @@ __device__ inline bool group_barrier(unsigned int* counter, unsigned int target,
       unsigned int v = *((volatile unsigned int*)counter);
       if (v >= target) break;
       if (*abort_flag) { ok = 0; break; }
-      if (++spins > FIFA_SPIN_LIMIT) {
+      if (++spins > limit) {
         atomicOr(err, FIFA_DEV_TIMEOUT);
         *abort_flag = 1;
         ok = 0;

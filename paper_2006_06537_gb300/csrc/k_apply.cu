@@ -507,7 +507,7 @@ __device__ bool fs_global_level(const FactDesc* __restrict__ Fd, int l, int ls, 
   }
   (void)lane;
   ++phase;
-  if (!group_barrier(bar, (unsigned)C * phase, Fd->status, abort_flag)) return false;
+  if (!group_barrier(bar, (unsigned)C * phase, Fd->status, abort_flag, Fd->spin)) return false;
   if (r == 0) return true;
   // p over the node: the left half of its CTAs for rows of the left child, the
   // right half for the right child, summed in a fixed order
@@ -826,7 +826,7 @@ __global__ void __launch_bounds__(256, RPT <= 8 ? 4 : 2) k_mv_fused(const HmatDe
   }
   if (ls > 0) {
     unsigned int phase = 1;
-    if (!group_barrier(bar, (unsigned)C * phase, Hd->status, abort_flag)) return;
+    if (!group_barrier(bar, (unsigned)C * phase, Hd->status, abort_flag, Hd->spin)) return;
   }
   // levels < ls: the partner half's projection, then the rows' sums
   for (int l = 0; l < ls; ++l) {

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256, 4) k_aca(const HmatDesc* __restrict__ Hd,
       if (G > 1) {
         if (threadIdx.x == 0) part[3 * (base + g)] = best;
         ++phase;
-        if (!group_barrier(bar + base, G * phase, Hd->status, abort_flag)) return;
+        if (!group_barrier(bar + base, G * phase, Hd->status, abort_flag, Hd->spin)) return;
         ArgMax t{-1.0, 0x7fffffff, 0.0};
         for (int q = threadIdx.x; q < G; q += blockDim.x) {
           const ArgMax* pq = part + 3 * (base + q);
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256, 4) k_aca(const HmatDesc* __restrict__ Hd,
           part[3 * (base + g) + 2] = nb;
         }
         ++phase;
-        if (!group_barrier(bar + base, G * phase, Hd->status, abort_flag)) return;
+        if (!group_barrier(bar + base, G * phase, Hd->status, abort_flag, Hd->spin)) return;
         double tm = 0.0;
         ArgMax t{-1.0, 0x7fffffff, 0.0};
         for (int q = threadIdx.x; q < G; q += blockDim.x) {

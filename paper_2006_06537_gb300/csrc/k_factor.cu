@@ -303,7 +303,7 @@ template <typename T> __device__ __forceinline__ double clamp_cap() { return siz
 // memory), so a large group costs a few loads per thread, not G serial ones.
 __device__ inline bool group_reduce(double* dst, const double* src_local, int count, int G, int g, int base,
                                     double* part, size_t pstride, unsigned int* bar, unsigned int& phase,
-                                    int* status, int* abort_flag, double* red) {
+                                    int* status, int* abort_flag, double* red, unsigned int spin) {
   if (G == 1) return true;
   // two slot sets alternate with the barrier count: a slot is rewritten only
   // after a later barrier that every reader of its previous contents has passed
@@ -311,7 +311,7 @@ __device__ inline bool group_reduce(double* dst, const double* src_local, int co
   double* mine = part + (set + base + g) * pstride;
   for (int t = threadIdx.x; t < count; t += blockDim.x) mine[t] = src_local[t];
   ++phase;
-  if (!group_barrier(bar + base, (unsigned)G * phase, status, abort_flag)) return false;
+  if (!group_barrier(bar + base, (unsigned)G * phase, status, abort_flag, spin)) return false;
   const double* slots = part + (set + base) * pstride;
   if (count >= (int)blockDim.x) {
     for (int t = threadIdx.x; t < count; t += blockDim.x) {
@@ -550,7 +550,8 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
   for (int pass = 0; pass < 2; ++pass) {
     gram_tiled<T>(Qb, n, r, sa0, sa1, tile, tbuf, part, Ri);
     gram_tiled<T>(Qb, n, r, sb0, sb1, tile, tbuf, part, Ri + npk);
-    if (!group_reduce(Ri, Ri, 2 * npk, G, g, base, gpart, pstride, bar, phase, status, abort_flag, part)) return;
+    if (!group_reduce(Ri, Ri, 2 * npk, G, g, base, gpart, pstride, bar, phase, status, abort_flag, part, Fd->spin))
+      return;
     gram_unpack(Ri, r, Gm, ldm);
     gram_unpack(Ri + npk, r, Gm2, ldm);
     if (r <= 8) {
@@ -680,7 +681,7 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
   }
   if (G > 1) {
     ++phase;
-    if (!group_barrier(bar + base, (unsigned)G * phase, status, abort_flag)) return;
+    if (!group_barrier(bar + base, (unsigned)G * phase, status, abort_flag, Fd->spin)) return;
   }
   if (lvl == 0) return;
 
@@ -707,7 +708,8 @@ __global__ void __launch_bounds__(256, RB == 4 ? 4 : (RB == 16 ? 3 : 2))
     __syncthreads();
     proj_tiled<T, W>(Qb, Bp, w, n, r, max(r0, s), min(r1, h), tile, tbuf, part, Pm);
     proj_tiled<T, W>(Qb, Bp, w, n, r, max(r0, h), min(r1, e), tile, tbuf, part, Pm + r * W);
-    if (!group_reduce(Pm, Pm, r2 * W, G, g, base, gpart, pstride, bar, phase, status, abort_flag, part)) return;
+    if (!group_reduce(Pm, Pm, r2 * W, G, g, base, gpart, pstride, bar, phase, status, abort_flag, part, Fd->spin))
+      return;
     for (int t = threadIdx.x; t < r2 * W; t += blockDim.x) {
       const int a = t / W, j = t % W;
       double acc = 0.0;
@@ -1263,7 +1265,8 @@ __global__ void k_logdet_reduce(const FactDesc* __restrict__ Fd) {
   __shared__ double red[40];
   const int cnt = Fd->nleaf + (1 << Fd->L) - 1;
   double v = 0.0;
-  for (int t = threadIdx.x; t < cnt; t += blockDim.x) v += Fd->ld_parts[t];
+#pragma unroll 8
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) v += Fd->ld_parts[t];  // eight loads in flight per thread
   v = block_sum(v, red);
   if (threadIdx.x == 0) Fd->logdet[0] = 2.0 * v;
 }
@@ -1412,6 +1415,6 @@ int level_bucket_coresident(int prec, int b, int cap) {
 }
 
 cudaError_t launch_logdet_reduce(const FactDesc* Fd, cudaStream_t st, int nprob) {
-  k_logdet_reduce<<<dim3(1, nprob), 256, 0, st>>>(Fd);
+  k_logdet_reduce<<<dim3(1, nprob), 1024, 0, st>>>(Fd);
   return cudaGetLastError();
 }

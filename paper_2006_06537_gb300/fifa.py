@@ -32,7 +32,8 @@ class fifa_hyper(C.Structure):
 
 class fifa_opts(C.Structure):
     _fields_ = [("leaf_size", C.c_int), ("aca_tol", C.c_double), ("rank_cap", C.c_int), ("prec", C.c_int),
-                ("refine_tol", C.c_double), ("refine_max", C.c_int), ("independent_ctas", C.c_int)]
+                ("refine_tol", C.c_double), ("refine_max", C.c_int), ("independent_ctas", C.c_int),
+                ("wait_polls", C.c_int)]
 
 
 class fifa_plan_info(C.Structure):
@@ -92,6 +93,12 @@ def lib():
         "fifa_add_diagonal": (C.c_int, [_P, _P, C.c_double, _P, C.POINTER(_P)]),
         "fifa_sample_hetero": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, _P, C.c_uint64, C.c_uint64, C.c_uint64,
                                          _P, _P]),
+        "fifa_predict": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int64, C.c_double, _P, _P]),
+        "fifa_grid_create": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.c_double, _P, C.c_int, _P, C.POINTER(_P)]),
+        "fifa_grid_draw": (C.c_int, [_P, _P, _P, C.c_double, C.c_uint64, C.c_uint64, C.c_uint64,
+                                     C.POINTER(C.c_int), _P]),
+        "fifa_grid_get": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(_P)]),
+        "fifa_destroy_grid": (None, [_P, _P]),
         "fifa_factor": (C.c_int, [_P, _P, C.POINTER(_P)]),
         "fifa_logdet": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
         "fifa_solve": (C.c_int, [_P, _P, _P, _P, C.c_int]),
@@ -120,6 +127,12 @@ def lib():
         "fifa_additive_get": (C.c_int, [_P, _P, _P, C.POINTER(C.c_double), C.POINTER(fifa_hyper)]),
         "fifa_additive_kernel_nodes": (C.c_int, [_P, C.POINTER(C.c_int)]),
         "fifa_destroy_additive": (None, [_P, _P]),
+        "fifa_tensor_create": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, C.POINTER(fifa_hyper), C.POINTER(fifa_prior),
+                                         C.c_double, C.c_double, C.c_double, C.c_uint64, C.POINTER(_P)]),
+        "fifa_tensor_sweep": (C.c_int, [_P, _P, C.c_int, _P]),
+        "fifa_tensor_get": (C.c_int, [_P, _P, _P, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                      C.POINTER(fifa_hyper)]),
+        "fifa_destroy_tensor": (None, [_P, _P]),
         "fifa_hmat_dims": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "fifa_plan_describe": (C.c_int, [C.POINTER(fifa_opts), C.c_int64, C.c_int, _P, C.POINTER(fifa_plan_info), _P, _P, _P]),
@@ -197,6 +210,39 @@ def fifa_sample_hetero(ctx, Cm, WC, WP, y, tau2, d, seed, stream_id, it, f, R=No
     _check(lib().fifa_sample_hetero(ctx, Cm, WC, WP, _ptr(y), C.c_double(tau2), _ptr(d), C.c_uint64(seed),
                                     C.c_uint64(stream_id), C.c_uint64(it), _ptr(f), _ptr(R)), "fifa_sample_hetero",
            ctx=ctx)
+
+
+def fifa_predict(ctx, Cm, WC, x, f, xstar, nstar, tau2, mu=None, var=None):
+    _check(lib().fifa_predict(ctx, Cm, WC, _ptr(x), _ptr(f), _ptr(xstar), C.c_int64(nstar), C.c_double(tau2), _ptr(mu),
+                              _ptr(var)), "fifa_predict", ctx=ctx)
+
+
+def fifa_grid_create(ctx, x, n, kernel, nugget, rhos, log_prior=None):
+    r = np.ascontiguousarray(rhos, dtype=np.float64)
+    lp = np.ascontiguousarray(log_prior, dtype=np.float64) if log_prior is not None else None
+    h = C.c_void_p()
+    _check(lib().fifa_grid_create(ctx, _ptr(x), C.c_int64(n), int(kernel), C.c_double(nugget), _np_ptr(r), len(r),
+                                  _np_ptr(lp), C.byref(h)), "fifa_grid_create", ctx=ctx)
+    return h
+
+
+def fifa_grid_draw(ctx, grid, f, tau2, seed, stream_id, it, G=None):
+    """(index, probabilities (G floats, when G is given))."""
+    idx = C.c_int()
+    pr = np.zeros(G) if G else None
+    _check(lib().fifa_grid_draw(ctx, grid, _ptr(f), C.c_double(tau2), C.c_uint64(seed), C.c_uint64(stream_id),
+                                C.c_uint64(it), C.byref(idx), _np_ptr(pr)), "fifa_grid_draw", ctx=ctx)
+    return idx.value, pr
+
+
+def fifa_grid_get(grid, h):
+    Cm, W = C.c_void_p(), C.c_void_p()
+    _check(lib().fifa_grid_get(grid, int(h), C.byref(Cm), C.byref(W)), "fifa_grid_get")
+    return Cm, W
+
+
+def fifa_destroy_grid(ctx, grid):
+    lib().fifa_destroy_grid(ctx, grid)
 
 
 def fifa_factor(ctx, A):
@@ -308,6 +354,37 @@ def fifa_additive_kernel_nodes(model):
 
 def fifa_destroy_additive(ctx, model):
     lib().fifa_destroy_additive(ctx, model)
+
+
+def fifa_tensor_trace_fields(d: int) -> int:
+    return 5 + 2 * d
+
+
+def fifa_tensor_create(ctx, X_cols, y, n, d, init: fifa_hyper, prior: fifa_prior, beta0: float, beta_mu: float,
+                       beta_sd: float, seed: int):
+    """X_cols: d x n device doubles (coordinate h of point i at [h, i])."""
+    h = C.c_void_p()
+    _check(lib().fifa_tensor_create(ctx, _ptr(X_cols), _ptr(y), C.c_int64(n), C.c_int(d), C.byref(init),
+                                    C.byref(prior), C.c_double(beta0), C.c_double(beta_mu), C.c_double(beta_sd),
+                                    C.c_uint64(seed), C.byref(h)), "fifa_tensor_create", ctx=ctx)
+    return h
+
+
+def fifa_tensor_sweep(ctx, model, sweeps: int, trace: np.ndarray | None = None, allow=()):
+    tp = trace.ctypes.data_as(C.c_void_p) if trace is not None else None
+    return _check(lib().fifa_tensor_sweep(ctx, model, int(sweeps), tp), "fifa_tensor_sweep", allow, ctx=ctx)
+
+
+def fifa_tensor_get(ctx, model, d: int, F=None):
+    """Returns (beta, sigma2, [fifa_hyper] * d); F (d x n device doubles) receives f_1..f_d."""
+    b, s2 = C.c_double(), C.c_double()
+    hs = (fifa_hyper * d)()
+    _check(lib().fifa_tensor_get(ctx, model, _ptr(F), C.byref(b), C.byref(s2), hs), "fifa_tensor_get", ctx=ctx)
+    return b.value, s2.value, list(hs)
+
+
+def fifa_destroy_tensor(ctx, model):
+    lib().fifa_destroy_tensor(ctx, model)
 
 
 def fifa_server_create(opts: fifa_opts, hbm_budget: int, slots: int, wide_min_n: int = 0):
@@ -454,7 +531,7 @@ def fifa_probe_fp64_fma(ctx, iters: int = 200000):
 # ---------------------------------------------------------------------------
 class Context:
     def __init__(self, leaf_size=64, aca_tol=1e-12, rank_cap=32, prec=FIFA_FP64, refine_tol=1e-12, refine_max=3,
-                 arena_bytes=1 << 30, device="cuda", stream=None, independent_ctas=0):
+                 arena_bytes=1 << 30, device="cuda", stream=None, independent_ctas=0, wait_polls=0):
         import torch
 
         self.torch = torch
@@ -462,7 +539,7 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.device)
         self.opts = fifa_opts(int(leaf_size), float(aca_tol), int(rank_cap), int(prec), float(refine_tol),
-                              int(refine_max), int(independent_ctas))
+                              int(refine_max), int(independent_ctas), int(wait_polls))
         self.h = fifa_create(self.opts, self.stream.cuda_stream, self.arena.data_ptr(), int(arena_bytes))
 
     def close(self):
