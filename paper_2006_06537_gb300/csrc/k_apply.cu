@@ -571,6 +571,189 @@ __device__ void fs_leaves(const FactDesc* __restrict__ Fd, int ls, int c, T* vs,
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Warp-owned subtrees.  Below the fused level ls every warp of the CTA owns
+// the subtree of one level-lw node, lw = min(L, ls + FS_WL) (eight warps: three
+// levels), and applies the leaves and the levels >= lw of that subtree alone:
+// lanes stride over the node's rows, projections are reduced with warp
+// shuffles, and no block barrier is passed.  Levels ls <= l < lw combine one
+// partial projection per warp through shared memory with one block barrier
+// per level.  The per-warp arrays: p and t of the current node (pj, 2 FS_WSL
+// entries per warp) and the warp partials of the block levels (tv, two
+// buffers alternating by level).  Ranks above FS_RFAST(T, NR) take the
+// block-wide path instead.  FP32 only: in FP64 the shuffle reductions (two
+// 32-bit shuffles and a DADD per step) cost more FP64 issue than the block
+// barriers they replace (the FP64 W^-1 sweep at n = 2^20: 1.06 ms block-wide,
+// 1.21 ms warp-owned).
+// ---------------------------------------------------------------------------
+#define FS_WARP_OWNED(T) (sizeof(T) == 4)
+#define FS_WL 3
+#define FS_WSL 32                                           // p or t entries per warp: 2 r nrhs <= 32
+#define FS_RFAST(T, NR) ((sizeof(T) == 4 ? 16 : 8) / (NR))  // ranks the warp path takes
+
+template <typename T>
+__device__ __forceinline__ T warp_allsum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// t = op(Z) p for a node of rank r: lane k < 2 r nrhs computes t[k]
+// (k = (row, j)); p and t interleaved by right-hand side.
+template <typename T, int NR>
+__device__ __forceinline__ void fw_apply_z(const double* __restrict__ Z, int ld2, int r, int zt, const T* pw, T* tw,
+                                           int lane) {
+  constexpr int nrhs = NR;
+  if (lane < 2 * r * nrhs) {
+    const int row = lane / nrhs, j = lane % nrhs;
+    T acc = (T)0;
+    for (int b = 0; b < 2 * r; ++b) acc += (T)(zt ? Z[b * ld2 + row] : Z[row * ld2 + b]) * pw[b * nrhs + j];
+    tw[lane] = acc;
+  }
+  __syncwarp();
+}
+
+// Projection of rows [a0, a1) onto the r columns of Qb, accumulated per lane
+// (rows lane, lane + 32, ...) and reduced over the warp; every lane ends with
+// the sums, lane 0 stores them at out[a nrhs + j].
+template <typename T, int NR>
+__device__ __forceinline__ void fw_project(const T* __restrict__ Qb, int64_t n, int r, const T* vs, int rows, int S,
+                                           int a0, int a1, T* out, int lane) {
+  constexpr int nrhs = NR;
+  constexpr int RF = FS_RFAST(T, NR);
+  T acc[RF][NR];
+#pragma unroll
+  for (int a = 0; a < RF; ++a)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[a][j] = (T)0;
+  for (int p = a0 + lane; p < a1; p += 32) {
+    T v[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) v[j] = vs[(size_t)j * rows + p - S];
+    T q[RF];
+#pragma unroll
+    for (int a = 0; a < RF; ++a) q[a] = a < r ? Qb[(size_t)a * n + p] : (T)0;
+#pragma unroll
+    for (int a = 0; a < RF; ++a)
+      if (a < r)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) acc[a][j] += q[a] * v[j];
+  }
+#pragma unroll
+  for (int a = 0; a < RF; ++a)
+    if (a < r)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        const T t = warp_allsum(acc[a][j]);
+        if (lane == 0) out[a * nrhs + j] = t;
+      }
+}
+
+// v_p += sum_a Q[a][p] t[(off + a) nrhs + j] for rows [a0, a1), lanes striding.
+template <typename T, int NR>
+__device__ __forceinline__ void fw_update(const T* __restrict__ Qb, int64_t n, int r, T* vs, int rows, int S, int a0,
+                                          int a1, const T* tw, int off) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll 2
+  for (int p = a0 + lane; p < a1; p += 32) {
+    T acc0 = vs[p - S], acc1 = NR > 1 ? vs[rows + p - S] : (T)0;
+    fs_row_update<T, NR>(Qb, n, p, r, tw + off * NR, acc0, acc1);
+    vs[p - S] = acc0;
+    if (NR > 1) vs[rows + p - S] = acc1;
+  }
+}
+
+// One node of a warp-owned level: projection of both sides, t = op(Z) p, update.
+template <typename T, int NR>
+__device__ void fw_node(const FactDesc* __restrict__ Fd, int l, int i, T* vs, int rows, int S, int zsel, int zt,
+                        T* pw, T* tw, int lane) {
+  const int cap = Fd->cap, ld2 = 2 * cap;
+  const int64_t n = Fd->n;
+  const int nid = node_id(l, i);
+  const int r = Fd->rank[nid];
+  if (r == 0) return;
+  int s0, h0, e0;
+  node_range(Fd->bnd, l, i, s0, h0, e0);
+  const T* Qb = (const T*)Fd->Q + (size_t)l * cap * n;
+  fw_project<T, NR>(Qb, n, r, vs, rows, S, s0, h0, pw, lane);
+  fw_project<T, NR>(Qb, n, r, vs, rows, S, h0, e0, pw + r * NR, lane);
+  __syncwarp();
+  fw_apply_z<T, NR>((zsel ? Fd->Zi : Fd->Zf) + (size_t)nid * ld2 * ld2, ld2, r, zt, pw, tw, lane);
+  fw_update<T, NR>(Qb, n, r, vs, rows, S, s0, h0, tw, 0);
+  fw_update<T, NR>(Qb, n, r, vs, rows, S, h0, e0, tw, r);
+  __syncwarp();
+}
+
+// The leaves and levels >= lw of warp w's subtree (root node wi at level lw),
+// in the sweep's order: up = leaves first, then levels L-1 .. lw; else the
+// levels lw .. L-1, then the leaves.
+template <typename T, int NR>
+__device__ void fw_subtree(const FactDesc* __restrict__ Fd, int lw, int wi, T* vs, int rows, int S, int mode, bool up,
+                           int zsel, int zt, T* pw, T* tw, int lane) {
+  const int L = Fd->L, Bm = Fd->Bm;
+  auto leaves = [&]() {
+    const int nl = 1 << (L - lw), first = wi << (L - lw);
+    for (int q = 0; q < nl; ++q) {
+      const int leaf = first + q;
+      const int s = Fd->bnd[bnd_off(L) + leaf], e = Fd->bnd[bnd_off(L) + leaf + 1];
+      const T* Lm = (const T*)Fd->Lleaf + (size_t)leaf * Bm * Bm;
+      const T* dinv = (const T*)Fd->Ldinv + (size_t)leaf * Bm;
+      if (Bm <= 32)
+        leaf_warp_apply32<T, T>(Lm, dinv, Bm, e - s, vs + (s - S), NR > 1 ? vs + rows + (s - S) : nullptr, mode,
+                                lane);
+      else
+        for (int j = 0; j < NR; ++j) leaf_warp_apply<T, T>(Lm, dinv, Bm, e - s, vs + (size_t)j * rows + (s - S), mode, lane);
+      __syncwarp();
+    }
+  };
+  if (up) {
+    leaves();
+    for (int l = L - 1; l >= lw; --l)
+      for (int q = 0; q < (1 << (l - lw)); ++q) fw_node<T, NR>(Fd, l, (wi << (l - lw)) + q, vs, rows, S, zsel, zt, pw, tw, lane);
+  } else {
+    for (int l = lw; l < L; ++l)
+      for (int q = 0; q < (1 << (l - lw)); ++q) fw_node<T, NR>(Fd, l, (wi << (l - lw)) + q, vs, rows, S, zsel, zt, pw, tw, lane);
+    leaves();
+  }
+}
+
+// One level ls <= l < lw: warp w's rows (those of its level-lw node) lie in
+// one side of a level-l node; one partial per warp in shared memory, one block
+// barrier, then every warp forms p from its node's warps (fixed order),
+// t = op(Z) p and updates its own rows.  nsub: warps that own a subtree.
+template <typename T, int NR>
+__device__ void fw_block_level(const FactDesc* __restrict__ Fd, int l, int lw, int c, int nsub, T* vs, int rows,
+                               int S, int zsel, int zt, T* part, T* pw, T* tw, int warp, int lane) {
+  constexpr int nrhs = NR;
+  const int cap = Fd->cap, ld2 = 2 * cap;
+  const int64_t n = Fd->n;
+  const bool own = warp < nsub;
+  const int wi = (c * nsub) + warp;           // the warp's level-lw node
+  const int span = lw - l, i = wi >> span;    // its level-l node
+  const int nid = node_id(l, i);
+  const int r = Fd->rank[nid];
+  const T* Qb = (const T*)Fd->Q + (size_t)l * cap * n;
+  if (own && r > 0) {
+    const int a0 = Fd->bnd[bnd_off(lw) + wi], a1 = Fd->bnd[bnd_off(lw) + wi + 1];
+    fw_project<T, NR>(Qb, n, r, vs, rows, S, a0, a1, part + warp * FS_WSL, lane);
+  }
+  __syncthreads();
+  if (!own || r == 0) return;
+  // warps of node i: [i << span, (i + 1) << span) - c nsub, left half first
+  const int w0 = (i << span) - c * nsub, half = 1 << (span - 1);
+  const int side = (wi >> (span - 1)) & 1;
+  if (lane < 2 * r * nrhs) {
+    const int sd = lane / (r * nrhs), k = lane % (r * nrhs);
+    T acc = (T)0;
+    for (int q = 0; q < half; ++q) acc += part[(w0 + sd * half + q) * FS_WSL + k];
+    pw[lane] = acc;
+  }
+  __syncwarp();
+  fw_apply_z<T, NR>((zsel ? Fd->Zi : Fd->Zf) + (size_t)nid * ld2 * ld2, ld2, r, zt, pw, tw, lane);
+  const int a0 = Fd->bnd[bnd_off(lw) + wi], a1 = Fd->bnd[bnd_off(lw) + wi + 1];
+  fw_update<T, NR>(Qb, n, r, vs, rows, S, a0, a1, tw, side * r);
+  __syncwarp();
+}
+
 // mode 0: v <- W v, 1: W^-1 v, 2: W^T v, 3: W^-T v; mode 4: v <- W^-T W^-1 v
 // (both inverse sweeps, v kept in shared memory in between: a full solve with
 // the factor).  Arithmetic in T: FP64 for an FP64 factor, FP32 for an FP32
@@ -596,22 +779,58 @@ __global__ void __launch_bounds__(256, 4) k_sweep_fused(const FactDesc* __restri
   const int L = Fd->L;
   const int64_t n = Fd->n;
   const int S = Fd->bnd[bnd_off(ls) + c], E = Fd->bnd[bnd_off(ls) + c + 1];
+  // warp-owned subtrees when every rank of the CTA's levels >= ls is small
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lw = min(L, ls + FS_WL), nsub = 1 << (lw - ls);
+  __shared__ int rk_big;
+  if (threadIdx.x == 0) rk_big = 0;
   for (int j = 0; j < nrhs; ++j)
     for (int p = threadIdx.x; p < E - S; p += blockDim.x) vs[(size_t)j * rows + p] = (T)v[(size_t)j * n + S + p];
-  {
+  __syncthreads();
+  for (int l = ls; l < L; ++l)
+    for (int q = threadIdx.x; q < (1 << (l - ls)); q += blockDim.x)
+      if (Fd->rank[node_id(l, (c << (l - ls)) + q)] > FS_RFAST(T, NR)) rk_big = 1;
+  __syncthreads();
+  const bool fast = FS_WARP_OWNED(T) && !rk_big && nsub <= FS_WARPS;
+  if (!fast) {  // the block-wide path: the local leaf of every row
     const int nl = 1 << (L - ls), first = c << (L - ls);
     for (int q = threadIdx.x; q < nl; q += blockDim.x) {
       const int s0 = Fd->bnd[bnd_off(L) + first + q], e0 = Fd->bnd[bnd_off(L) + first + q + 1];
       for (int p = s0; p < e0; ++p) sh.lmap[p - S] = (unsigned short)q;
     }
+    __syncthreads();
   }
-  __syncthreads();
   unsigned int phase = 0;
   bool ok = true;
+  T* pw = sh.pj + warp * 2 * FS_WSL;  // p of the warp's node
+  T* tw = pw + FS_WSL;                // t of the warp's node
+  auto local_up = [&](int md, int zsel, int zt) {
+    if (!fast) {
+      fs_leaves<T, NR>(Fd, ls, c, vs, rows, S, md);
+      for (int l = L - 1; l >= ls; --l) fs_local_level<T, NR>(Fd, l, ls, c, vs, rows, S, E - S, zsel, zt, sh);
+      return;
+    }
+    if (warp < nsub) fw_subtree<T, NR>(Fd, lw, (c << (lw - ls)) + warp, vs, rows, S, md, true, zsel, zt, pw, tw, lane);
+    for (int l = lw - 1; l >= ls; --l)
+      fw_block_level<T, NR>(Fd, l, lw, c, nsub, vs, rows, S, zsel, zt, sh.tv + (l & 1) * FS_WARPS * FS_WSL, pw, tw,
+                            warp, lane);
+    __syncthreads();
+  };
+  auto local_down = [&](int md, int zsel, int zt) {
+    if (!fast) {
+      for (int l = ls; l < L; ++l) fs_local_level<T, NR>(Fd, l, ls, c, vs, rows, S, E - S, zsel, zt, sh);
+      fs_leaves<T, NR>(Fd, ls, c, vs, rows, S, md);
+      return;
+    }
+    for (int l = ls; l < lw; ++l)
+      fw_block_level<T, NR>(Fd, l, lw, c, nsub, vs, rows, S, zsel, zt, sh.tv + (l & 1) * FS_WARPS * FS_WSL, pw, tw,
+                            warp, lane);
+    if (warp < nsub) fw_subtree<T, NR>(Fd, lw, (c << (lw - ls)) + warp, vs, rows, S, md, false, zsel, zt, pw, tw, lane);
+    __syncthreads();
+  };
   auto up = [&](int md) {  // leaves first, then the levels upward (W^-1, W^T)
     const int zsel = md == 1 ? 1 : 0, zt = md == 2 ? 1 : 0;
-    fs_leaves<T, NR>(Fd, ls, c, vs, rows, S, md);
-    for (int l = L - 1; l >= ls; --l) fs_local_level<T, NR>(Fd, l, ls, c, vs, rows, S, E - S, zsel, zt, sh);
+    local_up(md, zsel, zt);
     for (int l = ls - 1; l >= 0 && ok; --l)
       ok = fs_global_level<T, NR>(Fd, l, ls, c, vs, rows, S, E, zsel, zt, part, phase & 1, bar, phase, abort_flag,
                               sh);
@@ -621,10 +840,7 @@ __global__ void __launch_bounds__(256, 4) k_sweep_fused(const FactDesc* __restri
     for (int l = 0; l < ls && ok; ++l)
       ok = fs_global_level<T, NR>(Fd, l, ls, c, vs, rows, S, E, zsel, zt, part, phase & 1, bar, phase, abort_flag,
                               sh);
-    if (ok) {
-      for (int l = ls; l < L; ++l) fs_local_level<T, NR>(Fd, l, ls, c, vs, rows, S, E - S, zsel, zt, sh);
-      fs_leaves<T, NR>(Fd, ls, c, vs, rows, S, md);
-    }
+    if (ok) local_down(md, zsel, zt);
   };
   if (mode == 1 || mode == 2) {
     up(mode);

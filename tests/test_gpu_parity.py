@@ -145,7 +145,14 @@ def test_factor_apply_solve_parity(case, indep):
     assert code == fifa.FIFA_OK
     # logdet: both sides backward stable; bound 1e-10 relative plus n * u * cond(W)^2 slack
     assert abs(ld - Fo.logdet) <= 1e-10 * abs(Fo.logdet) + 1e-6
-    kappa = np.linalg.cond(hodlr.dense(Ao)) if n <= 4096 else 1e4
+    if n <= 4096:
+        kappa = np.linalg.cond(hodlr.dense(Ao))
+    else:
+        # M~ = s C~ + I with C~ positive semidefinite and entrywise nonnegative
+        # (SE): lambda_min >= 1 and lambda_max <= 1 + s ||C~||_inf, the row sums
+        # of C~ (plus the compression error, n eps per row)
+        assert sh is not None and kind == 0
+        kappa = 1.0 + sh * (hodlr.matvec(Ho, np.ones(n)).max() + n * eps)
     wtol = max(1e-10, 8 * kappa * 1.1e-16)
     g = np.random.default_rng(9)
     v = g.standard_normal((2, n))
