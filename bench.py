@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--refine-tol", type=float, default=1e-10,
                     help="mixed path: conjugate gradients stop at ||b - M~ x|| <= tol ||b||")
     ap.add_argument("--no-roofline", action="store_true", help="skip the roofline probe")
+    ap.add_argument("--profile-factor", action="store_true",
+                    help="only assemble C~(rho0) of the workload and factor it once (a target for ncu), then exit")
     return ap.parse_args()
 
 
@@ -279,6 +281,9 @@ def gpu_arm(args):
     n = args.n
     x, y = clustered(n, 2 + rank, noise=NOISE)  # replicas: each rank its own chain and data
     stream = torch.cuda.Stream()
+    if args.profile_factor:
+        profile_factor(args, fifa, torch, stream, x)
+        return
     prior_mu = math.log(RHO0)
     vy = float(np.var(y))
 
@@ -420,6 +425,10 @@ def gpu_arm(args):
     value, e2e_value = job_rates(per_head, e2e_s, world)
     if rank != 0:
         return
+    try:
+        kl = kl_report(fifa, torch, leaf, args.nugget)
+    except Exception as exc:  # a report, not part of the timed path
+        kl = {"kl": None, "note": f"failed: {exc}"}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         try:
@@ -446,6 +455,7 @@ def gpu_arm(args):
         "chain": {"rho": float(tr[-1, 3]), "sigma2": float(tr[-1, 1]), "tau2": float(tr[-1, 2]),
                   "accept_rate": float(tr[:, 4].mean())},
         "roofline": roof,
+        "kl": kl,
         "serving": serving,
         "additive": additive,
         "cpu_baseline": cpu,
@@ -453,6 +463,86 @@ def gpu_arm(args):
         "clocks": results[head]["clocks"],
     }
     print(json.dumps(line))
+
+
+def profile_factor(args, fifa, torch, stream, x):
+    """One assembly and one FP64 factorization of C~(rho0) of the workload, with
+    the leaf size the bench uses; nothing else runs (the ncu traffic capture of
+    the factorization kernels)."""
+    from paper_2006_06537_gb300 import autotune
+
+    entry = autotune.load(autotune.workload_key("clustered_se", args.n))
+    leaf = args.leaf or (entry["leaf"] if entry else 32)
+    with torch.cuda.stream(stream):
+        ctx = fifa.Context(leaf_size=leaf, aca_tol=EPS, rank_cap=args.cap, arena_bytes=int(args.arena_gb) << 30,
+                           stream=stream)
+        xd = torch.tensor(x, device="cuda")
+        H = fifa.fifa_assemble(ctx.h, xd, args.n, fifa.fifa_hyper(0, 1.0, RHO0, 1.0, args.nugget))
+        F = fifa.fifa_factor(ctx.h, H)
+        ld, code = fifa.fifa_logdet(ctx.h, F)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_factor": {"n": args.n, "leaf": leaf, "logdet": ld, "status": int(code)}}))
+    fifa.fifa_destroy_fact(ctx.h, F)
+    fifa.fifa_destroy_hmat(ctx.h, H)
+    ctx.close()
+
+
+def dense_ctilde(ex, n):
+    """C~ written out densely from fifa_hmat_export (leaves column-major,
+    level-l bases: U on the left child's rows, V on the right child's)."""
+    L = ex["L"]
+    nodes = [(0, n)]
+    Ct = np.zeros((n, n))
+    for lvl in range(L):
+        for i, (s, e) in enumerate(nodes):
+            h = s + (e - s) // 2
+            r = int(ex["ranks"][(1 << lvl) - 1 + i])
+            U = ex["bases"][lvl, :r, s:h].T
+            V = ex["bases"][lvl, :r, h:e].T
+            Ct[s:h, h:e] = U @ V.T
+            Ct[h:e, s:h] = V @ U.T
+        nodes = [b for s, e in nodes for b in ((s, s + (e - s) // 2), (s + (e - s) // 2, e))]
+    for i, (s, e) in enumerate(nodes):
+        Ct[s:e, s:e] = ex["leaves"][i, :e - s, :e - s].T
+    return Ct
+
+
+def kl_report(fifa, torch, leaf, nugget, n_kl=2048):
+    """KL(P || Q) of Sec. 4.1.3 (Theorem 4.1) for the library's C~ on the
+    workload's recipe at n_kl points: P the exact posterior of f for
+    K = tau2 (C + nugget I), Q the law Algorithm 1 samples for K~ = tau2 C~
+    (covariance K~ M~^-1, M~ = K~ / sigma2 + I, mean that covariance times
+    y / sigma2).  C~ is assembled on the GPU and exported; both Gaussians are
+    formed densely in FP64 here."""
+    x, y = clustered(n_kl, 2, noise=NOISE)
+    tau2, sigma2 = float(np.var(y)), NOISE * NOISE
+    ctx = fifa.Context(leaf_size=leaf, aca_tol=EPS, rank_cap=CAP, arena_bytes=1 << 28)
+    H = fifa.fifa_assemble(ctx.h, torch.tensor(x, device="cuda"), n_kl, fifa.fifa_hyper(0, 1.0, RHO0, 1.0, nugget))
+    ex = fifa.fifa_hmat_export(ctx.h, H)
+    ctx.close()
+    dx = x[:, None] - x[None, :]
+    eye = np.eye(n_kl)
+    K = tau2 * (np.exp(-dx * dx / (2 * RHO0 * RHO0)) + nugget * eye)
+    Kt = tau2 * dense_ctilde(ex, n_kl)
+
+    def post(Km):
+        S = Km @ np.linalg.inv(Km / sigma2 + eye)
+        S = 0.5 * (S + S.T)
+        return S @ y / sigma2, S
+
+    mp, Sp = post(K)
+    mq, Sq = post(Kt)
+    ldq, ldp = np.linalg.slogdet(Sq)[1], np.linalg.slogdet(Sp)[1]
+    tr = float(np.trace(np.linalg.solve(Sq, Sp))) - n_kl
+    dm = mq - mp
+    quad = float(dm @ np.linalg.solve(Sq, dm))
+    e_max = float(np.abs(Kt - K).max())
+    return {"kl": 0.5 * (ldq - ldp + tr + quad), "n": n_kl, "leaf": leaf, "aca_tol": EPS,
+            "workload": f"clustered SE n={n_kl}, 8 clusters, rho={RHO0}, tau2=var(y), sigma2={sigma2:g}, "
+                        f"nugget={nugget:g}",
+            "parts": {"logdet": 0.5 * (ldq - ldp), "trace": 0.5 * tr, "quad": 0.5 * quad},
+            "e_max": e_max, "ranks_max": int(np.max(ex["ranks"])),
+            "note": "C~ from fifa_assemble + fifa_hmat_export; P and Q formed densely in numpy FP64"}
 
 
 def serving_leg(fifa, count, slots, prec, leaf, iters=100, ndraws=20, rate=200.0, budget=120 << 30,
@@ -622,6 +712,13 @@ def apply_work(n, leaves_m, ranks, L, nrhs=2):
     return float(sweep), float(precond), float(mv_bytes), float(mv_flops)
 
 
+def sweep_flops(n, leaves_m, ranks, L, nrhs=2):
+    """FP64 flops of one W^-1 sweep: the leaf triangular solves (m^2 each) and
+    per level the projection and the update (2 r flops per row each)."""
+    rank_rows = n * float(sum(ranks[(1 << l) - 1:(1 << (l + 1)) - 1].mean() for l in range(L)))
+    return float((np.sum(leaves_m ** 2) + 4 * rank_rows) * nrhs)
+
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, summed over every
 # launch of one FP64 factorization of C~(rho0) of this workload at n = 2^20,
 # leaf 32) from one ncu capture; None until the current kernels are captured.
@@ -688,6 +785,10 @@ def roofline_probe(ctx, fifa, torch, stream, xd, n, leaf, nugget):
         return {"bound": "hbm", "op": op, "ms": ms_, "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
                 "bytes": bytes_, "peak_source": src}
 
+    sw = hbm_entry("fused W^-1 sweep, FP64, 2 right-hand sides", ms_sw, sweep_b)
+    sw_f = sweep_flops(n, leaves_m, ranks, L)
+    sw["fp64"] = {"flops": sw_f, "achieved": sw_f / (ms_sw * 1e-3) / 1e12, "peak": peak_fp64, "unit": "TFLOP/s",
+                  "frac": sw_f / (ms_sw * 1e-3) / 1e12 / peak_fp64}
     mv = hbm_entry("fused H-matrix product C~ x, FP64, 2 right-hand sides", ms_mv, mv_b)
     mv["fp64"] = {"flops": mv_f, "achieved": mv_f / (ms_mv * 1e-3) / 1e12, "peak": peak_fp64, "unit": "TFLOP/s",
                   "frac": mv_f / (ms_mv * 1e-3) / 1e12 / peak_fp64}
@@ -698,7 +799,7 @@ def roofline_probe(ctx, fifa, torch, stream, xd, n, leaf, nugget):
             "gflops_leaves_then_levels_deep_to_top": [round(f / 1e9, 4) for f in per_level],
             "rank_mean_per_level": [round(float(ranks[(1 << l) - 1:(1 << (l + 1)) - 1].mean()), 2) for l in range(L)],
             "peak_source": f"FP64 FMA throughput measured in this run (fifa_probe_fp64_fma, {probe_ms:.1f} ms)",
-            "sweep": hbm_entry("fused W^-1 sweep, FP64, 2 right-hand sides", ms_sw, sweep_b),
+            "sweep": sw,
             "matvec": mv,
             "precond_fp32": hbm_entry("FP32 preconditioner solve W32^-T W32^-1 (one fused launch), 2 right-hand sides",
                                       ms_pc, pc_b),
