@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--refine-tol", type=float, default=1e-10,
                     help="mixed path: conjugate gradients stop at ||b - M~ x|| <= tol ||b||")
     ap.add_argument("--no-roofline", action="store_true", help="skip the roofline probe")
+    ap.add_argument("--config-table", action="store_true",
+                    help="time the other single-chain configurations (n = 2048 sine, FP64; n = 131072 Matern-5/2, "
+                         "FP64 and mixed) and print one JSON object, instead of the bench line")
     ap.add_argument("--profile-factor", action="store_true",
                     help="only assemble C~(rho0) of the workload and factor it once (a target for ncu), then exit")
     return ap.parse_args()
@@ -284,6 +287,9 @@ def gpu_arm(args):
     if args.profile_factor:
         profile_factor(args, fifa, torch, stream, x)
         return
+    if args.config_table:
+        config_table(args, fifa, torch, stream)
+        return
     prior_mu = math.log(RHO0)
     vy = float(np.var(y))
 
@@ -407,11 +413,14 @@ def gpu_arm(args):
     roof = None
     if not args.no_roofline:
         with torch.cuda.stream(stream):
-            pctx = fifa.Context(leaf_size=leaf, aca_tol=EPS, rank_cap=CAP, prec=fifa.FIFA_MIXED, refine_max=8,
+            pctx = fifa.Context(leaf_size=leaf, aca_tol=EPS, rank_cap=CAP, prec=fifa.FIFA_FP64,
+                                arena_bytes=min(24, args.arena_gb) << 30, stream=stream)
+            mctx = fifa.Context(leaf_size=leaf, aca_tol=EPS, rank_cap=CAP, prec=fifa.FIFA_MIXED, refine_max=8,
                                 refine_tol=1e-12, arena_bytes=min(24, args.arena_gb) << 30, stream=stream)
             xd = torch.tensor(x, device="cuda")
-        roof = roofline_probe(pctx, fifa, torch, stream, xd, n, leaf, args.nugget)
+        roof = roofline_probe(pctx, mctx, fifa, torch, stream, xd, n, leaf, args.nugget)
         pctx.close()
+        mctx.close()
 
     # serving (continuous batching, p50/p99) and the d-block additive model:
     # measured after the headline, outside its timed region
@@ -485,6 +494,48 @@ def profile_factor(args, fifa, torch, stream, x):
     fifa.fifa_destroy_fact(ctx.h, F)
     fifa.fifa_destroy_hmat(ctx.h, H)
     ctx.close()
+
+
+def config_table(args, fifa, torch, stream):
+    """Iterations/s of the single-chain configurations other than the headline:
+    n = 2048 uniform inputs, y = sin(2 pi x) + N(0, 0.1^2), SE, leaf 64, ACA
+    tolerance 1e-12, FP64, 200 iterations; n = 131072 uniform inputs, y a
+    Matern-5/2 draw (rho = 0.05) + N(0, 0.2^2), Matern-5/2 kernel, leaf 128,
+    tolerance 1e-10, FP64 and mixed, `args.steps` iterations.  CUDA events
+    around the iterations after `args.warmup` untimed ones."""
+    from paper_2006_06537_gb300.inputs import matern_draw, uniform_sine
+
+    def run(x, y, kind, rho, leaf, eps, prec, steps):
+        n = len(x)
+        vy = float(np.var(y))
+        with torch.cuda.stream(stream):
+            ctx = fifa.Context(leaf_size=leaf, aca_tol=eps, rank_cap=CAP, prec=prec, refine_max=8,
+                               refine_tol=args.refine_tol, arena_bytes=8 << 30, stream=stream)
+            ch = fifa.fifa_chain_create(ctx.h, torch.tensor(x, device="cuda"), torch.tensor(y, device="cuda"), n,
+                                        fifa.fifa_hyper(kind, vy, rho, 0.5 * vy, 1e-6),
+                                        fifa.fifa_prior(1.0, 1.0, 1.0, 1.0, math.log(rho), 1.0, 0.2), 0, 0)
+            if args.warmup:
+                fifa.fifa_gibbs_step(ctx.h, ch, args.warmup, None)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            tr = np.zeros((steps, fifa.FIFA_TRACE_FIELDS))
+            fifa.fifa_gibbs_step(ctx.h, ch, steps, tr)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        fifa.fifa_destroy_chain(ctx.h, ch)
+        ctx.close()
+        return {"ms_per_iter": ms, "iters_per_s": 1e3 / ms, "iters_timed": steps,
+                "accept_rate": float(tr[:, 4].mean())}
+
+    out = {}
+    x, y = uniform_sine(2048, 0)
+    out["sine_se_n2048_leaf64_fp64"] = run(x, y, 0, 0.1, 64, 1e-12, fifa.FIFA_FP64, 200)
+    x, y, _ = matern_draw(131072, 1, rho=0.05, var=1.0, noise=0.2)
+    for name, prec in (("fp64", fifa.FIFA_FP64), ("mixed", fifa.FIFA_MIXED)):
+        out[f"matern52_n131072_leaf128_{name}"] = run(x, y, 1, 0.05, 128, 1e-10, prec, args.steps)
+    print(json.dumps({"config_table": out}))
 
 
 def dense_ctilde(ex, n):
@@ -725,11 +776,12 @@ def sweep_flops(n, leaves_m, ranks, L, nrhs=2):
 FACTOR_TRAFFIC_BYTES = None
 
 
-def roofline_probe(ctx, fifa, torch, stream, xd, n, leaf, nugget):
+def roofline_probe(ctx, mctx, fifa, torch, stream, xd, n, leaf, nugget):
     """The FP64 factorization of C~(rho0) of this workload (the dominant
     operation) and the application kernels, each timed alone with CUDA events
-    on the library stream; peaks: the FP64 FMA probe of this run and the
-    measured HBM copy bandwidth."""
+    on the library stream (ctx an FP64 context; mctx a mixed-precision one for
+    the preconditioner and the mixed solve); peaks: the FP64 FMA probe of this
+    run and the measured HBM copy bandwidth."""
     hbm, src = peaks()
     peak_fp64, probe_ms = fifa.fifa_probe_fp64_fma(ctx.h, 20000)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -766,16 +818,19 @@ def roofline_probe(ctx, fifa, torch, stream, xd, n, leaf, nugget):
         w = torch.empty_like(v)
         ms_sw = timed(lambda: fifa.fifa_apply_W(ctx.h, F, 0, 1, v, v, 2), 5)
         ms_mv = timed(lambda: fifa.fifa_matvec(ctx.h, H, v, w, 2), 5)
-        # M~ = s C~ + I at the chain's s (tau2 / sigma2 ~ 0.5 / 0.05^2) and its
-        # mixed factor: the FP32 preconditioner solve and a whole mixed solve
-        M = fifa.fifa_shift_scale(ctx.h, H, 200.0)
-        FM = fifa.fifa_factor(ctx.h, M)
-        ms_pc = timed(lambda: fifa.fifa_apply_precond(ctx.h, FM, v, w, 2), 5)
-        ms_solve = timed(lambda: fifa.fifa_solve(ctx.h, FM, v, w, 2), 3)
-        fifa.fifa_destroy_fact(ctx.h, FM)
-        fifa.fifa_destroy_hmat(ctx.h, M)
         fifa.fifa_destroy_fact(ctx.h, F)
         fifa.fifa_destroy_hmat(ctx.h, H)
+        # the mixed context: M~ = s C~ + I at the chain's s (tau2 / sigma2 ~
+        # 0.5 / 0.05^2) with its kept factor: the FP32 preconditioner solve and
+        # a whole mixed solve
+        Hm = fifa.fifa_assemble(mctx.h, xd, n, fifa.fifa_hyper(0, 1.0, RHO0, 1.0, nugget))
+        M = fifa.fifa_shift_scale(mctx.h, Hm, 200.0)
+        FM = fifa.fifa_factor(mctx.h, M)
+        ms_pc = timed(lambda: fifa.fifa_apply_precond(mctx.h, FM, v, w, 2), 5)
+        ms_solve = timed(lambda: fifa.fifa_solve(mctx.h, FM, v, w, 2), 3)
+        fifa.fifa_destroy_fact(mctx.h, FM)
+        fifa.fifa_destroy_hmat(mctx.h, M)
+        fifa.fifa_destroy_hmat(mctx.h, Hm)
     flops, L, per_level, leaves_m = factor_work(n, leaf, ranks)
     sweep_b, pc_b, mv_b, mv_f = apply_work(n, leaves_m, ranks, L)
     achieved = flops / (ms * 1e-3) / 1e12
