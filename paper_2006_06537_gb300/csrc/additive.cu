@@ -70,6 +70,10 @@ struct fifa_additive {
   HmatDesc* h_desc[2] = {nullptr, nullptr};  // d each: current / proposal C~
   char* scratch = nullptr;      // d * scratch_stride
   size_t scratch_stride = 0;
+  // the blocks' tau2 / rho sweeps of f as one launch (sweep_batch_config;
+  // fsb_ls < 0: one sweep per block): the blocks' copies of f
+  double** tmp_list = nullptr;  // d device pointers
+  int fsb_ls = -1, fsb_rows = 0;
 };
 
 // Enqueue fn(k) for every block k, as concurrent branches forked from and
@@ -145,21 +149,41 @@ static fifa_status additive_sweep_enqueue(fifa_ctx* ctx, fifa_additive* A) {
         launch_add_sigma2(A->g, A->blk_dev, d, ctx->stream) != cudaSuccess)
       st = FIFA_ERR_CUDA;
   }
-  // tau2_k and rho_k of every block: the proposals' factorizations batched
+  // tau2_k and rho_k of every block: the blocks' sweeps of f, the proposals'
+  // assemblies and their factorizations each in shared launches for all d
+  // blocks (they do not depend on one another)
   if (st == FIFA_OK && A->fm_desc) {
+    Plan* P = A->blk[0]->plan;
+    auto sweeps = [&](int q) -> fifa_status {  // tmp_k = W_{C,k}^-1 f_k with the current (0) / proposal (1) factors
+      for (int k = 0; k < d; ++k) {
+        fifa_chain* ch = A->blk[k];
+        if (cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+          return FIFA_ERR_CUDA;
+      }
+      if (A->fsb_ls >= 0)
+        return sweep_enqueue_batched(ctx, P, A->f_desc[q], A->tmp_list, d, 1, A->fsb_ls, A->fsb_rows, A->scratch,
+                                     A->scratch_stride);
+      for (int k = 0; k < d; ++k) {
+        fifa_chain* ch = A->blk[k];
+        ctx->active_scratch = ch->scratch;
+        fifa_status e = sweep_enqueue(ctx, ch->F[q], 0, 1, ch->tmp, 1);
+        if (e != FIFA_OK) return e;
+      }
+      return FIFA_OK;
+    };
+    st = sweeps(0);
     for (int k = 0; k < d && st == FIFA_OK; ++k) {
       fifa_chain* ch = A->blk[k];
       ctx->active_scratch = ch->scratch;
-      Scratch S = carve(ctx, ch->plan);
-      st = chain_phase_hyper_pre(ctx, ch, S);
+      st = chain_hyper_tau2_propose(ctx, ch, carve(ctx, P));
     }
-    if (st == FIFA_OK)
-      st = fact_enqueue_batched(ctx, A->blk[0]->plan, A->f_desc[1], A->h_desc[1], d, A->scratch, A->scratch_stride);
+    if (st == FIFA_OK) st = hmat_assemble_batched(ctx, P, A->h_desc[1], d, A->scratch, A->scratch_stride);
+    if (st == FIFA_OK) st = fact_enqueue_batched(ctx, P, A->f_desc[1], A->h_desc[1], d, A->scratch, A->scratch_stride);
+    if (st == FIFA_OK) st = sweeps(1);
     for (int k = 0; k < d && st == FIFA_OK; ++k) {
       fifa_chain* ch = A->blk[k];
       ctx->active_scratch = ch->scratch;
-      Scratch S = carve(ctx, ch->plan);
-      st = chain_phase_hyper_post(ctx, ch, S);
+      st = chain_hyper_mh(ctx, ch, carve(ctx, P));
     }
   } else if (st == FIFA_OK) {
     st = for_blocks(ctx, A, [&](int k) {
@@ -271,6 +295,13 @@ extern "C" fifa_status fifa_additive_create(fifa_ctx* ctx, const double* X_dev, 
       }
       ch->scratch = A->scratch + (size_t)k * A->scratch_stride;
     }
+    // the blocks' copies of f, for the batched sweeps
+    double* tl[FIFA_ADDITIVE_MAX_D] = {};
+    for (int k = 0; k < d; ++k) tl[k] = A->blk[k]->tmp;
+    if (!(A->tmp_list = (double**)ctx->arena.alloc(sizeof(double*) * d))) return fail(FIFA_ERR_OOM);
+    CK(cudaMemcpyAsync(A->tmp_list, tl, sizeof(double*) * d, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    if (!sweep_batch_config(ctx, P, d, &A->fsb_ls, &A->fsb_rows)) A->fsb_ls = -1;
   }
   ChainDev* ptrs[FIFA_ADDITIVE_MAX_D] = {};
   for (int k = 0; k < d; ++k) ptrs[k] = A->blk[k]->dev;
@@ -442,6 +473,7 @@ extern "C" void fifa_destroy_additive(fifa_ctx* ctx, fifa_additive* A) {
     ctx->arena.release(A->h_desc[q]);
   }
   ctx->arena.release(A->scratch);
+  ctx->arena.release(A->tmp_list);
   for (int k = 0; k < FIFA_ADDITIVE_MAX_D; ++k) {
     if (A->side[k]) cudaStreamDestroy(A->side[k]);
     if (A->ev_join[k]) cudaEventDestroy(A->ev_join[k]);

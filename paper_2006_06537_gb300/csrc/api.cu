@@ -562,6 +562,37 @@ fifa_status hmat_assemble_enqueue(fifa_ctx* ctx, fifa_hmat* H) {
   return FIFA_OK;
 }
 
+fifa_status hmat_assemble_batched(fifa_ctx* ctx, Plan* P, HmatDesc* H0, int nprob, void* scratch0, size_t sstride) {
+  void* saved = ctx->active_scratch;
+  ctx->active_scratch = scratch0;
+  Scratch S = carve(ctx, P);
+  ctx->active_scratch = saved;
+  cudaStream_t s = ctx->stream;
+  CK(launch_prep_hmat(H0, P->nnodes, s, nprob));
+  CK(launch_leaf_assemble(H0, P->nleaf, s, nprob));
+  if (P->aca_ncoop > 0) {
+    if ((int64_t)P->aca_ncoop * nprob <= ctx->aca_coresident) {  // every problem's groups co-resident at once
+      CK(cudaMemset2DAsync(S.aca_bar, sstride, 0, sizeof(unsigned int) * P->aca_ncoop, nprob, s));
+      CK(cudaMemset2DAsync(S.flags, sstride, 0, sizeof(int), nprob, s));
+      CK(launch_aca(H0, P->aca_work, P->aca_ncoop, true, S.aca_part, S.aca_bar, S.flags, s, nprob, sstride));
+    } else {
+      for (int q = 0; q < nprob; ++q) {  // one grouped launch per problem, each filling the GPU
+        const size_t off = (size_t)q * sstride;
+        unsigned int* bar = (unsigned int*)((char*)S.aca_bar + off);
+        int* flags = (int*)((char*)S.flags + off);
+        CK(cudaMemsetAsync(bar, 0, sizeof(unsigned int) * P->aca_ncoop, s));
+        CK(cudaMemsetAsync(flags, 0, sizeof(int), s));
+        CK(launch_aca(H0 + q, P->aca_work, P->aca_ncoop, true, (ArgMax*)((char*)S.aca_part + off), bar, flags, s));
+      }
+    }
+  }
+  if (P->aca_nsolo > 0)
+    CK(launch_aca(H0, P->aca_work + P->aca_ncoop, P->aca_nsolo, false, S.aca_part, S.aca_bar, S.flags, s, nprob,
+                  sstride));
+  if (P->aca_nwarp > 0) CK(launch_aca_warp(H0, P->aca_work + P->aca_ncoop + P->aca_nsolo, P->aca_nwarp, s, nprob));
+  return FIFA_OK;
+}
+
 static double kernel_const(int kind, double rho) { return kind == 0 ? 0.5 / (rho * rho) : sqrt(5.0) / rho; }
 
 extern "C" fifa_status fifa_assemble(fifa_ctx* ctx, const double* x_dev, int64_t n, const fifa_hyper* hyper,
@@ -833,6 +864,33 @@ extern "C" fifa_status fifa_logdet(fifa_ctx* ctx, const fifa_fact* F, double* ou
 // ---------------------------------------------------------------------------
 // Sweeps, solve, matvec
 // ---------------------------------------------------------------------------
+bool sweep_batch_config(fifa_ctx* ctx, const Plan* P, int nprob, int* ls, int* rows) {
+  if (P->fs_ls < 0 || nprob < 1) return false;
+  for (int k = P->fs_ls; k >= 0; --k) {
+    int r = 0;
+    for (int i = 0; i < (1 << k); ++i) r = std::max(r, P->bnd_host[bnd_off(k) + i + 1] - P->bnd_host[bnd_off(k) + i]);
+    if ((int64_t)sweep_fused_coresident(0, r, ctx->opts.rank_cap) >= ((int64_t)nprob << k)) {
+      *ls = k;
+      *rows = r;
+      return true;
+    }
+  }
+  return false;
+}
+
+fifa_status sweep_enqueue_batched(fifa_ctx* ctx, Plan* P, const FactDesc* F0, double* const* vlist, int nprob,
+                                  int mode, int ls, int rows, void* scratch0, size_t sstride) {
+  void* saved = ctx->active_scratch;
+  ctx->active_scratch = scratch0;
+  Scratch S = carve(ctx, P);
+  ctx->active_scratch = saved;
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemset2DAsync(S.fs_bar, sstride, 0, sizeof(unsigned int), nprob, s));
+  CK(cudaMemset2DAsync(S.flags, sstride, 0, sizeof(int), nprob, s));
+  CK(launch_sweep_fused_batched(F0, ls, rows, vlist, nprob, mode, S.fs_part, S.fs_bar, S.flags, sstride, s));
+  return FIFA_OK;
+}
+
 fifa_status sweep_enqueue_desc(fifa_ctx* ctx, Plan* P, const FactDesc* Fdev, int prec, int mode, double* v, int nrhs,
                                const int* active) {
   Scratch S = carve(ctx, P);

@@ -61,30 +61,41 @@ fifa_status chain_phase_sigma2(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) 
 // chain's iteration counter).
 // Phase 3a: q, tau2 | f, rho, the proposal rho' and the assembly of C~(rho').
 fifa_status chain_phase_hyper_pre(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
-  const int64_t n = ch->plan->n;
-  cudaStream_t s = ctx->stream;
-  ChainDev* c = ch->dev;
-  if (cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+  if (cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * ch->plan->n, cudaMemcpyDeviceToDevice, ctx->stream) !=
+      cudaSuccess)
     return FIFA_ERR_CUDA;
   fifa_status st = sweep_enqueue(ctx, ch->F[0], 0, 1, ch->tmp, 1);
-  if (st != FIFA_OK) return st;
-  if (launch_sumsq(ch->tmp, nullptr, n, S.red, &c->q, s) != cudaSuccess) return FIFA_ERR_CUDA;
+  if (st == FIFA_OK) st = chain_hyper_tau2_propose(ctx, ch, S);
+  return st == FIFA_OK ? hmat_assemble_enqueue(ctx, ch->H[1]) : st;
+}
+
+// Phase 3a's middle: q = |W_C^-1 f|^2 from the swept copy of f in tmp, tau2 |
+// f, rho, and the proposal rho' (written into the proposal's descriptor).
+fifa_status chain_hyper_tau2_propose(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
+  cudaStream_t s = ctx->stream;
+  ChainDev* c = ch->dev;
+  if (launch_sumsq(ch->tmp, nullptr, ch->plan->n, S.red, &c->q, s) != cudaSuccess) return FIFA_ERR_CUDA;
   if (launch_chain_tau2(c, s) != cudaSuccess) return FIFA_ERR_CUDA;
   if (launch_chain_propose(c, ch->H[1]->dev, s) != cudaSuccess) return FIFA_ERR_CUDA;
-  return hmat_assemble_enqueue(ctx, ch->H[1]);
+  return FIFA_OK;
 }
 
 // Phase 3c (after the factorization of C~(rho'), phase 3b): q' and the
 // Metropolis step on log rho (advances the chain's iteration counter).
 fifa_status chain_phase_hyper_post(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
-  const int64_t n = ch->plan->n;
-  cudaStream_t s = ctx->stream;
-  ChainDev* c = ch->dev;
-  if (cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+  if (cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * ch->plan->n, cudaMemcpyDeviceToDevice, ctx->stream) !=
+      cudaSuccess)
     return FIFA_ERR_CUDA;
   fifa_status st = sweep_enqueue(ctx, ch->F[1], 0, 1, ch->tmp, 1);
-  if (st != FIFA_OK) return st;
-  if (launch_sumsq(ch->tmp, nullptr, n, S.red, &c->q_prop, s) != cudaSuccess) return FIFA_ERR_CUDA;
+  return st == FIFA_OK ? chain_hyper_mh(ctx, ch, S) : st;
+}
+
+// Phase 3c's end: q' = |W_C'^-1 f|^2 from the swept copy of f in tmp and the
+// Metropolis step.
+fifa_status chain_hyper_mh(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
+  cudaStream_t s = ctx->stream;
+  ChainDev* c = ch->dev;
+  if (launch_sumsq(ch->tmp, nullptr, ch->plan->n, S.red, &c->q_prop, s) != cudaSuccess) return FIFA_ERR_CUDA;
   if (launch_chain_mh(c, ch->H[0]->dev, ch->H[1]->dev, ch->F[0]->dev, ch->F[1]->dev, ch->FM->dev, s) != cudaSuccess)
     return FIFA_ERR_CUDA;
   return FIFA_OK;

@@ -103,6 +103,18 @@ Scratch carve(fifa_ctx* ctx, Plan* P);
 fifa_status ensure_scratch(fifa_ctx* ctx, Plan* P);
 fifa_status hmat_alloc(fifa_ctx* ctx, Plan* P, int kind, fifa_hmat** out);
 fifa_status hmat_assemble_enqueue(fifa_ctx* ctx, fifa_hmat* H);
+// Assemble nprob H-matrices of plan P (descriptor array H0) in shared launches;
+// problem q's scratch at scratch0 + q * sstride bytes.
+fifa_status hmat_assemble_batched(fifa_ctx* ctx, Plan* P, HmatDesc* H0, int nprob, void* scratch0, size_t sstride);
+// Grid of a fused sweep of nprob factors of plan P in one launch: 2^ls CTAs per
+// problem of rows rows each; false if the plan has no fused sweep or nprob
+// problems' CTAs cannot all be co-resident.
+bool sweep_batch_config(fifa_ctx* ctx, const Plan* P, int nprob, int* ls, int* rows);
+// FP64 sweeps (mode as launch_sweep_fused) of nprob factors of plan P
+// (descriptor array F0) on one vector each (device array vlist), in one launch
+// configured by sweep_batch_config; scratch as hmat_assemble_batched.
+fifa_status sweep_enqueue_batched(fifa_ctx* ctx, Plan* P, const FactDesc* F0, double* const* vlist, int nprob,
+                                  int mode, int ls, int rows, void* scratch0, size_t sstride);
 // with32: also allocate the FP32 copy (a mixed-precision factor of M~).
 fifa_status fact_alloc(fifa_ctx* ctx, Plan* P, int with32, fifa_fact** out);
 // Point the factor's skip flag at a device int (nullable) and upload its descriptor.
@@ -132,7 +144,7 @@ fifa_status sample_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* W
                            int* iters_dev = nullptr, const fifa_hmat* op = nullptr);
 
 // vector kernels (k_vec.cu)
-cudaError_t launch_prep_hmat(HmatDesc* H, int nnodes, cudaStream_t st);
+cudaError_t launch_prep_hmat(HmatDesc* H, int nnodes, cudaStream_t st, int nprob = 1);
 cudaError_t launch_prep_fact(FactDesc* F, const HmatDesc* H, int nnodes, cudaStream_t st, int nprob = 1);
 cudaError_t launch_sumsq(const double* a, const double* b, int64_t n, double* part, double* out, cudaStream_t st);
 cudaError_t launch_axpy(double a, const double* x, double* y, int64_t n, cudaStream_t st);

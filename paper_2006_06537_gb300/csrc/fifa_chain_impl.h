@@ -41,6 +41,10 @@ fifa_status chain_phase_hyper(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
 // factorization of C~(rho') into F[1], post (q' and the Metropolis step)
 fifa_status chain_phase_hyper_pre(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
 fifa_status chain_phase_hyper_post(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
+// The parts of phases 3a / 3c after their sweep of the copy of f in tmp (the
+// additive model runs the blocks' sweeps in one batched launch).
+fifa_status chain_hyper_tau2_propose(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
+fifa_status chain_hyper_mh(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
 
 // Serving helpers.  chain_run_collect runs `iters` iterations (graph replay)
 // and gathers on the device: mean_acc = sum of the conditional means

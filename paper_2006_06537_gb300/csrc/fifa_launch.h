@@ -4,11 +4,14 @@
 #include <stddef.h>
 #include "fifa_common.cuh"
 
-cudaError_t launch_leaf_assemble(const HmatDesc* Hd, int nleaf, cudaStream_t st);
+// Assembly launchers take nprob problems of one plan (descriptor arrays,
+// blockIdx.y); the grouped ACA's partials / barriers / abort flags of problem q
+// sit q * pstride bytes after problem 0's.
+cudaError_t launch_leaf_assemble(const HmatDesc* Hd, int nleaf, cudaStream_t st, int nprob = 1);
 #define ACA_WARP_MAX 128  // largest side of a block that the warp-per-block ACA takes
-cudaError_t launch_aca_warp(const HmatDesc* Hd, const int4* work, int nwork, cudaStream_t st);
+cudaError_t launch_aca_warp(const HmatDesc* Hd, const int4* work, int nwork, cudaStream_t st, int nprob = 1);
 cudaError_t launch_aca(const HmatDesc* Hd, const int4* work, int ncta, bool cooperative, ArgMax* part,
-                       unsigned int* bar, int* abort_flag, cudaStream_t st);
+                       unsigned int* bar, int* abort_flag, cudaStream_t st, int nprob = 1, size_t pstride = 0);
 int aca_max_coresident_ctas();
 
 size_t leaf_factor_smem(int Bm, int L, int cap, int prec);
@@ -48,6 +51,11 @@ int sweep_fused_coresident(int prec, int rows, int cap);
 cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, int cap, double* v, int nrhs,
                                int mode, double* part, unsigned int* bar, int* abort_flag, cudaStream_t st,
                                const int* active = nullptr);
+// nprob FP64 factors of one plan in one launch (one right-hand side each at
+// vlist[q]; per-problem partials / barrier / abort flag pstride bytes apart)
+cudaError_t launch_sweep_fused_batched(const FactDesc* Fd, int ls, int rows, double* const* vlist, int nprob,
+                                       int mode, double* part, unsigned int* bar, int* abort_flag, size_t pstride,
+                                       cudaStream_t st);
 // Fused H-matrix product (one cooperative launch of 2^ls CTAs, rows <= 4096).
 // part: 2^ls * ls * MV_PART_STRIDE doubles; bar zeroed before.
 #define MV_FUSED_ROWS_MAX 4096

@@ -760,14 +760,25 @@ __device__ void fw_block_level(const FactDesc* __restrict__ Fd, int l, int lw, i
 // copy (the global v stays FP64, converted on load and store).  active
 // (nullable): when *active == 0 the launch does nothing (a converged
 // iteration).  Dynamic shared memory: nrhs * rows entries of T (rows >= the
-// longest level-ls node), then the FsShared arrays.
+// longest level-ls node), then the FsShared arrays.  vlist (nullable): several
+// factors of one plan in one launch, problem blockIdx.y: its descriptor
+// Fd[blockIdx.y], its vector vlist[blockIdx.y], its partials, barrier and
+// abort flag pstride bytes after the previous problem's.
 template <typename T, int NR>
 __global__ void __launch_bounds__(256, 4) k_sweep_fused(const FactDesc* __restrict__ Fd, double* __restrict__ v,
                                                         int mode, int ls, int rows, double* __restrict__ part,
                                                         unsigned int* __restrict__ bar, int* __restrict__ abort_flag,
-                                                        const int* __restrict__ active) {
+                                                        const int* __restrict__ active, double* const* vlist,
+                                                        size_t pstride) {
   constexpr int nrhs = NR;
   if (active && *active == 0) return;
+  if (vlist) {
+    Fd += blockIdx.y;
+    v = vlist[blockIdx.y];
+    part = (double*)((char*)part + blockIdx.y * pstride);
+    bar = (unsigned int*)((char*)bar + blockIdx.y * pstride);
+    abort_flag = (int*)((char*)abort_flag + blockIdx.y * pstride);
+  }
   extern __shared__ __align__(16) unsigned char fs_smem[];
   T* vs = (T*)fs_smem;
   FsShared<T> sh;
@@ -810,11 +821,14 @@ __global__ void __launch_bounds__(256, 4) k_sweep_fused(const FactDesc* __restri
       for (int l = L - 1; l >= ls; --l) fs_local_level<T, NR>(Fd, l, ls, c, vs, rows, S, E - S, zsel, zt, sh);
       return;
     }
-    if (warp < nsub) fw_subtree<T, NR>(Fd, lw, (c << (lw - ls)) + warp, vs, rows, S, md, true, zsel, zt, pw, tw, lane);
-    for (int l = lw - 1; l >= ls; --l)
-      fw_block_level<T, NR>(Fd, l, lw, c, nsub, vs, rows, S, zsel, zt, sh.tv + (l & 1) * FS_WARPS * FS_WSL, pw, tw,
-                            warp, lane);
-    __syncthreads();
+    if constexpr (FS_WARP_OWNED(T)) {
+      if (warp < nsub)
+        fw_subtree<T, NR>(Fd, lw, (c << (lw - ls)) + warp, vs, rows, S, md, true, zsel, zt, pw, tw, lane);
+      for (int l = lw - 1; l >= ls; --l)
+        fw_block_level<T, NR>(Fd, l, lw, c, nsub, vs, rows, S, zsel, zt, sh.tv + (l & 1) * FS_WARPS * FS_WSL, pw, tw,
+                              warp, lane);
+      __syncthreads();
+    }
   };
   auto local_down = [&](int md, int zsel, int zt) {
     if (!fast) {
@@ -822,11 +836,14 @@ __global__ void __launch_bounds__(256, 4) k_sweep_fused(const FactDesc* __restri
       fs_leaves<T, NR>(Fd, ls, c, vs, rows, S, md);
       return;
     }
-    for (int l = ls; l < lw; ++l)
-      fw_block_level<T, NR>(Fd, l, lw, c, nsub, vs, rows, S, zsel, zt, sh.tv + (l & 1) * FS_WARPS * FS_WSL, pw, tw,
-                            warp, lane);
-    if (warp < nsub) fw_subtree<T, NR>(Fd, lw, (c << (lw - ls)) + warp, vs, rows, S, md, false, zsel, zt, pw, tw, lane);
-    __syncthreads();
+    if constexpr (FS_WARP_OWNED(T)) {
+      for (int l = ls; l < lw; ++l)
+        fw_block_level<T, NR>(Fd, l, lw, c, nsub, vs, rows, S, zsel, zt, sh.tv + (l & 1) * FS_WARPS * FS_WSL, pw, tw,
+                              warp, lane);
+      if (warp < nsub)
+        fw_subtree<T, NR>(Fd, lw, (c << (lw - ls)) + warp, vs, rows, S, md, false, zsel, zt, pw, tw, lane);
+      __syncthreads();
+    }
   };
   auto up = [&](int md) {  // leaves first, then the levels upward (W^-1, W^T)
     const int zsel = md == 1 ? 1 : 0, zt = md == 2 ? 1 : 0;
@@ -886,10 +903,31 @@ int sweep_fused_coresident(int prec, int rows, int cap) {
 template <typename T, int NR>
 static cudaError_t launch_sweep_fused_t(cudaLaunchConfig_t& cfg, const FactDesc* Fd, double* v, int mode, int ls,
                                         int rows, double* part, unsigned int* bar, int* abort_flag,
-                                        const int* active, int prec) {
+                                        const int* active, int prec, double* const* vlist = nullptr,
+                                        size_t pstride = 0) {
   cudaFuncSetAttribute(k_sweep_fused<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sweep_fused_smem(rows, SW_RHS_MAX, prec));
-  return cudaLaunchKernelEx(&cfg, k_sweep_fused<T, NR>, Fd, v, mode, ls, rows, part, bar, abort_flag, active);
+  return cudaLaunchKernelEx(&cfg, k_sweep_fused<T, NR>, Fd, v, mode, ls, rows, part, bar, abort_flag, active, vlist,
+                            pstride);
+}
+
+// nprob FP64 factors of one plan (descriptor array Fd), one right-hand side
+// each at vlist[q], in one cooperative launch of 2^ls x nprob CTAs.
+cudaError_t launch_sweep_fused_batched(const FactDesc* Fd, int ls, int rows, double* const* vlist, int nprob,
+                                       int mode, double* part, unsigned int* bar, int* abort_flag, size_t pstride,
+                                       cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1u << ls, nprob);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = sweep_fused_smem(rows, 1, 0);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return launch_sweep_fused_t<double, 1>(cfg, Fd, nullptr, mode, ls, rows, part, bar, abort_flag, nullptr, 0, vlist,
+                                         pstride);
 }
 
 cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, int cap, double* v, int nrhs,

@@ -10,6 +10,7 @@
 // a shared-memory tile so both stores stay coalesced.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_leaf_assemble(const HmatDesc* __restrict__ Hd) {
+  Hd += blockIdx.y;  // problem of a batched launch (descriptor arrays)
   const int leaf = blockIdx.x;
   const int L = Hd->L, Bm = Hd->Bm, kind = Hd->kind;
   const double kc = Hd->kc, nug = Hd->nugget;
@@ -76,7 +77,13 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(const HmatDesc* __restric
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 4) k_aca(const HmatDesc* __restrict__ Hd, const int4* __restrict__ work,
                                               ArgMax* __restrict__ part, unsigned int* __restrict__ bar,
-                                              int* __restrict__ abort_flag) {
+                                              int* __restrict__ abort_flag, size_t pstride) {
+  // problem of a batched launch: its descriptor, its partials, barriers and
+  // abort flag pstride bytes after the previous problem's
+  Hd += blockIdx.y;
+  part = (ArgMax*)((char*)part + blockIdx.y * pstride);
+  bar = (unsigned int*)((char*)bar + blockIdx.y * pstride);
+  abort_flag = (int*)((char*)abort_flag + blockIdx.y * pstride);
   const int4 w = work[blockIdx.x];
   const int lvl = w.x, bi = w.y, g = w.z, G = w.w;
   const int base = blockIdx.x - g;
@@ -217,6 +224,7 @@ __device__ __forceinline__ ArgMax warp_argmax_all(ArgMax a) {
 
 __global__ void __launch_bounds__(256, 3) k_aca_warp(const HmatDesc* __restrict__ Hd, const int4* __restrict__ work,
                                                   int nwork) {
+  Hd += blockIdx.y;  // problem of a batched launch (descriptor arrays)
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.x * 8 + wl;
   if (item >= nwork) return;  // whole warp
@@ -308,22 +316,22 @@ __global__ void __launch_bounds__(256, 3) k_aca_warp(const HmatDesc* __restrict_
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
-cudaError_t launch_aca_warp(const HmatDesc* Hd, const int4* work, int nwork, cudaStream_t st) {
+cudaError_t launch_aca_warp(const HmatDesc* Hd, const int4* work, int nwork, cudaStream_t st, int nprob) {
   if (nwork <= 0) return cudaSuccess;
-  k_aca_warp<<<(nwork + 7) / 8, 256, 0, st>>>(Hd, work, nwork);
+  k_aca_warp<<<dim3((nwork + 7) / 8, nprob), 256, 0, st>>>(Hd, work, nwork);
   return cudaGetLastError();
 }
 
-cudaError_t launch_leaf_assemble(const HmatDesc* Hd, int nleaf, cudaStream_t st) {
-  k_leaf_assemble<<<nleaf, 256, 0, st>>>(Hd);
+cudaError_t launch_leaf_assemble(const HmatDesc* Hd, int nleaf, cudaStream_t st, int nprob) {
+  k_leaf_assemble<<<dim3(nleaf, nprob), 256, 0, st>>>(Hd);
   return cudaGetLastError();
 }
 
 cudaError_t launch_aca(const HmatDesc* Hd, const int4* work, int ncta, bool cooperative, ArgMax* part,
-                       unsigned int* bar, int* abort_flag, cudaStream_t st) {
+                       unsigned int* bar, int* abort_flag, cudaStream_t st, int nprob, size_t pstride) {
   if (ncta <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(ncta);
+  cfg.gridDim = dim3(ncta, nprob);
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
@@ -332,7 +340,7 @@ cudaError_t launch_aca(const HmatDesc* Hd, const int4* work, int ncta, bool coop
   attr[0].val.cooperative = cooperative ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_aca, Hd, work, part, bar, abort_flag);
+  return cudaLaunchKernelEx(&cfg, k_aca, Hd, work, part, bar, abort_flag, pstride);
 }
 
 int aca_max_coresident_ctas() {

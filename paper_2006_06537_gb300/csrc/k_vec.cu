@@ -132,6 +132,7 @@ cudaError_t launch_alg1_finish(const double* wr, const double* Cr, double* f, do
 // factor and zero its status.
 // ---------------------------------------------------------------------------
 __global__ void k_prep_hmat(HmatDesc* __restrict__ H, int nnodes) {
+  H += blockIdx.y;  // problem of a batched launch (descriptor arrays)
   int* rk = H->rank;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nnodes; i += gridDim.x * blockDim.x) rk[i] = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) *H->status = 0;
@@ -147,8 +148,8 @@ __global__ void k_prep_fact(FactDesc* __restrict__ F, const HmatDesc* __restrict
   if (blockIdx.x == 0 && threadIdx.x == 0) *F->status = 0;
 }
 
-cudaError_t launch_prep_hmat(HmatDesc* H, int nnodes, cudaStream_t st) {
-  k_prep_hmat<<<grid_for(nnodes > 0 ? nnodes : 1), 256, 0, st>>>(H, nnodes);
+cudaError_t launch_prep_hmat(HmatDesc* H, int nnodes, cudaStream_t st, int nprob) {
+  k_prep_hmat<<<dim3(grid_for(nnodes > 0 ? nnodes : 1), nprob), 256, 0, st>>>(H, nnodes);
   return cudaGetLastError();
 }
 cudaError_t launch_prep_fact(FactDesc* F, const HmatDesc* H, int nnodes, cudaStream_t st, int nprob) {
