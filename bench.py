@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests of the serving stream to run (0 = skip the serving leg)")
     ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-wide-min", type=int, default=1 << 15,
+                    help="requests with n >= this run on the server's one wide worker (CTA groups, fused sweeps)")
     ap.add_argument("--paths", default="fp64,mixed", help="chain precisions to time (comma list of fp64, mixed)")
     ap.add_argument("--additive-sweeps", type=int, default=10, help="0 = skip the d-block additive leg")
     ap.add_argument("--arena-gb", type=int, default=40, help="device arena of each chain context (GB)")
@@ -426,7 +428,8 @@ def gpu_arm(args):
     # measured after the headline, outside its timed region
     serving = additive = None
     if rank == 0 and args.serve_requests > 0:
-        serving = serving_leg(fifa, args.serve_requests, args.serve_slots, fifa.FIFA_MIXED, 32)
+        serving = serving_leg(fifa, args.serve_requests, args.serve_slots, fifa.FIFA_MIXED, 32,
+                              wide_min_n=args.serve_wide_min)
     if rank == 0 and args.additive_sweeps > 0:
         additive = additive_leg(fifa, torch, args.additive_sweeps, 32)
 
@@ -770,10 +773,12 @@ def sweep_flops(n, leaves_m, ranks, L, nrhs=2):
     return float((np.sum(leaves_m ** 2) + 4 * rank_rows) * nrhs)
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, summed over every
-# launch of one FP64 factorization of C~(rho0) of this workload at n = 2^20,
-# leaf 32) from one ncu capture; None until the current kernels are captured.
-FACTOR_TRAFFIC_BYTES = None
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, summed over the 44
+# launches of one FP64 factorization of C~(rho0) of this workload at n = 2^20,
+# leaf 32: 6.42 GB read + 4.07 GB written) from one ncu capture of
+# `bench.py --profile-factor` on the current factorization kernels.
+FACTOR_TRAFFIC_BYTES = 10.49e9
+FACTOR_TRAFFIC_CONFIG = (1 << 20, 32)  # (n, leaf) it was captured at
 
 
 def roofline_probe(ctx, mctx, fifa, torch, stream, xd, n, leaf, nugget):
@@ -850,7 +855,7 @@ def roofline_probe(ctx, mctx, fifa, torch, stream, xd, n, leaf, nugget):
     return {"bound": "alu", "op": "FP64 HODLR factorization of C~ (leaf Cholesky + TRSM, per-level CholeskyQR2, "
                                   "capacitance, ancestor update)",
             "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s", "frac": achieved / peak_fp64,
-            "traffic": FACTOR_TRAFFIC_BYTES, "ms": ms, "flops": flops, "rank_mean": float(ranks.mean()), "levels": L,
+            "traffic": FACTOR_TRAFFIC_BYTES if (n, leaf) == FACTOR_TRAFFIC_CONFIG else None, "ms": ms, "flops": flops, "rank_mean": float(ranks.mean()), "levels": L,
             "gflops_leaves_then_levels_deep_to_top": [round(f / 1e9, 4) for f in per_level],
             "rank_mean_per_level": [round(float(ranks[(1 << l) - 1:(1 << (l + 1)) - 1].mean()), 2) for l in range(L)],
             "peak_source": f"FP64 FMA throughput measured in this run (fifa_probe_fp64_fma, {probe_ms:.1f} ms)",
