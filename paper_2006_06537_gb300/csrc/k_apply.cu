@@ -586,7 +586,7 @@ __device__ void fs_leaves(const FactDesc* __restrict__ Fd, int ls, int c, T* vs,
 // barriers they replace (the FP64 W^-1 sweep at n = 2^20: 1.06 ms block-wide,
 // 1.21 ms warp-owned).
 // ---------------------------------------------------------------------------
-#define FS_WARP_OWNED(T) (sizeof(T) == 4)
+#define FS_WARP_OWNED(T, NR) (sizeof(T) == 4)
 #define FS_WL 3
 #define FS_WSL 32                                           // p or t entries per warp: 2 r nrhs <= 32
 #define FS_RFAST(T, NR) ((sizeof(T) == 4 ? 16 : 8) / (NR))  // ranks the warp path takes
@@ -619,33 +619,35 @@ template <typename T, int NR>
 __device__ __forceinline__ void fw_project(const T* __restrict__ Qb, int64_t n, int r, const T* vs, int rows, int S,
                                            int a0, int a1, T* out, int lane) {
   constexpr int nrhs = NR;
-  constexpr int RF = FS_RFAST(T, NR);
-  T acc[RF][NR];
+  constexpr int CG = 8 / NR;  // columns per pass over the rows (registers: CG NR accumulators)
+  for (int c0 = 0; c0 < r; c0 += CG) {
+    T acc[CG][NR];
 #pragma unroll
-  for (int a = 0; a < RF; ++a)
+    for (int a = 0; a < CG; ++a)
 #pragma unroll
-    for (int j = 0; j < NR; ++j) acc[a][j] = (T)0;
-  for (int p = a0 + lane; p < a1; p += 32) {
-    T v[NR];
+      for (int j = 0; j < NR; ++j) acc[a][j] = (T)0;
+    for (int p = a0 + lane; p < a1; p += 32) {
+      T v[NR];
 #pragma unroll
-    for (int j = 0; j < NR; ++j) v[j] = vs[(size_t)j * rows + p - S];
-    T q[RF];
+      for (int j = 0; j < NR; ++j) v[j] = vs[(size_t)j * rows + p - S];
+      T q[CG];
 #pragma unroll
-    for (int a = 0; a < RF; ++a) q[a] = a < r ? Qb[(size_t)a * n + p] : (T)0;
+      for (int a = 0; a < CG; ++a) q[a] = c0 + a < r ? Qb[(size_t)(c0 + a) * n + p] : (T)0;
 #pragma unroll
-    for (int a = 0; a < RF; ++a)
-      if (a < r)
+      for (int a = 0; a < CG; ++a)
+        if (c0 + a < r)
 #pragma unroll
-        for (int j = 0; j < NR; ++j) acc[a][j] += q[a] * v[j];
+          for (int j = 0; j < NR; ++j) acc[a][j] += q[a] * v[j];
+    }
+#pragma unroll
+    for (int a = 0; a < CG; ++a)
+      if (c0 + a < r)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          const T t = warp_allsum(acc[a][j]);
+          if (lane == 0) out[(c0 + a) * nrhs + j] = t;
+        }
   }
-#pragma unroll
-  for (int a = 0; a < RF; ++a)
-    if (a < r)
-#pragma unroll
-      for (int j = 0; j < NR; ++j) {
-        const T t = warp_allsum(acc[a][j]);
-        if (lane == 0) out[a * nrhs + j] = t;
-      }
 }
 
 // v_p += sum_a Q[a][p] t[(off + a) nrhs + j] for rows [a0, a1), lanes striding.
@@ -764,7 +766,7 @@ __device__ void fw_block_level(const FactDesc* __restrict__ Fd, int l, int lw, i
 // factors of one plan in one launch, problem blockIdx.y: its descriptor
 // Fd[blockIdx.y], its vector vlist[blockIdx.y], its partials, barrier and
 // abort flag pstride bytes after the previous problem's.
-template <typename T, int NR>
+template <typename T, int NR, bool BATCH = false>
 __global__ void __launch_bounds__(256, 4) k_sweep_fused(const FactDesc* __restrict__ Fd, double* __restrict__ v,
                                                         int mode, int ls, int rows, double* __restrict__ part,
                                                         unsigned int* __restrict__ bar, int* __restrict__ abort_flag,
@@ -772,7 +774,9 @@ __global__ void __launch_bounds__(256, 4) k_sweep_fused(const FactDesc* __restri
                                                         size_t pstride) {
   constexpr int nrhs = NR;
   if (active && *active == 0) return;
-  if (vlist) {
+  // (a separate instantiation: re-pointed arguments live in registers for the
+  // whole kernel, which the single-problem kernels cannot afford)
+  if constexpr (BATCH) {
     Fd += blockIdx.y;
     v = vlist[blockIdx.y];
     part = (double*)((char*)part + blockIdx.y * pstride);
@@ -802,7 +806,7 @@ __global__ void __launch_bounds__(256, 4) k_sweep_fused(const FactDesc* __restri
     for (int q = threadIdx.x; q < (1 << (l - ls)); q += blockDim.x)
       if (Fd->rank[node_id(l, (c << (l - ls)) + q)] > FS_RFAST(T, NR)) rk_big = 1;
   __syncthreads();
-  const bool fast = FS_WARP_OWNED(T) && !rk_big && nsub <= FS_WARPS;
+  const bool fast = FS_WARP_OWNED(T, NR) && !rk_big && nsub <= FS_WARPS;
   if (!fast) {  // the block-wide path: the local leaf of every row
     const int nl = 1 << (L - ls), first = c << (L - ls);
     for (int q = threadIdx.x; q < nl; q += blockDim.x) {
@@ -821,7 +825,7 @@ __global__ void __launch_bounds__(256, 4) k_sweep_fused(const FactDesc* __restri
       for (int l = L - 1; l >= ls; --l) fs_local_level<T, NR>(Fd, l, ls, c, vs, rows, S, E - S, zsel, zt, sh);
       return;
     }
-    if constexpr (FS_WARP_OWNED(T)) {
+    if constexpr (FS_WARP_OWNED(T, NR)) {
       if (warp < nsub)
         fw_subtree<T, NR>(Fd, lw, (c << (lw - ls)) + warp, vs, rows, S, md, true, zsel, zt, pw, tw, lane);
       for (int l = lw - 1; l >= ls; --l)
@@ -836,7 +840,7 @@ __global__ void __launch_bounds__(256, 4) k_sweep_fused(const FactDesc* __restri
       fs_leaves<T, NR>(Fd, ls, c, vs, rows, S, md);
       return;
     }
-    if constexpr (FS_WARP_OWNED(T)) {
+    if constexpr (FS_WARP_OWNED(T, NR)) {
       for (int l = ls; l < lw; ++l)
         fw_block_level<T, NR>(Fd, l, lw, c, nsub, vs, rows, S, zsel, zt, sh.tv + (l & 1) * FS_WARPS * FS_WSL, pw, tw,
                               warp, lane);
@@ -877,11 +881,12 @@ size_t sweep_fused_smem(int rows, int nrhs, int prec) {
   return esz * ((size_t)rows * nrhs + 2 * FS_BUF + 256) + sizeof(unsigned short) * (size_t)rows;
 }
 
-template <typename T, int NR>
+template <typename T, int NR, bool BATCH = false>
 static int sweep_fused_per_sm(size_t smem) {
   int per_sm = 0;
-  cudaFuncSetAttribute(k_sweep_fused<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_fused<T, NR>, 256, smem) != cudaSuccess) per_sm = 0;
+  cudaFuncSetAttribute(k_sweep_fused<T, NR, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_fused<T, NR, BATCH>, 256, smem) != cudaSuccess)
+    per_sm = 0;
   cudaGetLastError();
   return per_sm;
 }
@@ -895,20 +900,22 @@ int sweep_fused_coresident(int prec, int rows, int cap) {
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (smem > (size_t)optin) return 0;
-  const int per_sm = prec ? std::min(sweep_fused_per_sm<float, 1>(smem), sweep_fused_per_sm<float, 2>(smem))
-                          : std::min(sweep_fused_per_sm<double, 1>(smem), sweep_fused_per_sm<double, 2>(smem));
+  const int per_sm =
+      prec ? std::min(sweep_fused_per_sm<float, 1>(smem), sweep_fused_per_sm<float, 2>(smem))
+           : std::min(std::min(sweep_fused_per_sm<double, 1>(smem), sweep_fused_per_sm<double, 2>(smem)),
+                      sweep_fused_per_sm<double, 1, true>(smem));
   return sms * per_sm;
 }
 
-template <typename T, int NR>
+template <typename T, int NR, bool BATCH = false>
 static cudaError_t launch_sweep_fused_t(cudaLaunchConfig_t& cfg, const FactDesc* Fd, double* v, int mode, int ls,
                                         int rows, double* part, unsigned int* bar, int* abort_flag,
                                         const int* active, int prec, double* const* vlist = nullptr,
                                         size_t pstride = 0) {
-  cudaFuncSetAttribute(k_sweep_fused<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_sweep_fused<T, NR, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sweep_fused_smem(rows, SW_RHS_MAX, prec));
-  return cudaLaunchKernelEx(&cfg, k_sweep_fused<T, NR>, Fd, v, mode, ls, rows, part, bar, abort_flag, active, vlist,
-                            pstride);
+  return cudaLaunchKernelEx(&cfg, k_sweep_fused<T, NR, BATCH>, Fd, v, mode, ls, rows, part, bar, abort_flag, active,
+                            vlist, pstride);
 }
 
 // nprob FP64 factors of one plan (descriptor array Fd), one right-hand side
@@ -926,8 +933,8 @@ cudaError_t launch_sweep_fused_batched(const FactDesc* Fd, int ls, int rows, dou
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return launch_sweep_fused_t<double, 1>(cfg, Fd, nullptr, mode, ls, rows, part, bar, abort_flag, nullptr, 0, vlist,
-                                         pstride);
+  return launch_sweep_fused_t<double, 1, true>(cfg, Fd, nullptr, mode, ls, rows, part, bar, abort_flag, nullptr, 0,
+                                               vlist, pstride);
 }
 
 cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, int cap, double* v, int nrhs,
