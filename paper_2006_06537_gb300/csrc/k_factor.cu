@@ -272,22 +272,39 @@ __device__ void rowmul_pass(T* __restrict__ Xb, int64_t n, int r, int a0, int a1
   __syncthreads();
 }
 
-// Rows [a0, a1): B_j[p] += sum_a Q[a][p] Tm[a * W + j] (W columns per chunk).
-template <typename T, int W>
-__device__ void update_pass(const T* __restrict__ Qb, T* const* Bp, int w, int64_t n, int r, int a0, int a1,
-                            const T* Tm) {
+// Rows [a0, a1): B_j[p] += sum_a Q[a][p] Tm[a * W + j] for the WN columns of
+// a chunk (Tm rows W apart).
+template <typename T, int W, int WN>
+__device__ void update_pass_n(const T* __restrict__ Qb, T* const* Bp, int64_t n, int r, int a0, int a1, const T* Tm) {
   for (int p = a0 + threadIdx.x; p < a1; p += blockDim.x) {
-    T acc[W];
+    T acc[WN];
 #pragma unroll
-    for (int j = 0; j < W; ++j) acc[j] = j < w ? Bp[j][p] : (T)0;
+    for (int j = 0; j < WN; ++j) acc[j] = Bp[j][p];
     for (int a = 0; a < r; ++a) {
       const T q = Qb[(size_t)a * n + p];
 #pragma unroll
-      for (int j = 0; j < W; ++j) acc[j] += q * Tm[a * W + j];
+      for (int j = 0; j < WN; ++j) acc[j] += q * Tm[a * W + j];
     }
 #pragma unroll
-    for (int j = 0; j < W; ++j)
-      if (j < w) Bp[j][p] = acc[j];
+    for (int j = 0; j < WN; ++j) Bp[j][p] = acc[j];
+  }
+}
+
+// The same for w <= W columns: a full chunk, or the last one with exactly its
+// w columns (no products for the missing ones).
+template <typename T, int W>
+__device__ void update_pass(const T* __restrict__ Qb, T* const* Bp, int w, int64_t n, int r, int a0, int a1,
+                            const T* Tm) {
+  static_assert(W == 8, "chunks of 8 ancestor columns");
+  switch (w) {
+    case 8: update_pass_n<T, W, 8>(Qb, Bp, n, r, a0, a1, Tm); break;
+    case 7: update_pass_n<T, W, 7>(Qb, Bp, n, r, a0, a1, Tm); break;
+    case 6: update_pass_n<T, W, 6>(Qb, Bp, n, r, a0, a1, Tm); break;
+    case 5: update_pass_n<T, W, 5>(Qb, Bp, n, r, a0, a1, Tm); break;
+    case 4: update_pass_n<T, W, 4>(Qb, Bp, n, r, a0, a1, Tm); break;
+    case 3: update_pass_n<T, W, 3>(Qb, Bp, n, r, a0, a1, Tm); break;
+    case 2: update_pass_n<T, W, 2>(Qb, Bp, n, r, a0, a1, Tm); break;
+    default: update_pass_n<T, W, 1>(Qb, Bp, n, r, a0, a1, Tm); break;
   }
 }
 
