@@ -775,9 +775,9 @@ def sweep_flops(n, leaves_m, ranks, L, nrhs=2):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, summed over the 44
 # launches of one FP64 factorization of C~(rho0) of this workload at n = 2^20,
-# leaf 32: 6.42 GB read + 4.07 GB written) from one ncu capture of
+# leaf 32: 6.44 GB read + 4.07 GB written) from one ncu capture of
 # `bench.py --profile-factor` on the current factorization kernels.
-FACTOR_TRAFFIC_BYTES = 10.49e9
+FACTOR_TRAFFIC_BYTES = 10.51e9
 FACTOR_TRAFFIC_CONFIG = (1 << 20, 32)  # (n, leaf) it was captured at
 
 

@@ -74,6 +74,12 @@ struct fifa_additive {
   // fsb_ls < 0: one sweep per block): the blocks' copies of f
   double** tmp_list = nullptr;  // d device pointers
   int fsb_ls = -1, fsb_rows = 0;
+  // the prior part of every block's Algorithm 1 (normals, C~ a, W_C b, rhs0)
+  // in shared launches: the blocks' vectors (device arrays) and the fused
+  // product's grid for d problems (mvb_ls < 0: one product per block)
+  Alg1Prior* prior = nullptr;    // d
+  double** vec_lists = nullptr;  // 3 d: a, b, Ca of every block
+  int mvb_ls = -1, mvb_rows = 0;
 };
 
 // Enqueue fn(k) for every block k, as concurrent branches forked from and
@@ -127,7 +133,20 @@ static fifa_status additive_sweep_enqueue(fifa_ctx* ctx, fifa_additive* A) {
       return chain_phase_factor_m(ctx, A->blk[k]);
     });
   }
-  // f_k | y - sum_{j != k} f_j, blocks in order
+  // the data-independent part of every block's draw (normals, C~_k a_k,
+  // W_{C,k} b_k and the first right-hand side) at once
+  if (st == FIFA_OK && A->prior) {
+    const fifa_hmat* Ce[FIFA_ADDITIVE_MAX_D];
+    const fifa_fact* We[FIFA_ADDITIVE_MAX_D];
+    for (int k = 0; k < d; ++k) {
+      Ce[k] = A->blk[k]->H[0];
+      We[k] = A->blk[k]->F[0];
+    }
+    st = sample_prior_batched(ctx, A->blk[0]->plan, A->h_desc[0], A->f_desc[0], A->prior, A->vec_lists,
+                              A->vec_lists + d, A->vec_lists + 2 * d, d, A->blk[0]->init.seed, A->fsb_ls, A->fsb_rows,
+                              A->mvb_ls, A->mvb_rows, A->scratch, A->scratch_stride, Ce, We);
+  }
+  // f_k | y - sum_{j != k} f_j, blocks in order (block Gibbs)
   for (int k = 0; k < d && st == FIFA_OK; ++k) {
     fifa_chain* ch = A->blk[k];
     if (launch_add_gather(A->y, A->F, A->perm + (size_t)k * n, n, d, k, ch->y, ctx->stream) != cudaSuccess) {
@@ -135,7 +154,7 @@ static fifa_status additive_sweep_enqueue(fifa_ctx* ctx, fifa_additive* A) {
       break;
     }
     ctx->active_scratch = ch->scratch;
-    st = chain_phase_sample(ctx, ch);
+    st = A->prior ? chain_phase_sample_data(ctx, ch) : chain_phase_sample(ctx, ch);
     if (st == FIFA_OK &&
         launch_add_scatter(ch->f, A->perm + (size_t)k * n, n, A->F + (size_t)k * n, ctx->stream) != cudaSuccess)
       st = FIFA_ERR_CUDA;
@@ -302,6 +321,28 @@ extern "C" fifa_status fifa_additive_create(fifa_ctx* ctx, const double* X_dev, 
     CK(cudaMemcpyAsync(A->tmp_list, tl, sizeof(double*) * d, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     if (!sweep_batch_config(ctx, P, d, &A->fsb_ls, &A->fsb_rows)) A->fsb_ls = -1;
+    if (!mv_batch_config(ctx, P, d, &A->mvb_ls, &A->mvb_rows)) A->mvb_ls = -1;
+    // the blocks' Algorithm 1 vectors in their scratch (the layout of
+    // sample_prior_enqueue: a, b, Ca, rhs at 0, n, 2n, 3n of the scratch vectors)
+    Alg1Prior pr[FIFA_ADDITIVE_MAX_D];
+    double* vl[3 * FIFA_ADDITIVE_MAX_D];
+    for (int k = 0; k < d; ++k) {
+      fifa_chain* ch = A->blk[k];
+      ctx->active_scratch = ch->scratch;
+      Scratch S = carve(ctx, ch->plan);
+      ctx->active_scratch = nullptr;
+      pr[k] = Alg1Prior{&ch->dev->iter, ch->init.chain_id, S.vec, S.vec + n, S.vec + 2 * n, S.vec + 3 * n,
+                        &ch->dev->tau2};
+      vl[k] = S.vec;
+      vl[d + k] = S.vec + n;
+      vl[2 * d + k] = S.vec + 2 * n;
+    }
+    A->prior = (Alg1Prior*)ctx->arena.alloc(sizeof(Alg1Prior) * d);
+    A->vec_lists = (double**)ctx->arena.alloc(sizeof(double*) * 3 * d);
+    if (!A->prior || !A->vec_lists) return fail(FIFA_ERR_OOM);
+    CK(cudaMemcpyAsync(A->prior, pr, sizeof(Alg1Prior) * d, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(A->vec_lists, vl, sizeof(double*) * 3 * d, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
   }
   ChainDev* ptrs[FIFA_ADDITIVE_MAX_D] = {};
   for (int k = 0; k < d; ++k) ptrs[k] = A->blk[k]->dev;
@@ -474,6 +515,8 @@ extern "C" void fifa_destroy_additive(fifa_ctx* ctx, fifa_additive* A) {
   }
   ctx->arena.release(A->scratch);
   ctx->arena.release(A->tmp_list);
+  ctx->arena.release(A->prior);
+  ctx->arena.release(A->vec_lists);
   for (int k = 0; k < FIFA_ADDITIVE_MAX_D; ++k) {
     if (A->side[k]) cudaStreamDestroy(A->side[k]);
     if (A->ev_join[k]) cudaEventDestroy(A->ev_join[k]);

@@ -1052,29 +1052,42 @@ extern "C" fifa_status fifa_solve(fifa_ctx* ctx, const fifa_fact* F, const doubl
 // ---------------------------------------------------------------------------
 // Algorithm 1
 // ---------------------------------------------------------------------------
-fifa_status sample_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, const fifa_fact* WM, const double* y,
-                           double tau2, double sigma2, uint64_t seed, uint64_t sid, const uint64_t* iter_dev,
-                           uint64_t iter_host, double* f, double* mean, const double* scal_dev, double* res_dev,
-                           int* iters_dev, const fifa_hmat* op) {
+fifa_status sample_prior_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, double tau2, double sigma2,
+                                 uint64_t seed, uint64_t sid, const uint64_t* iter_dev, uint64_t iter_host,
+                                 const double* scal_dev) {
   Plan* P = C->plan;
   const int64_t n = P->n;
   Scratch S = carve(ctx, P);
   cudaStream_t s = ctx->stream;
-  double* a = S.vec;          // n
-  double* b = S.vec + n;      // n
-  double* Ca = S.vec + 2 * n; // n
-  double* rhs = S.vec + 3 * n;// 2n : [Z, y/sigma2] -> [w, r]
-  double* Cr = S.vec + 5 * n; // n
-  double* bsave = S.vec + 6 * n; // 2n (iteration right-hand sides)
-  double* work = S.vec + 8 * n; // 8n (conjugate-gradient vectors)
+  double* a = S.vec;           // n
+  double* b = S.vec + n;       // n
+  double* Ca = S.vec + 2 * n;  // n
+  double* rhs = S.vec + 3 * n; // 2n : [Z, y/sigma2] -> [w, r]
   CK(launch_normals(seed, 0, iter_dev, iter_host, sid, a, n, s));
   CK(launch_normals(seed, 1, iter_dev, iter_host, sid, b, n, s));
   fifa_status st = matvec_enqueue(ctx, C, a, Ca, 1);
   if (st != FIFA_OK) return st;
   st = sweep_enqueue(ctx, WC, 0, 0, b, 1);
   if (st != FIFA_OK) return st;
-  // rhs0 = (tau2/sigma) Ca + tau Wb ; rhs1 = y / sigma2
-  CK(launch_alg1_rhs(Ca, b, y, rhs, n, tau2, sigma2, scal_dev, s));
+  // rhs0 = (tau2/sigma) Ca + tau Wb
+  CK(launch_alg1_rhs_part(Ca, b, nullptr, rhs, n, tau2, sigma2, scal_dev, 0, s));
+  return FIFA_OK;
+}
+
+fifa_status sample_data_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WM, const double* y, double tau2,
+                                double sigma2, double* f, double* mean, const double* scal_dev, double* res_dev,
+                                int* iters_dev, const fifa_hmat* op) {
+  Plan* P = C->plan;
+  const int64_t n = P->n;
+  Scratch S = carve(ctx, P);
+  cudaStream_t s = ctx->stream;
+  double* rhs = S.vec + 3 * n;    // 2n : [Z, y/sigma2] -> [w, r]
+  double* Cr = S.vec + 5 * n;     // n
+  double* bsave = S.vec + 6 * n;  // 2n (iteration right-hand sides)
+  double* work = S.vec + 8 * n;   // 8n (conjugate-gradient vectors)
+  // rhs1 = y / sigma2
+  CK(launch_alg1_rhs_part(nullptr, nullptr, y, rhs, n, tau2, sigma2, scal_dev, 1, s));
+  fifa_status st;
   if (WM->has32) {
     CK(cudaMemcpyAsync(bsave, rhs, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, s));
     st = solve_enqueue(ctx, WM, bsave, rhs, 2, work, res_dev, iters_dev, op, false);
@@ -1085,6 +1098,63 @@ fifa_status sample_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* W
   st = matvec_enqueue(ctx, C, rhs + n, Cr, 1);
   if (st != FIFA_OK) return st;
   CK(launch_alg1_finish(rhs, Cr, f, mean, n, tau2, scal_dev, s));
+  return FIFA_OK;
+}
+
+fifa_status sample_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, const fifa_fact* WM, const double* y,
+                           double tau2, double sigma2, uint64_t seed, uint64_t sid, const uint64_t* iter_dev,
+                           uint64_t iter_host, double* f, double* mean, const double* scal_dev, double* res_dev,
+                           int* iters_dev, const fifa_hmat* op) {
+  fifa_status st = sample_prior_enqueue(ctx, C, WC, tau2, sigma2, seed, sid, iter_dev, iter_host, scal_dev);
+  if (st != FIFA_OK) return st;
+  return sample_data_enqueue(ctx, C, WM, y, tau2, sigma2, f, mean, scal_dev, res_dev, iters_dev, op);
+}
+
+bool mv_batch_config(fifa_ctx* ctx, const Plan* P, int nprob, int* ls, int* rows) {
+  (void)ctx;
+  if (P->mv_ls < 0 || nprob < 1) return false;
+  for (int k = P->mv_ls; k >= 0; --k) {
+    int r = 0;
+    for (int i = 0; i < (1 << k); ++i) r = std::max(r, P->bnd_host[bnd_off(k) + i + 1] - P->bnd_host[bnd_off(k) + i]);
+    if (r > MV_FUSED_ROWS_MAX) return false;
+    if ((int64_t)mv_fused_coresident(r) >= ((int64_t)nprob << k)) {
+      *ls = k;
+      *rows = r;
+      return true;
+    }
+  }
+  return false;
+}
+
+fifa_status sample_prior_batched(fifa_ctx* ctx, Plan* P, const HmatDesc* C0, const FactDesc* WC0, const Alg1Prior* P_dev,
+                                 const double* const* a_list, double* const* b_list, double* const* Ca_list, int nprob,
+                                 uint64_t seed, int sweep_ls, int sweep_rows, int mv_ls, int mv_rows, void* scratch0,
+                                 size_t sstride, const fifa_hmat* const* C_each, const fifa_fact* const* WC_each) {
+  const int64_t n = P->n;
+  cudaStream_t s = ctx->stream;
+  CK(launch_alg1_prior_normals(seed, P_dev, nprob, n, s));
+  void* saved = ctx->active_scratch;
+  ctx->active_scratch = scratch0;
+  Scratch S = carve(ctx, P);
+  ctx->active_scratch = saved;
+  fifa_status st = FIFA_OK;
+  if (mv_ls >= 0) {  // C~ a for every block in one launch
+    CK(cudaMemset2DAsync(S.mv_bar, sstride, 0, sizeof(unsigned int), nprob, s));
+    CK(cudaMemset2DAsync(S.flags, sstride, 0, sizeof(int), nprob, s));
+    CK(launch_mv_fused_batched(C0, mv_ls, mv_rows, a_list, Ca_list, nprob, S.mv_fpart, S.mv_bar, S.flags, sstride, s));
+  }
+  if (sweep_ls >= 0)  // W_C b for every block in one launch
+    st = sweep_enqueue_batched(ctx, P, WC0, b_list, nprob, 0, sweep_ls, sweep_rows, scratch0, sstride);
+  // blocks without a shared launch: one product / sweep each, on their own scratch
+  for (int q = 0; q < nprob && st == FIFA_OK && (mv_ls < 0 || sweep_ls < 0); ++q) {
+    ctx->active_scratch = (char*)scratch0 + (size_t)q * sstride;
+    Scratch Sq = carve(ctx, P);
+    if (mv_ls < 0) st = matvec_enqueue(ctx, C_each[q], Sq.vec, Sq.vec + 2 * n, 1);
+    if (st == FIFA_OK && sweep_ls < 0) st = sweep_enqueue(ctx, WC_each[q], 0, 0, Sq.vec + n, 1);
+  }
+  ctx->active_scratch = saved;
+  if (st != FIFA_OK) return st;
+  CK(launch_alg1_prior_rhs(P_dev, nprob, n, s));
   return FIFA_OK;
 }
 

@@ -44,6 +44,14 @@ fifa_status chain_phase_sample(fifa_ctx* ctx, fifa_chain* ch) {
                         0, ch->f, ch->mean, &c->tau2, &c->refine_res, &c->pcg_iters, ch->Mv);
 }
 
+// Phase 1b's data part (after the prior part has run for this chain,
+// sample_prior_enqueue or sample_prior_batched).
+fifa_status chain_phase_sample_data(fifa_ctx* ctx, fifa_chain* ch) {
+  ChainDev* c = ch->dev;
+  return sample_data_enqueue(ctx, ch->H[0], ch->FM, ch->y, 0.0, 0.0, ch->f, ch->mean, &c->tau2, &c->refine_res,
+                             &c->pcg_iters, ch->Mv);
+}
+
 // Phase 1: phases 1a and 1b.
 fifa_status chain_phase_draw(fifa_ctx* ctx, fifa_chain* ch) {
   fifa_status st = chain_phase_factor_m(ctx, ch);

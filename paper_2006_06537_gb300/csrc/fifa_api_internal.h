@@ -142,16 +142,51 @@ fifa_status sample_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* W
                            double tau2, double sigma2, uint64_t seed, uint64_t sid, const uint64_t* iter_dev,
                            uint64_t iter_host, double* f, double* mean, const double* scal_dev, double* res_dev = nullptr,
                            int* iters_dev = nullptr, const fifa_hmat* op = nullptr);
+// Algorithm 1's two parts (sample_enqueue runs both): the prior part (normals
+// a, b; C~ a; W_C b; rhs0 = (tau2 / sigma) C~ a + tau W_C b) reads no data; the
+// data part (rhs1 = y / sigma2, the solves with M~, C~ r, f) does.  Both use
+// the plan scratch vectors a, b, Ca, rhs of the active scratch.
+fifa_status sample_prior_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WC, double tau2, double sigma2,
+                                 uint64_t seed, uint64_t sid, const uint64_t* iter_dev, uint64_t iter_host,
+                                 const double* scal_dev);
+fifa_status sample_data_enqueue(fifa_ctx* ctx, const fifa_hmat* C, const fifa_fact* WM, const double* y, double tau2,
+                                double sigma2, double* f, double* mean, const double* scal_dev, double* res_dev,
+                                int* iters_dev, const fifa_hmat* op);
+// One block's vectors and state for the prior part of Algorithm 1 run for
+// several blocks at once.
+struct Alg1Prior {
+  const uint64_t* iter;  // the block's iteration counter (device)
+  uint64_t sid;          // its Philox stream id
+  double* a;             // n: normals of tag 0
+  double* b;             // n: normals of tag 1, then W_C b in place
+  double* Ca;            // n
+  double* rhs;           // rhs0 at rhs[0..n)
+  const double* scal;    // tau2, sigma2 (device)
+};
+// The prior part for nprob blocks of plan P at once: descriptor arrays C0 (C~)
+// and WC0 (W_C); P_dev the blocks' Alg1Prior (device); a_list / b_list /
+// Ca_list device arrays of their a, b, Ca; the shared launches' grids (ls < 0:
+// one product / sweep per block, C_each / WC_each); scratch as
+// hmat_assemble_batched.
+fifa_status sample_prior_batched(fifa_ctx* ctx, Plan* P, const HmatDesc* C0, const FactDesc* WC0, const Alg1Prior* P_dev,
+                                 const double* const* a_list, double* const* b_list, double* const* Ca_list, int nprob,
+                                 uint64_t seed, int sweep_ls, int sweep_rows, int mv_ls, int mv_rows, void* scratch0,
+                                 size_t sstride, const fifa_hmat* const* C_each, const fifa_fact* const* WC_each);
+// Grid of a fused H-matrix product of nprob problems of plan P in one launch
+// (as sweep_batch_config).
+bool mv_batch_config(fifa_ctx* ctx, const Plan* P, int nprob, int* ls, int* rows);
 
 // vector kernels (k_vec.cu)
 cudaError_t launch_prep_hmat(HmatDesc* H, int nnodes, cudaStream_t st, int nprob = 1);
 cudaError_t launch_prep_fact(FactDesc* F, const HmatDesc* H, int nnodes, cudaStream_t st, int nprob = 1);
 cudaError_t launch_sumsq(const double* a, const double* b, int64_t n, double* part, double* out, cudaStream_t st);
 cudaError_t launch_axpy(double a, const double* x, double* y, int64_t n, cudaStream_t st);
-cudaError_t launch_alg1_rhs(const double* Ca, const double* Wb, const double* y, double* rhs, int64_t n, double tau2,
-                            double sigma2, const double* scal_dev, cudaStream_t st);
 cudaError_t launch_alg1_finish(const double* wr, const double* Cr, double* f, double* mean, int64_t n, double tau2,
                                const double* scal_dev, cudaStream_t st);
+cudaError_t launch_alg1_rhs_part(const double* Ca, const double* Wb, const double* y, double* rhs, int64_t n,
+                                 double tau2, double sigma2, const double* scal_dev, int part, cudaStream_t st);
+cudaError_t launch_alg1_prior_normals(uint64_t seed, const Alg1Prior* P, int nprob, int64_t n, cudaStream_t st);
+cudaError_t launch_alg1_prior_rhs(const Alg1Prior* P, int nprob, int64_t n, cudaStream_t st);
 cudaError_t launch_alg1h_scale(const double* d, double* a, int64_t n, cudaStream_t st);
 cudaError_t launch_alg1h_rhs(const double* Ca, const double* Wb, const double* y, double* rhs, int64_t n, double tau2,
                              cudaStream_t st);

@@ -45,6 +45,8 @@ fifa_status chain_phase_hyper_post(fifa_ctx* ctx, fifa_chain* ch, const Scratch&
 // additive model runs the blocks' sweeps in one batched launch).
 fifa_status chain_hyper_tau2_propose(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
 fifa_status chain_hyper_mh(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
+// Phase 1b without its prior part (run for several blocks at once by the additive model).
+fifa_status chain_phase_sample_data(fifa_ctx* ctx, fifa_chain* ch);
 
 // Serving helpers.  chain_run_collect runs `iters` iterations (graph replay)
 // and gathers on the device: mean_acc = sum of the conditional means

@@ -62,6 +62,12 @@ cudaError_t launch_sweep_fused_batched(const FactDesc* Fd, int ls, int rows, dou
 int mv_fused_coresident(int rows);
 cudaError_t launch_mv_fused(const HmatDesc* Hd, int ls, int rows, const double* x, int nrhs, double* y, double* part,
                             unsigned int* bar, int* abort_flag, cudaStream_t st, const int* active = nullptr);
+// nprob H-matrices of one plan in one launch (one right-hand side each:
+// xlist[q] -> ylist[q]; per-problem partials / barrier / abort flag pstride
+// bytes apart)
+cudaError_t launch_mv_fused_batched(const HmatDesc* Hd, int ls, int rows, const double* const* xlist,
+                                    double* const* ylist, int nprob, double* part, unsigned int* bar, int* abort_flag,
+                                    size_t pstride, cudaStream_t st);
 cudaError_t launch_sweep_leaf(const FactDesc* Fd, int prec, int nleaf, double* v, int nrhs, int mode, cudaStream_t st,
                               const int* active = nullptr);
 cudaError_t launch_matvec(const HmatDesc* Hd, int nleaf, int L, const double* x, int nrhs, double* part, double* proj,

@@ -974,12 +974,25 @@ cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, i
 #define MV_PROJ_BUF 1024                       // doubles of node projections per batch
 #define MV_PART_STRIDE (FIFA_CAP_MAX * SW_RHS_MAX)  // one CTA's partial of one level
 
-template <int RPT>
+// BATCH: several H-matrices of one plan in one launch, problem blockIdx.y: its
+// descriptor Hd[blockIdx.y], input xlist[blockIdx.y] and output ylist[...],
+// its partials, barrier and abort flag pstride bytes after the previous
+// problem's (a separate instantiation: re-pointed arguments stay in registers).
+template <int RPT, bool BATCH = false>
 __global__ void __launch_bounds__(256, RPT <= 8 ? 4 : 2) k_mv_fused(const HmatDesc* __restrict__ Hd, const double* __restrict__ x, int nrhs,
                                                   double* __restrict__ y, int ls, int rows, double* __restrict__ part,
                                                   unsigned int* __restrict__ bar, int* __restrict__ abort_flag,
-                                                  const int* __restrict__ active) {
+                                                  const int* __restrict__ active, const double* const* xlist,
+                                                  double* const* ylist, size_t pstride) {
   if (active && *active == 0) return;  // a converged iteration: nothing to compute
+  if constexpr (BATCH) {
+    Hd += blockIdx.y;
+    x = xlist[blockIdx.y];
+    y = ylist[blockIdx.y];
+    part = (double*)((char*)part + blockIdx.y * pstride);
+    bar = (unsigned int*)((char*)bar + blockIdx.y * pstride);
+    abort_flag = (int*)((char*)abort_flag + blockIdx.y * pstride);
+  }
   extern __shared__ double sm[];
   double* xs = sm;                                   // nrhs x rows
   double* pj = xs + (size_t)rows * nrhs;             // MV_PROJ_BUF node projections
@@ -1145,17 +1158,24 @@ size_t mv_fused_smem(int rows) {
   return sizeof(double) * ((size_t)rows * SW_RHS_MAX + MV_PROJ_BUF + 256) + sizeof(int) * (size_t)rows;
 }
 
-template <int RPT>
-static int mv_fused_per_sm(int rows) {
+template <int RPT, bool BATCH>
+static int mv_fused_per_sm_v(int rows) {
   const size_t smem = mv_fused_smem(rows);
   int dev = 0, optin = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (smem > (size_t)optin) return 0;
-  cudaFuncSetAttribute(k_mv_fused<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mv_fused<RPT>, 256, smem) != cudaSuccess) per_sm = 0;
+  cudaFuncSetAttribute(k_mv_fused<RPT, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mv_fused<RPT, BATCH>, 256, smem) != cudaSuccess)
+    per_sm = 0;
   cudaGetLastError();
   return per_sm;
+}
+
+// the smaller of the single-problem and the multi-problem instantiations
+template <int RPT>
+static int mv_fused_per_sm(int rows) {
+  return std::min(mv_fused_per_sm_v<RPT, false>(rows), mv_fused_per_sm_v<RPT, true>(rows));
 }
 
 static int mv_rpt(int rows) {
@@ -1178,14 +1198,15 @@ int mv_fused_coresident(int rows) {
   }
 }
 
-template <int RPT>
+template <int RPT, bool BATCH = false>
 static cudaError_t launch_mv_fused_t(const HmatDesc* Hd, int ls, int rows, const double* x, int nrhs, double* y,
                                      double* part, unsigned int* bar, int* abort_flag, cudaStream_t st,
-                                     const int* active) {
+                                     const int* active, const double* const* xlist = nullptr,
+                                     double* const* ylist = nullptr, int nprob = 1, size_t pstride = 0) {
   const size_t smem = mv_fused_smem(rows);
-  cudaFuncSetAttribute(k_mv_fused<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_mv_fused<RPT, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(1u << ls);
+  cfg.gridDim = dim3(1u << ls, nprob);
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
@@ -1194,7 +1215,27 @@ static cudaError_t launch_mv_fused_t(const HmatDesc* Hd, int ls, int rows, const
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_mv_fused<RPT>, Hd, x, nrhs, y, ls, rows, part, bar, abort_flag, active);
+  return cudaLaunchKernelEx(&cfg, k_mv_fused<RPT, BATCH>, Hd, x, nrhs, y, ls, rows, part, bar, abort_flag, active,
+                            xlist, ylist, pstride);
+}
+
+// nprob H-matrices of one plan (descriptor array Hd), one right-hand side each
+// (xlist[q] -> ylist[q]), in one cooperative launch of 2^ls x nprob CTAs.
+cudaError_t launch_mv_fused_batched(const HmatDesc* Hd, int ls, int rows, const double* const* xlist,
+                                    double* const* ylist, int nprob, double* part, unsigned int* bar, int* abort_flag,
+                                    size_t pstride, cudaStream_t st) {
+#define MVB(R)                                                                                                    \
+  launch_mv_fused_t<R, true>(Hd, ls, rows, nullptr, 1, nullptr, part, bar, abort_flag, st, nullptr, xlist, ylist, \
+                             nprob, pstride)
+  switch (mv_rpt(rows)) {
+    case 1: return MVB(1);
+    case 2: return MVB(2);
+    case 4: return MVB(4);
+    case 8: return MVB(8);
+    case 16: return MVB(16);
+    default: return cudaErrorInvalidValue;
+  }
+#undef MVB
 }
 
 cudaError_t launch_mv_fused(const HmatDesc* Hd, int ls, int rows, const double* x, int nrhs, double* y, double* part,

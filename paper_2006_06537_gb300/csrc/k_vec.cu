@@ -86,18 +86,44 @@ __global__ void k_axpy(double a, const double* __restrict__ x, double* __restric
 }
 
 
-// rhs[0:n] = (tau2 / sigma) Ca + tau Wb ; rhs[n:2n] = y / sigma2
-__global__ void k_alg1_rhs(const double* __restrict__ Ca, const double* __restrict__ Wb, const double* __restrict__ y,
-                           double* __restrict__ rhs, int64_t n, double tau2, double sigma2, const double* scal) {
+// The two halves of the right-hand sides of Algorithm 1: rhs[0..n) =
+// (tau2 / sigma) Ca + tau Wb (part 0), rhs[n..2n) = y / sigma2 (part 1).
+__global__ void k_alg1_rhs_part(const double* __restrict__ Ca, const double* __restrict__ Wb,
+                                const double* __restrict__ y, double* __restrict__ rhs, int64_t n, double tau2,
+                                double sigma2, const double* scal, int part) {
   if (scal) {
     tau2 = scal[0];
     sigma2 = scal[1];
   }
   const double tau = sqrt(tau2), sig = sqrt(sigma2), a = tau2 / sig;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    rhs[i] = a * Ca[i] + tau * Wb[i];
-    rhs[n + i] = y[i] / sigma2;
+    if (part == 0) rhs[i] = a * Ca[i] + tau * Wb[i];
+    else rhs[n + i] = y[i] / sigma2;
   }
+}
+
+// The data-independent start of Algorithm 1 for several blocks at once
+// (blockIdx.y): normals a (tag 0) and b (tag 1) of each block's Philox stream,
+// and after its products rhs0 = (tau2 / sigma) C a + tau W_C b.
+__global__ void k_alg1_prior_normals(uint64_t seed, const Alg1Prior* __restrict__ P, int64_t n) {
+  const Alg1Prior& q = P[blockIdx.y >> 1];
+  const uint32_t tag = blockIdx.y & 1;
+  double* out = tag ? q.b : q.a;
+  const uint64_t it = *q.iter;
+  const int64_t nq = (n + 1) / 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+    double z0, z1;
+    philox_normal_pair(seed, (uint32_t)i, tag, it, q.sid, z0, z1);
+    out[2 * i] = z0;
+    if (2 * i + 1 < n) out[2 * i + 1] = z1;
+  }
+}
+__global__ void k_alg1_prior_rhs(const Alg1Prior* __restrict__ P, int64_t n) {
+  const Alg1Prior& q = P[blockIdx.y];
+  const double tau2 = q.scal[0], sigma2 = q.scal[1];
+  const double tau = sqrt(tau2), sig = sqrt(sigma2), a = tau2 / sig;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    q.rhs[i] = a * q.Ca[i] + tau * q.b[i];
 }
 
 // f = w + tau2 C r ; mean = tau2 C r
@@ -115,9 +141,17 @@ cudaError_t launch_axpy(double a, const double* x, double* y, int64_t n, cudaStr
   k_axpy<<<grid_for(n), 256, 0, st>>>(a, x, y, n);
   return cudaGetLastError();
 }
-cudaError_t launch_alg1_rhs(const double* Ca, const double* Wb, const double* y, double* rhs, int64_t n, double tau2,
-                            double sigma2, const double* scal_dev, cudaStream_t st) {
-  k_alg1_rhs<<<grid_for(n), 256, 0, st>>>(Ca, Wb, y, rhs, n, tau2, sigma2, scal_dev);
+cudaError_t launch_alg1_rhs_part(const double* Ca, const double* Wb, const double* y, double* rhs, int64_t n,
+                                 double tau2, double sigma2, const double* scal_dev, int part, cudaStream_t st) {
+  k_alg1_rhs_part<<<grid_for(n), 256, 0, st>>>(Ca, Wb, y, rhs, n, tau2, sigma2, scal_dev, part);
+  return cudaGetLastError();
+}
+cudaError_t launch_alg1_prior_normals(uint64_t seed, const Alg1Prior* P, int nprob, int64_t n, cudaStream_t st) {
+  k_alg1_prior_normals<<<dim3(grid_for((n + 1) / 2), 2 * nprob), 256, 0, st>>>(seed, P, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_alg1_prior_rhs(const Alg1Prior* P, int nprob, int64_t n, cudaStream_t st) {
+  k_alg1_prior_rhs<<<dim3(grid_for(n), nprob), 256, 0, st>>>(P, n);
   return cudaGetLastError();
 }
 cudaError_t launch_alg1_finish(const double* wr, const double* Cr, double* f, double* mean, int64_t n, double tau2,
