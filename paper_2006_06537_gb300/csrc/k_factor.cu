@@ -1024,15 +1024,19 @@ __global__ void __launch_bounds__(256) k_level_multi(const FactDesc* __restrict_
   __syncthreads();
   const double cg = clamp_gram<T>();
   for (int pass = 0; pass < 2; ++pass) {
-    // Gram entries (j, side, a <= b), one thread each, serial over the side's rows
+    // Gram entries (j, side, a <= b), one thread each, serial over the side's
+    // rows.  Pairs in column order of the upper triangle (q < r (r + 1) / 2 are
+    // exactly a rank-r node's pairs) and the nodes' sides fastest: the active
+    // lanes are the first threads, not a few in every warp.
     constexpr int NPAIR = R * (R + 1) / 2;
     for (int t = tid; t < NPC * 2 * NPAIR; t += nt) {
-      const int js = t / NPAIR, q = t % NPAIR, j = js / 2, side = js % 2;
+      const int q = t / (NPC * 2), js = t % (NPC * 2), j = js / 2, side = js % 2;
       const int* in = info + j * 8;
       const int r = in[0];
       if (!in[4]) continue;
-      int a, b;
-      pair_decode(q, R, a, b);
+      int b = 0;
+      while ((b + 1) * (b + 2) / 2 <= q) ++b;
+      const int a = q - b * (b + 1) / 2;
       if (b >= r) continue;
       const int m = side ? in[3] - in[2] : in[2] - in[1];
       const double* X = Xs + (size_t)js * R * MS;
