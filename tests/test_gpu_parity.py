@@ -133,6 +133,8 @@ FACTOR_CASES = [
     (2048, 64, 0, 0.1, 1e-8, 1e-12, 250.0, "sine"),   # M~ = s C~ + I of the first workload
     (20000, 64, 0, 0.01, 1e-8, 1e-10, 400.0, "cluster"),
     (65, 64, 1, 0.3, 1e-6, 1e-12, None, "sine"),
+    (1, 64, 0, 0.1, 1e-6, 1e-12, None, "sine"),        # a single point: one 1 x 1 leaf, no level
+    (2, 64, 0, 0.1, 1e-6, 1e-12, 3.0, "sine"),         # two points, shifted view
 ]
 
 
