@@ -574,10 +574,23 @@ def kl_report(fifa, torch, leaf, nugget, n_kl=2048):
     H = fifa.fifa_assemble(ctx.h, torch.tensor(x, device="cuda"), n_kl, fifa.fifa_hyper(0, 1.0, RHO0, 1.0, nugget))
     ex = fifa.fifa_hmat_export(ctx.h, H)
     ctx.close()
+    out = kl_terms(x, y, dense_ctilde(ex, n_kl), tau2, sigma2, RHO0, nugget)
+    out.update({"n": n_kl, "leaf": leaf, "aca_tol": EPS,
+                "workload": f"clustered SE n={n_kl}, 8 clusters, rho={RHO0}, tau2=var(y), sigma2={sigma2:g}, "
+                            f"nugget={nugget:g}",
+                "ranks_max": int(np.max(ex["ranks"])),
+                "note": "C~ from fifa_assemble + fifa_hmat_export; P and Q formed densely in numpy FP64"})
+    return out
+
+
+def kl_terms(x, y, Ct, tau2, sigma2, rho, nugget):
+    """KL(P || Q) and its parts for the SE kernel: P the exact posterior for
+    K = tau2 (C + nugget I), Q the one for K~ = tau2 C~ (Ct dense)."""
+    n = len(x)
     dx = x[:, None] - x[None, :]
-    eye = np.eye(n_kl)
-    K = tau2 * (np.exp(-dx * dx / (2 * RHO0 * RHO0)) + nugget * eye)
-    Kt = tau2 * dense_ctilde(ex, n_kl)
+    eye = np.eye(n)
+    K = tau2 * (np.exp(-dx * dx / (2 * rho * rho)) + nugget * eye)
+    Kt = tau2 * Ct
 
     def post(Km):
         S = Km @ np.linalg.inv(Km / sigma2 + eye)
@@ -587,16 +600,12 @@ def kl_report(fifa, torch, leaf, nugget, n_kl=2048):
     mp, Sp = post(K)
     mq, Sq = post(Kt)
     ldq, ldp = np.linalg.slogdet(Sq)[1], np.linalg.slogdet(Sp)[1]
-    tr = float(np.trace(np.linalg.solve(Sq, Sp))) - n_kl
+    tr = float(np.trace(np.linalg.solve(Sq, Sp))) - n
     dm = mq - mp
     quad = float(dm @ np.linalg.solve(Sq, dm))
-    e_max = float(np.abs(Kt - K).max())
-    return {"kl": 0.5 * (ldq - ldp + tr + quad), "n": n_kl, "leaf": leaf, "aca_tol": EPS,
-            "workload": f"clustered SE n={n_kl}, 8 clusters, rho={RHO0}, tau2=var(y), sigma2={sigma2:g}, "
-                        f"nugget={nugget:g}",
+    return {"kl": 0.5 * (ldq - ldp + tr + quad),
             "parts": {"logdet": 0.5 * (ldq - ldp), "trace": 0.5 * tr, "quad": 0.5 * quad},
-            "e_max": e_max, "ranks_max": int(np.max(ex["ranks"])),
-            "note": "C~ from fifa_assemble + fifa_hmat_export; P and Q formed densely in numpy FP64"}
+            "e_max": float(np.abs(Kt - K).max())}
 
 
 def serving_leg(fifa, count, slots, prec, leaf, iters=100, ndraws=20, rate=200.0, budget=120 << 30,
