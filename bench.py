@@ -64,7 +64,8 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=10,
+                    help="untimed iterations before the timed ones (the measurement plan asks for 10)")
     ap.add_argument("--impl", default="fifa", choices=["fifa", "reference"])
     ap.add_argument("--n", type=int, default=N_FULL)
     ap.add_argument("--leaf", type=int, default=0, help="leaf size (0 = the autotuner's cached choice)")
