@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=10,
-                    help="untimed iterations before the timed ones (the measurement plan asks for 10)")
+                    help="untimed iterations before the timed ones (the chain leaves its start, and the mixed chain's kept M~ factor settles, within the first few)")
     ap.add_argument("--impl", default="fifa", choices=["fifa", "reference"])
     ap.add_argument("--n", type=int, default=N_FULL)
     ap.add_argument("--leaf", type=int, default=0, help="leaf size (0 = the autotuner's cached choice)")
