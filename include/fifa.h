@@ -82,6 +82,10 @@ typedef struct {
                          (each followed by a 64 ns sleep), sets FIFA_ERR_TIMEOUT in the object's
                          status and makes the whole launch return; 0: the default 2^26 polls
                          (seconds).  Objects take the value of the context that created them. */
+  int coresident_share; /* 0 or 1: a launch whose CTAs wait on each other may use every CTA the
+                           GPU holds at once.  k > 1: at most 1/k of them, so that k contexts
+                           with independent_ctas = 0 may launch such work side by side (their
+                           waiting launches then fit on the GPU together).  1..64 */
 } fifa_opts;
 
 /* Priors: inverse-gamma IG(shape, scale) on tau2 and sigma2 (the conjugate
@@ -389,17 +393,21 @@ void fifa_destroy_tensor(fifa_ctx* ctx, fifa_tensor* model);
  * hold its chain (fifa_chain_bytes plus its input and result buffers);
  * admitted requests run concurrently and their kernels overlap on the GPU.
  * Narrow workers use independent CTAs (opts.independent_ctas forced to 1).
- * With wide_min_n > 0, worker 0 alone runs the requests with n >= wide_min_n,
- * with CTA groups and fused sweeps spanning the GPU (the only stream whose
- * kernels' CTAs wait on each other).  A request's worker type depends only on
- * its n, so its result does not depend on what else is in flight.  This API
+ * With wide_min_n > 0, the wide workers run the requests with n >= wide_min_n,
+ * with CTA groups and fused sweeps (the only streams whose kernels' CTAs wait
+ * on each other), each sized to 1 / wide_workers of the CTAs the GPU holds at
+ * once, so the wide workers' waiting launches always fit on the GPU together.
+ * A request's worker type depends only on its n, and every wide worker uses
+ * the same sizes, so its result does not depend on what else is in flight.  This API
  * has no counterpart in the paper; it serves its sampler to many users. */
 typedef struct fifa_server fifa_server;
 typedef struct {
   fifa_opts opts;     /* leaf size, ACA tolerance, rank cap, precision of every request */
   size_t hbm_budget;  /* device bytes reserved once for all requests in flight */
   int slots;          /* requests in flight at once, 1..256 */
-  int64_t wide_min_n; /* 0: all workers narrow; > 0: worker 0 is wide (needs slots >= 2) */
+  int64_t wide_min_n; /* 0: all workers narrow; > 0: the first wide_workers workers are wide */
+  int wide_workers;   /* wide workers when wide_min_n > 0 (0 means 1; < slots): each sizes its
+                         grouped launches to 1 / wide_workers of the GPU (coresident_share) */
 } fifa_server_opts;
 
 typedef struct {

@@ -282,7 +282,8 @@ Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st) {
       for (int i = 0; i < (1 << k); ++i)
         rows = std::max(rows, P->bnd_host[bnd_off(k) + i + 1] - P->bnd_host[bnd_off(k) + i]);
       const int cap = ctx->opts.rank_cap;
-      const int co = std::min(sweep_fused_coresident(0, rows, cap), sweep_fused_coresident(1, rows, cap));
+      const int co = std::min(sweep_fused_coresident(0, rows, cap), sweep_fused_coresident(1, rows, cap)) /
+                     coresident_share(ctx->opts);
       if (co >= (1 << k)) {
         P->fs_ls = k;
         P->fs_rows = rows;
@@ -295,7 +296,7 @@ Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st) {
       for (int i = 0; i < (1 << k); ++i)
         rows = std::max(rows, P->bnd_host[bnd_off(k) + i + 1] - P->bnd_host[bnd_off(k) + i]);
       if (rows > MV_FUSED_ROWS_MAX) break;
-      if (mv_fused_coresident(rows) >= (1 << k)) {
+      if (mv_fused_coresident(rows) / coresident_share(ctx->opts) >= (1 << k)) {
         P->mv_ls = k;
         P->mv_rows = rows;
         break;
@@ -359,8 +360,9 @@ extern "C" fifa_status fifa_chain_bytes(const fifa_opts* opts, int64_t n, size_t
   fifa_status st = FIFA_OK;
   int lvl_cores[LEVEL_BUCKETS];
   for (int b = 0; b < LEVEL_BUCKETS; ++b)
-    lvl_cores[b] = std::min(level_bucket_coresident(0, b, opts->rank_cap), level_bucket_coresident(1, b, opts->rank_cap));
-  Plan* P = plan_build(n, *opts, aca_max_coresident_ctas(), lvl_cores, &st);
+    lvl_cores[b] = std::min(level_bucket_coresident(0, b, opts->rank_cap), level_bucket_coresident(1, b, opts->rank_cap)) /
+                   coresident_share(*opts);
+  Plan* P = plan_build(n, *opts, aca_max_coresident_ctas() / coresident_share(*opts), lvl_cores, &st);
   if (!P) return st;
   *bytes_out = arena_round(256) /* context flags */ + arena_round(P->dev_bytes) + chain_bytes(P, *opts);
   delete P;
@@ -424,6 +426,7 @@ extern "C" fifa_status fifa_create(fifa_ctx** out, const fifa_opts* opts, void* 
   if (opts->prec != FIFA_FP64 && opts->prec != FIFA_MIXED) return FIFA_ERR_INVALID_ARG;
   if (opts->independent_ctas != 0 && opts->independent_ctas != 1) return FIFA_ERR_INVALID_ARG;
   if (opts->wait_polls < 0) return FIFA_ERR_INVALID_ARG;
+  if (opts->coresident_share < 0 || opts->coresident_share > 64) return FIFA_ERR_INVALID_ARG;
   if (arena_bytes < (1u << 20)) return FIFA_ERR_INVALID_ARG;
   fifa_ctx* ctx = new (std::nothrow) fifa_ctx();
   if (!ctx) return FIFA_ERR_OOM;
@@ -446,10 +449,12 @@ extern "C" fifa_status fifa_create(fifa_ctx** out, const fifa_opts* opts, void* 
   }
   ctx->arena.size = arena_bytes & ~(size_t)255;
   ctx->arena.free_[0] = ctx->arena.size;
-  ctx->aca_coresident = aca_max_coresident_ctas();
+  // the context's share of the CTAs the GPU holds at once (coresident_share)
+  ctx->aca_coresident = aca_max_coresident_ctas() / coresident_share(ctx->opts);
   for (int b = 0; b < LEVEL_BUCKETS; ++b)
     ctx->level_coresident[b] = std::min(level_bucket_coresident(0, b, ctx->opts.rank_cap),
-                                        level_bucket_coresident(1, b, ctx->opts.rank_cap));
+                                        level_bucket_coresident(1, b, ctx->opts.rank_cap)) /
+                               coresident_share(ctx->opts);
   ctx->flags = (int*)ctx->arena.alloc(256);
   ctx->host_flags = nullptr;
   cudaMallocHost((void**)&ctx->host_flags, 256);
@@ -869,7 +874,8 @@ bool sweep_batch_config(fifa_ctx* ctx, const Plan* P, int nprob, int* ls, int* r
   for (int k = P->fs_ls; k >= 0; --k) {
     int r = 0;
     for (int i = 0; i < (1 << k); ++i) r = std::max(r, P->bnd_host[bnd_off(k) + i + 1] - P->bnd_host[bnd_off(k) + i]);
-    if ((int64_t)sweep_fused_coresident(0, r, ctx->opts.rank_cap) >= ((int64_t)nprob << k)) {
+    if ((int64_t)(sweep_fused_coresident(0, r, ctx->opts.rank_cap) / coresident_share(ctx->opts)) >=
+        ((int64_t)nprob << k)) {
       *ls = k;
       *rows = r;
       return true;
@@ -1117,7 +1123,7 @@ bool mv_batch_config(fifa_ctx* ctx, const Plan* P, int nprob, int* ls, int* rows
     int r = 0;
     for (int i = 0; i < (1 << k); ++i) r = std::max(r, P->bnd_host[bnd_off(k) + i + 1] - P->bnd_host[bnd_off(k) + i]);
     if (r > MV_FUSED_ROWS_MAX) return false;
-    if ((int64_t)mv_fused_coresident(r) >= ((int64_t)nprob << k)) {
+    if ((int64_t)(mv_fused_coresident(r) / coresident_share(ctx->opts)) >= ((int64_t)nprob << k)) {
       *ls = k;
       *rows = r;
       return true;

@@ -92,6 +92,8 @@ struct fifa_fact {
 };
 
 Plan* get_plan(fifa_ctx* ctx, int64_t n, fifa_status* st);
+// The divisor of every co-resident CTA budget of a context (fifa_opts.coresident_share).
+inline int coresident_share(const fifa_opts& o) { return o.coresident_share > 1 ? o.coresident_share : 1; }
 // Point a context (created on a caller-provided arena) at another device
 // range: drops its plans and every object in the old arena (synchronizes).
 fifa_status ctx_rebind_arena(fifa_ctx* ctx, void* base, size_t bytes);

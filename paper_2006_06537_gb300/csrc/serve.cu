@@ -9,13 +9,15 @@
 // Admitted requests run concurrently, their kernels overlapping on the GPU.
 //
 // Narrow workers use independent CTAs (no CTA groups that wait on each other).
-// With wide_min_n > 0, worker 0 is the one wide worker: it runs exactly the
-// requests with n >= wide_min_n, with CTA groups and fused cooperative sweeps
-// that span the GPU; narrow workers run the rest.  Only one stream can then
-// hold kernels whose CTAs wait on each other, and every other kernel's CTAs
-// finish without waiting, so the wide worker's groups always become
-// co-resident.  Which worker runs a request depends only on its n, so its
-// arithmetic, and its result, is the same alone and in any mix.
+// With wide_min_n > 0, the first wide_workers workers are wide: they run
+// exactly the requests with n >= wide_min_n, with CTA groups and fused
+// cooperative sweeps, each launch sized to 1 / wide_workers of the CTAs the GPU
+// holds at once.  Only the wide streams hold kernels whose CTAs wait on each
+// other, at most one such launch each, and together they fit on the GPU; every
+// other kernel's CTAs finish without waiting, so the waiting launches always
+// become co-resident.  Which worker type runs a request depends only on its n,
+// and every wide worker uses the same sizes, so its arithmetic, and its
+// result, is the same alone and in any mix.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -89,6 +91,7 @@ static fifa_status request_bytes(const fifa_opts& o, const fifa_request& r, size
 static fifa_status run_request(fifa_server* S, fifa_ctx** pctx, cudaStream_t stream, Req* q) {
   fifa_opts o = S->o.opts;
   o.independent_ctas = q->wide ? 0 : 1;
+  o.coresident_share = q->wide ? S->o.wide_workers : 0;  // the wide workers' launches fit side by side
   fifa_status st;
   if (!*pctx) {
     st = fifa_create(pctx, &o, stream, q->mem, q->bytes);
@@ -196,11 +199,13 @@ static void worker_main(fifa_server* S, bool wide) {
 
 extern "C" fifa_status fifa_server_create(const fifa_server_opts* o, fifa_server** out) {
   if (!o || !out || o->slots < 1 || o->slots > 256 || o->hbm_budget < (16u << 20) || o->wide_min_n < 0 ||
-      (o->wide_min_n > 0 && o->slots < 2))
+      (o->wide_min_n > 0 && o->slots < 2) || o->wide_workers < 0 ||
+      (o->wide_min_n > 0 && std::max(1, o->wide_workers) >= o->slots) || o->wide_workers > 64)
     return FIFA_ERR_INVALID_ARG;
   *out = nullptr;
   fifa_opts fo = o->opts;
-  fo.independent_ctas = 1;  // per request: 0 for the wide worker's requests
+  fo.independent_ctas = 1;  // per request: 0 for the wide workers' requests
+  fo.coresident_share = 0;
   size_t probe = 0;
   fifa_status st = fifa_chain_bytes(&fo, 1024, &probe);  // validates the options
   if (st != FIFA_OK) return st;
@@ -208,6 +213,7 @@ extern "C" fifa_status fifa_server_create(const fifa_server_opts* o, fifa_server
   if (!S) return FIFA_ERR_OOM;
   S->o = *o;
   S->o.opts = fo;
+  S->o.wide_workers = o->wide_min_n > 0 ? std::max(1, o->wide_workers) : 0;
   S->t0 = std::chrono::steady_clock::now();
   cudaGetDevice(&S->device);
   void* p = nullptr;
@@ -220,7 +226,7 @@ extern "C" fifa_status fifa_server_create(const fifa_server_opts* o, fifa_server
   S->arena.base = S->pool;
   S->arena.size = o->hbm_budget & ~(size_t)255;
   S->arena.free_[0] = S->arena.size;
-  for (int k = 0; k < o->slots; ++k) S->workers.emplace_back(worker_main, S, k == 0 && o->wide_min_n > 0);
+  for (int k = 0; k < o->slots; ++k) S->workers.emplace_back(worker_main, S, k < S->o.wide_workers);
   *out = S;
   return FIFA_OK;
 }
@@ -239,6 +245,7 @@ extern "C" fifa_status fifa_server_submit(fifa_server* S, const fifa_request* r,
   q->wide = S->o.wide_min_n > 0 && r->n >= S->o.wide_min_n;
   fifa_opts ro = S->o.opts;
   ro.independent_ctas = q->wide ? 0 : 1;
+  ro.coresident_share = q->wide ? S->o.wide_workers : 0;
   fifa_status st = request_bytes(ro, *r, &q->bytes);
   if (st != FIFA_OK || q->bytes > S->arena.size) {
     delete q;

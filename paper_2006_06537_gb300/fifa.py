@@ -33,7 +33,7 @@ class fifa_hyper(C.Structure):
 class fifa_opts(C.Structure):
     _fields_ = [("leaf_size", C.c_int), ("aca_tol", C.c_double), ("rank_cap", C.c_int), ("prec", C.c_int),
                 ("refine_tol", C.c_double), ("refine_max", C.c_int), ("independent_ctas", C.c_int),
-                ("wait_polls", C.c_int)]
+                ("wait_polls", C.c_int), ("coresident_share", C.c_int)]
 
 
 class fifa_plan_info(C.Structure):
@@ -47,7 +47,8 @@ class fifa_prior(C.Structure):
 
 
 class fifa_server_opts(C.Structure):
-    _fields_ = [("opts", fifa_opts), ("hbm_budget", C.c_size_t), ("slots", C.c_int), ("wide_min_n", C.c_int64)]
+    _fields_ = [("opts", fifa_opts), ("hbm_budget", C.c_size_t), ("slots", C.c_int), ("wide_min_n", C.c_int64),
+                ("wide_workers", C.c_int)]
 
 
 class fifa_request(C.Structure):
@@ -387,9 +388,9 @@ def fifa_destroy_tensor(ctx, model):
     lib().fifa_destroy_tensor(ctx, model)
 
 
-def fifa_server_create(opts: fifa_opts, hbm_budget: int, slots: int, wide_min_n: int = 0):
+def fifa_server_create(opts: fifa_opts, hbm_budget: int, slots: int, wide_min_n: int = 0, wide_workers: int = 1):
     h = C.c_void_p()
-    so = fifa_server_opts(opts, C.c_size_t(int(hbm_budget)), int(slots), int(wide_min_n))
+    so = fifa_server_opts(opts, C.c_size_t(int(hbm_budget)), int(slots), int(wide_min_n), int(wide_workers))
     _check(lib().fifa_server_create(C.byref(so), C.byref(h)), "fifa_server_create")
     return h
 

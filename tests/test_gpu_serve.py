@@ -130,17 +130,21 @@ def _mix(count=10, seed=11):
 WIDE = 1 << 14  # requests with n >= WIDE run on the wide worker (CTA groups, fused sweeps)
 
 
-def test_server_result_same_alone_and_in_mix():
+@pytest.mark.parametrize("wide_workers", [1, 2])
+def test_server_result_same_alone_and_in_mix(wide_workers):
+    # with two wide workers, two requests' grouped launches (each sized to half
+    # the GPU) run side by side; a request's result must not depend on it
     reqs = _mix()
-    assert any(len(r[0]) >= WIDE for r in reqs) and any(len(r[0]) < WIDE for r in reqs)
-    srv = fifa.fifa_server_create(_opts(eps=1e-10), 8 << 30, 6, WIDE)
+    assert sum(len(r[0]) >= WIDE for r in reqs) >= 2 and any(len(r[0]) < WIDE for r in reqs)
+    srv = fifa.fifa_server_create(_opts(eps=1e-10), 8 << 30, 6, WIDE, wide_workers)
     mixed = _run(srv, reqs)
     stats = fifa.fifa_server_stats(srv)
     fifa.fifa_server_destroy(srv)
     assert stats.completed == len(reqs)
+    assert all(m[2].status == fifa.FIFA_OK for m in mixed)
     assert stats.peak_in_flight > 1  # requests really overlapped
     for k in (0, len(reqs) // 2, int(np.argmax([len(r[0]) for r in reqs]))):
-        srv = fifa.fifa_server_create(_opts(eps=1e-10), 8 << 30, 2, WIDE)
+        srv = fifa.fifa_server_create(_opts(eps=1e-10), 8 << 30, 1 + wide_workers, WIDE, wide_workers)
         (mean, draws, res), = _run(srv, [reqs[k]])
         fifa.fifa_server_destroy(srv)
         assert res.status == fifa.FIFA_OK and mixed[k][2].status == fifa.FIFA_OK
