@@ -75,9 +75,10 @@ typedef struct {
   int refine_max;     /* MIXED: conjugate-gradient steps captured per solve (fixed; once every system
                          has converged the remaining steps' launches return at once) */
   int independent_ctas; /* 1: no kernel splits a tree node over a group of CTAs that wait on each
-                           other (every CTA runs independently); required when several contexts
-                           launch work concurrently on one GPU, since grouped kernels size their
-                           groups to the whole GPU.  0: groups fill the GPU for the top levels. */
+                           other (every CTA runs independently).  0: groups fill the GPU (or the
+                           context's coresident_share of it) for the top levels.  Several
+                           contexts that launch work concurrently on one GPU need 1, or 0 with
+                           coresident_share >= the number of such contexts. */
   int wait_polls;     /* a CTA waiting for the rest of its group gives up after this many polls
                          (each followed by a 64 ns sleep), sets FIFA_ERR_TIMEOUT in the object's
                          status and makes the whole launch return; 0: the default 2^26 polls
