@@ -143,13 +143,15 @@ static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, const int*
   // ACA groups.  A level-l block has ~n/2^l rows + columns and every level has
   // about the same total work, so the co-resident CTA budget is split evenly
   // over the top levels: level l gets G_l = budget / (levels * 2^l) CTAs per
-  // block (>= 2 to be worth a group).  Levels below run one CTA per block in a
-  // second launch.
+  // block, at most one per 1024 block rows (>= 2 to be worth a group; blocks
+  // from 4096 rows).  Levels below run one CTA per block in a second launch.
+  // (Mid-size problems are latency-bound at their top levels: groups of one
+  // CTA per 4096 rows left the level-0 block of n = 2^14 on four SMs.)
   std::vector<int> Gl(P->L, 1);
   int ncoop_levels = 0;
   for (int l = 0; groups && l < P->L; ++l) {
     const int64_t entries = n >> l;
-    if (entries < 8192) break;
+    if (entries < 4096) break;
     ncoop_levels = l + 1;
   }
   while (ncoop_levels > 0) {
@@ -160,7 +162,7 @@ static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, const int*
   if (ncoop_levels > 0) {
     const int per_level = aca_cores / ncoop_levels;
     for (int l = 0; l < ncoop_levels; ++l) {
-      const int64_t want = std::max<int64_t>(2, (n >> l) / 4096);
+      const int64_t want = std::max<int64_t>(2, (n >> l) / 1024);
       Gl[l] = (int)std::min<int64_t>(want, per_level >> l);
       if (Gl[l] < 2) Gl[l] = 1;
     }
