@@ -188,17 +188,19 @@ static Plan* plan_build(int64_t n, const fifa_opts& o, int aca_cores, const int*
   P->work_host.insert(P->work_host.end(), solo.begin(), solo.end());
   P->work_host.insert(P->work_host.end(), warp.begin(), warp.end());
   // factor / sweep groups per level: levels with fewer nodes than the
-  // co-resident CTAs split each node's rows over a group of CTAs (>= 1024 rows
-  // each) that fills the GPU; each rank bucket's kernel has its own CTAs per SM
-  // and so its own group size
+  // co-resident CTAs split each node's rows over a group of CTAs that fills
+  // the GPU, each CTA with >= 512 rows (>= 256 up to n = 2^15, where the top
+  // levels' latency, not their work, sets the time); each rank bucket's kernel
+  // has its own CTAs per SM and so its own group size
   for (int b = 0; b < LEVEL_BUCKETS; ++b) P->lvl_G[b].assign(P->L, 1);
   P->sweep_G.assign(P->L, 1);
+  const int64_t per = n <= 32768 ? 256 : 512;
   for (int l = 0; l < P->L; ++l) {
     const int64_t len = (n + ((int64_t)1 << l) - 1) >> l;
     const int64_t nodes = (int64_t)1 << l;
     for (int b = 0; b < LEVEL_BUCKETS; ++b)
-      if (groups && 2 * nodes <= lvl_cores[b] && len >= 2048) {
-        const int64_t G = std::min<int64_t>(len / 1024, lvl_cores[b] / nodes);
+      if (groups && 2 * nodes <= lvl_cores[b] && len >= 2 * per) {
+        const int64_t G = std::min<int64_t>(len / per, lvl_cores[b] / nodes);
         P->lvl_G[b][l] = (int)std::max<int64_t>(1, G);
       }
     P->sweep_G[l] = (int)std::max<int64_t>(1, (len + 2047) / 2048);

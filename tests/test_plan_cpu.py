@@ -7,8 +7,8 @@
   CTAs within the co-resident budget), in the warp-per-block part exactly when
   its node spans at most 256 rows, otherwise one CTA per block;
 * the level kernels' CTA groups: a level gets groups (G > 1) only if its rows
-  give each CTA of a group at least 1024 and all groups of the level are
-  co-resident (nodes x G <= the bucket's budget);
+  give each CTA of a group at least 512 (256 for n <= 2^15) and all groups of
+  the level are co-resident (nodes x G <= the bucket's budget);
 * independent CTAs: no groups anywhere.
 """
 import os
@@ -100,7 +100,8 @@ def test_level_groups_are_co_resident(fifa, n, B):
             span = (n + nodes - 1) // nodes
             assert g >= 1
             if g > 1:
-                assert nodes * g <= BUDGET["lvl"][bkt] and span // g >= 1024 and 2 * nodes <= BUDGET["lvl"][bkt]
+                per = 256 if n <= 32768 else 512
+                assert nodes * g <= BUDGET["lvl"][bkt] and span // g >= per and 2 * nodes <= BUDGET["lvl"][bkt]
 
 
 def test_independent_ctas_have_no_groups(fifa):
