@@ -48,6 +48,11 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The serving leg runs 16 worker streams: with CUDA's default of 8 hardware
+# work queues, streams share queues and unrelated kernels wait on each other
+# (measured on the 48-request sample: 332 -> 375 iterations/s with 32 queues).
+# The setting is read when the process creates its CUDA context.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 from paper_2006_06537_gb300.inputs import clustered  # noqa: E402
 

@@ -399,8 +399,11 @@ void fifa_destroy_tensor(fifa_ctx* ctx, fifa_tensor* model);
  * on each other), each sized to 1 / wide_workers of the CTAs the GPU holds at
  * once, so the wide workers' waiting launches always fit on the GPU together.
  * A request's worker type depends only on its n, and every wide worker uses
- * the same sizes, so its result does not depend on what else is in flight.  This API
- * has no counterpart in the paper; it serves its sampler to many users. */
+ * the same sizes, so its result does not depend on what else is in flight.
+ * The workers' streams overlap only as far as the process's hardware work
+ * queues allow: CUDA_DEVICE_MAX_CONNECTIONS (default 8, read when the process
+ * creates its CUDA context) should be at least `slots`.  This API has no
+ * counterpart in the paper; it serves its sampler to many users. */
 typedef struct fifa_server fifa_server;
 typedef struct {
   fifa_opts opts;     /* leaf size, ACA tolerance, rank cap, precision of every request */
