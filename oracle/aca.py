@@ -11,23 +11,25 @@ so that the GPU reproduces the same pivots bit for bit:
         rho_j  = A[i, j] - sum_{l<k} U[i, l] V[j, l]      for every column j
         j*     = argmax over unused columns of |rho_j|    (lowest j on ties)
         if rho_j* == 0 (or every column is used): stop
-        v      = rho / rho_j*
+        v      = rho * (1 / rho_j*)         (one IEEE division, then products)
         u_i'   = A[i', j*] - sum_{l<k} U[i', l] V[j*, l]  for every row i'
         if max |u| <= eps: stop (this term is not kept)
         keep U[:, k] = u, V[:, k] = v; mark row i and column j* used
         i      = argmax over unused rows of |u_i'|        (lowest i on ties)
     if no unused row remains the loop ends.
 
-Every sum above is accumulated from l = 0 upward as acc = acc - (U * V): one
-IEEE binary64 product then one difference, never a fused multiply-add.  Since
-|v| <= 1 with equality at j*, max|u| * max|v| = max|u| is the size of the new
-term, the max-norm estimate of the remaining error.
+Every sum above is accumulated from l = 0 upward as acc = fma(-U, V, acc):
+acc - U * V with one rounding (IEEE fused multiply-add, `oracle/fmath.py`).
+Since |v| <= 1 (up to one rounding of the reciprocal and one of the product,
+|v| <= 1 + 2**-51) with v_j* within that of 1, max|u| * max|v| = max|u| is the
+size of the new term, the max-norm estimate of the remaining error.
 """
 from __future__ import annotations
 
 import numpy as np
 
 from .detmath import kernel_entries
+from .fmath import fma
 
 
 def aca_entries(row_fn, col_fn, m, p, eps, cap):
@@ -47,15 +49,15 @@ def aca_entries(row_fn, col_fn, m, p, eps, cap):
             break
         rho = np.array(row_fn(i), dtype=np.float64)
         for l in range(k):
-            rho = rho - Ucols[l][i] * Vcols[l]
+            rho = fma(-Ucols[l][i], Vcols[l], rho)
         a = np.where(col_used, -1.0, np.abs(rho))
         j = int(np.argmax(a))  # first maximal index
         if a[j] <= 0.0:
             break
-        v = rho / rho[j]
+        v = rho * (1.0 / rho[j])
         u = np.array(col_fn(j), dtype=np.float64)
         for l in range(k):
-            u = u - Ucols[l] * Vcols[l][j]
+            u = fma(-Ucols[l], Vcols[l][j], u)
         if np.max(np.abs(u)) <= eps:
             break
         Ucols.append(u)

@@ -3,18 +3,20 @@
 The ACA pivots must be bit-identical between this oracle and the GPU, so the
 kernel entries feeding them must be bit-identical too.  Library ``exp``
 functions differ in their last bit between platforms, so both sides evaluate
-``det_exp``: a fixed sequence of IEEE-754 binary64 multiplications and
-additions (no fused multiply-add), defined here from the textbook method
-(Tang's table-driven exponential):
+``det_exp``: a fixed sequence of IEEE-754 binary64 operations (products,
+and fused multiply-adds with one rounding each, `oracle/fmath.py`), defined
+here from the textbook method (Tang's table-driven exponential):
 
 * argument reduction x = (32 m + j) ln2/32 + r with k = 32 m + j = rint(x 32/ln2),
   0 <= j < 32, ln2/32 split as HI + LO where HI keeps only the leading 32
   significand bits so that k * HI is exact for |k| < 2**21 (Cody & Waite);
+  r = fma(-k, LO, fma(-k, HI, x));
 * e**x = 2**m 2**(j/32) e**r with 2**(j/32) from a 32-entry table of correctly
   rounded values (computed here in 60-digit decimal arithmetic) and
   e**r = 1 + q, q = r(1 + r/2 + ... + r**5/6!) (|r| <= ln2/64, truncation
-  below 4e-18 relative) by Horner's rule highest power first;
-* the result t + t q with t = 2**(j/32) 2**m built exactly (exponent field).
+  below 4e-18 relative) by Horner's rule highest power first, each step one
+  fused multiply-add p = fma(p, r, 1/j!), then q = p * r;
+* the result fma(t, q, t) with t = 2**(j/32) 2**m built exactly (exponent field).
 
 Inputs below -708 return exactly 0.0 (the true value is below 3.3e-308, and
 this cut keeps every nonzero result a normal number).
@@ -25,7 +27,8 @@ length-scale form used by the workloads):
 * squared exponential:  k(d) = exp(-d^2 / (2 rho^2)),
   evaluated as det_exp(-((d*d)*c)) with c = 0.5/(rho*rho);
 * Matern-5/2:  k(d) = (1 + t + t^2/3) exp(-t), t = sqrt(5)|d|/rho,
-  evaluated as ((1+t) + (t*t)/3) * det_exp(-t) with t = |d| * (sqrt(5)/rho).
+  evaluated as fma(t*t, THIRD, 1+t) * det_exp(-t) with t = |d| * (sqrt(5)/rho)
+  and THIRD = 1/3 rounded to binary64.
 
 Both are unit-variance correlations; the nugget is added to the diagonal by
 the caller (Sec. 4.1.4, "Additional considerations").
@@ -37,6 +40,8 @@ import struct
 from decimal import Decimal, getcontext
 
 import numpy as np
+
+from .fmath import fma
 
 KERNEL_SE = 0
 KERNEL_MATERN52 = 1
@@ -71,22 +76,23 @@ EXP2_TABLE = _exp2_table()
 # 1/j! correctly rounded; j! is exact in binary64 for j <= 18.
 TAYLOR = [1.0 / math.factorial(j) for j in range(7)]
 EXP_MIN_ARG = -708.0
+THIRD = 1.0 / 3.0  # binary64 nearest to 1/3 (IEEE division)
 
 
 def det_exp(x):
     """Elementwise e**x by the fixed operation sequence described in the module doc."""
     x = np.asarray(x, dtype=np.float64)
     k = np.rint(x * INV_LN2N)
-    r = (x - k * LN2N_HI) - k * LN2N_LO
-    q = np.full_like(x, TAYLOR[6])
+    r = fma(-k, LN2N_LO, fma(-k, LN2N_HI, x))
+    p = np.full_like(x, TAYLOR[6])
     for j in range(5, 0, -1):
-        q = q * r + TAYLOR[j]
-    q = q * r
+        p = fma(p, r, TAYLOR[j])
+    q = p * r
     ki = np.where(x < EXP_MIN_ARG, 0, k).astype(np.int64)
     j = ki & (EXP_TABLE_N - 1)
     m = ki >> 5
     t = (EXP2_TABLE[j].view(np.int64) + (m << 52)).view(np.float64)
-    out = t + t * q
+    out = fma(t, q, t)
     return np.where(x < EXP_MIN_ARG, 0.0, out)
 
 
@@ -106,6 +112,6 @@ def kernel_entries(kind: int, c: float, xa, xb):
         return det_exp(-((d * d) * c))
     if kind == KERNEL_MATERN52:
         t = np.abs(d) * c
-        poly = (1.0 + t) + (t * t) / 3.0
+        poly = fma(t * t, THIRD, 1.0 + t)
         return poly * det_exp(-t)
     raise ValueError("unknown kernel")

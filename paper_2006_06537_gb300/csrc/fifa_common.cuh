@@ -108,37 +108,40 @@ static __device__ const double kExp2Tab[32] = {
     0x1.d5818dcfba487p+0, 0x1.dfc97337b9b5fp+0, 0x1.ea4afa2a490dap+0, 0x1.f50765b6e4540p+0};
 
 // Deterministic e^x: x = (32 m + j) ln2/32 + r, k = rint(32 x / ln2) (ln2/32
-// split so that k * HI is exact), e^x = 2^m 2^(j/32) (1 + q) with
-// q = r (1 + r/2 + ... + r^5/6!) by Horner's rule, returned as t + t q with
-// t = 2^(j/32) 2^m built exactly.  Separate IEEE products and sums only (no
-// fused multiply-add), the same sequence as the CPU reference; x < -708 -> 0.
+// split as HI + LO), r = fma(-k, LO, fma(-k, HI, x)), e^x = 2^m 2^(j/32) (1 + q)
+// with p = 1 + r/2 + ... + r^5/6! by Horner's rule (one fused multiply-add
+// per step) and q = p r, returned as fma(t, q, t) with t = 2^(j/32) 2^m built
+// exactly.  Every operation is an explicitly rounded IEEE product or fused
+// multiply-add (none left to the compiler to contract), the same sequence as
+// the CPU reference; x < -708 -> 0.  11 FP64 operations.
 __device__ __forceinline__ double det_exp(double x) {
   if (!(x >= -708.0)) return x != x ? x : 0.0;
   const double INV_LN2N = 0x1.71547652b82fep+5;
   const double LN2N_HI = 0x1.62e42fee00000p-6;
   const double LN2N_LO = 0x1.a39ef35793c76p-38;
   const double k = rint(__dmul_rn(x, INV_LN2N));
-  const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(k, LN2N_HI)), __dmul_rn(k, LN2N_LO));
-  double q = 1.0 / 720.0;
-  q = __dadd_rn(__dmul_rn(q, r), 1.0 / 120.0);
-  q = __dadd_rn(__dmul_rn(q, r), 1.0 / 24.0);
-  q = __dadd_rn(__dmul_rn(q, r), 1.0 / 6.0);
-  q = __dadd_rn(__dmul_rn(q, r), 0.5);
-  q = __dadd_rn(__dmul_rn(q, r), 1.0);
-  q = __dmul_rn(q, r);
+  const double r = __fma_rn(-k, LN2N_LO, __fma_rn(-k, LN2N_HI, x));
+  double p = 1.0 / 720.0;
+  p = __fma_rn(p, r, 1.0 / 120.0);
+  p = __fma_rn(p, r, 1.0 / 24.0);
+  p = __fma_rn(p, r, 1.0 / 6.0);
+  p = __fma_rn(p, r, 0.5);
+  p = __fma_rn(p, r, 1.0);
+  const double q = __dmul_rn(p, r);
   const long long ki = (long long)k;
   const unsigned long long tb = (unsigned long long)__double_as_longlong(__ldg(&kExp2Tab[ki & 31])) +
                                 ((unsigned long long)(ki >> 5) << 52);
   const double t = __longlong_as_double((long long)tb);
-  return __dadd_rn(t, __dmul_rn(t, q));
+  return __fma_rn(t, q, t);
 }
 
-// Unit-variance kernel entry k(xa, xb), bit-identical to the CPU reference.
+// Unit-variance kernel entry k(xa, xb), bit-identical to the CPU reference:
+// SE det_exp(-((d d) c)); Matern-5/2 fma(t t, 1/3, 1 + t) det_exp(-t), t = |d| c.
 __device__ __forceinline__ double kern_entry(int kind, double kc, double xa, double xb) {
   double d = __dsub_rn(xa, xb);
   if (kind == 0) return det_exp(-__dmul_rn(__dmul_rn(d, d), kc));
   double t = __dmul_rn(fabs(d), kc);
-  double poly = __dadd_rn(__dadd_rn(1.0, t), __ddiv_rn(__dmul_rn(t, t), 3.0));
+  double poly = __fma_rn(__dmul_rn(t, t), 1.0 / 3.0, __dadd_rn(1.0, t));
   return __dmul_rn(poly, det_exp(-t));
 }
 

@@ -72,8 +72,9 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(const HmatDesc* __restric
 // ACA.  work[cta] = {level, node, g, G}: the G CTAs of one group split the
 // block's rows and columns; every CTA of the group takes identical pivot
 // decisions from the same reduced data, so only partial maxima are exchanged.
-// The arithmetic (products then differences, l ascending, IEEE division)
-// matches the CPU reference operation for operation.
+// The arithmetic (fused multiply-adds acc - U V with l ascending, the row
+// scaled by one IEEE reciprocal of the pivot) matches the CPU reference
+// operation for operation.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 4) k_aca(const HmatDesc* __restrict__ Hd, const int4* __restrict__ work,
                                               ArgMax* __restrict__ part, unsigned int* __restrict__ bar,
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(256, 4) k_aca(const HmatDesc* __restrict__ Hd,
       for (int j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
         double acc = kern_entry(kind, kc, xi, x[h + j]);
         for (int l = 0; l < k; ++l)
-          acc = __dsub_rn(acc, __dmul_rn(__ldcg(Bs + (size_t)l * n + s + i), Bs[(size_t)l * n + h + j]));
+          acc = __fma_rn(-__ldcg(Bs + (size_t)l * n + s + i), Bs[(size_t)l * n + h + j], acc);
         Bs[(size_t)k * n + h + j] = acc;
         // an entry that would win is checked against the used columns (the
         // check runs only then: same result as checking every entry)
@@ -143,9 +144,10 @@ __global__ void __launch_bounds__(256, 4) k_aca(const HmatDesc* __restrict__ Hd,
       if (!(best.v > 0.0)) break;
       const int js = best.i;
       const double piv = best.sv;
+      const double rpiv = __ddiv_rn(1.0, piv);
       for (int j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
         double* vp = Bs + (size_t)k * n + h + j;
-        *vp = __ddiv_rn(*vp, piv);
+        *vp = __dmul_rn(*vp, rpiv);
       }
       // residual of column js over this CTA's rows, stored in U[:, k]
       const double xj = x[h + js];
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(256, 4) k_aca(const HmatDesc* __restrict__ Hd,
       for (int ii = r0 + threadIdx.x; ii < r1; ii += blockDim.x) {
         double acc = kern_entry(kind, kc, x[s + ii], xj);
         for (int l = 0; l < k; ++l)
-          acc = __dsub_rn(acc, __dmul_rn(Bs[(size_t)l * n + s + ii], __ldcg(Bs + (size_t)l * n + h + js)));
+          acc = __fma_rn(-Bs[(size_t)l * n + s + ii], __ldcg(Bs + (size_t)l * n + h + js), acc);
         Bs[(size_t)k * n + s + ii] = acc;
         umax = nn_max(umax, fabs(acc));
         const ArgMax cand{fabs(acc), ii, acc};
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(256, 3) k_aca_warp(const HmatDesc* __restrict_
       for (int j = lane; j < p; j += 32) {
         double acc = kern_entry(kind, kc, xi, x[h + j]);
         for (int l = 0; l < k; ++l)
-          acc = __dsub_rn(acc, __dmul_rn(__ldcg(Bs + (size_t)l * n + s + i), __ldcg(Bs + (size_t)l * n + h + j)));
+          acc = __fma_rn(-__ldcg(Bs + (size_t)l * n + s + i), __ldcg(Bs + (size_t)l * n + h + j), acc);
         Bs[(size_t)k * n + h + j] = acc;
         // an entry that would win is checked against the used columns (the
         // check runs only then: same result as checking every entry)
@@ -269,9 +271,10 @@ __global__ void __launch_bounds__(256, 3) k_aca_warp(const HmatDesc* __restrict_
       if (!(best.v > 0.0)) break;
       const int js = best.i;
       const double piv = best.sv;
+      const double rpiv = __ddiv_rn(1.0, piv);
       for (int j = lane; j < p; j += 32) {
         double* vp = Bs + (size_t)k * n + h + j;
-        *vp = __ddiv_rn(*vp, piv);
+        *vp = __dmul_rn(*vp, rpiv);
       }
       __syncwarp();
       // residual of column js, stored in U[:, k]
@@ -281,7 +284,7 @@ __global__ void __launch_bounds__(256, 3) k_aca_warp(const HmatDesc* __restrict_
       for (int ii = lane; ii < m; ii += 32) {
         double acc = kern_entry(kind, kc, x[s + ii], xj);
         for (int l = 0; l < k; ++l)
-          acc = __dsub_rn(acc, __dmul_rn(__ldcg(Bs + (size_t)l * n + s + ii), __ldcg(Bs + (size_t)l * n + h + js)));
+          acc = __fma_rn(-__ldcg(Bs + (size_t)l * n + s + ii), __ldcg(Bs + (size_t)l * n + h + js), acc);
         Bs[(size_t)k * n + s + ii] = acc;
         umax = nn_max(umax, fabs(acc));
         const ArgMax cand{fabs(acc), ii, acc};

@@ -1,18 +1,44 @@
 """Pins for the oracle's deterministic exponential, kernels and random numbers.
 
-Each check ties the oracle to something outside itself: libm's exp and the
+Each check ties the oracle to something outside itself: exact rational
+arithmetic for the fused multiply-add, libm's exp and the
 closed-form kernels, the mathematical definitions of the Philox Weyl
 increments, distribution laws of uniforms / normals / gamma variates
 (scipy.stats), and bit-avalanche behaviour of a 10-round Philox.
 """
 import math
 from decimal import Decimal, getcontext
+from fractions import Fraction
 
 import numpy as np
 import pytest
 from scipy import stats
 
-from oracle import detmath, rng
+from oracle import detmath, fmath, rng
+
+
+def _fma_exact(a, b, c):
+    """a * b + c in exact rational arithmetic, rounded once (float(Fraction) rounds to nearest-even)."""
+    return float(Fraction(a) * Fraction(b) + Fraction(c))
+
+
+def test_fma_is_one_rounding_of_the_exact_value():
+    g = np.random.default_rng(5)
+    a = g.standard_normal(3000) * 2.0 ** g.integers(-40, 40, 3000)
+    b = g.standard_normal(3000) * 2.0 ** g.integers(-40, 40, 3000)
+    # c near -a*b: the cases where a separately rounded product loses the most
+    c = np.concatenate([-(a[:1000] * b[:1000]), g.standard_normal(2000)])
+    got = fmath.fma(a, b, c)
+    ref = np.array([_fma_exact(float(x), float(y), float(z)) for x, y, z in zip(a, b, c)])
+    assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
+    # a case a product-then-sum gets wrong: (1 + 2^-30)(1 - 2^-30) - 1 = -2^-60 exactly
+    t = fmath.fma(1 + 2.0 ** -30, 1 - 2.0 ** -30, -1.0)
+    assert t == -(2.0 ** -60) and (1 + 2.0 ** -30) * (1 - 2.0 ** -30) - 1.0 == 0.0
+    # ties round to even: 1 + 2^-53 (exactly between 1 and 1 + 2^-52)
+    assert fmath.fma(2.0 ** -27, 2.0 ** -26, 1.0) == 1.0
+    assert fmath.fma(3 * 2.0 ** -27, 2.0 ** -26, 1.0) == 1 + 2.0 ** -51
+    # broadcasting and shapes
+    assert fmath.fma(np.ones((2, 3)), 2.0, np.arange(3.0)).shape == (2, 3)
 
 
 def test_det_exp_within_one_ulp_of_libm():
