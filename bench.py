@@ -89,6 +89,9 @@ def parse():
     ap.add_argument("--cap", type=int, default=CAP, help="ACA rank cap (profiling runs: a smaller arena)")
     ap.add_argument("--refine-tol", type=float, default=1e-10,
                     help="mixed path: conjugate gradients stop at ||b - M~ x|| <= tol ||b||")
+    ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
+                    help="1: the proposal's assembly and factorization run on a second stream beside the draw "
+                         "(fifa_opts.overlap_proposal; same results as 0)")
     ap.add_argument("--no-roofline", action="store_true", help="skip the roofline probe")
     ap.add_argument("--config-table", action="store_true",
                     help="time the other single-chain configurations (n = 2048 sine, FP64; n = 131072 Matern-5/2, "
@@ -306,7 +309,8 @@ def gpu_arm(args):
     def make(prec, leaf, refine_max=8, arena_gb=args.arena_gb):
         with torch.cuda.stream(stream):
             ctx = fifa.Context(leaf_size=leaf, aca_tol=EPS, rank_cap=args.cap, prec=prec, refine_max=refine_max,
-                               refine_tol=args.refine_tol, arena_bytes=int(arena_gb) << 30, stream=stream)
+                               refine_tol=args.refine_tol, arena_bytes=int(arena_gb) << 30, stream=stream,
+                               overlap_proposal=args.overlap)
             xd = torch.tensor(x, device="cuda")
             yd = torch.tensor(y, device="cuda")
             pr = fifa.fifa_prior(1.0, 1.0, 1.0, 1.0, prior_mu, 1.0, 0.2)
@@ -466,7 +470,7 @@ def gpu_arm(args):
         "config": {"workload": f"clustered SE n={n}, 8 clusters, rho0={RHO0}, sigma={NOISE}", "n": n, "leaf": leaf,
                    "leaf_autotune_ms": tune, "aca_tol": EPS, "rank_cap": CAP, "nugget": args.nugget,
                    "precision": head, "l2": "inputs and H-matrices (>> 129 MB L2) resident; no flush needed",
-                   "parallelism": f"replicas x{world}"},
+                   "overlap_proposal": args.overlap, "parallelism": f"replicas x{world}"},
         "paths": paths,
         "mixed_vs_fp64": cmp,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
@@ -521,7 +525,8 @@ def config_table(args, fifa, torch, stream):
         vy = float(np.var(y))
         with torch.cuda.stream(stream):
             ctx = fifa.Context(leaf_size=leaf, aca_tol=eps, rank_cap=CAP, prec=prec, refine_max=8,
-                               refine_tol=args.refine_tol, arena_bytes=8 << 30, stream=stream)
+                               refine_tol=args.refine_tol, arena_bytes=8 << 30, stream=stream,
+                               overlap_proposal=args.overlap)
             ch = fifa.fifa_chain_create(ctx.h, torch.tensor(x, device="cuda"), torch.tensor(y, device="cuda"), n,
                                         fifa.fifa_hyper(kind, vy, rho, 0.5 * vy, 1e-6),
                                         fifa.fifa_prior(1.0, 1.0, 1.0, 1.0, math.log(rho), 1.0, 0.2), 0, 0)

@@ -87,6 +87,15 @@ typedef struct {
                            GPU holds at once.  k > 1: at most 1/k of them, so that k contexts
                            with independent_ctas = 0 may launch such work side by side (their
                            waiting launches then fit on the GPU together).  1..64 */
+  int overlap_proposal; /* 1: a chain of this context runs the assembly and factorization of its
+                           proposal C~(rho') on a second stream of its own, concurrently with
+                           Algorithm 1's draw and the sigma2 / tau2 updates (they do not depend
+                           on each other: rho' comes from the previous iteration's state).  Only
+                           kernels whose CTAs never wait on each other run beside the draw; the
+                           grouped top-level ACA runs before it and the grouped top-level
+                           factorization after it, so launch sizes and every result are the same
+                           as with 0.  Costs a second scratch area per chain (fifa_chain_bytes
+                           counts it).  0 or 1 */
 } fifa_opts;
 
 /* Priors: inverse-gamma IG(shape, scale) on tau2 and sigma2 (the conjugate

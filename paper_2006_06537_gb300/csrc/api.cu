@@ -431,6 +431,7 @@ extern "C" fifa_status fifa_create(fifa_ctx** out, const fifa_opts* opts, void* 
   if (opts->independent_ctas != 0 && opts->independent_ctas != 1) return FIFA_ERR_INVALID_ARG;
   if (opts->wait_polls < 0) return FIFA_ERR_INVALID_ARG;
   if (opts->coresident_share < 0 || opts->coresident_share > 64) return FIFA_ERR_INVALID_ARG;
+  if (opts->overlap_proposal != 0 && opts->overlap_proposal != 1) return FIFA_ERR_INVALID_ARG;
   if (arena_bytes < (1u << 20)) return FIFA_ERR_INVALID_ARG;
   fifa_ctx* ctx = new (std::nothrow) fifa_ctx();
   if (!ctx) return FIFA_ERR_OOM;
@@ -554,18 +555,36 @@ fifa_status hmat_alloc(fifa_ctx* ctx, Plan* P, int kind, fifa_hmat** out) {
 
 // Enqueue assembly of H for inputs x (device) with kernel constant kc (host value).
 fifa_status hmat_assemble_enqueue(fifa_ctx* ctx, fifa_hmat* H) {
+  fifa_status st = hmat_assemble_grouped_enqueue(ctx, H);
+  return st == FIFA_OK ? hmat_assemble_rest_enqueue(ctx, H) : st;
+}
+
+// First part of the assembly: descriptor reset and the grouped ACA launch (the
+// only assembly kernel whose CTAs wait on each other).
+fifa_status hmat_assemble_grouped_enqueue(fifa_ctx* ctx, fifa_hmat* H) {
   Plan* P = H->plan;
   fifa_status st = ensure_scratch(ctx, P);
   if (st != FIFA_OK) return st;
   Scratch S = carve(ctx, P);
   cudaStream_t s = ctx->stream;
   CK(launch_prep_hmat(H->dev, P->nnodes, s));
-  CK(launch_leaf_assemble(H->dev, P->nleaf, s));
   if (P->aca_ncoop > 0) {
     CK(cudaMemsetAsync(S.aca_bar, 0, sizeof(unsigned int) * P->aca_ncoop, s));
     CK(cudaMemsetAsync(S.flags, 0, sizeof(int), s));
     CK(launch_aca(H->dev, P->aca_work, P->aca_ncoop, true, S.aca_part, S.aca_bar, S.flags, s));
   }
+  return FIFA_OK;
+}
+
+// Second part (after the first in stream order): dense leaves, one-CTA and
+// one-warp ACA blocks; independent CTAs only.
+fifa_status hmat_assemble_rest_enqueue(fifa_ctx* ctx, fifa_hmat* H) {
+  Plan* P = H->plan;
+  fifa_status st = ensure_scratch(ctx, P);
+  if (st != FIFA_OK) return st;
+  Scratch S = carve(ctx, P);
+  cudaStream_t s = ctx->stream;
+  CK(launch_leaf_assemble(H->dev, P->nleaf, s));
   if (P->aca_nsolo > 0) CK(launch_aca(H->dev, P->aca_work + P->aca_ncoop, P->aca_nsolo, false, S.aca_part, S.aca_bar, S.flags, s));
   if (P->aca_nwarp > 0) CK(launch_aca_warp(H->dev, P->aca_work + P->aca_ncoop + P->aca_nsolo, P->aca_nwarp, s));
   return FIFA_OK;
@@ -768,15 +787,39 @@ fifa_status fact_set_skip(fifa_ctx* ctx, fifa_fact* F, const int* skip_dev) {
 
 // Enqueue the factorization of the (possibly view) matrix described by Hdev.
 fifa_status fact_enqueue(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev) {
+  fifa_status st = fact_enqueue_part(ctx, F, Hdev, 0);
+  return st == FIFA_OK ? fact_enqueue_part(ctx, F, Hdev, 1) : st;
+}
+
+// The deepest level whose level kernels split no node over a CTA group: levels
+// >= it run with independent CTAs (groups only ever take the top levels).
+int fact_ungrouped_from(const Plan* P) {
+  int l = P->L;
+  while (l > 0) {
+    const int q = l - 1;
+    if (std::max({P->lvl_G[0][q], P->lvl_G[1][q], P->lvl_G[2][q]}) > 1) break;
+    l = q;
+  }
+  return l;
+}
+
+// part 0: descriptor reset, leaves and the levels from the deepest up to
+// fact_ungrouped_from (independent CTAs only); part 1: the grouped levels
+// above, the log-determinant and the FP32 copy.  Part 1 after part 0.
+fifa_status fact_enqueue_part(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev, int part) {
   Plan* P = F->plan;
   fifa_status st = ensure_scratch(ctx, P);
   if (st != FIFA_OK) return st;
   Scratch S = carve(ctx, P);
   cudaStream_t s = ctx->stream;
   const int prec = F->host.prec, cap = ctx->opts.rank_cap;
-  CK(launch_prep_fact(F->dev, Hdev, P->nnodes, s));
-  CK(launch_leaf_factor(Hdev, F->dev, prec, P->nleaf, P->Bm, P->L, cap, s));
-  for (int l = P->L - 1; l >= 0; --l) {
+  const int lsplit = fact_ungrouped_from(P);
+  if (part == 0) {
+    CK(launch_prep_fact(F->dev, Hdev, P->nnodes, s));
+    CK(launch_leaf_factor(Hdev, F->dev, prec, P->nleaf, P->Bm, P->L, cap, s));
+  }
+  const int lhi = part == 0 ? P->L - 1 : lsplit - 1, llo = part == 0 ? lsplit : 0;
+  for (int l = lhi; l >= llo; --l) {
     const int Gb[LEVEL_BUCKETS] = {P->lvl_G[0][l], P->lvl_G[1][l], P->lvl_G[2][l]};
     if (*std::max_element(Gb, Gb + LEVEL_BUCKETS) > 1) {  // every rank bucket has its own barrier set
       CK(cudaMemsetAsync(S.lvl_bar, 0, sizeof(unsigned int) * LEVEL_BUCKETS * P->lvl_ctas_max, s));
@@ -785,6 +828,7 @@ fifa_status fact_enqueue(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev) {
     const int side_max = (int)(((n_of(P) + ((int64_t)1 << l) - 1) >> l) + 1) / 2;
     CK(launch_level(F->dev, prec, l, 1 << l, Gb, cap, S.lvl_part, S.lvl_bar, P->lvl_ctas_max, S.flags, side_max, s));
   }
+  if (part == 0) return FIFA_OK;
   CK(launch_logdet_reduce(F->dev, s));
   if (F->has32) CK(launch_demote(F->dev, F->dev32, P->n, s));
   return FIFA_OK;

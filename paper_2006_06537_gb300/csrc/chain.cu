@@ -80,11 +80,18 @@ fifa_status chain_phase_hyper_pre(fifa_ctx* ctx, fifa_chain* ch, const Scratch& 
 // Phase 3a's middle: q = |W_C^-1 f|^2 from the swept copy of f in tmp, tau2 |
 // f, rho, and the proposal rho' (written into the proposal's descriptor).
 fifa_status chain_hyper_tau2_propose(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
+  fifa_status st = chain_hyper_tau2(ctx, ch, S);
+  if (st != FIFA_OK) return st;
+  if (launch_chain_propose(ch->dev, ch->H[1]->dev, ctx->stream) != cudaSuccess) return FIFA_ERR_CUDA;
+  return FIFA_OK;
+}
+
+// q = |W_C^-1 f|^2 from the swept copy of f in tmp and tau2 | f, rho.
+fifa_status chain_hyper_tau2(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
   cudaStream_t s = ctx->stream;
   ChainDev* c = ch->dev;
   if (launch_sumsq(ch->tmp, nullptr, ch->plan->n, S.red, &c->q, s) != cudaSuccess) return FIFA_ERR_CUDA;
   if (launch_chain_tau2(c, s) != cudaSuccess) return FIFA_ERR_CUDA;
-  if (launch_chain_propose(c, ch->H[1]->dev, s) != cudaSuccess) return FIFA_ERR_CUDA;
   return FIFA_OK;
 }
 
@@ -118,23 +125,88 @@ fifa_status chain_phase_hyper(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
   return st;
 }
 
+// One iteration with the proposal's assembly and factorization beside the draw
+// (overlap_proposal).  rho' depends only on the state the previous iteration
+// left, so C~(rho') can be built while f, sigma2 and tau2 are drawn.
+//   ctx->stream: rho'; fork
+//   draw stream (highest priority): grouped ACA of C~(rho'); draw, sigma2, q,
+//     tau2
+//   branch stream (lowest priority, own scratch): dense leaves, one-CTA and
+//     one-warp ACA blocks; after the grouped ACA, the factorization's leaves
+//     and ungrouped levels
+//   ctx->stream: join; the grouped levels of C~(rho'), q' and the Metropolis
+//     step.
+// The branch runs only kernels whose CTAs never wait on each other, so the
+// draw stream's waiting launches (grouped ACA, fused sweeps and products, the
+// grouped levels of M~) keep their sizes and always become co-resident; the
+// priorities let the draw's CTAs take SMs first as the branch's CTAs finish.
+// Every kernel, size and result is that of the serial order.
+static fifa_status chain_iteration_overlap(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
+  cudaStream_t ms = ctx->stream, ds = ch->draw_stream, ps = ch->prop_stream;
+  CK(launch_chain_propose(ch->dev, ch->H[1]->dev, ms));
+  CK(cudaEventRecord(ch->ev_fork, ms));
+  CK(cudaStreamWaitEvent(ds, ch->ev_fork, 0));
+  CK(cudaStreamWaitEvent(ps, ch->ev_fork, 0));
+  // draw stream: grouped ACA, then the draw (ctx->stream points at it meanwhile)
+  ctx->stream = ds;
+  fifa_status st = hmat_assemble_grouped_enqueue(ctx, ch->H[1]);
+  cudaError_t e = st == FIFA_OK ? cudaEventRecord(ch->ev_aca, ds) : cudaSuccess;
+  if (st == FIFA_OK && e == cudaSuccess) {
+    // branch: its own stream and scratch
+    ctx->stream = ps;
+    ctx->active_scratch = ch->scratch_prop;
+    st = hmat_assemble_rest_enqueue(ctx, ch->H[1]);
+    if (st == FIFA_OK) e = cudaStreamWaitEvent(ps, ch->ev_aca, 0);
+    if (st == FIFA_OK && e == cudaSuccess) st = fact_enqueue_part(ctx, ch->F[1], ch->H[1]->dev, 0);
+    ctx->stream = ds;
+    ctx->active_scratch = ch->scratch;
+  }
+  if (st == FIFA_OK && e == cudaSuccess) st = chain_phase_draw(ctx, ch);
+  if (st == FIFA_OK && e == cudaSuccess) st = chain_phase_sigma2(ctx, ch, S);
+  if (st == FIFA_OK && e == cudaSuccess)
+    st = cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * ch->plan->n, cudaMemcpyDeviceToDevice, ds) == cudaSuccess
+             ? sweep_enqueue(ctx, ch->F[0], 0, 1, ch->tmp, 1)
+             : FIFA_ERR_CUDA;
+  if (st == FIFA_OK && e == cudaSuccess) st = chain_hyper_tau2(ctx, ch, S);
+  ctx->stream = ms;
+  // join both streams whatever happened above (a capture must end joined)
+  const cudaError_t e1 = cudaEventRecord(ch->ev_join_draw, ds);
+  const cudaError_t e2 = cudaEventRecord(ch->ev_join_prop, ps);
+  const cudaError_t e3 = cudaStreamWaitEvent(ms, ch->ev_join_draw, 0);
+  const cudaError_t e4 = cudaStreamWaitEvent(ms, ch->ev_join_prop, 0);
+  if (st != FIFA_OK) return st;
+  CK(e);
+  CK(e1);
+  CK(e2);
+  CK(e3);
+  CK(e4);
+  st = fact_enqueue_part(ctx, ch->F[1], ch->H[1]->dev, 1);
+  if (st == FIFA_OK) st = chain_phase_hyper_post(ctx, ch, S);
+  return st;
+}
+
 static fifa_status chain_iteration_enqueue(fifa_ctx* ctx, fifa_chain* ch) {
   ctx->active_scratch = ch->scratch;
   Scratch S = carve(ctx, ch->plan);
-  fifa_status st = chain_phase_draw(ctx, ch);
-  if (st == FIFA_OK) st = chain_phase_sigma2(ctx, ch, S);
-  if (st == FIFA_OK) st = chain_phase_hyper(ctx, ch, S);
+  fifa_status st;
+  if (ch->overlap) {
+    st = chain_iteration_overlap(ctx, ch, S);
+  } else {
+    st = chain_phase_draw(ctx, ch);
+    if (st == FIFA_OK) st = chain_phase_sigma2(ctx, ch, S);
+    if (st == FIFA_OK) st = chain_phase_hyper(ctx, ch, S);
+  }
   ctx->active_scratch = nullptr;
-  if (st == FIFA_ERR_CUDA) ctx->last_cuda = cudaGetLastError();
+  if (st == FIFA_ERR_CUDA && ctx->last_cuda == cudaSuccess) ctx->last_cuda = cudaGetLastError();
   return st;
 }
 
 size_t chain_bytes(const Plan* P, const fifa_opts& o) {
   auto r = [](size_t b) { return b == 0 ? (size_t)256 : (b + 255) & ~(size_t)255; };
   const int cap = o.rank_cap;
-  return 5 * r(sizeof(double) * P->n) + r(sizeof(double) * CHAIN_TRACE_CAP * CHAIN_TRACE_FIELDS) + r(P->scratch_bytes) +
-         r(sizeof(ChainDev)) + 2 * hmat_bytes(P, cap) + 2 * fact_bytes(P, cap, 0) + r(sizeof(HmatDesc)) +
-         fact_bytes(P, cap, o.prec == FIFA_MIXED ? 1 : 0);
+  return 5 * r(sizeof(double) * P->n) + r(sizeof(double) * CHAIN_TRACE_CAP * CHAIN_TRACE_FIELDS) +
+         (o.overlap_proposal ? 2 : 1) * r(P->scratch_bytes) + r(sizeof(ChainDev)) + 2 * hmat_bytes(P, cap) +
+         2 * fact_bytes(P, cap, 0) + r(sizeof(HmatDesc)) + fact_bytes(P, cap, o.prec == FIFA_MIXED ? 1 : 0);
 }
 
 static double kconst(int kind, double rho) { return kind == 0 ? 0.5 / (rho * rho) : sqrt(5.0) / rho; }
@@ -176,6 +248,24 @@ extern "C" fifa_status fifa_chain_create(fifa_ctx* ctx, const double* x_dev, con
   ch->dev = (ChainDev*)ctx->arena.alloc(sizeof(ChainDev));
   if (!ch->x || !ch->y || !ch->f || !ch->mean || !ch->tmp || !ch->trace || !ch->scratch || !ch->dev)
     return fail(FIFA_ERR_OOM);
+  if (ctx->opts.overlap_proposal) {
+    ch->scratch_prop = ctx->arena.alloc(P->scratch_bytes);
+    if (!ch->scratch_prop) return fail(FIFA_ERR_OOM);
+    int dev = -1, least = 0, greatest = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev != ctx->device) CK(cudaSetDevice(ctx->device));
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ch->draw_stream, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ch->prop_stream, cudaStreamNonBlocking, least);
+    for (cudaEvent_t* ev : {&ch->ev_fork, &ch->ev_aca, &ch->ev_join_draw, &ch->ev_join_prop})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (dev != ctx->device) cudaSetDevice(dev);
+    if (e != cudaSuccess) {
+      ctx->last_cuda = e;
+      return fail(FIFA_ERR_CUDA);
+    }
+    ch->overlap = true;
+  }
   cudaStream_t s = ctx->stream;
   CK(cudaMemcpyAsync(ch->x, x_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(ch->y, y_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -270,7 +360,9 @@ static fifa_status chain_build_graph(fifa_ctx* ctx, fifa_chain* ch) {
     ch->graph_failed = true;
     return FIFA_OK;
   }
-  if (cudaGraphInstantiate(&ch->exec, g, 0) != cudaSuccess) {
+  // per-node priorities: the overlapped iteration's draw stream outranks its branch
+  if (cudaGraphInstantiateWithFlags(&ch->exec, g, ch->overlap ? cudaGraphInstantiateFlagUseNodePriority : 0) !=
+      cudaSuccess) {
     cudaGetLastError();
     cudaGraphDestroy(g);
     ch->exec = nullptr;
@@ -402,6 +494,14 @@ extern "C" void fifa_destroy_chain(fifa_ctx* ctx, fifa_chain* ch) {
   ctx->arena.release(ch->tmp);
   ctx->arena.release(ch->trace);
   ctx->arena.release(ch->scratch);
+  for (cudaStream_t t : {ch->draw_stream, ch->prop_stream})
+    if (t) {
+      cudaStreamSynchronize(t);
+      cudaStreamDestroy(t);
+    }
+  for (cudaEvent_t ev : {ch->ev_fork, ch->ev_aca, ch->ev_join_draw, ch->ev_join_prop})
+    if (ev) cudaEventDestroy(ev);
+  if (ch->scratch_prop) ctx->arena.release(ch->scratch_prop);
   ctx->arena.release(ch->dev);
   delete ch;
 }

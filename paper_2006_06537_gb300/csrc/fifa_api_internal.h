@@ -105,6 +105,10 @@ Scratch carve(fifa_ctx* ctx, Plan* P);
 fifa_status ensure_scratch(fifa_ctx* ctx, Plan* P);
 fifa_status hmat_alloc(fifa_ctx* ctx, Plan* P, int kind, fifa_hmat** out);
 fifa_status hmat_assemble_enqueue(fifa_ctx* ctx, fifa_hmat* H);
+// The assembly in two parts: descriptor reset + grouped ACA (CTAs that wait on
+// each other), then leaves + one-CTA / one-warp ACA (independent CTAs).
+fifa_status hmat_assemble_grouped_enqueue(fifa_ctx* ctx, fifa_hmat* H);
+fifa_status hmat_assemble_rest_enqueue(fifa_ctx* ctx, fifa_hmat* H);
 // Assemble nprob H-matrices of plan P (descriptor array H0) in shared launches;
 // problem q's scratch at scratch0 + q * sstride bytes.
 fifa_status hmat_assemble_batched(fifa_ctx* ctx, Plan* P, HmatDesc* H0, int nprob, void* scratch0, size_t sstride);
@@ -122,6 +126,11 @@ fifa_status fact_alloc(fifa_ctx* ctx, Plan* P, int with32, fifa_fact** out);
 // Point the factor's skip flag at a device int (nullable) and upload its descriptor.
 fifa_status fact_set_skip(fifa_ctx* ctx, fifa_fact* F, const int* skip_dev);
 fifa_status fact_enqueue(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev);
+// The factorization in two parts: 0 = reset, leaves and the levels without CTA
+// groups (independent CTAs only); 1 = the grouped top levels, log-determinant
+// and FP32 copy.  fact_ungrouped_from: the first level of part 0's range.
+fifa_status fact_enqueue_part(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev, int part);
+int fact_ungrouped_from(const Plan* P);
 // F32_0 (nullable): the problems' FP32 copies, refreshed after the factorization.
 fifa_status fact_enqueue_batched(fifa_ctx* ctx, Plan* P, FactDesc* F0, const HmatDesc* H0, int nprob,
                                  void* scratch0, size_t sstride, const FactDesc* F32_0 = nullptr);

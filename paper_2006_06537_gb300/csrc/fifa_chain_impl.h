@@ -18,6 +18,12 @@ struct fifa_chain {
   fifa_hmat* Mv = nullptr;  // view descriptor refreshed every iteration
   double *x = nullptr, *y = nullptr, *f = nullptr, *mean = nullptr, *tmp = nullptr, *trace = nullptr;
   void* scratch = nullptr;
+  // overlap_proposal: the draw's stream (highest priority), the proposal
+  // branch's stream (lowest) and scratch, fork / hand-over / join events
+  bool overlap = false;
+  void* scratch_prop = nullptr;
+  cudaStream_t draw_stream = nullptr, prop_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_aca = nullptr, ev_join_draw = nullptr, ev_join_prop = nullptr;
   ChainDev* dev = nullptr;
   ChainDev init{};
   uint64_t iter_host = 0;
@@ -44,6 +50,7 @@ fifa_status chain_phase_hyper_post(fifa_ctx* ctx, fifa_chain* ch, const Scratch&
 // The parts of phases 3a / 3c after their sweep of the copy of f in tmp (the
 // additive model runs the blocks' sweeps in one batched launch).
 fifa_status chain_hyper_tau2_propose(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
+fifa_status chain_hyper_tau2(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);  // without the proposal
 fifa_status chain_hyper_mh(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S);
 // Phase 1b without its prior part (run for several blocks at once by the additive model).
 fifa_status chain_phase_sample_data(fifa_ctx* ctx, fifa_chain* ch);

@@ -33,7 +33,7 @@ class fifa_hyper(C.Structure):
 class fifa_opts(C.Structure):
     _fields_ = [("leaf_size", C.c_int), ("aca_tol", C.c_double), ("rank_cap", C.c_int), ("prec", C.c_int),
                 ("refine_tol", C.c_double), ("refine_max", C.c_int), ("independent_ctas", C.c_int),
-                ("wait_polls", C.c_int), ("coresident_share", C.c_int)]
+                ("wait_polls", C.c_int), ("coresident_share", C.c_int), ("overlap_proposal", C.c_int)]
 
 
 class fifa_plan_info(C.Structure):
@@ -532,7 +532,8 @@ def fifa_probe_fp64_fma(ctx, iters: int = 200000):
 # ---------------------------------------------------------------------------
 class Context:
     def __init__(self, leaf_size=64, aca_tol=1e-12, rank_cap=32, prec=FIFA_FP64, refine_tol=1e-12, refine_max=3,
-                 arena_bytes=1 << 30, device="cuda", stream=None, independent_ctas=0, wait_polls=0):
+                 arena_bytes=1 << 30, device="cuda", stream=None, independent_ctas=0, wait_polls=0,
+                 coresident_share=0, overlap_proposal=0):
         import torch
 
         self.torch = torch
@@ -540,7 +541,8 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.device)
         self.opts = fifa_opts(int(leaf_size), float(aca_tol), int(rank_cap), int(prec), float(refine_tol),
-                              int(refine_max), int(independent_ctas), int(wait_polls))
+                              int(refine_max), int(independent_ctas), int(wait_polls), int(coresident_share),
+                              int(overlap_proposal))
         self.h = fifa_create(self.opts, self.stream.cuda_stream, self.arena.data_ptr(), int(arena_bytes))
 
     def close(self):
