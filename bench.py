@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests of the serving stream to run (0 = skip the serving leg)")
     ap.add_argument("--serve-slots", type=int, default=16)
-    ap.add_argument("--serve-wide-min", type=int, default=1 << 14,
+    ap.add_argument("--serve-wide-min", type=int, default=1 << 13,
                     help="requests with n >= this run on the server's wide workers (CTA groups, fused sweeps)")
     ap.add_argument("--serve-wide-workers", type=int, default=4,
                     help="wide workers, each sizing its grouped launches to 1 / this of the GPU")
@@ -441,7 +441,8 @@ def gpu_arm(args):
     serving = additive = None
     if rank == 0 and args.serve_requests > 0:
         serving = serving_leg(fifa, args.serve_requests, args.serve_slots, fifa.FIFA_MIXED, 32,
-                              wide_min_n=args.serve_wide_min, wide_workers=args.serve_wide_workers)
+                              wide_min_n=args.serve_wide_min, wide_workers=args.serve_wide_workers,
+                              overlap=args.overlap)
     if rank == 0 and args.additive_sweeps > 0:
         additive = additive_leg(fifa, torch, args.additive_sweeps, 32)
 
@@ -622,7 +623,7 @@ def kl_terms(x, y, Ct, tau2, sigma2, rho, nugget):
 
 
 def serving_leg(fifa, count, slots, prec, leaf, iters=100, ndraws=20, rate=200.0, budget=120 << 30,
-                wide_min_n=1 << 14, wide_workers=4):
+                wide_min_n=1 << 14, wide_workers=4, overlap=0):
     """The serving workload: the first `count` requests of a Poisson stream at
     `rate` req/s, n log-uniform in [2^10, 2^18], SE or Matern-5/2 per request,
     each `iters` Gibbs iterations returning the posterior mean and `ndraws`
@@ -632,7 +633,7 @@ def serving_leg(fifa, count, slots, prec, leaf, iters=100, ndraws=20, rate=200.0
 
     reqs = serving_requests(count, rate)
     data = [request_data(r) for r in reqs]
-    opts = fifa.fifa_opts(leaf, EPS, CAP, prec, 1e-12, 8, 1)
+    opts = fifa.fifa_opts(leaf, EPS, CAP, prec, 1e-12, 8, 1, 0, 0, overlap)
     srv = fifa.fifa_server_create(opts, budget, slots, wide_min_n, wide_workers)
     ids = [None] * count
     res = [None] * count
@@ -684,7 +685,7 @@ def serving_leg(fifa, count, slots, prec, leaf, iters=100, ndraws=20, rate=200.0
         "workload": f"first {count} requests of a Poisson stream at {rate:g} req/s, n log-uniform in [2^10, 2^18], "
                     f"SE or Matern-5/2, {iters} iterations + posterior mean + {ndraws} draws each",
         "requests": count, "completed": len(ok), "offered_req_per_s": rate, "slots": slots,
-        "wide_min_n": wide_min_n, "wide_workers": wide_workers,
+        "wide_min_n": wide_min_n, "wide_workers": wide_workers, "overlap_proposal": overlap,
         "hbm_budget_gb": budget / 2**30, "precision": "fp64" if prec == fifa.FIFA_FP64 else "mixed",
         "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
         "mean_latency_s": float(lat.mean()), "iters_per_s": len(ok) * iters / span,

@@ -31,8 +31,8 @@ from paper_2006_06537_gb300 import fifa  # noqa: E402
 B, EPS, CAP = 64, 1e-12, 32
 
 
-def _opts(prec=fifa.FIFA_FP64, leaf=B, eps=EPS):
-    return fifa.fifa_opts(leaf, eps, CAP, prec, 1e-12, 3, 1)
+def _opts(prec=fifa.FIFA_FP64, leaf=B, eps=EPS, overlap=0):
+    return fifa.fifa_opts(leaf, eps, CAP, prec, 1e-12, 3, 1, 0, 0, overlap)
 
 
 def _prior(mu=math.log(0.1)):
@@ -130,13 +130,15 @@ def _mix(count=10, seed=11):
 WIDE = 1 << 14  # requests with n >= WIDE run on the wide worker (CTA groups, fused sweeps)
 
 
-@pytest.mark.parametrize("wide_workers", [1, 2])
-def test_server_result_same_alone_and_in_mix(wide_workers):
+@pytest.mark.parametrize("wide_workers,overlap", [(1, 0), (2, 0), (2, 1)])
+def test_server_result_same_alone_and_in_mix(wide_workers, overlap):
     # with two wide workers, two requests' grouped launches (each sized to half
-    # the GPU) run side by side; a request's result must not depend on it
+    # the GPU) run side by side; a request's result must not depend on it.
+    # overlap: every request's proposal runs on a branch stream beside its draw
+    # (fifa_opts.overlap_proposal), which must not change a bit either
     reqs = _mix()
     assert sum(len(r[0]) >= WIDE for r in reqs) >= 2 and any(len(r[0]) < WIDE for r in reqs)
-    srv = fifa.fifa_server_create(_opts(eps=1e-10), 8 << 30, 6, WIDE, wide_workers)
+    srv = fifa.fifa_server_create(_opts(eps=1e-10, overlap=overlap), 8 << 30, 6, WIDE, wide_workers)
     mixed = _run(srv, reqs)
     stats = fifa.fifa_server_stats(srv)
     fifa.fifa_server_destroy(srv)
@@ -144,7 +146,7 @@ def test_server_result_same_alone_and_in_mix(wide_workers):
     assert all(m[2].status == fifa.FIFA_OK for m in mixed)
     assert stats.peak_in_flight > 1  # requests really overlapped
     for k in (0, len(reqs) // 2, int(np.argmax([len(r[0]) for r in reqs]))):
-        srv = fifa.fifa_server_create(_opts(eps=1e-10), 8 << 30, 1 + wide_workers, WIDE, wide_workers)
+        srv = fifa.fifa_server_create(_opts(eps=1e-10, overlap=0), 8 << 30, 1 + wide_workers, WIDE, wide_workers)
         (mean, draws, res), = _run(srv, [reqs[k]])
         fifa.fifa_server_destroy(srv)
         assert res.status == fifa.FIFA_OK and mixed[k][2].status == fifa.FIFA_OK
