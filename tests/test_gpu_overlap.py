@@ -110,3 +110,23 @@ def test_overlap_chain_bytes_is_exact(prec):
                 fifa.fifa_chain_create(ctx.h, xd, yd, n, hy, pr, 0, 0)
             assert e.value.code == fifa.FIFA_ERR_OOM
         ctx.close()
+
+
+def test_overlap_matches_serial_at_full_size():
+    """The benchmark's configuration: clustered SE n = 2^20, leaf 32, mixed precision."""
+    n = 1 << 20
+    x, y = clustered(n, 2, noise=0.05)
+    outs = []
+    for overlap in (0, 1):
+        ctx, ch = _chain(x, y, 32, fifa.FIFA_MIXED, overlap, 0.01, 1e-6, arena=40 << 30)
+        tr = np.zeros((3, fifa.FIFA_TRACE_FIELDS))
+        fifa.fifa_gibbs_step(ctx.h, ch, 3, tr)
+        f = torch.empty(n, dtype=torch.float64, device="cuda")
+        fifa.fifa_chain_get(ctx.h, ch, f, None)
+        outs.append((tr, f.cpu().numpy()))
+        fifa.fifa_destroy_chain(ctx.h, ch)
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
+    assert np.array_equal(outs[0][0].view(np.uint64), outs[1][0].view(np.uint64))
+    assert np.array_equal(outs[0][1].view(np.uint64), outs[1][1].view(np.uint64))
