@@ -1056,6 +1056,7 @@ fifa_status solve_enqueue(fifa_ctx* ctx, const fifa_fact* F, const double* b, do
   int* ints = (int*)(S.pcg + PCG_OFF_INTS);
   int* act = ints;        // act[2]
   int* iters = ints + 2;  // iterations taken
+  int* act_sw = ints + 3; // this step's preconditioner needed
   double* r = work;
   double* z = work + nn;
   double* p = work + 2 * nn;
@@ -1073,8 +1074,8 @@ fifa_status solve_enqueue(fifa_ctx* ctx, const fifa_fact* F, const double* b, do
     const int cur = it & 1, nxt = cur ^ 1;
     if ((e = matvec_enqueue(ctx, op, p, q, nrhs, act + cur)) != FIFA_OK) return e;
     CK(launch_pcg_pq(p, q, n, nrhs, part, act + cur, s));
-    CK(launch_pcg_update(x, r, z, p, q, n, nrhs, st + cur * slot, part, act + cur, s));
-    if ((e = sweep_enqueue_desc(ctx, P, F->dev32, 1, 4, z, nrhs, act + cur)) != FIFA_OK) return e;
+    CK(launch_pcg_update(x, r, z, p, q, n, nrhs, st + cur * slot, part, act + cur, act_sw, tol2, s));
+    if ((e = sweep_enqueue_desc(ctx, P, F->dev32, 1, 4, z, nrhs, act_sw)) != FIFA_OK) return e;
     CK(launch_pcg_direction(r, p, z, n, nrhs, st + cur * slot, st + nxt * slot, act + cur, act + nxt, iters, part,
                             tol2, s));
   }

@@ -10,7 +10,7 @@
 #define PCG_SLOT 8      // doubles of state per right-hand side and parity slot
 #define PCG_RHS_MAX 2
 // Scratch of one solve (doubles): partials [0, 6 PCG_NB), state [768, 800),
-// then ints: act[2], iters, at double offset 800.
+// then ints: act[2], iters, act_sweep, at double offset 800.
 #define PCG_SCRATCH_DOUBLES 1024
 #define PCG_OFF_STATE 768
 #define PCG_OFF_INTS 800
@@ -25,8 +25,11 @@ cudaError_t launch_pcg_start(const double* r, const double* z, double* p, int64_
                              double* stt, int* act, int* iters, double tol2, cudaStream_t st);
 cudaError_t launch_pcg_pq(const double* p, const double* q, int64_t n, int nrhs, double* part, const int* active,
                           cudaStream_t st);
+// x, r (and z = r) updated, then act_sweep = whether any system still needs the
+// preconditioner this step (its updated residual above the tolerance).
 cudaError_t launch_pcg_update(double* x, double* r, double* z, const double* p, const double* q, int64_t n, int nrhs,
-                              const double* stt, double* part, const int* active, cudaStream_t st);
+                              const double* stt, double* part, const int* active, int* act_sweep, double tol2,
+                              cudaStream_t st);
 cudaError_t launch_pcg_direction(const double* r, double* p, const double* z, int64_t n, int nrhs,
                                  const double* st_cur, double* st_nxt, const int* act_cur, int* act_nxt, int* iters,
                                  double* part, double tol2, cudaStream_t st);

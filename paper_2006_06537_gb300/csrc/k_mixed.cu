@@ -186,6 +186,24 @@ __global__ void __launch_bounds__(256) k_pcg_xr(double* __restrict__ x, double* 
   if (threadIdx.x == 0) __stcg(part + PCG_PART(0, j) + blockIdx.x, rr);
 }
 
+// Whether the preconditioner must run this step: some system still iterating
+// whose updated residual is above the tolerance.  A system that has just met it
+// is marked done by k_pcg_dir from the same r^T r, so its z is never used and
+// the sweep is skipped when no other system needs it (one block).
+__global__ void k_pcg_gate(const double* __restrict__ st, const double* __restrict__ part,
+                           const int* __restrict__ active, int* __restrict__ act_sweep, int nrhs, double tol2) {
+  if (threadIdx.x != 0) return;
+  int any = 0;
+  if (*active != 0)
+    for (int j = 0; j < nrhs; ++j) {
+      const double* s = st + j * PCG_SLOT;
+      if (s[2] != 0.0) continue;
+      const double rr = pcg_sum(part, 0, j);
+      if (pcg_alpha(s, part, j) != 0.0 && rr > tol2 * s[1]) any = 1;
+    }
+  *act_sweep = any;
+}
+
 // Partials of r^T z (after z = P^-1 r).
 __global__ void __launch_bounds__(256) k_pcg_rz(const double* __restrict__ r, const double* __restrict__ z, int64_t n,
                                                double* __restrict__ part, const int* __restrict__ active) {
@@ -303,8 +321,10 @@ cudaError_t launch_pcg_pq(const double* p, const double* q, int64_t n, int nrhs,
   return cudaGetLastError();
 }
 cudaError_t launch_pcg_update(double* x, double* r, double* z, const double* p, const double* q, int64_t n, int nrhs,
-                              const double* stt, double* part, const int* active, cudaStream_t st) {
+                              const double* stt, double* part, const int* active, int* act_sweep, double tol2,
+                              cudaStream_t st) {
   k_pcg_xr<<<dim3(PCG_NB, nrhs), 256, 0, st>>>(x, r, z, p, q, n, stt, part, active);
+  k_pcg_gate<<<1, 32, 0, st>>>(stt, part, active, act_sweep, nrhs, tol2);
   return cudaGetLastError();
 }
 cudaError_t launch_pcg_direction(const double* r, double* p, const double* z, int64_t n, int nrhs,
