@@ -104,6 +104,19 @@ def test_level_groups_are_co_resident(fifa, n, B):
                 assert nodes * g <= BUDGET["lvl"][bkt] and span // g >= per and 2 * nodes <= BUDGET["lvl"][bkt]
 
 
+@pytest.mark.parametrize("n,B", CASES)
+def test_level_groups_cover_a_prefix_of_top_levels(fifa, n, B):
+    # the overlapped chain iteration splits a factorization at the deepest
+    # grouped level: everything below runs with independent CTAs, so in every
+    # rank bucket the grouped levels must be exactly levels 0 .. k-1
+    d = fifa.fifa_plan_describe(_opts(fifa, B), n, BUDGET["aca"], BUDGET["lvl"])
+    G = d["groups"]
+    for bkt in range(3):
+        grouped = [int(G[bkt, lvl]) > 1 for lvl in range(d["info"].levels)]
+        k = sum(grouped)
+        assert grouped == [True] * k + [False] * (len(grouped) - k), (bkt, grouped)
+
+
 def test_independent_ctas_have_no_groups(fifa):
     d = fifa.fifa_plan_describe(_opts(fifa, 32, indep=1), 1 << 20, BUDGET["aca"], BUDGET["lvl"])
     assert d["info"].aca_grouped_ctas == 0
