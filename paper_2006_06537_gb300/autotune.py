@@ -46,7 +46,7 @@ def store(key: str, entry: dict):
         json.dump(data, fh, indent=1, sort_keys=True)
 
 
-def time_leaf(x, y, leaf, rho0, eps, cap, nugget, iters=5, warmup=3, prec=0, refine_tol=1e-10):
+def time_leaf(x, y, leaf, rho0, eps, cap, nugget, iters=5, warmup=3, prec=0, refine_tol=1e-10, overlap=1):
     import torch
 
     from . import fifa
@@ -55,7 +55,7 @@ def time_leaf(x, y, leaf, rho0, eps, cap, nugget, iters=5, warmup=3, prec=0, ref
     vy = float(np.var(y))
     with torch.cuda.stream(stream):
         ctx = fifa.Context(leaf_size=leaf, aca_tol=eps, rank_cap=cap, prec=prec, refine_max=8, refine_tol=refine_tol,
-                           arena_bytes=40 << 30, stream=stream)
+                           arena_bytes=40 << 30, stream=stream, overlap_proposal=overlap)
         xd = torch.tensor(x, device="cuda")
         yd = torch.tensor(y, device="cuda")
         pr = fifa.fifa_prior(1.0, 1.0, 1.0, 1.0, math.log(rho0), 1.0, 0.2)
@@ -74,17 +74,17 @@ def time_leaf(x, y, leaf, rho0, eps, cap, nugget, iters=5, warmup=3, prec=0, ref
     return ms
 
 
-def tune_clustered(n: int, leaves=(32, 64, 128), rho0=0.01, eps=1e-10, cap=32, nugget=1e-6, noise=0.05):
+def tune_clustered(n: int, leaves=(32, 64, 128), rho0=0.01, eps=1e-10, cap=32, nugget=1e-6, noise=0.05, overlap=1):
     from .build import build
     from .inputs import clustered
 
     build()
     x, y = clustered(n, 2, noise=noise)
-    mixed = {str(b): time_leaf(x, y, b, rho0, eps, cap, nugget, prec=1) for b in leaves}
-    fp64 = {str(b): time_leaf(x, y, b, rho0, eps, cap, nugget, prec=0) for b in leaves}
+    mixed = {str(b): time_leaf(x, y, b, rho0, eps, cap, nugget, prec=1, overlap=overlap) for b in leaves}
+    fp64 = {str(b): time_leaf(x, y, b, rho0, eps, cap, nugget, prec=0, overlap=overlap) for b in leaves}
     best = int(min(mixed, key=mixed.get))
     entry = {"leaf": best, "ms_per_iter": mixed, "ms_per_iter_fp64": fp64, "rho0": rho0, "eps": eps, "cap": cap,
-             "nugget": nugget, "refine_tol": 1e-10, "iters_timed": 5, "warmup": 3}
+             "nugget": nugget, "refine_tol": 1e-10, "iters_timed": 5, "warmup": 3, "overlap_proposal": overlap}
     store(workload_key("clustered_se", n), entry)
     return entry
 
@@ -93,5 +93,7 @@ if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--leaves", type=int, nargs="+", default=[32, 64, 128])
+    ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
+                    help="time chains with the proposal overlapped on a second stream (the benchmark's default)")
     a = ap.parse_args()
-    print(json.dumps(tune_clustered(a.n, tuple(a.leaves))))
+    print(json.dumps(tune_clustered(a.n, tuple(a.leaves), overlap=a.overlap)))
