@@ -95,7 +95,9 @@ typedef struct {
                            grouped top-level ACA runs before it and the grouped top-level
                            factorization after it, so launch sizes and every result are the same
                            as with 0.  Costs a second scratch area per chain (fifa_chain_bytes
-                           counts it).  0 or 1 */
+                           counts it).  Applies to chains stepped whole (fifa_gibbs_step,
+                           serving); the additive and tensor-product models step their blocks
+                           phase by phase and do not use it.  0 or 1 */
 } fifa_opts;
 
 /* Priors: inverse-gamma IG(shape, scale) on tau2 and sigma2 (the conjugate

@@ -258,8 +258,12 @@ extern "C" fifa_status fifa_additive_create(fifa_ctx* ctx, const double* X_dev, 
     CK(cudaMemcpyAsync(A->perm + (size_t)k * n, idx.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(A->res, xs.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
-    // the block's data buffer is overwritten by the partial residual every sweep
+    // the block's data buffer is overwritten by the partial residual every sweep;
+    // blocks are stepped phase by phase, so they take no proposal-overlap resources
+    const int ov = ctx->opts.overlap_proposal;
+    ctx->opts.overlap_proposal = 0;
     fifa_status st = fifa_chain_create(ctx, A->res, A->y, n, init, prior, seed, (uint64_t)k, &A->blk[k]);
+    ctx->opts.overlap_proposal = ov;
     if (st != FIFA_OK) return fail(st);
   }
   // concurrent block branches only where no kernel's CTAs wait on each other

@@ -292,7 +292,11 @@ extern "C" fifa_status fifa_tensor_create(fifa_ctx* ctx, const double* X_dev, co
     CK(cudaMemcpyAsync(T->perm + (size_t)h * n, idx.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(T->dd, xs.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));  // staging
     CK(cudaStreamSynchronize(s));
+    // blocks are stepped phase by phase: no proposal-overlap resources
+    const int ov = ctx->opts.overlap_proposal;
+    ctx->opts.overlap_proposal = 0;
     fifa_status st = fifa_chain_create(ctx, T->dd, T->y, n, &bi, prior, seed, (uint64_t)h, &T->blk[h]);
+    ctx->opts.overlap_proposal = ov;
     if (st != FIFA_OK) return fail(st);
   }
   ChainDev* ptrs[FIFA_ADDITIVE_MAX_D] = {};
