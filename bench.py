@@ -78,7 +78,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests of the serving stream to run (0 = skip the serving leg)")
-    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-slots", type=int, default=20)
     ap.add_argument("--serve-wide-min", type=int, default=1 << 13,
                     help="requests with n >= this run on the server's wide workers (CTA groups, fused sweeps)")
     ap.add_argument("--serve-wide-workers", type=int, default=4,
