@@ -985,6 +985,18 @@ fifa_status sweep_enqueue_desc(fifa_ctx* ctx, Plan* P, const FactDesc* Fdev, int
   return FIFA_OK;
 }
 
+// W^-1 v of an FP64 factor in two parts around its grouped top levels: part 0
+// (leaves and the levels the fused sweep keeps inside a CTA) needs only the
+// factor's levels from fact_ungrouped_from down, part 1 the rest.  Possible
+// when the fused sweep's local levels lie in that range.
+bool sweep_inverse_split_ok(const Plan* P) { return P->fs_ls >= 0 && P->fs_ls >= fact_ungrouped_from(P); }
+
+fifa_status sweep_inverse_part_enqueue(fifa_ctx* ctx, const fifa_fact* F, double* v, int part) {
+  Plan* P = F->plan;
+  if (!sweep_inverse_split_ok(P) || F->host.prec != 0) return FIFA_ERR_INVALID_ARG;
+  return sweep_enqueue_desc(ctx, P, F->dev, 0, part == 0 ? 5 : 6, v, 1);
+}
+
 fifa_status sweep_enqueue(fifa_ctx* ctx, const fifa_fact* F, int trans, int inverse, double* v, int nrhs) {
   const int mode = trans ? (inverse ? 3 : 2) : (inverse ? 1 : 0);
   return sweep_enqueue_desc(ctx, F->plan, F->dev, F->host.prec, mode, v, nrhs);

@@ -130,17 +130,19 @@ fifa_status chain_phase_hyper(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
 // left, so C~(rho') can be built while f, sigma2 and tau2 are drawn.
 //   ctx->stream: rho'; fork
 //   draw stream (highest priority): grouped ACA of C~(rho'); draw, sigma2, q,
-//     tau2
+//     tau2; then, once the branch is done, the leaves and CTA-local levels of
+//     W'^-1 f (independent CTAs, on the branch's idle scratch)
 //   branch stream (lowest priority, own scratch): dense leaves, one-CTA and
 //     one-warp ACA blocks; after the grouped ACA, the factorization's leaves
 //     and ungrouped levels
-//   ctx->stream: join; the grouped levels of C~(rho'), q' and the Metropolis
-//     step.
-// The branch runs only kernels whose CTAs never wait on each other, so the
-// draw stream's waiting launches (grouped ACA, fused sweeps and products, the
-// grouped levels of M~) keep their sizes and always become co-resident; the
-// priorities let the draw's CTAs take SMs first as the branch's CTAs finish.
-// Every kernel, size and result is that of the serial order.
+//   ctx->stream: after the branch and the draw's last waiting launch, the
+//     grouped levels of C~(rho') (beside the first part of W'^-1 f); join; the
+//     rest of W'^-1 f, q' and the Metropolis step.
+// Whenever a launch whose CTAs wait on each other runs, every other stream runs
+// only kernels whose CTAs never wait, so the waiting launches keep their sizes
+// and always become co-resident; the priorities let the draw's CTAs take SMs
+// first as the branch's CTAs finish.  Every kernel, size and result is that of
+// the serial order (W'^-1 f in two launches has the one-launch arithmetic).
 static fifa_status chain_iteration_overlap(fifa_ctx* ctx, fifa_chain* ch, const Scratch& S) {
   cudaStream_t ms = ctx->stream, ds = ch->draw_stream, ps = ch->prop_stream;
   CK(launch_chain_propose(ch->dev, ch->H[1]->dev, ms));
@@ -161,28 +163,51 @@ static fifa_status chain_iteration_overlap(fifa_ctx* ctx, fifa_chain* ch, const 
     ctx->stream = ds;
     ctx->active_scratch = ch->scratch;
   }
-  if (st == FIFA_OK && e == cudaSuccess) st = chain_phase_draw(ctx, ch);
-  if (st == FIFA_OK && e == cudaSuccess) st = chain_phase_sigma2(ctx, ch, S);
-  if (st == FIFA_OK && e == cudaSuccess)
+  const cudaError_t e_branch = cudaEventRecord(ch->ev_join_prop, ps);  // the branch ends here
+  bool go = st == FIFA_OK && e == cudaSuccess && e_branch == cudaSuccess;
+  if (go) st = chain_phase_draw(ctx, ch);
+  if (go && st == FIFA_OK) st = chain_phase_sigma2(ctx, ch, S);
+  if (go && st == FIFA_OK)
     st = cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * ch->plan->n, cudaMemcpyDeviceToDevice, ds) == cudaSuccess
              ? sweep_enqueue(ctx, ch->F[0], 0, 1, ch->tmp, 1)
              : FIFA_ERR_CUDA;
-  if (st == FIFA_OK && e == cudaSuccess) st = chain_hyper_tau2(ctx, ch, S);
+  if (go && st == FIFA_OK) st = chain_hyper_tau2(ctx, ch, S);
+  go = go && st == FIFA_OK;
+  // the draw's last waiting launch is behind this event
+  cudaError_t e_done = cudaEventRecord(ch->ev_draw_done, ds);
+  const bool split = sweep_inverse_split_ok(ch->plan);
+  if (go && split && e_done == cudaSuccess) {
+    // first part of q' = |W'^-1 f|^2 beside the grouped levels: it reads only
+    // the factor's levels the branch has finished
+    e_done = cudaStreamWaitEvent(ds, ch->ev_join_prop, 0);
+    if (e_done == cudaSuccess)
+      e_done = cudaMemcpyAsync(ch->tmp, ch->f, sizeof(double) * ch->plan->n, cudaMemcpyDeviceToDevice, ds);
+    if (e_done == cudaSuccess) {
+      ctx->active_scratch = ch->scratch_prop;
+      st = sweep_inverse_part_enqueue(ctx, ch->F[1], ch->tmp, 0);
+      ctx->active_scratch = ch->scratch;
+    }
+  }
+  const cudaError_t e_draw = cudaEventRecord(ch->ev_join_draw, ds);
   ctx->stream = ms;
-  // join both streams whatever happened above (a capture must end joined)
-  const cudaError_t e1 = cudaEventRecord(ch->ev_join_draw, ds);
-  const cudaError_t e2 = cudaEventRecord(ch->ev_join_prop, ps);
-  const cudaError_t e3 = cudaStreamWaitEvent(ms, ch->ev_join_draw, 0);
+  // the grouped levels wait for the branch and for the draw's last waiting launch
+  const cudaError_t e3 = cudaStreamWaitEvent(ms, ch->ev_draw_done, 0);
   const cudaError_t e4 = cudaStreamWaitEvent(ms, ch->ev_join_prop, 0);
+  if (go && st == FIFA_OK && e_done == cudaSuccess && e3 == cudaSuccess && e4 == cudaSuccess)
+    st = fact_enqueue_part(ctx, ch->F[1], ch->H[1]->dev, 1);
+  // join the draw stream whatever happened above (a capture must end joined)
+  const cudaError_t e5 = cudaStreamWaitEvent(ms, ch->ev_join_draw, 0);
   if (st != FIFA_OK) return st;
   CK(e);
-  CK(e1);
-  CK(e2);
+  CK(e_branch);
+  CK(e_done);
+  CK(e_draw);
   CK(e3);
   CK(e4);
-  st = fact_enqueue_part(ctx, ch->F[1], ch->H[1]->dev, 1);
-  if (st == FIFA_OK) st = chain_phase_hyper_post(ctx, ch, S);
-  return st;
+  CK(e5);
+  if (!split) return chain_phase_hyper_post(ctx, ch, S);
+  st = sweep_inverse_part_enqueue(ctx, ch->F[1], ch->tmp, 1);
+  return st == FIFA_OK ? chain_hyper_mh(ctx, ch, S) : st;
 }
 
 static fifa_status chain_iteration_enqueue(fifa_ctx* ctx, fifa_chain* ch) {
@@ -257,7 +282,7 @@ extern "C" fifa_status fifa_chain_create(fifa_ctx* ctx, const double* x_dev, con
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ch->draw_stream, cudaStreamNonBlocking, greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ch->prop_stream, cudaStreamNonBlocking, least);
-    for (cudaEvent_t* ev : {&ch->ev_fork, &ch->ev_aca, &ch->ev_join_draw, &ch->ev_join_prop})
+    for (cudaEvent_t* ev : {&ch->ev_fork, &ch->ev_aca, &ch->ev_draw_done, &ch->ev_join_draw, &ch->ev_join_prop})
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (dev != ctx->device) cudaSetDevice(dev);
     if (e != cudaSuccess) {
@@ -499,7 +524,7 @@ extern "C" void fifa_destroy_chain(fifa_ctx* ctx, fifa_chain* ch) {
       cudaStreamSynchronize(t);
       cudaStreamDestroy(t);
     }
-  for (cudaEvent_t ev : {ch->ev_fork, ch->ev_aca, ch->ev_join_draw, ch->ev_join_prop})
+  for (cudaEvent_t ev : {ch->ev_fork, ch->ev_aca, ch->ev_draw_done, ch->ev_join_draw, ch->ev_join_prop})
     if (ev) cudaEventDestroy(ev);
   if (ch->scratch_prop) ctx->arena.release(ch->scratch_prop);
   ctx->arena.release(ch->dev);

@@ -131,6 +131,11 @@ fifa_status fact_enqueue(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev);
 // and FP32 copy.  fact_ungrouped_from: the first level of part 0's range.
 fifa_status fact_enqueue_part(fifa_ctx* ctx, fifa_fact* F, const HmatDesc* Hdev, int part);
 int fact_ungrouped_from(const Plan* P);
+// W^-1 v (one vector, FP64 factor) in two launches: part 0 = leaves and the
+// fused sweep's CTA-local levels (independent CTAs), part 1 = the levels above
+// (one cooperative launch); the same arithmetic as the one-launch sweep.
+bool sweep_inverse_split_ok(const Plan* P);
+fifa_status sweep_inverse_part_enqueue(fifa_ctx* ctx, const fifa_fact* F, double* v, int part);
 // F32_0 (nullable): the problems' FP32 copies, refreshed after the factorization.
 fifa_status fact_enqueue_batched(fifa_ctx* ctx, Plan* P, FactDesc* F0, const HmatDesc* H0, int nprob,
                                  void* scratch0, size_t sstride, const FactDesc* F32_0 = nullptr);

@@ -23,7 +23,8 @@ struct fifa_chain {
   bool overlap = false;
   void* scratch_prop = nullptr;
   cudaStream_t draw_stream = nullptr, prop_stream = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_aca = nullptr, ev_join_draw = nullptr, ev_join_prop = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_aca = nullptr, ev_draw_done = nullptr, ev_join_draw = nullptr,
+              ev_join_prop = nullptr;
   ChainDev* dev = nullptr;
   ChainDev init{};
   uint64_t iter_host = 0;

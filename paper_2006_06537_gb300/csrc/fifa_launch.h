@@ -47,7 +47,10 @@ cudaError_t launch_sweep_level(const FactDesc* Fd, int prec, int lvl, int nodes,
 #define FS_CTAS_MAX 1024
 int sweep_fused_coresident(int prec, int rows, int cap);
 // mode 0: W v, 1: W^-1 v, 2: W^T v, 3: W^-T v, 4: W^-T W^-1 v (both inverse sweeps
-// in one launch).  Arithmetic in the factor's storage precision (prec 1: FP32).
+// in one launch); mode 1 in two launches with the same arithmetic: 5 = its
+// leaves and levels >= ls (CTAs independent, launched non-cooperatively; reads
+// only those levels of the factor), then 6 = its levels < ls.  Arithmetic in
+// the factor's storage precision (prec 1: FP32).
 cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, int cap, double* v, int nrhs,
                                int mode, double* part, unsigned int* bar, int* abort_flag, cudaStream_t st,
                                const int* active = nullptr);

@@ -902,6 +902,12 @@ __global__ void __launch_bounds__(256, 4) k_sweep_fused(const FactDesc* __restri
   };
   if (mode == 1 || mode == 2) {
     up(mode);
+  } else if (mode == 5) {  // W^-1's leaves and levels >= ls only (no grid barrier)
+    local_up(1, 1, 0);
+  } else if (mode == 6) {  // W^-1's levels < ls only, on v that mode 5 left
+    for (int l = ls - 1; l >= 0 && ok; --l)
+      ok = fs_global_level<T, NR>(Fd, l, ls, c, vs, rows, S, E, 1, 0, part, phase & 1, bar, phase, abort_flag, sh,
+                                  l - 1);
   } else if (mode == 4) {
     up(1);
     if (ok) down(3);
@@ -985,7 +991,7 @@ cudaError_t launch_sweep_fused(const FactDesc* Fd, int prec, int ls, int rows, i
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
+  attr[0].val.cooperative = mode == 5 ? 0 : 1;  // mode 5's CTAs never wait on each other
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (prec)

@@ -3,8 +3,9 @@ on a second stream beside Algorithm 1's draw) against the same chain in serial
 order.
 
 The overlapped iteration launches the same kernels with the same sizes on the
-same data; only their order across the two streams differs, and no kernel of
-one stream reads what the other writes before the join.  So every trace field
+same data (W'^-1 f, for q', may run as two launches with the one-launch
+arithmetic); only their order across the streams differs, and no kernel of
+one stream reads what another writes before they are joined.  So every trace field
 (sigma2, tau2, rho, log alpha, acceptances, residuals), the draw f and the
 posterior mean must agree bit for bit with the serial chain, in FP64 and in
 mixed precision, for a size with CTA groups at the top levels (grouped ACA and
@@ -75,8 +76,9 @@ def test_overlap_matches_serial_bitwise(recipe, n, leaf, rho0, nugget, prec):
     assert np.array_equal(a[2].view(np.uint64), b[2].view(np.uint64))
     assert np.all(np.isfinite(b[0]))
     # the overlapped graph has the serial graph's kernels (the propose kernel
-    # moved, nothing added or dropped)
-    assert a[3] == b[3] and a[3] > 0
+    # moved, nothing dropped), plus one where W'^-1 f is split around the
+    # grouped levels (two launches of the one-launch sweep's arithmetic)
+    assert a[3] > 0 and b[3] in (a[3], a[3] + 1)
 
 
 def test_overlap_with_independent_ctas():
